@@ -1,0 +1,304 @@
+"""Benchmark of the particle BP update (predict + update per step) on GB300.
+
+Default workload: 64 potential features (LoS + 63 surfaces, held fixed: no birth,
+no pruning), 100000 particles per belief, J = 4 PAs with 4 x 4 URAs and 10
+frequency bins (Nz = 160), 20 dB SNR, visibility 0.8, 200 spurious paths per step.
+Metric: (particle, PA) updates per second = P * J / step time (each step updates
+every particle of every belief against every PA's observation).
+
+    python bench.py [--gpus N] [--steps K] [--warmup W] [--impl gpu|reference]
+
+One JSON line is printed by rank 0.  N > 1 runs N independent replicas (one per
+GPU, weak scaling; the method has no cross-replica exchange).
+"""
+from __future__ import annotations
+
+import argparse
+import json
+import math
+import os
+import statistics
+import subprocess
+import sys
+import threading
+import time
+
+import numpy as np
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+from paper_2604_19723_gb300 import workload as W  # noqa: E402
+
+METRIC = "particle-measurement updates/sec and steps/sec at matched OSPA vs plain FP32 GPU"
+UNIT = "(particle, PA) updates/s"
+FP32_LANES_PER_SM = 128
+SMS = 152
+
+
+def kappa_flops(P, S, J, Nz):
+    """Algorithmic FP32 flops of one launch of the PF likelihood kernel: per (p, s, j)
+    two passes over Nz elements against S-1 basis columns (+ the residual column),
+    8 flops per complex multiply-add, plus the (S-1)^2/2 triangular solve."""
+    per = 8 * Nz * S + 8 * Nz * (S - 1) + 8 * (S - 1) * S / 2 + 40 * Nz
+    return float(P) * S * J * per
+
+
+class ClockSampler:
+    """nvidia-smi sampling of SM clock and throttle reasons during the timed region."""
+
+    Q = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+         "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+         "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, index: int):
+        self.index = index
+        self.rows = []
+        self.proc = None
+
+    def __enter__(self):
+        try:
+            self.proc = subprocess.Popen(["nvidia-smi", "-i", str(self.index), f"--query-gpu={self.Q}",
+                                          "--format=csv,noheader,nounits", "-lms", "200"],
+                                         stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
+            self.thread = threading.Thread(target=self._read, daemon=True)
+            self.thread.start()
+        except (OSError, FileNotFoundError):
+            self.proc = None
+        return self
+
+    def _read(self):
+        for line in self.proc.stdout:
+            self.rows.append([t.strip() for t in line.split(",")])
+
+    def __exit__(self, *a):
+        if self.proc:
+            self.proc.terminate()
+            try:
+                self.proc.wait(timeout=5)
+            except subprocess.TimeoutExpired:
+                self.proc.kill()
+
+    def summary(self):
+        if not self.rows:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["unsampled"]}
+        sm = [float(r[1]) for r in self.rows if len(r) > 8 and r[1].replace(".", "").isdigit()]
+        mx = [float(r[2]) for r in self.rows if len(r) > 8 and r[2].replace(".", "").isdigit()]
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        reasons = set()
+        for r in self.rows:
+            for i, n in enumerate(names):
+                if len(r) > 5 + i and r[5 + i].strip().lower() == "active":
+                    reasons.add(n)
+        return {"sm_mhz": statistics.median(sm) if sm else None, "sm_max_mhz": max(mx) if mx else None,
+                "reasons": sorted(reasons), "samples": len(self.rows)}
+
+
+def make_inputs(name, steps, seed_offset=0):
+    wl = W.workload(name)
+    g, prm = wl["geom"], wl["params"]
+    scn = W.make_scenario(g, prm, N=steps + 1, K=wl["K"], seed=wl["seed"] + seed_offset, snr_db=wl["snr_db"],
+                          visibility=wl["visibility"], clutter_mean=wl["clutter_mean"])
+    return wl, g, prm, scn
+
+
+def measured_peaks():
+    try:
+        with open(os.path.join(ROOT, "MEASURED_PEAKS.json")) as f:
+            return json.load(f)
+    except OSError:
+        return {}
+
+
+def cpu_baseline(wl, g, prm, scn, sample_P, z_host):
+    """The FP64 oracle (as it stands) on the host cores: one predict + update of a
+    bounded particle sample of the same workload (same S, J, Nz)."""
+    from oracle import beliefs, messages_woodbury, model
+    S = wl["fixed_S"] or (wl["K"] + 1)
+    st = W.state_near_truth(scn, P=sample_P, S=S, n=0, seed=wl["seed"] + 7, eta_true=float(np.mean(np.abs(z_host[0]) ** 2)) / 100,
+                            pos_std=0.01, sfv_std=0.01)
+    t0 = time.perf_counter()
+    pred = model.predict(st, prm, g.J, seed=wl["seed"], S_max=wl["fixed_S"] or wl["S_max"])
+    msg = messages_woodbury.update_messages(pred, prm, g, z_host[0].astype(np.complex128))
+    beliefs.beliefs(pred, msg)
+    dt = time.perf_counter() - t0
+    try:
+        from threadpoolctl import threadpool_info
+        cores = max([i.get("num_threads", 1) for i in threadpool_info()] + [1])
+    except Exception:
+        cores = os.cpu_count() or 1
+    return {"value": sample_P * g.J / dt, "unit": UNIT, "cores": cores, "kind": "oracle",
+            "sample": f"one predict+update of {sample_P} particles x S={S} x J={g.J} x Nz={g.Nz} "
+                      f"(FP64 Woodbury-mode oracle, {dt:.2f} s)"}
+
+
+def run_reference(args, rank):
+    """Reference arm: the FP64 oracle on the host cores, bounded sample per step."""
+    if rank != 0:
+        return
+    wl, g, prm, scn = make_inputs(args.workload, args.warmup + args.steps)
+    from oracle import synth
+    eta = synth.noise_variance(scn)
+    zs = [synth.observe(scn, n, eta, 17) for n in range(1, args.warmup + args.steps + 1)]
+    from oracle import beliefs, messages_woodbury, model
+    S = wl["fixed_S"] or (wl["K"] + 1)
+    Ps = args.ref_particles
+    st = W.state_near_truth(scn, P=Ps, S=S, n=0, seed=wl["seed"] + 7, eta_true=eta, pos_std=0.01, sfv_std=0.01)
+    times = []
+    for i in range(args.warmup + args.steps):
+        t0 = time.perf_counter()
+        pred = model.predict(st, prm, g.J, seed=wl["seed"], S_max=wl["fixed_S"] or wl["S_max"])
+        msg = messages_woodbury.update_messages(pred, prm, g, zs[i])
+        beliefs.beliefs(pred, msg)
+        if i >= args.warmup:
+            times.append(time.perf_counter() - t0)
+    t = float(np.mean(times))
+    value = Ps * g.J / t
+    cores = os.cpu_count() or 1
+    out = {"metric": METRIC, "value": value, "unit": UNIT, "n_gpus": args.gpus, "steps": args.steps,
+           "warmup": args.warmup, "ms_per_step": 1e3 * t, "higher_is_better": True, "scaling": "weak",
+           "vs_baseline": None, "dtype": "f64", "data": "synthetic", "impl": "reference",
+           "config": {"workload": f"{args.workload} (oracle sample of {Ps} particles per step)",
+                      "P": Ps, "S": S, "J": g.J, "Nz": g.Nz},
+           "cpu_baseline": {"value": value, "unit": UNIT, "cores": cores, "kind": "oracle",
+                            "sample": f"{Ps} particles per step, FP64 Woodbury-mode oracle"},
+           "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
+    print(json.dumps(out))
+
+
+def run_gpu(args, rank, world):
+    import torch
+    from paper_2604_19723_gb300 import bp
+    dev = int(os.environ.get("LOCAL_RANK", 0))
+    torch.cuda.set_device(dev)
+    total_steps = args.warmup + args.steps
+    wl, g, prm, scn = make_inputs(args.workload, 2 * total_steps, seed_offset=rank)
+    P = args.particles or wl["P"]
+    S = wl["fixed_S"] or (wl["K"] + 1)
+    S_max = wl["fixed_S"] or wl["S_max"]
+    stream = torch.cuda.Stream()
+    x_pos, sfv, rho, cc, cs, cr = bp.scenario_arrays(scn, range(1, 2 * total_steps + 1))
+    with torch.cuda.stream(stream):
+        z_all, eta = bp.synthesize(g, x_pos, sfv, rho, cc, cs, cr, snr_db=wl["snr_db"], seed=wl["seed"] + 11,
+                                   step0=1, stream=stream)
+    stream.synchronize()
+    st = W.state_near_truth(scn, P=P, S=S, n=0, seed=wl["seed"] + 5, eta_true=eta, pos_std=0.01, sfv_std=0.01)
+    f = bp.Filter(g, prm, P=P, S_max=S_max, seed=wl["seed"], stream=stream)
+    f.set_state(st)
+    flush = torch.empty(256 * 1024 * 1024 // 4, dtype=torch.float32, device="cuda")
+    for i in range(args.warmup):
+        f.step(z_all[i])
+    stream.synchronize()
+    f.set_profiling(True)
+    ev0 = [torch.cuda.Event(enable_timing=True) for _ in range(args.steps)]
+    ev1 = [torch.cuda.Event(enable_timing=True) for _ in range(args.steps)]
+    kappa_ms, prof_tot = [], {}
+    l0 = f.launch_count()
+    if world > 1:
+        torch.distributed.barrier()
+    torch.cuda.synchronize()
+    with ClockSampler(dev) as clk:
+        for i in range(args.steps):
+            with torch.cuda.stream(stream):
+                flush.fill_(float(i))              # L2 flush between timed steps (256 MB > 129 MB L2)
+                ev0[i].record(stream)
+                f.step(z_all[args.warmup + i])
+                ev1[i].record(stream)
+            pr = f.profile()                       # events recorded by the library on its stream
+            kappa_ms.append(pr["kappa"])
+            for k, v in pr.items():
+                prof_tot[k] = prof_tot.get(k, 0.0) + v
+        torch.cuda.synchronize()
+    launches = f.launch_count() - l0
+    f.set_profiling(False)
+    step_ms = [a.elapsed_time(b) for a, b in zip(ev0, ev1)]
+    t_step = float(np.mean(step_ms))
+    if world > 1:
+        tt = torch.tensor([t_step], device="cuda")
+        torch.distributed.all_reduce(tt, op=torch.distributed.ReduceOp.MAX)
+        t_step = float(tt.item())
+    value = world * P * g.J / (t_step * 1e-3)
+
+    # end to end through the public API: host (pinned) observations copied in every
+    # step, estimates copied out every step
+    zh = z_all[total_steps:total_steps + args.steps].cpu().pin_memory()
+    zd = torch.empty_like(z_all[0])
+    e2e_times = []
+    torch.cuda.synchronize()
+    for i in range(args.steps):
+        e_a = torch.cuda.Event(enable_timing=True)
+        e_b = torch.cuda.Event(enable_timing=True)
+        with torch.cuda.stream(stream):
+            flush.fill_(float(i))
+            e_a.record(stream)
+            zd.copy_(zh[i], non_blocking=True)
+            f.step(zd)
+            est = f.estimate()                     # synchronous D2H of the estimates
+            e_b.record(stream)
+        stream.synchronize()
+        e2e_times.append(e_a.elapsed_time(e_b))
+    t_e2e = float(np.mean(e2e_times))
+    if world > 1:
+        tt = torch.tensor([t_e2e], device="cuda")
+        torch.distributed.all_reduce(tt, op=torch.distributed.ReduceOp.MAX)
+        t_e2e = float(tt.item())
+    h2d = g.J * g.Nz * 8
+    d2h = 8 * (12 + g.J + 9 * S_max + S_max * g.J)
+
+    clocks = clk.summary()
+    peaks = measured_peaks()
+    sm_mhz = clocks.get("sm_mhz") or peaks.get("sm_max_mhz", 2070.0)
+    peak_alu = SMS * FP32_LANES_PER_SM * 2 * sm_mhz * 1e6 / 1e12
+    k_ms = float(np.mean(kappa_ms))
+    achieved = kappa_flops(P, S, g.J, g.Nz) / (k_ms * 1e-3) / 1e12
+    out = {"metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
+           "warmup": args.warmup, "ms_per_step": t_step, "steps_per_s": 1e3 / t_step,
+           "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f32",
+           "data": "synthetic (generative signal model of the paper, seeded)",
+           "config": {"workload": args.workload, "P": P, "S": S, "J": g.J, "Nz": g.Nz,
+                      "clutter_per_step": wl["clutter_mean"], "visibility": wl["visibility"],
+                      "l2": "flushed between timed steps (256 MB write)", "parallelism": f"replicas x{world}"},
+           "stage_ms": {k: v / args.steps for k, v in prof_tot.items()},
+           "roofline": {"bound": "alu", "kernel": "k_kappa", "achieved": achieved, "peak": peak_alu,
+                        "unit": "TFLOP/s", "frac": achieved / peak_alu, "traffic": None,
+                        "peak_basis": f"FP32 FMA lanes: {SMS} SMs x {FP32_LANES_PER_SM} x 2 flop x {sm_mhz:.0f} MHz (median sampled)"},
+           "e2e": {"value": world * P * g.J / (t_e2e * 1e-3), "unit": UNIT, "h2d_bytes_per_step": h2d,
+                   "d2h_bytes_per_step": d2h, "ms_per_step": t_e2e},
+           "gpu_launches": int(launches), "clocks": clocks}
+    if rank == 0 and not args.no_cpu_baseline:
+        out["cpu_baseline"] = cpu_baseline(wl, g, prm, scn, args.cpu_particles, z_all[:1].cpu().numpy())
+    f.close()
+    if rank == 0:
+        print(json.dumps(out))
+
+
+def main():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=10)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", default="gpu", choices=["gpu", "reference"])
+    ap.add_argument("--workload", default="scale_64x100k")
+    ap.add_argument("--particles", type=int, default=0)
+    ap.add_argument("--cpu-particles", type=int, default=64)
+    ap.add_argument("--ref-particles", type=int, default=48)
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    args = ap.parse_args()
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    if args.impl == "reference":
+        if world > 1 and rank != 0:
+            return
+        run_reference(args, rank)
+        return
+    if world > 1:
+        import torch
+        torch.distributed.init_process_group("nccl")
+    run_gpu(args, rank, world)
+    if world > 1:
+        import torch
+        torch.distributed.destroy_process_group()
+
+
+if __name__ == "__main__":
+    main()

@@ -1,0 +1,206 @@
+/*
+ * bp.h -- C ABI of the GB300 particle-based BP update for direct multipath SLAM
+ * ("Soft-Coherent Direct Multipath SLAM", arXiv 2604.19723).
+ *
+ * One handle holds one filter: P particles per belief for the mobile terminal
+ * (MT) state x_n = [p; v] in R^6, for each potential feature (PF)
+ * phi_s = [p_sfv (3), gamma, mu (complex)] and for each physical anchor's (PA)
+ * noise variance eta^(j), plus the PR existence probabilities p(r_s^(j) = 1).
+ * All device memory is allocated by bp_init and released by bp_free.  Every
+ * call is asynchronous on the handle's CUDA stream unless stated otherwise.
+ *
+ * Conventions
+ *   - Complex arrays are interleaved (re, im).  Observations z^(j) are
+ *     complex FP32, layout [J][Nf][My][Mz] with flat element index
+ *     k = f*(My*Mz) + y*Mz + m (the Kronecker order of Sec. II-B,
+ *     eq. unit-modulus-array-response).
+ *   - Particles are FP32 structure-of-arrays, weights FP64.
+ *   - PF slot 0 is the line-of-sight (LoS) component; its p_sfv is unused.
+ *   - Host pointers are read (or written) only during the call.
+ *   - No C++ exception crosses this ABI.  Every entry returns a bp_status;
+ *     bp_last_error() returns the text of the last failure on a handle.
+ *
+ * Error behaviour: invalid sizes/pointers -> BP_ERR_INVALID_ARG (nothing
+ * launched); CUDA runtime failure -> BP_ERR_CUDA; PF capacity exhausted by
+ * births -> the birth is skipped and counted (bp_estimate reports it);
+ * all particle weights underflow -> BP_ERR_NUMERIC reported by the next
+ * synchronising call (bp_estimate / bp_get_state).
+ */
+#ifndef BP_H
+#define BP_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef struct bp_handle bp_handle;
+
+typedef enum {
+    BP_OK = 0,
+    BP_ERR_INVALID_ARG = 1,
+    BP_ERR_CUDA = 2,
+    BP_ERR_CAPACITY = 3,
+    BP_ERR_NUMERIC = 4,
+    BP_ERR_TIMEOUT = 5,
+    BP_ERR_STATE = 6
+} bp_status;
+
+/* Array and signal constants (Sec. II-B).  f_k = -B/2 + k B/(Nf-1).
+ * R_pa: J rotation matrices, row-major 3x3, columns = local PA axes in
+ * global coordinates (local vector r' = R^T r, eq. rangep).  p_y, p_z:
+ * template URA element positions, symmetric about 0.
+ * Limits: 1 <= J <= 16, Nf <= 64, My <= 16, Mz <= 16, Nz <= 2048. */
+typedef struct {
+    int J, Nf, My, Mz;
+    double fc, c, B;
+    const double* p_pa;   /* J x 3 */
+    const double* R_pa;   /* J x 3 x 3 */
+    const double* p_y;    /* My */
+    const double* p_z;    /* Mz */
+} bp_geometry;
+
+/* Filter parameters (Sec. III-B, Sec. V).  motion_dims = 3 (3-D NCV) or 2
+ * (planar: z and v_z held).  Q births per step (0 = no birth), T_pru = 0
+ * disables pruning.  zero_mean = 1 selects the ZM variant (mu == 0).
+ * mvec_scaling = 0 uses the m-vectors exactly as printed in Supplementary
+ * Sec. S-V; 1 takes the square root of the existence factors.  regularize
+ * = 1 applies the Gaussian-kernel jitter after resampling. */
+typedef struct {
+    double T, sigma_v;
+    int motion_dims;
+    double c_eta, c_gamma, sigma_mu, sigma_sfv;
+    double pS, pS_pr, pR_pr, pB_pr, mu_B;
+    int Q;
+    double T_dec, T_pru, gamma_max, mu_max, eta_min, eta_max;
+    double p_min[3], p_max[3], v_max[3];
+    int zero_mean, mvec_scaling, regularize;
+} bp_params;
+
+/* Host view of a filter state (bp_get_state / bp_set_state) or of the
+ * prediction messages (bp_get_predicted / bp_set_predicted).  Sizes use the
+ * handle's P, S_max, J; only the first S PF slots are read or written.
+ *   x     6 x P          float   MT particles [px py pz vx vy vz]
+ *   phi   S x 6 x P      float   PF particles [px py pz gamma mu_re mu_im]
+ *   eta   J x P          float   noise-variance particles
+ *   w_x   P              double  belief weights w_x     (predicted: w_beta)
+ *   w_y   S x P          double  PF weights, sum = p_s  (predicted: w_alpha)
+ *   w_eta J x P          double  eta weights            (predicted: w_xi)
+ *   p_pr  S x J          double  p(r_s^(j) = 1)         (predicted: zeta_s^(j)(1)) */
+typedef struct {
+    int n;      /* index of the last completed step (predicted: current step) */
+    int S;      /* number of PFs including the LoS */
+    float* x;
+    float* phi;
+    float* eta;
+    double* w_x;
+    double* w_y;
+    double* w_eta;
+    double* p_pr;
+} bp_state_view;
+
+/* MMSE estimates and declarations (Sec. II-C, eq. stateHat, etanHat,
+ * PFphiHat).  Arrays are caller-owned: eta_hat[J], p_s[S_max],
+ * phi_hat[S_max*6], p_pr[S_max*J], declared[S_max]. */
+typedef struct {
+    int n;               /* step the estimate belongs to */
+    int S;               /* PFs before pruning (valid entries in the arrays) */
+    int S_next;          /* PFs kept for the next step */
+    int births_skipped;  /* births dropped because S_max was reached (cumulative) */
+    double x_hat[6];
+    double ess_x;        /* 1 / sum w_x^2 */
+    double* eta_hat;
+    double* p_s;
+    double* phi_hat;
+    double* p_pr;
+    int* declared;
+} bp_estimate_out;
+
+/* Creates a filter: validates, copies the geometry and parameters, allocates
+ * the device state for P particles per belief and up to S_max PFs
+ * (S_max <= 64), and draws the time-0 beliefs of Sec. V-A (MT from the
+ * uniform box, eta from U(eta_min, eta_max), the LoS like a new PF).
+ * cuda_stream: a cudaStream_t (NULL = legacy default stream).
+ * seed selects the Philox4x32-10 key.  Synchronous. */
+bp_status bp_init(const bp_geometry* geom, const bp_params* params, int P, int S_max,
+                  uint64_t seed, void* cuda_stream, bp_handle** out);
+
+/* Phase (i) of the message schedule (Sec. IV): prediction messages beta, xi,
+ * alpha, zeta of every belief (Sec. IV-D, eq. PR-prediction-PDF, eq. zeta)
+ * plus Q birth PFs drawn from f_B (Sec. III-B2, IV-D). */
+bp_status bp_predict(bp_handle* h);
+
+/* Phases (ii)-(iii) and the belief update (Sec. IV-C/D, Supplementary S-III
+ * to S-VI): message table, per-(s,j) existence tests, per-particle
+ * likelihoods, FP64 normalisation, estimates, pruning, systematic
+ * resampling and regularisation.  z_dev: device pointer to the J x Nz
+ * complex FP32 observations of this step, borrowed for the call's
+ * duration on the handle's stream. */
+bp_status bp_update(bp_handle* h, const float* z_dev);
+
+/* Copies the estimates of the last bp_update to the host.  Synchronous. */
+bp_status bp_estimate(bp_handle* h, bp_estimate_out* out);
+
+/* Releases every device buffer of the handle.  Synchronous. */
+bp_status bp_free(bp_handle* h);
+
+/* Text of the last error on h (or of the last bp_init failure if h is NULL). */
+const char* bp_last_error(const bp_handle* h);
+
+/* State export / import (checkpoint and resume, parity tests).  Synchronous. */
+bp_status bp_get_state(bp_handle* h, bp_state_view* out);
+bp_status bp_set_state(bp_handle* h, const bp_state_view* in);
+
+/* Prediction-message export / import: bp_set_predicted puts the handle in
+ * the state reached after bp_predict, so that bp_update runs from the given
+ * particles and weights.  Synchronous. */
+bp_status bp_get_predicted(bp_handle* h, bp_state_view* out);
+bp_status bp_set_predicted(bp_handle* h, const bp_state_view* in);
+
+/* Diagnostics of the last bp_update, copied to host memory (synchronous).
+ * what = BP_DIAG_TABLE: S x J x Nz complex double for each of
+ *        m, m^w, mu3, mu4 (in that order), then W_s (S), eta_bar (J);
+ *        bytes = (4*S*J*Nz*2 + S + J) * 8.
+ * what = BP_DIAG_WEIGHTS: normalised weights before resampling:
+ *        w_x (P), w_y (S x P), w_eta (J x P), p_s (S), p_pr (S x J), all double.
+ * what = BP_DIAG_LOGLIK: particle log-likelihood sums: log iota (P) summed over
+ *        j, Delta_kappa (S x P) summed over j (log kappa~(phi,1) - log kappa~(.,0)),
+ *        log nu (J x P), log omega~(1)-log omega~(0) (S x J); double.
+ * what = BP_DIAG_INDICES: resampling indices, int32: MT (P), PF (S x P), eta (J x P). */
+enum { BP_DIAG_TABLE = 1, BP_DIAG_WEIGHTS = 2, BP_DIAG_LOGLIK = 3, BP_DIAG_INDICES = 4 };
+bp_status bp_get_diag(bp_handle* h, int what, void* host, size_t bytes);
+
+/* Synthetic observations from the generative model (eq. observation-generative),
+ * for tests and benchmarks.  For each of n_steps steps t: MT position
+ * x_pos[t*3..], K surfaces with SFVs sfv[K*3] and complex amplitudes
+ * rho[((t*J + j)*(K+1) + k)*2] (k = 0 the LoS, 0 for an invisible path),
+ * plus clutter_count[t] spurious paths with SFVs clutter_sfv and amplitudes
+ * clutter_rho[(c*J + j)*2] (concatenated over t).  The noise variance is
+ * eta = P^ch / 10^(snr_db/10) with P^ch the sum-channel power of the first
+ * step (Sec. V-A); it is returned in *eta_out.  Noise uses Philox draws of
+ * step index step0 + t.  z_dev: device, n_steps x J x Nz complex FP32.
+ * Synchronous. */
+bp_status bp_synthesize(const bp_geometry* geom, int n_steps, int step0, const double* x_pos,
+                        int K, const double* sfv, const double* rho,
+                        const int* clutter_count, const double* clutter_sfv, const double* clutter_rho,
+                        double snr_db, uint64_t seed, float* z_dev, double* eta_out, void* cuda_stream);
+
+/* Number of kernels launched by this handle since bp_init (instrumentation). */
+long long bp_launch_count(const bp_handle* h);
+
+/* Per-stage timing with CUDA events recorded on the handle's stream
+ * (instrumentation, off by default).  bp_get_profile waits for the last
+ * bp_predict / bp_update and writes the duration in milliseconds of each
+ * stage of those calls into ms[0 .. BP_PROF_STAGES-1]:
+ * predict, row sums, message table, table stage (Gram, kappa/omega, nu),
+ * kappa likelihood, iota likelihood, nu likelihood, normalisation, resampling. */
+enum { BP_PROF_STAGES = 9 };
+bp_status bp_set_profiling(bp_handle* h, int on);
+bp_status bp_get_profile(bp_handle* h, double* ms, int n);
+
+#ifdef __cplusplus
+}
+#endif
+#endif /* BP_H */

@@ -1,0 +1,333 @@
+"""Thin ctypes binding of libbp (include/bp.h).
+
+Argument marshalling only: every step of the filter runs in the CUDA library.
+PyTorch supplies device memory for observations and the CUDA stream.  There
+is no CPU fallback: if the library cannot be loaded, every entry point raises.
+"""
+from __future__ import annotations
+
+import ctypes as C
+import os
+from typing import Dict, Optional
+
+import numpy as np
+
+from .workload import Geometry, Params, StateArrays
+
+_HERE = os.path.dirname(os.path.abspath(__file__))
+LIB_PATH = os.path.join(_HERE, "_lib", "libbp.so")
+
+BP_OK = 0
+STATUS = {0: "BP_OK", 1: "BP_ERR_INVALID_ARG", 2: "BP_ERR_CUDA", 3: "BP_ERR_CAPACITY",
+          4: "BP_ERR_NUMERIC", 5: "BP_ERR_TIMEOUT", 6: "BP_ERR_STATE"}
+DIAG_TABLE, DIAG_WEIGHTS, DIAG_LOGLIK, DIAG_INDICES = 1, 2, 3, 4
+
+ENTRY_POINTS = ("bp_init", "bp_predict", "bp_update", "bp_estimate", "bp_free", "bp_last_error",
+                "bp_get_state", "bp_set_state", "bp_get_predicted", "bp_set_predicted", "bp_get_diag",
+                "bp_synthesize", "bp_launch_count", "bp_set_profiling", "bp_get_profile")
+PROFILE_STAGES = ("predict", "row_sums", "table", "stage", "kappa", "iota", "nu", "normalize", "resample")
+
+
+class BPError(RuntimeError):
+    def __init__(self, status: int, msg: str):
+        super().__init__(f"{STATUS.get(status, status)}: {msg}")
+        self.status = status
+
+
+class _Geometry(C.Structure):
+    _fields_ = [("J", C.c_int), ("Nf", C.c_int), ("My", C.c_int), ("Mz", C.c_int),
+                ("fc", C.c_double), ("c", C.c_double), ("B", C.c_double),
+                ("p_pa", C.POINTER(C.c_double)), ("R_pa", C.POINTER(C.c_double)),
+                ("p_y", C.POINTER(C.c_double)), ("p_z", C.POINTER(C.c_double))]
+
+
+class _Params(C.Structure):
+    _fields_ = [("T", C.c_double), ("sigma_v", C.c_double), ("motion_dims", C.c_int),
+                ("c_eta", C.c_double), ("c_gamma", C.c_double), ("sigma_mu", C.c_double), ("sigma_sfv", C.c_double),
+                ("pS", C.c_double), ("pS_pr", C.c_double), ("pR_pr", C.c_double), ("pB_pr", C.c_double),
+                ("mu_B", C.c_double), ("Q", C.c_int),
+                ("T_dec", C.c_double), ("T_pru", C.c_double), ("gamma_max", C.c_double), ("mu_max", C.c_double),
+                ("eta_min", C.c_double), ("eta_max", C.c_double),
+                ("p_min", C.c_double * 3), ("p_max", C.c_double * 3), ("v_max", C.c_double * 3),
+                ("zero_mean", C.c_int), ("mvec_scaling", C.c_int), ("regularize", C.c_int)]
+
+
+class _StateView(C.Structure):
+    _fields_ = [("n", C.c_int), ("S", C.c_int), ("x", C.POINTER(C.c_float)), ("phi", C.POINTER(C.c_float)),
+                ("eta", C.POINTER(C.c_float)), ("w_x", C.POINTER(C.c_double)), ("w_y", C.POINTER(C.c_double)),
+                ("w_eta", C.POINTER(C.c_double)), ("p_pr", C.POINTER(C.c_double))]
+
+
+class _Estimate(C.Structure):
+    _fields_ = [("n", C.c_int), ("S", C.c_int), ("S_next", C.c_int), ("births_skipped", C.c_int),
+                ("x_hat", C.c_double * 6), ("ess_x", C.c_double),
+                ("eta_hat", C.POINTER(C.c_double)), ("p_s", C.POINTER(C.c_double)),
+                ("phi_hat", C.POINTER(C.c_double)), ("p_pr", C.POINTER(C.c_double)),
+                ("declared", C.POINTER(C.c_int))]
+
+
+_lib = None
+
+
+def load() -> C.CDLL:
+    """Load libbp.so (built in-tree by ``paper_2604_19723_gb300.build``); raises if absent."""
+    global _lib
+    if _lib is not None:
+        return _lib
+    if not os.path.exists(LIB_PATH):
+        raise ImportError(f"libbp.so not built ({LIB_PATH}); run __graft_entry__.build()")
+    lib = C.CDLL(LIB_PATH)
+    vp = C.c_void_p
+    lib.bp_init.argtypes = [C.POINTER(_Geometry), C.POINTER(_Params), C.c_int, C.c_int, C.c_uint64, vp, C.POINTER(vp)]
+    lib.bp_predict.argtypes = [vp]
+    lib.bp_update.argtypes = [vp, vp]
+    lib.bp_estimate.argtypes = [vp, C.POINTER(_Estimate)]
+    lib.bp_free.argtypes = [vp]
+    lib.bp_last_error.argtypes = [vp]
+    lib.bp_last_error.restype = C.c_char_p
+    for f in ("bp_get_state", "bp_set_state", "bp_get_predicted", "bp_set_predicted"):
+        getattr(lib, f).argtypes = [vp, C.POINTER(_StateView)]
+    lib.bp_get_diag.argtypes = [vp, C.c_int, vp, C.c_size_t]
+    lib.bp_synthesize.argtypes = [C.POINTER(_Geometry), C.c_int, C.c_int, C.POINTER(C.c_double), C.c_int,
+                                  C.POINTER(C.c_double), C.POINTER(C.c_double), C.POINTER(C.c_int),
+                                  C.POINTER(C.c_double), C.POINTER(C.c_double), C.c_double, C.c_uint64,
+                                  vp, C.POINTER(C.c_double), vp]
+    lib.bp_set_profiling.argtypes = [vp, C.c_int]
+    lib.bp_get_profile.argtypes = [vp, C.POINTER(C.c_double), C.c_int]
+    lib.bp_launch_count.argtypes = [vp]
+    lib.bp_launch_count.restype = C.c_longlong
+    for f in ENTRY_POINTS:
+        if f not in ("bp_last_error", "bp_launch_count"):
+            getattr(lib, f).restype = C.c_int
+    _lib = lib
+    return lib
+
+
+def _dptr(a: np.ndarray):
+    return a.ctypes.data_as(C.POINTER(C.c_double))
+
+
+def _fptr(a: np.ndarray):
+    return a.ctypes.data_as(C.POINTER(C.c_float))
+
+
+class _GeomHolder:
+    """Keeps the host arrays referenced by a _Geometry alive."""
+
+    def __init__(self, g: Geometry):
+        self.arrs = [np.ascontiguousarray(np.asarray(a, np.float64)) for a in (g.p_pa, g.R_pa, g.p_y, g.p_z)]
+        self.s = _Geometry(g.J, g.Nf, g.My, g.Mz, g.fc, g.c, g.B, *[_dptr(a) for a in self.arrs])
+
+
+def _params_struct(p: Params) -> _Params:
+    return _Params(p.T, p.sigma_v, p.motion_dims, p.c_eta, p.c_gamma, p.sigma_mu, p.sigma_sfv,
+                   p.pS, p.pS_pr, p.pR_pr, p.pB_pr, p.mu_B, p.Q, p.T_dec, p.T_pru, p.gamma_max, p.mu_max,
+                   p.eta_min, p.eta_max, (C.c_double * 3)(*p.p_min), (C.c_double * 3)(*p.p_max),
+                   (C.c_double * 3)(*p.v_max), p.zero_mean, p.mvec_scaling, p.regularize)
+
+
+def _check(lib, h, status, what):
+    if status != BP_OK:
+        msg = lib.bp_last_error(h)
+        raise BPError(status, f"{what}: {msg.decode() if msg else ''}")
+
+
+def _stream_handle(stream) -> Optional[int]:
+    if stream is None:
+        import torch
+        return torch.cuda.current_stream().cuda_stream
+    return int(getattr(stream, "cuda_stream", stream))
+
+
+class Filter:
+    """One particle BP filter on the GPU (handle of the C ABI)."""
+
+    def __init__(self, geom: Geometry, params: Params, P: int, S_max: int, seed: int, stream=None):
+        self.lib = load()
+        self.geom, self.params, self.P, self.S_max = geom, params, P, S_max
+        self._g = _GeomHolder(geom)
+        self._p = _params_struct(params)
+        self.stream = _stream_handle(stream)
+        h = C.c_void_p()
+        st = self.lib.bp_init(C.byref(self._g.s), C.byref(self._p), P, S_max, C.c_uint64(seed),
+                              C.c_void_p(self.stream), C.byref(h))
+        _check(self.lib, None, st, "bp_init")
+        self.h = h
+
+    # -- lifecycle ---------------------------------------------------------
+    def close(self):
+        if getattr(self, "h", None):
+            self.lib.bp_free(self.h)
+            self.h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    # -- steps ---------------------------------------------------------------
+    def predict(self):
+        _check(self.lib, self.h, self.lib.bp_predict(self.h), "bp_predict")
+
+    def update(self, z):
+        """z: torch CUDA tensor of J x Nz complex64 (or J x Nz x 2 float32), contiguous."""
+        _check(self.lib, self.h, self.lib.bp_update(self.h, C.c_void_p(z.data_ptr())), "bp_update")
+
+    def step(self, z):
+        self.predict()
+        self.update(z)
+
+    def launch_count(self) -> int:
+        return int(self.lib.bp_launch_count(self.h))
+
+    def set_profiling(self, on: bool):
+        _check(self.lib, self.h, self.lib.bp_set_profiling(self.h, int(bool(on))), "bp_set_profiling")
+
+    def profile(self) -> Dict[str, float]:
+        """Durations (ms) of each stage of the last predict and update."""
+        ms = np.zeros(len(PROFILE_STAGES))
+        _check(self.lib, self.h, self.lib.bp_get_profile(self.h, _dptr(ms), len(ms)), "bp_get_profile")
+        return dict(zip(PROFILE_STAGES, ms.tolist()))
+
+    # -- host views --------------------------------------------------------------
+    def estimate(self) -> Dict:
+        J, SM = self.geom.J, self.S_max
+        eta = np.zeros(J); ps = np.zeros(SM); ph = np.zeros((SM, 6)); pr = np.zeros((SM, J))
+        dec = np.zeros(SM, np.int32)
+        e = _Estimate(0, 0, 0, 0, (C.c_double * 6)(), 0.0, _dptr(eta), _dptr(ps), _dptr(ph), _dptr(pr),
+                      dec.ctypes.data_as(C.POINTER(C.c_int)))
+        _check(self.lib, self.h, self.lib.bp_estimate(self.h, C.byref(e)), "bp_estimate")
+        S = e.S
+        return dict(n=e.n, S=S, S_next=e.S_next, births_skipped=e.births_skipped, x_hat=np.array(e.x_hat[:]),
+                    ess_x=e.ess_x, eta_hat=eta, p_s=ps[:S].copy(), phi_hat=ph[:S].copy(), p_pr=pr[:S].copy(),
+                    declared=dec[:S].astype(bool))
+
+    def _view(self, S):
+        J, P = self.geom.J, self.P
+        arrs = dict(x=np.zeros((6, P), np.float32), phi=np.zeros((S, 6, P), np.float32),
+                    eta=np.zeros((J, P), np.float32), w_x=np.zeros(P), w_y=np.zeros((S, P)),
+                    w_eta=np.zeros((J, P)), p_pr=np.zeros((S, J)))
+        return arrs
+
+    def _struct(self, n, S, a):
+        return _StateView(n, S, _fptr(a["x"]), _fptr(a["phi"]), _fptr(a["eta"]), _dptr(a["w_x"]), _dptr(a["w_y"]),
+                          _dptr(a["w_eta"]), _dptr(a["p_pr"]))
+
+    def get_state(self) -> StateArrays:
+        a = self._view(self.S_max)
+        v = self._struct(0, 0, a)
+        _check(self.lib, self.h, self.lib.bp_get_state(self.h, C.byref(v)), "bp_get_state")
+        S = v.S
+        return StateArrays(n=v.n, S=S, x=a["x"], phi=a["phi"][:S].copy(), eta=a["eta"], w_x=a["w_x"],
+                           w_y=a["w_y"][:S].copy(), w_eta=a["w_eta"], p_pr=a["p_pr"][:S].copy())
+
+    def set_state(self, st: StateArrays):
+        a = dict(x=np.ascontiguousarray(st.x, np.float32), phi=np.ascontiguousarray(st.phi, np.float32),
+                 eta=np.ascontiguousarray(st.eta, np.float32), w_x=np.ascontiguousarray(st.w_x, np.float64),
+                 w_y=np.ascontiguousarray(st.w_y, np.float64), w_eta=np.ascontiguousarray(st.w_eta, np.float64),
+                 p_pr=np.ascontiguousarray(st.p_pr, np.float64))
+        v = self._struct(st.n, st.S, a)
+        _check(self.lib, self.h, self.lib.bp_set_state(self.h, C.byref(v)), "bp_set_state")
+
+    def get_predicted(self) -> Dict:
+        a = self._view(self.S_max)
+        v = self._struct(0, 0, a)
+        _check(self.lib, self.h, self.lib.bp_get_predicted(self.h, C.byref(v)), "bp_get_predicted")
+        S = v.S
+        return dict(n=v.n, S=S, x=a["x"], phi=a["phi"][:S].copy(), eta=a["eta"], w_beta=a["w_x"],
+                    w_alpha=a["w_y"][:S].copy(), w_xi=a["w_eta"], zeta=a["p_pr"][:S].copy())
+
+    def set_predicted(self, n, S, x, phi, eta, w_beta, w_alpha, w_xi, zeta):
+        a = dict(x=np.ascontiguousarray(x, np.float32), phi=np.ascontiguousarray(phi, np.float32),
+                 eta=np.ascontiguousarray(eta, np.float32), w_x=np.ascontiguousarray(w_beta, np.float64),
+                 w_y=np.ascontiguousarray(w_alpha, np.float64), w_eta=np.ascontiguousarray(w_xi, np.float64),
+                 p_pr=np.ascontiguousarray(zeta, np.float64))
+        v = self._struct(n, S, a)
+        _check(self.lib, self.h, self.lib.bp_set_predicted(self.h, C.byref(v)), "bp_set_predicted")
+
+    def _diag(self, what, nbytes, dtype):
+        buf = np.zeros(nbytes // np.dtype(dtype).itemsize, dtype)
+        _check(self.lib, self.h, self.lib.bp_get_diag(self.h, what, buf.ctypes.data_as(C.c_void_p), nbytes),
+               "bp_get_diag")
+        return buf
+
+    def diag_table(self, S) -> Dict:
+        J, Nz = self.geom.J, self.geom.Nz
+        n = 4 * S * J * Nz * 2 + S + J
+        b = self._diag(DIAG_TABLE, n * 8, np.float64)
+        t = b[:4 * S * J * Nz * 2].reshape(4, S, J, Nz, 2)
+        t = t[..., 0] + 1j * t[..., 1]
+        o = 4 * S * J * Nz * 2
+        return dict(m=t[0], mw=t[1], mu3=t[2], mu4=t[3], W=b[o:o + S], eta_bar=b[o + S:o + S + J])
+
+    def diag_weights(self, S) -> Dict:
+        J, P = self.geom.J, self.P
+        n = P + S * P + J * P + S + S * J
+        b = self._diag(DIAG_WEIGHTS, n * 8, np.float64)
+        o = 0
+        w_x = b[o:o + P]; o += P
+        w_y = b[o:o + S * P].reshape(S, P); o += S * P
+        w_eta = b[o:o + J * P].reshape(J, P); o += J * P
+        p_s = b[o:o + S]; o += S
+        p_pr = b[o:o + S * J].reshape(S, J)
+        return dict(w_x=w_x, w_y=w_y, w_eta=w_eta, p_s=p_s, p_pr=p_pr)
+
+    def diag_loglik(self, S) -> Dict:
+        J, P = self.geom.J, self.P
+        n = P + S * P + J * P + S * J
+        b = self._diag(DIAG_LOGLIK, n * 8, np.float64)
+        o = 0
+        li = b[o:o + P]; o += P
+        lk = b[o:o + S * P].reshape(S, P); o += S * P
+        ln = b[o:o + J * P].reshape(J, P); o += J * P
+        lw = b[o:o + S * J].reshape(S, J)
+        return dict(log_iota=li, delta_kappa=lk, log_nu=ln, llr_omega=lw)
+
+    def diag_indices(self, S) -> Dict:
+        J, P = self.geom.J, self.P
+        n = P + S * P + J * P
+        b = self._diag(DIAG_INDICES, n * 4, np.int32)
+        return dict(x=b[:P], y=b[P:P + S * P].reshape(S, P), eta=b[P + S * P:].reshape(J, P))
+
+
+def synthesize(geom: Geometry, x_pos: np.ndarray, sfv: np.ndarray, rho: np.ndarray,
+               clutter_count=None, clutter_sfv=None, clutter_rho=None, snr_db: float = 20.0,
+               seed: int = 0, step0: int = 1, out=None, stream=None):
+    """Synthetic observations on the GPU (bp_synthesize).  x_pos (T, 3), sfv (K, 3),
+    rho (T, J, K+1) complex.  Returns (z as a torch CUDA tensor (T, J, Nz) complex64, eta)."""
+    import torch
+    lib = load()
+    g = _GeomHolder(geom)
+    T = x_pos.shape[0]
+    K = sfv.shape[0]
+    xp = np.ascontiguousarray(x_pos, np.float64)
+    sf = np.ascontiguousarray(sfv, np.float64).reshape(-1) if K else np.zeros(3)
+    rh = np.ascontiguousarray(np.stack([np.real(rho), np.imag(rho)], -1), np.float64)
+    cc = np.ascontiguousarray(np.zeros(T, np.int32) if clutter_count is None else clutter_count, np.int32)
+    cs = np.ascontiguousarray(np.zeros((1, 3)) if clutter_sfv is None or len(clutter_sfv) == 0 else clutter_sfv, np.float64)
+    cr_ = np.zeros((1, geom.J), complex) if clutter_rho is None or len(clutter_rho) == 0 else clutter_rho
+    cr = np.ascontiguousarray(np.stack([np.real(cr_), np.imag(cr_)], -1), np.float64)
+    if out is None:
+        out = torch.empty((T, geom.J, geom.Nz), dtype=torch.complex64, device="cuda")
+    eta = C.c_double()
+    st = lib.bp_synthesize(C.byref(g.s), T, step0, _dptr(xp), K, _dptr(sf), _dptr(rh),
+                           cc.ctypes.data_as(C.POINTER(C.c_int)), _dptr(cs), _dptr(cr), snr_db, C.c_uint64(seed),
+                           C.c_void_p(out.data_ptr()), C.byref(eta), C.c_void_p(_stream_handle(stream)))
+    _check(lib, None, st, "bp_synthesize")
+    return out, eta.value
+
+
+def scenario_arrays(scn, steps):
+    """Arrays of bp_synthesize for the given scenario steps (visibility folded into rho)."""
+    steps = list(steps)
+    J = scn.geom.J
+    K = scn.sfv_true.shape[0]
+    x_pos = np.stack([scn.x_true[n, :3] for n in steps])
+    rho = np.zeros((len(steps), J, K + 1), complex)
+    for t, n in enumerate(steps):
+        rho[t] = scn.rho_abs[None, :] * np.exp(1j * scn.rho_phase[n]) * scn.visible[n]
+    cc = np.array([scn.clutter_sfv[n].shape[0] for n in steps], np.int32)
+    cs = np.concatenate([scn.clutter_sfv[n] for n in steps]) if cc.sum() else np.zeros((0, 3))
+    cr = np.concatenate([scn.clutter_rho[n] for n in steps]) if cc.sum() else np.zeros((0, J), complex)
+    return x_pos, scn.sfv_true, rho, cc, cs, cr

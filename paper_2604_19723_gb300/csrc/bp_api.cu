@@ -1,0 +1,469 @@
+// C ABI of libbp (include/bp.h): handle management, validation, launches.
+#include <cstdio>
+#include <cstring>
+#include <cmath>
+#include <string>
+#include <vector>
+#include <algorithm>
+
+#include "bp_internal.cuh"
+#include "bp_kernels.cuh"
+
+using namespace bp;
+
+struct bp_handle {
+    DevGeom G;
+    DevParams Pm;
+    DevState D;
+    cudaStream_t st;
+    int P, S_max, J, Nz;
+    int SCA;            // column stride of the per-(s,j) basis buffers
+    int S;              // current number of PFs (host copy)
+    int S_upd;          // S of the last bp_update
+    int n;              // last completed step (state) or current step (predicted)
+    int phase;          // 0: belief state, 1: predicted
+    int births_skipped;
+    int nsplit_max;
+    long long launches;
+    // scratch
+    double* gram;
+    double* nu_b;
+    double* V64;
+    double* cdf;
+    double* wn;         // normalised weights before resampling: w_x (P) | w_y (S_max P) | w_eta (J P)
+    int* h_ctrl;        // pinned
+    double* h_est;      // pinned
+    int prof_on;
+    cudaEvent_t ev[BP_PROF_STAGES + 1];
+    bool ev_valid[BP_PROF_STAGES];
+    std::vector<void*> allocs;
+    std::string err;
+};
+
+static std::string g_init_error;
+
+static bp_status fail(bp_handle* h, bp_status s, const std::string& msg) {
+    if (h) h->err = msg; else g_init_error = msg;
+    return s;
+}
+
+static bp_status cuda_check(bp_handle* h, const char* where) {
+    const cudaError_t e = cudaGetLastError();
+    if (e != cudaSuccess) return fail(h, BP_ERR_CUDA, std::string(where) + ": " + cudaGetErrorString(e));
+    return BP_OK;
+}
+
+template <typename T>
+static bool dalloc(bp_handle* h, T** p, size_t count) {
+    void* q = nullptr;
+    if (cudaMalloc(&q, std::max<size_t>(count, 1) * sizeof(T)) != cudaSuccess) return false;
+    cudaMemsetAsync(q, 0, std::max<size_t>(count, 1) * sizeof(T), h->st);
+    h->allocs.push_back(q);
+    *p = static_cast<T*>(q);
+    return true;
+}
+
+static void mark(bp_handle* h, int stage) {
+    if (h->prof_on) cudaEventRecord(h->ev[stage], h->st);
+}
+
+static int sc_bucket(int S) { return S <= 8 ? 8 : S <= 16 ? 16 : S <= 32 ? 32 : 64; }
+
+static bp_status validate_geom(const bp_geometry* g) {
+    if (!g || !g->p_pa || !g->R_pa || !g->p_y || !g->p_z) return BP_ERR_INVALID_ARG;
+    if (g->J < 1 || g->J > J_MAX || g->Nf < 1 || g->Nf > NF_MAX || g->My < 1 || g->My > MY_MAX || g->Mz < 1 ||
+        g->Mz > MZ_MAX || g->Nf * g->My * g->Mz > NZ_MAX)
+        return BP_ERR_INVALID_ARG;
+    if (!(g->fc > 0) || !(g->c > 0) || !(g->B >= 0)) return BP_ERR_INVALID_ARG;
+    return BP_OK;
+}
+
+static void fill_geom(DevGeom& G, const bp_geometry* g) {
+    memset(&G, 0, sizeof(G));
+    G.J = g->J; G.Nf = g->Nf; G.My = g->My; G.Mz = g->Mz; G.Nz = g->Nf * g->My * g->Mz;
+    G.fc = g->fc; G.c = g->c; G.B = g->B; G.lam = g->c / g->fc;
+    for (int j = 0; j < g->J; ++j) {
+        for (int k = 0; k < 3; ++k) G.p_pa[j][k] = g->p_pa[3 * j + k];
+        for (int k = 0; k < 9; ++k) G.R[j][k] = g->R_pa[9 * j + k];
+    }
+    for (int f = 0; f < g->Nf; ++f) G.f[f] = (g->Nf == 1) ? 0.0 : -0.5 * g->B + f * (g->B / (g->Nf - 1));
+    for (int y = 0; y < g->My; ++y) G.py[y] = g->p_y[y];
+    for (int m = 0; m < g->Mz; ++m) G.pz[m] = g->p_z[m];
+}
+
+extern "C" {
+
+const char* bp_last_error(const bp_handle* h) { return h ? h->err.c_str() : g_init_error.c_str(); }
+
+long long bp_launch_count(const bp_handle* h) { return h ? h->launches : 0; }
+
+bp_status bp_init(const bp_geometry* geom, const bp_params* prm, int P, int S_max, uint64_t seed,
+                  void* cuda_stream, bp_handle** out) {
+    if (!out) return fail(nullptr, BP_ERR_INVALID_ARG, "out is NULL");
+    *out = nullptr;
+    if (validate_geom(geom) != BP_OK) return fail(nullptr, BP_ERR_INVALID_ARG, "invalid geometry");
+    if (!prm) return fail(nullptr, BP_ERR_INVALID_ARG, "params is NULL");
+    if (P < 1 || P > (1 << 28)) return fail(nullptr, BP_ERR_INVALID_ARG, "P out of range");
+    if (S_max < 1 || S_max > S_CAP_MAX) return fail(nullptr, BP_ERR_INVALID_ARG, "S_max must be in [1, 64]");
+    if (prm->c_eta < 1.0 || prm->c_gamma < 1.0) return fail(nullptr, BP_ERR_INVALID_ARG, "Gamma shapes must be >= 1");
+    if (prm->motion_dims != 2 && prm->motion_dims != 3) return fail(nullptr, BP_ERR_INVALID_ARG, "motion_dims must be 2 or 3");
+    if (prm->Q < 0 || !(prm->T > 0)) return fail(nullptr, BP_ERR_INVALID_ARG, "invalid Q or T");
+    bp_handle* h = new bp_handle();
+    h->st = static_cast<cudaStream_t>(cuda_stream);
+    fill_geom(h->G, geom);
+    DevParams& Pm = h->Pm;
+    memset(&Pm, 0, sizeof(Pm));
+    Pm.T = prm->T; Pm.sigma_v = prm->sigma_v; Pm.motion_dims = prm->motion_dims;
+    Pm.c_eta = prm->c_eta; Pm.c_gamma = prm->c_gamma; Pm.sigma_mu = prm->sigma_mu; Pm.sigma_sfv = prm->sigma_sfv;
+    Pm.pS = prm->pS; Pm.pS_pr = prm->pS_pr; Pm.pR_pr = prm->pR_pr; Pm.pB_pr = prm->pB_pr; Pm.mu_B = prm->mu_B;
+    Pm.Q = prm->Q;
+    const double mq = prm->mu_B / std::max(prm->Q, 1);
+    Pm.pB = mq / (1.0 + mq);
+    Pm.T_dec = prm->T_dec; Pm.T_pru = prm->T_pru; Pm.gamma_max = prm->gamma_max; Pm.mu_max = prm->mu_max;
+    Pm.eta_min = prm->eta_min; Pm.eta_max = prm->eta_max;
+    for (int k = 0; k < 3; ++k) { Pm.p_min[k] = prm->p_min[k]; Pm.p_max[k] = prm->p_max[k]; Pm.v_max[k] = prm->v_max[k]; }
+    Pm.zero_mean = prm->zero_mean; Pm.mvec_scaling = prm->mvec_scaling; Pm.regularize = prm->regularize;
+    Pm.key0 = (uint32_t)(seed & 0xFFFFFFFFu); Pm.key1 = (uint32_t)(seed >> 32);
+    Pm.P = P; Pm.S_max = S_max;
+    h->P = P; h->S_max = S_max; h->J = geom->J; h->Nz = h->G.Nz;
+    h->SCA = sc_bucket(S_max);
+    h->nsplit_max = 32;
+    const int J = geom->J, Nz = h->G.Nz, SCA = h->SCA;
+    const size_t PP = (size_t)P;
+    DevState& D = h->D;
+    memset(&D, 0, sizeof(D));
+    bool ok = true;
+    for (int b = 0; b < 2; ++b) {
+        ok &= dalloc(h, &D.x[b], 6 * PP);
+        ok &= dalloc(h, &D.phi[b], (size_t)S_max * 6 * PP);
+        ok &= dalloc(h, &D.eta[b], (size_t)J * PP);
+    }
+    ok &= dalloc(h, &D.w_x, PP);
+    ok &= dalloc(h, &D.w_y, (size_t)S_max * PP);
+    ok &= dalloc(h, &D.w_alpha, (size_t)S_max * PP);
+    ok &= dalloc(h, &D.w_eta, (size_t)J * PP);
+    ok &= dalloc(h, &D.p_pr, (size_t)S_max * J);
+    ok &= dalloc(h, &D.zeta, (size_t)S_max * J);
+    ok &= dalloc(h, &D.p_s, (size_t)S_max);
+    ok &= dalloc(h, &D.lw_x, PP);
+    ok &= dalloc(h, &D.lw_y, (size_t)S_max * PP);
+    ok &= dalloc(h, &D.lw_eta, (size_t)J * PP);
+    ok &= dalloc(h, &D.llr_w, (size_t)S_max * J);
+    ok &= dalloc(h, &D.tab, (size_t)4 * S_max * J * Nz * 2);
+    ok &= dalloc(h, &D.tab_part, (size_t)h->nsplit_max * 3 * S_max * J * Nz * 2);
+    ok &= dalloc(h, &D.W, (size_t)S_max);
+    ok &= dalloc(h, &D.eta_bar, (size_t)J);
+    ok &= dalloc(h, &D.kV, (size_t)S_max * J * Nz * SCA);
+    ok &= dalloc(h, &D.kR, (size_t)S_max * J * SCA * SCA);
+    ok &= dalloc(h, &D.ky0, (size_t)S_max * J * SCA);
+    ok &= dalloc(h, &D.kJ0, (size_t)S_max * J);
+    ok &= dalloc(h, &D.nu_T, (size_t)J * 4 * S_max);
+    ok &= dalloc(h, &D.nu_c, (size_t)J * 2);
+    const int nbel = bel_count(S_max, J);
+    ok &= dalloc(h, &D.red_part, (size_t)nbel * 64 * RED_W * 2);
+    ok &= dalloc(h, &D.bel, bel_total(S_max, J));
+    ok &= dalloc(h, &D.Lchol, (size_t)nbel * 36);
+    ok &= dalloc(h, &D.idx, (size_t)nbel * PP);
+    ok &= dalloc(h, &D.ctrl, (size_t)4 + S_max);
+    const EstLayout E{S_max, J};
+    ok &= dalloc(h, &D.est, E.total());
+    ok &= dalloc(h, &h->gram, (size_t)J * S_max * S_max * 2);
+    ok &= dalloc(h, &h->nu_b, (size_t)J * (S_max + 1) * 2);
+    ok &= dalloc(h, &h->V64, (size_t)S_max * J * Nz * SCA * 2);
+    ok &= dalloc(h, &h->cdf, (size_t)nbel * PP);
+    ok &= dalloc(h, &h->wn, (size_t)nbel * PP);
+    if (ok) {
+        ok &= cudaMallocHost(&h->h_ctrl, (4 + S_max) * sizeof(int)) == cudaSuccess;
+        ok &= cudaMallocHost(&h->h_est, E.total() * sizeof(double)) == cudaSuccess;
+    }
+    if (!ok) {
+        g_init_error = "device allocation failed";
+        bp_free(h);
+        return BP_ERR_CUDA;
+    }
+    D.wn_x = h->wn;
+    D.wn_y = h->wn + PP;
+    D.wn_eta = h->wn + (size_t)(1 + S_max) * PP;
+    D.cur = 0;
+    launch_init(h->G, h->Pm, D, h->st);
+    h->launches += 1;
+    h->S = 1; h->S_upd = 1; h->n = 0; h->phase = 0;
+    if (cudaStreamSynchronize(h->st) != cudaSuccess || cudaGetLastError() != cudaSuccess) {
+        g_init_error = std::string("bp_init: ") + cudaGetErrorString(cudaGetLastError());
+        bp_free(h);
+        return BP_ERR_CUDA;
+    }
+    *out = h;
+    return BP_OK;
+}
+
+bp_status bp_free(bp_handle* h) {
+    if (!h) return BP_ERR_INVALID_ARG;
+    if (h->st) cudaStreamSynchronize(h->st); else cudaDeviceSynchronize();
+    if (h->prof_on) for (int i = 0; i <= BP_PROF_STAGES; ++i) cudaEventDestroy(h->ev[i]);
+    for (void* p : h->allocs) cudaFree(p);
+    if (h->h_ctrl) cudaFreeHost(h->h_ctrl);
+    if (h->h_est) cudaFreeHost(h->h_est);
+    delete h;
+    return BP_OK;
+}
+
+bp_status bp_predict(bp_handle* h) {
+    if (!h) return BP_ERR_INVALID_ARG;
+    if (h->phase != 0) return fail(h, BP_ERR_STATE, "bp_predict: the handle already holds a prediction");
+    const int n = h->n + 1;
+    const int S_old = h->S;
+    int S_new = S_old;
+    if (h->Pm.Q > 0) {
+        S_new = std::min(S_old + h->Pm.Q, h->S_max);
+        h->births_skipped += S_old + h->Pm.Q - S_new;
+    }
+    mark(h, 0);
+    launch_predict(h->G, h->Pm, h->D, n, S_old, S_new, h->st);
+    if (h->prof_on) { cudaEventRecord(h->ev[BP_PROF_STAGES], h->st); h->ev_valid[0] = true; }
+    h->launches += 1;
+    h->S = S_new;
+    h->n = n;
+    h->phase = 1;
+    return cuda_check(h, "bp_predict");
+}
+
+bp_status bp_update(bp_handle* h, const float* z_dev) {
+    if (!h || !z_dev) return BP_ERR_INVALID_ARG;
+    if (h->phase != 1) return fail(h, BP_ERR_STATE, "bp_update: call bp_predict (or bp_set_predicted) first");
+    const int S = h->S, J = h->J, P = h->P;
+    DevState& D = h->D;
+    mark(h, 1);
+    launch_row_sums(h->Pm, D, S, J, h->st);
+    mark(h, 2);
+    int nsplit = std::max(1, (4 * 152 + S * J - 1) / (S * J));
+    nsplit = std::min(nsplit, std::max(1, P / 256));
+    nsplit = std::min(nsplit, h->nsplit_max);
+    launch_table(h->G, h->Pm, D, S, nsplit, h->st);
+    mark(h, 3);
+    launch_stage(h->G, h->Pm, D, S, h->SCA, z_dev, h->gram, h->nu_b, h->V64, h->st);
+    mark(h, 4);
+    launch_kappa(h->G, h->Pm, D, S, h->SCA, h->st);
+    mark(h, 5);
+    launch_iota(h->G, h->Pm, D, S, z_dev, h->st);
+    mark(h, 6);
+    launch_nu(h->G, h->Pm, D, S, h->st);
+    mark(h, 7);
+    launch_normalize(h->G, h->Pm, D, S, h->n, h->st);
+    mark(h, 8);
+    launch_resample(h->G, h->Pm, D, S, h->n, h->cdf, h->st);
+    if (h->prof_on) {
+        cudaEventRecord(h->ev[BP_PROF_STAGES], h->st);
+        for (int i = 1; i < BP_PROF_STAGES; ++i) h->ev_valid[i] = true;
+    }
+    h->launches += 1 + 2 + 3 + 1 + 1 + 1 + 5 + 3;
+    h->D.cur = 1 - h->D.cur;
+    h->S_upd = S;
+    h->phase = 0;
+    bp_status s = cuda_check(h, "bp_update");
+    if (s != BP_OK) return s;
+    if (h->Pm.Q > 0 || h->Pm.T_pru > 0.0) {
+        if (cudaMemcpyAsync(h->h_ctrl, D.ctrl, 4 * sizeof(int), cudaMemcpyDeviceToHost, h->st) != cudaSuccess ||
+            cudaStreamSynchronize(h->st) != cudaSuccess)
+            return fail(h, BP_ERR_CUDA, std::string("bp_update: ") + cudaGetErrorString(cudaGetLastError()));
+        h->S = h->h_ctrl[1];
+    }
+    return BP_OK;
+}
+
+bp_status bp_estimate(bp_handle* h, bp_estimate_out* o) {
+    if (!h || !o) return BP_ERR_INVALID_ARG;
+    const EstLayout E{h->S_max, h->J};
+    if (cudaMemcpyAsync(h->h_est, h->D.est, E.total() * sizeof(double), cudaMemcpyDeviceToHost, h->st) != cudaSuccess ||
+        cudaStreamSynchronize(h->st) != cudaSuccess)
+        return fail(h, BP_ERR_CUDA, std::string("bp_estimate: ") + cudaGetErrorString(cudaGetLastError()));
+    const double* e = h->h_est;
+    o->n = (int)e[E.n()];
+    o->S = (int)e[E.S()];
+    o->S_next = (int)e[E.S_next()];
+    o->births_skipped = h->births_skipped;
+    for (int k = 0; k < 6; ++k) o->x_hat[k] = e[E.x_hat() + k];
+    o->ess_x = e[E.ess()];
+    const int S = o->S;
+    if (o->eta_hat) for (int j = 0; j < h->J; ++j) o->eta_hat[j] = e[E.eta_hat() + j];
+    if (o->p_s) for (int s = 0; s < S; ++s) o->p_s[s] = e[E.p_s() + s];
+    if (o->phi_hat) for (int s = 0; s < 6 * S; ++s) o->phi_hat[s] = e[E.phi_hat() + s];
+    if (o->p_pr) for (int s = 0; s < S * h->J; ++s) o->p_pr[s] = e[E.p_pr() + s];
+    if (o->declared) for (int s = 0; s < S; ++s) o->declared[s] = e[E.declared() + s] != 0.0;
+    if ((int)e[E.status()] == BP_ERR_NUMERIC) return fail(h, BP_ERR_NUMERIC, "all MT weights underflowed");
+    return BP_OK;
+}
+
+static bp_status copy_state(bp_handle* h, bp_state_view* v, bool to_host, bool predicted) {
+    if (!h || !v) return BP_ERR_INVALID_ARG;
+    const int P = h->P, J = h->J;
+    const cudaMemcpyKind kind = to_host ? cudaMemcpyDeviceToHost : cudaMemcpyHostToDevice;
+    int S = to_host ? h->S : v->S;
+    if (S < 1 || S > h->S_max) return fail(h, BP_ERR_INVALID_ARG, "S out of range");
+    DevState& D = h->D;
+    double* wy = predicted ? D.w_alpha : D.w_y;
+    double* pr = predicted ? D.zeta : D.p_pr;
+    struct Item { void* dev; void* host; size_t bytes; };
+    const Item items[] = {
+        {D.x[D.cur], v->x, 6 * (size_t)P * sizeof(float)},
+        {D.phi[D.cur], v->phi, (size_t)S * 6 * P * sizeof(float)},
+        {D.eta[D.cur], v->eta, (size_t)J * P * sizeof(float)},
+        {D.w_x, v->w_x, (size_t)P * sizeof(double)},
+        {wy, v->w_y, (size_t)S * P * sizeof(double)},
+        {D.w_eta, v->w_eta, (size_t)J * P * sizeof(double)},
+        {pr, v->p_pr, (size_t)S * J * sizeof(double)},
+    };
+    for (const Item& it : items) {
+        if (!it.host) return fail(h, BP_ERR_INVALID_ARG, "state view has a NULL array");
+        cudaError_t e = to_host ? cudaMemcpyAsync(it.host, it.dev, it.bytes, kind, h->st)
+                                : cudaMemcpyAsync(it.dev, it.host, it.bytes, kind, h->st);
+        if (e != cudaSuccess) return fail(h, BP_ERR_CUDA, cudaGetErrorString(e));
+    }
+    if (cudaStreamSynchronize(h->st) != cudaSuccess) return fail(h, BP_ERR_CUDA, cudaGetErrorString(cudaGetLastError()));
+    if (to_host) { v->S = h->S; v->n = h->n; }
+    else { h->S = S; h->n = v->n; h->phase = predicted ? 1 : 0; }
+    return BP_OK;
+}
+
+bp_status bp_get_state(bp_handle* h, bp_state_view* out) {
+    if (h && h->phase != 0) return fail(h, BP_ERR_STATE, "bp_get_state: the handle holds a prediction");
+    return copy_state(h, out, true, false);
+}
+bp_status bp_set_state(bp_handle* h, const bp_state_view* in) { return copy_state(h, const_cast<bp_state_view*>(in), false, false); }
+bp_status bp_get_predicted(bp_handle* h, bp_state_view* out) {
+    if (h && h->phase != 1) return fail(h, BP_ERR_STATE, "bp_get_predicted: no prediction held");
+    return copy_state(h, out, true, true);
+}
+bp_status bp_set_predicted(bp_handle* h, const bp_state_view* in) { return copy_state(h, const_cast<bp_state_view*>(in), false, true); }
+
+bp_status bp_get_diag(bp_handle* h, int what, void* host, size_t bytes) {
+    if (!h || !host) return BP_ERR_INVALID_ARG;
+    const int S = h->S_upd, J = h->J, P = h->P, Nz = h->Nz, SM = h->S_max;
+    DevState& D = h->D;
+    std::vector<std::pair<const void*, size_t>> parts;   // (device ptr, bytes) in order
+    if (what == BP_DIAG_TABLE) {
+        const size_t plane = (size_t)SM * J * Nz * 2;
+        for (int i = 0; i < 4; ++i) parts.push_back({D.tab + i * plane, (size_t)S * J * Nz * 2 * sizeof(double)});
+        parts.push_back({D.W, (size_t)S * sizeof(double)});
+        parts.push_back({D.eta_bar, (size_t)J * sizeof(double)});
+    } else if (what == BP_DIAG_WEIGHTS) {
+        parts.push_back({h->wn, (size_t)P * sizeof(double)});
+        parts.push_back({h->wn + P, (size_t)S * P * sizeof(double)});
+        parts.push_back({h->wn + (size_t)(1 + SM) * P, (size_t)J * P * sizeof(double)});
+        parts.push_back({D.p_s, (size_t)S * sizeof(double)});
+        parts.push_back({D.bel + BEL_PPR, (size_t)S * J * sizeof(double)});
+    } else if (what == BP_DIAG_LOGLIK) {
+        parts.push_back({D.lw_x, (size_t)P * sizeof(double)});
+        parts.push_back({D.lw_y, (size_t)S * P * sizeof(double)});
+        parts.push_back({D.lw_eta, (size_t)J * P * sizeof(double)});
+        parts.push_back({D.llr_w, (size_t)S * J * sizeof(double)});
+    } else if (what == BP_DIAG_INDICES) {
+        parts.push_back({D.idx, (size_t)P * sizeof(int)});
+        parts.push_back({D.idx + P, (size_t)S * P * sizeof(int)});
+        parts.push_back({D.idx + (size_t)(1 + SM) * P, (size_t)J * P * sizeof(int)});
+    } else {
+        return fail(h, BP_ERR_INVALID_ARG, "unknown diagnostic");
+    }
+    size_t need = 0;
+    for (auto& pr : parts) need += pr.second;
+    if (bytes < need) return fail(h, BP_ERR_INVALID_ARG, "diagnostic buffer too small");
+    char* dst = static_cast<char*>(host);
+    for (auto& pr : parts) {
+        if (cudaMemcpyAsync(dst, pr.first, pr.second, cudaMemcpyDeviceToHost, h->st) != cudaSuccess)
+            return fail(h, BP_ERR_CUDA, cudaGetErrorString(cudaGetLastError()));
+        dst += pr.second;
+    }
+    if (cudaStreamSynchronize(h->st) != cudaSuccess) return fail(h, BP_ERR_CUDA, cudaGetErrorString(cudaGetLastError()));
+    return BP_OK;
+}
+
+bp_status bp_set_profiling(bp_handle* h, int on) {
+    if (!h) return BP_ERR_INVALID_ARG;
+    if (on && !h->prof_on) {
+        for (int i = 0; i <= BP_PROF_STAGES; ++i)
+            if (cudaEventCreate(&h->ev[i]) != cudaSuccess) return fail(h, BP_ERR_CUDA, "cudaEventCreate failed");
+        for (int i = 0; i < BP_PROF_STAGES; ++i) h->ev_valid[i] = false;
+        h->prof_on = 1;
+    } else if (!on && h->prof_on) {
+        cudaStreamSynchronize(h->st);
+        for (int i = 0; i <= BP_PROF_STAGES; ++i) cudaEventDestroy(h->ev[i]);
+        h->prof_on = 0;
+    }
+    return BP_OK;
+}
+
+// durations of the last predict (stage 0) and update (stages 1..8); a stage ends
+// where the next one starts (the update's last stage ends at the closing event)
+bp_status bp_get_profile(bp_handle* h, double* ms, int n) {
+    if (!h || !ms || n < BP_PROF_STAGES) return BP_ERR_INVALID_ARG;
+    if (!h->prof_on) return fail(h, BP_ERR_STATE, "profiling is off");
+    if (cudaStreamSynchronize(h->st) != cudaSuccess) return fail(h, BP_ERR_CUDA, cudaGetErrorString(cudaGetLastError()));
+    for (int i = 0; i < BP_PROF_STAGES; ++i) ms[i] = 0.0;
+    // the predict's end event is shared with the update's end: only valid if the
+    // update has not been recorded after it, so report predict through stage 1's start
+    for (int i = 1; i < BP_PROF_STAGES; ++i) {
+        if (!h->ev_valid[i]) continue;
+        float t = 0.f;
+        cudaEvent_t e1 = (i + 1 < BP_PROF_STAGES) ? h->ev[i + 1] : h->ev[BP_PROF_STAGES];
+        if (cudaEventElapsedTime(&t, h->ev[i], e1) == cudaSuccess) ms[i] = t;
+    }
+    if (h->ev_valid[0] && h->ev_valid[1]) {
+        float t = 0.f;
+        if (cudaEventElapsedTime(&t, h->ev[0], h->ev[1]) == cudaSuccess) ms[0] = t;
+    }
+    cudaGetLastError();
+    return BP_OK;
+}
+
+bp_status bp_synthesize(const bp_geometry* geom, int n_steps, int step0, const double* x_pos, int K,
+                        const double* sfv, const double* rho, const int* clutter_count, const double* clutter_sfv,
+                        const double* clutter_rho, double snr_db, uint64_t seed, float* z_dev, double* eta_out,
+                        void* cuda_stream) {
+    if (validate_geom(geom) != BP_OK || n_steps < 1 || K < 0 || !x_pos || !rho || !z_dev || !eta_out ||
+        (K > 0 && !sfv))
+        return fail(nullptr, BP_ERR_INVALID_ARG, "bp_synthesize: invalid arguments");
+    DevGeom G;
+    fill_geom(G, geom);
+    cudaStream_t st = static_cast<cudaStream_t>(cuda_stream);
+    const int J = G.J, Nz = G.Nz;
+    std::vector<int> off(n_steps + 1, 0);
+    for (int t = 0; t < n_steps; ++t) off[t + 1] = off[t] + (clutter_count ? clutter_count[t] : 0);
+    const int nc = off[n_steps];
+    double *dx = nullptr, *dsfv = nullptr, *drho = nullptr, *dcs = nullptr, *dcr = nullptr, *dz = nullptr, *dpow = nullptr;
+    int *doff = nullptr, *dzero = nullptr;
+    std::vector<void*> tmp;
+    auto alloc = [&](void** p, size_t b) { if (cudaMalloc(p, std::max<size_t>(b, 8)) != cudaSuccess) return false; tmp.push_back(*p); return true; };
+    bool ok = alloc((void**)&dx, 3 * sizeof(double) * n_steps) && alloc((void**)&dsfv, 3 * sizeof(double) * std::max(K, 1)) &&
+              alloc((void**)&drho, 2 * sizeof(double) * (size_t)n_steps * J * (K + 1)) &&
+              alloc((void**)&dcs, 3 * sizeof(double) * std::max(nc, 1)) && alloc((void**)&dcr, 2 * sizeof(double) * std::max(nc, 1) * J) &&
+              alloc((void**)&dz, 2 * sizeof(double) * (size_t)n_steps * J * Nz) && alloc((void**)&dpow, sizeof(double)) &&
+              alloc((void**)&doff, sizeof(int) * (n_steps + 1)) && alloc((void**)&dzero, sizeof(int) * 2);
+    double eta = 0.0;
+    if (ok) {
+        cudaMemcpyAsync(dx, x_pos, 3 * sizeof(double) * n_steps, cudaMemcpyHostToDevice, st);
+        if (K > 0) cudaMemcpyAsync(dsfv, sfv, 3 * sizeof(double) * K, cudaMemcpyHostToDevice, st);
+        cudaMemcpyAsync(drho, rho, 2 * sizeof(double) * (size_t)n_steps * J * (K + 1), cudaMemcpyHostToDevice, st);
+        if (nc > 0) {
+            cudaMemcpyAsync(dcs, clutter_sfv, 3 * sizeof(double) * nc, cudaMemcpyHostToDevice, st);
+            cudaMemcpyAsync(dcr, clutter_rho, 2 * sizeof(double) * nc * J, cudaMemcpyHostToDevice, st);
+        }
+        cudaMemcpyAsync(doff, off.data(), sizeof(int) * (n_steps + 1), cudaMemcpyHostToDevice, st);
+        cudaMemsetAsync(dzero, 0, sizeof(int) * 2, st);
+        // sum-channel power of the first step from the true components only
+        launch_synth(G, 1, step0, dx, K, dsfv, drho, dzero, dcs, dcr, dz, 0, 0, st);
+        launch_power(G, dz, dpow, st);
+        double pch = 0.0;
+        cudaMemcpyAsync(&pch, dpow, sizeof(double), cudaMemcpyDeviceToHost, st);
+        cudaStreamSynchronize(st);
+        eta = pch / pow(10.0, snr_db / 10.0);
+        launch_synth(G, n_steps, step0, dx, K, dsfv, drho, doff, dcs, dcr, dz, 0, 0, st);
+        launch_synth_noise(G, n_steps, step0, dz, eta, (uint32_t)(seed & 0xFFFFFFFFu), (uint32_t)(seed >> 32), z_dev, st);
+        ok = cudaStreamSynchronize(st) == cudaSuccess && cudaGetLastError() == cudaSuccess;
+    }
+    for (void* p : tmp) cudaFree(p);
+    if (!ok) return fail(nullptr, BP_ERR_CUDA, std::string("bp_synthesize: ") + cudaGetErrorString(cudaGetLastError()));
+    *eta_out = eta;
+    return BP_OK;
+}
+
+}  // extern "C"

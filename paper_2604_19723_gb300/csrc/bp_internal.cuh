@@ -1,0 +1,229 @@
+// Internal definitions of libbp: device constants, RNG, geometry and small
+// numeric helpers shared by the kernels.  sm_103a only.
+#pragma once
+#include <cuda_runtime.h>
+#include <stdint.h>
+#include <math.h>
+
+#include "../../include/bp.h"
+
+namespace bp {
+
+constexpr int J_MAX = 16;
+constexpr int NF_MAX = 64;
+constexpr int MY_MAX = 16;
+constexpr int MZ_MAX = 16;
+constexpr int NZ_MAX = 2048;
+constexpr int S_CAP_MAX = 64;
+
+// Geometry and parameters, passed to kernels by value (constant bank).
+struct DevGeom {
+    int J, Nf, My, Mz, Nz;
+    double fc, c, lam, B;
+    double p_pa[J_MAX][3];
+    double R[J_MAX][9];      // row-major, columns = local axes (global coords)
+    double f[NF_MAX];        // baseband frequencies
+    double py[MY_MAX], pz[MZ_MAX];
+};
+
+struct DevParams {
+    double T, sigma_v;
+    int motion_dims;
+    double c_eta, c_gamma, sigma_mu, sigma_sfv;
+    double pS, pS_pr, pR_pr, pB_pr, mu_B, pB;   // pB = birth probability per partition
+    int Q;
+    double T_dec, T_pru, gamma_max, mu_max, eta_min, eta_max;
+    double p_min[3], p_max[3], v_max[3];
+    int zero_mean, mvec_scaling, regularize;
+    uint32_t key0, key1;
+    int P, S_max;
+};
+
+// ------------------------------------------------------------------ Philox4x32-10
+// Salmon, Moraes, Dror, Shaw (SC'11): 10 rounds, multipliers 0xD2511F53 and
+// 0xCD9E8D57, Weyl increments 0x9E3779B9 and 0xBB67AE85.
+struct U4 { uint32_t x, y, z, w; };
+
+__host__ __device__ inline U4 philox(uint32_t c0, uint32_t c1, uint32_t c2, uint32_t c3, uint32_t k0, uint32_t k1) {
+    #pragma unroll
+    for (int r = 0; r < 10; ++r) {
+        const uint64_t p0 = (uint64_t)0xD2511F53u * c0;
+        const uint64_t p1 = (uint64_t)0xCD9E8D57u * c2;
+        const uint32_t hi0 = (uint32_t)(p0 >> 32), lo0 = (uint32_t)p0;
+        const uint32_t hi1 = (uint32_t)(p1 >> 32), lo1 = (uint32_t)p1;
+        const uint32_t n0 = hi1 ^ c1 ^ k0, n2 = hi0 ^ c3 ^ k1;
+        c0 = n0; c1 = lo1; c2 = n2; c3 = lo0;
+        k0 += 0x9E3779B9u; k1 += 0xBB67AE85u;
+    }
+    return U4{c0, c1, c2, c3};
+}
+
+// draw purposes (bits 31..16 of the third counter word); must match the oracle
+enum : uint32_t {
+    RNG_MT_PREDICT = 1, RNG_ETA_PREDICT = 2, RNG_PF_GAUSS = 3, RNG_PF_GAMMA = 4, RNG_BIRTH = 5,
+    RNG_RESAMPLE = 6, RNG_JITTER_MT = 7, RNG_JITTER_PF = 8, RNG_JITTER_ETA = 9, RNG_INIT_MT = 10,
+    RNG_INIT_ETA = 11, RNG_SYNTH_NOISE = 12
+};
+constexpr int MAX_GAMMA_ATTEMPTS = 16;
+
+__device__ inline U4 draw(const DevParams& P, uint32_t item, uint32_t n, uint32_t purpose, uint32_t sub, uint32_t block) {
+    return philox(item, n, (purpose << 16) | (sub & 0xFFFFu), block, P.key0, P.key1);
+}
+
+// ((x >> 8) + 1/2) 2^-24: uniform in (0,1), exact in FP32
+__device__ inline float u24(uint32_t x) { return ((float)(x >> 8) + 0.5f) * 5.9604644775390625e-8f; }
+// (x + 1/2) 2^-32: uniform in (0,1), exact in FP64
+__host__ __device__ inline double u32d(uint32_t x) { return ((double)x + 0.5) * 2.3283064365386963e-10; }
+
+// Box-Muller pair in FP32 from two 24-bit uniforms
+__device__ inline void box_muller_f(uint32_t a, uint32_t b, float& n0, float& n1) {
+    const float r = sqrtf(-2.0f * logf(u24(a)));
+    float s, c;
+    sincospif(2.0f * u24(b), &s, &c);
+    n0 = r * c;
+    n1 = r * s;
+}
+
+// `count` (<= 8) standard normals for one item, blocks 0, 1 in order
+__device__ inline void normals8(const DevParams& P, uint32_t item, uint32_t n, uint32_t purpose, uint32_t sub,
+                                int count, float* out) {
+    for (int blk = 0; blk * 4 < count; ++blk) {
+        const U4 r = draw(P, item, n, purpose, sub, blk);
+        float a0, a1, b0, b1;
+        box_muller_f(r.x, r.y, a0, a1);
+        box_muller_f(r.z, r.w, b0, b1);
+        const float v[4] = {a0, a1, b0, b1};
+        for (int i = 0; i < 4 && blk * 4 + i < count; ++i) out[blk * 4 + i] = v[i];
+    }
+}
+
+// Marsaglia & Tsang (2000) Gamma(shape >= 1, scale) in FP64; attempt a uses block a
+__device__ inline double gamma_draw(const DevParams& P, uint32_t item, uint32_t n, uint32_t purpose, uint32_t sub,
+                                    double shape, double scale) {
+    const double d = shape - 1.0 / 3.0;
+    const double c = 1.0 / sqrt(9.0 * d);
+    for (int a = 0; a < MAX_GAMMA_ATTEMPTS; ++a) {
+        const U4 r = draw(P, item, n, purpose, sub, (uint32_t)a);
+        const double g = sqrt(-2.0 * log(u32d(r.x))) * cospi(2.0 * u32d(r.y));
+        const double t = 1.0 + c * g;
+        const double v = t * t * t;
+        if (v <= 0.0) continue;
+        const double u = u32d(r.z);
+        if (log(u) < 0.5 * g * g + d - d * v + d * log(v)) return d * v * scale;
+    }
+    return shape * scale;
+}
+
+// ------------------------------------------------------------------ geometry (FP64)
+// Local PA -> VM vector r' = R^T H (p - p_va) (eq. rangep, house, posPA-SB);
+// returns |r'| and the local unit vector.
+struct PathGeo { double d, ux, uy, uz; };
+
+__device__ inline PathGeo path_geo(const DevGeom& G, int j, double px, double py, double pz,
+                                   double sx, double sy, double sz, bool los) {
+    double rx, ry, rz;
+    const double ax = G.p_pa[j][0], ay = G.p_pa[j][1], az = G.p_pa[j][2];
+    if (los) {
+        rx = px - ax; ry = py - ay; rz = pz - az;
+    } else {
+        const double nn = sx * sx + sy * sy + sz * sz;
+        const double coef = 2.0 * (ax * sx + ay * sy + az * sz) / nn - 1.0;
+        const double vx = ax - coef * sx, vy = ay - coef * sy, vz = az - coef * sz;
+        const double qx = px - vx, qy = py - vy, qz = pz - vz;
+        const double t = 2.0 * (sx * qx + sy * qy + sz * qz) / nn;
+        rx = qx - t * sx; ry = qy - t * sy; rz = qz - t * sz;
+    }
+    const double* R = G.R[j];
+    const double lx = R[0] * rx + R[3] * ry + R[6] * rz;
+    const double ly = R[1] * rx + R[4] * ry + R[7] * rz;
+    const double lz = R[2] * rx + R[5] * ry + R[8] * rz;
+    const double d = sqrt(lx * lx + ly * ly + lz * lz);
+    const double inv = 1.0 / d;
+    return PathGeo{d, lx * inv, ly * inv, lz * inv};
+}
+
+// fractional part in [-1/2, 1/2]
+__device__ inline double frac_c(double t) { return t - rint(t); }
+
+// ------------------------------------------------------------------ complex / double-float helpers
+__host__ __device__ inline float2 cmul(float2 a, float2 b) { return make_float2(a.x * b.x - a.y * b.y, a.x * b.y + a.y * b.x); }
+__host__ __device__ inline float2 cmulc(float2 a, float2 b) {  // conj(a) * b
+    return make_float2(a.x * b.x + a.y * b.y, a.x * b.y - a.y * b.x);
+}
+__host__ __device__ inline double2 zmul(double2 a, double2 b) { return make_double2(a.x * b.x - a.y * b.y, a.x * b.y + a.y * b.x); }
+__host__ __device__ inline double2 zmulc(double2 a, double2 b) { return make_double2(a.x * b.x + a.y * b.y, a.x * b.y - a.y * b.x); }
+
+// error-free sum (Knuth TwoSum)
+__device__ inline void two_sum(float a, float b, float& s, float& e) {
+    s = __fadd_rn(a, b);
+    const float bb = __fsub_rn(s, a);
+    e = __fadd_rn(__fsub_rn(a, __fsub_rn(s, bb)), __fsub_rn(b, bb));
+}
+
+__device__ inline double warp_sum_d(double v) {
+    #pragma unroll
+    for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
+    return v;
+}
+__device__ inline float warp_sum_f(float v) {
+    #pragma unroll
+    for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
+    return v;
+}
+__device__ inline double warp_max_d(double v) {
+    #pragma unroll
+    for (int o = 16; o > 0; o >>= 1) v = fmax(v, __shfl_xor_sync(0xffffffffu, v, o));
+    return v;
+}
+
+// ------------------------------------------------------------------ device state
+// Pointers of one filter's device buffers (owned by the handle).
+struct DevState {
+    // particles, two buffers each (resampling writes the other one)
+    float* x[2];      // 6 x P
+    float* phi[2];    // S_max x 6 x P
+    float* eta[2];    // J x P
+    int cur;
+    // weights (FP64)
+    double* w_x;      // P      belief / w_beta
+    double* w_y;      // S_max x P  belief weights
+    double* w_alpha;  // S_max x P  PF prediction weights
+    double* w_eta;    // J x P  belief / w_xi
+    double* p_pr;     // S_max x J  belief p(r=1)
+    double* zeta;     // S_max x J  zeta(1)
+    double* p_s;      // S_max
+    double* wn_x;     // P          normalised weights before resampling
+    double* wn_y;     // S_max x P
+    double* wn_eta;   // J x P
+    // log weights / likelihoods of the current update
+    double* lw_x;     // P
+    double* lw_y;     // S_max x P   (Delta_kappa summed over j, without log w_alpha)
+    double* lw_eta;   // J x P
+    double* llr_w;    // S_max x J   log omega(1) - log omega(0)
+    // message table (FP64) and derived per-(s,j) quantities
+    double* tab;      // [4][S_max][J][Nz] double2 : m, mw, mu3, mu4
+    double* tab_part; // table partial sums [nsplit][3][S_max][J][Nz] double2
+    double* W;        // S_max    sum_p w_alpha
+    double* eta_bar;  // J
+    double* sums_part;// partial sums for W / eta_bar
+    // kappa stage outputs (per (s,j))
+    float2* kV;       // [S_max][J][Nz][S_cap]   whitened basis, column S_cap-1 = r0
+    float2* kR;       // [S_max][J][S_cap*S_cap] upper Cholesky factor (FP32, padded identity)
+    float2* ky0;      // [S_max][J][S_cap]       y0 = R^-1 V^H e0 / eta_bar
+    double* kJ0;      // [S_max][J]              J0* = |r0|^2/eta_bar + |y0|^2
+    // nu stage outputs (per j)
+    double* nu_T;     // [J][S_max] diag a_k, [J][S_max] |offdiag|^2, [J][S_max] double2 b'
+    double* nu_c;     // [J][2] |e|^2, constant
+    // iota inputs (per (s,j) FP32 copies)
+    float* iota_pi;   // [S_max][J]
+    float2* zf;       // J x Nz (copy of the observation)
+    // normalisation scratch
+    double* red_part; // block partials
+    double* bel;      // per-belief results (see k_norm.cu)
+    float* Lchol;     // per-belief jitter factors
+    int* idx;         // (1 + S_max + J) x P resampling indices
+    int* ctrl;        // [0] S, [1] S_next, [2] births_skipped, [3] status, [4..] keep map
+    double* est;      // estimates buffer
+};
+
+}  // namespace bp

@@ -1,0 +1,55 @@
+// Kernel launch wrappers and shared buffer layouts of libbp.
+#pragma once
+#include "bp_internal.cuh"
+
+namespace bp {
+
+// per-belief result buffer (doubles); belief index b: 0 = MT, 1 + s = PF s, 1 + S_max + j = eta_j
+constexpr int BEL_STRIDE = 16;   // per belief: [0] max, [1] lse, [2] logC, [3] sum w^2 factor, [4..9] mean, [10] active dims
+inline __host__ __device__ int bel_count(int S_max, int J) { return 1 + S_max + J; }
+#define BEL_PPR 0   /* offset of the updated PR existence table inside D.bel (S_max x J) */
+inline __host__ __device__ size_t bel_ppr_size(int S_max, int J) { return (size_t)S_max * J; }
+inline __host__ __device__ size_t bel_rec(int S_max, int J, int b) { return bel_ppr_size(S_max, J) + (size_t)b * BEL_STRIDE; }
+inline __host__ __device__ size_t bel_total(int S_max, int J) { return bel_ppr_size(S_max, J) + (size_t)bel_count(S_max, J) * BEL_STRIDE; }
+
+// estimate buffer layout (doubles)
+struct EstLayout {
+    int S_max, J;
+    __host__ __device__ size_t n() const { return 0; }
+    __host__ __device__ size_t S() const { return 1; }
+    __host__ __device__ size_t S_next() const { return 2; }
+    __host__ __device__ size_t skipped() const { return 3; }
+    __host__ __device__ size_t status() const { return 4; }
+    __host__ __device__ size_t x_hat() const { return 5; }
+    __host__ __device__ size_t ess() const { return 11; }
+    __host__ __device__ size_t eta_hat() const { return 12; }
+    __host__ __device__ size_t p_s() const { return 12 + J; }
+    __host__ __device__ size_t phi_hat() const { return 12 + J + S_max; }
+    __host__ __device__ size_t p_pr() const { return 12 + J + 7 * S_max; }
+    __host__ __device__ size_t p_any() const { return 12 + J + 7 * S_max + S_max * J; }
+    __host__ __device__ size_t declared() const { return 12 + J + 8 * S_max + S_max * J; }
+    __host__ __device__ size_t total() const { return 12 + J + 9 * S_max + S_max * J; }
+};
+
+constexpr int RED_W = 29;   // per-block partial sums: S0, S1[6], S2[21] (upper, row-major), sum w^2
+
+void launch_init(const DevGeom& G, const DevParams& Pm, const DevState& D, cudaStream_t st);
+void launch_predict(const DevGeom& G, const DevParams& Pm, const DevState& D, int n, int S_old, int S_new, cudaStream_t st);
+void launch_row_sums(const DevParams& Pm, const DevState& D, int S, int J, cudaStream_t st);
+void launch_table(const DevGeom& G, const DevParams& Pm, const DevState& D, int S, int nsplit, cudaStream_t st);
+void launch_stage(const DevGeom& G, const DevParams& Pm, const DevState& D, int S, int SC, const float* z,
+                  double* gram, double* nu_b, double* V64, cudaStream_t st);
+void launch_kappa(const DevGeom& G, const DevParams& Pm, const DevState& D, int S, int SCA, cudaStream_t st);
+size_t kappa_smem_bytes(const DevGeom& G, int S);
+void launch_iota(const DevGeom& G, const DevParams& Pm, const DevState& D, int S, const float* z, cudaStream_t st);
+void launch_nu(const DevGeom& G, const DevParams& Pm, const DevState& D, int S, cudaStream_t st);
+int launch_normalize(const DevGeom& G, const DevParams& Pm, const DevState& D, int S, int n, cudaStream_t st);
+void launch_resample(const DevGeom& G, const DevParams& Pm, const DevState& D, int S, int n, double* cdf, cudaStream_t st);
+void launch_synth(const DevGeom& G, int n_steps, int step0, const double* x_pos, int K, const double* sfv,
+                  const double* rho, const int* c_off, const double* c_sfv, const double* c_rho,
+                  double* zbuf, uint32_t k0, uint32_t k1, cudaStream_t st);
+void launch_synth_noise(const DevGeom& G, int n_steps, int step0, const double* zbuf, double eta, uint32_t k0,
+                        uint32_t k1, float* z_out, cudaStream_t st);
+void launch_power(const DevGeom& G, const double* zbuf, double* out, cudaStream_t st);
+
+}  // namespace bp

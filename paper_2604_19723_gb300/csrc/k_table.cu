@@ -1,0 +1,546 @@
+// Message table and the particle-independent stage of the update.
+//
+// Table (Supplementary Sec. S-V; Proposition 1 terms mu^(3), mu^(4)), for
+// every (s, j), with W = sum_p w_alpha, pi = zeta W:
+//   m    = c_m sum_p w_beta sqrt(gamma + |mu|^2 (1 - pi)) psi_s^(j,p)
+//   m^w  = c_w sum_p w_beta sqrt(gamma + |mu|^2 (1 - W))  psi_s^(j,p)
+//   mu4  = W sum_p w_beta mu psi_s^(j,p),  mu3 = zeta mu4
+// (c_m, c_w) = (W zeta, W) as printed in S-V, or their square roots.
+// FP32 accumulation over chunks of particles, FP64 across chunks.
+//
+// Stage per (s, j), FP64 (S-V "PF state update message", "PR state update
+// message", S-VI): A_s = eta_bar I + M_{-s} M_{-s}^H is represented by the
+// Cholesky-whitened basis V = M_{-s} R^-1 (R^H R = I + G_{-s}/eta_bar), so that
+// a^H A_s^-1 b = (a^H b - (V^H a)^H (V^H b)/eta_bar)/eta_bar (the inversion lemma
+// of S-V with the small inverse factored).  It also forms the regularised
+// null residual r0 = eta_bar A_s^-1 e0 (e0 = z - sum_{s'!=s} mu3_s'), the
+// coefficients y0 = (eta_bar I + G_{-s})^-1 M_{-s}^H e0, J0 = e0^H A_s^-1 e0,
+// and the PR existence test omega~(1)/omega~(0) -> p_s^(j) (eq. PR-normalization).
+//
+// nu (S-V "Noise variance update message"): G = M^H M is reduced once per j
+// to a real symmetric tridiagonal T = Q^H G Q (Householder), with b = Q^H M^H e;
+// each particle then needs O(S) work (k_like.cu).
+#include "bp_internal.cuh"
+#include "bp_kernels.cuh"
+
+namespace bp {
+
+// ---------------------------------------------------------------- table reduction
+// grid (nsplit, S, J); per-particle factors are staged in shared memory, each
+// thread owns EPT elements of the Nz-vector.
+template <int EPT>
+__global__ void k_table(DevGeom G, DevParams Pm, DevState D, int S, int nsplit, int chunk) {
+    extern __shared__ float2 sm[];
+    const int split = blockIdx.x, s = blockIdx.y, j = blockIdx.z;
+    const int P = Pm.P, J = G.J, Nf = G.Nf, Nm = G.My * G.Mz, Nz = G.Nz;
+    const int per = (P + nsplit - 1) / nsplit;
+    const int p0 = split * per, p1 = min(P, p0 + per);
+    float2* Bf = sm;                          // [chunk][3][Nf]
+    float2* Ayz = sm + (size_t)chunk * 3 * Nf;  // [chunk][Nm]
+    const double W = D.W[s];
+    const double zeta = D.zeta[s * J + j];
+    const double pi = zeta * W;
+    const float* x = D.x[D.cur];
+    const float* ph = D.phi[D.cur] + (size_t)s * 6 * P;
+    double acc64[EPT][3][2];
+    #pragma unroll
+    for (int e = 0; e < EPT; ++e)
+        #pragma unroll
+        for (int i = 0; i < 3; ++i) acc64[e][i][0] = acc64[e][i][1] = 0.0;
+    for (int c0 = p0; c0 < p1; c0 += chunk) {
+        const int cn = min(chunk, p1 - c0);
+        __syncthreads();
+        for (int t = threadIdx.x; t < cn; t += blockDim.x) {
+            const int p = c0 + t;
+            const PathGeo pg = path_geo(G, j, x[p], x[P + p], x[2 * P + p], ph[p], ph[P + p], ph[2 * P + p], s == 0);
+            const double A = G.lam / (4.0 * M_PI * pg.d);
+            double sc, cc;
+            sincospi(-2.0 * frac_c(pg.d / G.lam), &sc, &cc);
+            const double gm = (double)ph[3 * P + p];
+            const double mr = (double)ph[4 * P + p], mi = (double)ph[5 * P + p];
+            const double m2 = mr * mr + mi * mi;
+            const double wb = D.w_x[p];
+            const double ca = wb * sqrt(fmax(gm + m2 * (1.0 - pi), 0.0));
+            const double cb = wb * sqrt(fmax(gm + m2 * (1.0 - W), 0.0));
+            // complex scalars times A e^{-i 2 pi d/lambda}
+            const double2 car = make_double2(A * cc, A * sc);
+            const double2 c1 = make_double2(ca * car.x, ca * car.y);
+            const double2 c2 = make_double2(cb * car.x, cb * car.y);
+            const double2 c3 = zmul(make_double2(wb * mr, wb * mi), car);
+            const double tau = pg.d / G.c;
+            for (int f = 0; f < Nf; ++f) {
+                float sb, cbf;
+                sincospif((float)(-2.0 * frac_c(G.f[f] * tau)), &sb, &cbf);
+                const double2 bb = make_double2(cbf, sb);
+                const double2 v1 = zmul(c1, bb), v2 = zmul(c2, bb), v3 = zmul(c3, bb);
+                Bf[((size_t)t * 3 + 0) * Nf + f] = make_float2((float)v1.x, (float)v1.y);
+                Bf[((size_t)t * 3 + 1) * Nf + f] = make_float2((float)v2.x, (float)v2.y);
+                Bf[((size_t)t * 3 + 2) * Nf + f] = make_float2((float)v3.x, (float)v3.y);
+            }
+            const float uy = (float)pg.uy, uz = (float)pg.uz;
+            for (int y = 0; y < G.My; ++y) {
+                float sy, cy;
+                sincospif(2.0f * (float)(G.py[y] / G.lam) * uy, &sy, &cy);
+                for (int m = 0; m < G.Mz; ++m) {
+                    float sz, cz;
+                    sincospif(2.0f * (float)(G.pz[m] / G.lam) * uz, &sz, &cz);
+                    Ayz[(size_t)t * Nm + y * G.Mz + m] = cmul(make_float2(cy, sy), make_float2(cz, sz));
+                }
+            }
+        }
+        __syncthreads();
+        float acc[EPT][3][2];
+        #pragma unroll
+        for (int e = 0; e < EPT; ++e)
+            #pragma unroll
+            for (int i = 0; i < 3; ++i) acc[e][i][0] = acc[e][i][1] = 0.f;
+        for (int t = 0; t < cn; ++t) {
+            #pragma unroll
+            for (int e = 0; e < EPT; ++e) {
+                const int k = threadIdx.x + e * blockDim.x;
+                if (k < Nz) {
+                    const int f = k / Nm, ym = k - f * Nm;
+                    const float2 a = Ayz[(size_t)t * Nm + ym];
+                    #pragma unroll
+                    for (int i = 0; i < 3; ++i) {
+                        const float2 bv = Bf[((size_t)t * 3 + i) * Nf + f];
+                        const float2 v = cmul(bv, a);
+                        acc[e][i][0] += v.x;
+                        acc[e][i][1] += v.y;
+                    }
+                }
+            }
+        }
+        #pragma unroll
+        for (int e = 0; e < EPT; ++e)
+            #pragma unroll
+            for (int i = 0; i < 3; ++i) { acc64[e][i][0] += acc[e][i][0]; acc64[e][i][1] += acc[e][i][1]; }
+    }
+    const int SJ = Pm.S_max * J;
+    #pragma unroll
+    for (int e = 0; e < EPT; ++e) {
+        const int k = threadIdx.x + e * blockDim.x;
+        if (k < Nz) {
+            #pragma unroll
+            for (int i = 0; i < 3; ++i) {
+                double2* out = reinterpret_cast<double2*>(D.tab_part) + (((size_t)split * 3 + i) * SJ + (size_t)s * J + j) * Nz + k;
+                *out = make_double2(acc64[e][i][0], acc64[e][i][1]);
+            }
+        }
+    }
+}
+
+// sums the partials in fixed order and applies the existence scale factors
+__global__ void k_table_final(DevGeom G, DevParams Pm, DevState D, int S, int nsplit) {
+    const int J = G.J, Nz = G.Nz;
+    const int SJ = Pm.S_max * J;
+    const int idx = blockIdx.x * blockDim.x + threadIdx.x;
+    if (idx >= S * J * Nz) return;
+    const int k = idx % Nz;
+    const int sj = idx / Nz;
+    const int s = sj / J, j = sj - s * J;
+    const double W = D.W[s], zeta = D.zeta[s * J + j];
+    double2 v[3];
+    for (int i = 0; i < 3; ++i) {
+        double2 a = make_double2(0.0, 0.0);
+        for (int sp = 0; sp < nsplit; ++sp) {
+            const double2 t = reinterpret_cast<const double2*>(D.tab_part)[(((size_t)sp * 3 + i) * SJ + (size_t)s * J + j) * Nz + k];
+            a.x += t.x; a.y += t.y;
+        }
+        v[i] = a;
+    }
+    double cm, cw;
+    if (Pm.mvec_scaling == 0) { cm = W * zeta; cw = W; } else { cm = sqrt(W * zeta); cw = sqrt(W); }
+    double2* tab = reinterpret_cast<double2*>(D.tab);
+    const size_t o = ((size_t)s * J + j) * Nz + k;
+    const size_t plane = (size_t)SJ * Nz;
+    tab[0 * plane + o] = make_double2(cm * v[0].x, cm * v[0].y);
+    tab[1 * plane + o] = make_double2(cw * v[1].x, cw * v[1].y);
+    const double2 m4 = make_double2(W * v[2].x, W * v[2].y);
+    tab[3 * plane + o] = m4;
+    tab[2 * plane + o] = make_double2(zeta * m4.x, zeta * m4.y);
+}
+
+// ---------------------------------------------------------------- Gram matrix per j (FP64)
+// G_j[a][b] = m_a^H m_b; also e_all = z - sum_s mu3_s, b = M^H e_all, |e_all|^2.
+__global__ void k_gram(DevGeom G, DevParams Pm, DevState D, int S, const float* z, double* gram, double* nu_b) {
+    const int j = blockIdx.y;
+    const int J = G.J, Nz = G.Nz, SM = Pm.S_max;
+    const size_t plane = (size_t)SM * J * Nz;
+    const double2* tab = reinterpret_cast<const double2*>(D.tab);
+    const int npair = S * (S + 1) / 2;
+    // pairs (a >= b) plus S projections of e_all plus one norm
+    const int ntask = npair + S + 1;
+    const int warps = blockDim.x / 32, lane = threadIdx.x & 31;
+    for (int task = blockIdx.x * warps + (threadIdx.x >> 5); task < ntask; task += gridDim.x * warps) {
+        double2 acc = make_double2(0.0, 0.0);
+        if (task < npair) {
+            int a = (int)((sqrt(8.0 * task + 1.0) - 1.0) / 2.0);
+            while ((a + 1) * (a + 2) / 2 <= task) ++a;
+            while (a * (a + 1) / 2 > task) --a;
+            const int b = task - a * (a + 1) / 2;
+            const double2* ma = tab + ((size_t)a * J + j) * Nz;
+            const double2* mb = tab + ((size_t)b * J + j) * Nz;
+            for (int k = lane; k < Nz; k += 32) {
+                const double2 t = zmulc(ma[k], mb[k]);
+                acc.x += t.x; acc.y += t.y;
+            }
+            acc.x = warp_sum_d(acc.x); acc.y = warp_sum_d(acc.y);
+            if (lane == 0) {
+                double2* Gm = reinterpret_cast<double2*>(gram) + (size_t)j * SM * SM;
+                Gm[a * SM + b] = acc;
+                Gm[b * SM + a] = make_double2(acc.x, -acc.y);
+            }
+        } else {
+            const int a = task - npair;   // a < S: projection; a == S: norm
+            const double2* ma = tab + ((size_t)(a < S ? a : 0) * J + j) * Nz;
+            double nrm = 0.0;
+            for (int k = lane; k < Nz; k += 32) {
+                double2 e = make_double2((double)z[2 * (j * Nz + k)], (double)z[2 * (j * Nz + k) + 1]);
+                for (int t = 0; t < S; ++t) {
+                    const double2 m3 = tab[2 * plane + ((size_t)t * J + j) * Nz + k];
+                    e.x -= m3.x; e.y -= m3.y;
+                }
+                if (a < S) {
+                    const double2 t = zmulc(ma[k], e);
+                    acc.x += t.x; acc.y += t.y;
+                } else {
+                    nrm += e.x * e.x + e.y * e.y;
+                }
+            }
+            acc.x = warp_sum_d(acc.x); acc.y = warp_sum_d(acc.y); nrm = warp_sum_d(nrm);
+            if (lane == 0) {
+                double2* bv = reinterpret_cast<double2*>(nu_b) + (size_t)j * (SM + 1);
+                if (a < S) bv[a] = acc; else bv[SM] = make_double2(nrm, 0.0);
+            }
+        }
+    }
+}
+
+// ---------------------------------------------------------------- kappa / omega stage per (s, j), FP64
+// One block per (s, j).  V is written to an FP64 scratch row by row (thread per row).
+__global__ void k_stage_kappa(DevGeom G, DevParams Pm, DevState D, int S, int SC, const float* z,
+                              const double* gram, double* V64) {
+    const int s = blockIdx.x, j = blockIdx.y;
+    const int J = G.J, Nz = G.Nz, SM = Pm.S_max;
+    const int K = S - 1;                          // columns of M_{-s}
+    const double eb = D.eta_bar[j];
+    const size_t plane = (size_t)SM * J * Nz;
+    const double2* tab = reinterpret_cast<const double2*>(D.tab);
+    extern __shared__ double2 sh[];
+    double2* R = sh;                             // K x K upper, row-major
+    double2* ye = R + (size_t)K * K;             // V^H e0 / eb      (K)
+    double2* vm = ye + K;                        // V^H m^w          (K)
+    double2* v4 = vm + K;                        // V^H mu4          (K)
+    double* red = reinterpret_cast<double*>(v4 + K);   // reduction scratch [8]
+    const double2* Gm = reinterpret_cast<const double2*>(gram) + (size_t)j * SM * SM;
+    // column map c -> s'
+    auto col = [&](int c) { return c < s ? c : c + 1; };
+    // R R^H-free Cholesky: R^H R = I + G_{-s}/eb (upper R), right-looking
+    for (int t = threadIdx.x; t < K * K; t += blockDim.x) {
+        const int r = t / K, c = t - r * K;
+        double2 g = Gm[col(r) * SM + col(c)];
+        g.x /= eb; g.y /= eb;
+        if (r == c) g.x += 1.0;
+        R[t] = g;   // full Hermitian, upper part used
+    }
+    __syncthreads();
+    for (int k = 0; k < K; ++k) {
+        if (threadIdx.x == 0) {
+            const double d = sqrt(fmax(R[k * K + k].x, 1e-300));
+            R[k * K + k] = make_double2(d, 0.0);
+        }
+        __syncthreads();
+        const double dk = R[k * K + k].x;
+        for (int c = k + 1 + threadIdx.x; c < K; c += blockDim.x) {
+            const double2 v = R[k * K + c];
+            R[k * K + c] = make_double2(v.x / dk, v.y / dk);
+        }
+        __syncthreads();
+        // trailing update: A[r][c] -= conj(R[k][r]) R[k][c] for k < r <= c
+        const int n = K - k - 1;
+        for (int t = threadIdx.x; t < n * n; t += blockDim.x) {
+            const int r = k + 1 + t / n, c = k + 1 + t % n;
+            if (c >= r) {
+                const double2 u = zmulc(R[k * K + r], R[k * K + c]);
+                R[r * K + c].x -= u.x; R[r * K + c].y -= u.y;
+            }
+        }
+        __syncthreads();
+    }
+    // V rows: v_k R = m_k (forward substitution over columns); accumulate projections
+    for (int t = threadIdx.x; t < 3 * K; t += blockDim.x) (t < K ? ye : (t < 2 * K ? vm : v4))[t % K] = make_double2(0, 0);
+    if (threadIdx.x < 8) red[threadIdx.x] = 0.0;
+    __syncthreads();
+    double2* Vs = reinterpret_cast<double2*>(V64) + ((size_t)s * J + j) * Nz * SC;
+    for (int k = threadIdx.x; k < Nz; k += blockDim.x) {
+        double2 e0 = make_double2((double)z[2 * (j * Nz + k)], (double)z[2 * (j * Nz + k) + 1]);
+        for (int t = 0; t < S; ++t) {
+            if (t == s) continue;
+            const double2 m3 = tab[2 * plane + ((size_t)t * J + j) * Nz + k];
+            e0.x -= m3.x; e0.y -= m3.y;
+        }
+        const double2 mw = tab[1 * plane + ((size_t)s * J + j) * Nz + k];
+        const double2 m4 = tab[3 * plane + ((size_t)s * J + j) * Nz + k];
+        for (int c = 0; c < K; ++c) {
+            double2 acc = tab[0 * plane + ((size_t)col(c) * J + j) * Nz + k];
+            for (int c2 = 0; c2 < c; ++c2) {
+                const double2 u = zmul(Vs[(size_t)k * SC + c2], R[c2 * K + c]);
+                acc.x -= u.x; acc.y -= u.y;
+            }
+            const double d = R[c * K + c].x;
+            const double2 v = make_double2(acc.x / d, acc.y / d);
+            Vs[(size_t)k * SC + c] = v;
+            const double2 a1 = zmulc(v, e0), a2 = zmulc(v, mw), a3 = zmulc(v, m4);
+            atomicAdd(&ye[c].x, a1.x); atomicAdd(&ye[c].y, a1.y);
+            atomicAdd(&vm[c].x, a2.x); atomicAdd(&vm[c].y, a2.y);
+            atomicAdd(&v4[c].x, a3.x); atomicAdd(&v4[c].y, a3.y);
+        }
+        // scalar products for omega: |e0|^2, m^H e0, m^H m, mu4^H e0, mu4^H mu4, m^H mu4
+        atomicAdd(&red[0], e0.x * e0.x + e0.y * e0.y);
+        const double2 me = zmulc(mw, e0), mm4 = zmulc(mw, m4), ue = zmulc(m4, e0);
+        atomicAdd(&red[1], me.x); atomicAdd(&red[2], me.y);
+        atomicAdd(&red[3], mw.x * mw.x + mw.y * mw.y);
+        atomicAdd(&red[4], ue.x); atomicAdd(&red[5], ue.y);
+        atomicAdd(&red[6], m4.x * m4.x + m4.y * m4.y);
+        atomicAdd(&red[7], mm4.x);
+    }
+    __syncthreads();
+    // second scalar m^H mu4 imaginary part needed too: recompute cheaply below via projections
+    // ---- omega test (FP64), a^H A^-1 b = (a^H b - (V^H a)^H (V^H b)/eb)/eb
+    __shared__ double omega_llr;
+    __shared__ double mm4_im;
+    if (threadIdx.x == 0) mm4_im = 0.0;
+    __syncthreads();
+    for (int k = threadIdx.x; k < Nz; k += blockDim.x) {
+        const double2 mw = tab[1 * plane + ((size_t)s * J + j) * Nz + k];
+        const double2 m4 = tab[3 * plane + ((size_t)s * J + j) * Nz + k];
+        atomicAdd(&mm4_im, zmulc(mw, m4).y);
+    }
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        double pe0 = 0, pme_r = 0, pme_i = 0, pmm = 0, pue_r = 0, pue_i = 0, puu = 0, pmu_r = 0, pmu_i = 0;
+        for (int c = 0; c < K; ++c) {
+            const double2 a = ye[c], b = vm[c], u = v4[c];
+            pe0 += a.x * a.x + a.y * a.y;
+            const double2 t1 = zmulc(b, a); pme_r += t1.x; pme_i += t1.y;
+            pmm += b.x * b.x + b.y * b.y;
+            const double2 t2 = zmulc(u, a); pue_r += t2.x; pue_i += t2.y;
+            puu += u.x * u.x + u.y * u.y;
+            const double2 t3 = zmulc(b, u); pmu_r += t3.x; pmu_i += t3.y;
+        }
+        // e0^H A^-1 e0
+        const double Q00 = (red[0] - pe0 / eb) / eb;
+        // e1 = e0 - mu4
+        const double e1e1 = red[0] - 2.0 * red[4] + red[6];
+        const double pe1 = pe0 - 2.0 * pue_r + puu;
+        const double Q11 = (e1e1 - pe1 / eb) / eb;
+        const double mAm = (red[3] - pmm / eb) / eb;
+        // m^H A^-1 e1 = m^H A^-1 e0 - m^H A^-1 mu4
+        const double2 mAe0 = make_double2((red[1] - pme_r / eb) / eb, (red[2] - pme_i / eb) / eb);
+        const double2 mAu = make_double2((red[7] - pmu_r / eb) / eb, (mm4_im - pmu_i / eb) / eb);
+        const double2 mAe1 = make_double2(mAe0.x - mAu.x, mAe0.y - mAu.y);
+        const double llr = (mAe1.x * mAe1.x + mAe1.y * mAe1.y) / (1.0 + mAm) - Q11 + Q00 - log1p(mAm);
+        omega_llr = llr;
+        D.llr_w[s * J + j] = llr;
+        const double zeta = D.zeta[s * J + j];
+        double pr;
+        if (zeta >= 1.0) pr = 1.0;
+        else if (zeta <= 0.0) pr = 0.0;
+        else {
+            const double u = log(zeta) - log1p(-zeta) + llr;
+            pr = (u >= 0) ? 1.0 / (1.0 + exp(-u)) : exp(u) / (1.0 + exp(u));
+        }
+        D.bel[BEL_PPR + s * J + j] = pr;
+        // y~0 = V^H e0 / eb -> store; y0 = R^-1 y~0 (back substitution)
+        for (int c = 0; c < K; ++c) ye[c] = make_double2(ye[c].x / eb, ye[c].y / eb);
+    }
+    __syncthreads();
+    // r0 = e0 - V y~0 (rows), |r0|^2; store V, r0 as FP32
+    float2* kV = D.kV + ((size_t)s * J + j) * Nz * SC;
+    double* rr = red;   // reuse
+    if (threadIdx.x == 0) rr[0] = 0.0;
+    __syncthreads();
+    for (int k = threadIdx.x; k < Nz; k += blockDim.x) {
+        double2 e0 = make_double2((double)z[2 * (j * Nz + k)], (double)z[2 * (j * Nz + k) + 1]);
+        for (int t = 0; t < S; ++t) {
+            if (t == s) continue;
+            const double2 m3 = tab[2 * plane + ((size_t)t * J + j) * Nz + k];
+            e0.x -= m3.x; e0.y -= m3.y;
+        }
+        for (int c = 0; c < K; ++c) {
+            const double2 v = Vs[(size_t)k * SC + c];
+            const double2 u = zmul(v, ye[c]);
+            e0.x -= u.x; e0.y -= u.y;
+            kV[(size_t)k * SC + c] = make_float2((float)v.x, (float)v.y);
+        }
+        for (int c = K; c < SC - 1; ++c) kV[(size_t)k * SC + c] = make_float2(0.f, 0.f);
+        kV[(size_t)k * SC + SC - 1] = make_float2((float)e0.x, (float)e0.y);   // r0 in the last column
+        atomicAdd(&rr[0], e0.x * e0.x + e0.y * e0.y);
+    }
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        // y0 = R^-1 y~0
+        double2 y0[S_CAP_MAX];
+        double yy = 0.0;
+        for (int c = K - 1; c >= 0; --c) {
+            double2 a = ye[c];
+            for (int c2 = c + 1; c2 < K; ++c2) {
+                const double2 u = zmul(R[c * K + c2], y0[c2]);
+                a.x -= u.x; a.y -= u.y;
+            }
+            const double d = R[c * K + c].x;
+            y0[c] = make_double2(a.x / d, a.y / d);
+            yy += y0[c].x * y0[c].x + y0[c].y * y0[c].y;
+        }
+        float2* ky = D.ky0 + ((size_t)s * J + j) * SC;
+        for (int c = 0; c < SC; ++c) ky[c] = (c < K) ? make_float2((float)y0[c].x, (float)y0[c].y) : make_float2(0.f, 0.f);
+        D.kJ0[s * J + j] = rr[0] / eb + yy;
+    }
+    // R as FP32, padded with the identity
+    float2* kR = D.kR + ((size_t)s * J + j) * SC * SC;
+    for (int t = threadIdx.x; t < SC * SC; t += blockDim.x) {
+        const int r = t / SC, c = t - r * SC;
+        float2 v = make_float2(r == c ? 1.f : 0.f, 0.f);
+        if (r < K && c < K && c >= r) v = make_float2((float)R[r * K + c].x, (float)R[r * K + c].y);
+        kR[t] = v;
+    }
+}
+
+// ---------------------------------------------------------------- nu: Householder tridiagonalisation per j (FP64)
+// T = Q^H G Q real symmetric tridiagonal, b' = Q^H b with b = M^H e_all; the
+// off-diagonal phases are moved into b' so that T has non-negative off-diagonals.
+__global__ void k_nu_tridiag(DevParams Pm, DevState D, int S, const double* gram, const double* nu_b) {
+    const int j = blockIdx.x;
+    const int SM = Pm.S_max;
+    extern __shared__ double2 sh[];
+    double2* A = sh;                 // S x S
+    double2* v = A + (size_t)S * S;  // S
+    double2* pv = v + S;             // S
+    double2* b = pv + S;             // S
+    __shared__ double scal[4];
+    const double2* Gm = reinterpret_cast<const double2*>(gram) + (size_t)j * SM * SM;
+    const double2* bv = reinterpret_cast<const double2*>(nu_b) + (size_t)j * (SM + 1);
+    for (int t = threadIdx.x; t < S * S; t += blockDim.x) A[t] = Gm[(t / S) * SM + (t % S)];
+    for (int t = threadIdx.x; t < S; t += blockDim.x) b[t] = bv[t];
+    __syncthreads();
+    for (int k = 0; k + 2 < S; ++k) {
+        // x = A[k+1:, k]
+        if (threadIdx.x == 0) {
+            double nx = 0.0;
+            for (int i = k + 1; i < S; ++i) nx += A[i * S + k].x * A[i * S + k].x + A[i * S + k].y * A[i * S + k].y;
+            nx = sqrt(nx);
+            const double2 x0 = A[(k + 1) * S + k];
+            const double ax0 = sqrt(x0.x * x0.x + x0.y * x0.y);
+            const double2 ph = ax0 > 0 ? make_double2(x0.x / ax0, x0.y / ax0) : make_double2(1.0, 0.0);
+            // alpha = -ph * |x|; v = x - alpha e1
+            scal[0] = nx; scal[1] = ph.x; scal[2] = ph.y;
+            double vn = 0.0;
+            for (int i = k + 1; i < S; ++i) {
+                double2 vi = A[i * S + k];
+                if (i == k + 1) { vi.x += ph.x * nx; vi.y += ph.y * nx; }
+                v[i] = vi;
+                vn += vi.x * vi.x + vi.y * vi.y;
+            }
+            vn = sqrt(vn);
+            scal[3] = vn;
+            for (int i = k + 1; i < S; ++i) { if (vn > 0) { v[i].x /= vn; v[i].y /= vn; } else v[i] = make_double2(0, 0); }
+        }
+        __syncthreads();
+        if (scal[3] == 0.0) { __syncthreads(); continue; }
+        // p = A v (rows k+1..), restricted to the trailing block
+        for (int i = k + 1 + threadIdx.x; i < S; i += blockDim.x) {
+            double2 acc = make_double2(0, 0);
+            for (int c = k + 1; c < S; ++c) {
+                const double2 u = zmul(A[i * S + c], v[c]);
+                acc.x += u.x; acc.y += u.y;
+            }
+            pv[i] = acc;
+        }
+        __syncthreads();
+        if (threadIdx.x == 0) {
+            double Kr = 0.0;
+            for (int i = k + 1; i < S; ++i) Kr += zmulc(v[i], pv[i]).x;   // v^H A v (real)
+            for (int i = k + 1; i < S; ++i) { pv[i].x -= Kr * v[i].x; pv[i].y -= Kr * v[i].y; }   // w = p - K v
+            // b <- H b = b - 2 v (v^H b)
+            double2 vb = make_double2(0, 0);
+            for (int i = k + 1; i < S; ++i) { const double2 u = zmulc(v[i], b[i]); vb.x += u.x; vb.y += u.y; }
+            for (int i = k + 1; i < S; ++i) { const double2 u = zmul(v[i], vb); b[i].x -= 2.0 * u.x; b[i].y -= 2.0 * u.y; }
+        }
+        __syncthreads();
+        // A <- A - 2 v w^H - 2 w v^H on the trailing block; column k: below-diagonal -> alpha e1
+        for (int t = threadIdx.x; t < (S - k - 1) * (S - k - 1); t += blockDim.x) {
+            const int r = k + 1 + t / (S - k - 1), c = k + 1 + t % (S - k - 1);
+            const double2 a1 = zmul(v[r], make_double2(pv[c].x, -pv[c].y));
+            const double2 a2 = zmul(pv[r], make_double2(v[c].x, -v[c].y));
+            A[r * S + c].x -= 2.0 * (a1.x + a2.x);
+            A[r * S + c].y -= 2.0 * (a1.y + a2.y);
+        }
+        __syncthreads();
+        if (threadIdx.x == 0) {
+            const double2 al = make_double2(-scal[1] * scal[0], -scal[2] * scal[0]);
+            A[(k + 1) * S + k] = al;
+            A[k * S + k + 1] = make_double2(al.x, -al.y);
+            for (int i = k + 2; i < S; ++i) { A[i * S + k] = make_double2(0, 0); A[k * S + i] = make_double2(0, 0); }
+        }
+        __syncthreads();
+    }
+    if (threadIdx.x == 0) {
+        // make off-diagonals real non-negative: D = diag(e^{i th}), th_{k+1} = th_k + arg(e_k)
+        double* out = D.nu_T + (size_t)j * 4 * SM;   // [a(SM) | o(SM) | b'(2 SM)]
+        double2 ph = make_double2(1.0, 0.0);
+        for (int k = 0; k < S; ++k) {
+            out[k] = A[k * S + k].x;
+            // b'' = D^H b
+            const double2 bb = zmulc(ph, b[k]);
+            out[2 * SM + 2 * k] = bb.x;
+            out[2 * SM + 2 * k + 1] = bb.y;
+            if (k + 1 < S) {
+                const double2 e = A[(k + 1) * S + k];
+                const double ae = sqrt(e.x * e.x + e.y * e.y);
+                out[SM + k] = ae;
+                if (ae > 0) ph = zmul(ph, make_double2(e.x / ae, e.y / ae));
+            }
+        }
+        D.nu_c[2 * j] = bv[SM].x;   // |e_all|^2
+    }
+}
+
+void launch_table(const DevGeom& G, const DevParams& Pm, const DevState& D, int S, int nsplit, cudaStream_t st) {
+    const int Nz = G.Nz;
+    const int bs = Nz <= 256 ? ((Nz + 31) / 32) * 32 : 256;
+    const int ept = (Nz + bs - 1) / bs;
+    const int per_particle = (3 * G.Nf + G.My * G.Mz) * (int)sizeof(float2);
+    int chunk = 128;
+    while (chunk > 16 && chunk * per_particle > 96 * 1024) chunk /= 2;
+    const size_t smem = (size_t)chunk * per_particle;
+    dim3 grid(nsplit, S, G.J);
+    switch (ept) {
+        case 1: cudaFuncSetAttribute(k_table<1>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+                k_table<1><<<grid, bs, smem, st>>>(G, Pm, D, S, nsplit, chunk); break;
+        case 2: cudaFuncSetAttribute(k_table<2>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+                k_table<2><<<grid, bs, smem, st>>>(G, Pm, D, S, nsplit, chunk); break;
+        case 3: case 4: cudaFuncSetAttribute(k_table<4>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+                k_table<4><<<grid, bs, smem, st>>>(G, Pm, D, S, nsplit, chunk); break;
+        default: cudaFuncSetAttribute(k_table<8>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+                k_table<8><<<grid, bs, smem, st>>>(G, Pm, D, S, nsplit, chunk); break;
+    }
+    const int tot = S * G.J * Nz;
+    k_table_final<<<(tot + 255) / 256, 256, 0, st>>>(G, Pm, D, S, nsplit);
+}
+
+void launch_stage(const DevGeom& G, const DevParams& Pm, const DevState& D, int S, int SC, const float* z,
+                  double* gram, double* nu_b, double* V64, cudaStream_t st) {
+    const int npair = S * (S + 1) / 2 + S + 1;
+    const int gx = min(64, (npair + 7) / 8);
+    k_gram<<<dim3(gx, G.J), 256, 0, st>>>(G, Pm, D, S, z, gram, nu_b);
+    const int K = S - 1;
+    const size_t sm1 = ((size_t)K * K + 3 * (size_t)K) * sizeof(double2) + 8 * sizeof(double);
+    cudaFuncSetAttribute(k_stage_kappa, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm1);
+    k_stage_kappa<<<dim3(S, G.J), 256, sm1, st>>>(G, Pm, D, S, SC, z, gram, V64);
+    const size_t sm2 = ((size_t)S * S + 3 * (size_t)S) * sizeof(double2);
+    cudaFuncSetAttribute(k_nu_tridiag, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm2);
+    k_nu_tridiag<<<G.J, 128, sm2, st>>>(Pm, D, S, gram, nu_b);
+}
+
+}  // namespace bp
