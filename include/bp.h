@@ -200,6 +200,32 @@ enum { BP_PROF_STAGES = 9 };
 bp_status bp_set_profiling(bp_handle* h, int on);
 bp_status bp_get_profile(bp_handle* h, double* ms, int n);
 
+/* Systematic resampling of one belief that allocates no device memory.
+ * The paper has no counterpart: this entry point exists for callers that
+ * cannot call cudaMalloc (code under CUDA graph capture, real-time loops that
+ * forbid allocator calls, hosts whose device memory belongs to another
+ * allocator).  It runs the resampler bp_update applies to every belief, with
+ * its FP64 cumulative-weight scratch in a static device array of
+ * BP_NOALLOC_MAX_P doubles (8 MiB) that every GPU loading the library holds
+ * until the process exits.
+ *   w_dev   device, P non-negative weights (need not be normalised), read only
+ *   P       1 .. BP_NOALLOC_MAX_P; larger P returns BP_ERR_CAPACITY, nothing launched
+ *   seed, n, kind, index   select the uniform U exactly as bp_update does for
+ *           the belief (kind 0 = MT, 1 = PF slot index, 2 = eta of PA index)
+ *           at step n; particle i takes the first k with CDF_k >= (U + i)/P
+ *   idx_dev device, P ints, written
+ *   cuda_stream  stream of the launch (NULL = legacy default stream)
+ * Asynchronous.  The first call on each device looks up the array's device
+ * address with that device current, so it should come before any stream
+ * capture.  All calls share the array and it keeps the previous call's
+ * contents (the first P entries are overwritten before use); calls whose
+ * kernels may overlap on the GPU race and must be serialised by the caller.
+ * Returns BP_ERR_INVALID_ARG for NULL pointers or out-of-range arguments,
+ * BP_ERR_CUDA if the device address lookup or the launch fails. */
+enum { BP_NOALLOC_MAX_P = 1 << 20 };
+bp_status bp_resample_noalloc(const double* w_dev, int P, uint64_t seed, int n, int kind, int index,
+                              int* idx_dev, void* cuda_stream);
+
 #ifdef __cplusplus
 }
 #endif

@@ -24,7 +24,8 @@ DIAG_TABLE, DIAG_WEIGHTS, DIAG_LOGLIK, DIAG_INDICES = 1, 2, 3, 4
 
 ENTRY_POINTS = ("bp_init", "bp_predict", "bp_update", "bp_estimate", "bp_free", "bp_last_error",
                 "bp_get_state", "bp_set_state", "bp_get_predicted", "bp_set_predicted", "bp_get_diag",
-                "bp_synthesize", "bp_launch_count", "bp_set_profiling", "bp_get_profile")
+                "bp_synthesize", "bp_launch_count", "bp_set_profiling", "bp_get_profile",
+                "bp_resample_noalloc")
 PROFILE_STAGES = ("predict", "row_sums", "table", "stage", "kappa", "iota", "nu", "normalize", "resample")
 
 
@@ -94,6 +95,7 @@ def load() -> C.CDLL:
                                   vp, C.POINTER(C.c_double), vp]
     lib.bp_set_profiling.argtypes = [vp, C.c_int]
     lib.bp_get_profile.argtypes = [vp, C.POINTER(C.c_double), C.c_int]
+    lib.bp_resample_noalloc.argtypes = [vp, C.c_int, C.c_uint64, C.c_int, C.c_int, C.c_int, vp, vp]
     lib.bp_launch_count.argtypes = [vp]
     lib.bp_launch_count.restype = C.c_longlong
     for f in ENTRY_POINTS:
@@ -289,6 +291,24 @@ class Filter:
         n = P + S * P + J * P
         b = self._diag(DIAG_INDICES, n * 4, np.int32)
         return dict(x=b[:P], y=b[P:P + S * P].reshape(S, P), eta=b[P + S * P:].reshape(J, P))
+
+
+NOALLOC_MAX_P = 1 << 20
+
+
+def resample_noalloc(w, seed: int, n: int, kind: int, index: int, out=None, stream=None):
+    """Systematic resampling through bp_resample_noalloc (no device allocation inside
+    the library).  w: torch CUDA float64 tensor of P weights; returns int32 indices."""
+    import torch
+    lib = load()
+    P = int(w.numel())
+    if out is None:
+        out = torch.empty(P, dtype=torch.int32, device=w.device)
+    st = lib.bp_resample_noalloc(C.c_void_p(w.data_ptr()), P, C.c_uint64(seed), n, kind, index,
+                                 C.c_void_p(out.data_ptr()), C.c_void_p(_stream_handle(stream)))
+    if st != BP_OK:
+        raise BPError(st, "bp_resample_noalloc" + (f": P = {P} exceeds {NOALLOC_MAX_P}" if st == 3 else ""))
+    return out
 
 
 def synthesize(geom: Geometry, x_pos: np.ndarray, sfv: np.ndarray, rho: np.ndarray,
