@@ -192,7 +192,7 @@ def run_gpu(args, rank, world):
     f.set_profiling(True)
     ev0 = [torch.cuda.Event(enable_timing=True) for _ in range(args.steps)]
     ev1 = [torch.cuda.Event(enable_timing=True) for _ in range(args.steps)]
-    kappa_ms, prof_tot = [], {}
+    kappa_ms, prof_tot, repaired = [], {}, []
     l0 = f.launch_count()
     if world > 1:
         torch.distributed.barrier()
@@ -205,6 +205,7 @@ def run_gpu(args, rank, world):
                 f.step(z_all[args.warmup + i])
                 ev1[i].record(stream)
             pr = f.profile()                       # events recorded by the library on its stream
+            repaired.append(f.estimate()["iota_repaired"])
             kappa_ms.append(pr["kappa"])
             for k, v in pr.items():
                 prof_tot[k] = prof_tot.get(k, 0.0) + v
@@ -264,7 +265,8 @@ def run_gpu(args, rank, world):
                         "peak_basis": f"FP32 FMA lanes: {SMS} SMs x {FP32_LANES_PER_SM} x 2 flop x {sm_mhz:.0f} MHz (median sampled)"},
            "e2e": {"value": world * P * g.J / (t_e2e * 1e-3), "unit": UNIT, "h2d_bytes_per_step": h2d,
                    "d2h_bytes_per_step": d2h, "ms_per_step": t_e2e},
-           "gpu_launches": int(launches), "clocks": clocks}
+           "gpu_launches": int(launches), "clocks": clocks,
+           "iota_fp64_repaired_per_step": float(np.mean(repaired)) if repaired else 0.0}
     if rank == 0 and not args.no_cpu_baseline:
         out["cpu_baseline"] = cpu_baseline(wl, g, prm, scn, args.cpu_particles, z_all[:1].cpu().numpy())
     f.close()

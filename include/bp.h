@@ -116,6 +116,7 @@ typedef struct {
     double* phi_hat;
     double* p_pr;
     int* declared;
+    int iota_repaired;   /* particles whose MT likelihood was recomputed in FP64 (ill-conditioned) */
 } bp_estimate_out;
 
 /* Creates a filter: validates, copies the geometry and parameters, allocates

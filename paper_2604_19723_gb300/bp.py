@@ -64,7 +64,7 @@ class _Estimate(C.Structure):
                 ("x_hat", C.c_double * 6), ("ess_x", C.c_double),
                 ("eta_hat", C.POINTER(C.c_double)), ("p_s", C.POINTER(C.c_double)),
                 ("phi_hat", C.POINTER(C.c_double)), ("p_pr", C.POINTER(C.c_double)),
-                ("declared", C.POINTER(C.c_int))]
+                ("declared", C.POINTER(C.c_int)), ("iota_repaired", C.c_int)]
 
 
 _lib = None
@@ -198,12 +198,12 @@ class Filter:
         eta = np.zeros(J); ps = np.zeros(SM); ph = np.zeros((SM, 6)); pr = np.zeros((SM, J))
         dec = np.zeros(SM, np.int32)
         e = _Estimate(0, 0, 0, 0, (C.c_double * 6)(), 0.0, _dptr(eta), _dptr(ps), _dptr(ph), _dptr(pr),
-                      dec.ctypes.data_as(C.POINTER(C.c_int)))
+                      dec.ctypes.data_as(C.POINTER(C.c_int)), 0)
         _check(self.lib, self.h, self.lib.bp_estimate(self.h, C.byref(e)), "bp_estimate")
         S = e.S
         return dict(n=e.n, S=S, S_next=e.S_next, births_skipped=e.births_skipped, x_hat=np.array(e.x_hat[:]),
                     ess_x=e.ess_x, eta_hat=eta, p_s=ps[:S].copy(), phi_hat=ph[:S].copy(), p_pr=pr[:S].copy(),
-                    declared=dec[:S].astype(bool))
+                    declared=dec[:S].astype(bool), iota_repaired=e.iota_repaired)
 
     def _view(self, S):
         J, P = self.geom.J, self.P

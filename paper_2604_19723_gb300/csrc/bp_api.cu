@@ -89,6 +89,18 @@ static void fill_geom(DevGeom& G, const bp_geometry* g) {
     for (int f = 0; f < g->Nf; ++f) G.f[f] = (g->Nf == 1) ? 0.0 : -0.5 * g->B + f * (g->B / (g->Nf - 1));
     for (int y = 0; y < g->My; ++y) G.py[y] = g->p_y[y];
     for (int m = 0; m < g->Mz; ++m) G.pz[m] = g->p_z[m];
+    // float-float constants for the phase reductions (cycles)
+    const double il = 1.0 / G.lam;
+    G.inv_lam_hi = (float)il;
+    G.inv_lam_lo = (float)(il - (double)G.inv_lam_hi);
+    for (int f = 0; f < g->Nf; ++f) {
+        const double v = G.f[f] / G.c;
+        G.fc_hi[f] = (float)v;
+        G.fc_lo[f] = (float)(v - (double)G.fc_hi[f]);
+    }
+    for (int y = 0; y < g->My; ++y) G.py_l[y] = (float)(G.py[y] / G.lam);
+    for (int m = 0; m < g->Mz; ++m) G.pz_l[m] = (float)(G.pz[m] / G.lam);
+    G.amp_c = (float)(G.lam / (4.0 * M_PI));
 }
 
 extern "C" {
@@ -149,6 +161,8 @@ bp_status bp_init(const bp_geometry* geom, const bp_params* prm, int P, int S_ma
     ok &= dalloc(h, &D.lw_y, (size_t)S_max * PP);
     ok &= dalloc(h, &D.lw_eta, (size_t)J * PP);
     ok &= dalloc(h, &D.llr_w, (size_t)S_max * J);
+    ok &= dalloc(h, &D.geo, (size_t)S_max * J * PP);
+    ok &= dalloc(h, &D.flags, PP + 1);
     ok &= dalloc(h, &D.tab, (size_t)4 * S_max * J * Nz * 2);
     ok &= dalloc(h, &D.tab_part, (size_t)h->nsplit_max * 3 * S_max * J * Nz * 2);
     ok &= dalloc(h, &D.W, (size_t)S_max);
@@ -239,6 +253,7 @@ bp_status bp_update(bp_handle* h, const float* z_dev) {
     int nsplit = std::max(1, (4 * 152 + S * J - 1) / (S * J));
     nsplit = std::min(nsplit, std::max(1, P / 256));
     nsplit = std::min(nsplit, h->nsplit_max);
+    launch_geom(h->G, h->Pm, D, S, h->st);
     launch_table(h->G, h->Pm, D, S, nsplit, h->st);
     mark(h, 3);
     launch_stage(h->G, h->Pm, D, S, h->SCA, z_dev, h->gram, h->nu_b, h->V64, h->st);
@@ -246,6 +261,7 @@ bp_status bp_update(bp_handle* h, const float* z_dev) {
     launch_kappa(h->G, h->Pm, D, S, h->SCA, h->st);
     mark(h, 5);
     launch_iota(h->G, h->Pm, D, S, z_dev, h->st);
+    launch_iota_repair(h->G, h->Pm, D, S, z_dev, h->st);
     mark(h, 6);
     launch_nu(h->G, h->Pm, D, S, h->st);
     mark(h, 7);
@@ -256,7 +272,7 @@ bp_status bp_update(bp_handle* h, const float* z_dev) {
         cudaEventRecord(h->ev[BP_PROF_STAGES], h->st);
         for (int i = 1; i < BP_PROF_STAGES; ++i) h->ev_valid[i] = true;
     }
-    h->launches += 1 + 2 + 3 + 1 + 1 + 1 + 5 + 3;
+    h->launches += 1 + 3 + 3 + 1 + 2 + 1 + 5 + 3;
     h->D.cur = 1 - h->D.cur;
     h->S_upd = S;
     h->phase = 0;
@@ -284,6 +300,7 @@ bp_status bp_estimate(bp_handle* h, bp_estimate_out* o) {
     o->births_skipped = h->births_skipped;
     for (int k = 0; k < 6; ++k) o->x_hat[k] = e[E.x_hat() + k];
     o->ess_x = e[E.ess()];
+    o->iota_repaired = (int)e[E.repaired()];
     const int S = o->S;
     if (o->eta_hat) for (int j = 0; j < h->J; ++j) o->eta_hat[j] = e[E.eta_hat() + j];
     if (o->p_s) for (int s = 0; s < S; ++s) o->p_s[s] = e[E.p_s() + s];

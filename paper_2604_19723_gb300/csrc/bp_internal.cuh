@@ -24,6 +24,11 @@ struct DevGeom {
     double R[J_MAX][9];      // row-major, columns = local axes (global coords)
     double f[NF_MAX];        // baseband frequencies
     double py[MY_MAX], pz[MZ_MAX];
+    // float-float constants for phases in cycles: 1/lambda, f_k/c; FP32 p/lambda
+    float inv_lam_hi, inv_lam_lo;
+    float fc_hi[NF_MAX], fc_lo[NF_MAX];
+    float py_l[MY_MAX], pz_l[MZ_MAX];
+    float amp_c;             // lambda / (4 pi)
 };
 
 struct DevParams {
@@ -145,6 +150,21 @@ __device__ inline PathGeo path_geo(const DevGeom& G, int j, double px, double py
 // fractional part in [-1/2, 1/2]
 __device__ inline double frac_c(double t) { return t - rint(t); }
 
+// Fractional part (in [-1/2, 1/2]) of the float-float product (ah + al)(bh + bl),
+// with the leading product split exactly by FMA (Dekker/Ogita two-product):
+// about 1e-8 absolute accuracy for products up to ~1e3 cycles, all in FP32.
+__device__ inline float ff_frac_mul(float ah, float al, float bh, float bl) {
+    const float p = ah * bh;
+    const float e = fmaf(ah, bh, -p);
+    const float n = rintf(p);
+    const float t = e + ah * bl + al * bh;
+    return (p - n) + t;
+}
+
+// Geometry record of one (particle, feature, PA): distance |r'| as a float-float
+// pair and the local direction cosines u_y, u_z (FP32).
+struct GeoRec { float d_hi, d_lo, uy, uz; };
+
 // ------------------------------------------------------------------ complex / double-float helpers
 __host__ __device__ inline float2 cmul(float2 a, float2 b) { return make_float2(a.x * b.x - a.y * b.y, a.x * b.y + a.y * b.x); }
 __host__ __device__ inline float2 cmulc(float2 a, float2 b) {  // conj(a) * b
@@ -153,11 +173,61 @@ __host__ __device__ inline float2 cmulc(float2 a, float2 b) {  // conj(a) * b
 __host__ __device__ inline double2 zmul(double2 a, double2 b) { return make_double2(a.x * b.x - a.y * b.y, a.x * b.y + a.y * b.x); }
 __host__ __device__ inline double2 zmulc(double2 a, double2 b) { return make_double2(a.x * b.x + a.y * b.y, a.x * b.y - a.y * b.x); }
 
-// error-free sum (Knuth TwoSum)
+// ------------------------------------------------------------------ float-float (FP32 pairs)
+// Error-free transformations (Knuth TwoSum, Dekker/FMA TwoProd) and the
+// float-float operations built on them (about 44 significant bits).
 __device__ inline void two_sum(float a, float b, float& s, float& e) {
     s = __fadd_rn(a, b);
     const float bb = __fsub_rn(s, a);
     e = __fadd_rn(__fsub_rn(a, __fsub_rn(s, bb)), __fsub_rn(b, bb));
+}
+__device__ inline void fast_two_sum(float a, float b, float& s, float& e) {   // |a| >= |b|
+    s = __fadd_rn(a, b);
+    e = __fsub_rn(b, __fsub_rn(s, a));
+}
+struct ff { float hi, lo; };
+__device__ inline ff ff_add(ff x, ff y) {
+    float s, e;
+    two_sum(x.hi, y.hi, s, e);
+    e = __fadd_rn(e, __fadd_rn(x.lo, y.lo));
+    ff r;
+    fast_two_sum(s, e, r.hi, r.lo);
+    return r;
+}
+__device__ inline ff ff_neg(ff x) { return ff{-x.hi, -x.lo}; }
+__device__ inline ff ff_mul(ff x, ff y) {
+    const float p = __fmul_rn(x.hi, y.hi);
+    float e = fmaf(x.hi, y.hi, -p);
+    e = fmaf(x.hi, y.lo, fmaf(x.lo, y.hi, e));
+    ff r;
+    fast_two_sum(p, e, r.hi, r.lo);
+    return r;
+}
+__device__ inline ff ff_prod(float a, float b) {       // exact product of two floats
+    const float p = __fmul_rn(a, b);
+    return ff{p, fmaf(a, b, -p)};
+}
+__device__ inline ff ff_div(ff x, ff y) {              // one Newton correction
+    const float q = __fdiv_rn(x.hi, y.hi);
+    const ff r = ff_add(x, ff_neg(ff_mul(ff{q, 0.f}, y)));
+    const float q2 = __fdiv_rn(r.hi, y.hi);
+    ff out;
+    fast_two_sum(q, q2, out.hi, out.lo);
+    return out;
+}
+struct cff { ff re, im; };
+__device__ inline cff cff_add(cff a, cff b) { return cff{ff_add(a.re, b.re), ff_add(a.im, b.im)}; }
+__device__ inline cff cff_sub(cff a, cff b) { return cff{ff_add(a.re, ff_neg(b.re)), ff_add(a.im, ff_neg(b.im))}; }
+__device__ inline cff cff_mul(cff a, cff b) {
+    return cff{ff_add(ff_mul(a.re, b.re), ff_neg(ff_mul(a.im, b.im))), ff_add(ff_mul(a.re, b.im), ff_mul(a.im, b.re))};
+}
+__device__ inline cff cff_mulc(cff a, cff b) {         // conj(a) * b
+    return cff{ff_add(ff_mul(a.re, b.re), ff_mul(a.im, b.im)), ff_add(ff_mul(a.re, b.im), ff_neg(ff_mul(a.im, b.re)))};
+}
+__device__ inline cff cff_from(float2 v) { return cff{ff{v.x, 0.f}, ff{v.y, 0.f}}; }
+// exact conj(a) * b of two FP32 complex numbers
+__device__ inline cff cff_prodc(float2 a, float2 b) {
+    return cff{ff_add(ff_prod(a.x, b.x), ff_prod(a.y, b.y)), ff_add(ff_prod(a.x, b.y), ff_neg(ff_prod(a.y, b.x)))};
 }
 
 __device__ inline double warp_sum_d(double v) {
@@ -201,6 +271,8 @@ struct DevState {
     double* lw_eta;   // J x P
     double* llr_w;    // S_max x J   log omega(1) - log omega(0)
     // message table (FP64) and derived per-(s,j) quantities
+    float4* geo;      // [S_max][J][P] GeoRec of the current prediction
+    int* flags;       // [0] count of flagged particles, then their indices (iota repair)
     double* tab;      // [4][S_max][J][Nz] double2 : m, mw, mu3, mu4
     double* tab_part; // table partial sums [nsplit][3][S_max][J][Nz] double2
     double* W;        // S_max    sum_p w_alpha

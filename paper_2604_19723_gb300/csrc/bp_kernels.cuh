@@ -20,18 +20,50 @@ struct EstLayout {
     __host__ __device__ size_t S_next() const { return 2; }
     __host__ __device__ size_t skipped() const { return 3; }
     __host__ __device__ size_t status() const { return 4; }
-    __host__ __device__ size_t x_hat() const { return 5; }
-    __host__ __device__ size_t ess() const { return 11; }
-    __host__ __device__ size_t eta_hat() const { return 12; }
-    __host__ __device__ size_t p_s() const { return 12 + J; }
-    __host__ __device__ size_t phi_hat() const { return 12 + J + S_max; }
-    __host__ __device__ size_t p_pr() const { return 12 + J + 7 * S_max; }
-    __host__ __device__ size_t p_any() const { return 12 + J + 7 * S_max + S_max * J; }
-    __host__ __device__ size_t declared() const { return 12 + J + 8 * S_max + S_max * J; }
-    __host__ __device__ size_t total() const { return 12 + J + 9 * S_max + S_max * J; }
+    __host__ __device__ size_t repaired() const { return 5; }
+    __host__ __device__ size_t x_hat() const { return 6; }
+    __host__ __device__ size_t ess() const { return 12; }
+    __host__ __device__ size_t eta_hat() const { return 13; }
+    __host__ __device__ size_t p_s() const { return 13 + J; }
+    __host__ __device__ size_t phi_hat() const { return 13 + J + S_max; }
+    __host__ __device__ size_t p_pr() const { return 13 + J + 7 * S_max; }
+    __host__ __device__ size_t p_any() const { return 13 + J + 7 * S_max + S_max * J; }
+    __host__ __device__ size_t declared() const { return 13 + J + 8 * S_max + S_max * J; }
+    __host__ __device__ size_t total() const { return 13 + J + 9 * S_max + S_max * J; }
 };
 
 constexpr int RED_W = 29;   // per-block partial sums: S0, S1[6], S2[21] (upper, row-major), sum w^2
+
+// Steering-vector factors from a geometry record, FP32 only:
+// psi = c (b kron a_y kron a_z), c = lambda/(4 pi d) e^{-i 2 pi d/lambda},
+// b_f = e^{-i 2 pi f_f d/c}, a_y = e^{i 2 pi p_y u_y/lambda}, a_z = e^{i 2 pi p_z u_z/lambda}
+// (eq. array-response, unit-modulus-array-response); phases reduced to cycles
+// with float-float products.
+__device__ inline float2 factors_from_geo(const DevGeom& G, float4 g, float2* b, float2* ay, float2* az, int stride) {
+    const float d = g.x + g.y;
+    const float A = G.amp_c / d;
+    float s, c;
+    sincospif(-2.0f * ff_frac_mul(g.x, g.y, G.inv_lam_hi, G.inv_lam_lo), &s, &c);
+    for (int f = 0; f < G.Nf; ++f) {
+        float sf, cf;
+        sincospif(-2.0f * ff_frac_mul(g.x, g.y, G.fc_hi[f], G.fc_lo[f]), &sf, &cf);
+        b[f * stride] = make_float2(cf, sf);
+    }
+    for (int y = 0; y < G.My; ++y) {
+        float sy, cy;
+        sincospif(2.0f * G.py_l[y] * g.z, &sy, &cy);
+        ay[y * stride] = make_float2(cy, sy);
+    }
+    for (int m = 0; m < G.Mz; ++m) {
+        float sz, cz;
+        sincospif(2.0f * G.pz_l[m] * g.w, &sz, &cz);
+        az[m * stride] = make_float2(cz, sz);
+    }
+    return make_float2(A * c, A * s);
+}
+
+void launch_geom(const DevGeom& G, const DevParams& Pm, const DevState& D, int S, cudaStream_t st);
+void launch_iota_repair(const DevGeom& G, const DevParams& Pm, const DevState& D, int S, const float* z, cudaStream_t st);
 
 void launch_init(const DevGeom& G, const DevParams& Pm, const DevState& D, cudaStream_t st);
 void launch_predict(const DevGeom& G, const DevParams& Pm, const DevState& D, int n, int S_old, int S_new, cudaStream_t st);

@@ -18,48 +18,12 @@
 //  nu~(eta^(j,p)) for every (j, p) through the tridiagonal form of G = M^H M.
 //
 // Steering vectors psi_s^(j,p) = lambda/(4 pi d) e^{-i 2 pi d/lambda} (b kron a_y kron a_z)
-// (eq. array-response, unit-modulus-array-response) with d and the local
-// direction from FP64 geometry and every phase reduced to cycles in FP64.
+// (eq. array-response, unit-modulus-array-response) are rebuilt in FP32 from the
+// per-(p, s, j) geometry records of k_geom (FP64 distance and direction).
 #include "bp_internal.cuh"
 #include "bp_kernels.cuh"
 
 namespace bp {
-
-// FP32 factors of one steering vector; carrier and amplitude in c.
-struct Factors {
-    float2 c;
-    double A, d;
-};
-
-__device__ inline Factors steering_factors(const DevGeom& G, int j, float px, float py, float pz,
-                                           float sx, float sy, float sz, bool los,
-                                           float2* b, float2* ay, float2* az, int stride) {
-    const PathGeo pg = path_geo(G, j, px, py, pz, sx, sy, sz, los);
-    Factors F;
-    F.d = pg.d;
-    F.A = G.lam / (4.0 * M_PI * pg.d);
-    double sc, cc;
-    sincospi(-2.0 * frac_c(pg.d / G.lam), &sc, &cc);
-    F.c = make_float2((float)(F.A * cc), (float)(F.A * sc));
-    const double tau = pg.d / G.c;
-    for (int f = 0; f < G.Nf; ++f) {
-        float s, c;
-        sincospif((float)(-2.0 * frac_c(G.f[f] * tau)), &s, &c);
-        b[f * stride] = make_float2(c, s);
-    }
-    const float uy = (float)pg.uy, uz = (float)pg.uz;
-    for (int y = 0; y < G.My; ++y) {
-        float s, c;
-        sincospif(2.0f * (float)(G.py[y] / G.lam) * uy, &s, &c);
-        ay[y * stride] = make_float2(c, s);
-    }
-    for (int m = 0; m < G.Mz; ++m) {
-        float s, c;
-        sincospif(2.0f * (float)(G.pz[m] / G.lam) * uz, &s, &c);
-        az[m * stride] = make_float2(c, s);
-    }
-    return F;
-}
 
 // ---------------------------------------------------------------- kappa
 // block = (particle tile of KT threads, s); loop over j; V_{s,j} staged in shared memory.
@@ -79,10 +43,8 @@ __global__ void __launch_bounds__(128) k_kappa(DevGeom G, DevParams Pm, DevState
     const int p = blockIdx.x * KT + tid;
     const bool act = p < P;
     const int pp = act ? p : 0;
-    const float* x = D.x[D.cur];
     const float* ph = D.phi[D.cur] + (size_t)s * 6 * P;
-    const float px = x[pp], py = x[P + pp], pz = x[2 * P + pp];
-    const float sx = ph[pp], sy = ph[P + pp], sz = ph[2 * P + pp];
+    const float4* geo_s = D.geo + (size_t)s * J * P;
     const double gm = ph[3 * P + pp];
     const double mr = ph[4 * P + pp], mi = ph[5 * P + pp];
     double delta_sum = 0.0;
@@ -110,7 +72,7 @@ __global__ void __launch_bounds__(128) k_kappa(DevGeom G, DevParams Pm, DevState
         float2* fb = fac + tid;
         float2* fy = fb + G.Nf * KT;
         float2* fz = fy + G.My * KT;
-        const Factors F = steering_factors(G, j, px, py, pz, sx, sy, sz, s == 0, fb, fy, fz, KT);
+        const float2 Fc = factors_from_geo(G, geo_s[(size_t)j * P + pp], fb, fy, fz, KT);
         // pass 1: h = psi^H V, pr = psi^H r0
         float2 h[NC];
         #pragma unroll
@@ -118,7 +80,7 @@ __global__ void __launch_bounds__(128) k_kappa(DevGeom G, DevParams Pm, DevState
         float2 pr = make_float2(0.f, 0.f);
         float nps = 0.f;
         for (int f = 0; f < G.Nf; ++f) {
-            const float2 cb = cmul(F.c, fb[f * KT]);
+            const float2 cb = cmul(Fc, fb[f * KT]);
             for (int y = 0; y < G.My; ++y) {
                 const float2 w = cmul(cb, fy[y * KT]);
                 for (int m = 0; m < G.Mz; ++m) {
@@ -158,7 +120,7 @@ __global__ void __launch_bounds__(128) k_kappa(DevGeom G, DevParams Pm, DevState
         double rr = 0.0;
         float pn = 0.f;
         for (int f = 0; f < G.Nf; ++f) {
-            const float2 cb = cmul(F.c, fb[f * KT]);
+            const float2 cb = cmul(Fc, fb[f * KT]);
             for (int y = 0; y < G.My; ++y) {
                 const float2 w = cmul(cb, fy[y * KT]);
                 float rr_chunk = 0.f;          // FP32 over the Mz antennas, FP64 across chunks
@@ -216,201 +178,182 @@ __global__ void __launch_bounds__(128) k_kappa(DevGeom G, DevParams Pm, DevState
 }
 
 // ---------------------------------------------------------------- iota (warp per particle)
-// The S x S algebra (Gram of the paired steering vectors, Cholesky, solves) is
-// in FP64: the Gram is accumulated from exact FP32 x FP32 products, so that
-// log det(eta_bar I + D G D) stays accurate when two columns nearly coincide
-// (a FP32 Gram loses 1 - |rho|^2 to rounding).  The residual is FP32.
-// per-warp shared memory: factors [S][nfac] (float2), c [S] (double2), c32 [S] (float2),
-// d [S] (double), cm [S] (double2), g [S] (double2), A packed lower [S(S+1)/2] (double2)
-__device__ inline int tri(int i, int j) { return i * (i + 1) / 2 + j; }
+// Fast path in FP32: factors from the geometry records, g = Psi^H z, the Gram
+// G = Psi^H Psi from the Kronecker factors, Cholesky of eta_bar I + D G D,
+// solves, and the element-wise residual (squared sums in FP64).  The FP32
+// log det loses accuracy when a pivot cancels, i.e. when a column nearly lies
+// in the span of the previous ones (1 - |rho|^2 small, e.g. a fresh birth PF
+// next to a real component): each pivot's ratio A_kk / L_kk^2 measures that
+// loss, and particles with sqrt(sum ratio^2) > IOTA_RATIO_MAX are queued for
+// k_iota_ff, which recomputes them with a float-float Gram and factorisation.
+// The FP32 log det error per pivot is about 8 eps ratio (measured), so the
+// bound keeps unrepaired particles within ~5e-5 in log-likelihood.
+constexpr float IOTA_RATIO_MAX = 100.0f;
 
-// bytes of one warp's region, rounded up to 16 so that every warp's double2 arrays stay aligned
-__host__ __device__ inline size_t iota_warp_bytes(int S, int nfac) {
-    const size_t b = (size_t)S * 16 * 3                  // cS, cmS, gS (double2)
-                   + (size_t)S * (S + 1) / 2 * 16        // A packed (double2)
-                   + (size_t)S * 8                       // dS (double)
-                   + (size_t)S * 8                       // c32 (float2)
-                   + (size_t)S * nfac * 8;               // factors (float2)
-    return (b + 15) / 16 * 16;
+__device__ inline int tri(int i, int j) { return i * (i + 1) / 2 + j; }
+__device__ inline void tri_ab(int t, int& a, int& b) {
+    a = (int)((sqrtf(8.f * t + 1.f) - 1.f) * 0.5f);
+    while ((a + 1) * (a + 2) / 2 <= t) ++a;
+    while (a * (a + 1) / 2 > t) --a;
+    b = t - a * (a + 1) / 2;
+}
+
+// per-warp shared memory of the FP32 path (float2 units)
+__host__ __device__ inline size_t iota32_warp_f2(int S, int nfac, int Nf) {
+    return (size_t)S * nfac + 4 * (size_t)S + (size_t)S * (S + 1) / 2 + (size_t)S * Nf + (size_t)S;
 }
 
 __global__ void k_iota(DevGeom G, DevParams Pm, DevState D, int S, const float* z) {
-    extern __shared__ double2 smd[];
+    extern __shared__ float2 sm32[];
     const int lane = threadIdx.x & 31, wib = threadIdx.x >> 5;
     const int wpb = blockDim.x >> 5;
-    const int P = Pm.P, J = G.J, Nz = G.Nz, Nm = G.My * G.Mz;
-    const int nfac = G.Nf + G.My + G.Mz;
-    float2* zs = reinterpret_cast<float2*>(smd);                               // [Nz]
-    char* base = reinterpret_cast<char*>(smd) + (((size_t)Nz * 8 + 15) / 16) * 16 + wib * iota_warp_bytes(S, nfac);
-    double2* cS = reinterpret_cast<double2*>(base);                            // [S]
-    double2* cmS = cS + S;                                                     // [S]
-    double2* gS = cmS + S;                                                     // [S]
-    double2* Am = gS + S;                                                      // [S(S+1)/2]
-    double* dS = reinterpret_cast<double*>(Am + (size_t)S * (S + 1) / 2);      // [S]
-    float2* c32 = reinterpret_cast<float2*>(dS + S);                           // [S]
-    float2* fac = c32 + S;                                                     // [S][nfac]
+    const int P = Pm.P, J = G.J, Nz = G.Nz, Nm = G.My * G.Mz, Nf = G.Nf;
+    const int nfac = Nf + G.My + G.Mz;
+    float2* zs = sm32;                                                    // [Nz]
+    float2* base = zs + Nz + wib * iota32_warp_f2(S, nfac, Nf);
+    float2* fac = base;                                                   // [S][nfac]
+    float2* cS = fac + (size_t)S * nfac;                                  // [S] carrier*amplitude
+    float2* cmS = cS + S;                                                 // [S] pi mu, then w
+    float2* gS = cmS + S;                                                 // [S] g, rhs, solution
+    float2* dS = gS + S;                                                  // [S] (d, A_kk)
+    float2* Am = dS + S;                                                  // [S(S+1)/2] packed lower
+    float2* gpart = Am + (size_t)S * (S + 1) / 2;                         // [S][Nf] partial g
     const int p = blockIdx.x * wpb + wib;
     const bool act = p < P;
     const int pp = act ? p : 0;
-    const float* x = D.x[D.cur];
     const float* phi = D.phi[D.cur];
-    double total = 0.0;
+    double total = 0.0, ratio2 = 0.0;
     for (int j = 0; j < J; ++j) {
         __syncthreads();
         for (int k = threadIdx.x; k < Nz; k += blockDim.x)
             zs[k] = make_float2(z[2 * (j * Nz + k)], z[2 * (j * Nz + k) + 1]);
         __syncthreads();
         const double eb = D.eta_bar[j];
+        const float ebf = (float)eb;
         // 1. factors and coefficients, lanes over s
         for (int s = lane; s < S; s += 32) {
             const float* ph = phi + (size_t)s * 6 * P;
             float2* fs = fac + (size_t)s * nfac;
-            const Factors F = steering_factors(G, j, x[pp], x[P + pp], x[2 * P + pp], ph[pp], ph[P + pp], ph[2 * P + pp],
-                                               s == 0, fs, fs + G.Nf, fs + G.Nf + G.My, 1);
-            double sc, cc;
-            sincospi(-2.0 * frac_c(F.d / G.lam), &sc, &cc);
-            cS[s] = make_double2(F.A * cc, F.A * sc);
-            c32[s] = F.c;
-            const double pi = D.zeta[s * J + j] * D.W[s];
-            const double gm = ph[3 * P + pp], mr = ph[4 * P + pp], mi = ph[5 * P + pp];
-            dS[s] = sqrt(fmax(pi * (gm + (mr * mr + mi * mi) * (1.0 - pi)), 0.0));
-            cmS[s] = make_double2(pi * mr, pi * mi);
+            cS[s] = factors_from_geo(G, D.geo[((size_t)s * J + j) * P + pp], fs, fs + Nf, fs + Nf + G.My, 1);
+            const float pi = (float)(D.zeta[s * J + j] * D.W[s]);
+            const float gm = ph[3 * P + pp], mr = ph[4 * P + pp], mi = ph[5 * P + pp];
+            dS[s] = make_float2(sqrtf(fmaxf(pi * (gm + (mr * mr + mi * mi) * (1.0f - pi)), 0.0f)), 0.f);
+            cmS[s] = make_float2(pi * mr, pi * mi);
         }
         __syncwarp();
-        // 2. g_s = psi_s^H z (lanes over s, separable contraction, FP32 -> FP64)
-        for (int s = lane; s < S; s += 32) {
+        // 2. g_s = psi_s^H z: tasks (s, f) contract over the antennas, then sum over f
+        for (int t = lane; t < S * Nf; t += 32) {
+            const int s = t / Nf, f = t - s * Nf;
             const float2* fs = fac + (size_t)s * nfac;
-            float2 acc = make_float2(0.f, 0.f);
-            for (int f = 0; f < G.Nf; ++f) {
-                float2 accy = make_float2(0.f, 0.f);
-                for (int y = 0; y < G.My; ++y) {
-                    float2 accm = make_float2(0.f, 0.f);
-                    for (int m = 0; m < G.Mz; ++m) {
-                        const float2 t = cmulc(fs[G.Nf + G.My + m], zs[f * Nm + y * G.Mz + m]);
-                        accm.x += t.x; accm.y += t.y;
-                    }
-                    const float2 t = cmulc(fs[G.Nf + y], accm);
-                    accy.x += t.x; accy.y += t.y;
+            float2 accy = make_float2(0.f, 0.f);
+            for (int y = 0; y < G.My; ++y) {
+                float2 accm = make_float2(0.f, 0.f);
+                for (int m = 0; m < G.Mz; ++m) {
+                    const float2 u = cmulc(fs[Nf + G.My + m], zs[f * Nm + y * G.Mz + m]);
+                    accm.x += u.x; accm.y += u.y;
                 }
-                const float2 t = cmulc(fs[f], accy);
-                acc.x += t.x; acc.y += t.y;
+                const float2 u = cmulc(fs[Nf + y], accm);
+                accy.x += u.x; accy.y += u.y;
             }
-            gS[s] = zmulc(cS[s], make_double2(acc.x, acc.y));
+            gpart[t] = cmulc(fs[f], accy);
         }
-        // 3. Gram G_ab = psi_a^H psi_b (a >= b) from the Kronecker factors, FP64 accumulation
+        // 3. Gram (packed lower) from the Kronecker factors
         const int npair = S * (S + 1) / 2;
         for (int t = lane; t < npair; t += 32) {
-            int a = (int)((sqrtf(8.f * t + 1.f) - 1.f) * 0.5f);
-            while ((a + 1) * (a + 2) / 2 <= t) ++a;
-            while (a * (a + 1) / 2 > t) --a;
-            const int b = t - a * (a + 1) / 2;
+            int a, b;
+            tri_ab(t, a, b);
             const float2* fa = fac + (size_t)a * nfac;
-            const float2* fbb = fac + (size_t)b * nfac;
-            double2 sf = make_double2(0, 0), sy = sf, sz = sf;
-            for (int f = 0; f < G.Nf; ++f) {
-                const double2 u = zmulc(make_double2(fa[f].x, fa[f].y), make_double2(fbb[f].x, fbb[f].y));
-                sf.x += u.x; sf.y += u.y;
-            }
-            for (int y = G.Nf; y < G.Nf + G.My; ++y) {
-                const double2 u = zmulc(make_double2(fa[y].x, fa[y].y), make_double2(fbb[y].x, fbb[y].y));
-                sy.x += u.x; sy.y += u.y;
-            }
-            for (int m = G.Nf + G.My; m < nfac; ++m) {
-                const double2 u = zmulc(make_double2(fa[m].x, fa[m].y), make_double2(fbb[m].x, fbb[m].y));
-                sz.x += u.x; sz.y += u.y;
-            }
-            Am[t] = zmul(zmulc(cS[a], cS[b]), zmul(sf, zmul(sy, sz)));
+            const float2* fb2 = fac + (size_t)b * nfac;
+            float2 sf = make_float2(0.f, 0.f), sy = sf, sz = sf;
+            for (int f = 0; f < Nf; ++f) { const float2 u = cmulc(fa[f], fb2[f]); sf.x += u.x; sf.y += u.y; }
+            for (int y = Nf; y < Nf + G.My; ++y) { const float2 u = cmulc(fa[y], fb2[y]); sy.x += u.x; sy.y += u.y; }
+            for (int m = Nf + G.My; m < nfac; ++m) { const float2 u = cmulc(fa[m], fb2[m]); sz.x += u.x; sz.y += u.y; }
+            Am[t] = cmul(cmulc(cS[a], cS[b]), cmul(sf, cmul(sy, sz)));
+        }
+        __syncwarp();
+        for (int s = lane; s < S; s += 32) {
+            float2 acc = make_float2(0.f, 0.f);
+            for (int f = 0; f < Nf; ++f) { acc.x += gpart[s * Nf + f].x; acc.y += gpart[s * Nf + f].y; }
+            gS[s] = cmulc(cS[s], acc);
         }
         __syncwarp();
         // 4. rhs_a = d_a (g_a - sum_b G_ab cm_b)
         for (int a = lane; a < S; a += 32) {
-            double2 acc = gS[a];
+            float2 acc = gS[a];
             for (int b = 0; b < S; ++b) {
-                const double2 gab = (b <= a) ? Am[tri(a, b)] : make_double2(Am[tri(b, a)].x, -Am[tri(b, a)].y);
-                const double2 u = zmul(gab, cmS[b]);
+                const float2 gab = (b <= a) ? Am[tri(a, b)] : make_float2(Am[tri(b, a)].x, -Am[tri(b, a)].y);
+                const float2 u = cmul(gab, cmS[b]);
                 acc.x -= u.x; acc.y -= u.y;
             }
-            gS[a] = make_double2(dS[a] * acc.x, dS[a] * acc.y);
+            gS[a] = make_float2(dS[a].x * acc.x, dS[a].x * acc.y);
         }
         __syncwarp();
-        // 5. A = eta_bar I + D G D (packed lower), Cholesky in place
+        // 5. A = eta_bar I + D G D, keep the original diagonal; Cholesky in place
         for (int t = lane; t < npair; t += 32) {
-            int a = (int)((sqrtf(8.f * t + 1.f) - 1.f) * 0.5f);
-            while ((a + 1) * (a + 2) / 2 <= t) ++a;
-            while (a * (a + 1) / 2 > t) --a;
-            const int b = t - a * (a + 1) / 2;
-            const double dd = dS[a] * dS[b];
-            double2 v = Am[t];
-            Am[t] = make_double2(dd * v.x + (a == b ? eb : 0.0), dd * v.y);
+            int a, b;
+            tri_ab(t, a, b);
+            const float dd = dS[a].x * dS[b].x;
+            const float2 v = Am[t];
+            Am[t] = make_float2(dd * v.x + (a == b ? ebf : 0.f), dd * v.y);
+            if (a == b) dS[a].y = dd * v.x + ebf;
         }
         __syncwarp();
         double logdet = 0.0;
         for (int k = 0; k < S; ++k) {
-            const double dk = sqrt(fmax(Am[tri(k, k)].x, 1e-300));
-            logdet += 2.0 * log(dk);
+            const float piv = fmaxf(Am[tri(k, k)].x, 1e-30f);
+            const float dk = sqrtf(piv);
+            logdet += log((double)piv);
+            const double rk = (double)dS[k].y / (double)piv;
+            ratio2 += rk * rk;
             __syncwarp();
             for (int i = k + 1 + lane; i < S; i += 32) {
-                const double2 v = Am[tri(i, k)];
-                Am[tri(i, k)] = make_double2(v.x / dk, v.y / dk);
+                const float2 v = Am[tri(i, k)];
+                Am[tri(i, k)] = make_float2(v.x / dk, v.y / dk);
             }
-            if (lane == 0) Am[tri(k, k)] = make_double2(dk, 0.0);
+            if (lane == 0) Am[tri(k, k)] = make_float2(dk, 0.f);
             __syncwarp();
             const int n = S - k - 1;
             for (int t = lane; t < n * (n + 1) / 2; t += 32) {
-                int a = (int)((sqrtf(8.f * t + 1.f) - 1.f) * 0.5f);
-                while ((a + 1) * (a + 2) / 2 <= t) ++a;
-                while (a * (a + 1) / 2 > t) --a;
-                const int i = k + 1 + a, c = k + 1 + (t - a * (a + 1) / 2);
-                const double2 u = zmul(Am[tri(i, k)], make_double2(Am[tri(c, k)].x, -Am[tri(c, k)].y));
-                Am[tri(i, c)].x -= u.x; Am[tri(i, c)].y -= u.y;
+                int a, c;
+                tri_ab(t, a, c);
+                const int i = k + 1 + a, cc = k + 1 + c;
+                const float2 u = cmul(Am[tri(i, k)], make_float2(Am[tri(cc, k)].x, -Am[tri(cc, k)].y));
+                Am[tri(i, cc)].x -= u.x; Am[tri(i, cc)].y -= u.y;
             }
             __syncwarp();
         }
         // 6. solve L L^H y = rhs
         for (int i = 0; i < S; ++i) {
-            double2 acc = make_double2(0, 0);
-            for (int b = lane; b < i; b += 32) {
-                const double2 u = zmul(Am[tri(i, b)], gS[b]);
-                acc.x += u.x; acc.y += u.y;
-            }
-            acc.x = warp_sum_d(acc.x); acc.y = warp_sum_d(acc.y);
-            if (lane == 0) {
-                const double dd = Am[tri(i, i)].x;
-                gS[i] = make_double2((gS[i].x - acc.x) / dd, (gS[i].y - acc.y) / dd);
-            }
+            float2 acc = make_float2(0.f, 0.f);
+            for (int b = lane; b < i; b += 32) { const float2 u = cmul(Am[tri(i, b)], gS[b]); acc.x += u.x; acc.y += u.y; }
+            acc.x = warp_sum_f(acc.x); acc.y = warp_sum_f(acc.y);
+            if (lane == 0) { const float dd = Am[tri(i, i)].x; gS[i] = make_float2((gS[i].x - acc.x) / dd, (gS[i].y - acc.y) / dd); }
             __syncwarp();
         }
         for (int i = S - 1; i >= 0; --i) {
-            double2 acc = make_double2(0, 0);
-            for (int b = i + 1 + lane; b < S; b += 32) {
-                const double2 u = zmulc(Am[tri(b, i)], gS[b]);
-                acc.x += u.x; acc.y += u.y;
-            }
-            acc.x = warp_sum_d(acc.x); acc.y = warp_sum_d(acc.y);
-            if (lane == 0) {
-                const double dd = Am[tri(i, i)].x;
-                gS[i] = make_double2((gS[i].x - acc.x) / dd, (gS[i].y - acc.y) / dd);
-            }
+            float2 acc = make_float2(0.f, 0.f);
+            for (int b = i + 1 + lane; b < S; b += 32) { const float2 u = cmulc(Am[tri(b, i)], gS[b]); acc.x += u.x; acc.y += u.y; }
+            acc.x = warp_sum_f(acc.x); acc.y = warp_sum_f(acc.y);
+            if (lane == 0) { const float dd = Am[tri(i, i)].x; gS[i] = make_float2((gS[i].x - acc.x) / dd, (gS[i].y - acc.y) / dd); }
             __syncwarp();
         }
-        // 7. coefficients w = cm + d y (FP32 copy in c32's slot after use: keep c32, write w into cmS); |y|^2
+        // 7. w = cm + d y; |y|^2
         double yy = 0.0;
         for (int a = lane; a < S; a += 32) {
-            const double2 y = gS[a];
-            yy += y.x * y.x + y.y * y.y;
-            cmS[a] = make_double2(cmS[a].x + dS[a] * y.x, cmS[a].y + dS[a] * y.y);
+            const float2 y = gS[a];
+            yy += (double)y.x * y.x + (double)y.y * y.y;
+            cmS[a] = make_float2(cmS[a].x + dS[a].x * y.x, cmS[a].y + dS[a].x * y.y);
         }
         yy = warp_sum_d(yy);
         __syncwarp();
-        // 8. residual r = z - sum_s w_s psi_s, element-wise (lanes over elements)
-        double rr = 0.0;                   // FP32 per element, FP64 across elements and lanes
+        // 8. residual z - sum_s w_s psi_s, element-wise
+        double rr = 0.0;
         for (int k = lane; k < Nz; k += 32) {
             const int f = k / Nm, ym = k - f * Nm, y = ym / G.Mz, m = ym - y * G.Mz;
             float2 acc = zs[k];
             for (int s = 0; s < S; ++s) {
                 const float2* fs = fac + (size_t)s * nfac;
-                const float2 ps = cmul(cmul(cmul(c32[s], fs[f]), fs[G.Nf + y]), fs[G.Nf + G.My + m]);
-                const float2 u = cmul(make_float2((float)cmS[s].x, (float)cmS[s].y), ps);
+                const float2 u = cmul(cmul(cmS[s], cS[s]), cmul(fs[f], cmul(fs[Nf + y], fs[Nf + G.My + m])));
                 acc.x -= u.x; acc.y -= u.y;
             }
             rr += (double)(acc.x * acc.x + acc.y * acc.y);
@@ -418,7 +361,197 @@ __global__ void k_iota(DevGeom G, DevParams Pm, DevState D, int S, const float* 
         rr = warp_sum_d(rr);
         total += -(rr / eb + yy) - (logdet - S * log(eb)) - Nz * log(M_PI * eb);
     }
-    if (act && lane == 0) D.lw_x[p] = total;
+    if (act && lane == 0) {
+        D.lw_x[p] = total;
+        if (sqrt(ratio2) > IOTA_RATIO_MAX) {
+            const int slot = atomicAdd(&D.flags[0], 1);
+            D.flags[1 + slot] = p;
+        }
+    }
+}
+
+// ---------------------------------------------------------------- iota, float-float Gram and Cholesky
+// For the particles the FP32 path flags (or for every particle when S is large):
+// the Gram is accumulated from exact two-products of the FP32 factors and the
+// Cholesky of eta_bar I + D G D runs in float-float arithmetic, so that the
+// pivots (and log det) keep ~44 bits when columns nearly coincide.  The
+// solves and the residual stay FP32 (they enter the variational form only at
+// second order).
+// per-warp shared memory (float units): A packed lower [S(S+1)/2] cff (4 floats),
+// factors [S][nfac] float2, c [S] float2, cm [S] float2, g [S] float2, d [S] float2
+__host__ __device__ inline size_t iota_ff_warp_floats(int S, int nfac) {
+    return (size_t)S * (S + 1) / 2 * 4 + (size_t)S * nfac * 2 + (size_t)S * 2 * 4;
+}
+
+__global__ void k_iota_ff(DevGeom G, DevParams Pm, DevState D, int S, const float* z, int all) {
+    extern __shared__ float smf[];
+    const int lane = threadIdx.x & 31, wib = threadIdx.x >> 5;
+    const int wpb = blockDim.x >> 5;
+    const int P = Pm.P, J = G.J, Nz = G.Nz, Nm = G.My * G.Mz, Nf = G.Nf;
+    const int nfac = Nf + G.My + G.Mz;
+    float* base = smf + wib * iota_ff_warp_floats(S, nfac);
+    cff* Am = reinterpret_cast<cff*>(base);
+    float2* fac = reinterpret_cast<float2*>(base + (size_t)S * (S + 1) / 2 * 4);
+    float2* cS = fac + (size_t)S * nfac;
+    float2* cmS = cS + S;
+    float2* gS = cmS + S;
+    float2* dS = gS + S;
+    const int count = all ? P : D.flags[0];
+    const float* phi = D.phi[D.cur];
+    for (int w = blockIdx.x * wpb + wib; w < count; w += gridDim.x * wpb) {
+        const int pp = all ? w : D.flags[1 + w];
+        double total = 0.0;
+        for (int j = 0; j < J; ++j) {
+            const double eb = D.eta_bar[j];
+            const float ebf = (float)eb;
+            for (int s = lane; s < S; s += 32) {
+                const float* ph = phi + (size_t)s * 6 * P;
+                float2* fs = fac + (size_t)s * nfac;
+                cS[s] = factors_from_geo(G, D.geo[((size_t)s * J + j) * P + pp], fs, fs + Nf, fs + Nf + G.My, 1);
+                const float pi = (float)(D.zeta[s * J + j] * D.W[s]);
+                const float gm = ph[3 * P + pp], mr = ph[4 * P + pp], mi = ph[5 * P + pp];
+                dS[s] = make_float2(sqrtf(fmaxf(pi * (gm + (mr * mr + mi * mi) * (1.0f - pi)), 0.0f)), 0.f);
+                cmS[s] = make_float2(pi * mr, pi * mi);
+            }
+            __syncwarp();
+            // g_s = psi_s^H z (FP32, lanes over s)
+            for (int s = lane; s < S; s += 32) {
+                const float2* fs = fac + (size_t)s * nfac;
+                float2 acc = make_float2(0.f, 0.f);
+                for (int f = 0; f < Nf; ++f) {
+                    float2 accy = make_float2(0.f, 0.f);
+                    for (int y = 0; y < G.My; ++y) {
+                        float2 accm = make_float2(0.f, 0.f);
+                        for (int m = 0; m < G.Mz; ++m) {
+                            const int k = f * Nm + y * G.Mz + m;
+                            const float2 zk = make_float2(z[2 * (j * Nz + k)], z[2 * (j * Nz + k) + 1]);
+                            const float2 u = cmulc(fs[Nf + G.My + m], zk);
+                            accm.x += u.x; accm.y += u.y;
+                        }
+                        const float2 u = cmulc(fs[Nf + y], accm);
+                        accy.x += u.x; accy.y += u.y;
+                    }
+                    const float2 u = cmulc(fs[f], accy);
+                    acc.x += u.x; acc.y += u.y;
+                }
+                gS[s] = cmulc(cS[s], acc);
+            }
+            // Gram (float-float) -> A = eta_bar I + D G D
+            const int npair = S * (S + 1) / 2;
+            for (int t = lane; t < npair; t += 32) {
+                int a, b;
+                tri_ab(t, a, b);
+                const float2* fa = fac + (size_t)a * nfac;
+                const float2* fb2 = fac + (size_t)b * nfac;
+                cff sf = cff_prodc(fa[0], fb2[0]);
+                for (int f = 1; f < Nf; ++f) sf = cff_add(sf, cff_prodc(fa[f], fb2[f]));
+                cff sy = cff_prodc(fa[Nf], fb2[Nf]);
+                for (int y = Nf + 1; y < Nf + G.My; ++y) sy = cff_add(sy, cff_prodc(fa[y], fb2[y]));
+                cff sz = cff_prodc(fa[Nf + G.My], fb2[Nf + G.My]);
+                for (int m = Nf + G.My + 1; m < nfac; ++m) sz = cff_add(sz, cff_prodc(fa[m], fb2[m]));
+                const cff cc = cff_prodc(cS[a], cS[b]);
+                cff gab = cff_mul(cc, cff_mul(sf, cff_mul(sy, sz)));
+                const ff dd = ff_prod(dS[a].x, dS[b].x);
+                gab.re = ff_mul(gab.re, dd);
+                gab.im = ff_mul(gab.im, dd);
+                if (a == b) { gab.re = ff_add(gab.re, ff{ebf, (float)(eb - (double)ebf)}); gab.im = ff{0.f, 0.f}; }
+                Am[t] = gab;
+            }
+            __syncwarp();
+            // rhs_a = d_a (g_a - sum_b G_ab cm_b) with G recovered from A (FP32 is enough here)
+            for (int a = lane; a < S; a += 32) {
+                float2 acc = gS[a];
+                for (int b = 0; b < S; ++b) {
+                    if (dS[a].x == 0.f || dS[b].x == 0.f) continue;
+                    const cff e = (b <= a) ? Am[tri(a, b)] : Am[tri(b, a)];
+                    float re = e.re.hi + e.re.lo, im = (b <= a) ? (e.im.hi + e.im.lo) : -(e.im.hi + e.im.lo);
+                    if (a == b) re -= ebf;
+                    const float inv = 1.0f / (dS[a].x * dS[b].x);
+                    const float2 u = cmul(make_float2(re * inv, im * inv), cmS[b]);
+                    acc.x -= u.x; acc.y -= u.y;
+                }
+                gS[a] = make_float2(dS[a].x * acc.x, dS[a].x * acc.y);
+            }
+            __syncwarp();
+            // float-float Cholesky (right-looking), log det from the pivots
+            double logdet = 0.0;
+            for (int k = 0; k < S; ++k) {
+                ff piv = Am[tri(k, k)].re;
+                if (!(piv.hi > 0.f)) piv = ff{1e-30f, 0.f};
+                logdet += log((double)piv.hi) + (double)piv.lo / (double)piv.hi;
+                // L_kk = sqrt(piv) in float-float (one Newton step)
+                const float r0 = sqrtf(piv.hi);
+                const ff r0sq = ff_prod(r0, r0);
+                const ff resid = ff_add(piv, ff_neg(r0sq));
+                ff lk;
+                fast_two_sum(r0, resid.hi / (2.0f * r0), lk.hi, lk.lo);
+                __syncwarp();
+                for (int i = k + 1 + lane; i < S; i += 32) {
+                    cff v = Am[tri(i, k)];
+                    v.re = ff_div(v.re, lk);
+                    v.im = ff_div(v.im, lk);
+                    Am[tri(i, k)] = v;
+                }
+                __syncwarp();
+                if (lane == 0) Am[tri(k, k)] = cff{lk, ff{0.f, 0.f}};
+                const int n = S - k - 1;
+                for (int t = lane; t < n * (n + 1) / 2; t += 32) {
+                    int a, c;
+                    tri_ab(t, a, c);
+                    const int i = k + 1 + a, cc = k + 1 + c;
+                    const cff u = cff_mulc(Am[tri(cc, k)], Am[tri(i, k)]);   // L_ik conj(L_ck)
+                    Am[tri(i, cc)] = cff_sub(Am[tri(i, cc)], u);
+                }
+                __syncwarp();
+            }
+            // solves with the FP32 parts of L
+            for (int i = 0; i < S; ++i) {
+                float2 acc = make_float2(0.f, 0.f);
+                for (int b = lane; b < i; b += 32) {
+                    const cff l = Am[tri(i, b)];
+                    const float2 u = cmul(make_float2(l.re.hi + l.re.lo, l.im.hi + l.im.lo), gS[b]);
+                    acc.x += u.x; acc.y += u.y;
+                }
+                acc.x = warp_sum_f(acc.x); acc.y = warp_sum_f(acc.y);
+                if (lane == 0) { const float dd = Am[tri(i, i)].re.hi; gS[i] = make_float2((gS[i].x - acc.x) / dd, (gS[i].y - acc.y) / dd); }
+                __syncwarp();
+            }
+            for (int i = S - 1; i >= 0; --i) {
+                float2 acc = make_float2(0.f, 0.f);
+                for (int b = i + 1 + lane; b < S; b += 32) {
+                    const cff l = Am[tri(b, i)];
+                    const float2 u = cmulc(make_float2(l.re.hi + l.re.lo, l.im.hi + l.im.lo), gS[b]);
+                    acc.x += u.x; acc.y += u.y;
+                }
+                acc.x = warp_sum_f(acc.x); acc.y = warp_sum_f(acc.y);
+                if (lane == 0) { const float dd = Am[tri(i, i)].re.hi; gS[i] = make_float2((gS[i].x - acc.x) / dd, (gS[i].y - acc.y) / dd); }
+                __syncwarp();
+            }
+            double yy = 0.0;
+            for (int a = lane; a < S; a += 32) {
+                const float2 y = gS[a];
+                yy += (double)y.x * y.x + (double)y.y * y.y;
+                cmS[a] = make_float2(cmS[a].x + dS[a].x * y.x, cmS[a].y + dS[a].x * y.y);
+            }
+            yy = warp_sum_d(yy);
+            __syncwarp();
+            double rr = 0.0;
+            for (int k = lane; k < Nz; k += 32) {
+                const int f = k / Nm, ym = k - f * Nm, y = ym / G.Mz, m = ym - y * G.Mz;
+                float2 acc = make_float2(z[2 * (j * Nz + k)], z[2 * (j * Nz + k) + 1]);
+                for (int s = 0; s < S; ++s) {
+                    const float2* fs = fac + (size_t)s * nfac;
+                    const float2 u = cmul(cmul(cmS[s], cS[s]), cmul(fs[f], cmul(fs[Nf + y], fs[Nf + G.My + m])));
+                    acc.x -= u.x; acc.y -= u.y;
+                }
+                rr += (double)(acc.x * acc.x + acc.y * acc.y);
+            }
+            rr = warp_sum_d(rr);
+            total += -(rr / eb + yy) - (logdet - S * log(eb)) - Nz * log(M_PI * eb);
+            __syncwarp();
+        }
+        if (lane == 0) D.lw_x[pp] = total;
+    }
 }
 
 // ---------------------------------------------------------------- nu (thread per (j, p), FP64)
@@ -474,15 +607,32 @@ size_t kappa_smem_bytes(const DevGeom& G, int S) {
     return ((size_t)G.Nz * SC + (size_t)SC * SC + SC + (size_t)nfac * 128) * sizeof(float2);
 }
 
+// S below which the FP32 path runs first and only flagged particles are redone
+constexpr int IOTA_FF_ALL_S = 24;
+
 void launch_iota(const DevGeom& G, const DevParams& Pm, const DevState& D, int S, const float* z, cudaStream_t st) {
+    if (S >= IOTA_FF_ALL_S) return;   // k_iota_ff handles every particle (launch_iota_repair)
     const int nfac = G.Nf + G.My + G.Mz;
-    const size_t per_warp = iota_warp_bytes(S, nfac);
-    const size_t zb = (((size_t)G.Nz * 8 + 15) / 16) * 16;
+    const size_t per_warp = iota32_warp_f2(S, nfac, G.Nf) * sizeof(float2);
     int wpb = 8;
-    while (wpb > 1 && zb + wpb * per_warp > 96 * 1024) wpb /= 2;
-    const size_t smem = zb + wpb * per_warp;
+    while (wpb > 1 && (size_t)G.Nz * sizeof(float2) + wpb * per_warp > 64 * 1024) wpb /= 2;
+    const size_t smem = (size_t)G.Nz * sizeof(float2) + wpb * per_warp;
+    cudaMemsetAsync(D.flags, 0, sizeof(int), st);
     cudaFuncSetAttribute(k_iota, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
     k_iota<<<(Pm.P + wpb - 1) / wpb, 32 * wpb, smem, st>>>(G, Pm, D, S, z);
+}
+
+void launch_iota_repair(const DevGeom& G, const DevParams& Pm, const DevState& D, int S, const float* z, cudaStream_t st) {
+    const int nfac = G.Nf + G.My + G.Mz;
+    const size_t per_warp = iota_ff_warp_floats(S, nfac) * sizeof(float);
+    int wpb = 4;
+    while (wpb > 1 && wpb * per_warp > 160 * 1024) wpb /= 2;
+    const size_t smem = wpb * per_warp;
+    const int all = S >= IOTA_FF_ALL_S ? 1 : 0;
+    if (all) cudaMemsetAsync(D.flags, 0, sizeof(int), st);
+    cudaFuncSetAttribute(k_iota_ff, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    const int blocks = all ? (Pm.P + wpb - 1) / wpb : 4 * 152;
+    k_iota_ff<<<blocks, 32 * wpb, smem, st>>>(G, Pm, D, S, z, all);
 }
 
 void launch_nu(const DevGeom& G, const DevParams& Pm, const DevState& D, int S, cudaStream_t st) {

@@ -194,6 +194,7 @@ __global__ void k_estimate(DevGeom G, DevParams Pm, DevState D, int S, int n) {
     double* est = D.est;
     est[E.n()] = n;
     est[E.S()] = S;
+    est[E.repaired()] = D.flags[0];
     const double* r0 = D.bel + bel_rec(SM, J, 0);
     for (int k = 0; k < 6; ++k) est[E.x_hat() + k] = r0[4 + k];
     est[E.ess()] = 1.0 / r0[3];

@@ -35,13 +35,16 @@ __global__ void k_table(DevGeom G, DevParams Pm, DevState D, int S, int nsplit, 
     const int P = Pm.P, J = G.J, Nf = G.Nf, Nm = G.My * G.Mz, Nz = G.Nz;
     const int per = (P + nsplit - 1) / nsplit;
     const int p0 = split * per, p1 = min(P, p0 + per);
-    float2* Bf = sm;                          // [chunk][3][Nf]
-    float2* Ayz = sm + (size_t)chunk * 3 * Nf;  // [chunk][Nm]
+    float2* Bf = sm;                                          // [chunk][3][Nf]
+    float2* Ayz = sm + (size_t)chunk * 3 * Nf;                // [chunk][Nm]
+    float2* Fyz = Ayz + (size_t)chunk * Nm;                   // [chunk][My + Mz] scratch
+    const int nyz = G.My + G.Mz;
     const double W = D.W[s];
     const double zeta = D.zeta[s * J + j];
-    const double pi = zeta * W;
-    const float* x = D.x[D.cur];
+    const float pi = (float)(zeta * W);
+    const float pd = (float)(1.0 - W);
     const float* ph = D.phi[D.cur] + (size_t)s * 6 * P;
+    const float4* geo = D.geo + ((size_t)s * J + j) * P;
     double acc64[EPT][3][2];
     #pragma unroll
     for (int e = 0; e < EPT; ++e)
@@ -52,41 +55,26 @@ __global__ void k_table(DevGeom G, DevParams Pm, DevState D, int S, int nsplit, 
         __syncthreads();
         for (int t = threadIdx.x; t < cn; t += blockDim.x) {
             const int p = c0 + t;
-            const PathGeo pg = path_geo(G, j, x[p], x[P + p], x[2 * P + p], ph[p], ph[P + p], ph[2 * P + p], s == 0);
-            const double A = G.lam / (4.0 * M_PI * pg.d);
-            double sc, cc;
-            sincospi(-2.0 * frac_c(pg.d / G.lam), &sc, &cc);
-            const double gm = (double)ph[3 * P + p];
-            const double mr = (double)ph[4 * P + p], mi = (double)ph[5 * P + p];
-            const double m2 = mr * mr + mi * mi;
-            const double wb = D.w_x[p];
-            const double ca = wb * sqrt(fmax(gm + m2 * (1.0 - pi), 0.0));
-            const double cb = wb * sqrt(fmax(gm + m2 * (1.0 - W), 0.0));
-            // complex scalars times A e^{-i 2 pi d/lambda}
-            const double2 car = make_double2(A * cc, A * sc);
-            const double2 c1 = make_double2(ca * car.x, ca * car.y);
-            const double2 c2 = make_double2(cb * car.x, cb * car.y);
-            const double2 c3 = zmul(make_double2(wb * mr, wb * mi), car);
-            const double tau = pg.d / G.c;
+            float2* b0 = Bf + (size_t)t * 3 * Nf;
+            float2* fy = Fyz + (size_t)t * nyz;
+            const float2 c = factors_from_geo(G, geo[p], b0, fy, fy + G.My, 1);
+            const float gm = ph[3 * P + p], mr = ph[4 * P + p], mi = ph[5 * P + p];
+            const float m2 = mr * mr + mi * mi;
+            const float wb = (float)D.w_x[p];
+            const float ca = wb * sqrtf(fmaxf(gm + m2 * (1.0f - pi), 0.0f));
+            const float cb = wb * sqrtf(fmaxf(gm + m2 * pd, 0.0f));
+            const float2 c1 = make_float2(ca * c.x, ca * c.y);
+            const float2 c2 = make_float2(cb * c.x, cb * c.y);
+            const float2 c3 = cmul(make_float2(wb * mr, wb * mi), c);
             for (int f = 0; f < Nf; ++f) {
-                float sb, cbf;
-                sincospif((float)(-2.0 * frac_c(G.f[f] * tau)), &sb, &cbf);
-                const double2 bb = make_double2(cbf, sb);
-                const double2 v1 = zmul(c1, bb), v2 = zmul(c2, bb), v3 = zmul(c3, bb);
-                Bf[((size_t)t * 3 + 0) * Nf + f] = make_float2((float)v1.x, (float)v1.y);
-                Bf[((size_t)t * 3 + 1) * Nf + f] = make_float2((float)v2.x, (float)v2.y);
-                Bf[((size_t)t * 3 + 2) * Nf + f] = make_float2((float)v3.x, (float)v3.y);
+                const float2 bb = b0[f];
+                b0[Nf + f] = cmul(c2, bb);
+                b0[2 * Nf + f] = cmul(c3, bb);
+                b0[f] = cmul(c1, bb);
             }
-            const float uy = (float)pg.uy, uz = (float)pg.uz;
-            for (int y = 0; y < G.My; ++y) {
-                float sy, cy;
-                sincospif(2.0f * (float)(G.py[y] / G.lam) * uy, &sy, &cy);
-                for (int m = 0; m < G.Mz; ++m) {
-                    float sz, cz;
-                    sincospif(2.0f * (float)(G.pz[m] / G.lam) * uz, &sz, &cz);
-                    Ayz[(size_t)t * Nm + y * G.Mz + m] = cmul(make_float2(cy, sy), make_float2(cz, sz));
-                }
-            }
+            for (int y = 0; y < G.My; ++y)
+                for (int m = 0; m < G.Mz; ++m)
+                    Ayz[(size_t)t * Nm + y * G.Mz + m] = cmul(fy[y], fy[G.My + m]);
         }
         __syncthreads();
         float acc[EPT][3][2];
@@ -510,7 +498,7 @@ void launch_table(const DevGeom& G, const DevParams& Pm, const DevState& D, int 
     const int Nz = G.Nz;
     const int bs = Nz <= 256 ? ((Nz + 31) / 32) * 32 : 256;
     const int ept = (Nz + bs - 1) / bs;
-    const int per_particle = (3 * G.Nf + G.My * G.Mz) * (int)sizeof(float2);
+    const int per_particle = (3 * G.Nf + G.My * G.Mz + G.My + G.Mz) * (int)sizeof(float2);
     int chunk = 128;
     while (chunk > 16 && chunk * per_particle > 96 * 1024) chunk /= 2;
     const size_t smem = (size_t)chunk * per_particle;
