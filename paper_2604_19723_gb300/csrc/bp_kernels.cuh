@@ -72,7 +72,6 @@ void launch_table(const DevGeom& G, const DevParams& Pm, const DevState& D, int 
 void launch_stage(const DevGeom& G, const DevParams& Pm, const DevState& D, int S, int SC, const float* z,
                   double* gram, double* nu_b, double* V64, cudaStream_t st);
 void launch_kappa(const DevGeom& G, const DevParams& Pm, const DevState& D, int S, int SCA, cudaStream_t st);
-size_t kappa_smem_bytes(const DevGeom& G, int S);
 void launch_iota(const DevGeom& G, const DevParams& Pm, const DevState& D, int S, const float* z, cudaStream_t st);
 void launch_nu(const DevGeom& G, const DevParams& Pm, const DevState& D, int S, cudaStream_t st);
 int launch_normalize(const DevGeom& G, const DevParams& Pm, const DevState& D, int S, int n, cudaStream_t st);

@@ -26,19 +26,25 @@
 namespace bp {
 
 // ---------------------------------------------------------------- kappa
-// block = (particle tile of KT threads, s); loop over j; V_{s,j} staged in shared memory.
+// block = (particle tile of KT threads, s); loop over j; V_{s,j} staged in shared
+// memory as rows of SC complex values (columns 0..SC-2 the whitened basis, column
+// SC-1 the null residual r0), read two columns per 128-bit broadcast load; R as
+// a packed upper triangle.
 template <int SC>
-__global__ void __launch_bounds__(128) k_kappa(DevGeom G, DevParams Pm, DevState D, int S, int SCA) {
-    constexpr int KT = 128;
+__host__ __device__ constexpr int kappa_rpack() { return (SC - 1) * SC / 2; }
+
+template <int SC>
+__global__ void __launch_bounds__(256, 1) k_kappa(DevGeom G, DevParams Pm, DevState D, int S, int SCA, int fch) {
+    constexpr int KT = 256;
     constexpr int NC = SC - 1;           // basis columns (zero beyond S-2)
-    extern __shared__ float2 sm[];
+    constexpr int NP = SC / 2;           // column pairs per row
+    extern __shared__ float4 sm4[];
     const int s = blockIdx.y;
     const int P = Pm.P, J = G.J, Nz = G.Nz, Nm = G.My * G.Mz;
-    const int nfac = G.Nf + G.My + G.Mz;
-    float2* Vs = sm;                                   // [Nz][SC] (last column r0)
-    float2* Rs = Vs + (size_t)Nz * SC;                 // [SC][SC]
-    float2* y0s = Rs + (size_t)SC * SC;                // [SC]
-    float2* fac = y0s + SC;                            // [nfac][KT]
+    float4* Vs = sm4;                                                  // [Nz][NP]
+    float2* Rs = reinterpret_cast<float2*>(Vs + (size_t)Nz * NP);      // packed upper NC x NC
+    float2* y0s = Rs + kappa_rpack<SC>();                              // [SC]
+    float2* fac = y0s + SC;                                            // [nfac][KT]
     const int tid = threadIdx.x;
     const int p = blockIdx.x * KT + tid;
     const bool act = p < P;
@@ -49,16 +55,24 @@ __global__ void __launch_bounds__(128) k_kappa(DevGeom G, DevParams Pm, DevState
     const double mr = ph[4 * P + pp], mi = ph[5 * P + pp];
     double delta_sum = 0.0;
     for (int j = 0; j < J; ++j) {
-        __syncthreads();
-        {   // stage V_{s,j} (first NC columns + r0), R, y0
-            const float2* gV = D.kV + ((size_t)s * J + j) * Nz * SCA;
-            for (int t = tid; t < Nz * SC; t += KT) {
-                const int k = t / SC, c = t - k * SC;
-                Vs[t] = (c < NC) ? gV[(size_t)k * SCA + c] : gV[(size_t)k * SCA + SCA - 1];
+        const float2* gV = D.kV + ((size_t)s * J + j) * Nz * SCA;
+        // rows of frequencies [f0, f0 + fch) -> Vs (called by all threads)
+        auto stage_rows = [&](int f0) {
+            float2* Vs2 = reinterpret_cast<float2*>(Vs);
+            const int nrow = min(fch, G.Nf - f0) * Nm;
+            for (int t = tid; t < nrow * SC; t += KT) {
+                const int k = f0 * Nm + t / SC, c = t % SC;
+                Vs2[t] = (c < NC) ? gV[(size_t)k * SCA + c] : gV[(size_t)k * SCA + SCA - 1];
             }
+        };
+        __syncthreads();
+        {
+            if (fch >= G.Nf) stage_rows(0);
             const float2* gR = D.kR + ((size_t)s * J + j) * SCA * SCA;
-            for (int t = tid; t < SC * SC; t += KT) {
-                const int r = t / SC, c = t - r * SC;
+            for (int t = tid; t < kappa_rpack<SC>(); t += KT) {
+                int r = 0, off = 0;
+                while (off + (NC - r) <= t) { off += NC - r; ++r; }
+                const int c = r + (t - off);
                 Rs[t] = gR[(size_t)r * SCA + c];
             }
             const float2* gy = D.ky0 + ((size_t)s * J + j) * SCA;
@@ -79,28 +93,33 @@ __global__ void __launch_bounds__(128) k_kappa(DevGeom G, DevParams Pm, DevState
         for (int c = 0; c < NC; ++c) h[c] = make_float2(0.f, 0.f);
         float2 pr = make_float2(0.f, 0.f);
         float nps = 0.f;
-        for (int f = 0; f < G.Nf; ++f) {
+        for (int f0 = 0; f0 < G.Nf; f0 += fch) {
+          if (fch < G.Nf) { __syncthreads(); stage_rows(f0); __syncthreads(); }
+          for (int f = f0; f < min(G.Nf, f0 + fch); ++f) {
             const float2 cb = cmul(Fc, fb[f * KT]);
             for (int y = 0; y < G.My; ++y) {
                 const float2 w = cmul(cb, fy[y * KT]);
                 for (int m = 0; m < G.Mz; ++m) {
                     const float2 ps = cmul(w, fz[m * KT]);
-                    const int k = f * Nm + y * G.Mz + m;
-                    const float2* row = Vs + (size_t)k * SC;
+                    const float4* row = Vs + (size_t)((f - f0) * Nm + y * G.Mz + m) * NP;
                     #pragma unroll
-                    for (int c = 0; c < NC; ++c) {
-                        const float2 v = row[c];
-                        h[c].x += ps.x * v.x + ps.y * v.y;
-                        h[c].y += ps.x * v.y - ps.y * v.x;
+                    for (int c2 = 0; c2 < NP; ++c2) {
+                        const float4 v = row[c2];
+                        h[2 * c2].x += ps.x * v.x + ps.y * v.y;
+                        h[2 * c2].y += ps.x * v.y - ps.y * v.x;
+                        if (2 * c2 + 1 < NC) {
+                            h[2 * c2 + 1].x += ps.x * v.z + ps.y * v.w;
+                            h[2 * c2 + 1].y += ps.x * v.w - ps.y * v.z;
+                        } else {
+                            pr.x += ps.x * v.z + ps.y * v.w;
+                            pr.y += ps.x * v.w - ps.y * v.z;
+                        }
                     }
-                    const float2 r0 = row[NC];
-                    pr.x += ps.x * r0.x + ps.y * r0.y;
-                    pr.y += ps.x * r0.y - ps.y * r0.x;
                     nps += ps.x * ps.x + ps.y * ps.y;
                 }
             }
+          }
         }
-        // scalar assembly (FP64)
         double hh = 0.0;
         #pragma unroll
         for (int c = 0; c < NC; ++c) hh += (double)h[c].x * h[c].x + (double)h[c].y * h[c].y;
@@ -116,46 +135,58 @@ __global__ void __launch_bounds__(128) k_kappa(DevGeom G, DevParams Pm, DevState
             tau = a;
         }
         const float2 tf = make_float2((float)tau.x, (float)tau.y);
-        // pass 2: r = r0 - tau (psi - V V^H psi / eta_bar), |r|^2
+        // pass 2: r = r0 - tau (psi - V V^H psi / eta_bar), |r|^2 and |psi_perp|^2
+        const float ieb = 1.0f / ebf;
         double rr = 0.0;
         float pn = 0.f;
-        for (int f = 0; f < G.Nf; ++f) {
+        for (int f0 = 0; f0 < G.Nf; f0 += fch) {
+          if (fch < G.Nf) { __syncthreads(); stage_rows(f0); __syncthreads(); }
+          for (int f = f0; f < min(G.Nf, f0 + fch); ++f) {
             const float2 cb = cmul(Fc, fb[f * KT]);
             for (int y = 0; y < G.My; ++y) {
                 const float2 w = cmul(cb, fy[y * KT]);
-                float rr_chunk = 0.f;          // FP32 over the Mz antennas, FP64 across chunks
+                float rr_chunk = 0.f;
                 for (int m = 0; m < G.Mz; ++m) {
                     const float2 ps = cmul(w, fz[m * KT]);
-                    const int k = f * Nm + y * G.Mz + m;
-                    const float2* row = Vs + (size_t)k * SC;
-                    float2 vv = make_float2(0.f, 0.f);       // V (V^H psi) = sum_c V_kc conj(h_c)
+                    const float4* row = Vs + (size_t)((f - f0) * Nm + y * G.Mz + m) * NP;
+                    float2 vv = make_float2(0.f, 0.f);
+                    float2 r0 = make_float2(0.f, 0.f);
                     #pragma unroll
-                    for (int c = 0; c < NC; ++c) {
-                        const float2 v = row[c];
-                        vv.x += v.x * h[c].x + v.y * h[c].y;
-                        vv.y += v.y * h[c].x - v.x * h[c].y;
+                    for (int c2 = 0; c2 < NP; ++c2) {
+                        const float4 v = row[c2];
+                        vv.x += v.x * h[2 * c2].x + v.y * h[2 * c2].y;
+                        vv.y += v.y * h[2 * c2].x - v.x * h[2 * c2].y;
+                        if (2 * c2 + 1 < NC) {
+                            vv.x += v.z * h[2 * c2 + 1].x + v.w * h[2 * c2 + 1].y;
+                            vv.y += v.w * h[2 * c2 + 1].x - v.z * h[2 * c2 + 1].y;
+                        } else {
+                            r0 = make_float2(v.z, v.w);
+                        }
                     }
-                    const float2 pp2 = make_float2(ps.x - vv.x / ebf, ps.y - vv.y / ebf);
+                    const float2 pp2 = make_float2(ps.x - vv.x * ieb, ps.y - vv.y * ieb);
                     pn += pp2.x * pp2.x + pp2.y * pp2.y;
-                    const float2 r0 = row[NC];
                     const float2 t = cmul(tf, pp2);
                     const float rx = r0.x - t.x, ry = r0.y - t.y;
                     rr_chunk += rx * rx + ry * ry;
                 }
                 rr += rr_chunk;
             }
+          }
         }
         // y = y0 - tau R^-1 V^H psi / eta_bar (back substitution in place: h <- R^-1 conj(h))
         double yy = 0.0, gg = 0.0;
         #pragma unroll
         for (int c = NC - 1; c >= 0; --c) {
+            const int off = c * NC - c * (c - 1) / 2;    // packed row c starts at R[c][c]
             float2 g = make_float2(h[c].x, -h[c].y);
             #pragma unroll
-            for (int c2 = c + 1; c2 < NC; ++c2) {
-                const float2 u = cmul(Rs[c * SC + c2], h[c2]);
-                g.x -= u.x; g.y -= u.y;
+            for (int e = 1; e < NC; ++e) {      // fixed trip count: unrolls fully, h stays in registers
+                if (c + e < NC) {
+                    const float2 u = cmul(Rs[off + e], h[c + e]);
+                    g.x -= u.x; g.y -= u.y;
+                }
             }
-            const float dr = Rs[c * SC + c].x;
+            const float dr = Rs[off].x;
             h[c] = make_float2(g.x / dr, g.y / dr);
             gg += (double)h[c].x * h[c].x + (double)h[c].y * h[c].y;
             const float2 tg = cmul(tf, h[c]);
@@ -588,10 +619,16 @@ __global__ void k_nu(DevGeom G, DevParams Pm, DevState D, int S) {
 template <int SC>
 static void launch_kappa_sc(const DevGeom& G, const DevParams& Pm, const DevState& D, int S, int SCA, cudaStream_t st) {
     const int nfac = G.Nf + G.My + G.Mz;
-    const size_t smem = ((size_t)G.Nz * SC + (size_t)SC * SC + SC + (size_t)nfac * 128) * sizeof(float2);
+    const int Nm = G.My * G.Mz;
+    const size_t fixed = ((size_t)kappa_rpack<SC>() + SC + (size_t)nfac * 256) * sizeof(float2);
+    const size_t per_f = (size_t)Nm * SC * sizeof(float2);
+    const size_t limit = 200 * 1024;
+    int fch = G.Nf;
+    while (fch > 1 && fixed + fch * per_f > limit) fch = (fch + 1) / 2;
+    const size_t smem = fixed + fch * per_f;
     cudaFuncSetAttribute(k_kappa<SC>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
-    dim3 grid((Pm.P + 127) / 128, S);
-    k_kappa<SC><<<grid, 128, smem, st>>>(G, Pm, D, S, SCA);
+    dim3 grid((Pm.P + 255) / 256, S);
+    k_kappa<SC><<<grid, 256, smem, st>>>(G, Pm, D, S, SCA, fch);
 }
 
 void launch_kappa(const DevGeom& G, const DevParams& Pm, const DevState& D, int S, int SCA, cudaStream_t st) {
@@ -601,11 +638,6 @@ void launch_kappa(const DevGeom& G, const DevParams& Pm, const DevState& D, int 
     else launch_kappa_sc<64>(G, Pm, D, S, SCA, st);
 }
 
-size_t kappa_smem_bytes(const DevGeom& G, int S) {
-    const int SC = S <= 8 ? 8 : S <= 16 ? 16 : S <= 32 ? 32 : 64;
-    const int nfac = G.Nf + G.My + G.Mz;
-    return ((size_t)G.Nz * SC + (size_t)SC * SC + SC + (size_t)nfac * 128) * sizeof(float2);
-}
 
 // S below which the FP32 path runs first and only flagged particles are redone
 constexpr int IOTA_FF_ALL_S = 24;
