@@ -62,6 +62,31 @@ __device__ inline float2 factors_from_geo(const DevGeom& G, float4 g, float2* b,
     return make_float2(A * c, A * s);
 }
 
+// As factors_from_geo, with the carrier phase folded into the frequency factor:
+// psi = A (b' kron a_y kron a_z), b'_f = e^{-i 2 pi d (1/lambda + f_f/c)}, A = lambda/(4 pi d).
+// The two fractional cycle counts are added before one sincospi, so |b'_f| = 1
+// to FP32 rounding.  Returns A.
+__device__ inline float factors_from_geo_folded(const DevGeom& G, float4 g, float2* b, float2* ay, float2* az, int stride) {
+    const float d = g.x + g.y;
+    const float ph0 = ff_frac_mul(g.x, g.y, G.inv_lam_hi, G.inv_lam_lo);
+    for (int f = 0; f < G.Nf; ++f) {
+        float sf, cf;
+        sincospif(-2.0f * (ph0 + ff_frac_mul(g.x, g.y, G.fc_hi[f], G.fc_lo[f])), &sf, &cf);
+        b[f * stride] = make_float2(cf, sf);
+    }
+    for (int y = 0; y < G.My; ++y) {
+        float sy, cy;
+        sincospif(2.0f * G.py_l[y] * g.z, &sy, &cy);
+        ay[y * stride] = make_float2(cy, sy);
+    }
+    for (int m = 0; m < G.Mz; ++m) {
+        float sz, cz;
+        sincospif(2.0f * G.pz_l[m] * g.w, &sz, &cz);
+        az[m * stride] = make_float2(cz, sz);
+    }
+    return G.amp_c / d;
+}
+
 void launch_geom(const DevGeom& G, const DevParams& Pm, const DevState& D, int S, cudaStream_t st);
 void launch_iota_repair(const DevGeom& G, const DevParams& Pm, const DevState& D, int S, const float* z, cudaStream_t st);
 

@@ -216,7 +216,7 @@ __global__ void __launch_bounds__(256, 1) k_kappa(DevGeom G, DevParams Pm, DevSt
 // in the span of the previous ones (1 - |rho|^2 small, e.g. a fresh birth PF
 // next to a real component): each pivot's ratio A_kk / L_kk^2 measures that
 // loss, and particles with sqrt(sum ratio^2) > IOTA_RATIO_MAX are queued for
-// k_iota_ff, which recomputes them with a float-float Gram and factorisation.
+// k_iota_blk, which recomputes them with a float-float Gram and factorisation.
 // The FP32 log det error per pivot is about 8 eps ratio (measured), so the
 // bound keeps unrepaired particles within ~5e-5 in log-likelihood.
 constexpr float IOTA_RATIO_MAX = 100.0f;
@@ -403,185 +403,311 @@ __global__ void k_iota(DevGeom G, DevParams Pm, DevState D, int S, const float* 
 
 // ---------------------------------------------------------------- iota, float-float Gram and Cholesky
 // For the particles the FP32 path flags (or for every particle when S is large):
-// the Gram is accumulated from exact two-products of the FP32 factors and the
-// Cholesky of eta_bar I + D G D runs in float-float arithmetic, so that the
-// pivots (and log det) keep ~44 bits when columns nearly coincide.  The
-// solves and the residual stay FP32 (they enter the variational form only at
-// second order).
-// per-warp shared memory (float units): A packed lower [S(S+1)/2] cff (4 floats),
-// factors [S][nfac] float2, c [S] float2, cm [S] float2, g [S] float2, d [S] float2
-__host__ __device__ inline size_t iota_ff_warp_floats(int S, int nfac) {
-    return (size_t)S * (S + 1) / 2 * 4 + (size_t)S * nfac * 2 + (size_t)S * 2 * 4;
+// the same log-likelihood with the pivots of eta_bar I + D G D kept to ~44 bits,
+// so that nearly coinciding columns lose nothing.  One block of IB_T threads per
+// particle; the lower triangle of A (S <= 64) lives in registers, distributed as
+// row pairs (rp, 63 - rp) x column groups c = 4q + cg, so that every thread holds
+// about S(S+1)/256 entries and every row's scaled column entry is formed by four
+// threads only.
+//  - Gram: G'_ab = (sum_f conj(b'_af) b'_bf)(sum_y ..)(sum_m ..) of the unit-modulus
+//    factors, each sum exact to ~2^-40 (products split on a fixed 2^-16 grid,
+//    remainders by FMA); A_ab = A_a d_a A_b d_b G'_ab + eta_bar delta_ab in float-float.
+//  - Right-looking Cholesky, one barrier per pivot: step k scales column k by
+//    1/pivot, subtracts the rank-one term from the trailing entries, and the owners
+//    of column k+1 publish it (and its pivot with the reciprocal) for step k+1.
+//  - Forward/back solves with the FP32 parts of L, residual in FP32 with FP64 sums
+//    (both enter the variational form only at second order).
+constexpr int IB_T = 128;
+constexpr int IB_SMAX = 64;
+
+__device__ inline cff fx_dotc(const float2* x, const float2* y, int n) {
+    // sum_k conj(x_k) y_k for |x_k|, |y_k| <= 1 + O(eps), n <= 127: fmaf(a, b, M) - M
+    // rounds a*b to a multiple of 2^-16 (M = 1.5 * 2^7), so the grid parts add
+    // exactly while |sum| < 256, and fmaf(a, b, -grid part) is the remainder.
+    const float M = 192.0f;
+    float rh = 0.f, rl = 0.f, ih = 0.f, il = 0.f;
+    for (int k = 0; k < n; ++k) {
+        const float2 a = x[k], b = y[k];
+        float t = __fsub_rn(fmaf(a.x, b.x, M), M);
+        rh = __fadd_rn(rh, t); rl = __fadd_rn(rl, fmaf(a.x, b.x, -t));
+        t = __fsub_rn(fmaf(a.y, b.y, M), M);
+        rh = __fadd_rn(rh, t); rl = __fadd_rn(rl, fmaf(a.y, b.y, -t));
+        t = __fsub_rn(fmaf(a.x, b.y, M), M);
+        ih = __fadd_rn(ih, t); il = __fadd_rn(il, fmaf(a.x, b.y, -t));
+        t = __fsub_rn(fmaf(-a.y, b.x, M), M);
+        ih = __fadd_rn(ih, t); il = __fadd_rn(il, fmaf(-a.y, b.x, -t));
+    }
+    cff r;
+    two_sum(rh, rl, r.re.hi, r.re.lo);
+    two_sum(ih, il, r.im.hi, r.im.lo);
+    return r;
 }
 
-__global__ void k_iota_ff(DevGeom G, DevParams Pm, DevState D, int S, const float* z, int all) {
-    extern __shared__ float smf[];
-    const int lane = threadIdx.x & 31, wib = threadIdx.x >> 5;
-    const int wpb = blockDim.x >> 5;
+// A -= x1 y1 + x2 y2 in float-float: exact high products, first-order cross terms,
+// both roundings of the high sum captured; A.lo is left unnormalised.
+__device__ inline void ff_sub_dot2(ff& A, ff x1, ff y1, ff x2, ff y2) {
+    const float p1 = __fmul_rn(x1.hi, y1.hi), e1 = fmaf(x1.hi, y1.hi, -p1);
+    const float p2 = __fmul_rn(x2.hi, y2.hi), e2 = fmaf(x2.hi, y2.hi, -p2);
+    float s, t1, t2;
+    two_sum(A.hi, -p1, s, t1);
+    two_sum(s, -p2, A.hi, t2);
+    const float cross = fmaf(x1.hi, y1.lo, fmaf(x1.lo, y1.hi, fmaf(x2.hi, y2.lo, __fmul_rn(x2.lo, y2.hi))));
+    A.lo = __fadd_rn(A.lo, __fsub_rn(__fadd_rn(t1, t2), __fadd_rn(__fadd_rn(e1, e2), cross)));
+}
+// A -= l conj(a)
+__device__ inline void cff_sub_mulc(cff& A, const cff& l, const cff& a) {
+    ff_sub_dot2(A.re, l.re, a.re, l.im, a.im);
+    ff_sub_dot2(A.im, l.im, a.re, ff_neg(l.re), a.im);
+}
+__device__ inline ff ff_norm(ff x) { ff r; two_sum(x.hi, x.lo, r.hi, r.lo); return r; }
+__device__ inline cff cff_norm(cff x) { return cff{ff_norm(x.re), ff_norm(x.im)}; }
+__device__ inline ff ff_recip(ff x) {
+    const float r = __frcp_rn(x.hi);
+    const float e = __fsub_rn(fmaf(-x.hi, r, 1.0f), __fmul_rn(x.lo, r));   // 1 - x r
+    ff o;
+    fast_two_sum(r, __fmul_rn(r, e), o.hi, o.lo);
+    return o;
+}
+
+// shared memory of k_iota_blk (bytes): colbuf [2][64] cff, pivbuf [2][2] ff, red [8]
+// double, then float2 z [Nz], factors [S][nfac], cm [S], g [S], L packed [S(S+1)/2]
+// (also the partial sums g [S][Nf] before the Gram), then float amplitude [S],
+// A d [S], d [S]
+__host__ __device__ inline size_t iota_blk_lsize(int S, int Nf) {
+    const size_t a = (size_t)S * (S + 1) / 2, b = (size_t)S * Nf;
+    return a > b ? a : b;
+}
+__host__ __device__ inline size_t iota_blk_smem(int S, int nfac, int Nf, int Nz) {
+    return 2 * IB_SMAX * 16 + 4 * 8 + 8 * 8 +
+           ((size_t)Nz + (size_t)S * nfac + 2 * (size_t)S + iota_blk_lsize(S, Nf)) * 8 + 3 * (size_t)S * 4;
+}
+
+__global__ void __launch_bounds__(IB_T, 3) k_iota_blk(DevGeom G, DevParams Pm, DevState D, int S, const float* z, int all) {
+    extern __shared__ float4 smb[];
+    cff* colbuf = reinterpret_cast<cff*>(smb);                    // [2][IB_SMAX]
+    ff* pivbuf = reinterpret_cast<ff*>(colbuf + 2 * IB_SMAX);     // [2][piv, 1/piv]
+    double* red = reinterpret_cast<double*>(pivbuf + 4);          // [8]
     const int P = Pm.P, J = G.J, Nz = G.Nz, Nm = G.My * G.Mz, Nf = G.Nf;
     const int nfac = Nf + G.My + G.Mz;
-    float* base = smf + wib * iota_ff_warp_floats(S, nfac);
-    cff* Am = reinterpret_cast<cff*>(base);
-    float2* fac = reinterpret_cast<float2*>(base + (size_t)S * (S + 1) / 2 * 4);
-    float2* cS = fac + (size_t)S * nfac;
-    float2* cmS = cS + S;
-    float2* gS = cmS + S;
-    float2* dS = gS + S;
-    const int count = all ? P : D.flags[0];
+    float2* zs = reinterpret_cast<float2*>(red + 8);              // [Nz]
+    float2* fac = zs + Nz;                                        // [S][nfac]: b', a_y, a_z
+    float2* cmS = fac + (size_t)S * nfac;                         // [S] pi mu, then A (pi mu + d y)
+    float2* gS = cmS + S;                                         // [S] g, rhs, solution
+    float2* Lsm = gS + S;                                         // FP32 G, then L (packed lower)
+    float2* gpart = Lsm;                                          // [S][Nf] (before the Gram)
+    float* amp = reinterpret_cast<float*>(Lsm + iota_blk_lsize(S, Nf));     // [S]
+    float* adS = amp + S;                                         // [S] A d
+    float* dS = adS + S;                                          // [S] d
+    const int tid = threadIdx.x, lane = tid & 31, wid = tid >> 5;
+    const int cg = tid & 3;
+    const int rp = (wid << 3) + (lane >> 2);
+    const int ra = rp, rb = IB_SMAX - 1 - rp;
     const float* phi = D.phi[D.cur];
-    for (int w = blockIdx.x * wpb + wib; w < count; w += gridDim.x * wpb) {
+    const int count = all ? P : D.flags[0];
+    for (int w = blockIdx.x; w < count; w += gridDim.x) {
         const int pp = all ? w : D.flags[1 + w];
         double total = 0.0;
         for (int j = 0; j < J; ++j) {
+            __syncthreads();
+            for (int k = tid; k < Nz; k += IB_T) zs[k] = make_float2(z[2 * (j * Nz + k)], z[2 * (j * Nz + k) + 1]);
             const double eb = D.eta_bar[j];
             const float ebf = (float)eb;
-            for (int s = lane; s < S; s += 32) {
+            const ff ebff = ff{ebf, (float)(eb - (double)ebf)};
+            for (int s = tid; s < S; s += IB_T) {
                 const float* ph = phi + (size_t)s * 6 * P;
                 float2* fs = fac + (size_t)s * nfac;
-                cS[s] = factors_from_geo(G, D.geo[((size_t)s * J + j) * P + pp], fs, fs + Nf, fs + Nf + G.My, 1);
+                const float A = factors_from_geo_folded(G, D.geo[((size_t)s * J + j) * P + pp], fs, fs + Nf, fs + Nf + G.My, 1);
                 const float pi = (float)(D.zeta[s * J + j] * D.W[s]);
                 const float gm = ph[3 * P + pp], mr = ph[4 * P + pp], mi = ph[5 * P + pp];
-                dS[s] = make_float2(sqrtf(fmaxf(pi * (gm + (mr * mr + mi * mi) * (1.0f - pi)), 0.0f)), 0.f);
+                const float d = sqrtf(fmaxf(pi * (gm + (mr * mr + mi * mi) * (1.0f - pi)), 0.0f));
+                amp[s] = A;
+                dS[s] = d;
+                adS[s] = A * d;
                 cmS[s] = make_float2(pi * mr, pi * mi);
             }
-            __syncwarp();
-            // g_s = psi_s^H z (FP32, lanes over s)
-            for (int s = lane; s < S; s += 32) {
+            __syncthreads();
+            // g_s = psi_s^H z: tasks (s, f) contract over the antennas
+            for (int t = tid; t < S * Nf; t += IB_T) {
+                const int s = t / Nf, f = t - s * Nf;
                 const float2* fs = fac + (size_t)s * nfac;
-                float2 acc = make_float2(0.f, 0.f);
-                for (int f = 0; f < Nf; ++f) {
-                    float2 accy = make_float2(0.f, 0.f);
-                    for (int y = 0; y < G.My; ++y) {
-                        float2 accm = make_float2(0.f, 0.f);
-                        for (int m = 0; m < G.Mz; ++m) {
-                            const int k = f * Nm + y * G.Mz + m;
-                            const float2 zk = make_float2(z[2 * (j * Nz + k)], z[2 * (j * Nz + k) + 1]);
-                            const float2 u = cmulc(fs[Nf + G.My + m], zk);
-                            accm.x += u.x; accm.y += u.y;
-                        }
-                        const float2 u = cmulc(fs[Nf + y], accm);
-                        accy.x += u.x; accy.y += u.y;
+                float2 accy = make_float2(0.f, 0.f);
+                for (int y = 0; y < G.My; ++y) {
+                    float2 accm = make_float2(0.f, 0.f);
+                    for (int m = 0; m < G.Mz; ++m) {
+                        const float2 u = cmulc(fs[Nf + G.My + m], zs[f * Nm + y * G.Mz + m]);
+                        accm.x += u.x; accm.y += u.y;
                     }
-                    const float2 u = cmulc(fs[f], accy);
-                    acc.x += u.x; acc.y += u.y;
+                    const float2 u = cmulc(fs[Nf + y], accm);
+                    accy.x += u.x; accy.y += u.y;
                 }
-                gS[s] = cmulc(cS[s], acc);
+                gpart[t] = cmulc(fs[f], accy);
             }
-            // Gram (float-float) -> A = eta_bar I + D G D
-            const int npair = S * (S + 1) / 2;
-            for (int t = lane; t < npair; t += 32) {
-                int a, b;
-                tri_ab(t, a, b);
+            __syncthreads();
+            for (int s = tid; s < S; s += IB_T) {
+                float2 acc = make_float2(0.f, 0.f);
+                for (int f = 0; f < Nf; ++f) { acc.x += gpart[s * Nf + f].x; acc.y += gpart[s * Nf + f].y; }
+                gS[s] = make_float2(amp[s] * acc.x, amp[s] * acc.y);
+            }
+            __syncthreads();
+            // Gram entries of this thread's slots (rows ra: q < 8, rb: q < 16)
+            cff Ar[8], Br[16];
+            auto gram = [&](int a, int b) -> cff {
                 const float2* fa = fac + (size_t)a * nfac;
-                const float2* fb2 = fac + (size_t)b * nfac;
-                cff sf = cff_prodc(fa[0], fb2[0]);
-                for (int f = 1; f < Nf; ++f) sf = cff_add(sf, cff_prodc(fa[f], fb2[f]));
-                cff sy = cff_prodc(fa[Nf], fb2[Nf]);
-                for (int y = Nf + 1; y < Nf + G.My; ++y) sy = cff_add(sy, cff_prodc(fa[y], fb2[y]));
-                cff sz = cff_prodc(fa[Nf + G.My], fb2[Nf + G.My]);
-                for (int m = Nf + G.My + 1; m < nfac; ++m) sz = cff_add(sz, cff_prodc(fa[m], fb2[m]));
-                const cff cc = cff_prodc(cS[a], cS[b]);
-                cff gab = cff_mul(cc, cff_mul(sf, cff_mul(sy, sz)));
-                const ff dd = ff_prod(dS[a].x, dS[b].x);
-                gab.re = ff_mul(gab.re, dd);
-                gab.im = ff_mul(gab.im, dd);
-                if (a == b) { gab.re = ff_add(gab.re, ff{ebf, (float)(eb - (double)ebf)}); gab.im = ff{0.f, 0.f}; }
-                Am[t] = gab;
+                const float2* fb = fac + (size_t)b * nfac;
+                const cff sf = fx_dotc(fa, fb, Nf);
+                const cff sy = fx_dotc(fa + Nf, fb + Nf, G.My);
+                const cff sz = fx_dotc(fa + Nf + G.My, fb + Nf + G.My, G.Mz);
+                const cff gu = cff_mul(sf, cff_mul(sy, sz));
+                const float aa = amp[a] * amp[b];
+                Lsm[tri(a, b)] = make_float2(aa * (gu.re.hi + gu.re.lo), aa * (gu.im.hi + gu.im.lo));
+                const ff sc = ff_prod(adS[a], adS[b]);
+                cff v{ff_mul(gu.re, sc), ff_mul(gu.im, sc)};
+                if (a == b) { v.re = ff_add(v.re, ebff); v.im = ff{0.f, 0.f}; }
+                if (b == 0) colbuf[a] = v;
+                if (a == 0 && b == 0) { pivbuf[0] = v.re; pivbuf[1] = ff_recip(v.re); }
+                return v;
+            };
+            #pragma unroll
+            for (int q = 0; q < 8; ++q) {
+                const int c = 4 * q + cg;
+                if (c <= ra && ra < S) Ar[q] = gram(ra, c);
             }
-            __syncwarp();
-            // rhs_a = d_a (g_a - sum_b G_ab cm_b) with G recovered from A (FP32 is enough here)
-            for (int a = lane; a < S; a += 32) {
+            #pragma unroll
+            for (int q = 0; q < 16; ++q) {
+                const int c = 4 * q + cg;
+                if (c <= rb && rb < S) Br[q] = gram(rb, c);
+            }
+            __syncthreads();
+            // rhs_a = d_a (g_a - sum_b G_ab pi_b mu_b), FP32
+            float2 rhs = make_float2(0.f, 0.f);
+            if (tid < S) {
+                const int a = tid;
                 float2 acc = gS[a];
                 for (int b = 0; b < S; ++b) {
-                    if (dS[a].x == 0.f || dS[b].x == 0.f) continue;
-                    const cff e = (b <= a) ? Am[tri(a, b)] : Am[tri(b, a)];
-                    float re = e.re.hi + e.re.lo, im = (b <= a) ? (e.im.hi + e.im.lo) : -(e.im.hi + e.im.lo);
-                    if (a == b) re -= ebf;
-                    const float inv = 1.0f / (dS[a].x * dS[b].x);
-                    const float2 u = cmul(make_float2(re * inv, im * inv), cmS[b]);
+                    const float2 e = (b <= a) ? Lsm[tri(a, b)] : make_float2(Lsm[tri(b, a)].x, -Lsm[tri(b, a)].y);
+                    const float2 u = cmul(e, cmS[b]);
                     acc.x -= u.x; acc.y -= u.y;
                 }
-                gS[a] = make_float2(dS[a].x * acc.x, dS[a].x * acc.y);
+                rhs = make_float2(dS[a] * acc.x, dS[a] * acc.y);
             }
-            __syncwarp();
-            // float-float Cholesky (right-looking), log det from the pivots
-            double logdet = 0.0;
+            __syncthreads();
+            if (tid < S) gS[tid] = rhs;
+            // float-float Cholesky; log det from the product of the pivots (exponent kept apart)
+            ff prod{1.f, 0.f};
+            int pexp = 0;
             for (int k = 0; k < S; ++k) {
-                ff piv = Am[tri(k, k)].re;
-                if (!(piv.hi > 0.f)) piv = ff{1e-30f, 0.f};
-                logdet += log((double)piv.hi) + (double)piv.lo / (double)piv.hi;
-                // L_kk = sqrt(piv) in float-float (one Newton step)
-                const float r0 = sqrtf(piv.hi);
-                const ff r0sq = ff_prod(r0, r0);
-                const ff resid = ff_add(piv, ff_neg(r0sq));
-                ff lk;
-                fast_two_sum(r0, resid.hi / (2.0f * r0), lk.hi, lk.lo);
-                __syncwarp();
-                for (int i = k + 1 + lane; i < S; i += 32) {
-                    cff v = Am[tri(i, k)];
-                    v.re = ff_div(v.re, lk);
-                    v.im = ff_div(v.im, lk);
-                    Am[tri(i, k)] = v;
+                const int cur = k & 1, nxt = cur ^ 1;
+                const cff* col = colbuf + cur * IB_SMAX;
+                cff* ncol = colbuf + nxt * IB_SMAX;
+                ff piv = pivbuf[2 * cur];
+                ff inv = pivbuf[2 * cur + 1];
+                if (!(piv.hi > 0.f)) { piv = ff{1e-30f, 0.f}; inv = ff{1e30f, 0.f}; }
+                const float lkk = sqrtf(piv.hi + piv.lo);
+                if (tid == 0) {
+                    prod = ff_mul(prod, piv);
+                    int e;
+                    frexpf(prod.hi, &e);
+                    prod.hi = ldexpf(prod.hi, -e); prod.lo = ldexpf(prod.lo, -e);
+                    pexp += e;
+                    Lsm[tri(k, k)] = make_float2(lkk, 0.f);
                 }
-                __syncwarp();
-                if (lane == 0) Am[tri(k, k)] = cff{lk, ff{0.f, 0.f}};
-                const int n = S - k - 1;
-                for (int t = lane; t < n * (n + 1) / 2; t += 32) {
-                    int a, c;
-                    tri_ab(t, a, c);
-                    const int i = k + 1 + a, cc = k + 1 + c;
-                    const cff u = cff_mulc(Am[tri(cc, k)], Am[tri(i, k)]);   // L_ik conj(L_ck)
-                    Am[tri(i, cc)] = cff_sub(Am[tri(i, cc)], u);
+                {
+                    const int i = k + 1 + tid;
+                    if (i < S) {
+                        const cff v = col[i];
+                        const float il = 1.0f / lkk;
+                        Lsm[tri(i, k)] = make_float2((v.re.hi + v.re.lo) * il, (v.im.hi + v.im.lo) * il);
+                    }
                 }
-                __syncwarp();
-            }
-            // solves with the FP32 parts of L
-            for (int i = 0; i < S; ++i) {
-                float2 acc = make_float2(0.f, 0.f);
-                for (int b = lane; b < i; b += 32) {
-                    const cff l = Am[tri(i, b)];
-                    const float2 u = cmul(make_float2(l.re.hi + l.re.lo, l.im.hi + l.im.lo), gS[b]);
-                    acc.x += u.x; acc.y += u.y;
+                cff la{}, lb{};
+                if (ra > k && ra < S) { const cff v = col[ra]; la = cff{ff_mul(v.re, inv), ff_mul(v.im, inv)}; }
+                if (rb > k && rb < S) { const cff v = col[rb]; lb = cff{ff_mul(v.re, inv), ff_mul(v.im, inv)}; }
+                #pragma unroll
+                for (int q = 0; q < 8; ++q) {
+                    const int c = 4 * q + cg;
+                    if (c > k && c <= ra && ra < S) {
+                        cff_sub_mulc(Ar[q], la, col[c]);
+                        if (c == k + 1) {
+                            const cff v = cff_norm(Ar[q]);
+                            ncol[ra] = v;
+                            if (ra == c) { pivbuf[2 * nxt] = v.re; pivbuf[2 * nxt + 1] = ff_recip(v.re); }
+                        }
+                    }
                 }
-                acc.x = warp_sum_f(acc.x); acc.y = warp_sum_f(acc.y);
-                if (lane == 0) { const float dd = Am[tri(i, i)].re.hi; gS[i] = make_float2((gS[i].x - acc.x) / dd, (gS[i].y - acc.y) / dd); }
-                __syncwarp();
-            }
-            for (int i = S - 1; i >= 0; --i) {
-                float2 acc = make_float2(0.f, 0.f);
-                for (int b = i + 1 + lane; b < S; b += 32) {
-                    const cff l = Am[tri(b, i)];
-                    const float2 u = cmulc(make_float2(l.re.hi + l.re.lo, l.im.hi + l.im.lo), gS[b]);
-                    acc.x += u.x; acc.y += u.y;
+                #pragma unroll
+                for (int q = 0; q < 16; ++q) {
+                    const int c = 4 * q + cg;
+                    if (c > k && c <= rb && rb < S) {
+                        cff_sub_mulc(Br[q], lb, col[c]);
+                        if (c == k + 1) {
+                            const cff v = cff_norm(Br[q]);
+                            ncol[rb] = v;
+                            if (rb == c) { pivbuf[2 * nxt] = v.re; pivbuf[2 * nxt + 1] = ff_recip(v.re); }
+                        }
+                    }
                 }
-                acc.x = warp_sum_f(acc.x); acc.y = warp_sum_f(acc.y);
-                if (lane == 0) { const float dd = Am[tri(i, i)].re.hi; gS[i] = make_float2((gS[i].x - acc.x) / dd, (gS[i].y - acc.y) / dd); }
-                __syncwarp();
+                __syncthreads();
             }
-            double yy = 0.0;
-            for (int a = lane; a < S; a += 32) {
-                const float2 y = gS[a];
-                yy += (double)y.x * y.x + (double)y.y * y.y;
-                cmS[a] = make_float2(cmS[a].x + dS[a].x * y.x, cmS[a].y + dS[a].x * y.y);
+            // solves L u = rhs, L^H y = u (warp 0; lane owns rows lane and lane + 32)
+            if (wid == 0) {
+                float2 r0 = (lane < S) ? gS[lane] : make_float2(0.f, 0.f);
+                float2 r1 = (lane + 32 < S) ? gS[lane + 32] : make_float2(0.f, 0.f);
+                for (int k = 0; k < S; ++k) {
+                    const float2 own = (k < 32) ? r0 : r1;
+                    const float dkk = Lsm[tri(k, k)].x;
+                    float2 uk = make_float2(__shfl_sync(0xffffffffu, own.x, k & 31) / dkk,
+                                            __shfl_sync(0xffffffffu, own.y, k & 31) / dkk);
+                    if (lane == (k & 31)) { if (k < 32) r0 = uk; else r1 = uk; }
+                    if (lane > k && lane < S) { const float2 u = cmul(Lsm[tri(lane, k)], uk); r0.x -= u.x; r0.y -= u.y; }
+                    if (lane + 32 > k && lane + 32 < S) { const float2 u = cmul(Lsm[tri(lane + 32, k)], uk); r1.x -= u.x; r1.y -= u.y; }
+                }
+                for (int k = S - 1; k >= 0; --k) {
+                    const float2 own = (k < 32) ? r0 : r1;
+                    const float dkk = Lsm[tri(k, k)].x;
+                    float2 yk = make_float2(__shfl_sync(0xffffffffu, own.x, k & 31) / dkk,
+                                            __shfl_sync(0xffffffffu, own.y, k & 31) / dkk);
+                    if (lane == (k & 31)) { if (k < 32) r0 = yk; else r1 = yk; }
+                    if (lane < k) { const float2 u = cmulc(Lsm[tri(k, lane)], yk); r0.x -= u.x; r0.y -= u.y; }
+                    if (lane + 32 < k) { const float2 u = cmulc(Lsm[tri(k, lane + 32)], yk); r1.x -= u.x; r1.y -= u.y; }
+                }
+                double yy = 0.0;
+                if (lane < S) {
+                    yy += (double)r0.x * r0.x + (double)r0.y * r0.y;
+                    const float2 c = cmS[lane];
+                    cmS[lane] = make_float2(amp[lane] * (c.x + dS[lane] * r0.x), amp[lane] * (c.y + dS[lane] * r0.y));
+                }
+                if (lane + 32 < S) {
+                    yy += (double)r1.x * r1.x + (double)r1.y * r1.y;
+                    const float2 c = cmS[lane + 32];
+                    cmS[lane + 32] = make_float2(amp[lane + 32] * (c.x + dS[lane + 32] * r1.x),
+                                                 amp[lane + 32] * (c.y + dS[lane + 32] * r1.y));
+                }
+                yy = warp_sum_d(yy);
+                if (lane == 0) red[0] = yy;
             }
-            yy = warp_sum_d(yy);
-            __syncwarp();
+            __syncthreads();
+            // residual r = z - sum_s A_s (pi mu + d y)_s (b' kron a_y kron a_z)_s
             double rr = 0.0;
-            for (int k = lane; k < Nz; k += 32) {
+            for (int k = tid; k < Nz; k += IB_T) {
                 const int f = k / Nm, ym = k - f * Nm, y = ym / G.Mz, m = ym - y * G.Mz;
-                float2 acc = make_float2(z[2 * (j * Nz + k)], z[2 * (j * Nz + k) + 1]);
+                float2 acc = zs[k];
                 for (int s = 0; s < S; ++s) {
                     const float2* fs = fac + (size_t)s * nfac;
-                    const float2 u = cmul(cmul(cmS[s], cS[s]), cmul(fs[f], cmul(fs[Nf + y], fs[Nf + G.My + m])));
+                    const float2 u = cmul(cmul(cmS[s], fs[f]), cmul(fs[Nf + y], fs[Nf + G.My + m]));
                     acc.x -= u.x; acc.y -= u.y;
                 }
                 rr += (double)(acc.x * acc.x + acc.y * acc.y);
             }
             rr = warp_sum_d(rr);
-            total += -(rr / eb + yy) - (logdet - S * log(eb)) - Nz * log(M_PI * eb);
-            __syncwarp();
+            if (lane == 0) red[4 + wid] = rr;
+            __syncthreads();
+            if (tid == 0) {
+                const double rrs = red[4] + red[5] + red[6] + red[7];
+                const double logdet = log((double)prod.hi + (double)prod.lo) + pexp * M_LN2;
+                total += -(rrs / eb + red[0]) - (logdet - S * log(eb)) - Nz * log(M_PI * eb);
+            }
         }
-        if (lane == 0) D.lw_x[pp] = total;
+        if (tid == 0) D.lw_x[pp] = total;
     }
 }
 
@@ -643,7 +769,7 @@ void launch_kappa(const DevGeom& G, const DevParams& Pm, const DevState& D, int 
 constexpr int IOTA_FF_ALL_S = 24;
 
 void launch_iota(const DevGeom& G, const DevParams& Pm, const DevState& D, int S, const float* z, cudaStream_t st) {
-    if (S >= IOTA_FF_ALL_S) return;   // k_iota_ff handles every particle (launch_iota_repair)
+    if (S >= IOTA_FF_ALL_S) return;   // k_iota_blk handles every particle (launch_iota_repair)
     const int nfac = G.Nf + G.My + G.Mz;
     const size_t per_warp = iota32_warp_f2(S, nfac, G.Nf) * sizeof(float2);
     int wpb = 8;
@@ -656,15 +782,13 @@ void launch_iota(const DevGeom& G, const DevParams& Pm, const DevState& D, int S
 
 void launch_iota_repair(const DevGeom& G, const DevParams& Pm, const DevState& D, int S, const float* z, cudaStream_t st) {
     const int nfac = G.Nf + G.My + G.Mz;
-    const size_t per_warp = iota_ff_warp_floats(S, nfac) * sizeof(float);
-    int wpb = 4;
-    while (wpb > 1 && wpb * per_warp > 160 * 1024) wpb /= 2;
-    const size_t smem = wpb * per_warp;
+    const size_t smem = iota_blk_smem(S, nfac, G.Nf, G.Nz);
     const int all = S >= IOTA_FF_ALL_S ? 1 : 0;
     if (all) cudaMemsetAsync(D.flags, 0, sizeof(int), st);
-    cudaFuncSetAttribute(k_iota_ff, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
-    const int blocks = all ? (Pm.P + wpb - 1) / wpb : 4 * 152;
-    k_iota_ff<<<blocks, 32 * wpb, smem, st>>>(G, Pm, D, S, z, all);
+    cudaFuncSetAttribute(k_iota_blk, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    const int wave = 3 * 152;
+    const int blocks = all ? std::min(Pm.P, 16 * wave) : wave;
+    k_iota_blk<<<blocks, IB_T, smem, st>>>(G, Pm, D, S, z, all);
 }
 
 void launch_nu(const DevGeom& G, const DevParams& Pm, const DevState& D, int S, cudaStream_t st) {
