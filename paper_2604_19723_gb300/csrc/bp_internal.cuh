@@ -282,7 +282,7 @@ struct DevState {
     float2* kV;       // [S_max][J][Nz][S_cap]   whitened basis, column S_cap-1 = r0
     float2* kR;       // [S_max][J][S_cap*S_cap] upper Cholesky factor (FP32, padded identity)
     float2* ky0;      // [S_max][J][S_cap]       y0 = R^-1 V^H e0 / eta_bar
-    double* kJ0;      // [S_max][J]              J0* = |r0|^2/eta_bar + |y0|^2
+    double* kJ0;      // [S_max][J]              |r0|^2/eta_bar
     // nu stage outputs (per j)
     double* nu_T;     // [J][S_max] diag a_k, [J][S_max] |offdiag|^2, [J][S_max] double2 b'
     double* nu_c;     // [J][2] |e|^2, constant

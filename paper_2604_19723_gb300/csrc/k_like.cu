@@ -82,7 +82,7 @@ __global__ void __launch_bounds__(256, 1) k_kappa(DevGeom G, DevParams Pm, DevSt
         const double eb = D.eta_bar[j];
         const float ebf = (float)eb;
         const double zeta = D.zeta[s * J + j];
-        const double J0 = D.kJ0[s * J + j];
+        const double J0r = D.kJ0[s * J + j];   // |r0|^2 / eta_bar
         float2* fb = fac + tid;
         float2* fy = fb + G.Nf * KT;
         float2* fz = fy + G.My * KT;
@@ -120,10 +120,10 @@ __global__ void __launch_bounds__(256, 1) k_kappa(DevGeom G, DevParams Pm, DevSt
             }
           }
         }
-        double hh = 0.0;
+        float hh = 0.f;   // alpha here only places tau (the objective is evaluated exactly at it)
         #pragma unroll
-        for (int c = 0; c < NC; ++c) hh += (double)h[c].x * h[c].x + (double)h[c].y * h[c].y;
-        const double alpha = ((double)nps - hh / eb) / eb;
+        for (int c = 0; c < NC; ++c) hh = fmaf(h[c].x, h[c].x, fmaf(h[c].y, h[c].y, hh));
+        const double alpha = ((double)nps - (double)hh / eb) / eb;
         const double2 beta = make_double2(pr.x / eb, pr.y / eb);
         const double2 a = make_double2(zeta * mr, zeta * mi);
         const double q = (gm + (mr * mr + mi * mi) * (1.0 - zeta)) * zeta;
@@ -137,7 +137,7 @@ __global__ void __launch_bounds__(256, 1) k_kappa(DevGeom G, DevParams Pm, DevSt
         const float2 tf = make_float2((float)tau.x, (float)tau.y);
         // pass 2: r = r0 - tau (psi - V V^H psi / eta_bar), |r|^2 and |psi_perp|^2
         const float ieb = 1.0f / ebf;
-        double rr = 0.0;
+        ff rr{0.f, 0.f};   // |r|^2, float-float over (f, y) chunks
         float pn = 0.f;
         for (int f0 = 0; f0 < G.Nf; f0 += fch) {
           if (fch < G.Nf) { __syncthreads(); stage_rows(f0); __syncthreads(); }
@@ -169,12 +169,13 @@ __global__ void __launch_bounds__(256, 1) k_kappa(DevGeom G, DevParams Pm, DevSt
                     const float rx = r0.x - t.x, ry = r0.y - t.y;
                     rr_chunk += rx * rx + ry * ry;
                 }
-                rr += rr_chunk;
+                rr = ff_add(rr, ff{rr_chunk, 0.f});
             }
           }
         }
-        // y = y0 - tau R^-1 V^H psi / eta_bar (back substitution in place: h <- R^-1 conj(h))
-        double yy = 0.0, gg = 0.0;
+        // y = y0 - u, u = tau R^-1 V^H psi / eta_bar (back substitution in place:
+        // h <- R^-1 conj(h)); |y0|^2 - |y|^2 = 2 Re(conj(y0) u) - |u|^2 in FP32
+        float dy0 = 0.f, dy1 = 0.f, gg0 = 0.f, gg1 = 0.f;
         #pragma unroll
         for (int c = NC - 1; c >= 0; --c) {
             const int off = c * NC - c * (c - 1) / 2;    // packed row c starts at R[c][c]
@@ -188,22 +189,25 @@ __global__ void __launch_bounds__(256, 1) k_kappa(DevGeom G, DevParams Pm, DevSt
             }
             const float dr = Rs[off].x;
             h[c] = make_float2(g.x / dr, g.y / dr);
-            gg += (double)h[c].x * h[c].x + (double)h[c].y * h[c].y;
-            const float2 tg = cmul(tf, h[c]);
+            const float2 u = cmul(tf, make_float2(h[c].x * ieb, h[c].y * ieb));
             const float2 y0 = y0s[c];
-            const double yx = (double)y0.x - (double)tg.x / eb, yi = (double)y0.y - (double)tg.y / eb;
-            yy += yx * yx + yi * yi;
+            if (c & 1) {
+                gg1 = fmaf(h[c].x, h[c].x, fmaf(h[c].y, h[c].y, gg1));
+                dy1 += 2.f * (y0.x * u.x + y0.y * u.y) - (u.x * u.x + u.y * u.y);
+            } else {
+                gg0 = fmaf(h[c].x, h[c].x, fmaf(h[c].y, h[c].y, gg0));
+                dy0 += 2.f * (y0.x * u.x + y0.y * u.y) - (u.x * u.x + u.y * u.y);
+            }
         }
-        double Jt = rr / eb + yy;
-        double logdet = 0.0;
+        double dlt = J0r - (rr.hi + (double)rr.lo) / eb + (double)(dy0 + dy1);
         if (q > 0.0) {
-            const double dx = tau.x - a.x, dy = tau.y - a.y;
-            Jt += (dx * dx + dy * dy) / q;
+            const double dx = tau.x - a.x, dyt = tau.y - a.y;
+            dlt -= (dx * dx + dyt * dyt) / q;
             // alpha = psi^H A^-1 psi = |psi_perp|^2/eta_bar + |R^-1 V^H psi|^2/eta_bar^2 (non-negative terms)
-            const double alpha_acc = (double)pn / eb + gg / (eb * eb);
-            logdet = log1p(q * alpha_acc);
+            const float alpha_acc = pn * ieb + (gg0 + gg1) * ieb * ieb;
+            dlt -= (double)log1pf((float)q * alpha_acc);
         }
-        delta_sum += J0 - Jt - logdet;
+        delta_sum += dlt;
     }
     if (act) D.lw_y[(size_t)s * P + p] = delta_sum;
 }
@@ -470,7 +474,7 @@ __device__ inline ff ff_recip(ff x) {
 }
 
 // shared memory of k_iota_blk (bytes): colbuf [2][64] cff, pivbuf [2][2] ff, red [8]
-// double, then float2 z [Nz], factors [S][nfac], cm [S], g [S], L packed [S(S+1)/2]
+// double, A packed lower [S(S+1)/2] cff, then float2 z [Nz], factors [S][nfac], cm [S], g [S], L packed [S(S+1)/2]
 // (also the partial sums g [S][Nf] before the Gram), then float amplitude [S],
 // A d [S], d [S]
 __host__ __device__ inline size_t iota_blk_lsize(int S, int Nf) {
@@ -478,7 +482,7 @@ __host__ __device__ inline size_t iota_blk_lsize(int S, int Nf) {
     return a > b ? a : b;
 }
 __host__ __device__ inline size_t iota_blk_smem(int S, int nfac, int Nf, int Nz) {
-    return 2 * IB_SMAX * 16 + 4 * 8 + 8 * 8 +
+    return 2 * IB_SMAX * 16 + 4 * 8 + 8 * 8 + (size_t)S * (S + 1) / 2 * 16 +
            ((size_t)Nz + (size_t)S * nfac + 2 * (size_t)S + iota_blk_lsize(S, Nf)) * 8 + 3 * (size_t)S * 4;
 }
 
@@ -489,7 +493,8 @@ __global__ void __launch_bounds__(IB_T, 3) k_iota_blk(DevGeom G, DevParams Pm, D
     double* red = reinterpret_cast<double*>(pivbuf + 4);          // [8]
     const int P = Pm.P, J = G.J, Nz = G.Nz, Nm = G.My * G.Mz, Nf = G.Nf;
     const int nfac = Nf + G.My + G.Mz;
-    float2* zs = reinterpret_cast<float2*>(red + 8);              // [Nz]
+    cff* Apk = reinterpret_cast<cff*>(red + 8);                    // [S(S+1)/2] float-float A
+    float2* zs = reinterpret_cast<float2*>(Apk + (size_t)S * (S + 1) / 2);   // [Nz]
     float2* fac = zs + Nz;                                        // [S][nfac]: b', a_y, a_z
     float2* cmS = fac + (size_t)S * nfac;                         // [S] pi mu, then A (pi mu + d y)
     float2* gS = cmS + S;                                         // [S] g, rhs, solution
@@ -549,9 +554,10 @@ __global__ void __launch_bounds__(IB_T, 3) k_iota_blk(DevGeom G, DevParams Pm, D
                 gS[s] = make_float2(amp[s] * acc.x, amp[s] * acc.y);
             }
             __syncthreads();
-            // Gram entries of this thread's slots (rows ra: q < 8, rb: q < 16)
-            cff Ar[8], Br[16];
-            auto gram = [&](int a, int b) -> cff {
+            // Gram, one packed entry per task (a >= b), into shared memory
+            for (int t = tid; t < S * (S + 1) / 2; t += IB_T) {
+                int a, b;
+                tri_ab(t, a, b);
                 const float2* fa = fac + (size_t)a * nfac;
                 const float2* fb = fac + (size_t)b * nfac;
                 const cff sf = fx_dotc(fa, fb, Nf);
@@ -559,25 +565,27 @@ __global__ void __launch_bounds__(IB_T, 3) k_iota_blk(DevGeom G, DevParams Pm, D
                 const cff sz = fx_dotc(fa + Nf + G.My, fb + Nf + G.My, G.Mz);
                 const cff gu = cff_mul(sf, cff_mul(sy, sz));
                 const float aa = amp[a] * amp[b];
-                Lsm[tri(a, b)] = make_float2(aa * (gu.re.hi + gu.re.lo), aa * (gu.im.hi + gu.im.lo));
+                Lsm[t] = make_float2(aa * (gu.re.hi + gu.re.lo), aa * (gu.im.hi + gu.im.lo));
                 const ff sc = ff_prod(adS[a], adS[b]);
                 cff v{ff_mul(gu.re, sc), ff_mul(gu.im, sc)};
                 if (a == b) { v.re = ff_add(v.re, ebff); v.im = ff{0.f, 0.f}; }
+                Apk[t] = v;
                 if (b == 0) colbuf[a] = v;
-                if (a == 0 && b == 0) { pivbuf[0] = v.re; pivbuf[1] = ff_recip(v.re); }
-                return v;
-            };
+                if (t == 0) { pivbuf[0] = v.re; pivbuf[1] = ff_recip(v.re); }
+            }
+            __syncthreads();
+            // this thread's slots (rows ra: q < 8, rb: q < 16) into registers
+            cff Ar[8], Br[16];
             #pragma unroll
             for (int q = 0; q < 8; ++q) {
                 const int c = 4 * q + cg;
-                if (c <= ra && ra < S) Ar[q] = gram(ra, c);
+                if (c <= ra && ra < S) Ar[q] = Apk[tri(ra, c)];
             }
             #pragma unroll
             for (int q = 0; q < 16; ++q) {
                 const int c = 4 * q + cg;
-                if (c <= rb && rb < S) Br[q] = gram(rb, c);
+                if (c <= rb && rb < S) Br[q] = Apk[tri(rb, c)];
             }
-            __syncthreads();
             // rhs_a = d_a (g_a - sum_b G_ab pi_b mu_b), FP32
             float2 rhs = make_float2(0.f, 0.f);
             if (tid < S) {

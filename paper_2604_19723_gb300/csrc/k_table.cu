@@ -370,7 +370,6 @@ __global__ void k_stage_kappa(DevGeom G, DevParams Pm, DevState D, int S, int SC
     if (threadIdx.x == 0) {
         // y0 = R^-1 y~0
         double2 y0[S_CAP_MAX];
-        double yy = 0.0;
         for (int c = K - 1; c >= 0; --c) {
             double2 a = ye[c];
             for (int c2 = c + 1; c2 < K; ++c2) {
@@ -379,11 +378,10 @@ __global__ void k_stage_kappa(DevGeom G, DevParams Pm, DevState D, int S, int SC
             }
             const double d = R[c * K + c].x;
             y0[c] = make_double2(a.x / d, a.y / d);
-            yy += y0[c].x * y0[c].x + y0[c].y * y0[c].y;
         }
         float2* ky = D.ky0 + ((size_t)s * J + j) * SC;
         for (int c = 0; c < SC; ++c) ky[c] = (c < K) ? make_float2((float)y0[c].x, (float)y0[c].y) : make_float2(0.f, 0.f);
-        D.kJ0[s * J + j] = rr[0] / eb + yy;
+        D.kJ0[s * J + j] = rr[0] / eb;   // the |y|^2 part enters the particle kernel as a difference
     }
     // R as FP32, padded with the identity
     float2* kR = D.kR + ((size_t)s * J + j) * SC * SC;
