@@ -230,6 +230,32 @@ __device__ inline cff cff_prodc(float2 a, float2 b) {
     return cff{ff_add(ff_prod(a.x, b.x), ff_prod(a.y, b.y)), ff_add(ff_prod(a.x, b.y), ff_neg(ff_prod(a.y, b.x)))};
 }
 
+// acc += |v|^2 with exact squares; acc.lo is left unnormalised
+__device__ inline void ff_acc_sq(ff& acc, float2 v) {
+    const float p1 = __fmul_rn(v.x, v.x), e1 = fmaf(v.x, v.x, -p1);
+    const float p2 = __fmul_rn(v.y, v.y), e2 = fmaf(v.y, v.y, -p2);
+    float s, e, t;
+    two_sum(acc.hi, p1, s, e);
+    two_sum(s, p2, acc.hi, t);
+    acc.lo = __fadd_rn(acc.lo, __fadd_rn(__fadd_rn(e, t), __fadd_rn(e1, e2)));
+}
+__device__ inline double ff_to_d(ff v) { return (double)v.hi + (double)v.lo; }
+// running product of positive factors as a float-float mantissa in [0.5, 1) and an exponent
+struct ffexp { ff m; int e; };
+__device__ inline void ffexp_mul(ffexp& x, ff f) {
+    x.m = ff_mul(x.m, f);
+    int e;
+    frexpf(x.m.hi, &e);
+    x.m.hi = ldexpf(x.m.hi, -e);
+    x.m.lo = ldexpf(x.m.lo, -e);
+    x.e += e;
+}
+// log of the product: logf is applied to the mantissa only (|log m| < 0.7, so its
+// 1-ulp error is below 1e-7), the exponent enters exactly
+__device__ inline double ffexp_log(const ffexp& x) {
+    return (double)logf(x.m.hi) + (double)(x.m.lo / x.m.hi) + (double)x.e * 0.69314718055994530942;
+}
+
 __device__ inline double warp_sum_d(double v) {
     #pragma unroll
     for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
@@ -238,6 +264,14 @@ __device__ inline double warp_sum_d(double v) {
 __device__ inline float warp_sum_f(float v) {
     #pragma unroll
     for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
+    return v;
+}
+__device__ inline ff warp_sum_ff(ff v) {
+    #pragma unroll
+    for (int o = 16; o > 0; o >>= 1) {
+        const ff w{__shfl_xor_sync(0xffffffffu, v.hi, o), __shfl_xor_sync(0xffffffffu, v.lo, o)};
+        v = ff_add(v, w);
+    }
     return v;
 }
 __device__ inline double warp_max_d(double v) {

@@ -34,7 +34,7 @@ template <int SC>
 __host__ __device__ constexpr int kappa_rpack() { return (SC - 1) * SC / 2; }
 
 template <int SC>
-__global__ void __launch_bounds__(256, 1) k_kappa(DevGeom G, DevParams Pm, DevState D, int S, int SCA, int fch) {
+__global__ void __launch_bounds__(256, (SC <= 16 ? 2 : 1)) k_kappa(DevGeom G, DevParams Pm, DevState D, int S, int SCA, int fch) {
     constexpr int KT = 256;
     constexpr int NC = SC - 1;           // basis columns (zero beyond S-2)
     constexpr int NP = SC / 2;           // column pairs per row
@@ -51,8 +51,9 @@ __global__ void __launch_bounds__(256, 1) k_kappa(DevGeom G, DevParams Pm, DevSt
     const int pp = act ? p : 0;
     const float* ph = D.phi[D.cur] + (size_t)s * 6 * P;
     const float4* geo_s = D.geo + (size_t)s * J * P;
-    const double gm = ph[3 * P + pp];
-    const double mr = ph[4 * P + pp], mi = ph[5 * P + pp];
+    const float gmf = ph[3 * P + pp];
+    const float mrf = ph[4 * P + pp], mif = ph[5 * P + pp];
+    const double mr = mrf, mi = mif;
     double delta_sum = 0.0;
     for (int j = 0; j < J; ++j) {
         const float2* gV = D.kV + ((size_t)s * J + j) * Nz * SCA;
@@ -81,6 +82,7 @@ __global__ void __launch_bounds__(256, 1) k_kappa(DevGeom G, DevParams Pm, DevSt
         __syncthreads();
         const double eb = D.eta_bar[j];
         const float ebf = (float)eb;
+        const double ieb64 = 1.0 / eb;
         const double zeta = D.zeta[s * J + j];
         const double J0r = D.kJ0[s * J + j];   // |r0|^2 / eta_bar
         float2* fb = fac + tid;
@@ -123,20 +125,20 @@ __global__ void __launch_bounds__(256, 1) k_kappa(DevGeom G, DevParams Pm, DevSt
         float hh = 0.f;   // alpha here only places tau (the objective is evaluated exactly at it)
         #pragma unroll
         for (int c = 0; c < NC; ++c) hh = fmaf(h[c].x, h[c].x, fmaf(h[c].y, h[c].y, hh));
-        const double alpha = ((double)nps - (double)hh / eb) / eb;
-        const double2 beta = make_double2(pr.x / eb, pr.y / eb);
-        const double2 a = make_double2(zeta * mr, zeta * mi);
-        const double q = (gm + (mr * mr + mi * mi) * (1.0 - zeta)) * zeta;
-        double2 tau;
-        if (q > 0.0) {
-            const double den = alpha + 1.0 / q;
-            tau = make_double2((beta.x + a.x / q) / den, (beta.y + a.y / q) / den);
-        } else {
-            tau = a;
-        }
-        const float2 tf = make_float2((float)tau.x, (float)tau.y);
-        // pass 2: r = r0 - tau (psi - V V^H psi / eta_bar), |r|^2 and |psi_perp|^2
+        // tau in FP32: J is evaluated exactly at the tau used, so its rounding
+        // enters Delta at second order only
         const float ieb = 1.0f / ebf;
+        const float alpha = (nps - hh * ieb) * ieb;
+        const float zf = (float)zeta;
+        const float2 af = make_float2(zf * mrf, zf * mif);
+        const float q = (gmf + (mrf * mrf + mif * mif) * (1.0f - zf)) * zf;
+        const float iq = (q > 0.f) ? 1.0f / q : 0.f;
+        float2 tf = af;
+        if (q > 0.f) {
+            const float den = alpha + iq;
+            tf = make_float2((pr.x * ieb + af.x * iq) / den, (pr.y * ieb + af.y * iq) / den);
+        }
+        // pass 2: r = r0 - tau (psi - V V^H psi / eta_bar), |r|^2 and |psi_perp|^2
         ff rr{0.f, 0.f};   // |r|^2, float-float over (f, y) chunks
         float pn = 0.f;
         for (int f0 = 0; f0 < G.Nf; f0 += fch) {
@@ -199,13 +201,15 @@ __global__ void __launch_bounds__(256, 1) k_kappa(DevGeom G, DevParams Pm, DevSt
                 dy0 += 2.f * (y0.x * u.x + y0.y * u.y) - (u.x * u.x + u.y * u.y);
             }
         }
-        double dlt = J0r - (rr.hi + (double)rr.lo) / eb + (double)(dy0 + dy1);
-        if (q > 0.0) {
-            const double dx = tau.x - a.x, dyt = tau.y - a.y;
-            dlt -= (dx * dx + dyt * dyt) / q;
+        double dlt = J0r - ((double)rr.hi + (double)rr.lo) * ieb64 + (double)(dy0 + dy1);
+        if (q > 0.f) {
+            // prior term |tau - a|^2 / q with the difference taken in FP64 (a may be
+            // much larger than the innovation)
+            const double dx = (double)tf.x - zeta * mr, dyt = (double)tf.y - zeta * mi;
+            dlt -= (dx * dx + dyt * dyt) * (double)iq;
             // alpha = psi^H A^-1 psi = |psi_perp|^2/eta_bar + |R^-1 V^H psi|^2/eta_bar^2 (non-negative terms)
             const float alpha_acc = pn * ieb + (gg0 + gg1) * ieb * ieb;
-            dlt -= (double)log1pf((float)q * alpha_acc);
+            dlt -= (double)log1pf(q * alpha_acc);
         }
         delta_sum += dlt;
     }
@@ -224,6 +228,7 @@ __global__ void __launch_bounds__(256, 1) k_kappa(DevGeom G, DevParams Pm, DevSt
 // The FP32 log det error per pivot is about 8 eps ratio (measured), so the
 // bound keeps unrepaired particles within ~5e-5 in log-likelihood.
 constexpr float IOTA_RATIO_MAX = 100.0f;
+constexpr double LOG_PI = 1.14472988584940017414;   // log(pi)
 
 __device__ inline int tri(int i, int j) { return i * (i + 1) / 2 + j; }
 __device__ inline void tri_ab(int t, int& a, int& b) {
@@ -257,7 +262,10 @@ __global__ void k_iota(DevGeom G, DevParams Pm, DevState D, int S, const float* 
     const bool act = p < P;
     const int pp = act ? p : 0;
     const float* phi = D.phi[D.cur];
-    double total = 0.0, ratio2 = 0.0;
+    __shared__ double lg_eb[J_MAX], inv_eb[J_MAX];
+    if (threadIdx.x < J) { lg_eb[threadIdx.x] = log(D.eta_bar[threadIdx.x]); inv_eb[threadIdx.x] = 1.0 / D.eta_bar[threadIdx.x]; }
+    double total = 0.0;
+    float ratio2 = 0.f;
     for (int j = 0; j < J; ++j) {
         __syncthreads();
         for (int k = threadIdx.x; k < Nz; k += blockDim.x)
@@ -333,12 +341,12 @@ __global__ void k_iota(DevGeom G, DevParams Pm, DevState D, int S, const float* 
             if (a == b) dS[a].y = dd * v.x + ebf;
         }
         __syncwarp();
-        double logdet = 0.0;
+        ffexp det{ff{1.f, 0.f}, 0};
         for (int k = 0; k < S; ++k) {
             const float piv = fmaxf(Am[tri(k, k)].x, 1e-30f);
             const float dk = sqrtf(piv);
-            logdet += log((double)piv);
-            const double rk = (double)dS[k].y / (double)piv;
+            ffexp_mul(det, ff{piv, 0.f});
+            const float rk = dS[k].y / piv;
             ratio2 += rk * rk;
             __syncwarp();
             for (int i = k + 1 + lane; i < S; i += 32) {
@@ -372,17 +380,17 @@ __global__ void k_iota(DevGeom G, DevParams Pm, DevState D, int S, const float* 
             if (lane == 0) { const float dd = Am[tri(i, i)].x; gS[i] = make_float2((gS[i].x - acc.x) / dd, (gS[i].y - acc.y) / dd); }
             __syncwarp();
         }
-        // 7. w = cm + d y; |y|^2
-        double yy = 0.0;
+        // 7. w = cm + d y; |y|^2 (exact squares, float-float sums)
+        ff yy{0.f, 0.f};
         for (int a = lane; a < S; a += 32) {
             const float2 y = gS[a];
-            yy += (double)y.x * y.x + (double)y.y * y.y;
+            ff_acc_sq(yy, y);
             cmS[a] = make_float2(cmS[a].x + dS[a].x * y.x, cmS[a].y + dS[a].x * y.y);
         }
-        yy = warp_sum_d(yy);
+        yy = warp_sum_ff(yy);
         __syncwarp();
         // 8. residual z - sum_s w_s psi_s, element-wise
-        double rr = 0.0;
+        ff rr{0.f, 0.f};
         for (int k = lane; k < Nz; k += 32) {
             const int f = k / Nm, ym = k - f * Nm, y = ym / G.Mz, m = ym - y * G.Mz;
             float2 acc = zs[k];
@@ -391,14 +399,15 @@ __global__ void k_iota(DevGeom G, DevParams Pm, DevState D, int S, const float* 
                 const float2 u = cmul(cmul(cmS[s], cS[s]), cmul(fs[f], cmul(fs[Nf + y], fs[Nf + G.My + m])));
                 acc.x -= u.x; acc.y -= u.y;
             }
-            rr += (double)(acc.x * acc.x + acc.y * acc.y);
+            ff_acc_sq(rr, acc);
         }
-        rr = warp_sum_d(rr);
-        total += -(rr / eb + yy) - (logdet - S * log(eb)) - Nz * log(M_PI * eb);
+        rr = warp_sum_ff(rr);
+        const double lg = lg_eb[j];
+        total += -(ff_to_d(rr) * inv_eb[j] + ff_to_d(yy)) - (ffexp_log(det) - S * lg) - Nz * (LOG_PI + lg);
     }
     if (act && lane == 0) {
         D.lw_x[p] = total;
-        if (sqrt(ratio2) > IOTA_RATIO_MAX) {
+        if (sqrtf(ratio2) > IOTA_RATIO_MAX) {
             const int slot = atomicAdd(&D.flags[0], 1);
             D.flags[1 + slot] = p;
         }
@@ -508,6 +517,8 @@ __global__ void __launch_bounds__(IB_T, 3) k_iota_blk(DevGeom G, DevParams Pm, D
     const int rp = (wid << 3) + (lane >> 2);
     const int ra = rp, rb = IB_SMAX - 1 - rp;
     const float* phi = D.phi[D.cur];
+    __shared__ double lg_eb[J_MAX], inv_eb[J_MAX];
+    if (tid < J) { lg_eb[tid] = log(D.eta_bar[tid]); inv_eb[tid] = 1.0 / D.eta_bar[tid]; }
     const int count = all ? P : D.flags[0];
     for (int w = blockIdx.x; w < count; w += gridDim.x) {
         const int pp = all ? w : D.flags[1 + w];
@@ -601,8 +612,7 @@ __global__ void __launch_bounds__(IB_T, 3) k_iota_blk(DevGeom G, DevParams Pm, D
             __syncthreads();
             if (tid < S) gS[tid] = rhs;
             // float-float Cholesky; log det from the product of the pivots (exponent kept apart)
-            ff prod{1.f, 0.f};
-            int pexp = 0;
+            ffexp det{ff{1.f, 0.f}, 0};
             for (int k = 0; k < S; ++k) {
                 const int cur = k & 1, nxt = cur ^ 1;
                 const cff* col = colbuf + cur * IB_SMAX;
@@ -612,11 +622,7 @@ __global__ void __launch_bounds__(IB_T, 3) k_iota_blk(DevGeom G, DevParams Pm, D
                 if (!(piv.hi > 0.f)) { piv = ff{1e-30f, 0.f}; inv = ff{1e30f, 0.f}; }
                 const float lkk = sqrtf(piv.hi + piv.lo);
                 if (tid == 0) {
-                    prod = ff_mul(prod, piv);
-                    int e;
-                    frexpf(prod.hi, &e);
-                    prod.hi = ldexpf(prod.hi, -e); prod.lo = ldexpf(prod.lo, -e);
-                    pexp += e;
+                    ffexp_mul(det, piv);
                     Lsm[tri(k, k)] = make_float2(lkk, 0.f);
                 }
                 {
@@ -678,24 +684,24 @@ __global__ void __launch_bounds__(IB_T, 3) k_iota_blk(DevGeom G, DevParams Pm, D
                     if (lane < k) { const float2 u = cmulc(Lsm[tri(k, lane)], yk); r0.x -= u.x; r0.y -= u.y; }
                     if (lane + 32 < k) { const float2 u = cmulc(Lsm[tri(k, lane + 32)], yk); r1.x -= u.x; r1.y -= u.y; }
                 }
-                double yy = 0.0;
+                ff yy{0.f, 0.f};
                 if (lane < S) {
-                    yy += (double)r0.x * r0.x + (double)r0.y * r0.y;
+                    ff_acc_sq(yy, r0);
                     const float2 c = cmS[lane];
                     cmS[lane] = make_float2(amp[lane] * (c.x + dS[lane] * r0.x), amp[lane] * (c.y + dS[lane] * r0.y));
                 }
                 if (lane + 32 < S) {
-                    yy += (double)r1.x * r1.x + (double)r1.y * r1.y;
+                    ff_acc_sq(yy, r1);
                     const float2 c = cmS[lane + 32];
                     cmS[lane + 32] = make_float2(amp[lane + 32] * (c.x + dS[lane + 32] * r1.x),
                                                  amp[lane + 32] * (c.y + dS[lane + 32] * r1.y));
                 }
-                yy = warp_sum_d(yy);
-                if (lane == 0) red[0] = yy;
+                yy = warp_sum_ff(yy);
+                if (lane == 0) red[0] = ff_to_d(yy);
             }
             __syncthreads();
             // residual r = z - sum_s A_s (pi mu + d y)_s (b' kron a_y kron a_z)_s
-            double rr = 0.0;
+            ff rr{0.f, 0.f};
             for (int k = tid; k < Nz; k += IB_T) {
                 const int f = k / Nm, ym = k - f * Nm, y = ym / G.Mz, m = ym - y * G.Mz;
                 float2 acc = zs[k];
@@ -704,15 +710,15 @@ __global__ void __launch_bounds__(IB_T, 3) k_iota_blk(DevGeom G, DevParams Pm, D
                     const float2 u = cmul(cmul(cmS[s], fs[f]), cmul(fs[Nf + y], fs[Nf + G.My + m]));
                     acc.x -= u.x; acc.y -= u.y;
                 }
-                rr += (double)(acc.x * acc.x + acc.y * acc.y);
+                ff_acc_sq(rr, acc);
             }
-            rr = warp_sum_d(rr);
-            if (lane == 0) red[4 + wid] = rr;
+            rr = warp_sum_ff(rr);
+            if (lane == 0) red[4 + wid] = ff_to_d(rr);
             __syncthreads();
             if (tid == 0) {
                 const double rrs = red[4] + red[5] + red[6] + red[7];
-                const double logdet = log((double)prod.hi + (double)prod.lo) + pexp * M_LN2;
-                total += -(rrs / eb + red[0]) - (logdet - S * log(eb)) - Nz * log(M_PI * eb);
+                const double lg = lg_eb[j];
+                total += -(rrs * inv_eb[j] + red[0]) - (ffexp_log(det) - S * lg) - Nz * (LOG_PI + lg);
             }
         }
         if (tid == 0) D.lw_x[pp] = total;
