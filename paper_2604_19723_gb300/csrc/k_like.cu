@@ -106,15 +106,16 @@ __global__ void __launch_bounds__(256, (SC <= 16 ? 2 : 1)) k_kappa(DevGeom G, De
                     const float4* row = Vs + (size_t)((f - f0) * Nm + y * G.Mz + m) * NP;
                     #pragma unroll
                     for (int c2 = 0; c2 < NP; ++c2) {
+                        // conj(psi) v as explicit FMA chains (4 FMA per complex term)
                         const float4 v = row[c2];
-                        h[2 * c2].x += ps.x * v.x + ps.y * v.y;
-                        h[2 * c2].y += ps.x * v.y - ps.y * v.x;
+                        h[2 * c2].x = fmaf(ps.x, v.x, fmaf(ps.y, v.y, h[2 * c2].x));
+                        h[2 * c2].y = fmaf(ps.x, v.y, fmaf(-ps.y, v.x, h[2 * c2].y));
                         if (2 * c2 + 1 < NC) {
-                            h[2 * c2 + 1].x += ps.x * v.z + ps.y * v.w;
-                            h[2 * c2 + 1].y += ps.x * v.w - ps.y * v.z;
+                            h[2 * c2 + 1].x = fmaf(ps.x, v.z, fmaf(ps.y, v.w, h[2 * c2 + 1].x));
+                            h[2 * c2 + 1].y = fmaf(ps.x, v.w, fmaf(-ps.y, v.z, h[2 * c2 + 1].y));
                         } else {
-                            pr.x += ps.x * v.z + ps.y * v.w;
-                            pr.y += ps.x * v.w - ps.y * v.z;
+                            pr.x = fmaf(ps.x, v.z, fmaf(ps.y, v.w, pr.x));
+                            pr.y = fmaf(ps.x, v.w, fmaf(-ps.y, v.z, pr.y));
                         }
                     }
                     nps += ps.x * ps.x + ps.y * ps.y;
@@ -151,21 +152,21 @@ __global__ void __launch_bounds__(256, (SC <= 16 ? 2 : 1)) k_kappa(DevGeom G, De
                 for (int m = 0; m < G.Mz; ++m) {
                     const float2 ps = cmul(w, fz[m * KT]);
                     const float4* row = Vs + (size_t)((f - f0) * Nm + y * G.Mz + m) * NP;
-                    float2 vv = make_float2(0.f, 0.f);
+                    float2 vv = make_float2(0.f, 0.f), vw = make_float2(0.f, 0.f);   // two chains
                     float2 r0 = make_float2(0.f, 0.f);
                     #pragma unroll
                     for (int c2 = 0; c2 < NP; ++c2) {
                         const float4 v = row[c2];
-                        vv.x += v.x * h[2 * c2].x + v.y * h[2 * c2].y;
-                        vv.y += v.y * h[2 * c2].x - v.x * h[2 * c2].y;
+                        vv.x = fmaf(v.x, h[2 * c2].x, fmaf(v.y, h[2 * c2].y, vv.x));
+                        vv.y = fmaf(v.y, h[2 * c2].x, fmaf(-v.x, h[2 * c2].y, vv.y));
                         if (2 * c2 + 1 < NC) {
-                            vv.x += v.z * h[2 * c2 + 1].x + v.w * h[2 * c2 + 1].y;
-                            vv.y += v.w * h[2 * c2 + 1].x - v.z * h[2 * c2 + 1].y;
+                            vw.x = fmaf(v.z, h[2 * c2 + 1].x, fmaf(v.w, h[2 * c2 + 1].y, vw.x));
+                            vw.y = fmaf(v.w, h[2 * c2 + 1].x, fmaf(-v.z, h[2 * c2 + 1].y, vw.y));
                         } else {
                             r0 = make_float2(v.z, v.w);
                         }
                     }
-                    const float2 pp2 = make_float2(ps.x - vv.x * ieb, ps.y - vv.y * ieb);
+                    const float2 pp2 = make_float2(ps.x - (vv.x + vw.x) * ieb, ps.y - (vv.y + vw.y) * ieb);
                     pn += pp2.x * pp2.x + pp2.y * pp2.y;
                     const float2 t = cmul(tf, pp2);
                     const float rx = r0.x - t.x, ry = r0.y - t.y;
