@@ -418,11 +418,11 @@ __global__ void k_iota(DevGeom G, DevParams Pm, DevState D, int S, const float* 
 // ---------------------------------------------------------------- iota, float-float Gram and Cholesky
 // For the particles the FP32 path flags (or for every particle when S is large):
 // the same log-likelihood with the pivots of eta_bar I + D G D kept to ~44 bits,
-// so that nearly coinciding columns lose nothing.  One block of IB_T threads per
+// so that nearly coinciding columns lose nothing.  One block per
 // particle; the lower triangle of A (S <= 64) lives in registers, distributed as
-// row pairs (rp, 63 - rp) x column groups c = 4q + cg, so that every thread holds
-// about S(S+1)/256 entries and every row's scaled column entry is formed by four
-// threads only.
+// row pairs (rp, 63 - rp) x column groups c = NCG q + cg (32 NCG threads), so that
+// every thread holds about S(S+1)/(64 NCG) entries and every row's scaled column
+// entry is formed by NCG threads only.
 //  - Gram: G'_ab = (sum_f conj(b'_af) b'_bf)(sum_y ..)(sum_m ..) of the unit-modulus
 //    factors, each sum exact to ~2^-40 (products split on a fixed 2^-16 grid,
 //    remainders by FMA); A_ab = A_a d_a A_b d_b G'_ab + eta_bar delta_ab in float-float.
@@ -431,8 +431,8 @@ __global__ void k_iota(DevGeom G, DevParams Pm, DevState D, int S, const float* 
 //    of column k+1 publish it (and its pivot with the reciprocal) for step k+1.
 //  - Forward/back solves with the FP32 parts of L, residual in FP32 with FP64 sums
 //    (both enter the variational form only at second order).
-constexpr int IB_T = 128;
 constexpr int IB_SMAX = 64;
+constexpr int IOTA_BLK_NCG = 8;   // column groups: 256 threads, 12 register slots per thread
 
 __device__ inline cff fx_dotc(const float2* x, const float2* y, int n) {
     // sum_k conj(x_k) y_k for |x_k|, |y_k| <= 1 + O(eps), n <= 127: fmaf(a, b, M) - M
@@ -483,7 +483,45 @@ __device__ inline ff ff_recip(ff x) {
     return o;
 }
 
-// shared memory of k_iota_blk (bytes): colbuf [2][64] cff, pivbuf [2][2] ff, red [8]
+// One trailing entry (i, c) of the factorisation, held as an exact multiple of a
+// per-entry grid (h) plus an FP32 remainder (l).  With 2^E >= 4 sqrt(A_ii A_cc),
+// every partial Schur complement and every product l_ik conj(l_ck) is below 2^(E-2)
+// in modulus (Cauchy-Schwarz for the positive definite A), so fmaf(x, y, M) - M
+// (M = 1.5 * 2^E) rounds a product onto the multiples of 2^(E-23), the grid parts
+// subtract exactly, and the remainders (exact to 2^(E-48) by FMA) collect in l.
+// The row factor enters in float-float, the column factor rounded to FP32: the log
+// determinant then stays within ~1e-5 of exact on 64 near-collinear columns.
+struct gent { float hr, lr, hi, li, M; };
+__device__ inline gent gent_make(const cff& a, float bound) {
+    int e;
+    frexpf(4.0f * bound, &e);   // 2^e > 4 bound
+    gent g;
+    g.M = ldexpf(1.5f, e);
+    g.hr = __fsub_rn(__fadd_rn(a.re.hi, g.M), g.M);
+    g.lr = __fadd_rn(__fsub_rn(a.re.hi, g.hr), a.re.lo);
+    g.hi = __fsub_rn(__fadd_rn(a.im.hi, g.M), g.M);
+    g.li = __fadd_rn(__fsub_rn(a.im.hi, g.hi), a.im.lo);
+    return g;
+}
+__device__ inline void grid_sub(float& h, float& l, ff x, float y, float M) {   // h + l -= x y
+    const float ph = __fsub_rn(fmaf(x.hi, y, M), M);
+    h = __fsub_rn(h, ph);
+    l = __fsub_rn(l, fmaf(x.lo, y, fmaf(x.hi, y, -ph)));
+}
+__device__ inline void gent_sub_mulc(gent& g, const cff& x, float2 a) {   // A_ic -= x conj(a)
+    grid_sub(g.hr, g.lr, x.re, a.x, g.M);
+    grid_sub(g.hr, g.lr, x.im, a.y, g.M);
+    grid_sub(g.hi, g.li, x.im, a.x, g.M);
+    grid_sub(g.hi, g.li, ff_neg(x.re), a.y, g.M);
+}
+__device__ inline cff gent_value(const gent& g) {
+    cff v;
+    two_sum(g.hr, g.lr, v.re.hi, v.re.lo);
+    two_sum(g.hi, g.li, v.im.hi, v.im.lo);
+    return v;
+}
+
+// shared memory of k_iota_blk (bytes): colbuf [2][64] cff, colh [2][64] float2, pivbuf [2][2] ff, red [16]
 // double, A packed lower [S(S+1)/2] cff, then float2 z [Nz], factors [S][nfac], cm [S], g [S], L packed [S(S+1)/2]
 // (also the partial sums g [S][Nf] before the Gram), then float amplitude [S],
 // A d [S], d [S]
@@ -492,18 +530,22 @@ __host__ __device__ inline size_t iota_blk_lsize(int S, int Nf) {
     return a > b ? a : b;
 }
 __host__ __device__ inline size_t iota_blk_smem(int S, int nfac, int Nf, int Nz) {
-    return 2 * IB_SMAX * 16 + 4 * 8 + 8 * 8 + (size_t)S * (S + 1) / 2 * 16 +
+    return 2 * IB_SMAX * 16 + 2 * IB_SMAX * 8 + 4 * 8 + 16 * 8 + (size_t)S * (S + 1) / 2 * 16 +
            ((size_t)Nz + (size_t)S * nfac + 2 * (size_t)S + iota_blk_lsize(S, Nf)) * 8 + 3 * (size_t)S * 4;
 }
 
-__global__ void __launch_bounds__(IB_T, 3) k_iota_blk(DevGeom G, DevParams Pm, DevState D, int S, const float* z, int all) {
+template <int NCG>
+__global__ void __launch_bounds__(32 * NCG, (NCG == 4 ? 3 : 2)) k_iota_blk(DevGeom G, DevParams Pm, DevState D, int S, const float* z, int all) {
+    constexpr int IB_T = 32 * NCG;
+    constexpr int QA = 32 / NCG, QB = 64 / NCG;   // register slots of rows ra (< 32) and rb (>= 32)
     extern __shared__ float4 smb[];
-    cff* colbuf = reinterpret_cast<cff*>(smb);                    // [2][IB_SMAX]
-    ff* pivbuf = reinterpret_cast<ff*>(colbuf + 2 * IB_SMAX);     // [2][piv, 1/piv]
-    double* red = reinterpret_cast<double*>(pivbuf + 4);          // [8]
+    cff* colbuf = reinterpret_cast<cff*>(smb);                    // [2][IB_SMAX] published column (row side)
+    float2* colh = reinterpret_cast<float2*>(colbuf + 2 * IB_SMAX);   // [2][IB_SMAX] same, rounded (column side)
+    ff* pivbuf = reinterpret_cast<ff*>(colh + 2 * IB_SMAX);       // [2][piv, 1/piv]
+    double* red = reinterpret_cast<double*>(pivbuf + 4);          // [16]: yy, then per-warp |r|^2 at 8 + warp
     const int P = Pm.P, J = G.J, Nz = G.Nz, Nm = G.My * G.Mz, Nf = G.Nf;
     const int nfac = Nf + G.My + G.Mz;
-    cff* Apk = reinterpret_cast<cff*>(red + 8);                    // [S(S+1)/2] float-float A
+    cff* Apk = reinterpret_cast<cff*>(red + 16);                   // [S(S+1)/2] float-float A
     float2* zs = reinterpret_cast<float2*>(Apk + (size_t)S * (S + 1) / 2);   // [Nz]
     float2* fac = zs + Nz;                                        // [S][nfac]: b', a_y, a_z
     float2* cmS = fac + (size_t)S * nfac;                         // [S] pi mu, then A (pi mu + d y)
@@ -514,8 +556,8 @@ __global__ void __launch_bounds__(IB_T, 3) k_iota_blk(DevGeom G, DevParams Pm, D
     float* adS = amp + S;                                         // [S] A d
     float* dS = adS + S;                                          // [S] d
     const int tid = threadIdx.x, lane = tid & 31, wid = tid >> 5;
-    const int cg = tid & 3;
-    const int rp = (wid << 3) + (lane >> 2);
+    const int cg = lane % NCG;
+    const int rp = wid * (32 / NCG) + lane / NCG;
     const int ra = rp, rb = IB_SMAX - 1 - rp;
     const float* phi = D.phi[D.cur];
     __shared__ double lg_eb[J_MAX], inv_eb[J_MAX];
@@ -582,21 +624,25 @@ __global__ void __launch_bounds__(IB_T, 3) k_iota_blk(DevGeom G, DevParams Pm, D
                 cff v{ff_mul(gu.re, sc), ff_mul(gu.im, sc)};
                 if (a == b) { v.re = ff_add(v.re, ebff); v.im = ff{0.f, 0.f}; }
                 Apk[t] = v;
-                if (b == 0) colbuf[a] = v;
+                if (b == 0) { colbuf[a] = v; colh[a] = make_float2(v.re.hi, v.im.hi); }
                 if (t == 0) { pivbuf[0] = v.re; pivbuf[1] = ff_recip(v.re); }
             }
             __syncthreads();
             // this thread's slots (rows ra: q < 8, rb: q < 16) into registers
-            cff Ar[8], Br[16];
-            #pragma unroll
-            for (int q = 0; q < 8; ++q) {
-                const int c = 4 * q + cg;
-                if (c <= ra && ra < S) Ar[q] = Apk[tri(ra, c)];
-            }
-            #pragma unroll
-            for (int q = 0; q < 16; ++q) {
-                const int c = 4 * q + cg;
-                if (c <= rb && rb < S) Br[q] = Apk[tri(rb, c)];
+            gent Ar[QA], Br[QB];
+            {
+                const float sa = (ra < S) ? sqrtf(Apk[tri(ra, ra)].re.hi) : 0.f;
+                const float sb = (rb < S) ? sqrtf(Apk[tri(rb, rb)].re.hi) : 0.f;
+                #pragma unroll
+                for (int q = 0; q < QA; ++q) {
+                    const int c = NCG * q + cg;
+                    if (c <= ra && ra < S) Ar[q] = gent_make(Apk[tri(ra, c)], sa * sqrtf(Apk[tri(c, c)].re.hi));
+                }
+                #pragma unroll
+                for (int q = 0; q < QB; ++q) {
+                    const int c = NCG * q + cg;
+                    if (c <= rb && rb < S) Br[q] = gent_make(Apk[tri(rb, c)], sb * sqrtf(Apk[tri(c, c)].re.hi));
+                }
             }
             // rhs_a = d_a (g_a - sum_b G_ab pi_b mu_b), FP32
             float2 rhs = make_float2(0.f, 0.f);
@@ -612,12 +658,15 @@ __global__ void __launch_bounds__(IB_T, 3) k_iota_blk(DevGeom G, DevParams Pm, D
             }
             __syncthreads();
             if (tid < S) gS[tid] = rhs;
-            // float-float Cholesky; log det from the product of the pivots (exponent kept apart)
+            // Cholesky with exactly accumulated trailing entries; log det from the
+            // float-float product of the pivots (exponent kept apart)
             ffexp det{ff{1.f, 0.f}, 0};
             for (int k = 0; k < S; ++k) {
                 const int cur = k & 1, nxt = cur ^ 1;
                 const cff* col = colbuf + cur * IB_SMAX;
+                const float2* colr = colh + cur * IB_SMAX;
                 cff* ncol = colbuf + nxt * IB_SMAX;
+                float2* ncolr = colh + nxt * IB_SMAX;
                 ff piv = pivbuf[2 * cur];
                 ff inv = pivbuf[2 * cur + 1];
                 if (!(piv.hi > 0.f)) { piv = ff{1e-30f, 0.f}; inv = ff{1e30f, 0.f}; }
@@ -638,25 +687,27 @@ __global__ void __launch_bounds__(IB_T, 3) k_iota_blk(DevGeom G, DevParams Pm, D
                 if (ra > k && ra < S) { const cff v = col[ra]; la = cff{ff_mul(v.re, inv), ff_mul(v.im, inv)}; }
                 if (rb > k && rb < S) { const cff v = col[rb]; lb = cff{ff_mul(v.re, inv), ff_mul(v.im, inv)}; }
                 #pragma unroll
-                for (int q = 0; q < 8; ++q) {
-                    const int c = 4 * q + cg;
+                for (int q = 0; q < QA; ++q) {
+                    const int c = NCG * q + cg;
                     if (c > k && c <= ra && ra < S) {
-                        cff_sub_mulc(Ar[q], la, col[c]);
+                        gent_sub_mulc(Ar[q], la, colr[c]);
                         if (c == k + 1) {
-                            const cff v = cff_norm(Ar[q]);
+                            const cff v = gent_value(Ar[q]);
                             ncol[ra] = v;
+                            ncolr[ra] = make_float2(v.re.hi, v.im.hi);
                             if (ra == c) { pivbuf[2 * nxt] = v.re; pivbuf[2 * nxt + 1] = ff_recip(v.re); }
                         }
                     }
                 }
                 #pragma unroll
-                for (int q = 0; q < 16; ++q) {
-                    const int c = 4 * q + cg;
+                for (int q = 0; q < QB; ++q) {
+                    const int c = NCG * q + cg;
                     if (c > k && c <= rb && rb < S) {
-                        cff_sub_mulc(Br[q], lb, col[c]);
+                        gent_sub_mulc(Br[q], lb, colr[c]);
                         if (c == k + 1) {
-                            const cff v = cff_norm(Br[q]);
+                            const cff v = gent_value(Br[q]);
                             ncol[rb] = v;
+                            ncolr[rb] = make_float2(v.re.hi, v.im.hi);
                             if (rb == c) { pivbuf[2 * nxt] = v.re; pivbuf[2 * nxt + 1] = ff_recip(v.re); }
                         }
                     }
@@ -714,10 +765,11 @@ __global__ void __launch_bounds__(IB_T, 3) k_iota_blk(DevGeom G, DevParams Pm, D
                 ff_acc_sq(rr, acc);
             }
             rr = warp_sum_ff(rr);
-            if (lane == 0) red[4 + wid] = ff_to_d(rr);
+            if (lane == 0) red[8 + wid] = ff_to_d(rr);
             __syncthreads();
             if (tid == 0) {
-                const double rrs = red[4] + red[5] + red[6] + red[7];
+                double rrs = 0.0;
+                for (int w2 = 0; w2 < IB_T / 32; ++w2) rrs += red[8 + w2];
                 const double lg = lg_eb[j];
                 total += -(rrs * inv_eb[j] + red[0]) - (ffexp_log(det) - S * lg) - Nz * (LOG_PI + lg);
             }
@@ -800,10 +852,11 @@ void launch_iota_repair(const DevGeom& G, const DevParams& Pm, const DevState& D
     const size_t smem = iota_blk_smem(S, nfac, G.Nf, G.Nz);
     const int all = S >= IOTA_FF_ALL_S ? 1 : 0;
     if (all) cudaMemsetAsync(D.flags, 0, sizeof(int), st);
-    cudaFuncSetAttribute(k_iota_blk, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
-    const int wave = 3 * 152;
+    constexpr int NCG = IOTA_BLK_NCG;
+    cudaFuncSetAttribute(k_iota_blk<NCG>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    const int wave = (NCG == 4 ? 3 : 2) * 152;
     const int blocks = all ? std::min(Pm.P, 16 * wave) : wave;
-    k_iota_blk<<<blocks, IB_T, smem, st>>>(G, Pm, D, S, z, all);
+    k_iota_blk<NCG><<<blocks, 32 * NCG, smem, st>>>(G, Pm, D, S, z, all);
 }
 
 void launch_nu(const DevGeom& G, const DevParams& Pm, const DevState& D, int S, cudaStream_t st) {

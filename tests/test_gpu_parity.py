@@ -57,18 +57,23 @@ CASES = [
     (dict(J=4, Nf=10, My=4, Mz=4), 4, 5, 700, 12, 0.003),         # paper shape, ragged P
     (dict(J=2, Nf=6, My=3, Mz=2), 3, 4, 333, 13, 0.01),           # odd sizes, Nz = 36
     (dict(J=3, Nf=10, My=4, Mz=4), 10, 12, 300, 14, 0.004),       # S bucket 16
+    (dict(J=4, Nf=10, My=4, Mz=4), 63, 64, 256, 15, 0.005),       # 64 PFs: float-float likelihoods for all particles
 ]
+
+
+def s_max_for(S):
+    return 16 if S <= 16 else 64
 
 
 @pytest.mark.parametrize("case", CASES)
 def test_predict_parity(case):
     geom_kw, K, S, P, seed, pos = case
     g, prm, scn, eta, z, st = setup_case(geom_kw, K, S, P, seed, pos)
-    f = bp.Filter(g, prm, P=P, S_max=16, seed=seed)
+    f = bp.Filter(g, prm, P=P, S_max=s_max_for(S), seed=seed)
     f.set_state(st)
     f.predict()
     gp = f.get_predicted()
-    op = model.predict(st, prm, g.J, seed=seed, S_max=16)
+    op = model.predict(st, prm, g.J, seed=seed, S_max=s_max_for(S))
     assert gp["S"] == op.S
     scale = np.maximum(np.abs(op.x.astype(float)), 1.0)
     assert np.max(np.abs(gp["x"] - op.x) / scale) < 1e-6
@@ -86,8 +91,8 @@ def test_predict_parity(case):
 def test_update_parity(case):
     geom_kw, K, S, P, seed, pos = case
     g, prm, scn, eta, z, st = setup_case(geom_kw, K, S, P, seed, pos)
-    pred = model.predict(st, prm, g.J, seed=seed, S_max=16)
-    f = gpu_update_from(pred, g, prm, z, P, 16, seed)
+    pred = model.predict(st, prm, g.J, seed=seed, S_max=s_max_for(S))
+    f = gpu_update_from(pred, g, prm, z, P, s_max_for(S), seed)
     msg = messages_woodbury.update_messages(pred, prm, g, z)
     bel = beliefs.beliefs(pred, msg)
     est = beliefs.estimate(pred, bel, prm)
