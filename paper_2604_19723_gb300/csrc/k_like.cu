@@ -524,14 +524,14 @@ __device__ inline cff gent_value(const gent& g) {
 // shared memory of k_iota_blk (bytes): colbuf [2][64] cff, colh [2][64] float2, pivbuf [2][2] ff, red [16]
 // double, A packed lower [S(S+1)/2] cff, then float2 z [Nz], factors [S][nfac], cm [S], g [S], L packed [S(S+1)/2]
 // (also the partial sums g [S][Nf] before the Gram), then float amplitude [S],
-// A d [S], d [S]
+// A d [S], d [S], 1/L_kk [64]
 __host__ __device__ inline size_t iota_blk_lsize(int S, int Nf) {
     const size_t a = (size_t)S * (S + 1) / 2, b = (size_t)S * Nf;
     return a > b ? a : b;
 }
 __host__ __device__ inline size_t iota_blk_smem(int S, int nfac, int Nf, int Nz) {
     return 2 * IB_SMAX * 16 + 2 * IB_SMAX * 8 + 4 * 8 + 16 * 8 + (size_t)S * (S + 1) / 2 * 16 +
-           ((size_t)Nz + (size_t)S * nfac + 2 * (size_t)S + iota_blk_lsize(S, Nf)) * 8 + 3 * (size_t)S * 4;
+           ((size_t)Nz + (size_t)S * nfac + 2 * (size_t)S + iota_blk_lsize(S, Nf)) * 8 + 3 * (size_t)S * 4 + IB_SMAX * 4;
 }
 
 template <int NCG>
@@ -555,6 +555,7 @@ __global__ void __launch_bounds__(32 * NCG, (NCG == 4 ? 3 : 2)) k_iota_blk(DevGe
     float* amp = reinterpret_cast<float*>(Lsm + iota_blk_lsize(S, Nf));     // [S]
     float* adS = amp + S;                                         // [S] A d
     float* dS = adS + S;                                          // [S] d
+    float* ild = dS + S;                                          // [IB_SMAX] 1 / L_kk
     const int tid = threadIdx.x, lane = tid & 31, wid = tid >> 5;
     const int cg = lane % NCG;
     const int rp = wid * (32 / NCG) + lane / NCG;
@@ -657,7 +658,6 @@ __global__ void __launch_bounds__(32 * NCG, (NCG == 4 ? 3 : 2)) k_iota_blk(DevGe
                 rhs = make_float2(dS[a] * acc.x, dS[a] * acc.y);
             }
             __syncthreads();
-            if (tid < S) gS[tid] = rhs;
             // Cholesky with exactly accumulated trailing entries; log det from the
             // float-float product of the pivots (exponent kept apart)
             ffexp det{ff{1.f, 0.f}, 0};
@@ -671,15 +671,25 @@ __global__ void __launch_bounds__(32 * NCG, (NCG == 4 ? 3 : 2)) k_iota_blk(DevGe
                 ff inv = pivbuf[2 * cur + 1];
                 if (!(piv.hi > 0.f)) { piv = ff{1e-30f, 0.f}; inv = ff{1e30f, 0.f}; }
                 const float lkk = sqrtf(piv.hi + piv.lo);
+                const float il = 1.0f / lkk;
                 if (tid == 0) {
                     ffexp_mul(det, piv);
                     Lsm[tri(k, k)] = make_float2(lkk, 0.f);
+                    ild[k] = il;
+                }
+                // forward substitution L u = rhs, one column behind the factorisation:
+                // row i takes column k-1 (published last step), then row k yields u_k
+                if (tid < S && tid >= k) {
+                    if (k > 0) {
+                        const float2 u = cmul(Lsm[tri(tid, k - 1)], gS[k - 1]);
+                        rhs.x -= u.x; rhs.y -= u.y;
+                    }
+                    if (tid == k) gS[k] = make_float2(rhs.x * il, rhs.y * il);
                 }
                 {
                     const int i = k + 1 + tid;
                     if (i < S) {
                         const cff v = col[i];
-                        const float il = 1.0f / lkk;
                         Lsm[tri(i, k)] = make_float2((v.re.hi + v.re.lo) * il, (v.im.hi + v.im.lo) * il);
                     }
                 }
@@ -714,27 +724,22 @@ __global__ void __launch_bounds__(32 * NCG, (NCG == 4 ? 3 : 2)) k_iota_blk(DevGe
                 }
                 __syncthreads();
             }
-            // solves L u = rhs, L^H y = u (warp 0; lane owns rows lane and lane + 32)
+            // back substitution L^H y = u (warp 0; lane owns rows lane and lane + 32)
             if (wid == 0) {
                 float2 r0 = (lane < S) ? gS[lane] : make_float2(0.f, 0.f);
                 float2 r1 = (lane + 32 < S) ? gS[lane + 32] : make_float2(0.f, 0.f);
-                for (int k = 0; k < S; ++k) {
-                    const float2 own = (k < 32) ? r0 : r1;
-                    const float dkk = Lsm[tri(k, k)].x;
-                    float2 uk = make_float2(__shfl_sync(0xffffffffu, own.x, k & 31) / dkk,
-                                            __shfl_sync(0xffffffffu, own.y, k & 31) / dkk);
-                    if (lane == (k & 31)) { if (k < 32) r0 = uk; else r1 = uk; }
-                    if (lane > k && lane < S) { const float2 u = cmul(Lsm[tri(lane, k)], uk); r0.x -= u.x; r0.y -= u.y; }
-                    if (lane + 32 > k && lane + 32 < S) { const float2 u = cmul(Lsm[tri(lane + 32, k)], uk); r1.x -= u.x; r1.y -= u.y; }
-                }
+                const float i0 = (lane < S) ? ild[lane] : 0.f, i1 = (lane + 32 < S) ? ild[lane + 32] : 0.f;
                 for (int k = S - 1; k >= 0; --k) {
-                    const float2 own = (k < 32) ? r0 : r1;
-                    const float dkk = Lsm[tri(k, k)].x;
-                    float2 yk = make_float2(__shfl_sync(0xffffffffu, own.x, k & 31) / dkk,
-                                            __shfl_sync(0xffffffffu, own.y, k & 31) / dkk);
-                    if (lane == (k & 31)) { if (k < 32) r0 = yk; else r1 = yk; }
-                    if (lane < k) { const float2 u = cmulc(Lsm[tri(k, lane)], yk); r0.x -= u.x; r0.y -= u.y; }
-                    if (lane + 32 < k) { const float2 u = cmulc(Lsm[tri(k, lane + 32)], yk); r1.x -= u.x; r1.y -= u.y; }
+                    const float2 lr0 = (lane < k) ? Lsm[tri(k, lane)] : make_float2(0.f, 0.f);
+                    const float2 lr1 = (lane + 32 < k) ? Lsm[tri(k, lane + 32)] : make_float2(0.f, 0.f);
+                    const bool hi_row = k >= 32;
+                    const float2 own = hi_row ? r1 : r0;
+                    const float io = hi_row ? i1 : i0;
+                    const float2 yk = make_float2(__shfl_sync(0xffffffffu, own.x * io, k & 31),
+                                                  __shfl_sync(0xffffffffu, own.y * io, k & 31));
+                    if (lane == (k & 31)) { if (hi_row) r1 = yk; else r0 = yk; }
+                    if (lane < k) { const float2 u = cmulc(lr0, yk); r0.x -= u.x; r0.y -= u.y; }
+                    if (lane + 32 < k) { const float2 u = cmulc(lr1, yk); r1.x -= u.x; r1.y -= u.y; }
                 }
                 ff yy{0.f, 0.f};
                 if (lane < S) {
