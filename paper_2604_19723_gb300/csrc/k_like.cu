@@ -522,7 +522,7 @@ __device__ inline cff gent_value(const gent& g) {
 }
 
 // shared memory of k_iota_blk (bytes): colbuf [2][64] cff, colh [2][64] float2, pivbuf [2][2] ff, red [16]
-// double, A packed lower [S(S+1)/2] cff, then float2 z [Nz], factors [S][nfac], cm [S], g [S], L packed [S(S+1)/2]
+// double, A packed lower [S(S+1)/2] cff, then float2 z [Nz], factors [S][nfac | 1], cm [S], g [S], L packed [S(S+1)/2]
 // (also the partial sums g [S][Nf] before the Gram), then float amplitude [S],
 // A d [S], d [S], 1/L_kk [64]
 __host__ __device__ inline size_t iota_blk_lsize(int S, int Nf) {
@@ -531,7 +531,7 @@ __host__ __device__ inline size_t iota_blk_lsize(int S, int Nf) {
 }
 __host__ __device__ inline size_t iota_blk_smem(int S, int nfac, int Nf, int Nz) {
     return 2 * IB_SMAX * 16 + 2 * IB_SMAX * 8 + 4 * 8 + 16 * 8 + (size_t)S * (S + 1) / 2 * 16 +
-           ((size_t)Nz + (size_t)S * nfac + 2 * (size_t)S + iota_blk_lsize(S, Nf)) * 8 + 3 * (size_t)S * 4 + IB_SMAX * 4;
+           ((size_t)Nz + (size_t)S * (nfac | 1) + 2 * (size_t)S + iota_blk_lsize(S, Nf)) * 8 + 3 * (size_t)S * 4 + IB_SMAX * 4;
 }
 
 template <int NCG>
@@ -544,7 +544,7 @@ __global__ void __launch_bounds__(32 * NCG, (NCG == 4 ? 3 : 2)) k_iota_blk(DevGe
     ff* pivbuf = reinterpret_cast<ff*>(colh + 2 * IB_SMAX);       // [2][piv, 1/piv]
     double* red = reinterpret_cast<double*>(pivbuf + 4);          // [16]: yy, then per-warp |r|^2 at 8 + warp
     const int P = Pm.P, J = G.J, Nz = G.Nz, Nm = G.My * G.Mz, Nf = G.Nf;
-    const int nfac = Nf + G.My + G.Mz;
+    const int nfac = (Nf + G.My + G.Mz) | 1;   // factor row stride, odd in float2 against bank conflicts
     cff* Apk = reinterpret_cast<cff*>(red + 16);                   // [S(S+1)/2] float-float A
     float2* zs = reinterpret_cast<float2*>(Apk + (size_t)S * (S + 1) / 2);   // [Nz]
     float2* fac = zs + Nz;                                        // [S][nfac]: b', a_y, a_z
@@ -588,7 +588,7 @@ __global__ void __launch_bounds__(32 * NCG, (NCG == 4 ? 3 : 2)) k_iota_blk(DevGe
             __syncthreads();
             // g_s = psi_s^H z: tasks (s, f) contract over the antennas
             for (int t = tid; t < S * Nf; t += IB_T) {
-                const int s = t / Nf, f = t - s * Nf;
+                const int f = t / S, s = t - f * S;   // lanes over s: z_f broadcast
                 const float2* fs = fac + (size_t)s * nfac;
                 float2 accy = make_float2(0.f, 0.f);
                 for (int y = 0; y < G.My; ++y) {
@@ -600,7 +600,7 @@ __global__ void __launch_bounds__(32 * NCG, (NCG == 4 ? 3 : 2)) k_iota_blk(DevGe
                     const float2 u = cmulc(fs[Nf + y], accm);
                     accy.x += u.x; accy.y += u.y;
                 }
-                gpart[t] = cmulc(fs[f], accy);
+                gpart[s * Nf + f] = cmulc(fs[f], accy);
             }
             __syncthreads();
             for (int s = tid; s < S; s += IB_T) {
