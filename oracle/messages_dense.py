@@ -82,6 +82,59 @@ def message_table(pred, params, psi) -> Table:
     return Table(W=W, pi=pi, m=m, mw=mw, mu3=mu3, mu4=mu4, eta_bar=eta_bar)
 
 
+def table_sums(x, phi, w_beta, pi, W, geom):
+    """The particle sums of `message_table` over one set of particles (S-V):
+    sum_p w_beta^p sqrt(gamma_s^p + |mu_s^p|^2 pddot_s^(j)) psi_s^(j,p),
+    sum_p w_beta^p sqrt(gamma_s^p + |mu_s^p|^2 pdot_s) psi_s^(j,p) and
+    sum_p w_beta^p mu_s^p psi_s^(j,p), each (S, J, Nz).  pi and W are those of the
+    whole particle set.  Sums over disjoint particle sets add up to the full sums."""
+    S, J = phi.shape[0], pi.shape[1]
+    pos = x[:3].astype(np.float64).T
+    gam = phi[:, 3].astype(np.float64)
+    mu = phi[:, 4].astype(np.float64) + 1j * phi[:, 5].astype(np.float64)
+    sa = np.zeros((S, J, geom.Nz), complex)
+    sb = np.zeros((S, J, geom.Nz), complex)
+    sc = np.zeros((S, J, geom.Nz), complex)
+    for s in range(S):
+        sfv = phi[s, :3].astype(np.float64).T
+        for j in range(J):
+            ps = geometry.steering(geom, j, pos, sfv, los=(s == 0))
+            sa[s, j] = (w_beta * np.sqrt(gam[s] + np.abs(mu[s]) ** 2 * (1.0 - pi[s, j]))) @ ps
+            sb[s, j] = (w_beta * np.sqrt(gam[s] + np.abs(mu[s]) ** 2 * (1.0 - W[s]))) @ ps
+            sc[s, j] = (w_beta * mu[s]) @ ps
+    return sa, sb, sc
+
+
+def _table_sums_task(args):
+    return table_sums(*args)
+
+
+def message_table_streamed(pred, params, geom, chunk: int = 4096, pool=None) -> Table:
+    """`message_table` for particle sets too large to hold every steering vector at
+    once: the same sums, taken over particle chunks (optionally in a process pool)
+    and added, then scaled as in `message_table`."""
+    S, J = pred.S, pred.zeta.shape[1]
+    P = pred.x.shape[1]
+    W = pred.w_alpha.sum(axis=1)
+    zeta = pred.zeta
+    pi = zeta * W[:, None]
+    tasks = [(pred.x[:, sl], pred.phi[:, :, sl], pred.w_beta[sl], pi, W, geom) for sl in _chunks(P, chunk)]
+    parts = (pool.map(_table_sums_task, tasks) if pool is not None else [_table_sums_task(t) for t in tasks])
+    sa = sum(p[0] for p in parts)
+    sb = sum(p[1] for p in parts)
+    sc = sum(p[2] for p in parts)
+    if params.mvec_scaling == 0:
+        cm, cw = W[:, None] * zeta, np.broadcast_to(W[:, None], (S, J))
+    else:
+        cm, cw = np.sqrt(W[:, None] * zeta), np.broadcast_to(np.sqrt(W)[:, None], (S, J))
+    m = cm[:, :, None] * sa
+    mw = cw[:, :, None] * sb
+    mu4 = W[:, None, None] * sc
+    mu3 = zeta[:, :, None] * mu4
+    eta_bar = np.sum(pred.w_xi * pred.eta.astype(np.float64), axis=1)
+    return Table(W=W, pi=pi, m=m, mw=mw, mu3=mu3, mu4=mu4, eta_bar=eta_bar)
+
+
 def log_cn(z: np.ndarray, mean: np.ndarray, C: np.ndarray) -> np.ndarray:
     """log CN(z; mean, C) for batches: mean (..., Nz), C (..., Nz, Nz)."""
     Nz = z.shape[-1]

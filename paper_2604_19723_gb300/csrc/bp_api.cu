@@ -98,8 +98,16 @@ static void fill_geom(DevGeom& G, const bp_geometry* g) {
         G.fc_hi[f] = (float)v;
         G.fc_lo[f] = (float)(v - (double)G.fc_hi[f]);
     }
-    for (int y = 0; y < g->My; ++y) G.py_l[y] = (float)(G.py[y] / G.lam);
-    for (int m = 0; m < g->Mz; ++m) G.pz_l[m] = (float)(G.pz[m] / G.lam);
+    for (int y = 0; y < g->My; ++y) {
+        const double v = G.py[y] / G.lam;
+        G.py_l[y] = (float)v;
+        G.py_lo[y] = (float)(v - (double)G.py_l[y]);
+    }
+    for (int m = 0; m < g->Mz; ++m) {
+        const double v = G.pz[m] / G.lam;
+        G.pz_l[m] = (float)v;
+        G.pz_lo[m] = (float)(v - (double)G.pz_l[m]);
+    }
     G.amp_c = (float)(G.lam / (4.0 * M_PI));
 }
 
@@ -162,12 +170,14 @@ bp_status bp_init(const bp_geometry* geom, const bp_params* prm, int P, int S_ma
     ok &= dalloc(h, &D.lw_eta, (size_t)J * PP);
     ok &= dalloc(h, &D.llr_w, (size_t)S_max * J);
     ok &= dalloc(h, &D.geo, (size_t)S_max * J * PP);
+    ok &= dalloc(h, &D.geo_lo, (size_t)S_max * J * PP);
     ok &= dalloc(h, &D.flags, PP + 1);
     ok &= dalloc(h, &D.tab, (size_t)4 * S_max * J * Nz * 2);
     ok &= dalloc(h, &D.tab_part, (size_t)h->nsplit_max * 3 * S_max * J * Nz * 2);
     ok &= dalloc(h, &D.W, (size_t)S_max);
     ok &= dalloc(h, &D.eta_bar, (size_t)J);
     ok &= dalloc(h, &D.kV, (size_t)S_max * J * Nz * SCA);
+    ok &= dalloc(h, &D.kr0l, (size_t)S_max * J * Nz);
     ok &= dalloc(h, &D.kR, (size_t)S_max * J * SCA * SCA);
     ok &= dalloc(h, &D.ky0, (size_t)S_max * J * SCA);
     ok &= dalloc(h, &D.kJ0, (size_t)S_max * J);

@@ -27,7 +27,8 @@ struct DevGeom {
     // float-float constants for phases in cycles: 1/lambda, f_k/c; FP32 p/lambda
     float inv_lam_hi, inv_lam_lo;
     float fc_hi[NF_MAX], fc_lo[NF_MAX];
-    float py_l[MY_MAX], pz_l[MZ_MAX];
+    float py_l[MY_MAX], pz_l[MZ_MAX];     // p_y / lambda, p_z / lambda (float-float with *_lo)
+    float py_lo[MY_MAX], pz_lo[MZ_MAX];
     float amp_c;             // lambda / (4 pi)
 };
 
@@ -161,8 +162,25 @@ __device__ inline float ff_frac_mul(float ah, float al, float bh, float bl) {
     return (p - n) + t;
 }
 
+// The same fraction as an unevaluated pair hi + lo (hi = p - rint(p) exactly, lo the
+// low-order terms), for a phase kept beyond FP32 rounding.
+__device__ inline void ff_frac_mul2(float ah, float al, float bh, float bl, float& hi, float& lo) {
+    const float p = __fmul_rn(ah, bh);
+    const float e = fmaf(ah, bh, -p);
+    hi = __fsub_rn(p, rintf(p));
+    lo = fmaf(ah, bl, fmaf(al, bh, e));
+}
+// (cos, sin) of pi (a + b) for |b| < 1e-4: sincospi of the leading part and the
+// first-order term of the small one (second order below 5e-8 relative)
+__device__ inline float2 cispi_ff(float a, float b) {
+    float sn, cs;
+    sincospif(a, &sn, &cs);
+    const float pb = 3.14159265358979f * b;
+    return make_float2(fmaf(-pb, sn, cs), fmaf(pb, cs, sn));
+}
+
 // Geometry record of one (particle, feature, PA): distance |r'| as a float-float
-// pair and the local direction cosines u_y, u_z (FP32).
+// pair and the local direction cosines u_y, u_z (float-float, low parts apart).
 struct GeoRec { float d_hi, d_lo, uy, uz; };
 
 // ------------------------------------------------------------------ complex / double-float helpers
@@ -305,7 +323,8 @@ struct DevState {
     double* lw_eta;   // J x P
     double* llr_w;    // S_max x J   log omega(1) - log omega(0)
     // message table (FP64) and derived per-(s,j) quantities
-    float4* geo;      // [S_max][J][P] GeoRec of the current prediction
+    float4* geo;      // [S_max][J][P] GeoRec of the current prediction: |r'| (hi, lo), u_y, u_z
+    float2* geo_lo;   // [S_max][J][P] low parts of u_y, u_z
     int* flags;       // [0] count of flagged particles, then their indices (iota repair)
     double* tab;      // [4][S_max][J][Nz] double2 : m, mw, mu3, mu4
     double* tab_part; // table partial sums [nsplit][3][S_max][J][Nz] double2
@@ -313,7 +332,8 @@ struct DevState {
     double* eta_bar;  // J
     double* sums_part;// partial sums for W / eta_bar
     // kappa stage outputs (per (s,j))
-    float2* kV;       // [S_max][J][Nz][S_cap]   whitened basis, column S_cap-1 = r0
+    float2* kV;       // [S_max][J][Nz][S_cap]   whitened basis, column S_cap-1 = r0 (FP32 part)
+    float2* kr0l;     // [S_max][J][Nz]          low part of r0 (r0 = FP32 part + low part)
     float2* kR;       // [S_max][J][S_cap*S_cap] upper Cholesky factor (FP32, padded identity)
     float2* ky0;      // [S_max][J][S_cap]       y0 = R^-1 V^H e0 / eta_bar
     double* kJ0;      // [S_max][J]              |r0|^2/eta_bar

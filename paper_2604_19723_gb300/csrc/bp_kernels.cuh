@@ -34,56 +34,53 @@ struct EstLayout {
 
 constexpr int RED_W = 29;   // per-block partial sums: S0, S1[6], S2[21] (upper, row-major), sum w^2
 
-// Steering-vector factors from a geometry record, FP32 only:
+// Steering-vector factors from a geometry record (g, gl), FP32 arithmetic:
 // psi = c (b kron a_y kron a_z), c = lambda/(4 pi d) e^{-i 2 pi d/lambda},
 // b_f = e^{-i 2 pi f_f d/c}, a_y = e^{i 2 pi p_y u_y/lambda}, a_z = e^{i 2 pi p_z u_z/lambda}
-// (eq. array-response, unit-modulus-array-response); phases reduced to cycles
-// with float-float products.
-__device__ inline float2 factors_from_geo(const DevGeom& G, float4 g, float2* b, float2* ay, float2* az, int stride) {
-    const float d = g.x + g.y;
-    const float A = G.amp_c / d;
-    float s, c;
-    sincospif(-2.0f * ff_frac_mul(g.x, g.y, G.inv_lam_hi, G.inv_lam_lo), &s, &c);
-    for (int f = 0; f < G.Nf; ++f) {
-        float sf, cf;
-        sincospif(-2.0f * ff_frac_mul(g.x, g.y, G.fc_hi[f], G.fc_lo[f]), &sf, &cf);
-        b[f * stride] = make_float2(cf, sf);
-    }
-    for (int y = 0; y < G.My; ++y) {
-        float sy, cy;
-        sincospif(2.0f * G.py_l[y] * g.z, &sy, &cy);
-        ay[y * stride] = make_float2(cy, sy);
+// (eq. array-response, unit-modulus-array-response).  Every phase is formed as a
+// float-float number of cycles (distance and direction cosines carry low parts) and
+// enters sincospi with its first-order low-part correction, so the factors are exact
+// to a few FP32 ulps; their products then decide the accuracy of psi.
+__device__ inline void array_factors(const DevGeom& G, float4 g, float2 gl, float2* ay, float2* az, int stride) {
+    for (int y = 0; y < G.My; ++y) {   // 2 p_y u_y / lambda half-cycles
+        const float p = __fmul_rn(G.py_l[y], g.z);
+        const float e = fmaf(G.py_l[y], gl.x, fmaf(G.py_lo[y], g.z, fmaf(G.py_l[y], g.z, -p)));
+        ay[y * stride] = cispi_ff(2.0f * p, 2.0f * e);
     }
     for (int m = 0; m < G.Mz; ++m) {
-        float sz, cz;
-        sincospif(2.0f * G.pz_l[m] * g.w, &sz, &cz);
-        az[m * stride] = make_float2(cz, sz);
+        const float p = __fmul_rn(G.pz_l[m], g.w);
+        const float e = fmaf(G.pz_l[m], gl.y, fmaf(G.pz_lo[m], g.w, fmaf(G.pz_l[m], g.w, -p)));
+        az[m * stride] = cispi_ff(2.0f * p, 2.0f * e);
     }
-    return make_float2(A * c, A * s);
+}
+__device__ inline float2 factors_from_geo(const DevGeom& G, float4 g, float2 gl, float2* b, float2* ay, float2* az, int stride) {
+    const float d = g.x + g.y;
+    const float A = G.amp_c / d;
+    float h, l;
+    ff_frac_mul2(g.x, g.y, G.inv_lam_hi, G.inv_lam_lo, h, l);
+    const float2 c = cispi_ff(-2.0f * h, -2.0f * l);
+    for (int f = 0; f < G.Nf; ++f) {
+        ff_frac_mul2(g.x, g.y, G.fc_hi[f], G.fc_lo[f], h, l);
+        b[f * stride] = cispi_ff(-2.0f * h, -2.0f * l);
+    }
+    array_factors(G, g, gl, ay, az, stride);
+    return make_float2(A * c.x, A * c.y);
 }
 
 // As factors_from_geo, with the carrier phase folded into the frequency factor:
-// psi = A (b' kron a_y kron a_z), b'_f = e^{-i 2 pi d (1/lambda + f_f/c)}, A = lambda/(4 pi d).
-// The two fractional cycle counts are added before one sincospi, so |b'_f| = 1
-// to FP32 rounding.  Returns A.
-__device__ inline float factors_from_geo_folded(const DevGeom& G, float4 g, float2* b, float2* ay, float2* az, int stride) {
+// psi = A (b' kron a_y kron a_z), b'_f = e^{-i 2 pi d (1/lambda + f_f/c)}, A = lambda/(4 pi d),
+// one sincospi per frequency on the summed cycle count.  Returns A.
+__device__ inline float factors_from_geo_folded(const DevGeom& G, float4 g, float2 gl, float2* b, float2* ay, float2* az, int stride) {
     const float d = g.x + g.y;
-    const float ph0 = ff_frac_mul(g.x, g.y, G.inv_lam_hi, G.inv_lam_lo);
+    float h0, l0;
+    ff_frac_mul2(g.x, g.y, G.inv_lam_hi, G.inv_lam_lo, h0, l0);
     for (int f = 0; f < G.Nf; ++f) {
-        float sf, cf;
-        sincospif(-2.0f * (ph0 + ff_frac_mul(g.x, g.y, G.fc_hi[f], G.fc_lo[f])), &sf, &cf);
-        b[f * stride] = make_float2(cf, sf);
+        float hf, lf, h, e;
+        ff_frac_mul2(g.x, g.y, G.fc_hi[f], G.fc_lo[f], hf, lf);
+        two_sum(h0, hf, h, e);
+        b[f * stride] = cispi_ff(-2.0f * h, -2.0f * (e + l0 + lf));
     }
-    for (int y = 0; y < G.My; ++y) {
-        float sy, cy;
-        sincospif(2.0f * G.py_l[y] * g.z, &sy, &cy);
-        ay[y * stride] = make_float2(cy, sy);
-    }
-    for (int m = 0; m < G.Mz; ++m) {
-        float sz, cz;
-        sincospif(2.0f * G.pz_l[m] * g.w, &sz, &cz);
-        az[m * stride] = make_float2(cz, sz);
-    }
+    array_factors(G, g, gl, ay, az, stride);
     return G.amp_c / d;
 }
 

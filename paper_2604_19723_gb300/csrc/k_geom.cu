@@ -20,7 +20,9 @@ __global__ void k_geom(DevGeom G, DevParams Pm, DevState D, int S) {
     const PathGeo pg = path_geo(G, j, x[p], x[P + p], x[2 * P + p], ph[p], ph[P + p], ph[2 * P + p], s == 0);
     const float dh = (float)pg.d;
     const float dl = (float)(pg.d - (double)dh);
-    D.geo[idx] = make_float4(dh, dl, (float)pg.uy, (float)pg.uz);
+    const float uyh = (float)pg.uy, uzh = (float)pg.uz;
+    D.geo[idx] = make_float4(dh, dl, uyh, uzh);
+    D.geo_lo[idx] = make_float2((float)(pg.uy - (double)uyh), (float)(pg.uz - (double)uzh));
 }
 
 void launch_geom(const DevGeom& G, const DevParams& Pm, const DevState& D, int S, cudaStream_t st) {

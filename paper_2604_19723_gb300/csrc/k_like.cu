@@ -45,19 +45,22 @@ __global__ void __launch_bounds__(256, (SC <= 16 ? 2 : 1)) k_kappa(DevGeom G, De
     float2* Rs = reinterpret_cast<float2*>(Vs + (size_t)Nz * NP);      // packed upper NC x NC
     float2* y0s = Rs + kappa_rpack<SC>();                              // [SC]
     float2* fac = y0s + SC;                                            // [nfac][KT]
+    float2* r0ls = fac + (size_t)(G.Nf + G.My + G.Mz) * KT;           // [fch * Nm] low part of r0
     const int tid = threadIdx.x;
     const int p = blockIdx.x * KT + tid;
     const bool act = p < P;
     const int pp = act ? p : 0;
     const float* ph = D.phi[D.cur] + (size_t)s * 6 * P;
     const float4* geo_s = D.geo + (size_t)s * J * P;
+    const float2* geol_s = D.geo_lo + (size_t)s * J * P;
     const float gmf = ph[3 * P + pp];
     const float mrf = ph[4 * P + pp], mif = ph[5 * P + pp];
     const double mr = mrf, mi = mif;
     double delta_sum = 0.0;
     for (int j = 0; j < J; ++j) {
         const float2* gV = D.kV + ((size_t)s * J + j) * Nz * SCA;
-        // rows of frequencies [f0, f0 + fch) -> Vs (called by all threads)
+        const float2* gr0l = D.kr0l + ((size_t)s * J + j) * Nz;
+        // rows of frequencies [f0, f0 + fch) -> Vs, r0ls (called by all threads)
         auto stage_rows = [&](int f0) {
             float2* Vs2 = reinterpret_cast<float2*>(Vs);
             const int nrow = min(fch, G.Nf - f0) * Nm;
@@ -65,6 +68,7 @@ __global__ void __launch_bounds__(256, (SC <= 16 ? 2 : 1)) k_kappa(DevGeom G, De
                 const int k = f0 * Nm + t / SC, c = t % SC;
                 Vs2[t] = (c < NC) ? gV[(size_t)k * SCA + c] : gV[(size_t)k * SCA + SCA - 1];
             }
+            for (int t = tid; t < nrow; t += KT) r0ls[t] = gr0l[f0 * Nm + t];
         };
         __syncthreads();
         {
@@ -88,7 +92,7 @@ __global__ void __launch_bounds__(256, (SC <= 16 ? 2 : 1)) k_kappa(DevGeom G, De
         float2* fb = fac + tid;
         float2* fy = fb + G.Nf * KT;
         float2* fz = fy + G.My * KT;
-        const float2 Fc = factors_from_geo(G, geo_s[(size_t)j * P + pp], fb, fy, fz, KT);
+        const float2 Fc = factors_from_geo(G, geo_s[(size_t)j * P + pp], geol_s[(size_t)j * P + pp], fb, fy, fz, KT);
         // pass 1: h = psi^H V, pr = psi^H r0
         float2 h[NC];
         #pragma unroll
@@ -139,8 +143,12 @@ __global__ void __launch_bounds__(256, (SC <= 16 ? 2 : 1)) k_kappa(DevGeom G, De
             const float den = alpha + iq;
             tf = make_float2((pr.x * ieb + af.x * iq) / den, (pr.y * ieb + af.y * iq) / den);
         }
-        // pass 2: r = r0 - tau (psi - V V^H psi / eta_bar), |r|^2 and |psi_perp|^2
-        ff rr{0.f, 0.f};   // |r|^2, float-float over (f, y) chunks
+        // pass 2: r = r0 - tau (psi - V V^H psi / eta_bar), |r|^2 and |psi_perp|^2.
+        // |r|^2/eta_bar can reach ~1e4 (unmodelled paths), so r is formed in
+        // float-float from the exact product tau psi_perp and the two parts of r0,
+        // and its squares are summed exactly; V V^H psi runs in four FP32 chains of
+        // a quarter of the columns each.
+        ff rr{0.f, 0.f};
         float pn = 0.f;
         for (int f0 = 0; f0 < G.Nf; f0 += fch) {
           if (fch < G.Nf) { __syncthreads(); stage_rows(f0); __syncthreads(); }
@@ -148,31 +156,46 @@ __global__ void __launch_bounds__(256, (SC <= 16 ? 2 : 1)) k_kappa(DevGeom G, De
             const float2 cb = cmul(Fc, fb[f * KT]);
             for (int y = 0; y < G.My; ++y) {
                 const float2 w = cmul(cb, fy[y * KT]);
-                float rr_chunk = 0.f;
                 for (int m = 0; m < G.Mz; ++m) {
                     const float2 ps = cmul(w, fz[m * KT]);
-                    const float4* row = Vs + (size_t)((f - f0) * Nm + y * G.Mz + m) * NP;
-                    float2 vv = make_float2(0.f, 0.f), vw = make_float2(0.f, 0.f);   // two chains
+                    const int kr = (f - f0) * Nm + y * G.Mz + m;
+                    const float4* row = Vs + (size_t)kr * NP;
+                    float2 va[4] = {make_float2(0.f, 0.f), make_float2(0.f, 0.f), make_float2(0.f, 0.f), make_float2(0.f, 0.f)};
                     float2 r0 = make_float2(0.f, 0.f);
                     #pragma unroll
                     for (int c2 = 0; c2 < NP; ++c2) {
+                        const int ch = (4 * c2) / NP;
                         const float4 v = row[c2];
-                        vv.x = fmaf(v.x, h[2 * c2].x, fmaf(v.y, h[2 * c2].y, vv.x));
-                        vv.y = fmaf(v.y, h[2 * c2].x, fmaf(-v.x, h[2 * c2].y, vv.y));
+                        va[ch].x = fmaf(v.x, h[2 * c2].x, fmaf(v.y, h[2 * c2].y, va[ch].x));
+                        va[ch].y = fmaf(v.y, h[2 * c2].x, fmaf(-v.x, h[2 * c2].y, va[ch].y));
                         if (2 * c2 + 1 < NC) {
-                            vw.x = fmaf(v.z, h[2 * c2 + 1].x, fmaf(v.w, h[2 * c2 + 1].y, vw.x));
-                            vw.y = fmaf(v.w, h[2 * c2 + 1].x, fmaf(-v.z, h[2 * c2 + 1].y, vw.y));
+                            va[ch].x = fmaf(v.z, h[2 * c2 + 1].x, fmaf(v.w, h[2 * c2 + 1].y, va[ch].x));
+                            va[ch].y = fmaf(v.w, h[2 * c2 + 1].x, fmaf(-v.z, h[2 * c2 + 1].y, va[ch].y));
                         } else {
                             r0 = make_float2(v.z, v.w);
                         }
                     }
-                    const float2 pp2 = make_float2(ps.x - (vv.x + vw.x) * ieb, ps.y - (vv.y + vw.y) * ieb);
+                    const float vsx = (va[0].x + va[1].x) + (va[2].x + va[3].x);
+                    const float vsy = (va[0].y + va[1].y) + (va[2].y + va[3].y);
+                    const float2 pp2 = make_float2(ps.x - vsx * ieb, ps.y - vsy * ieb);
                     pn += pp2.x * pp2.x + pp2.y * pp2.y;
-                    const float2 t = cmul(tf, pp2);
-                    const float rx = r0.x - t.x, ry = r0.y - t.y;
-                    rr_chunk += rx * rx + ry * ry;
+                    // t = tau pp2 exactly: re = p1 - p2, im = p3 + p4 (+ FMA errors)
+                    const float p1 = __fmul_rn(tf.x, pp2.x), e1 = fmaf(tf.x, pp2.x, -p1);
+                    const float p2 = __fmul_rn(tf.y, pp2.y), e2 = fmaf(tf.y, pp2.y, -p2);
+                    const float p3 = __fmul_rn(tf.x, pp2.y), e3 = fmaf(tf.x, pp2.y, -p3);
+                    const float p4 = __fmul_rn(tf.y, pp2.x), e4 = fmaf(tf.y, pp2.x, -p4);
+                    const float2 rl = r0ls[kr];
+                    float sx, ex1, ex2, sy, ey1, ey2;
+                    ff rx, ry;
+                    two_sum(r0.x, -p1, sx, ex1);
+                    two_sum(sx, p2, rx.hi, ex2);
+                    rx.lo = __fadd_rn(__fadd_rn(rl.x, __fsub_rn(e2, e1)), __fadd_rn(ex1, ex2));
+                    two_sum(r0.y, -p3, sy, ey1);
+                    two_sum(sy, -p4, ry.hi, ey2);
+                    ry.lo = __fsub_rn(__fadd_rn(rl.y, __fadd_rn(ey1, ey2)), __fadd_rn(e3, e4));
+                    ff_acc_sq(rr, make_float2(rx.hi, ry.hi));
+                    rr.lo = fmaf(2.0f * rx.hi, rx.lo, fmaf(2.0f * ry.hi, ry.lo, rr.lo));
                 }
-                rr = ff_add(rr, ff{rr_chunk, 0.f});
             }
           }
         }
@@ -278,7 +301,8 @@ __global__ void k_iota(DevGeom G, DevParams Pm, DevState D, int S, const float* 
         for (int s = lane; s < S; s += 32) {
             const float* ph = phi + (size_t)s * 6 * P;
             float2* fs = fac + (size_t)s * nfac;
-            cS[s] = factors_from_geo(G, D.geo[((size_t)s * J + j) * P + pp], fs, fs + Nf, fs + Nf + G.My, 1);
+            const size_t gi = ((size_t)s * J + j) * P + pp;
+            cS[s] = factors_from_geo(G, D.geo[gi], D.geo_lo[gi], fs, fs + Nf, fs + Nf + G.My, 1);
             const float pi = (float)(D.zeta[s * J + j] * D.W[s]);
             const float gm = ph[3 * P + pp], mr = ph[4 * P + pp], mi = ph[5 * P + pp];
             dS[s] = make_float2(sqrtf(fmaxf(pi * (gm + (mr * mr + mi * mi) * (1.0f - pi)), 0.0f)), 0.f);
@@ -576,7 +600,8 @@ __global__ void __launch_bounds__(32 * NCG, (NCG == 4 ? 3 : 2)) k_iota_blk(DevGe
             for (int s = tid; s < S; s += IB_T) {
                 const float* ph = phi + (size_t)s * 6 * P;
                 float2* fs = fac + (size_t)s * nfac;
-                const float A = factors_from_geo_folded(G, D.geo[((size_t)s * J + j) * P + pp], fs, fs + Nf, fs + Nf + G.My, 1);
+                const size_t gi = ((size_t)s * J + j) * P + pp;
+                const float A = factors_from_geo_folded(G, D.geo[gi], D.geo_lo[gi], fs, fs + Nf, fs + Nf + G.My, 1);
                 const float pi = (float)(D.zeta[s * J + j] * D.W[s]);
                 const float gm = ph[3 * P + pp], mr = ph[4 * P + pp], mi = ph[5 * P + pp];
                 const float d = sqrtf(fmaxf(pi * (gm + (mr * mr + mi * mi) * (1.0f - pi)), 0.0f));
@@ -819,7 +844,7 @@ static void launch_kappa_sc(const DevGeom& G, const DevParams& Pm, const DevStat
     const int nfac = G.Nf + G.My + G.Mz;
     const int Nm = G.My * G.Mz;
     const size_t fixed = ((size_t)kappa_rpack<SC>() + SC + (size_t)nfac * 256) * sizeof(float2);
-    const size_t per_f = (size_t)Nm * SC * sizeof(float2);
+    const size_t per_f = (size_t)Nm * (SC + 1) * sizeof(float2);   // V rows and the low part of r0
     const size_t limit = 200 * 1024;
     int fch = G.Nf;
     while (fch > 1 && fixed + fch * per_f > limit) fch = (fch + 1) / 2;

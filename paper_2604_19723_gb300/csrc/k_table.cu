@@ -45,6 +45,7 @@ __global__ void k_table(DevGeom G, DevParams Pm, DevState D, int S, int nsplit, 
     const float pd = (float)(1.0 - W);
     const float* ph = D.phi[D.cur] + (size_t)s * 6 * P;
     const float4* geo = D.geo + ((size_t)s * J + j) * P;
+    const float2* geol = D.geo_lo + ((size_t)s * J + j) * P;
     double acc64[EPT][3][2];
     #pragma unroll
     for (int e = 0; e < EPT; ++e)
@@ -57,7 +58,7 @@ __global__ void k_table(DevGeom G, DevParams Pm, DevState D, int S, int nsplit, 
             const int p = c0 + t;
             float2* b0 = Bf + (size_t)t * 3 * Nf;
             float2* fy = Fyz + (size_t)t * nyz;
-            const float2 c = factors_from_geo(G, geo[p], b0, fy, fy + G.My, 1);
+            const float2 c = factors_from_geo(G, geo[p], geol[p], b0, fy, fy + G.My, 1);
             const float gm = ph[3 * P + p], mr = ph[4 * P + p], mi = ph[5 * P + p];
             const float m2 = mr * mr + mi * mi;
             const float wb = (float)D.w_x[p];
@@ -363,7 +364,9 @@ __global__ void k_stage_kappa(DevGeom G, DevParams Pm, DevState D, int S, int SC
             kV[(size_t)k * SC + c] = make_float2((float)v.x, (float)v.y);
         }
         for (int c = K; c < SC - 1; ++c) kV[(size_t)k * SC + c] = make_float2(0.f, 0.f);
-        kV[(size_t)k * SC + SC - 1] = make_float2((float)e0.x, (float)e0.y);   // r0 in the last column
+        const float2 r0h = make_float2((float)e0.x, (float)e0.y);
+        kV[(size_t)k * SC + SC - 1] = r0h;   // r0 in the last column, its low part apart
+        D.kr0l[((size_t)s * J + j) * Nz + k] = make_float2((float)(e0.x - (double)r0h.x), (float)(e0.y - (double)r0h.y));
         atomicAdd(&rr[0], e0.x * e0.x + e0.y * e0.y);
     }
     __syncthreads();

@@ -257,6 +257,22 @@ def test_woodbury_equals_dense(zero_mean, scaling):
         assert np.max(np.abs(x - y) / np.maximum(1.0, np.abs(x))) < 1e-10, k
 
 
+@pytest.mark.parametrize("scaling", [0, 1])
+def test_streamed_table_equals_table(scaling):
+    """The chunked particle sums of message_table_streamed add up to message_table."""
+    g = W.make_geometry(J=2, Nf=4, My=2, Mz=2)
+    prm = W.Params(mvec_scaling=scaling)
+    scn = W.make_scenario(g, prm, N=2, K=3, seed=8)
+    eta = synth.noise_variance(scn)
+    st0 = W.state_near_truth(scn, P=101, S=4, n=0, seed=2, eta_true=eta, pos_std=0.05)
+    pred = model.predict(st0, prm, g.J, seed=9, S_max=8)
+    a = messages_dense.message_table(pred, prm, messages_dense.all_steering(pred, g))
+    b = messages_dense.message_table_streamed(pred, prm, g, chunk=16)
+    for k in ("W", "pi", "m", "mw", "mu3", "mu4", "eta_bar"):
+        x, y = getattr(a, k), getattr(b, k)
+        assert np.max(np.abs(x - y)) <= 1e-12 * max(np.max(np.abs(x)), 1e-300), k
+
+
 # ---------------------------------------------------------------- special cases (P4)
 def test_zero_mean_variant_equals_nzm_with_zero_means():
     """P4: NZM with all mu = 0 is the ZM method; the mean terms vanish (Sec. V)."""
