@@ -146,8 +146,8 @@ __global__ void __launch_bounds__(256, (SC <= 16 ? 2 : 1)) k_kappa(DevGeom G, De
         // pass 2: r = r0 - tau (psi - V V^H psi / eta_bar), |r|^2 and |psi_perp|^2.
         // |r|^2/eta_bar can reach ~1e4 (unmodelled paths), so r is formed in
         // float-float from the exact product tau psi_perp and the two parts of r0,
-        // and its squares are summed exactly; V V^H psi runs in four FP32 chains of
-        // a quarter of the columns each.
+        // and its squares are summed exactly; V V^H psi runs in eight FP32 chains of
+        // an eighth of the columns each, added pairwise.
         ff rr{0.f, 0.f};
         float pn = 0.f;
         for (int f0 = 0; f0 < G.Nf; f0 += fch) {
@@ -160,11 +160,14 @@ __global__ void __launch_bounds__(256, (SC <= 16 ? 2 : 1)) k_kappa(DevGeom G, De
                     const float2 ps = cmul(w, fz[m * KT]);
                     const int kr = (f - f0) * Nm + y * G.Mz + m;
                     const float4* row = Vs + (size_t)kr * NP;
-                    float2 va[4] = {make_float2(0.f, 0.f), make_float2(0.f, 0.f), make_float2(0.f, 0.f), make_float2(0.f, 0.f)};
+                    constexpr int NCH = NP >= 8 ? 8 : NP;
+                    float2 va[NCH];
+                    #pragma unroll
+                    for (int i = 0; i < NCH; ++i) va[i] = make_float2(0.f, 0.f);
                     float2 r0 = make_float2(0.f, 0.f);
                     #pragma unroll
                     for (int c2 = 0; c2 < NP; ++c2) {
-                        const int ch = (4 * c2) / NP;
+                        const int ch = (NCH * c2) / NP;
                         const float4 v = row[c2];
                         va[ch].x = fmaf(v.x, h[2 * c2].x, fmaf(v.y, h[2 * c2].y, va[ch].x));
                         va[ch].y = fmaf(v.y, h[2 * c2].x, fmaf(-v.x, h[2 * c2].y, va[ch].y));
@@ -175,8 +178,13 @@ __global__ void __launch_bounds__(256, (SC <= 16 ? 2 : 1)) k_kappa(DevGeom G, De
                             r0 = make_float2(v.z, v.w);
                         }
                     }
-                    const float vsx = (va[0].x + va[1].x) + (va[2].x + va[3].x);
-                    const float vsy = (va[0].y + va[1].y) + (va[2].y + va[3].y);
+                    float vsx = 0.f, vsy = 0.f;   // pairwise sum of the chains
+                    #pragma unroll
+                    for (int w2 = NCH / 2; w2 >= 1; w2 /= 2) {
+                        #pragma unroll
+                        for (int i = 0; i < w2; ++i) { va[i].x += va[i + w2].x; va[i].y += va[i + w2].y; }
+                    }
+                    vsx = va[0].x; vsy = va[0].y;
                     const float2 pp2 = make_float2(ps.x - vsx * ieb, ps.y - vsy * ieb);
                     pn += pp2.x * pp2.x + pp2.y * pp2.y;
                     // t = tau pp2 exactly: re = p1 - p2, im = p3 + p4 (+ FMA errors)
