@@ -664,18 +664,19 @@ __global__ void __launch_bounds__(32 * NCG, (NCG == 4 ? 3 : 2)) k_iota_blk(DevGe
             __syncthreads();
             // this thread's slots (rows ra: q < 8, rb: q < 16) into registers
             gent Ar[QA], Br[QB];
+            unsigned liveA = 0u, liveB = 0u;   // slots of the lower triangle; cleared as columns finish
             {
                 const float sa = (ra < S) ? sqrtf(Apk[tri(ra, ra)].re.hi) : 0.f;
                 const float sb = (rb < S) ? sqrtf(Apk[tri(rb, rb)].re.hi) : 0.f;
                 #pragma unroll
                 for (int q = 0; q < QA; ++q) {
                     const int c = NCG * q + cg;
-                    if (c <= ra && ra < S) Ar[q] = gent_make(Apk[tri(ra, c)], sa * sqrtf(Apk[tri(c, c)].re.hi));
+                    if (c <= ra && ra < S) { Ar[q] = gent_make(Apk[tri(ra, c)], sa * sqrtf(Apk[tri(c, c)].re.hi)); liveA |= 1u << q; }
                 }
                 #pragma unroll
                 for (int q = 0; q < QB; ++q) {
                     const int c = NCG * q + cg;
-                    if (c <= rb && rb < S) Br[q] = gent_make(Apk[tri(rb, c)], sb * sqrtf(Apk[tri(c, c)].re.hi));
+                    if (c <= rb && rb < S) { Br[q] = gent_make(Apk[tri(rb, c)], sb * sqrtf(Apk[tri(c, c)].re.hi)); liveB |= 1u << q; }
                 }
             }
             // rhs_a = d_a (g_a - sum_b G_ab pi_b mu_b), FP32
@@ -703,8 +704,12 @@ __global__ void __launch_bounds__(32 * NCG, (NCG == 4 ? 3 : 2)) k_iota_blk(DevGe
                 ff piv = pivbuf[2 * cur];
                 ff inv = pivbuf[2 * cur + 1];
                 if (!(piv.hi > 0.f)) { piv = ff{1e-30f, 0.f}; inv = ff{1e30f, 0.f}; }
-                const float lkk = sqrtf(piv.hi + piv.lo);
-                const float il = 1.0f / lkk;
+                // FP32 factor for the (variational) solves: 1/L_kk by the fast reciprocal square root
+                const float il = rsqrtf(piv.hi + piv.lo);
+                const float lkk = (piv.hi + piv.lo) * il;
+                // column c = NCG q + cg takes updates while c > k: the slot of column k retires
+                const int kc = k - cg;
+                if (kc >= 0 && kc % NCG == 0) { liveA &= ~(1u << (kc / NCG)); liveB &= ~(1u << (kc / NCG)); }
                 if (tid == 0) {
                     ffexp_mul(det, piv);
                     Lsm[tri(k, k)] = make_float2(lkk, 0.f);
@@ -732,9 +737,9 @@ __global__ void __launch_bounds__(32 * NCG, (NCG == 4 ? 3 : 2)) k_iota_blk(DevGe
                 #pragma unroll
                 for (int q = 0; q < QA; ++q) {
                     const int c = NCG * q + cg;
-                    if (c > k && c <= ra && ra < S) {
+                    if (liveA & (1u << q)) {
                         gent_sub_mulc(Ar[q], la, colr[c]);
-                        if (c == k + 1) {
+                        if (NCG * q == kc + 1) {
                             const cff v = gent_value(Ar[q]);
                             ncol[ra] = v;
                             ncolr[ra] = make_float2(v.re.hi, v.im.hi);
@@ -745,9 +750,9 @@ __global__ void __launch_bounds__(32 * NCG, (NCG == 4 ? 3 : 2)) k_iota_blk(DevGe
                 #pragma unroll
                 for (int q = 0; q < QB; ++q) {
                     const int c = NCG * q + cg;
-                    if (c > k && c <= rb && rb < S) {
+                    if (liveB & (1u << q)) {
                         gent_sub_mulc(Br[q], lb, colr[c]);
-                        if (c == k + 1) {
+                        if (NCG * q == kc + 1) {
                             const cff v = gent_value(Br[q]);
                             ncol[rb] = v;
                             ncolr[rb] = make_float2(v.re.hi, v.im.hi);
