@@ -44,6 +44,64 @@ def kappa_flops(P, S, J, Nz):
     return float(P) * S * J * per
 
 
+def iota_flops(P, S, J, Nf, My, Mz):
+    """Algorithmic flops of one launch of the MT likelihood kernel, per (p, j): the
+    Kronecker-factored Gram (S(S+1)/2 entries, Nf + My + Mz complex multiply-adds and
+    two complex products each), g = Psi^H z, the right-hand side, the Cholesky
+    factorisation (S^3/6 complex multiply-adds), two triangular solves and the
+    element-wise residual (three complex products and one accumulation per (s, k)).
+    Counted as plain FP32 flops; the kernel runs them in float-float arithmetic."""
+    Nz = Nf * My * Mz
+    per = (S * (S + 1) / 2 * 8 * (Nf + My + Mz + 2) + 8 * S * Nf * (My * Mz + My + 1) + 8 * S * S
+           + 8 * S ** 3 / 6 + 8 * S * S + 20 * Nz * S)
+    return float(P) * J * per
+
+
+def a5_flops(P, S, J, Nz):
+    """The fused-likelihood step's algorithmic flops in the survey's count (per (j, p):
+    8 Nz S(2S+1) + 4 Nz S(S+1) + 9.3 S^3), for the three likelihood kernels together."""
+    return float(P) * J * (8 * Nz * S * (2 * S + 1) + 4 * Nz * S * (S + 1) + 9.3 * S ** 3)
+
+
+# DRAM bytes per launch from one ncu capture (dram__bytes_read.sum + dram__bytes_write.sum,
+# a single-pass metric set, at the full size of the workload), valid while the kernel
+# sources hash to the recorded value.
+TRAFFIC_RECORDS = {
+    "k_kappa": {"workload": "scale_64x100k", "P": 100000, "bytes": None, "sources_sha256": None,
+                "profile": "profiles/dram_scale_64x100k.md"},
+    "k_iota_blk": {"workload": "scale_64x100k", "P": 100000, "bytes": None, "sources_sha256": None,
+                   "profile": "profiles/dram_scale_64x100k.md"},
+}
+KERNEL_SOURCES = ("paper_2604_19723_gb300/csrc/k_like.cu", "paper_2604_19723_gb300/csrc/bp_kernels.cuh",
+                  "paper_2604_19723_gb300/csrc/bp_internal.cuh")
+
+
+def kernel_sources_sha256():
+    import hashlib
+    h = hashlib.sha256()
+    for rel in KERNEL_SOURCES:
+        with open(os.path.join(ROOT, rel), "rb") as fh:
+            h.update(fh.read())
+    return h.hexdigest()
+
+
+def traffic_for(kernel, workload, P):
+    rec = TRAFFIC_RECORDS.get(kernel)
+    if not rec or rec["bytes"] is None or rec["workload"] != workload or rec["P"] != P:
+        return None
+    return rec["bytes"] if rec["sources_sha256"] == kernel_sources_sha256() else None
+
+
+def reduce_max(x, world, device):
+    """Max of a scalar over the ranks of the process group (a no-op for one rank)."""
+    if world <= 1:
+        return float(x)
+    import torch
+    t = torch.tensor([float(x)], dtype=torch.float64, device=device)
+    torch.distributed.all_reduce(t, op=torch.distributed.ReduceOp.MAX)
+    return float(t.item())
+
+
 class ClockSampler:
     """nvidia-smi sampling of SM clock and throttle reasons during the timed region."""
 
@@ -158,8 +216,10 @@ def run_reference(args, rank):
     out = {"metric": METRIC, "value": value, "unit": UNIT, "n_gpus": args.gpus, "steps": args.steps,
            "warmup": args.warmup, "ms_per_step": 1e3 * t, "higher_is_better": True, "scaling": "weak",
            "vs_baseline": None, "dtype": "f64", "data": "synthetic", "impl": "reference",
-           "config": {"workload": f"{args.workload} (oracle sample of {Ps} particles per step)",
-                      "P": Ps, "S": S, "J": g.J, "Nz": g.Nz},
+           "config": {"workload": args.workload, "P": wl["P"], "S": S, "J": g.J, "Nz": g.Nz,
+                      "clutter_per_step": wl["clutter_mean"], "visibility": wl["visibility"],
+                      "parallelism": "oracle on the host cores",
+                      "sample": f"{Ps} of the workload's {wl['P']} particles per step; value = sample updates / time"},
            "cpu_baseline": {"value": value, "unit": UNIT, "cores": cores, "kind": "oracle",
                             "sample": f"{Ps} particles per step, FP64 Woodbury-mode oracle"},
            "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
@@ -192,7 +252,7 @@ def run_gpu(args, rank, world):
     f.set_profiling(True)
     ev0 = [torch.cuda.Event(enable_timing=True) for _ in range(args.steps)]
     ev1 = [torch.cuda.Event(enable_timing=True) for _ in range(args.steps)]
-    kappa_ms, prof_tot, repaired = [], {}, []
+    kappa_ms, iota_ms, prof_tot, repaired = [], [], {}, []
     l0 = f.launch_count()
     if world > 1:
         torch.distributed.barrier()
@@ -207,17 +267,16 @@ def run_gpu(args, rank, world):
             pr = f.profile()                       # events recorded by the library on its stream
             repaired.append(f.estimate()["iota_repaired"])
             kappa_ms.append(pr["kappa"])
+            iota_ms.append(pr["iota"])
             for k, v in pr.items():
                 prof_tot[k] = prof_tot.get(k, 0.0) + v
         torch.cuda.synchronize()
+        if world > 1:
+            torch.distributed.barrier()
     launches = f.launch_count() - l0
     f.set_profiling(False)
     step_ms = [a.elapsed_time(b) for a, b in zip(ev0, ev1)]
-    t_step = float(np.mean(step_ms))
-    if world > 1:
-        tt = torch.tensor([t_step], device="cuda")
-        torch.distributed.all_reduce(tt, op=torch.distributed.ReduceOp.MAX)
-        t_step = float(tt.item())
+    t_step = reduce_max(float(np.mean(step_ms)), world, "cuda")
     value = world * P * g.J / (t_step * 1e-3)
 
     # end to end through the public API: host (pinned) observations copied in every
@@ -238,11 +297,7 @@ def run_gpu(args, rank, world):
             e_b.record(stream)
         stream.synchronize()
         e2e_times.append(e_a.elapsed_time(e_b))
-    t_e2e = float(np.mean(e2e_times))
-    if world > 1:
-        tt = torch.tensor([t_e2e], device="cuda")
-        torch.distributed.all_reduce(tt, op=torch.distributed.ReduceOp.MAX)
-        t_e2e = float(tt.item())
+    t_e2e = reduce_max(float(np.mean(e2e_times)), world, "cuda")
     h2d = g.J * g.Nz * 8
     d2h = 8 * (12 + g.J + 9 * S_max + S_max * g.J)
 
@@ -250,8 +305,23 @@ def run_gpu(args, rank, world):
     peaks = measured_peaks()
     sm_mhz = clocks.get("sm_mhz") or peaks.get("sm_max_mhz", 2070.0)
     peak_alu = SMS * FP32_LANES_PER_SM * 2 * sm_mhz * 1e6 / 1e12
-    k_ms = float(np.mean(kappa_ms))
-    achieved = kappa_flops(P, S, g.J, g.Nz) / (k_ms * 1e-3) / 1e12
+    # roofline of the dominant kernel (by its measured time in this run)
+    k_ms, i_ms = float(np.mean(kappa_ms)), float(np.mean(iota_ms))
+    per_kernel = {
+        "k_kappa": (k_ms, kappa_flops(P, S, g.J, g.Nz)),
+        "k_iota_blk": (i_ms, iota_flops(P, S, g.J, g.Nf, g.My, g.Mz)),
+    }
+    def roof(name):
+        ms, fl = per_kernel[name]
+        a = fl / (ms * 1e-3) / 1e12
+        return {"bound": "alu", "kernel": name, "achieved": a, "peak": peak_alu, "unit": "TFLOP/s",
+                "frac": a / peak_alu, "traffic": traffic_for(name, args.workload, P), "ms_per_launch": ms,
+                "peak_basis": f"FP32 FMA lanes: {SMS} SMs x {FP32_LANES_PER_SM} x 2 flop x {sm_mhz:.0f} MHz "
+                              f"(median sampled); derived, not in MEASURED_PEAKS.json"}
+    dominant = max(per_kernel, key=lambda n: per_kernel[n][0])
+    other = "k_iota_blk" if dominant == "k_kappa" else "k_kappa"
+    a5_ms = k_ms + i_ms + prof_tot.get("nu", 0.0) / args.steps
+    a5_ach = a5_flops(P, S, g.J, g.Nz) / (a5_ms * 1e-3) / 1e12
     out = {"metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
            "warmup": args.warmup, "ms_per_step": t_step, "steps_per_s": 1e3 / t_step,
            "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f32",
@@ -260,9 +330,11 @@ def run_gpu(args, rank, world):
                       "clutter_per_step": wl["clutter_mean"], "visibility": wl["visibility"],
                       "l2": "flushed between timed steps (256 MB write)", "parallelism": f"replicas x{world}"},
            "stage_ms": {k: v / args.steps for k, v in prof_tot.items()},
-           "roofline": {"bound": "alu", "kernel": "k_kappa", "achieved": achieved, "peak": peak_alu,
-                        "unit": "TFLOP/s", "frac": achieved / peak_alu, "traffic": None,
-                        "peak_basis": f"FP32 FMA lanes: {SMS} SMs x {FP32_LANES_PER_SM} x 2 flop x {sm_mhz:.0f} MHz (median sampled)"},
+           "roofline": roof(dominant),
+           "roofline_next_kernel": roof(other),
+           "roofline_a5_fused": {"bound": "alu", "kernels": "k_kappa + k_iota_blk + k_nu",
+                                 "achieved": a5_ach, "peak": peak_alu, "unit": "TFLOP/s", "frac": a5_ach / peak_alu,
+                                 "flops_basis": "P J [8 Nz S(2S+1) + 4 Nz S(S+1) + 9.3 S^3]"},
            "e2e": {"value": world * P * g.J / (t_e2e * 1e-3), "unit": UNIT, "h2d_bytes_per_step": h2d,
                    "d2h_bytes_per_step": d2h, "ms_per_step": t_e2e},
            "gpu_launches": int(launches), "clocks": clocks,
