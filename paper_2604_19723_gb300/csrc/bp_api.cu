@@ -178,7 +178,7 @@ bp_status bp_init(const bp_geometry* geom, const bp_params* prm, int P, int S_ma
     ok &= dalloc(h, &D.eta_bar, (size_t)J);
     ok &= dalloc(h, &D.kV, (size_t)S_max * J * Nz * SCA);
     ok &= dalloc(h, &D.kr0l, (size_t)S_max * J * Nz);
-    ok &= dalloc(h, &D.kR, (size_t)S_max * J * SCA * SCA);
+    ok &= dalloc(h, &D.kdl, (size_t)S_max * J * SCA);
     ok &= dalloc(h, &D.ky0, (size_t)S_max * J * SCA);
     ok &= dalloc(h, &D.kJ0, (size_t)S_max * J);
     ok &= dalloc(h, &D.nu_T, (size_t)J * 4 * S_max);

@@ -334,8 +334,8 @@ struct DevState {
     // kappa stage outputs (per (s,j))
     float2* kV;       // [S_max][J][Nz][S_cap]   whitened basis, column S_cap-1 = r0 (FP32 part)
     float2* kr0l;     // [S_max][J][Nz]          low part of r0 (r0 = FP32 part + low part)
-    float2* kR;       // [S_max][J][S_cap*S_cap] upper Cholesky factor (FP32, padded identity)
-    float2* ky0;      // [S_max][J][S_cap]       y0 = R^-1 V^H e0 / eta_bar
+    float2* kdl;      // [S_max][J][S_cap]       1/lambda_c of the eigen-whitened basis (.x; zero-padded)
+    float2* ky0;      // [S_max][J][S_cap]       w_c = y~0_c / lambda_c, y~0 = V^H e0 / eta_bar
     double* kJ0;      // [S_max][J]              |r0|^2/eta_bar
     // nu stage outputs (per j)
     double* nu_T;     // [J][S_max] diag a_k, [J][S_max] |offdiag|^2, [J][S_max] double2 b'

@@ -10,7 +10,8 @@
 //
 //  kappa~(phi_s^p, 1)/kappa~(., 0) for every (s, p), summed over j:
 //     Delta = J0 - J(tau*) - log(1 + q alpha),
-//     J(tau) = |r0 - tau psi_perp|^2/eta_bar + |y0 - tau R^-1 V^H psi/eta_bar|^2 + |tau - a|^2/q,
+//     J(tau) = |r0 - tau psi_perp|^2/eta_bar + |y0 - tau Lambda^-1/2 V^H psi/eta_bar|^2 + |tau - a|^2/q
+//     (amplitudes in the eigenbasis of I + M^H M/eta_bar, V its whitened basis),
 //     psi_perp = psi - V V^H psi/eta_bar, a = zeta mu^p, q = (gamma^p + |mu^p|^2 (1 - zeta)) zeta,
 //     alpha = psi^H A_s^-1 psi, tau* = (psi^H r0/eta_bar + a/q)/(alpha + 1/q).
 //  iota~(x^p) for every p, summed over j (columns sqrt(pi (gamma + |mu|^2 (1 - pi))) psi_s):
@@ -27,11 +28,10 @@ namespace bp {
 
 // ---------------------------------------------------------------- kappa
 // block = (particle tile of KT threads, s); loop over j; V_{s,j} staged in shared
-// memory as rows of SC complex values (columns 0..SC-2 the whitened basis, column
-// SC-1 the null residual r0), read two columns per 128-bit broadcast load; R as
-// a packed upper triangle.
-template <int SC>
-__host__ __device__ constexpr int kappa_rpack() { return (SC - 1) * SC / 2; }
+// memory as rows of SC complex values (columns 0..SC-2 the eigen-whitened basis,
+// column SC-1 the null residual r0), read two columns per 128-bit broadcast load;
+// 1/lambda_c and w_c = y~0_c/lambda_c beside it.  The basis columns are orthogonal,
+// so every amplitude term is a diagonal sum over the columns.
 
 template <int SC>
 __global__ void __launch_bounds__(256, (SC <= 16 ? 2 : 1)) k_kappa(DevGeom G, DevParams Pm, DevState D, int S, int SCA, int fch) {
@@ -42,8 +42,8 @@ __global__ void __launch_bounds__(256, (SC <= 16 ? 2 : 1)) k_kappa(DevGeom G, De
     const int s = blockIdx.y;
     const int P = Pm.P, J = G.J, Nz = G.Nz, Nm = G.My * G.Mz;
     float4* Vs = sm4;                                                  // [Nz][NP]
-    float2* Rs = reinterpret_cast<float2*>(Vs + (size_t)Nz * NP);      // packed upper NC x NC
-    float2* y0s = Rs + kappa_rpack<SC>();                              // [SC]
+    float2* dls = reinterpret_cast<float2*>(Vs + (size_t)Nz * NP);     // [SC] 1/lambda_c (.x)
+    float2* y0s = dls + SC;                                            // [SC] w_c
     float2* fac = y0s + SC;                                            // [nfac][KT]
     float2* r0ls = fac + (size_t)(G.Nf + G.My + G.Mz) * KT;           // [fch * Nm] low part of r0
     const int tid = threadIdx.x;
@@ -73,15 +73,9 @@ __global__ void __launch_bounds__(256, (SC <= 16 ? 2 : 1)) k_kappa(DevGeom G, De
         __syncthreads();
         {
             if (fch >= G.Nf) stage_rows(0);
-            const float2* gR = D.kR + ((size_t)s * J + j) * SCA * SCA;
-            for (int t = tid; t < kappa_rpack<SC>(); t += KT) {
-                int r = 0, off = 0;
-                while (off + (NC - r) <= t) { off += NC - r; ++r; }
-                const int c = r + (t - off);
-                Rs[t] = gR[(size_t)r * SCA + c];
-            }
+            const float2* gd = D.kdl + ((size_t)s * J + j) * SCA;
             const float2* gy = D.ky0 + ((size_t)s * J + j) * SCA;
-            for (int t = tid; t < SC; t += KT) y0s[t] = gy[t];
+            for (int t = tid; t < SC; t += KT) { dls[t] = gd[t]; y0s[t] = gy[t]; }
         }
         __syncthreads();
         const double eb = D.eta_bar[j];
@@ -207,40 +201,37 @@ __global__ void __launch_bounds__(256, (SC <= 16 ? 2 : 1)) k_kappa(DevGeom G, De
             }
           }
         }
-        // y = y0 - u, u = tau R^-1 V^H psi / eta_bar (back substitution in place:
-        // h <- R^-1 conj(h)); |y0|^2 - |y|^2 = 2 Re(conj(y0) u) - |u|^2 in FP32
-        float dy0 = 0.f, dy1 = 0.f, gg0 = 0.f, gg1 = 0.f;
+        // amplitude terms in the eigenbasis, x_c = conj(h_c) (= (V^H psi)_c):
+        // |y0|^2 - |y|^2 = 2 Re(tau y0^H x_amp)/eta_bar - |tau|^2 |x_amp|^2/eta_bar^2 with
+        // y0^H x_amp = sum_c conj(w_c) x_c = conj(sum_c w_c h_c), |x_amp|^2 = sum_c |h_c|^2/lambda_c
+        float tx0 = 0.f, ty0 = 0.f, tx1 = 0.f, ty1 = 0.f, gg0 = 0.f, gg1 = 0.f;
         #pragma unroll
-        for (int c = NC - 1; c >= 0; --c) {
-            const int off = c * NC - c * (c - 1) / 2;    // packed row c starts at R[c][c]
-            float2 g = make_float2(h[c].x, -h[c].y);
-            #pragma unroll
-            for (int e = 1; e < NC; ++e) {      // fixed trip count: unrolls fully, h stays in registers
-                if (c + e < NC) {
-                    const float2 u = cmul(Rs[off + e], h[c + e]);
-                    g.x -= u.x; g.y -= u.y;
-                }
-            }
-            const float dr = Rs[off].x;
-            h[c] = make_float2(g.x / dr, g.y / dr);
-            const float2 u = cmul(tf, make_float2(h[c].x * ieb, h[c].y * ieb));
-            const float2 y0 = y0s[c];
+        for (int c = 0; c < NC; ++c) {
+            const float2 w = y0s[c];
+            const float dl = dls[c].x;
+            const float m2 = fmaf(h[c].x, h[c].x, h[c].y * h[c].y);
             if (c & 1) {
-                gg1 = fmaf(h[c].x, h[c].x, fmaf(h[c].y, h[c].y, gg1));
-                dy1 += 2.f * (y0.x * u.x + y0.y * u.y) - (u.x * u.x + u.y * u.y);
+                tx1 = fmaf(w.x, h[c].x, fmaf(-w.y, h[c].y, tx1));
+                ty1 = fmaf(w.x, h[c].y, fmaf(w.y, h[c].x, ty1));
+                gg1 = fmaf(dl, m2, gg1);
             } else {
-                gg0 = fmaf(h[c].x, h[c].x, fmaf(h[c].y, h[c].y, gg0));
-                dy0 += 2.f * (y0.x * u.x + y0.y * u.y) - (u.x * u.x + u.y * u.y);
+                tx0 = fmaf(w.x, h[c].x, fmaf(-w.y, h[c].y, tx0));
+                ty0 = fmaf(w.x, h[c].y, fmaf(w.y, h[c].x, ty0));
+                gg0 = fmaf(dl, m2, gg0);
             }
         }
-        double dlt = J0r - ((double)rr.hi + (double)rr.lo) * ieb64 + (double)(dy0 + dy1);
+        // T = sum w h; Re(tau conj(T)) = tau.x T.x + tau.y T.y
+        const float Tx = tx0 + tx1, Ty = ty0 + ty1, gg = gg0 + gg1;
+        const double dyd = 2.0 * ((double)tf.x * Tx + (double)tf.y * Ty) * ieb64 -
+                           ((double)tf.x * tf.x + (double)tf.y * tf.y) * (double)gg * ieb64 * ieb64;
+        double dlt = J0r - ((double)rr.hi + (double)rr.lo) * ieb64 + dyd;
         if (q > 0.f) {
             // prior term |tau - a|^2 / q with the difference taken in FP64 (a may be
             // much larger than the innovation)
             const double dx = (double)tf.x - zeta * mr, dyt = (double)tf.y - zeta * mi;
             dlt -= (dx * dx + dyt * dyt) * (double)iq;
             // alpha = psi^H A^-1 psi = |psi_perp|^2/eta_bar + |R^-1 V^H psi|^2/eta_bar^2 (non-negative terms)
-            const float alpha_acc = pn * ieb + (gg0 + gg1) * ieb * ieb;
+            const float alpha_acc = pn * ieb + gg * ieb * ieb;
             dlt -= (double)log1pf(q * alpha_acc);
         }
         delta_sum += dlt;
@@ -856,7 +847,7 @@ template <int SC>
 static void launch_kappa_sc(const DevGeom& G, const DevParams& Pm, const DevState& D, int S, int SCA, cudaStream_t st) {
     const int nfac = G.Nf + G.My + G.Mz;
     const int Nm = G.My * G.Mz;
-    const size_t fixed = ((size_t)kappa_rpack<SC>() + SC + (size_t)nfac * 256) * sizeof(float2);
+    const size_t fixed = (2 * (size_t)SC + (size_t)nfac * 256) * sizeof(float2);
     const size_t per_f = (size_t)Nm * (SC + 1) * sizeof(float2);   // V rows and the low part of r0
     const size_t limit = 200 * 1024;
     int fch = G.Nf;

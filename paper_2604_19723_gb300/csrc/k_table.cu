@@ -207,7 +207,122 @@ __global__ void k_gram(DevGeom G, DevParams Pm, DevState D, int S, const float* 
 }
 
 // ---------------------------------------------------------------- kappa / omega stage per (s, j), FP64
-// One block per (s, j).  V is written to an FP64 scratch row by row (thread per row).
+// One block per (s, j).  The inverse of A_s = eta_bar I + M_{-s} M_{-s}^H (S-V) enters
+// through B = I + M_{-s}^H M_{-s}/eta_bar = U diag(lambda) U^H, found by cyclic Jacobi
+// rotations: the whitened basis V = M_{-s} U diag(lambda)^{-1/2} has orthogonal
+// columns and V V^H = M_{-s} B^{-1} M_{-s}^H, so A_s^{-1} = (I - V V^H/eta_bar)/eta_bar,
+// and the per-particle amplitude terms |B^{-1/2} U^H M^H psi|^2 become diagonal sums.
+// V is written to an FP64 scratch row by row (thread per row).
+
+// Hermitian eigen-decomposition of the n x n matrix A (row-major, shared) by cyclic
+// Jacobi with the round-robin parallel ordering: in each of the n2 - 1 rounds of a sweep
+// (n2 = n rounded up to even) the n2/2 disjoint pairs rotate at once.  For the pair
+// (p, q) with a_pq = |a_pq| e^{i phi}, zeta = (a_qq - a_pp)/(2|a_pq|) and
+// t = sign(zeta)/(|zeta| + sqrt(1 + zeta^2)) the unitary G (columns p, q:
+// (c, -s e^{-i phi}), (s, c e^{-i phi}), c = 1/sqrt(1 + t^2), s = t c) zeroes a_pq in
+// G^H A G.  U accumulates the G's (from the identity, or from a given start).  Sweeps
+// stop when the off-diagonal energy falls below tol of the diagonal energy, after at
+// most max_sweeps.  T is float or double; all threads of the block call it.
+template <typename T> struct cplx;
+template <> struct cplx<float> { using t = float2; };
+template <> struct cplx<double> { using t = double2; };
+template <typename T> struct JRot { T c, s, er, ei; };   // cos, sin, e^{i phi}
+
+template <typename T>
+__device__ void jacobi_herm(typename cplx<T>::t* A, typename cplx<T>::t* U, int n, JRot<T>* rot, double* red,
+                            bool init_identity, double tol, int max_sweeps) {
+    using C = typename cplx<T>::t;
+    const int tid = threadIdx.x, nt = blockDim.x;
+    if (init_identity)
+        for (int t = tid; t < n * n; t += nt) { U[t].x = (t / n == t % n) ? T(1) : T(0); U[t].y = T(0); }
+    __syncthreads();
+    if (n < 2) return;
+    const int n2 = n + (n & 1), half = n2 / 2;
+    auto pair_of = [&](int r, int i, int& p, int& q) {
+        int a, b;
+        if (i == 0) { a = n2 - 1; b = r; }
+        else { a = (r + i) % (n2 - 1); b = (r - i + n2 - 1) % (n2 - 1); }
+        p = min(a, b); q = max(a, b);
+    };
+    for (int sweep = 0; sweep < max_sweeps; ++sweep) {
+        // convergence test on the current matrix
+        if (tid == 0) { red[0] = 0.0; red[1] = 0.0; }
+        __syncthreads();
+        double off = 0.0, dia = 0.0;
+        for (int t = tid; t < n * n; t += nt) {
+            const int r = t / n, c = t - r * n;
+            const double m2 = (double)A[t].x * A[t].x + (double)A[t].y * A[t].y;
+            if (r == c) dia += m2; else off += m2;
+        }
+        off = warp_sum_d(off); dia = warp_sum_d(dia);
+        if ((tid & 31) == 0) { atomicAdd(&red[0], off); atomicAdd(&red[1], dia); }
+        __syncthreads();
+        const bool done = !(red[0] > tol * red[1]);
+        __syncthreads();
+        if (done) break;
+        for (int r = 0; r < n2 - 1; ++r) {
+            // rotation parameters of this round's pairs
+            for (int i = tid; i < half; i += nt) {
+                int p, q;
+                pair_of(r, i, p, q);
+                JRot<T> g{T(1), T(0), T(1), T(0)};
+                if (q < n) {
+                    const C apq = A[p * n + q];
+                    const T m = sqrt(apq.x * apq.x + apq.y * apq.y);
+                    if (m > T(1e-30)) {
+                        const T zeta = (A[q * n + q].x - A[p * n + p].x) / (T(2) * m);
+                        const T t = (zeta >= T(0) ? T(1) : T(-1)) / (fabs(zeta) + sqrt(T(1) + zeta * zeta));
+                        const T c = T(1) / sqrt(T(1) + t * t);
+                        g = JRot<T>{c, t * c, apq.x / m, apq.y / m};
+                    }
+                }
+                rot[i] = g;
+            }
+            __syncthreads();
+            // columns p, q of A and U:  (x_p, x_q) <- (c x_p - s e^{-i phi} x_q, s x_p + c e^{-i phi} x_q)
+            for (int t = tid; t < half * n; t += nt) {
+                const int i = t / n, row = t - i * n;
+                int p, q;
+                pair_of(r, i, p, q);
+                if (q >= n) continue;
+                const JRot<T> g = rot[i];
+                for (int w = 0; w < 2; ++w) {
+                    C* X = w ? U : A;
+                    const C xp = X[row * n + p], xq = X[row * n + q];
+                    const T eqx = g.er * xq.x + g.ei * xq.y, eqy = g.er * xq.y - g.ei * xq.x;   // e^{-i phi} x_q
+                    X[row * n + p].x = g.c * xp.x - g.s * eqx; X[row * n + p].y = g.c * xp.y - g.s * eqy;
+                    X[row * n + q].x = g.s * xp.x + g.c * eqx; X[row * n + q].y = g.s * xp.y + g.c * eqy;
+                }
+            }
+            __syncthreads();
+            // rows p, q of A:  (a_p, a_q) <- (c a_p - s e^{i phi} a_q, s a_p + c e^{i phi} a_q)
+            for (int t = tid; t < half * n; t += nt) {
+                const int i = t / n, cc = t - i * n;
+                int p, q;
+                pair_of(r, i, p, q);
+                if (q >= n) continue;
+                const JRot<T> g = rot[i];
+                const C ap = A[p * n + cc], aq = A[q * n + cc];
+                const T eqx = g.er * aq.x - g.ei * aq.y, eqy = g.er * aq.y + g.ei * aq.x;   // e^{i phi} a_q
+                A[p * n + cc].x = g.c * ap.x - g.s * eqx; A[p * n + cc].y = g.c * ap.y - g.s * eqy;
+                A[q * n + cc].x = g.s * ap.x + g.c * eqx; A[q * n + cc].y = g.s * ap.y + g.c * eqy;
+            }
+            __syncthreads();
+            // the rotated pair: exact zeros off the diagonal, real diagonal
+            for (int i = tid; i < half; i += nt) {
+                int p, q;
+                pair_of(r, i, p, q);
+                if (q >= n) continue;
+                A[p * n + q].x = T(0); A[p * n + q].y = T(0);
+                A[q * n + p].x = T(0); A[q * n + p].y = T(0);
+                A[p * n + p].y = T(0);
+                A[q * n + q].y = T(0);
+            }
+            __syncthreads();
+        }
+    }
+}
+
 __global__ void k_stage_kappa(DevGeom G, DevParams Pm, DevState D, int S, int SC, const float* z,
                               const double* gram, double* V64) {
     const int s = blockIdx.x, j = blockIdx.y;
@@ -217,47 +332,88 @@ __global__ void k_stage_kappa(DevGeom G, DevParams Pm, DevState D, int S, int SC
     const size_t plane = (size_t)SM * J * Nz;
     const double2* tab = reinterpret_cast<const double2*>(D.tab);
     extern __shared__ double2 sh[];
-    double2* R = sh;                             // K x K upper, row-major
-    double2* ye = R + (size_t)K * K;             // V^H e0 / eb      (K)
+    double2* R = sh;                             // K x K: B, then U^H B U, then its eigenvalues
+    double2* Ue = R + (size_t)K * K;             // K x K eigenvectors (columns)
+    double2* Wk = Ue + (size_t)K * K;            // K x K work: the FP32 solve (A32, U32), then B U
+    float2* A32 = reinterpret_cast<float2*>(Wk);
+    float2* U32 = A32 + (size_t)K * K;
+    double2* ye = Wk + (size_t)K * K;            // V^H e0 / eb      (K)
     double2* vm = ye + K;                        // V^H m^w          (K)
     double2* v4 = vm + K;                        // V^H mu4          (K)
-    double* red = reinterpret_cast<double*>(v4 + K);   // reduction scratch [8]
+    double* dinv = reinterpret_cast<double*>(v4 + K);   // lambda^{-1/2}  (K)
+    double* red = dinv + K;                      // reduction scratch [8]
+    JRot<double>* rot = reinterpret_cast<JRot<double>*>(red + 8);   // Jacobi pair rotations [32]
+    JRot<float>* rot32 = reinterpret_cast<JRot<float>*>(rot);
     const double2* Gm = reinterpret_cast<const double2*>(gram) + (size_t)j * SM * SM;
     // column map c -> s'
     auto col = [&](int c) { return c < s ? c : c + 1; };
-    // R R^H-free Cholesky: R^H R = I + G_{-s}/eb (upper R), right-looking
+    // B = I + G_{-s}/eb (Hermitian), then B = U diag(lambda) U^H
     for (int t = threadIdx.x; t < K * K; t += blockDim.x) {
         const int r = t / K, c = t - r * K;
         double2 g = Gm[col(r) * SM + col(c)];
         g.x /= eb; g.y /= eb;
-        if (r == c) g.x += 1.0;
-        R[t] = g;   // full Hermitian, upper part used
+        if (r == c) { g.x += 1.0; g.y = 0.0; }
+        R[t] = g;
+    }
+    // eigenvectors to FP32 accuracy by FP32 sweeps, then B rotated into that basis in FP64
+    // (nearly diagonal) and finished by FP64 sweeps, which converge quadratically from there
+    for (int t = threadIdx.x; t < K * K; t += blockDim.x) A32[t] = make_float2((float)R[t].x, (float)R[t].y);
+    jacobi_herm<float>(A32, U32, K, rot32, red, true, 1e-10, 16);
+    for (int t = threadIdx.x; t < K * K; t += blockDim.x) Ue[t] = make_double2((double)U32[t].x, (double)U32[t].y);
+    __syncthreads();
+    {   // the FP32 columns are orthonormal to ~1e-5 only: modified Gram-Schmidt in FP64, so
+        // that U^H B U below is a similarity transform of B
+        const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5, nw = blockDim.x >> 5;
+        for (int c = 0; c < K; ++c) {
+            if (wid == 0) {
+                double a = 0.0;
+                for (int r = lane; r < K; r += 32) a += Ue[r * K + c].x * Ue[r * K + c].x + Ue[r * K + c].y * Ue[r * K + c].y;
+                a = warp_sum_d(a);
+                if (lane == 0) red[0] = 1.0 / sqrt(a);
+            }
+            __syncthreads();
+            const double inv = red[0];
+            for (int r = threadIdx.x; r < K; r += blockDim.x) { Ue[r * K + c].x *= inv; Ue[r * K + c].y *= inv; }
+            __syncthreads();
+            for (int c2 = c + 1 + wid; c2 < K; c2 += nw) {
+                double dx = 0.0, dy = 0.0;
+                for (int r = lane; r < K; r += 32) {
+                    const double2 u = zmulc(Ue[r * K + c], Ue[r * K + c2]);
+                    dx += u.x; dy += u.y;
+                }
+                dx = warp_sum_d(dx); dy = warp_sum_d(dy);
+                for (int r = lane; r < K; r += 32) {
+                    const double2 u = zmul(make_double2(dx, dy), Ue[r * K + c]);
+                    Ue[r * K + c2].x -= u.x; Ue[r * K + c2].y -= u.y;
+                }
+            }
+            __syncthreads();
+        }
+    }
+    for (int t = threadIdx.x; t < K * K; t += blockDim.x) {          // Wk = B U
+        const int r = t / K, c = t - r * K;
+        double2 acc = make_double2(0.0, 0.0);
+        for (int m = 0; m < K; ++m) {
+            const double2 u = zmul(R[r * K + m], Ue[m * K + c]);
+            acc.x += u.x; acc.y += u.y;
+        }
+        Wk[t] = acc;
     }
     __syncthreads();
-    for (int k = 0; k < K; ++k) {
-        if (threadIdx.x == 0) {
-            const double d = sqrt(fmax(R[k * K + k].x, 1e-300));
-            R[k * K + k] = make_double2(d, 0.0);
+    for (int t = threadIdx.x; t < K * K; t += blockDim.x) {          // R = U^H (B U)
+        const int r = t / K, c = t - r * K;
+        double2 acc = make_double2(0.0, 0.0);
+        for (int m = 0; m < K; ++m) {
+            const double2 u = zmulc(Ue[m * K + r], Wk[m * K + c]);
+            acc.x += u.x; acc.y += u.y;
         }
-        __syncthreads();
-        const double dk = R[k * K + k].x;
-        for (int c = k + 1 + threadIdx.x; c < K; c += blockDim.x) {
-            const double2 v = R[k * K + c];
-            R[k * K + c] = make_double2(v.x / dk, v.y / dk);
-        }
-        __syncthreads();
-        // trailing update: A[r][c] -= conj(R[k][r]) R[k][c] for k < r <= c
-        const int n = K - k - 1;
-        for (int t = threadIdx.x; t < n * n; t += blockDim.x) {
-            const int r = k + 1 + t / n, c = k + 1 + t % n;
-            if (c >= r) {
-                const double2 u = zmulc(R[k * K + r], R[k * K + c]);
-                R[r * K + c].x -= u.x; R[r * K + c].y -= u.y;
-            }
-        }
-        __syncthreads();
+        R[t] = acc;
     }
-    // V rows: v_k R = m_k (forward substitution over columns); accumulate projections
+    __syncthreads();
+    jacobi_herm<double>(R, Ue, K, rot, red, false, 1e-24, 1);   // one sweep: off-diagonal 1e-5 -> ~1e-10
+    for (int c = threadIdx.x; c < K; c += blockDim.x) dinv[c] = 1.0 / sqrt(fmax(R[c * K + c].x, 1.0));
+    __syncthreads();
+    // V rows: v_k = m_k U diag(lambda)^{-1/2}; accumulate projections
     for (int t = threadIdx.x; t < 3 * K; t += blockDim.x) (t < K ? ye : (t < 2 * K ? vm : v4))[t % K] = make_double2(0, 0);
     if (threadIdx.x < 8) red[threadIdx.x] = 0.0;
     __syncthreads();
@@ -272,13 +428,12 @@ __global__ void k_stage_kappa(DevGeom G, DevParams Pm, DevState D, int S, int SC
         const double2 mw = tab[1 * plane + ((size_t)s * J + j) * Nz + k];
         const double2 m4 = tab[3 * plane + ((size_t)s * J + j) * Nz + k];
         for (int c = 0; c < K; ++c) {
-            double2 acc = tab[0 * plane + ((size_t)col(c) * J + j) * Nz + k];
-            for (int c2 = 0; c2 < c; ++c2) {
-                const double2 u = zmul(Vs[(size_t)k * SC + c2], R[c2 * K + c]);
-                acc.x -= u.x; acc.y -= u.y;
+            double2 acc = make_double2(0.0, 0.0);
+            for (int t = 0; t < K; ++t) {
+                const double2 u = zmul(tab[0 * plane + ((size_t)col(t) * J + j) * Nz + k], Ue[t * K + c]);
+                acc.x += u.x; acc.y += u.y;
             }
-            const double d = R[c * K + c].x;
-            const double2 v = make_double2(acc.x / d, acc.y / d);
+            const double2 v = make_double2(acc.x * dinv[c], acc.y * dinv[c]);
             Vs[(size_t)k * SC + c] = v;
             const double2 a1 = zmulc(v, e0), a2 = zmulc(v, mw), a3 = zmulc(v, m4);
             atomicAdd(&ye[c].x, a1.x); atomicAdd(&ye[c].y, a1.y);
@@ -297,7 +452,6 @@ __global__ void k_stage_kappa(DevGeom G, DevParams Pm, DevState D, int S, int SC
     __syncthreads();
     // second scalar m^H mu4 imaginary part needed too: recompute cheaply below via projections
     // ---- omega test (FP64), a^H A^-1 b = (a^H b - (V^H a)^H (V^H b)/eb)/eb
-    __shared__ double omega_llr;
     __shared__ double mm4_im;
     if (threadIdx.x == 0) mm4_im = 0.0;
     __syncthreads();
@@ -330,7 +484,6 @@ __global__ void k_stage_kappa(DevGeom G, DevParams Pm, DevState D, int S, int SC
         const double2 mAu = make_double2((red[7] - pmu_r / eb) / eb, (mm4_im - pmu_i / eb) / eb);
         const double2 mAe1 = make_double2(mAe0.x - mAu.x, mAe0.y - mAu.y);
         const double llr = (mAe1.x * mAe1.x + mAe1.y * mAe1.y) / (1.0 + mAm) - Q11 + Q00 - log1p(mAm);
-        omega_llr = llr;
         D.llr_w[s * J + j] = llr;
         const double zeta = D.zeta[s * J + j];
         double pr;
@@ -370,29 +523,16 @@ __global__ void k_stage_kappa(DevGeom G, DevParams Pm, DevState D, int S, int SC
         atomicAdd(&rr[0], e0.x * e0.x + e0.y * e0.y);
     }
     __syncthreads();
-    if (threadIdx.x == 0) {
-        // y0 = R^-1 y~0
-        double2 y0[S_CAP_MAX];
-        for (int c = K - 1; c >= 0; --c) {
-            double2 a = ye[c];
-            for (int c2 = c + 1; c2 < K; ++c2) {
-                const double2 u = zmul(R[c * K + c2], y0[c2]);
-                a.x -= u.x; a.y -= u.y;
-            }
-            const double d = R[c * K + c].x;
-            y0[c] = make_double2(a.x / d, a.y / d);
-        }
-        float2* ky = D.ky0 + ((size_t)s * J + j) * SC;
-        for (int c = 0; c < SC; ++c) ky[c] = (c < K) ? make_float2((float)y0[c].x, (float)y0[c].y) : make_float2(0.f, 0.f);
-        D.kJ0[s * J + j] = rr[0] / eb;   // the |y|^2 part enters the particle kernel as a difference
-    }
-    // R as FP32, padded with the identity
-    float2* kR = D.kR + ((size_t)s * J + j) * SC * SC;
-    for (int t = threadIdx.x; t < SC * SC; t += blockDim.x) {
-        const int r = t / SC, c = t - r * SC;
-        float2 v = make_float2(r == c ? 1.f : 0.f, 0.f);
-        if (r < K && c < K && c >= r) v = make_float2((float)R[r * K + c].x, (float)R[r * K + c].y);
-        kR[t] = v;
+    if (threadIdx.x == 0) D.kJ0[s * J + j] = rr[0] / eb;   // the |y|^2 part enters the particle kernel as a difference
+    // per-particle amplitude terms in the eigenbasis: with y~0 = V^H e0/eb and x = V^H psi,
+    // y0^H x_amp = sum_c lambda_c^{-1} conj(y~0_c) x_c and |x_amp|^2 = sum_c lambda_c^{-1} |x_c|^2:
+    // w_c = lambda_c^{-1} y~0_c and lambda_c^{-1} (padded with zeros)
+    float2* ky = D.ky0 + ((size_t)s * J + j) * SC;
+    float2* kd = D.kdl + ((size_t)s * J + j) * SC;
+    for (int c = threadIdx.x; c < SC; c += blockDim.x) {
+        const double il = (c < K) ? dinv[c] * dinv[c] : 0.0;
+        ky[c] = (c < K) ? make_float2((float)(il * ye[c].x), (float)(il * ye[c].y)) : make_float2(0.f, 0.f);
+        kd[c] = make_float2((float)il, 0.f);
     }
 }
 
@@ -524,7 +664,8 @@ void launch_stage(const DevGeom& G, const DevParams& Pm, const DevState& D, int 
     const int gx = min(64, (npair + 7) / 8);
     k_gram<<<dim3(gx, G.J), 256, 0, st>>>(G, Pm, D, S, z, gram, nu_b);
     const int K = S - 1;
-    const size_t sm1 = ((size_t)K * K + 3 * (size_t)K) * sizeof(double2) + 8 * sizeof(double);
+    const size_t sm1 = (3 * (size_t)K * K + 3 * (size_t)K) * sizeof(double2) + ((size_t)K + 8) * sizeof(double) +
+                       32 * sizeof(JRot<double>);
     cudaFuncSetAttribute(k_stage_kappa, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm1);
     k_stage_kappa<<<dim3(S, G.J), 256, sm1, st>>>(G, Pm, D, S, SC, z, gram, V64);
     const size_t sm2 = ((size_t)S * S + 3 * (size_t)S) * sizeof(double2);
