@@ -42,9 +42,10 @@ SMS = 152
 
 def kappa_flops(P, S, J, Nz):
     """Algorithmic FP32 flops of one launch of the PF likelihood kernel: per (p, s, j)
-    two passes over Nz elements against S-1 basis columns (+ the residual column),
-    8 flops per complex multiply-add, plus the (S-1)^2/2 triangular solve."""
-    per = 8 * Nz * S + 8 * Nz * (S - 1) + 8 * (S - 1) * S / 2 + 40 * Nz
+    two passes over Nz elements against the S-1 (eigen-whitened, orthogonal) basis
+    columns plus the residual column, 8 flops per complex multiply-add, the steering
+    vector and residual element work (40 per element) and the O(S) amplitude sums."""
+    per = 8 * Nz * S + 8 * Nz * (S - 1) + 40 * Nz + 16 * (S - 1)
     return float(P) * S * J * per
 
 

@@ -547,14 +547,15 @@ __device__ inline cff gent_value(const gent& g) {
 // shared memory of k_iota_blk (bytes): colbuf [2][64] cff, colh [2][64] float2, pivbuf [2][2] ff, red [16]
 // double, A packed lower [S(S+1)/2] cff, then float2 z [Nz], factors [S][nfac | 1], cm [S], g [S], L packed [S(S+1)/2]
 // (also the partial sums g [S][Nf] before the Gram), then float amplitude [S],
-// A d [S], d [S], 1/L_kk [64]
+// A d [S], d [S], 1/L_kk [64], pivots [64] ff
 __host__ __device__ inline size_t iota_blk_lsize(int S, int Nf) {
     const size_t a = (size_t)S * (S + 1) / 2, b = (size_t)S * Nf;
     return a > b ? a : b;
 }
 __host__ __device__ inline size_t iota_blk_smem(int S, int nfac, int Nf, int Nz) {
     return 2 * IB_SMAX * 16 + 2 * IB_SMAX * 8 + 4 * 8 + 16 * 8 + (size_t)S * (S + 1) / 2 * 16 +
-           ((size_t)Nz + (size_t)S * (nfac | 1) + 2 * (size_t)S + iota_blk_lsize(S, Nf)) * 8 + 3 * (size_t)S * 4 + IB_SMAX * 4;
+           ((size_t)Nz + (size_t)S * (nfac | 1) + 2 * (size_t)S + iota_blk_lsize(S, Nf)) * 8 + 3 * (size_t)S * 4 + IB_SMAX * 4 +
+           IB_SMAX * 8;
 }
 
 template <int NCG>
@@ -579,6 +580,7 @@ __global__ void __launch_bounds__(32 * NCG, (NCG == 4 ? 3 : 2)) k_iota_blk(DevGe
     float* adS = amp + S;                                         // [S] A d
     float* dS = adS + S;                                          // [S] d
     float* ild = dS + S;                                          // [IB_SMAX] 1 / L_kk
+    ff* pivs = reinterpret_cast<ff*>(ild + IB_SMAX);              // [IB_SMAX] pivots
     const int tid = threadIdx.x, lane = tid & 31, wid = tid >> 5;
     const int cg = lane % NCG;
     const int rp = wid * (32 / NCG) + lane / NCG;
@@ -672,8 +674,9 @@ __global__ void __launch_bounds__(32 * NCG, (NCG == 4 ? 3 : 2)) k_iota_blk(DevGe
             }
             // rhs_a = d_a (g_a - sum_b G_ab pi_b mu_b), FP32
             float2 rhs = make_float2(0.f, 0.f);
-            if (tid < S) {
-                const int a = tid;
+            const int fst = tid - 64;   // forward-substitution row of this thread (warps 2-3)
+            if (fst >= 0 && fst < S) {
+                const int a = fst;
                 float2 acc = gS[a];
                 for (int b = 0; b < S; ++b) {
                     const float2 e = (b <= a) ? Lsm[tri(a, b)] : make_float2(Lsm[tri(b, a)].x, -Lsm[tri(b, a)].y);
@@ -685,7 +688,6 @@ __global__ void __launch_bounds__(32 * NCG, (NCG == 4 ? 3 : 2)) k_iota_blk(DevGe
             __syncthreads();
             // Cholesky with exactly accumulated trailing entries; log det from the
             // float-float product of the pivots (exponent kept apart)
-            ffexp det{ff{1.f, 0.f}, 0};
             for (int k = 0; k < S; ++k) {
                 const int cur = k & 1, nxt = cur ^ 1;
                 const cff* col = colbuf + cur * IB_SMAX;
@@ -702,22 +704,22 @@ __global__ void __launch_bounds__(32 * NCG, (NCG == 4 ? 3 : 2)) k_iota_blk(DevGe
                 const int kc = k - cg;
                 if (kc >= 0 && kc % NCG == 0) { liveA &= ~(1u << (kc / NCG)); liveB &= ~(1u << (kc / NCG)); }
                 if (tid == 0) {
-                    ffexp_mul(det, piv);
+                    pivs[k] = piv;
                     Lsm[tri(k, k)] = make_float2(lkk, 0.f);
                     ild[k] = il;
                 }
                 // forward substitution L u = rhs, one column behind the factorisation:
                 // row i takes column k-1 (published last step), then row k yields u_k
-                if (tid < S && tid >= k) {
+                if (fst >= k && fst < S) {
                     if (k > 0) {
-                        const float2 u = cmul(Lsm[tri(tid, k - 1)], gS[k - 1]);
+                        const float2 u = cmul(Lsm[tri(fst, k - 1)], gS[k - 1]);
                         rhs.x -= u.x; rhs.y -= u.y;
                     }
-                    if (tid == k) gS[k] = make_float2(rhs.x * il, rhs.y * il);
+                    if (fst == k) gS[k] = make_float2(rhs.x * il, rhs.y * il);
                 }
-                {
-                    const int i = k + 1 + tid;
-                    if (i < S) {
+                {   // FP32 column k of L for the solves (warps 4-5)
+                    const int i = k + 1 + (tid - 128);
+                    if (tid >= 128 && i < S) {
                         const cff v = col[i];
                         Lsm[tri(i, k)] = make_float2((v.re.hi + v.re.lo) * il, (v.im.hi + v.im.lo) * il);
                     }
@@ -753,8 +755,19 @@ __global__ void __launch_bounds__(32 * NCG, (NCG == 4 ? 3 : 2)) k_iota_blk(DevGe
                 }
                 __syncthreads();
             }
-            // back substitution L^H y = u (warp 0; lane owns rows lane and lane + 32)
+            // back substitution L^H y = u (warp 0; lane owns rows lane and lane + 32); log det
+            // from the float-float product of the pivots (exponents apart)
             if (wid == 0) {
+                ffexp det{ff{1.f, 0.f}, 0};
+                for (int k = lane; k < S; k += 32) ffexp_mul(det, pivs[k]);
+                #pragma unroll
+                for (int o = 16; o > 0; o >>= 1) {
+                    const ff om{__shfl_xor_sync(0xffffffffu, det.m.hi, o), __shfl_xor_sync(0xffffffffu, det.m.lo, o)};
+                    const int oe = __shfl_xor_sync(0xffffffffu, det.e, o);
+                    ffexp_mul(det, om);
+                    det.e += oe;
+                }
+                if (lane == 0) red[1] = ffexp_log(det);
                 float2 r0 = (lane < S) ? gS[lane] : make_float2(0.f, 0.f);
                 float2 r1 = (lane + 32 < S) ? gS[lane + 32] : make_float2(0.f, 0.f);
                 const float i0 = (lane < S) ? ild[lane] : 0.f, i1 = (lane + 32 < S) ? ild[lane + 32] : 0.f;
@@ -805,7 +818,7 @@ __global__ void __launch_bounds__(32 * NCG, (NCG == 4 ? 3 : 2)) k_iota_blk(DevGe
                 double rrs = 0.0;
                 for (int w2 = 0; w2 < IB_T / 32; ++w2) rrs += red[8 + w2];
                 const double lg = lg_eb[j];
-                total += -(rrs * inv_eb[j] + red[0]) - (ffexp_log(det) - S * lg) - Nz * (LOG_PI + lg);
+                total += -(rrs * inv_eb[j] + red[0]) - (red[1] - S * lg) - Nz * (LOG_PI + lg);
             }
         }
         if (tid == 0) D.lw_x[pp] = total;
