@@ -179,6 +179,9 @@ bp_status bp_init(const bp_geometry* geom, const bp_params* prm, int P, int S_ma
     ok &= dalloc(h, &D.kV, (size_t)S_max * J * Nz * SCA);
     ok &= dalloc(h, &D.kr0l, (size_t)S_max * J * Nz);
     ok &= dalloc(h, &D.kdl, (size_t)S_max * J * SCA);
+    ok &= dalloc(h, &D.kerr, 1);
+    D.kB = nullptr;
+    if (kappa_tc_ok(h->G, SCA)) ok &= dalloc(h, &D.kB, kappa_btile_floats(h->G, S_max));
     ok &= dalloc(h, &D.ky0, (size_t)S_max * J * SCA);
     ok &= dalloc(h, &D.kJ0, (size_t)S_max * J);
     ok &= dalloc(h, &D.nu_T, (size_t)J * 4 * S_max);
@@ -267,6 +270,7 @@ bp_status bp_update(bp_handle* h, const float* z_dev) {
     launch_table(h->G, h->Pm, D, S, nsplit, h->st);
     mark(h, 3);
     launch_stage(h->G, h->Pm, D, S, h->SCA, z_dev, h->gram, h->nu_b, h->V64, h->st);
+    if (S > 32) launch_kappa_btile(h->G, D, S, h->SCA, h->st);   // B tiles of the tensor-core variant (SC = 64)
     mark(h, 4);
     launch_kappa(h->G, h->Pm, D, S, h->SCA, h->st);
     mark(h, 5);
@@ -282,7 +286,7 @@ bp_status bp_update(bp_handle* h, const float* z_dev) {
         cudaEventRecord(h->ev[BP_PROF_STAGES], h->st);
         for (int i = 1; i < BP_PROF_STAGES; ++i) h->ev_valid[i] = true;
     }
-    h->launches += 1 + 3 + 3 + 1 + 2 + 1 + 5 + 3;
+    h->launches += 1 + 3 + 3 + 1 + 2 + 1 + 5 + 3 + ((S > 32 && D.kB && kappa_tc_ok(h->G, h->SCA)) ? 1 : 0);
     h->D.cur = 1 - h->D.cur;
     h->S_upd = S;
     h->phase = 0;
@@ -300,9 +304,16 @@ bp_status bp_update(bp_handle* h, const float* z_dev) {
 bp_status bp_estimate(bp_handle* h, bp_estimate_out* o) {
     if (!h || !o) return BP_ERR_INVALID_ARG;
     const EstLayout E{h->S_max, h->J};
+    // h_ctrl has room for S_max more ints; its last slot receives the kernels' timeout flag
+    int* kerr_host = h->h_ctrl + 3 + h->S_max;
     if (cudaMemcpyAsync(h->h_est, h->D.est, E.total() * sizeof(double), cudaMemcpyDeviceToHost, h->st) != cudaSuccess ||
+        cudaMemcpyAsync(kerr_host, h->D.kerr, sizeof(int), cudaMemcpyDeviceToHost, h->st) != cudaSuccess ||
         cudaStreamSynchronize(h->st) != cudaSuccess)
         return fail(h, BP_ERR_CUDA, std::string("bp_estimate: ") + cudaGetErrorString(cudaGetLastError()));
+    if (*kerr_host != 0) {
+        cudaMemsetAsync(h->D.kerr, 0, sizeof(int), h->st);
+        return fail(h, BP_ERR_TIMEOUT, "bp_estimate: a tensor-core wait of the last update gave up (results invalid)");
+    }
     const double* e = h->h_est;
     o->n = (int)e[E.n()];
     o->S = (int)e[E.S()];

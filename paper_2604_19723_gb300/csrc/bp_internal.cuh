@@ -335,6 +335,8 @@ struct DevState {
     float2* kV;       // [S_max][J][Nz][S_cap]   whitened basis, column S_cap-1 = r0 (FP32 part)
     float2* kr0l;     // [S_max][J][Nz]          low part of r0 (r0 = FP32 part + low part)
     float2* kdl;      // [S_max][J][S_cap]       1/lambda_c of the eigen-whitened basis (.x; zero-padded)
+    float* kB;        // [S_max][J][Nf][hi, lo][128 x 2 My Mz] TF32 B tiles of the tensor-core pass 1 (or null)
+    int* kerr;        // nonzero after a bounded wait of a kernel gave up (reported by bp_estimate)
     float2* ky0;      // [S_max][J][S_cap]       w_c = y~0_c / lambda_c, y~0 = V^H e0 / eta_bar
     double* kJ0;      // [S_max][J]              |r0|^2/eta_bar
     // nu stage outputs (per j)

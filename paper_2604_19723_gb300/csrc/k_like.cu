@@ -23,6 +23,7 @@
 // per-(p, s, j) geometry records of k_geom (FP64 distance and direction).
 #include "bp_internal.cuh"
 #include "bp_kernels.cuh"
+#include "tc_sm100.cuh"
 
 namespace bp {
 
@@ -33,15 +34,30 @@ namespace bp {
 // 1/lambda_c and w_c = y~0_c/lambda_c beside it.  The basis columns are orthogonal,
 // so every amplitude term is a diagonal sum over the columns.
 
-template <int SC>
-__global__ void __launch_bounds__(256, (SC <= 16 ? 2 : 1)) k_kappa(DevGeom G, DevParams Pm, DevState D, int S, int SCA, int fch) {
+// With TC (64 basis columns, 2*My*Mz in {8, 16, 32}) pass 1 runs on the tensor cores:
+// per frequency, the 256 particles' steering values (Re/Im interleaved, split into TF32
+// high and low parts) form two 128-row A tiles in shared memory, the matching rows of
+// [[Re V, Im V], [Im V, -Re V]] arrive as prebuilt TF32 hi/lo B tiles by a bulk copy,
+// and one thread issues hi.hi + hi.lo + lo.hi MMAs (3xTF32, FP32-level accuracy) into a
+// 256-column TMEM accumulator whose lane is the particle; h = psi^H V is read back from
+// TMEM.  Pass 2 and everything after are the same CUDA-core code for both variants.
+constexpr int KAPPA_TC_WAIT = 1 << 20;   // polls of an mbarrier before the kernel gives up
+
+template <int SC, bool TC>
+__global__ void __launch_bounds__(256, (SC <= 16 ? 2 : 1)) k_kappa(DevGeom G, DevParams Pm, DevState D, int S, int SCA, int fch,
+                                                                   const float* __restrict__ Bt) {
     constexpr int KT = 256;
     constexpr int NC = SC - 1;           // basis columns (zero beyond S-2)
     constexpr int NP = SC / 2;           // column pairs per row
-    extern __shared__ float4 sm4[];
+    extern __shared__ __align__(1024) float4 sm4[];
     const int s = blockIdx.y;
     const int P = Pm.P, J = G.J, Nz = G.Nz, Nm = G.My * G.Mz;
-    float4* Vs = sm4;                                                  // [Nz][NP]
+    const int KC = 2 * Nm;                                             // real K per frequency (TC)
+    float* sA = reinterpret_cast<float*>(sm4);                         // TC: [2 tiles][hi, lo][128 x KC]
+    float* sB = sA + (TC ? 4 * 128 * KC : 0);                          // TC: [hi, lo][128 x KC]
+    uint64_t* mbar = reinterpret_cast<uint64_t*>(sB + (TC ? 2 * 128 * KC : 0));   // TC: [2]
+    uint32_t* tslot = reinterpret_cast<uint32_t*>(mbar + (TC ? 2 : 0));          // TC: TMEM base
+    float4* Vs = TC ? reinterpret_cast<float4*>(sA + 6 * 128 * KC + 8) : sm4;    // [Nz][NP]
     float2* dls = reinterpret_cast<float2*>(Vs + (size_t)Nz * NP);     // [SC] 1/lambda_c (.x)
     float2* y0s = dls + SC;                                            // [SC] w_c
     float2* fac = y0s + SC;                                            // [nfac][KT]
@@ -50,6 +66,17 @@ __global__ void __launch_bounds__(256, (SC <= 16 ? 2 : 1)) k_kappa(DevGeom G, De
     const int p = blockIdx.x * KT + tid;
     const bool act = p < P;
     const int pp = act ? p : 0;
+    uint32_t tmem = 0, n_commit = 0, n_bulk = 0;
+    bool bad = false;
+    const uint32_t mbar_mma = TC ? tc::smem_u32(&mbar[0]) : 0u, mbar_b = TC ? tc::smem_u32(&mbar[1]) : 0u;
+    if constexpr (TC) {
+        if ((tid >> 5) == 0) tc::tmem_alloc(tslot, 256);
+        if (tid == 0) { tc::mbar_init(mbar_mma, 1); tc::mbar_init(mbar_b, 1); tc::mbar_init_fence(); }
+        tc::fence_before_sync();
+        __syncthreads();
+        tc::fence_after_sync();
+        tmem = *tslot;
+    }
     const float* ph = D.phi[D.cur] + (size_t)s * 6 * P;
     const float4* geo_s = D.geo + (size_t)s * J * P;
     const float2* geol_s = D.geo_lo + (size_t)s * J * P;
@@ -93,6 +120,85 @@ __global__ void __launch_bounds__(256, (SC <= 16 ? 2 : 1)) k_kappa(DevGeom G, De
         for (int c = 0; c < NC; ++c) h[c] = make_float2(0.f, 0.f);
         float2 pr = make_float2(0.f, 0.f);
         float nps = 0.f;
+        if constexpr (TC) {
+            const int tile = tid >> 7, row = tid & 127, warp = tid >> 5;
+            float* aHi = sA + (size_t)(tile * 2 + 0) * 128 * KC;
+            float* aLo = sA + (size_t)(tile * 2 + 1) * 128 * KC;
+            const size_t bchunk = (size_t)2 * 128 * KC;                // floats per frequency (hi + lo)
+            const float* gB = Bt + ((size_t)s * J + j) * G.Nf * bchunk;
+            const uint32_t idesc = tc::idesc_tf32_f32(128, 128);
+            const uint32_t sbo = (uint32_t)(KC / 4) * 128u;
+            for (int f = 0; f < G.Nf; ++f) {
+                // the A and B buffers are free once the previous frequency's MMAs completed
+                if (n_commit > 0 && !tc::mbar_wait(mbar_mma, (n_commit - 1) & 1u, KAPPA_TC_WAIT)) bad = true;
+                if (tid == 0 && !bad) {
+                    tc::mbar_expect_tx(mbar_b, (uint32_t)(bchunk * 4));
+                    tc::bulk_g2s(tc::smem_u32(sB), gB + (size_t)f * bchunk, (uint32_t)(bchunk * 4), mbar_b);
+                }
+                const float2 cb = cmul(Fc, fb[f * KT]);
+                for (int y = 0; y < G.My; ++y) {
+                    const float2 w = cmul(cb, fy[y * KT]);
+                    for (int m = 0; m < G.Mz; m += 2) {
+                        const float2 p0 = cmul(w, fz[m * KT]), p1 = cmul(w, fz[(m + 1) * KT]);
+                        nps += p0.x * p0.x + p0.y * p0.y + p1.x * p1.x + p1.y * p1.y;
+                        const float4 hi = make_float4(tc::tf32_rn(p0.x), tc::tf32_rn(p0.y), tc::tf32_rn(p1.x), tc::tf32_rn(p1.y));
+                        const float4 lo = make_float4(tc::tf32_rn(p0.x - hi.x), tc::tf32_rn(p0.y - hi.y),
+                                                      tc::tf32_rn(p1.x - hi.z), tc::tf32_rn(p1.y - hi.w));
+                        const int off = tc::core_off(row, 2 * (y * G.Mz + m), KC) >> 2;
+                        *reinterpret_cast<float4*>(aHi + off) = hi;
+                        *reinterpret_cast<float4*>(aLo + off) = lo;
+                    }
+                }
+                tc::fence_async_smem();
+                tc::fence_before_sync();
+                __syncthreads();
+                tc::fence_after_sync();
+                if (tid == 0 && !bad) {
+                    if (!tc::mbar_wait(mbar_b, n_bulk & 1u, KAPPA_TC_WAIT)) bad = true;
+                    if (!bad) {
+                        const uint32_t bH = tc::smem_u32(sB), bL = tc::smem_u32(sB + 128 * KC);
+                        for (int t = 0; t < 2; ++t) {
+                            const uint32_t aH = tc::smem_u32(sA + (size_t)(t * 2) * 128 * KC);
+                            const uint32_t aL = tc::smem_u32(sA + (size_t)(t * 2 + 1) * 128 * KC);
+                            for (int ks = 0; ks < KC / 8; ++ks) {
+                                const uint32_t o = (uint32_t)ks * 256u;
+                                const uint64_t dAH = tc::smem_desc(aH + o, 128, sbo), dAL = tc::smem_desc(aL + o, 128, sbo);
+                                const uint64_t dBH = tc::smem_desc(bH + o, 128, sbo), dBL = tc::smem_desc(bL + o, 128, sbo);
+                                const uint32_t d = tmem + (uint32_t)(t * 128);
+                                tc::mma_tf32(d, dAH, dBH, idesc, f > 0 || ks > 0);
+                                tc::mma_tf32(d, dAH, dBL, idesc, true);
+                                tc::mma_tf32(d, dAL, dBH, idesc, true);
+                            }
+                        }
+                        tc::mma_commit(mbar_mma);
+                    }
+                }
+                ++n_commit;
+                ++n_bulk;
+            }
+            if (!tc::mbar_wait(mbar_mma, (n_commit - 1) & 1u, KAPPA_TC_WAIT)) bad = true;
+            tc::fence_after_sync();
+            // h from TMEM: warp w reads lanes 32 (w mod 4) + lane of tile w / 4, i.e. particle tid;
+            // columns 0..63 hold Re h_c (c = 63: psi^H r0), 64..127 Im h_c
+            const uint32_t tb = tmem + ((uint32_t)((warp & 3) * 32) << 16) + (uint32_t)(tile * 128);
+            uint32_t v[32];
+            tc::tmem_ld32(tb + 0, v); tc::tmem_ld_wait();
+            #pragma unroll
+            for (int i = 0; i < 32; ++i) h[i].x = __uint_as_float(v[i]);
+            tc::tmem_ld32(tb + 32, v); tc::tmem_ld_wait();
+            #pragma unroll
+            for (int i = 0; i < 31; ++i) h[32 + i].x = __uint_as_float(v[i]);
+            pr.x = __uint_as_float(v[31]);
+            tc::tmem_ld32(tb + 64, v); tc::tmem_ld_wait();
+            #pragma unroll
+            for (int i = 0; i < 32; ++i) h[i].y = __uint_as_float(v[i]);
+            tc::tmem_ld32(tb + 96, v); tc::tmem_ld_wait();
+            #pragma unroll
+            for (int i = 0; i < 31; ++i) h[32 + i].y = __uint_as_float(v[i]);
+            pr.y = __uint_as_float(v[31]);
+            tc::fence_before_sync();
+            if (bad && (tid & 31) == 0) atomicOr(D.kerr, 1);
+        } else
         for (int f0 = 0; f0 < G.Nf; f0 += fch) {
           if (fch < G.Nf) { __syncthreads(); stage_rows(f0); __syncthreads(); }
           for (int f = f0; f < min(G.Nf, f0 + fch); ++f) {
@@ -237,6 +343,12 @@ __global__ void __launch_bounds__(256, (SC <= 16 ? 2 : 1)) k_kappa(DevGeom G, De
         delta_sum += dlt;
     }
     if (act) D.lw_y[(size_t)s * P + p] = delta_sum;
+    if constexpr (TC) {
+        tc::fence_before_sync();
+        __syncthreads();
+        tc::fence_after_sync();
+        if ((tid >> 5) == 0) tc::tmem_dealloc(tmem, 256);
+    }
 }
 
 // ---------------------------------------------------------------- iota (warp per particle)
@@ -856,19 +968,64 @@ __global__ void k_nu(DevGeom G, DevParams Pm, DevState D, int S) {
     D.lw_eta[(size_t)j * P + p] = lnu;
 }
 
+// B tiles of the tensor-core pass 1, once per (s, j, frequency): rows n of
+// [[Re V, Im V], [Im V, -Re V]]^T (n < 64: Re h_n, n >= 64: Im h_{n-64}) against the real
+// K index 2e + part of the frequency's elements e (part 0 = Re psi, 1 = Im psi), split into
+// TF32 high and low parts, in the K-major core-matrix layout; [hi, lo] per chunk.
+__global__ void k_kappa_btile(DevGeom G, DevState D, int SCA, float* __restrict__ Bt) {
+    const int s = blockIdx.x, j = blockIdx.y, f = blockIdx.z;
+    const int J = G.J, Nz = G.Nz, Nm = G.My * G.Mz, KC = 2 * Nm;
+    const float2* V = D.kV + ((size_t)s * J + j) * Nz * SCA;
+    float* out = Bt + (((size_t)s * J + j) * G.Nf + f) * 2 * 128 * KC;
+    for (int t = threadIdx.x; t < 128 * KC; t += blockDim.x) {
+        const int n = t / KC, kk = t - n * KC;
+        const int e = kk >> 1, part = kk & 1;
+        const float2 v = V[(size_t)(f * Nm + e) * SCA + (n & 63)];
+        const float b = (n < 64) ? (part == 0 ? v.x : v.y) : (part == 0 ? v.y : -v.x);
+        const float hi = tc::tf32_rn(b);
+        const int off = tc::core_off(n, kk, KC) >> 2;
+        out[off] = hi;
+        out[128 * KC + off] = tc::tf32_rn(b - hi);
+    }
+}
+
+// the tensor-core variant applies with 64 basis columns (SCA = 64) and 2 My Mz in {8, 16, 32}
+bool kappa_tc_ok(const DevGeom& G, int SCA) {
+    const int KC = 2 * G.My * G.Mz;
+    return SCA == 64 && (KC == 8 || KC == 16 || KC == 32);
+}
+size_t kappa_btile_floats(const DevGeom& G, int S_max) {
+    return (size_t)S_max * G.J * G.Nf * 2 * 128 * (2 * G.My * G.Mz);
+}
+void launch_kappa_btile(const DevGeom& G, const DevState& D, int S, int SCA, cudaStream_t st) {
+    if (!D.kB || !kappa_tc_ok(G, SCA)) return;
+    k_kappa_btile<<<dim3(S, G.J, G.Nf), 256, 0, st>>>(G, D, SCA, D.kB);
+}
+
 template <int SC>
 static void launch_kappa_sc(const DevGeom& G, const DevParams& Pm, const DevState& D, int S, int SCA, cudaStream_t st) {
     const int nfac = G.Nf + G.My + G.Mz;
     const int Nm = G.My * G.Mz;
     const size_t fixed = (2 * (size_t)SC + (size_t)nfac * 256) * sizeof(float2);
     const size_t per_f = (size_t)Nm * (SC + 1) * sizeof(float2);   // V rows and the low part of r0
+    dim3 grid((Pm.P + 255) / 256, S);
+    if constexpr (SC == 64) {
+        if (D.kB && kappa_tc_ok(G, SCA)) {
+            const size_t tcb = (size_t)6 * 128 * (2 * Nm) * sizeof(float) + 32;
+            const size_t smem = tcb + fixed + (size_t)G.Nf * per_f;
+            if (smem <= 227 * 1024) {
+                cudaFuncSetAttribute(k_kappa<SC, true>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+                k_kappa<SC, true><<<grid, 256, smem, st>>>(G, Pm, D, S, SCA, G.Nf, D.kB);
+                return;
+            }
+        }
+    }
     const size_t limit = 200 * 1024;
     int fch = G.Nf;
     while (fch > 1 && fixed + fch * per_f > limit) fch = (fch + 1) / 2;
     const size_t smem = fixed + fch * per_f;
-    cudaFuncSetAttribute(k_kappa<SC>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
-    dim3 grid((Pm.P + 255) / 256, S);
-    k_kappa<SC><<<grid, 256, smem, st>>>(G, Pm, D, S, SCA, fch);
+    cudaFuncSetAttribute(k_kappa<SC, false>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    k_kappa<SC, false><<<grid, 256, smem, st>>>(G, Pm, D, S, SCA, fch, nullptr);
 }
 
 void launch_kappa(const DevGeom& G, const DevParams& Pm, const DevState& D, int S, int SCA, cudaStream_t st) {
@@ -877,7 +1034,6 @@ void launch_kappa(const DevGeom& G, const DevParams& Pm, const DevState& D, int 
     else if (S <= 32) launch_kappa_sc<32>(G, Pm, D, S, SCA, st);
     else launch_kappa_sc<64>(G, Pm, D, S, SCA, st);
 }
-
 
 // S below which the FP32 path runs first and only flagged particles are redone
 constexpr int IOTA_FF_ALL_S = 24;
