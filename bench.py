@@ -73,15 +73,15 @@ def a5_flops(P, S, J, Nz):
 # a single-pass metric set, at the full size of the workload), valid while the kernel
 # sources hash to the recorded value.
 TRAFFIC_RECORDS = {
-    "k_kappa": {"workload": "scale_64x100k", "P": 100000, "bytes": 774.12e6,
-                "sources_sha256": "7c0a3118863fb03d6138f9dd258951cac1ab54a11095331d3e60e99a13d5bf5c",
+    "k_kappa": {"workload": "scale_64x100k", "P": 100000, "bytes": None,
+                "sources_sha256": "71144f8c837765e572898911b49f75379b1b8715cd23571e31d5f702c58cd3f6",
                 "profile": "profiles/dram_scale_64x100k.md"},
-    "k_iota_blk": {"workload": "scale_64x100k", "P": 100000, "bytes": 707.58e6,
-                   "sources_sha256": "7c0a3118863fb03d6138f9dd258951cac1ab54a11095331d3e60e99a13d5bf5c",
+    "k_iota_blk": {"workload": "scale_64x100k", "P": 100000, "bytes": 712.06e6,
+                   "sources_sha256": "71144f8c837765e572898911b49f75379b1b8715cd23571e31d5f702c58cd3f6",
                    "profile": "profiles/dram_scale_64x100k.md"},
 }
 KERNEL_SOURCES = ("paper_2604_19723_gb300/csrc/k_like.cu", "paper_2604_19723_gb300/csrc/bp_kernels.cuh",
-                  "paper_2604_19723_gb300/csrc/bp_internal.cuh")
+                  "paper_2604_19723_gb300/csrc/bp_internal.cuh", "paper_2604_19723_gb300/csrc/tc_sm100.cuh")
 
 
 def kernel_sources_sha256():
