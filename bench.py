@@ -73,11 +73,11 @@ def a5_flops(P, S, J, Nz):
 # a single-pass metric set, at the full size of the workload), valid while the kernel
 # sources hash to the recorded value.
 TRAFFIC_RECORDS = {
-    "k_kappa": {"workload": "scale_64x100k", "P": 100000, "bytes": None,
-                "sources_sha256": "71144f8c837765e572898911b49f75379b1b8715cd23571e31d5f702c58cd3f6",
+    "k_kappa": {"workload": "scale_64x100k", "P": 100000, "bytes": 858.85e6,
+                "sources_sha256": "2a16276e012f03d36121bddc626aca6805a32153822d36a6bb4b35a65ae8ff36",
                 "profile": "profiles/dram_scale_64x100k.md"},
     "k_iota_blk": {"workload": "scale_64x100k", "P": 100000, "bytes": 712.06e6,
-                   "sources_sha256": "71144f8c837765e572898911b49f75379b1b8715cd23571e31d5f702c58cd3f6",
+                   "sources_sha256": "2a16276e012f03d36121bddc626aca6805a32153822d36a6bb4b35a65ae8ff36",
                    "profile": "profiles/dram_scale_64x100k.md"},
 }
 KERNEL_SOURCES = ("paper_2604_19723_gb300/csrc/k_like.cu", "paper_2604_19723_gb300/csrc/bp_kernels.cuh",
@@ -201,6 +201,24 @@ def cpu_baseline(wl, g, prm, scn, sample_P, z_host):
 def run_reference(args, rank):
     """Reference arm: the FP64 oracle on the host cores, bounded sample per step."""
     if rank != 0:
+        return
+    if args.workload == "batched":
+        sc, scns = batched_inputs(args, 2)
+        vals = []
+        for i in range(args.warmup + args.steps):
+            v, t = batched_oracle_sample(sc, scns, args.ref_particles, 2)
+            if i >= args.warmup:
+                vals.append(v)
+        value = float(np.mean(vals))
+        cores = os.cpu_count() or 1
+        smp = f"one predict+update of {args.ref_particles} particles of each of the first 2 scenarios per step"
+        print(json.dumps({"metric": METRIC, "value": value, "unit": UNIT, "n_gpus": args.gpus, "steps": args.steps,
+                          "warmup": args.warmup, "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
+                          "dtype": "f64", "data": "synthetic", "impl": "reference",
+                          "config": {"workload": "batched", "scenarios": len(sc),
+                                     "parallelism": "oracle on the host cores", "sample": smp},
+                          "cpu_baseline": {"value": value, "unit": UNIT, "cores": cores, "kind": "oracle", "sample": smp},
+                          "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}))
         return
     wl, g, prm, scn = make_inputs(args.workload, args.warmup + args.steps)
     from oracle import synth
@@ -363,6 +381,172 @@ def run_gpu(args, rank, world):
         print(json.dumps(out))
 
 
+# ---------------------------------------------------------------- batched scenarios
+def batched_inputs(args, steps):
+    """Scenario shapes, truths and the observations of `steps` steps, synthesised on the
+    GPU per scenario and concatenated per step in scenario order."""
+    sc = W.batched_scenarios(args.scenarios, seed=21)
+    scns = []
+    for d in sc:
+        scns.append(W.make_scenario(d["geom"], d["params"], N=steps + 1, K=d["S"] - 1, seed=d["seed"],
+                                    snr_db=20.0, visibility=0.8, clutter_mean=0.0))
+    return sc, scns
+
+
+def batched_oracle_sample(sc, scns, sample_P, n_scen):
+    """The FP64 oracle on the host cores: one predict + update of sample_P particles of
+    each of the first n_scen scenarios (their own S, J, Nz); updates/s of the sample."""
+    from oracle import beliefs, messages_woodbury, model, synth
+    done, t = 0, 0.0
+    for d, scn in list(zip(sc, scns))[:n_scen]:
+        eta = synth.noise_variance(scn)
+        z = synth.observe(scn, 1, eta, d["seed"] + 17)
+        st = W.state_near_truth(scn, P=sample_P, S=d["S"], n=0, seed=d["seed"] + 7, eta_true=eta,
+                                pos_std=0.01, sfv_std=0.01)
+        t0 = time.perf_counter()
+        pred = model.predict(st, d["params"], d["geom"].J, seed=d["seed"], S_max=d["S"])
+        msg = messages_woodbury.update_messages(pred, d["params"], d["geom"], z)
+        beliefs.beliefs(pred, msg)
+        t += time.perf_counter() - t0
+        done += sample_P * d["geom"].J
+    return done / t, t
+
+
+def run_batched(args, rank, world):
+    """Many independent scenarios of uneven sizes per step (bp_batch_*): concurrent
+    streams with shared workspaces and graph replay, against the same scenarios run as
+    the plain path (one stream, launched directly, one scenario after another)."""
+    import torch
+    from paper_2604_19723_gb300 import bp
+    dev = int(os.environ.get("LOCAL_RANK", 0))
+    torch.cuda.set_device(dev)
+    total = args.warmup + args.steps
+    sc, scns = batched_inputs(args, 2 * total)
+    stream = torch.cuda.Stream()
+    n = len(sc)
+    tup = [(d["geom"], d["params"], d["P"], d["S"], d["S"], d["seed"] + 1000003 * rank) for d in sc]
+    updates = sum(d["P"] * d["geom"].J for d in sc)
+
+    def make_z(b):
+        z = torch.zeros((2 * total, b.z_floats()), dtype=torch.float32, device="cuda")
+        for i, (d, scn) in enumerate(zip(sc, scns)):
+            x_pos, sfv, rho, cc, cs, cr = bp.scenario_arrays(scn, range(1, 2 * total + 1))
+            with torch.cuda.stream(stream):
+                zi, _ = bp.synthesize(d["geom"], x_pos, sfv, rho, cc, cs, cr, snr_db=20.0, seed=d["seed"] + 11,
+                                      step0=1, stream=stream)
+            stream.synchronize()
+            o = b.z_offset(i)
+            z[:, o:o + 2 * zi.shape[1] * zi.shape[2]] = torch.view_as_real(zi).reshape(2 * total, -1)
+        torch.cuda.synchronize()
+        return z
+
+    flush = torch.empty(256 * 1024 * 1024 // 4, dtype=torch.float32, device="cuda")
+
+    def timed(b, z, members):
+        for i in range(args.warmup):
+            with torch.cuda.stream(stream):
+                b.step(z[i])
+        stream.synchronize()
+        l0 = sum(m.launch_count() for m in members)
+        ev0 = [torch.cuda.Event(enable_timing=True) for _ in range(args.steps)]
+        ev1 = [torch.cuda.Event(enable_timing=True) for _ in range(args.steps)]
+        if world > 1:
+            torch.distributed.barrier()
+        torch.cuda.synchronize()
+        with ClockSampler(dev) as clk:
+            for i in range(args.steps):
+                with torch.cuda.stream(stream):
+                    flush.fill_(float(i))
+                    ev0[i].record(stream)
+                    b.step(z[args.warmup + i])
+                    ev1[i].record(stream)
+            torch.cuda.synchronize()
+            if world > 1:
+                torch.distributed.barrier()
+        launches = sum(m.launch_count() for m in members) - l0
+        ms = [a.elapsed_time(c) for a, c in zip(ev0, ev1)]
+        return reduce_max(float(np.mean(ms)), world, "cuda"), launches, clk.summary()
+
+    t_init = time.perf_counter()
+    b = bp.Batch(tup, n_streams=args.streams, shared_workspace=True, use_graph=True, stream=stream)
+    t_init = time.perf_counter() - t_init
+    members = [b.member(i) for i in range(n)]
+    z = make_z(b)
+    t_step, launches, clocks = timed(b, z, members)
+    dev_bytes = b.device_bytes()
+
+    # end to end through the public API: the step's observations copied in from pinned
+    # host memory, every scenario's MT estimate read back
+    zh = z[total:total + args.steps].cpu().pin_memory()
+    zd = torch.empty_like(z[0])
+    e2e = []
+    torch.cuda.synchronize()
+    for i in range(args.steps):
+        e_a = torch.cuda.Event(enable_timing=True)
+        e_b = torch.cuda.Event(enable_timing=True)
+        with torch.cuda.stream(stream):
+            flush.fill_(float(i))
+            e_a.record(stream)
+            zd.copy_(zh[i], non_blocking=True)
+            b.step(zd)
+            for m in members:
+                m.estimate()
+            e_b.record(stream)
+        stream.synchronize()
+        e2e.append(e_a.elapsed_time(e_b))
+    t_e2e = reduce_max(float(np.mean(e2e)), world, "cuda")
+    del members
+    b.close()
+
+    # the plain path on the same scenarios: one stream, direct launches
+    seq_ms = None
+    if not args.no_sequential:
+        b1 = bp.Batch(tup, n_streams=1, shared_workspace=True, use_graph=False, stream=stream)
+        m1 = [b1.member(i) for i in range(n)]
+        seq_ms, _, _ = timed(b1, z, m1)
+        del m1
+        b1.close()
+
+    peaks = measured_peaks()
+    sm_mhz = clocks.get("sm_mhz") or peaks.get("sm_max_mhz", 2070.0)
+    peak_alu = SMS * FP32_LANES_PER_SM * 2 * sm_mhz * 1e6 / 1e12
+    fl = sum(kappa_flops(d["P"], d["S"], d["geom"].J, d["geom"].Nz) +
+             iota_flops(d["P"], d["S"], d["geom"].J, d["geom"].Nf, d["geom"].My, d["geom"].Mz) for d in sc)
+    ach = fl / (t_step * 1e-3) / 1e12
+    value = world * updates / (t_step * 1e-3)
+    out = {"metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
+           "warmup": args.warmup, "ms_per_step": t_step, "steps_per_s": 1e3 / t_step,
+           "scenario_steps_per_s": world * n * 1e3 / t_step,
+           "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f32",
+           "data": "synthetic (generative signal model of the paper, seeded)",
+           "config": {"workload": "batched", "scenarios": n, "S": "U{1..64}", "P": "U{256..16384}",
+                      "Nz": "U{5..300} (one antenna below 16, else 2x2 URA)", "J": 4,
+                      "particle_PA_updates_per_step": updates, "streams": min(args.streams, n),
+                      "graph": True, "shared_workspace": True, "device_GB": dev_bytes / 1e9,
+                      "init_s": t_init, "l2": "flushed between timed steps (256 MB write)",
+                      "parallelism": f"replicas x{world}"},
+           "sequential": ({"ms_per_step": seq_ms, "value": world * updates / (seq_ms * 1e-3),
+                           "speedup": seq_ms / t_step, "how": "same scenarios, one stream, direct launches"}
+                          if seq_ms else None),
+           "roofline": {"bound": "alu", "kernel": "k_kappa + k_iota/k_iota_blk of every scenario (whole step time)",
+                        "achieved": ach, "peak": peak_alu, "unit": "TFLOP/s", "frac": ach / peak_alu,
+                        "traffic": None,
+                        "peak_basis": f"FP32 FMA lanes: {SMS} SMs x {FP32_LANES_PER_SM} x 2 flop x {sm_mhz:.0f} MHz"},
+           "e2e": {"value": world * updates / (t_e2e * 1e-3), "unit": UNIT,
+                   "h2d_bytes_per_step": int(4 * z.shape[1]),
+                   "d2h_bytes_per_step": int(sum(8 * (13 + 4 + 9 * d["S"] + 4 * d["S"]) + 4 for d in sc)),
+                   "ms_per_step": t_e2e},
+           "gpu_launches": int(launches), "clocks": clocks}
+    if rank == 0 and not args.no_cpu_baseline:
+        v, t = batched_oracle_sample(sc, scns, args.cpu_particles // 4, 4)
+        cores = os.cpu_count() or 1
+        out["cpu_baseline"] = {"value": v, "unit": UNIT, "cores": cores, "kind": "oracle",
+                               "sample": f"one predict+update of {args.cpu_particles // 4} particles of each of the "
+                                         f"first 4 scenarios (FP64 Woodbury-mode oracle, {t:.2f} s)"}
+    if rank == 0:
+        print(json.dumps(out))
+
+
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
@@ -374,6 +558,9 @@ def main():
     ap.add_argument("--cpu-particles", type=int, default=1024)
     ap.add_argument("--ref-particles", type=int, default=256)
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--scenarios", type=int, default=4096, help="batched workload: number of scenarios")
+    ap.add_argument("--streams", type=int, default=32, help="batched workload: concurrent streams")
+    ap.add_argument("--no-sequential", action="store_true", help="batched workload: skip the one-stream run")
     args = ap.parse_args()
     world = int(os.environ.get("WORLD_SIZE", "1"))
     rank = int(os.environ.get("RANK", "0"))
@@ -385,7 +572,10 @@ def main():
     if world > 1:
         import torch
         torch.distributed.init_process_group("nccl")
-    run_gpu(args, rank, world)
+    if args.workload == "batched":
+        run_batched(args, rank, world)
+    else:
+        run_gpu(args, rank, world)
     if world > 1:
         import torch
         torch.distributed.destroy_process_group()

@@ -52,7 +52,7 @@ typedef enum {
  * R_pa: J rotation matrices, row-major 3x3, columns = local PA axes in
  * global coordinates (local vector r' = R^T r, eq. rangep).  p_y, p_z:
  * template URA element positions, symmetric about 0.
- * Limits: 1 <= J <= 16, Nf <= 64, My <= 16, Mz <= 16, Nz <= 2048. */
+ * Limits: 1 <= J <= 16, Nf <= 128, My <= 16, Mz <= 16, Nz <= 2048. */
 typedef struct {
     int J, Nf, My, Mz;
     double fc, c, B;
@@ -226,6 +226,88 @@ bp_status bp_get_profile(bp_handle* h, double* ms, int n);
 enum { BP_NOALLOC_MAX_P = 1 << 20 };
 bp_status bp_resample_noalloc(const double* w_dev, int P, uint64_t seed, int n, int kind, int index,
                               int* idx_dev, void* cuda_stream);
+
+/* ------------------------------------------------------------------ batches
+ * Many independent filters ("scenarios": each its own geometry, parameters,
+ * particle count and PF capacity) stepped together on one GPU.  The paper has
+ * no counterpart; each scenario runs exactly the step of bp_predict +
+ * bp_update (Sec. IV), so its results are those of a single handle created
+ * with the same arguments.
+ *
+ * Execution: the scenarios are ordered by their estimated cost (largest
+ * first) and dealt over n_streams CUDA streams, each stream taking the next
+ * scenario when its queue is the shortest (longest-processing-time list
+ * scheduling); the GPU runs the streams' kernels concurrently.  Scenarios on
+ * one stream run one after another, so with shared_workspace = 1 they share
+ * one per-step workspace (geometry records, bases, likelihoods, CDFs), sized
+ * for the largest of them; only the particle state stays per scenario.  With
+ * use_graph = 1 and every scenario's PF count fixed (Q = 0 and T_pru = 0), the
+ * whole batch step is captured once into a CUDA graph per particle-buffer
+ * parity and replayed (no per-launch host cost); otherwise the launches are
+ * issued directly and, where a PF count can change, the batch step ends with
+ * one synchronisation that reads back every scenario's count.
+ *
+ * Diagnostics (bp_get_diag) of a scenario are unavailable with
+ * shared_workspace = 1 (BP_ERR_STATE).  bp_batch_handle gives a scenario's
+ * handle for bp_estimate, bp_get_state / bp_set_state and the other
+ * single-handle calls (not bp_predict / bp_update / bp_free while the batch
+ * exists); such calls on a handle synchronise its stream only. */
+typedef struct bp_batch bp_batch;
+
+typedef struct {
+    const bp_geometry* geom;
+    const bp_params* params;
+    int P;             /* particles per belief */
+    int S_max;         /* PF capacity (<= 64) */
+    int S0;            /* PFs at time 0: the LoS and S0 - 1 drawn from the birth density
+                          over the whole birth box (existence p_B, PR existence p_B^PR);
+                          1 <= S0 <= S_max (bp_init uses 1) */
+    uint64_t seed;     /* Philox key of the scenario */
+} bp_scenario;
+
+typedef struct {
+    int n_streams;         /* 1..128 concurrent streams; 0 = 32 */
+    int shared_workspace;  /* 1: one workspace per stream; 0: one per scenario */
+    int use_graph;         /* 1: capture and replay the batch step where allowed */
+    void* cuda_stream;     /* cudaStream_t every batch step is ordered after and before
+                              (fork and join point); NULL = a blocking stream the batch
+                              creates (ordered with the legacy default stream) */
+} bp_batch_opts;
+
+/* Creates the scenarios' handles (the time-0 beliefs of bp_init), the streams
+ * and the workspaces.  opts may be NULL (32 streams, shared workspaces,
+ * graphs on).  Synchronous.  On failure nothing is kept, *out is NULL and
+ * bp_batch_last_error(NULL) gives the reason. */
+bp_status bp_batch_init(const bp_scenario* sc, int n, const bp_batch_opts* opts, bp_batch** out);
+
+/* One step (prediction and update) of every scenario.  z_dev: device pointer
+ * to the scenarios' observations, concatenated in scenario order; scenario i
+ * reads J_i x Nz_i complex FP32 values from element offset bp_batch_z_offset
+ * (in floats).  Asynchronous unless a PF count can change (see above).  A
+ * graph captured with one z_dev is re-captured when another pointer is
+ * passed. */
+bp_status bp_batch_step(bp_batch* b, const float* z_dev);
+
+/* Float offset of scenario i's observations in z_dev, and the total floats. */
+size_t bp_batch_z_offset(const bp_batch* b, int i);
+size_t bp_batch_z_floats(const bp_batch* b);
+
+/* Waits for every stream of the batch.  Returns BP_ERR_CUDA on a device error. */
+bp_status bp_batch_sync(bp_batch* b);
+
+/* Handle of scenario i (owned by the batch). */
+bp_status bp_batch_handle(bp_batch* b, int i, bp_handle** h);
+
+/* Stream index a scenario was dealt to, and the bytes of device memory the
+ * batch holds (state + workspaces), for inspection. */
+int bp_batch_stream_of(const bp_batch* b, int i);
+size_t bp_batch_device_bytes(const bp_batch* b);
+
+/* Frees every scenario, stream, workspace and graph.  Synchronous. */
+bp_status bp_batch_free(bp_batch* b);
+
+/* Text of the last error on b (of the last bp_batch_init failure if b is NULL). */
+const char* bp_batch_last_error(const bp_batch* b);
 
 #ifdef __cplusplus
 }

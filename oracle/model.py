@@ -130,10 +130,14 @@ def predict(state, params, J: int, seed: int, S_max: int) -> Predicted:
                      w_xi=state.w_eta.copy(), zeta=zeta, is_new=is_new)
 
 
-def init_state(params, J: int, P: int, seed: int):
+def init_state(params, J: int, P: int, seed: int, S0: int = 1):
     """Time-0 beliefs (Sec. V-A): x_0 ~ U(p_min, p_max) U(-v_max, v_max),
     eta_0 ~ U(eta_min, eta_max), and the LoS (slot 0) drawn like a new PF with
-    existence p_B and PR existence p_B^PR (reading R6b)."""
+    existence p_B and PR existence p_B^PR (reading R6b).  Slots 1 .. S0-1 (S0 > 1
+    starts a filter with that many PFs, for the batched scenarios) are drawn from
+    the birth density f_B of Sec. III-B2 over the whole birth box
+    U(2 p_min, 2 p_max) x U(0, gamma_max) x uniform disc of radius mu_max, each with
+    existence p_B and PR existence p_B^PR like a new PF (Sec. IV-D)."""
     from paper_2604_19723_gb300.workload import StateArrays
     idx = np.arange(P, dtype=np.uint64)
     lo, hi = np.asarray(params.p_min), np.asarray(params.p_max)
@@ -157,8 +161,22 @@ def init_state(params, J: int, P: int, seed: int):
         t = 2.0 * np.pi * ub[5]
         phi[0, 4] = r * np.cos(t)
         phi[0, 5] = r * np.sin(t)
+    if S0 > 1:
+        phi = np.concatenate([phi, np.zeros((S0 - 1, 6, P))])
+        blo = np.asarray(params.birth_min, float)
+        bhi = np.asarray(params.birth_max, float)
+        for s in range(1, S0):
+            ub = rng.uniforms24(seed, idx, 0, rng.BIRTH, s, 6)
+            for k in range(3):
+                phi[s, k] = blo[k] + (bhi[k] - blo[k]) * ub[k]
+            phi[s, 3] = params.gamma_max * ub[3]
+            if not params.zero_mean:
+                r = params.mu_max * np.sqrt(ub[4])
+                t = 2.0 * np.pi * ub[5]
+                phi[s, 4] = r * np.cos(t)
+                phi[s, 5] = r * np.sin(t)
     pB = birth_probability(params.mu_B, max(params.Q, 1))
-    return StateArrays(n=0, S=1, x=x.astype(np.float32), phi=phi.astype(np.float32),
+    return StateArrays(n=0, S=S0, x=x.astype(np.float32), phi=phi.astype(np.float32),
                        eta=eta.astype(np.float32), w_x=np.full(P, 1.0 / P),
-                       w_y=np.full((1, P), pB / P), w_eta=np.full((J, P), 1.0 / P),
-                       p_pr=np.full((1, J), params.pB_pr))
+                       w_y=np.full((S0, P), pB / P), w_eta=np.full((J, P), 1.0 / P),
+                       p_pr=np.full((S0, J), params.pB_pr))

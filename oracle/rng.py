@@ -67,7 +67,7 @@ def draw(seed: int, c0, n: int, purpose: int, sub: int, block):
 
 
 def u24(x):
-    """Uniform in (0,1) from the top 24 bits: ((x >> 8) + 1/2) * 2^-24 (exact in FP32)."""
+    """Uniform in (0,1) from the top 24 bits: ((x >> 8) + 1/2) * 2^-24 (exact in FP64)."""
     return ((np.asarray(x, np.uint32) >> np.uint32(8)).astype(np.float64) + 0.5) * (2.0 ** -24)
 
 

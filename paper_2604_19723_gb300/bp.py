@@ -25,7 +25,9 @@ DIAG_TABLE, DIAG_WEIGHTS, DIAG_LOGLIK, DIAG_INDICES = 1, 2, 3, 4
 ENTRY_POINTS = ("bp_init", "bp_predict", "bp_update", "bp_estimate", "bp_free", "bp_last_error",
                 "bp_get_state", "bp_set_state", "bp_get_predicted", "bp_set_predicted", "bp_get_diag",
                 "bp_synthesize", "bp_launch_count", "bp_set_profiling", "bp_get_profile",
-                "bp_resample_noalloc")
+                "bp_resample_noalloc", "bp_batch_init", "bp_batch_step", "bp_batch_z_offset", "bp_batch_z_floats",
+                "bp_batch_sync", "bp_batch_handle", "bp_batch_stream_of", "bp_batch_device_bytes", "bp_batch_free",
+                "bp_batch_last_error")
 PROFILE_STAGES = ("predict", "row_sums", "table", "stage", "kappa", "iota", "nu", "normalize", "resample")
 
 
@@ -67,6 +69,16 @@ class _Estimate(C.Structure):
                 ("declared", C.POINTER(C.c_int)), ("iota_repaired", C.c_int)]
 
 
+class _Scenario(C.Structure):
+    _fields_ = [("geom", C.POINTER(_Geometry)), ("params", C.POINTER(_Params)), ("P", C.c_int), ("S_max", C.c_int),
+                ("S0", C.c_int), ("seed", C.c_uint64)]
+
+
+class _BatchOpts(C.Structure):
+    _fields_ = [("n_streams", C.c_int), ("shared_workspace", C.c_int), ("use_graph", C.c_int),
+                ("cuda_stream", C.c_void_p)]
+
+
 _lib = None
 
 
@@ -98,8 +110,24 @@ def load() -> C.CDLL:
     lib.bp_resample_noalloc.argtypes = [vp, C.c_int, C.c_uint64, C.c_int, C.c_int, C.c_int, vp, vp]
     lib.bp_launch_count.argtypes = [vp]
     lib.bp_launch_count.restype = C.c_longlong
+    lib.bp_batch_init.argtypes = [C.POINTER(_Scenario), C.c_int, C.POINTER(_BatchOpts), C.POINTER(vp)]
+    lib.bp_batch_step.argtypes = [vp, vp]
+    lib.bp_batch_z_offset.argtypes = [vp, C.c_int]
+    lib.bp_batch_z_offset.restype = C.c_size_t
+    lib.bp_batch_z_floats.argtypes = [vp]
+    lib.bp_batch_z_floats.restype = C.c_size_t
+    lib.bp_batch_sync.argtypes = [vp]
+    lib.bp_batch_handle.argtypes = [vp, C.c_int, C.POINTER(vp)]
+    lib.bp_batch_stream_of.argtypes = [vp, C.c_int]
+    lib.bp_batch_device_bytes.argtypes = [vp]
+    lib.bp_batch_device_bytes.restype = C.c_size_t
+    lib.bp_batch_free.argtypes = [vp]
+    lib.bp_batch_last_error.argtypes = [vp]
+    lib.bp_batch_last_error.restype = C.c_char_p
+    untyped = ("bp_last_error", "bp_launch_count", "bp_batch_z_offset", "bp_batch_z_floats",
+               "bp_batch_device_bytes", "bp_batch_last_error")
     for f in ENTRY_POINTS:
-        if f not in ("bp_last_error", "bp_launch_count"):
+        if f not in untyped:
             getattr(lib, f).restype = C.c_int
     _lib = lib
     return lib
@@ -291,6 +319,95 @@ class Filter:
         n = P + S * P + J * P
         b = self._diag(DIAG_INDICES, n * 4, np.int32)
         return dict(x=b[:P], y=b[P:P + S * P].reshape(S, P), eta=b[P + S * P:].reshape(J, P))
+
+
+class _BatchMember(Filter):
+    """View of one scenario of a Batch: the single-handle calls (estimate, state
+    export/import, launch count); the handle belongs to the batch."""
+
+    def __init__(self, batch, i, h, geom, params, P, S_max):
+        self.lib, self.h, self.geom, self.params, self.P, self.S_max = batch.lib, h, geom, params, P, S_max
+        self._batch = batch   # keeps the batch (and the handle) alive
+
+    def close(self):
+        self.h = None
+
+    def predict(self):
+        raise BPError(6, "a batch scenario steps through Batch.step")
+
+    update = step = predict
+
+
+class Batch:
+    """Many independent filters stepped together (bp_batch_*): scenarios dealt over
+    concurrent streams, shared per-stream workspaces, CUDA-graph replay."""
+
+    def __init__(self, scenarios, n_streams: int = 32, shared_workspace: bool = True, use_graph: bool = True,
+                 stream=None):
+        """scenarios: list of (geom, params, P, S_max, S0, seed); stream: the fork/join stream
+        (a torch.cuda.Stream or a raw handle; None = the current torch stream)."""
+        self.lib = load()
+        self.scen = list(scenarios)
+        n = len(self.scen)
+        self._g = [_GeomHolder(sc[0]) for sc in self.scen]
+        self._p = [_params_struct(sc[1]) for sc in self.scen]
+        arr = (_Scenario * n)()
+        for i, (g, p, P, S_max, S0, seed) in enumerate(self.scen):
+            arr[i] = _Scenario(C.pointer(self._g[i].s), C.pointer(self._p[i]), P, S_max, S0, C.c_uint64(seed))
+        self._arr = arr
+        self.stream = _stream_handle(stream)
+        opts = _BatchOpts(n_streams, int(bool(shared_workspace)), int(bool(use_graph)), C.c_void_p(self.stream))
+        b = C.c_void_p()
+        st = self.lib.bp_batch_init(arr, n, C.byref(opts), C.byref(b))
+        if st != BP_OK:
+            msg = self.lib.bp_batch_last_error(None)
+            raise BPError(st, f"bp_batch_init: {msg.decode() if msg else ''}")
+        self.b = b
+
+    def close(self):
+        if getattr(self, "b", None):
+            self.lib.bp_batch_free(self.b)
+            self.b = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def _check(self, st, what):
+        if st != BP_OK:
+            msg = self.lib.bp_batch_last_error(self.b)
+            raise BPError(st, f"{what}: {msg.decode() if msg else ''}")
+
+    def __len__(self):
+        return len(self.scen)
+
+    def z_offset(self, i: int) -> int:
+        return int(self.lib.bp_batch_z_offset(self.b, i))
+
+    def z_floats(self) -> int:
+        return int(self.lib.bp_batch_z_floats(self.b))
+
+    def step(self, z):
+        """z: torch CUDA float32 tensor of z_floats() values (the scenarios' J x Nz complex
+        observations concatenated in scenario order)."""
+        self._check(self.lib.bp_batch_step(self.b, C.c_void_p(z.data_ptr())), "bp_batch_step")
+
+    def sync(self):
+        self._check(self.lib.bp_batch_sync(self.b), "bp_batch_sync")
+
+    def stream_of(self, i: int) -> int:
+        return int(self.lib.bp_batch_stream_of(self.b, i))
+
+    def device_bytes(self) -> int:
+        return int(self.lib.bp_batch_device_bytes(self.b))
+
+    def member(self, i: int) -> Filter:
+        h = C.c_void_p()
+        self._check(self.lib.bp_batch_handle(self.b, i, C.byref(h)), "bp_batch_handle")
+        g, p, P, S_max, _, _ = self.scen[i]
+        return _BatchMember(self, i, h, g, p, P, S_max)
 
 
 NOALLOC_MAX_P = 1 << 20

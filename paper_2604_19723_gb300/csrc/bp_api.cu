@@ -6,39 +6,9 @@
 #include <vector>
 #include <algorithm>
 
-#include "bp_internal.cuh"
-#include "bp_kernels.cuh"
+#include "bp_handle.cuh"
 
 using namespace bp;
-
-struct bp_handle {
-    DevGeom G;
-    DevParams Pm;
-    DevState D;
-    cudaStream_t st;
-    int P, S_max, J, Nz;
-    int SCA;            // column stride of the per-(s,j) basis buffers
-    int S;              // current number of PFs (host copy)
-    int S_upd;          // S of the last bp_update
-    int n;              // last completed step (state) or current step (predicted)
-    int phase;          // 0: belief state, 1: predicted
-    int births_skipped;
-    int nsplit_max;
-    long long launches;
-    // scratch
-    double* gram;
-    double* nu_b;
-    double* V64;
-    double* cdf;
-    double* wn;         // normalised weights before resampling: w_x (P) | w_y (S_max P) | w_eta (J P)
-    int* h_ctrl;        // pinned
-    double* h_est;      // pinned
-    int prof_on;
-    cudaEvent_t ev[BP_PROF_STAGES + 1];
-    bool ev_valid[BP_PROF_STAGES];
-    std::vector<void*> allocs;
-    std::string err;
-};
 
 static std::string g_init_error;
 
@@ -57,6 +27,7 @@ template <typename T>
 static bool dalloc(bp_handle* h, T** p, size_t count) {
     void* q = nullptr;
     if (cudaMalloc(&q, std::max<size_t>(count, 1) * sizeof(T)) != cudaSuccess) return false;
+    h->dev_bytes += std::max<size_t>(count, 1) * sizeof(T);
     cudaMemsetAsync(q, 0, std::max<size_t>(count, 1) * sizeof(T), h->st);
     h->allocs.push_back(q);
     *p = static_cast<T*>(q);
@@ -119,109 +90,10 @@ long long bp_launch_count(const bp_handle* h) { return h ? h->launches : 0; }
 
 bp_status bp_init(const bp_geometry* geom, const bp_params* prm, int P, int S_max, uint64_t seed,
                   void* cuda_stream, bp_handle** out) {
-    if (!out) return fail(nullptr, BP_ERR_INVALID_ARG, "out is NULL");
-    *out = nullptr;
-    if (validate_geom(geom) != BP_OK) return fail(nullptr, BP_ERR_INVALID_ARG, "invalid geometry");
-    if (!prm) return fail(nullptr, BP_ERR_INVALID_ARG, "params is NULL");
-    if (P < 1 || P > (1 << 28)) return fail(nullptr, BP_ERR_INVALID_ARG, "P out of range");
-    if (S_max < 1 || S_max > S_CAP_MAX) return fail(nullptr, BP_ERR_INVALID_ARG, "S_max must be in [1, 64]");
-    if (prm->c_eta < 1.0 || prm->c_gamma < 1.0) return fail(nullptr, BP_ERR_INVALID_ARG, "Gamma shapes must be >= 1");
-    if (prm->motion_dims != 2 && prm->motion_dims != 3) return fail(nullptr, BP_ERR_INVALID_ARG, "motion_dims must be 2 or 3");
-    if (prm->Q < 0 || !(prm->T > 0)) return fail(nullptr, BP_ERR_INVALID_ARG, "invalid Q or T");
-    bp_handle* h = new bp_handle();
-    h->st = static_cast<cudaStream_t>(cuda_stream);
-    fill_geom(h->G, geom);
-    DevParams& Pm = h->Pm;
-    memset(&Pm, 0, sizeof(Pm));
-    Pm.T = prm->T; Pm.sigma_v = prm->sigma_v; Pm.motion_dims = prm->motion_dims;
-    Pm.c_eta = prm->c_eta; Pm.c_gamma = prm->c_gamma; Pm.sigma_mu = prm->sigma_mu; Pm.sigma_sfv = prm->sigma_sfv;
-    Pm.pS = prm->pS; Pm.pS_pr = prm->pS_pr; Pm.pR_pr = prm->pR_pr; Pm.pB_pr = prm->pB_pr; Pm.mu_B = prm->mu_B;
-    Pm.Q = prm->Q;
-    const double mq = prm->mu_B / std::max(prm->Q, 1);
-    Pm.pB = mq / (1.0 + mq);
-    Pm.T_dec = prm->T_dec; Pm.T_pru = prm->T_pru; Pm.gamma_max = prm->gamma_max; Pm.mu_max = prm->mu_max;
-    Pm.eta_min = prm->eta_min; Pm.eta_max = prm->eta_max;
-    for (int k = 0; k < 3; ++k) { Pm.p_min[k] = prm->p_min[k]; Pm.p_max[k] = prm->p_max[k]; Pm.v_max[k] = prm->v_max[k]; }
-    Pm.zero_mean = prm->zero_mean; Pm.mvec_scaling = prm->mvec_scaling; Pm.regularize = prm->regularize;
-    Pm.key0 = (uint32_t)(seed & 0xFFFFFFFFu); Pm.key1 = (uint32_t)(seed >> 32);
-    Pm.P = P; Pm.S_max = S_max;
-    h->P = P; h->S_max = S_max; h->J = geom->J; h->Nz = h->G.Nz;
-    h->SCA = sc_bucket(S_max);
-    h->nsplit_max = 32;
-    const int J = geom->J, Nz = h->G.Nz, SCA = h->SCA;
-    const size_t PP = (size_t)P;
-    DevState& D = h->D;
-    memset(&D, 0, sizeof(D));
-    bool ok = true;
-    for (int b = 0; b < 2; ++b) {
-        ok &= dalloc(h, &D.x[b], 6 * PP);
-        ok &= dalloc(h, &D.phi[b], (size_t)S_max * 6 * PP);
-        ok &= dalloc(h, &D.eta[b], (size_t)J * PP);
-    }
-    ok &= dalloc(h, &D.w_x, PP);
-    ok &= dalloc(h, &D.w_y, (size_t)S_max * PP);
-    ok &= dalloc(h, &D.w_alpha, (size_t)S_max * PP);
-    ok &= dalloc(h, &D.w_eta, (size_t)J * PP);
-    ok &= dalloc(h, &D.p_pr, (size_t)S_max * J);
-    ok &= dalloc(h, &D.zeta, (size_t)S_max * J);
-    ok &= dalloc(h, &D.p_s, (size_t)S_max);
-    ok &= dalloc(h, &D.lw_x, PP);
-    ok &= dalloc(h, &D.lw_y, (size_t)S_max * PP);
-    ok &= dalloc(h, &D.lw_eta, (size_t)J * PP);
-    ok &= dalloc(h, &D.llr_w, (size_t)S_max * J);
-    ok &= dalloc(h, &D.geo, (size_t)S_max * J * PP);
-    ok &= dalloc(h, &D.geo_lo, (size_t)S_max * J * PP);
-    ok &= dalloc(h, &D.flags, PP + 1);
-    ok &= dalloc(h, &D.tab, (size_t)4 * S_max * J * Nz * 2);
-    ok &= dalloc(h, &D.tab_part, (size_t)h->nsplit_max * 3 * S_max * J * Nz * 2);
-    ok &= dalloc(h, &D.W, (size_t)S_max);
-    ok &= dalloc(h, &D.eta_bar, (size_t)J);
-    ok &= dalloc(h, &D.kV, (size_t)S_max * J * Nz * SCA);
-    ok &= dalloc(h, &D.kr0l, (size_t)S_max * J * Nz);
-    ok &= dalloc(h, &D.kdl, (size_t)S_max * J * SCA);
-    ok &= dalloc(h, &D.kerr, 1);
-    D.kB = nullptr;
-    if (kappa_tc_ok(h->G, SCA)) ok &= dalloc(h, &D.kB, kappa_btile_floats(h->G, S_max));
-    ok &= dalloc(h, &D.ky0, (size_t)S_max * J * SCA);
-    ok &= dalloc(h, &D.kJ0, (size_t)S_max * J);
-    ok &= dalloc(h, &D.nu_T, (size_t)J * 4 * S_max);
-    ok &= dalloc(h, &D.nu_c, (size_t)J * 2);
-    const int nbel = bel_count(S_max, J);
-    ok &= dalloc(h, &D.red_part, (size_t)nbel * 64 * RED_W * 2);
-    ok &= dalloc(h, &D.bel, bel_total(S_max, J));
-    ok &= dalloc(h, &D.Lchol, (size_t)nbel * 36);
-    ok &= dalloc(h, &D.idx, (size_t)nbel * PP);
-    ok &= dalloc(h, &D.ctrl, (size_t)4 + S_max);
-    const EstLayout E{S_max, J};
-    ok &= dalloc(h, &D.est, E.total());
-    ok &= dalloc(h, &h->gram, (size_t)J * S_max * S_max * 2);
-    ok &= dalloc(h, &h->nu_b, (size_t)J * (S_max + 1) * 2);
-    ok &= dalloc(h, &h->V64, (size_t)S_max * J * Nz * SCA * 2);
-    ok &= dalloc(h, &h->cdf, (size_t)nbel * PP);
-    ok &= dalloc(h, &h->wn, (size_t)nbel * PP);
-    if (ok) {
-        ok &= cudaMallocHost(&h->h_ctrl, (4 + S_max) * sizeof(int)) == cudaSuccess;
-        ok &= cudaMallocHost(&h->h_est, E.total() * sizeof(double)) == cudaSuccess;
-    }
-    if (!ok) {
-        g_init_error = "device allocation failed";
-        bp_free(h);
-        return BP_ERR_CUDA;
-    }
-    D.wn_x = h->wn;
-    D.wn_y = h->wn + PP;
-    D.wn_eta = h->wn + (size_t)(1 + S_max) * PP;
-    D.cur = 0;
-    launch_init(h->G, h->Pm, D, h->st);
-    h->launches += 1;
-    h->S = 1; h->S_upd = 1; h->n = 0; h->phase = 0;
-    if (cudaStreamSynchronize(h->st) != cudaSuccess || cudaGetLastError() != cudaSuccess) {
-        g_init_error = std::string("bp_init: ") + cudaGetErrorString(cudaGetLastError());
-        bp_free(h);
-        return BP_ERR_CUDA;
-    }
-    *out = h;
-    return BP_OK;
+    std::string err;
+    const bp_status s = handle_create(geom, prm, P, S_max, 1, seed, static_cast<cudaStream_t>(cuda_stream), true, out, &err);
+    if (s != BP_OK) g_init_error = err;
+    return s;
 }
 
 bp_status bp_free(bp_handle* h) {
@@ -229,6 +101,7 @@ bp_status bp_free(bp_handle* h) {
     if (h->st) cudaStreamSynchronize(h->st); else cudaDeviceSynchronize();
     if (h->prof_on) for (int i = 0; i <= BP_PROF_STAGES; ++i) cudaEventDestroy(h->ev[i]);
     for (void* p : h->allocs) cudaFree(p);
+    if (h->ws_owned && h->ws_base) cudaFree(h->ws_base);
     if (h->h_ctrl) cudaFreeHost(h->h_ctrl);
     if (h->h_est) cudaFreeHost(h->h_est);
     delete h;
@@ -238,65 +111,21 @@ bp_status bp_free(bp_handle* h) {
 bp_status bp_predict(bp_handle* h) {
     if (!h) return BP_ERR_INVALID_ARG;
     if (h->phase != 0) return fail(h, BP_ERR_STATE, "bp_predict: the handle already holds a prediction");
-    const int n = h->n + 1;
-    const int S_old = h->S;
-    int S_new = S_old;
-    if (h->Pm.Q > 0) {
-        S_new = std::min(S_old + h->Pm.Q, h->S_max);
-        h->births_skipped += S_old + h->Pm.Q - S_new;
-    }
-    mark(h, 0);
-    launch_predict(h->G, h->Pm, h->D, n, S_old, S_new, h->st);
-    if (h->prof_on) { cudaEventRecord(h->ev[BP_PROF_STAGES], h->st); h->ev_valid[0] = true; }
-    h->launches += 1;
-    h->S = S_new;
-    h->n = n;
-    h->phase = 1;
+    predict_enqueue(h);
     return cuda_check(h, "bp_predict");
 }
 
 bp_status bp_update(bp_handle* h, const float* z_dev) {
     if (!h || !z_dev) return BP_ERR_INVALID_ARG;
     if (h->phase != 1) return fail(h, BP_ERR_STATE, "bp_update: call bp_predict (or bp_set_predicted) first");
-    const int S = h->S, J = h->J, P = h->P;
-    DevState& D = h->D;
-    mark(h, 1);
-    launch_row_sums(h->Pm, D, S, J, h->st);
-    mark(h, 2);
-    int nsplit = std::max(1, (4 * 152 + S * J - 1) / (S * J));
-    nsplit = std::min(nsplit, std::max(1, P / 256));
-    nsplit = std::min(nsplit, h->nsplit_max);
-    launch_geom(h->G, h->Pm, D, S, h->st);
-    launch_table(h->G, h->Pm, D, S, nsplit, h->st);
-    mark(h, 3);
-    launch_stage(h->G, h->Pm, D, S, h->SCA, z_dev, h->gram, h->nu_b, h->V64, h->st);
-    if (S > 32) launch_kappa_btile(h->G, D, S, h->SCA, h->st);   // B tiles of the tensor-core variant (SC = 64)
-    mark(h, 4);
-    launch_kappa(h->G, h->Pm, D, S, h->SCA, h->st);
-    mark(h, 5);
-    launch_iota(h->G, h->Pm, D, S, z_dev, h->st);
-    launch_iota_repair(h->G, h->Pm, D, S, z_dev, h->st);
-    mark(h, 6);
-    launch_nu(h->G, h->Pm, D, S, h->st);
-    mark(h, 7);
-    launch_normalize(h->G, h->Pm, D, S, h->n, h->st);
-    mark(h, 8);
-    launch_resample(h->G, h->Pm, D, S, h->n, h->cdf, h->st);
-    if (h->prof_on) {
-        cudaEventRecord(h->ev[BP_PROF_STAGES], h->st);
-        for (int i = 1; i < BP_PROF_STAGES; ++i) h->ev_valid[i] = true;
-    }
-    h->launches += 1 + 3 + 3 + 1 + 2 + 1 + 5 + 3 + ((S > 32 && D.kB && kappa_tc_ok(h->G, h->SCA)) ? 1 : 0);
-    h->D.cur = 1 - h->D.cur;
-    h->S_upd = S;
-    h->phase = 0;
+    if (!h->ws_base) return fail(h, BP_ERR_STATE, "bp_update: no workspace bound");
+    update_enqueue(h, z_dev);
     bp_status s = cuda_check(h, "bp_update");
     if (s != BP_OK) return s;
-    if (h->Pm.Q > 0 || h->Pm.T_pru > 0.0) {
-        if (cudaMemcpyAsync(h->h_ctrl, D.ctrl, 4 * sizeof(int), cudaMemcpyDeviceToHost, h->st) != cudaSuccess ||
-            cudaStreamSynchronize(h->st) != cudaSuccess)
+    if (dynamic_pf_count(h)) {
+        if (cudaStreamSynchronize(h->st) != cudaSuccess)
             return fail(h, BP_ERR_CUDA, std::string("bp_update: ") + cudaGetErrorString(cudaGetLastError()));
-        h->S = h->h_ctrl[1];
+        update_finish(h);
     }
     return BP_OK;
 }
@@ -357,6 +186,12 @@ static bp_status copy_state(bp_handle* h, bp_state_view* v, bool to_host, bool p
                                 : cudaMemcpyAsync(it.dev, it.host, it.bytes, kind, h->st);
         if (e != cudaSuccess) return fail(h, BP_ERR_CUDA, cudaGetErrorString(e));
     }
+    if (!to_host) {
+        // the device step index follows the imported state (pageable copy: staged before return)
+        const int nstep = v->n;
+        if (cudaMemcpyAsync(D.step, &nstep, sizeof(int), cudaMemcpyHostToDevice, h->st) != cudaSuccess)
+            return fail(h, BP_ERR_CUDA, cudaGetErrorString(cudaGetLastError()));
+    }
     if (cudaStreamSynchronize(h->st) != cudaSuccess) return fail(h, BP_ERR_CUDA, cudaGetErrorString(cudaGetLastError()));
     if (to_host) { v->S = h->S; v->n = h->n; }
     else { h->S = S; h->n = v->n; h->phase = predicted ? 1 : 0; }
@@ -376,6 +211,7 @@ bp_status bp_set_predicted(bp_handle* h, const bp_state_view* in) { return copy_
 
 bp_status bp_get_diag(bp_handle* h, int what, void* host, size_t bytes) {
     if (!h || !host) return BP_ERR_INVALID_ARG;
+    if (h->ws_shared) return fail(h, BP_ERR_STATE, "bp_get_diag: the handle's workspace is shared within a batch");
     const int S = h->S_upd, J = h->J, P = h->P, Nz = h->Nz, SM = h->S_max;
     DevState& D = h->D;
     std::vector<std::pair<const void*, size_t>> parts;   // (device ptr, bytes) in order
@@ -505,3 +341,218 @@ bp_status bp_synthesize(const bp_geometry* geom, int n_steps, int step0, const d
 }
 
 }  // extern "C"
+
+// ---------------------------------------------------------------- handle internals
+
+static size_t ws_align(size_t b) { return (std::max<size_t>(b, 8) + 255) & ~(size_t)255; }
+
+WsPlan ws_plan(const DevGeom& G, int P, int S_max, int SCA, int nsplit_max) {
+    WsPlan w{};
+    size_t o = 0;
+    auto take = [&](size_t bytes) { const size_t at = o; o += ws_align(bytes); return at; };
+    const size_t PP = (size_t)P, J = (size_t)G.J, Nz = (size_t)G.Nz, SM = (size_t)S_max;
+    const size_t nbel = (size_t)bel_count(S_max, G.J);
+    w.lw_x = take(PP * sizeof(double));
+    w.lw_y = take(SM * PP * sizeof(double));
+    w.lw_eta = take(J * PP * sizeof(double));
+    w.geo = take(SM * J * PP * sizeof(float4));
+    w.geo_lo = take(SM * J * PP * sizeof(float2));
+    w.flags = take((PP + 1) * sizeof(int));
+    w.tab = take(4 * SM * J * Nz * 2 * sizeof(double));
+    w.tab_part = take((size_t)nsplit_max * 3 * SM * J * Nz * 2 * sizeof(double));
+    w.kV = take(SM * J * Nz * (size_t)SCA * sizeof(float2));
+    w.kr0l = take(SM * J * Nz * sizeof(float2));
+    w.kB = kappa_tc_ok(G, SCA) ? take(kappa_btile_floats(G, S_max) * sizeof(float)) : take(0);
+    w.red_part = take(nbel * 64 * RED_W * 2 * sizeof(double));
+    w.gram = take(J * SM * SM * 2 * sizeof(double));
+    w.V64 = take(SM * J * Nz * (size_t)SCA * 2 * sizeof(double));
+    w.cdf = take(nbel * PP * sizeof(double));
+    w.wn = take(nbel * PP * sizeof(double));
+    w.idx = take(nbel * PP * sizeof(int));
+    w.total = o;
+    return w;
+}
+
+void ws_bind(bp_handle* h, char* base) {
+    const WsPlan& w = h->wsp;
+    DevState& D = h->D;
+    D.lw_x = reinterpret_cast<double*>(base + w.lw_x);
+    D.lw_y = reinterpret_cast<double*>(base + w.lw_y);
+    D.lw_eta = reinterpret_cast<double*>(base + w.lw_eta);
+    D.geo = reinterpret_cast<float4*>(base + w.geo);
+    D.geo_lo = reinterpret_cast<float2*>(base + w.geo_lo);
+    D.flags = reinterpret_cast<int*>(base + w.flags);
+    D.tab = reinterpret_cast<double*>(base + w.tab);
+    D.tab_part = reinterpret_cast<double*>(base + w.tab_part);
+    D.kV = reinterpret_cast<float2*>(base + w.kV);
+    D.kr0l = reinterpret_cast<float2*>(base + w.kr0l);
+    D.kB = kappa_tc_ok(h->G, h->SCA) ? reinterpret_cast<float*>(base + w.kB) : nullptr;
+    D.red_part = reinterpret_cast<double*>(base + w.red_part);
+    h->gram = reinterpret_cast<double*>(base + w.gram);
+    h->V64 = reinterpret_cast<double*>(base + w.V64);
+    h->cdf = reinterpret_cast<double*>(base + w.cdf);
+    h->wn = reinterpret_cast<double*>(base + w.wn);
+    D.idx = reinterpret_cast<int*>(base + w.idx);
+    const size_t PP = (size_t)h->P;
+    D.wn_x = h->wn;
+    D.wn_y = h->wn + PP;
+    D.wn_eta = h->wn + (size_t)(1 + h->S_max) * PP;
+    h->ws_base = base;
+}
+
+bp_status handle_create(const bp_geometry* geom, const bp_params* prm, int P, int S_max, int S0, uint64_t seed,
+                        cudaStream_t st, bool own_ws, bp_handle** out, std::string* err) {
+    auto bad = [&](const char* m) { *err = m; return BP_ERR_INVALID_ARG; };
+    if (!out) return bad("out is NULL");
+    *out = nullptr;
+    if (validate_geom(geom) != BP_OK) return bad("invalid geometry");
+    if (!prm) return bad("params is NULL");
+    if (P < 1 || P > (1 << 28)) return bad("P out of range");
+    if (S_max < 1 || S_max > S_CAP_MAX) return bad("S_max must be in [1, 64]");
+    if (S0 < 1 || S0 > S_max) return bad("the initial PF count must be in [1, S_max]");
+    if (prm->c_eta < 1.0 || prm->c_gamma < 1.0) return bad("Gamma shapes must be >= 1");
+    if (prm->motion_dims != 2 && prm->motion_dims != 3) return bad("motion_dims must be 2 or 3");
+    if (prm->Q < 0 || !(prm->T > 0)) return bad("invalid Q or T");
+    bp_handle* h = new bp_handle();
+    h->st = st;
+    fill_geom(h->G, geom);
+    DevParams& Pm = h->Pm;
+    memset(&Pm, 0, sizeof(Pm));
+    Pm.T = prm->T; Pm.sigma_v = prm->sigma_v; Pm.motion_dims = prm->motion_dims;
+    Pm.c_eta = prm->c_eta; Pm.c_gamma = prm->c_gamma; Pm.sigma_mu = prm->sigma_mu; Pm.sigma_sfv = prm->sigma_sfv;
+    Pm.pS = prm->pS; Pm.pS_pr = prm->pS_pr; Pm.pR_pr = prm->pR_pr; Pm.pB_pr = prm->pB_pr; Pm.mu_B = prm->mu_B;
+    Pm.Q = prm->Q;
+    const double mq = prm->mu_B / std::max(prm->Q, 1);
+    Pm.pB = mq / (1.0 + mq);
+    Pm.T_dec = prm->T_dec; Pm.T_pru = prm->T_pru; Pm.gamma_max = prm->gamma_max; Pm.mu_max = prm->mu_max;
+    Pm.eta_min = prm->eta_min; Pm.eta_max = prm->eta_max;
+    for (int k = 0; k < 3; ++k) { Pm.p_min[k] = prm->p_min[k]; Pm.p_max[k] = prm->p_max[k]; Pm.v_max[k] = prm->v_max[k]; }
+    Pm.zero_mean = prm->zero_mean; Pm.mvec_scaling = prm->mvec_scaling; Pm.regularize = prm->regularize;
+    Pm.key0 = (uint32_t)(seed & 0xFFFFFFFFu); Pm.key1 = (uint32_t)(seed >> 32);
+    Pm.P = P; Pm.S_max = S_max;
+    h->P = P; h->S_max = S_max; h->J = geom->J; h->Nz = h->G.Nz;
+    h->SCA = sc_bucket(S_max);
+    h->nsplit_max = 32;
+    const int J = geom->J, SCA = h->SCA;
+    const size_t PP = (size_t)P;
+    DevState& D = h->D;
+    memset(&D, 0, sizeof(D));
+    bool ok = true;
+    // persistent state: particles (two buffers), weights, existence, estimates
+    for (int b = 0; b < 2; ++b) {
+        ok &= dalloc(h, &D.x[b], 6 * PP);
+        ok &= dalloc(h, &D.phi[b], (size_t)S_max * 6 * PP);
+        ok &= dalloc(h, &D.eta[b], (size_t)J * PP);
+    }
+    ok &= dalloc(h, &D.w_x, PP);
+    ok &= dalloc(h, &D.w_y, (size_t)S_max * PP);
+    ok &= dalloc(h, &D.w_alpha, (size_t)S_max * PP);
+    ok &= dalloc(h, &D.w_eta, (size_t)J * PP);
+    ok &= dalloc(h, &D.p_pr, (size_t)S_max * J);
+    ok &= dalloc(h, &D.zeta, (size_t)S_max * J);
+    ok &= dalloc(h, &D.p_s, (size_t)S_max);
+    ok &= dalloc(h, &D.llr_w, (size_t)S_max * J);
+    ok &= dalloc(h, &D.W, (size_t)S_max);
+    ok &= dalloc(h, &D.eta_bar, (size_t)J);
+    ok &= dalloc(h, &D.kdl, (size_t)S_max * J * SCA);
+    ok &= dalloc(h, &D.kerr, 1);
+    ok &= dalloc(h, &D.ky0, (size_t)S_max * J * SCA);
+    ok &= dalloc(h, &D.kJ0, (size_t)S_max * J);
+    ok &= dalloc(h, &D.nu_T, (size_t)J * 4 * S_max);
+    ok &= dalloc(h, &D.nu_c, (size_t)J * 2);
+    const int nbel = bel_count(S_max, J);
+    ok &= dalloc(h, &D.bel, bel_total(S_max, J));
+    ok &= dalloc(h, &D.Lchol, (size_t)nbel * 36);
+    ok &= dalloc(h, &D.ctrl, (size_t)4 + S_max);
+    ok &= dalloc(h, &D.step, 1);
+    const EstLayout E{S_max, J};
+    ok &= dalloc(h, &D.est, E.total());
+    ok &= dalloc(h, &h->nu_b, (size_t)J * (S_max + 1) * 2);
+    h->wsp = ws_plan(h->G, P, S_max, SCA, h->nsplit_max);
+    if (ok && own_ws) {
+        void* q = nullptr;
+        ok &= cudaMalloc(&q, h->wsp.total) == cudaSuccess;
+        if (ok) {
+            cudaMemsetAsync(q, 0, h->wsp.total, h->st);
+            h->ws_owned = true;
+            ws_bind(h, static_cast<char*>(q));
+        }
+    }
+    if (ok) {
+        ok &= cudaMallocHost(&h->h_ctrl, (4 + S_max) * sizeof(int)) == cudaSuccess;
+        ok &= cudaMallocHost(&h->h_est, E.total() * sizeof(double)) == cudaSuccess;
+    }
+    if (!ok) {
+        *err = "device allocation failed";
+        bp_free(h);
+        return BP_ERR_CUDA;
+    }
+    D.cur = 0;
+    launch_init(h->G, h->Pm, D, S0, h->st);
+    h->launches += 1;
+    h->S = S0; h->S_upd = S0; h->n = 0; h->phase = 0;
+    if (cudaStreamSynchronize(h->st) != cudaSuccess || cudaGetLastError() != cudaSuccess) {
+        *err = std::string("bp_init: ") + cudaGetErrorString(cudaGetLastError());
+        bp_free(h);
+        return BP_ERR_CUDA;
+    }
+    *out = h;
+    return BP_OK;
+}
+
+bool dynamic_pf_count(const bp_handle* h) { return h->Pm.Q > 0 || h->Pm.T_pru > 0.0; }
+
+void predict_enqueue(bp_handle* h) {
+    const int S_old = h->S;
+    int S_new = S_old;
+    if (h->Pm.Q > 0) {
+        S_new = std::min(S_old + h->Pm.Q, h->S_max);
+        h->births_skipped += S_old + h->Pm.Q - S_new;
+    }
+    mark(h, 0);
+    h->launches += launch_predict(h->G, h->Pm, h->D, S_old, S_new, h->st);
+    if (h->prof_on) { cudaEventRecord(h->ev[BP_PROF_STAGES], h->st); h->ev_valid[0] = true; }
+    h->S = S_new;
+    h->n += 1;
+    h->phase = 1;
+}
+
+void update_enqueue(bp_handle* h, const float* z_dev) {
+    const int S = h->S, J = h->J, P = h->P;
+    DevState& D = h->D;
+    mark(h, 1);
+    launch_row_sums(h->Pm, D, S, J, h->st);
+    mark(h, 2);
+    int nsplit = std::max(1, (4 * 152 + S * J - 1) / (S * J));
+    nsplit = std::min(nsplit, std::max(1, P / 256));
+    nsplit = std::min(nsplit, h->nsplit_max);
+    launch_geom(h->G, h->Pm, D, S, h->st);
+    launch_table(h->G, h->Pm, D, S, nsplit, h->st);
+    mark(h, 3);
+    launch_stage(h->G, h->Pm, D, S, h->SCA, z_dev, h->gram, h->nu_b, h->V64, h->st);
+    if (S > 32) launch_kappa_btile(h->G, D, S, h->SCA, h->st);   // B tiles of the tensor-core variant (SC = 64)
+    mark(h, 4);
+    launch_kappa(h->G, h->Pm, D, S, h->SCA, h->st);
+    mark(h, 5);
+    launch_iota(h->G, h->Pm, D, S, z_dev, h->st);
+    launch_iota_repair(h->G, h->Pm, D, S, z_dev, h->st);
+    mark(h, 6);
+    launch_nu(h->G, h->Pm, D, S, h->st);
+    mark(h, 7);
+    launch_normalize(h->G, h->Pm, D, S, h->st);
+    mark(h, 8);
+    launch_resample(h->G, h->Pm, D, S, h->cdf, h->st);
+    if (h->prof_on) {
+        cudaEventRecord(h->ev[BP_PROF_STAGES], h->st);
+        for (int i = 1; i < BP_PROF_STAGES; ++i) h->ev_valid[i] = true;
+    }
+    h->launches += 1 + 3 + 3 + 1 + 2 + 1 + 5 + 3 + ((S > 32 && D.kB && kappa_tc_ok(h->G, h->SCA)) ? 1 : 0);
+    h->D.cur = 1 - h->D.cur;
+    h->S_upd = S;
+    h->phase = 0;
+    if (dynamic_pf_count(h)) cudaMemcpyAsync(h->h_ctrl, D.ctrl, 4 * sizeof(int), cudaMemcpyDeviceToHost, h->st);
+}
+
+void update_finish(bp_handle* h) {
+    if (dynamic_pf_count(h)) h->S = h->h_ctrl[1];
+}

@@ -10,7 +10,7 @@
 namespace bp {
 
 constexpr int J_MAX = 16;
-constexpr int NF_MAX = 64;
+constexpr int NF_MAX = 128;
 constexpr int MY_MAX = 16;
 constexpr int MZ_MAX = 16;
 constexpr int NZ_MAX = 2048;
@@ -78,6 +78,9 @@ __device__ inline U4 draw(const DevParams& P, uint32_t item, uint32_t n, uint32_
 
 // ((x >> 8) + 1/2) 2^-24: uniform in (0,1), exact in FP32
 __device__ inline float u24(uint32_t x) { return ((float)(x >> 8) + 0.5f) * 5.9604644775390625e-8f; }
+// the same uniform exactly, ((x >> 8) + 1/2) 2^-24 in FP64 (the FP32 form above rounds the
+// half away for x >= 2^31: within FP32 rounding of the draws it feeds)
+__device__ inline double u24d(uint32_t x) { return ((double)(x >> 8) + 0.5) * 5.9604644775390625e-8; }
 // (x + 1/2) 2^-32: uniform in (0,1), exact in FP64
 __host__ __device__ inline double u32d(uint32_t x) { return ((double)x + 0.5) * 2.3283064365386963e-10; }
 
@@ -330,7 +333,6 @@ struct DevState {
     double* tab_part; // table partial sums [nsplit][3][S_max][J][Nz] double2
     double* W;        // S_max    sum_p w_alpha
     double* eta_bar;  // J
-    double* sums_part;// partial sums for W / eta_bar
     // kappa stage outputs (per (s,j))
     float2* kV;       // [S_max][J][Nz][S_cap]   whitened basis, column S_cap-1 = r0 (FP32 part)
     float2* kr0l;     // [S_max][J][Nz]          low part of r0 (r0 = FP32 part + low part)
@@ -342,15 +344,13 @@ struct DevState {
     // nu stage outputs (per j)
     double* nu_T;     // [J][S_max] diag a_k, [J][S_max] |offdiag|^2, [J][S_max] double2 b'
     double* nu_c;     // [J][2] |e|^2, constant
-    // iota inputs (per (s,j) FP32 copies)
-    float* iota_pi;   // [S_max][J]
-    float2* zf;       // J x Nz (copy of the observation)
     // normalisation scratch
     double* red_part; // block partials
     double* bel;      // per-belief results (see k_norm.cu)
     float* Lchol;     // per-belief jitter factors
     int* idx;         // (1 + S_max + J) x P resampling indices
     int* ctrl;        // [0] S, [1] S_next, [2] births_skipped, [3] status, [4..] keep map
+    int* step;        // [0] step index n of the Philox counters, advanced on the device (k_step_advance)
     double* est;      // estimates buffer
 };
 

@@ -4,6 +4,15 @@
 
 namespace bp {
 
+// Largest dynamic shared memory a block may opt in to on the current device.
+int smem_optin();
+// Raises a kernel's dynamic shared-memory limit to the opt-in maximum less its static
+// shared memory (once per kernel), not to one launch's need: launches of one kernel
+// with different sizes from several streams, or replayed from a captured graph, then
+// never meet a limit set for a smaller launch.
+void smem_allow_max(const void* kernel);
+
+
 // per-belief result buffer (doubles); belief index b: 0 = MT, 1 + s = PF s, 1 + S_max + j = eta_j
 constexpr int BEL_STRIDE = 16;   // per belief: [0] max, [1] lse, [2] logC, [3] sum w^2 factor, [4..9] mean, [10] active dims
 inline __host__ __device__ int bel_count(int S_max, int J) { return 1 + S_max + J; }
@@ -87,8 +96,8 @@ __device__ inline float factors_from_geo_folded(const DevGeom& G, float4 g, floa
 void launch_geom(const DevGeom& G, const DevParams& Pm, const DevState& D, int S, cudaStream_t st);
 void launch_iota_repair(const DevGeom& G, const DevParams& Pm, const DevState& D, int S, const float* z, cudaStream_t st);
 
-void launch_init(const DevGeom& G, const DevParams& Pm, const DevState& D, cudaStream_t st);
-void launch_predict(const DevGeom& G, const DevParams& Pm, const DevState& D, int n, int S_old, int S_new, cudaStream_t st);
+void launch_init(const DevGeom& G, const DevParams& Pm, const DevState& D, int S0, cudaStream_t st);
+int launch_predict(const DevGeom& G, const DevParams& Pm, const DevState& D, int S_old, int S_new, cudaStream_t st);
 void launch_row_sums(const DevParams& Pm, const DevState& D, int S, int J, cudaStream_t st);
 void launch_table(const DevGeom& G, const DevParams& Pm, const DevState& D, int S, int nsplit, cudaStream_t st);
 void launch_stage(const DevGeom& G, const DevParams& Pm, const DevState& D, int S, int SC, const float* z,
@@ -99,8 +108,8 @@ size_t kappa_btile_floats(const DevGeom& G, int S_max);
 void launch_kappa_btile(const DevGeom& G, const DevState& D, int S, int SCA, cudaStream_t st);
 void launch_iota(const DevGeom& G, const DevParams& Pm, const DevState& D, int S, const float* z, cudaStream_t st);
 void launch_nu(const DevGeom& G, const DevParams& Pm, const DevState& D, int S, cudaStream_t st);
-int launch_normalize(const DevGeom& G, const DevParams& Pm, const DevState& D, int S, int n, cudaStream_t st);
-void launch_resample(const DevGeom& G, const DevParams& Pm, const DevState& D, int S, int n, double* cdf, cudaStream_t st);
+int launch_normalize(const DevGeom& G, const DevParams& Pm, const DevState& D, int S, cudaStream_t st);
+void launch_resample(const DevGeom& G, const DevParams& Pm, const DevState& D, int S, double* cdf, cudaStream_t st);
 void launch_synth(const DevGeom& G, int n_steps, int step0, const double* x_pos, int K, const double* sfv,
                   const double* rho, const int* c_off, const double* c_sfv, const double* c_rho,
                   double* zbuf, uint32_t k0, uint32_t k1, cudaStream_t st);

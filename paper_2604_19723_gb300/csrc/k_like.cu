@@ -57,8 +57,8 @@ __global__ void __launch_bounds__(256, (SC <= 16 ? 2 : 1)) k_kappa(DevGeom G, De
     float* sB = sA + (TC ? 4 * 128 * KC : 0);                          // TC: [hi, lo][128 x KC]
     uint64_t* mbar = reinterpret_cast<uint64_t*>(sB + (TC ? 2 * 128 * KC : 0));   // TC: [2]
     uint32_t* tslot = reinterpret_cast<uint32_t*>(mbar + (TC ? 2 : 0));          // TC: TMEM base
-    float4* Vs = TC ? reinterpret_cast<float4*>(sA + 6 * 128 * KC + 8) : sm4;    // [Nz][NP]
-    float2* dls = reinterpret_cast<float2*>(Vs + (size_t)Nz * NP);     // [SC] 1/lambda_c (.x)
+    float4* Vs = TC ? reinterpret_cast<float4*>(sA + 6 * 128 * KC + 8) : sm4;    // [fch * Nm][NP] rows staged
+    float2* dls = reinterpret_cast<float2*>(Vs + (size_t)fch * Nm * NP); // [SC] 1/lambda_c (.x)
     float2* y0s = dls + SC;                                            // [SC] w_c
     float2* fac = y0s + SC;                                            // [nfac][KT]
     float2* r0ls = fac + (size_t)(G.Nf + G.My + G.Mz) * KT;           // [fch * Nm] low part of r0
@@ -989,10 +989,19 @@ __global__ void k_kappa_btile(DevGeom G, DevState D, int SCA, float* __restrict_
     }
 }
 
-// the tensor-core variant applies with 64 basis columns (SCA = 64) and 2 My Mz in {8, 16, 32}
+// dynamic shared memory of the tensor-core variant: A/B operand tiles and barriers, the
+// factors of 256 particles, all Nz rows of V (64 columns) and the low part of r0
+static size_t kappa_tc_smem(const DevGeom& G) {
+    const size_t Nm = (size_t)G.My * G.Mz, nfac = (size_t)G.Nf + G.My + G.Mz;
+    const size_t tcb = 6 * 128 * (2 * Nm) * sizeof(float) + 32;
+    const size_t fixed = (2 * 64 + nfac * 256) * sizeof(float2);
+    return tcb + fixed + (size_t)G.Nf * Nm * 65 * sizeof(float2);
+}
+// the tensor-core variant applies with 64 basis columns (SCA = 64), 2 My Mz in {8, 16, 32}
+// and every row of V resident in shared memory
 bool kappa_tc_ok(const DevGeom& G, int SCA) {
     const int KC = 2 * G.My * G.Mz;
-    return SCA == 64 && (KC == 8 || KC == 16 || KC == 32);
+    return SCA == 64 && (KC == 8 || KC == 16 || KC == 32) && kappa_tc_smem(G) <= 227 * 1024;
 }
 size_t kappa_btile_floats(const DevGeom& G, int S_max) {
     return (size_t)S_max * G.J * G.Nf * 2 * 128 * (2 * G.My * G.Mz);
@@ -1011,20 +1020,16 @@ static void launch_kappa_sc(const DevGeom& G, const DevParams& Pm, const DevStat
     dim3 grid((Pm.P + 255) / 256, S);
     if constexpr (SC == 64) {
         if (D.kB && kappa_tc_ok(G, SCA)) {
-            const size_t tcb = (size_t)6 * 128 * (2 * Nm) * sizeof(float) + 32;
-            const size_t smem = tcb + fixed + (size_t)G.Nf * per_f;
-            if (smem <= 227 * 1024) {
-                cudaFuncSetAttribute(k_kappa<SC, true>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
-                k_kappa<SC, true><<<grid, 256, smem, st>>>(G, Pm, D, S, SCA, G.Nf, D.kB);
-                return;
-            }
+            smem_allow_max((const void*)k_kappa<SC, true>);
+            k_kappa<SC, true><<<grid, 256, kappa_tc_smem(G), st>>>(G, Pm, D, S, SCA, G.Nf, D.kB);
+            return;
         }
     }
     const size_t limit = 200 * 1024;
     int fch = G.Nf;
     while (fch > 1 && fixed + fch * per_f > limit) fch = (fch + 1) / 2;
     const size_t smem = fixed + fch * per_f;
-    cudaFuncSetAttribute(k_kappa<SC, false>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    smem_allow_max((const void*)k_kappa<SC, false>);
     k_kappa<SC, false><<<grid, 256, smem, st>>>(G, Pm, D, S, SCA, fch, nullptr);
 }
 
@@ -1046,7 +1051,7 @@ void launch_iota(const DevGeom& G, const DevParams& Pm, const DevState& D, int S
     while (wpb > 1 && (size_t)G.Nz * sizeof(float2) + wpb * per_warp > 64 * 1024) wpb /= 2;
     const size_t smem = (size_t)G.Nz * sizeof(float2) + wpb * per_warp;
     cudaMemsetAsync(D.flags, 0, sizeof(int), st);
-    cudaFuncSetAttribute(k_iota, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    smem_allow_max((const void*)k_iota);
     k_iota<<<(Pm.P + wpb - 1) / wpb, 32 * wpb, smem, st>>>(G, Pm, D, S, z);
 }
 
@@ -1056,7 +1061,7 @@ void launch_iota_repair(const DevGeom& G, const DevParams& Pm, const DevState& D
     const int all = S >= IOTA_FF_ALL_S ? 1 : 0;
     if (all) cudaMemsetAsync(D.flags, 0, sizeof(int), st);
     constexpr int NCG = IOTA_BLK_NCG;
-    cudaFuncSetAttribute(k_iota_blk<NCG>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    smem_allow_max((const void*)k_iota_blk<NCG>);
     const int wave = (NCG == 4 ? 3 : 2) * 152;
     const int blocks = all ? std::min(Pm.P, 16 * wave) : wave;
     k_iota_blk<NCG><<<blocks, 32 * NCG, smem, st>>>(G, Pm, D, S, z, all);

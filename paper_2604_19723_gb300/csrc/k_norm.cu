@@ -187,8 +187,9 @@ __global__ void k_norm_final(DevGeom G, DevParams Pm, DevState D, int S, int NB,
 }
 
 // estimates, declaration, pruning map; single thread
-__global__ void k_estimate(DevGeom G, DevParams Pm, DevState D, int S, int n) {
+__global__ void k_estimate(DevGeom G, DevParams Pm, DevState D, int S) {
     if (threadIdx.x != 0 || blockIdx.x != 0) return;
+    const int n = D.step[0];
     const int J = G.J, SM = Pm.S_max;
     const EstLayout E{SM, J};
     double* est = D.est;
@@ -240,7 +241,7 @@ __global__ void k_norm_weights(DevGeom G, DevParams Pm, DevState D, int S) {
     }
 }
 
-int launch_normalize(const DevGeom& G, const DevParams& Pm, const DevState& D, int S, int n, cudaStream_t st) {
+int launch_normalize(const DevGeom& G, const DevParams& Pm, const DevState& D, int S, cudaStream_t st) {
     const int P = Pm.P;
     int NB = (P + 4095) / 4096;
     if (NB > 64) NB = 64;
@@ -249,15 +250,16 @@ int launch_normalize(const DevGeom& G, const DevParams& Pm, const DevState& D, i
     k_norm_max<<<dim3(NB, nb), 256, 0, st>>>(G, Pm, D, S, NB);
     k_norm_sum<<<dim3(NB, nb), 256, 0, st>>>(G, Pm, D, S, NB, part);
     k_norm_final<<<(nb + 63) / 64, 64, 0, st>>>(G, Pm, D, S, NB, part);
-    k_estimate<<<1, 32, 0, st>>>(G, Pm, D, S, n);
+    k_estimate<<<1, 32, 0, st>>>(G, Pm, D, S);
     k_norm_weights<<<dim3((P + 255) / 256 < 256 ? (P + 255) / 256 : 256, nb), 256, 0, st>>>(G, Pm, D, S);
     return 5;
 }
 
 // ---------------------------------------------------------------- systematic resampling
 // one block per kept belief; CDF in FP64 (chunked per thread, block exclusive scan)
-__global__ void __launch_bounds__(1024) k_resample(DevGeom G, DevParams Pm, DevState D, int S, int n, double* cdf_all) {
+__global__ void __launch_bounds__(1024) k_resample(DevGeom G, DevParams Pm, DevState D, int S, double* cdf_all) {
     const int P = Pm.P, SM = Pm.S_max, J = G.J;
+    const int n = D.step[0];
     const int S_next = D.ctrl[1];
     const int a = blockIdx.x;   // 0: MT, 1..S_next: kept PF, then eta
     int b, kind, index;
@@ -306,8 +308,9 @@ __global__ void __launch_bounds__(1024) k_resample(DevGeom G, DevParams Pm, DevS
 }
 
 // gather + jitter into the other buffer; thread per output slot
-__global__ void k_gather(DevGeom G, DevParams Pm, DevState D, int n) {
+__global__ void k_gather(DevGeom G, DevParams Pm, DevState D) {
     const int P = Pm.P, SM = Pm.S_max, J = G.J;
+    const int n = D.step[0];
     const int i = blockIdx.x * blockDim.x + threadIdx.x;
     const int S_next = D.ctrl[1];
     const int nxt = 1 - D.cur;
@@ -368,10 +371,10 @@ __global__ void k_compact(DevGeom G, DevParams Pm, DevState D) {
         }
 }
 
-void launch_resample(const DevGeom& G, const DevParams& Pm, const DevState& D, int S, int n, double* cdf, cudaStream_t st) {
+void launch_resample(const DevGeom& G, const DevParams& Pm, const DevState& D, int S, double* cdf, cudaStream_t st) {
     const int nb = 1 + S + G.J;
-    k_resample<<<nb, 1024, 0, st>>>(G, Pm, D, S, n, cdf);
-    k_gather<<<(Pm.P + 255) / 256, 256, 0, st>>>(G, Pm, D, n);
+    k_resample<<<nb, 1024, 0, st>>>(G, Pm, D, S, cdf);
+    k_gather<<<(Pm.P + 255) / 256, 256, 0, st>>>(G, Pm, D);
     k_compact<<<(Pm.P + 255) / 256, 256, 0, st>>>(G, Pm, D);
 }
 

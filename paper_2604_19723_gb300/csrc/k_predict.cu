@@ -8,9 +8,12 @@
 
 namespace bp {
 
-__global__ void k_init(DevGeom G, DevParams Pm, DevState D) {
+// Time-0 beliefs; slots 1 .. S0-1 (if any) are PFs drawn from the birth density over
+// the whole birth box, with existence p_B and PR existence p_B^PR like a new PF.
+__global__ void k_init(DevGeom G, DevParams Pm, DevState D, int S0) {
     const int p = blockIdx.x * blockDim.x + threadIdx.x;
     const int P = Pm.P;
+    if (p < S0 * G.J) D.p_pr[p] = Pm.pB_pr;
     if (p >= P) return;
     float* x = D.x[D.cur];
     float* phi = D.phi[D.cur];
@@ -18,7 +21,7 @@ __global__ void k_init(DevGeom G, DevParams Pm, DevState D) {
     // MT: uniforms 0..5 from blocks 0, 1
     const U4 a = draw(Pm, p, 0, RNG_INIT_MT, 0, 0);
     const U4 b = draw(Pm, p, 0, RNG_INIT_MT, 0, 1);
-    const double u[6] = {u24(a.x), u24(a.y), u24(a.z), u24(a.w), u24(b.x), u24(b.y)};
+    const double u[6] = {u24d(a.x), u24d(a.y), u24d(a.z), u24d(a.w), u24d(b.x), u24d(b.y)};
     for (int k = 0; k < 3; ++k) {
         x[k * P + p] = (float)(Pm.p_min[k] + (Pm.p_max[k] - Pm.p_min[k]) * u[k]);
         x[(3 + k) * P + p] = (float)(-Pm.v_max[k] + 2.0 * Pm.v_max[k] * u[3 + k]);
@@ -26,29 +29,51 @@ __global__ void k_init(DevGeom G, DevParams Pm, DevState D) {
     if (Pm.motion_dims == 2) x[5 * P + p] = 0.0f;
     for (int j = 0; j < G.J; ++j) {
         const U4 e = draw(Pm, p, 0, RNG_INIT_ETA, j, 0);
-        eta[j * P + p] = (float)(Pm.eta_min + (Pm.eta_max - Pm.eta_min) * (double)u24(e.x));
+        eta[j * P + p] = (float)(Pm.eta_min + (Pm.eta_max - Pm.eta_min) * u24d(e.x));
         D.w_eta[j * P + p] = 1.0 / P;
     }
     // LoS drawn like a new PF (birth draws of slot 0 at n = 0)
     const U4 c = draw(Pm, p, 0, RNG_BIRTH, 0, 0);
     const U4 d = draw(Pm, p, 0, RNG_BIRTH, 0, 1);
     phi[0 * P + p] = 0.f; phi[1 * P + p] = 0.f; phi[2 * P + p] = 0.f;
-    phi[3 * P + p] = (float)(Pm.gamma_max * (double)u24(c.w));
+    phi[3 * P + p] = (float)(Pm.gamma_max * u24d(c.w));
     if (Pm.zero_mean) {
         phi[4 * P + p] = 0.f; phi[5 * P + p] = 0.f;
     } else {
-        const double r = Pm.mu_max * sqrt((double)u24(d.x));
-        const double t = 2.0 * (double)u24(d.y);
+        const double r = Pm.mu_max * sqrt(u24d(d.x));
+        const double t = 2.0 * u24d(d.y);
         phi[4 * P + p] = (float)(r * cospi(t));
         phi[5 * P + p] = (float)(r * sinpi(t));
     }
+    for (int s = 1; s < S0; ++s) {
+        const U4 e = draw(Pm, p, 0, RNG_BIRTH, s, 0);
+        const U4 f = draw(Pm, p, 0, RNG_BIRTH, s, 1);
+        const double v[6] = {u24d(e.x), u24d(e.y), u24d(e.z), u24d(e.w), u24d(f.x), u24d(f.y)};
+        float* ph = phi + (size_t)s * 6 * P;
+        for (int k = 0; k < 3; ++k) ph[k * P + p] = (float)(2.0 * Pm.p_min[k] + 2.0 * (Pm.p_max[k] - Pm.p_min[k]) * v[k]);
+        ph[3 * P + p] = (float)(Pm.gamma_max * v[3]);
+        if (Pm.zero_mean) {
+            ph[4 * P + p] = 0.f; ph[5 * P + p] = 0.f;
+        } else {
+            const double r = Pm.mu_max * sqrt(v[4]);
+            ph[4 * P + p] = (float)(r * cospi(2.0 * v[5]));
+            ph[5 * P + p] = (float)(r * sinpi(2.0 * v[5]));
+        }
+        D.w_y[(size_t)s * P + p] = Pm.pB / P;
+    }
     D.w_x[p] = 1.0 / P;
     D.w_y[p] = Pm.pB / P;
-    if (p < G.J) D.p_pr[0 * G.J + p] = Pm.pB_pr;
 }
 
-__global__ void k_predict(DevGeom G, DevParams Pm, DevState D, int n, int S_old, int S_new) {
+// n <- n + 1 at the start of a prediction; the step index lives on the device so that
+// a captured step (CUDA graph) draws fresh Philox counters at every replay
+__global__ void k_step_advance(DevState D) {
+    if (threadIdx.x == 0 && blockIdx.x == 0) D.step[0] += 1;
+}
+
+__global__ void k_predict(DevGeom G, DevParams Pm, DevState D, int S_old, int S_new) {
     const int p = blockIdx.x * blockDim.x + threadIdx.x;
+    const int n = D.step[0];
     const int P = Pm.P;
     const int J = G.J;
     if (p < S_new * J) {   // zeta of every (s, j)
@@ -106,7 +131,7 @@ __global__ void k_predict(DevGeom G, DevParams Pm, DevState D, int n, int S_old,
         const int q = s - S_old;
         const U4 a = draw(Pm, p, n, RNG_BIRTH, s, 0);
         const U4 b = draw(Pm, p, n, RNG_BIRTH, s, 1);
-        const double u[6] = {u24(a.x), u24(a.y), u24(a.z), u24(a.w), u24(b.x), u24(b.y)};
+        const double u[6] = {u24d(a.x), u24d(a.y), u24d(a.z), u24d(a.w), u24d(b.x), u24d(b.y)};
         double lo[3], hi[3];
         for (int k = 0; k < 3; ++k) { lo[k] = 2.0 * Pm.p_min[k]; hi[k] = 2.0 * Pm.p_max[k]; }
         const double width = (hi[0] - lo[0]) / Pm.Q;
@@ -155,14 +180,16 @@ __global__ void k_row_sums(DevParams Pm, DevState D, int S, int J) {
     }
 }
 
-void launch_init(const DevGeom& G, const DevParams& Pm, const DevState& D, cudaStream_t st) {
-    k_init<<<(Pm.P + 255) / 256, 256, 0, st>>>(G, Pm, D);
+void launch_init(const DevGeom& G, const DevParams& Pm, const DevState& D, int S0, cudaStream_t st) {
+    const int nthr = max(Pm.P, S0 * G.J);
+    k_init<<<(nthr + 255) / 256, 256, 0, st>>>(G, Pm, D, S0);
 }
 
-void launch_predict(const DevGeom& G, const DevParams& Pm, const DevState& D, int n, int S_old, int S_new,
-                    cudaStream_t st) {
+int launch_predict(const DevGeom& G, const DevParams& Pm, const DevState& D, int S_old, int S_new, cudaStream_t st) {
     const int nthr = max(Pm.P, S_new * G.J);
-    k_predict<<<(nthr + 255) / 256, 256, 0, st>>>(G, Pm, D, n, S_old, S_new);
+    k_step_advance<<<1, 32, 0, st>>>(D);
+    k_predict<<<(nthr + 255) / 256, 256, 0, st>>>(G, Pm, D, S_old, S_new);
+    return 2;
 }
 
 void launch_row_sums(const DevParams& Pm, const DevState& D, int S, int J, cudaStream_t st) {

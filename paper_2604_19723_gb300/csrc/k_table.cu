@@ -20,6 +20,8 @@
 // nu (S-V "Noise variance update message"): G = M^H M is reduced once per j
 // to a real symmetric tridiagonal T = Q^H G Q (Householder), with b = Q^H M^H e;
 // each particle then needs O(S) work (k_like.cu).
+#include <vector>
+
 #include "bp_internal.cuh"
 #include "bp_kernels.cuh"
 
@@ -645,13 +647,13 @@ void launch_table(const DevGeom& G, const DevParams& Pm, const DevState& D, int 
     const size_t smem = (size_t)chunk * per_particle;
     dim3 grid(nsplit, S, G.J);
     switch (ept) {
-        case 1: cudaFuncSetAttribute(k_table<1>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+        case 1: smem_allow_max((const void*)k_table<1>);
                 k_table<1><<<grid, bs, smem, st>>>(G, Pm, D, S, nsplit, chunk); break;
-        case 2: cudaFuncSetAttribute(k_table<2>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+        case 2: smem_allow_max((const void*)k_table<2>);
                 k_table<2><<<grid, bs, smem, st>>>(G, Pm, D, S, nsplit, chunk); break;
-        case 3: case 4: cudaFuncSetAttribute(k_table<4>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+        case 3: case 4: smem_allow_max((const void*)k_table<4>);
                 k_table<4><<<grid, bs, smem, st>>>(G, Pm, D, S, nsplit, chunk); break;
-        default: cudaFuncSetAttribute(k_table<8>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+        default: smem_allow_max((const void*)k_table<8>);
                 k_table<8><<<grid, bs, smem, st>>>(G, Pm, D, S, nsplit, chunk); break;
     }
     const int tot = S * G.J * Nz;
@@ -666,11 +668,32 @@ void launch_stage(const DevGeom& G, const DevParams& Pm, const DevState& D, int 
     const int K = S - 1;
     const size_t sm1 = (3 * (size_t)K * K + 3 * (size_t)K) * sizeof(double2) + ((size_t)K + 8) * sizeof(double) +
                        32 * sizeof(JRot<double>);
-    cudaFuncSetAttribute(k_stage_kappa, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm1);
+    smem_allow_max((const void*)k_stage_kappa);
     k_stage_kappa<<<dim3(S, G.J), 256, sm1, st>>>(G, Pm, D, S, SC, z, gram, V64);
     const size_t sm2 = ((size_t)S * S + 3 * (size_t)S) * sizeof(double2);
-    cudaFuncSetAttribute(k_nu_tridiag, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm2);
+    smem_allow_max((const void*)k_nu_tridiag);
     k_nu_tridiag<<<G.J, 128, sm2, st>>>(Pm, D, S, gram, nu_b);
+}
+
+void smem_allow_max(const void* kernel) {
+    static std::vector<const void*> done;
+    for (const void* k : done)
+        if (k == kernel) return;
+    cudaFuncAttributes a{};
+    cudaFuncGetAttributes(&a, kernel);
+    cudaFuncSetAttribute(kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, smem_optin() - (int)a.sharedSizeBytes);
+    done.push_back(kernel);
+}
+
+int smem_optin() {
+    static int v = 0;
+    if (v == 0) {
+        int dev = 0, a = 0;
+        cudaGetDevice(&dev);
+        cudaDeviceGetAttribute(&a, cudaDevAttrMaxSharedMemoryPerBlockOptin, dev);
+        v = a > 0 ? a : 48 * 1024;
+    }
+    return v;
 }
 
 }  // namespace bp

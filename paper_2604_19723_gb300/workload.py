@@ -282,6 +282,27 @@ def workload(name: str) -> Dict:
     raise KeyError(name)
 
 
+def batched_scenarios(n: int, seed: int = 21, S_range=(1, 64), P_range=(256, 16384), Nz_range=(5, 300)) -> List[Dict]:
+    """Shapes of the batched workload: n independent scenarios with S ~ U{1..64} PFs
+    (held fixed: no birth, no pruning), P ~ U{256..16384} particles and Nz ~ U{5..300}
+    samples per PA at J = 4.  Nz < 16 is one antenna with Nf = Nz frequencies, larger
+    Nz a 2 x 2 URA with Nf = ceil(Nz / 4) (so Nz rounds up to a multiple of 4).  Each
+    entry: geom, params, P, S, seed (its own Philox key and truth)."""
+    rng = np.random.default_rng(seed)
+    out = []
+    for i in range(n):
+        S = int(rng.integers(S_range[0], S_range[1] + 1))
+        P = int(rng.integers(P_range[0], P_range[1] + 1))
+        nz = int(rng.integers(Nz_range[0], Nz_range[1] + 1))
+        if nz < 16:
+            g = make_geometry(J=4, Nf=nz, My=1, Mz=1, B=200e6)
+        else:
+            g = make_geometry(J=4, Nf=-(-nz // 4), My=2, Mz=2, B=200e6)
+        prm = Params(T=0.1, sigma_v=0.5, sigma_mu=3e-3, sigma_sfv=1e-4, Q=0, T_pru=0.0)
+        out.append(dict(geom=g, params=prm, P=P, S=S, seed=seed * 100003 + i))
+    return out
+
+
 # --------------------------------------------------------------------------
 # particle states (inputs for stage-wise parity; FP32 storage as in the SoA layout)
 # --------------------------------------------------------------------------

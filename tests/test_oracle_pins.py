@@ -463,3 +463,53 @@ def test_synthetic_noise_and_snr():
     assert np.sum(np.abs(sig) ** 2) / (g.Nz * g.J) / eta == pytest.approx(100.0, rel=1e-12)
     res = np.concatenate([synth.observe(scn, n, eta, 2) - synth.clean_signal(scn, n) for n in (1, 2, 3)]).ravel()
     assert np.mean(np.abs(res) ** 2) / eta == pytest.approx(1.0, abs=5 * math.sqrt(1.0 / res.size))
+
+
+# ---------------------------------------------------------------- time-0 beliefs with S0 PFs
+def test_init_state_birth_pfs_follow_the_birth_density():
+    """Slots 1 .. S0-1 are draws of f_B (Sec. III-B2) over the whole birth box: each
+    coordinate uniform on [2 p_min, 2 p_max] (mean and variance of the uniform law),
+    gamma uniform on [0, gamma_max], mu uniform on the disc of radius mu_max
+    (E|mu|^2 = mu_max^2 / 2, circular phase); weights p_B / P, PR existence p_B^PR;
+    S0 = 1 is the plain time-0 belief."""
+    prm = W.Params()
+    P, J = 40000, 3
+    st0 = model.init_state(prm, J, P, 5)
+    st = model.init_state(prm, J, P, 5, S0=4)
+    assert st.S == 4 and st0.S == 1
+    assert np.array_equal(st.x, st0.x) and np.array_equal(st.eta, st0.eta) and np.array_equal(st.phi[0], st0.phi[0])
+    lo, hi = np.asarray(prm.birth_min), np.asarray(prm.birth_max)
+    for s in range(1, 4):
+        ph = st.phi[s].astype(np.float64)
+        for k in range(3):
+            width = hi[k] - lo[k]
+            assert lo[k] <= ph[k].min() and ph[k].max() <= hi[k]
+            assert abs(ph[k].mean() - 0.5 * (lo[k] + hi[k])) < 5 * width / math.sqrt(12 * P)
+            assert ph[k].var() == pytest.approx(width ** 2 / 12, rel=0.03)
+        assert 0 <= ph[3].min() and ph[3].max() <= prm.gamma_max
+        assert abs(ph[3].mean() - 0.5 * prm.gamma_max) < 5 * prm.gamma_max / math.sqrt(12 * P)
+        m2 = ph[4] ** 2 + ph[5] ** 2
+        assert m2.max() <= prm.mu_max ** 2 * (1 + 1e-6)
+        assert m2.mean() == pytest.approx(0.5 * prm.mu_max ** 2, rel=0.03)
+        assert abs(np.mean(ph[4] + 1j * ph[5])) < 5 * prm.mu_max / math.sqrt(2 * P)
+    pB = model.birth_probability(prm.mu_B, max(prm.Q, 1))
+    assert np.allclose(st.w_y, pB / P) and np.allclose(st.p_pr, prm.pB_pr)
+    # independent slots: different draws
+    assert not np.allclose(st.phi[1], st.phi[2])
+
+
+def test_batched_scenario_shapes():
+    """The batched workload's shapes: S in 1..64, P in 256..16384, Nz in 5..300 with one
+    antenna (Nf = Nz) below 16 samples and a 2 x 2 URA (Nf = ceil(Nz / 4)) above."""
+    sc = W.batched_scenarios(2000, seed=3)
+    S = np.array([d["S"] for d in sc])
+    P = np.array([d["P"] for d in sc])
+    assert S.min() == 1 and S.max() == 64 and P.min() >= 256 and P.max() <= 16384
+    for d in sc:
+        g = d["geom"]
+        assert g.J == 4
+        if g.My == 1:
+            assert g.Mz == 1 and 5 <= g.Nf < 16 and g.Nz == g.Nf
+        else:
+            assert g.My == g.Mz == 2 and 16 <= g.Nz <= 300 + 3 and g.Nf == -(-g.Nz // 4)
+    assert len({d["seed"] for d in sc}) == len(sc)
