@@ -67,7 +67,14 @@ typedef struct {
  * disables pruning.  zero_mean = 1 selects the ZM variant (mu == 0).
  * mvec_scaling = 0 uses the m-vectors exactly as printed in Supplementary
  * Sec. S-V; 1 takes the square root of the existence factors.  regularize
- * = 1 applies the Gaussian-kernel jitter after resampling. */
+ * = 1 applies the Gaussian-kernel jitter after resampling.
+ * birth_proposal = 1 draws the positions of new PFs from the Gaussian proposal
+ * of Sec. IV-D ("An Efficient Birth Proposal PDF": residual of the observation
+ * after projecting out the LoS and legacy PFs, coherent Bartlett spectrum at
+ * N_g candidates uniform in the PF's partition, mode-matched mean and
+ * moment-matched covariance, weights 1_P / proposal density); 0 draws them
+ * from the birth density f_B.  The proposal needs the observation, so bp_update
+ * (not bp_predict) draws those particles.  1 <= N_g <= 65536. */
 typedef struct {
     double T, sigma_v;
     int motion_dims;
@@ -77,6 +84,7 @@ typedef struct {
     double T_dec, T_pru, gamma_max, mu_max, eta_min, eta_max;
     double p_min[3], p_max[3], v_max[3];
     int zero_mean, mvec_scaling, regularize;
+    int birth_proposal, N_g;
 } bp_params;
 
 /* Host view of a filter state (bp_get_state / bp_set_state) or of the
@@ -92,6 +100,9 @@ typedef struct {
 typedef struct {
     int n;      /* index of the last completed step (predicted: current step) */
     int S;      /* number of PFs including the LoS */
+    int S_legacy; /* predictions: PFs that existed before this step's births (slots
+                     S_legacy .. S-1 are new; 0 or S = none new); states: ignored,
+                     written as S */
     float* x;
     float* phi;
     float* eta;
@@ -169,8 +180,14 @@ bp_status bp_set_predicted(bp_handle* h, const bp_state_view* in);
  * what = BP_DIAG_LOGLIK: particle log-likelihood sums: log iota (P) summed over
  *        j, Delta_kappa (S x P) summed over j (log kappa~(phi,1) - log kappa~(.,0)),
  *        log nu (J x P), log omega~(1)-log omega~(0) (S x J); double.
- * what = BP_DIAG_INDICES: resampling indices, int32: MT (P), PF (S x P), eta (J x P). */
-enum { BP_DIAG_TABLE = 1, BP_DIAG_WEIGHTS = 2, BP_DIAG_LOGLIK = 3, BP_DIAG_INDICES = 4 };
+ * what = BP_DIAG_INDICES: resampling indices, int32: MT (P), PF (S x P), eta (J x P).
+ * what = BP_DIAG_PROPOSAL (birth_proposal = 1, new PFs in the last update; Qe =
+ *        their number, Ng = N_g): per new PF the statistics [32] doubles (valid,
+ *        i*, sum of costs, mu [3], C [3x3], L [3x3], 0-padded), the Bartlett costs
+ *        [Qe][Ng] and candidates [Qe][Ng][3] (double), the prediction weights
+ *        w_alpha [Qe][P] (double), then the new PFs' particle positions [Qe][3][P]
+ *        (float).  BP_ERR_STATE without a proposal in the last update. */
+enum { BP_DIAG_TABLE = 1, BP_DIAG_WEIGHTS = 2, BP_DIAG_LOGLIK = 3, BP_DIAG_INDICES = 4, BP_DIAG_PROPOSAL = 5 };
 bp_status bp_get_diag(bp_handle* h, int what, void* host, size_t bytes);
 
 /* Synthetic observations from the generative model (eq. observation-generative),

@@ -38,6 +38,8 @@ JITTER_ETA = 9
 INIT_MT = 10
 INIT_ETA = 11
 SYNTH_NOISE = 12
+BIRTH_CAND = 13      # candidate SFV positions of the birth proposal (item = candidate index, sub = partition)
+BIRTH_PROP = 14      # normals of particles drawn from the birth proposal (sub = PF slot)
 
 MAX_GAMMA_ATTEMPTS = 16
 

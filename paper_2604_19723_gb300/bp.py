@@ -20,7 +20,7 @@ LIB_PATH = os.path.join(_HERE, "_lib", "libbp.so")
 BP_OK = 0
 STATUS = {0: "BP_OK", 1: "BP_ERR_INVALID_ARG", 2: "BP_ERR_CUDA", 3: "BP_ERR_CAPACITY",
           4: "BP_ERR_NUMERIC", 5: "BP_ERR_TIMEOUT", 6: "BP_ERR_STATE"}
-DIAG_TABLE, DIAG_WEIGHTS, DIAG_LOGLIK, DIAG_INDICES = 1, 2, 3, 4
+DIAG_TABLE, DIAG_WEIGHTS, DIAG_LOGLIK, DIAG_INDICES, DIAG_PROPOSAL = 1, 2, 3, 4, 5
 
 ENTRY_POINTS = ("bp_init", "bp_predict", "bp_update", "bp_estimate", "bp_free", "bp_last_error",
                 "bp_get_state", "bp_set_state", "bp_get_predicted", "bp_set_predicted", "bp_get_diag",
@@ -52,11 +52,13 @@ class _Params(C.Structure):
                 ("T_dec", C.c_double), ("T_pru", C.c_double), ("gamma_max", C.c_double), ("mu_max", C.c_double),
                 ("eta_min", C.c_double), ("eta_max", C.c_double),
                 ("p_min", C.c_double * 3), ("p_max", C.c_double * 3), ("v_max", C.c_double * 3),
-                ("zero_mean", C.c_int), ("mvec_scaling", C.c_int), ("regularize", C.c_int)]
+                ("zero_mean", C.c_int), ("mvec_scaling", C.c_int), ("regularize", C.c_int),
+                ("birth_proposal", C.c_int), ("N_g", C.c_int)]
 
 
 class _StateView(C.Structure):
-    _fields_ = [("n", C.c_int), ("S", C.c_int), ("x", C.POINTER(C.c_float)), ("phi", C.POINTER(C.c_float)),
+    _fields_ = [("n", C.c_int), ("S", C.c_int), ("S_legacy", C.c_int),
+                ("x", C.POINTER(C.c_float)), ("phi", C.POINTER(C.c_float)),
                 ("eta", C.POINTER(C.c_float)), ("w_x", C.POINTER(C.c_double)), ("w_y", C.POINTER(C.c_double)),
                 ("w_eta", C.POINTER(C.c_double)), ("p_pr", C.POINTER(C.c_double))]
 
@@ -153,7 +155,8 @@ def _params_struct(p: Params) -> _Params:
     return _Params(p.T, p.sigma_v, p.motion_dims, p.c_eta, p.c_gamma, p.sigma_mu, p.sigma_sfv,
                    p.pS, p.pS_pr, p.pR_pr, p.pB_pr, p.mu_B, p.Q, p.T_dec, p.T_pru, p.gamma_max, p.mu_max,
                    p.eta_min, p.eta_max, (C.c_double * 3)(*p.p_min), (C.c_double * 3)(*p.p_max),
-                   (C.c_double * 3)(*p.v_max), p.zero_mean, p.mvec_scaling, p.regularize)
+                   (C.c_double * 3)(*p.v_max), p.zero_mean, p.mvec_scaling, p.regularize,
+                   p.birth_proposal, p.N_g)
 
 
 def _check(lib, h, status, what):
@@ -240,8 +243,8 @@ class Filter:
                     w_eta=np.zeros((J, P)), p_pr=np.zeros((S, J)))
         return arrs
 
-    def _struct(self, n, S, a):
-        return _StateView(n, S, _fptr(a["x"]), _fptr(a["phi"]), _fptr(a["eta"]), _dptr(a["w_x"]), _dptr(a["w_y"]),
+    def _struct(self, n, S, a, S_legacy=0):
+        return _StateView(n, S, S_legacy, _fptr(a["x"]), _fptr(a["phi"]), _fptr(a["eta"]), _dptr(a["w_x"]), _dptr(a["w_y"]),
                           _dptr(a["w_eta"]), _dptr(a["p_pr"]))
 
     def get_state(self) -> StateArrays:
@@ -265,15 +268,17 @@ class Filter:
         v = self._struct(0, 0, a)
         _check(self.lib, self.h, self.lib.bp_get_predicted(self.h, C.byref(v)), "bp_get_predicted")
         S = v.S
-        return dict(n=v.n, S=S, x=a["x"], phi=a["phi"][:S].copy(), eta=a["eta"], w_beta=a["w_x"],
+        return dict(n=v.n, S=S, S_legacy=v.S_legacy, x=a["x"], phi=a["phi"][:S].copy(), eta=a["eta"], w_beta=a["w_x"],
                     w_alpha=a["w_y"][:S].copy(), w_xi=a["w_eta"], zeta=a["p_pr"][:S].copy())
 
-    def set_predicted(self, n, S, x, phi, eta, w_beta, w_alpha, w_xi, zeta):
+    def set_predicted(self, n, S, x, phi, eta, w_beta, w_alpha, w_xi, zeta, S_legacy=None):
+        """S_legacy: PFs before this step's births (slots S_legacy .. S-1 are new and are
+        drawn from the birth proposal in the update when it is enabled); None = no new PF."""
         a = dict(x=np.ascontiguousarray(x, np.float32), phi=np.ascontiguousarray(phi, np.float32),
                  eta=np.ascontiguousarray(eta, np.float32), w_x=np.ascontiguousarray(w_beta, np.float64),
                  w_y=np.ascontiguousarray(w_alpha, np.float64), w_eta=np.ascontiguousarray(w_xi, np.float64),
                  p_pr=np.ascontiguousarray(zeta, np.float64))
-        v = self._struct(n, S, a)
+        v = self._struct(n, S, a, S if S_legacy is None else S_legacy)
         _check(self.lib, self.h, self.lib.bp_set_predicted(self.h, C.byref(v)), "bp_set_predicted")
 
     def _diag(self, what, nbytes, dtype):
@@ -313,6 +318,26 @@ class Filter:
         ln = b[o:o + J * P].reshape(J, P); o += J * P
         lw = b[o:o + S * J].reshape(S, J)
         return dict(log_iota=li, delta_kappa=lk, log_nu=ln, llr_omega=lw)
+
+    def diag_proposal(self, Qe: int) -> Dict:
+        """Birth proposal of the last update's Qe new PFs: statistics, Bartlett costs,
+        candidates, prediction weights and particle positions."""
+        P, Ng = self.P, self.params.N_g
+        nd = Qe * (32 + Ng + 3 * Ng + P)
+        nbytes = nd * 8 + Qe * 3 * P * 4
+        buf = np.zeros(nbytes, np.uint8)
+        _check(self.lib, self.h, self.lib.bp_get_diag(self.h, DIAG_PROPOSAL, buf.ctypes.data_as(C.c_void_p), nbytes),
+               "bp_get_diag")
+        d = buf[:nd * 8].view(np.float64)
+        o = 0
+        st = d[o:o + 32 * Qe].reshape(Qe, 32); o += 32 * Qe
+        costs = d[o:o + Qe * Ng].reshape(Qe, Ng); o += Qe * Ng
+        cand = d[o:o + 3 * Qe * Ng].reshape(Qe, Ng, 3); o += 3 * Qe * Ng
+        w_alpha = d[o:o + Qe * P].reshape(Qe, P)
+        pos = buf[nd * 8:].view(np.float32).reshape(Qe, 3, P)
+        return dict(valid=st[:, 0] != 0, i_star=st[:, 1].astype(int), cost_sum=st[:, 2], mu=st[:, 3:6],
+                    C=st[:, 6:15].reshape(Qe, 3, 3), L=st[:, 15:24].reshape(Qe, 3, 3), costs=costs, cand=cand,
+                    w_alpha=w_alpha, pos=pos)
 
     def diag_indices(self, S) -> Dict:
         J, P = self.geom.J, self.P

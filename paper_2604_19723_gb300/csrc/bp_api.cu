@@ -193,8 +193,14 @@ static bp_status copy_state(bp_handle* h, bp_state_view* v, bool to_host, bool p
             return fail(h, BP_ERR_CUDA, cudaGetErrorString(cudaGetLastError()));
     }
     if (cudaStreamSynchronize(h->st) != cudaSuccess) return fail(h, BP_ERR_CUDA, cudaGetErrorString(cudaGetLastError()));
-    if (to_host) { v->S = h->S; v->n = h->n; }
-    else { h->S = S; h->n = v->n; h->phase = predicted ? 1 : 0; }
+    if (to_host) { v->S = h->S; v->n = h->n; v->S_legacy = predicted ? h->S_legacy : h->S; }
+    else {
+        h->S = S;
+        // an imported prediction names its new PFs (their birth proposal runs in bp_update)
+        h->S_legacy = (predicted && v->S_legacy > 0 && v->S_legacy < S) ? v->S_legacy : S;
+        h->n = v->n;
+        h->phase = predicted ? 1 : 0;
+    }
     return BP_OK;
 }
 
@@ -231,6 +237,18 @@ bp_status bp_get_diag(bp_handle* h, int what, void* host, size_t bytes) {
         parts.push_back({D.lw_y, (size_t)S * P * sizeof(double)});
         parts.push_back({D.lw_eta, (size_t)J * P * sizeof(double)});
         parts.push_back({D.llr_w, (size_t)S * J * sizeof(double)});
+    } else if (what == BP_DIAG_PROPOSAL) {
+        const int Qe = S - h->S_legacy;
+        if (!D.bprop || Qe < 1) return fail(h, BP_ERR_STATE, "bp_get_diag: no birth proposal in the last update");
+        const BpropLayout B = bprop_layout(h->G, h->Pm);
+        const size_t Ng = (size_t)h->Pm.N_g;
+        parts.push_back({D.bprop + B.stats(0), (size_t)Qe * 32 * sizeof(double)});
+        parts.push_back({D.bprop + B.costs(), (size_t)Qe * Ng * sizeof(double)});
+        parts.push_back({D.bprop + B.cand(), (size_t)Qe * Ng * 3 * sizeof(double)});
+        parts.push_back({D.w_alpha + (size_t)h->S_legacy * P, (size_t)Qe * P * sizeof(double)});
+        // the predicted particles stay in the buffer the update resampled from
+        const float* pred_phi = D.phi[1 - D.cur];
+        for (int s = h->S_legacy; s < S; ++s) parts.push_back({pred_phi + (size_t)s * 6 * P, (size_t)3 * P * sizeof(float)});
     } else if (what == BP_DIAG_INDICES) {
         parts.push_back({D.idx, (size_t)P * sizeof(int)});
         parts.push_back({D.idx + P, (size_t)S * P * sizeof(int)});
@@ -346,7 +364,8 @@ bp_status bp_synthesize(const bp_geometry* geom, int n_steps, int step0, const d
 
 static size_t ws_align(size_t b) { return (std::max<size_t>(b, 8) + 255) & ~(size_t)255; }
 
-WsPlan ws_plan(const DevGeom& G, int P, int S_max, int SCA, int nsplit_max) {
+WsPlan ws_plan(const DevGeom& G, const DevParams& Pm, int SCA, int nsplit_max) {
+    const int P = Pm.P, S_max = Pm.S_max;
     WsPlan w{};
     size_t o = 0;
     auto take = [&](size_t bytes) { const size_t at = o; o += ws_align(bytes); return at; };
@@ -369,6 +388,10 @@ WsPlan ws_plan(const DevGeom& G, int P, int S_max, int SCA, int nsplit_max) {
     w.cdf = take(nbel * PP * sizeof(double));
     w.wn = take(nbel * PP * sizeof(double));
     w.idx = take(nbel * PP * sizeof(int));
+    const bool bprop = Pm.birth_proposal && Pm.Q > 0;
+    const BpropLayout B = bprop_layout(G, Pm);
+    w.bprop = take(bprop ? B.r_total() * sizeof(double) : 0);
+    w.bprop_c = take(bprop ? B.c_total() * sizeof(double2) : 0);
     w.total = o;
     return w;
 }
@@ -393,6 +416,9 @@ void ws_bind(bp_handle* h, char* base) {
     h->cdf = reinterpret_cast<double*>(base + w.cdf);
     h->wn = reinterpret_cast<double*>(base + w.wn);
     D.idx = reinterpret_cast<int*>(base + w.idx);
+    const bool bprop = h->Pm.birth_proposal && h->Pm.Q > 0;
+    D.bprop = bprop ? reinterpret_cast<double*>(base + w.bprop) : nullptr;
+    D.bprop_c = bprop ? reinterpret_cast<double2*>(base + w.bprop_c) : nullptr;
     const size_t PP = (size_t)h->P;
     D.wn_x = h->wn;
     D.wn_y = h->wn + PP;
@@ -413,6 +439,7 @@ bp_status handle_create(const bp_geometry* geom, const bp_params* prm, int P, in
     if (prm->c_eta < 1.0 || prm->c_gamma < 1.0) return bad("Gamma shapes must be >= 1");
     if (prm->motion_dims != 2 && prm->motion_dims != 3) return bad("motion_dims must be 2 or 3");
     if (prm->Q < 0 || !(prm->T > 0)) return bad("invalid Q or T");
+    if (prm->birth_proposal && (prm->N_g < 1 || prm->N_g > 65536)) return bad("N_g must be in [1, 65536]");
     bp_handle* h = new bp_handle();
     h->st = st;
     fill_geom(h->G, geom);
@@ -428,6 +455,8 @@ bp_status handle_create(const bp_geometry* geom, const bp_params* prm, int P, in
     Pm.eta_min = prm->eta_min; Pm.eta_max = prm->eta_max;
     for (int k = 0; k < 3; ++k) { Pm.p_min[k] = prm->p_min[k]; Pm.p_max[k] = prm->p_max[k]; Pm.v_max[k] = prm->v_max[k]; }
     Pm.zero_mean = prm->zero_mean; Pm.mvec_scaling = prm->mvec_scaling; Pm.regularize = prm->regularize;
+    Pm.birth_proposal = prm->birth_proposal ? 1 : 0;
+    Pm.N_g = prm->N_g;
     Pm.key0 = (uint32_t)(seed & 0xFFFFFFFFu); Pm.key1 = (uint32_t)(seed >> 32);
     Pm.P = P; Pm.S_max = S_max;
     h->P = P; h->S_max = S_max; h->J = geom->J; h->Nz = h->G.Nz;
@@ -468,7 +497,7 @@ bp_status handle_create(const bp_geometry* geom, const bp_params* prm, int P, in
     const EstLayout E{S_max, J};
     ok &= dalloc(h, &D.est, E.total());
     ok &= dalloc(h, &h->nu_b, (size_t)J * (S_max + 1) * 2);
-    h->wsp = ws_plan(h->G, P, S_max, SCA, h->nsplit_max);
+    h->wsp = ws_plan(h->G, h->Pm, SCA, h->nsplit_max);
     if (ok && own_ws) {
         void* q = nullptr;
         ok &= cudaMalloc(&q, h->wsp.total) == cudaSuccess;
@@ -511,6 +540,7 @@ void predict_enqueue(bp_handle* h) {
     }
     mark(h, 0);
     h->launches += launch_predict(h->G, h->Pm, h->D, S_old, S_new, h->st);
+    h->S_legacy = S_old;
     if (h->prof_on) { cudaEventRecord(h->ev[BP_PROF_STAGES], h->st); h->ev_valid[0] = true; }
     h->S = S_new;
     h->n += 1;
@@ -521,6 +551,8 @@ void update_enqueue(bp_handle* h, const float* z_dev) {
     const int S = h->S, J = h->J, P = h->P;
     DevState& D = h->D;
     mark(h, 1);
+    // births drawn from the proposal need this step's observation
+    h->launches += launch_birth_proposal(h->G, h->Pm, D, h->S_legacy, S, z_dev, h->st);
     launch_row_sums(h->Pm, D, S, J, h->st);
     mark(h, 2);
     int nsplit = std::max(1, (4 * 152 + S * J - 1) / (S * J));

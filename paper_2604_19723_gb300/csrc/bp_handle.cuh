@@ -15,6 +15,7 @@
 // same stream share one, sized for the largest of them.
 struct WsPlan {
     size_t lw_x, lw_y, lw_eta, geo, geo_lo, flags, tab, tab_part, kV, kr0l, kB, red_part, gram, V64, cdf, wn, idx;
+    size_t bprop, bprop_c;   // birth proposal scratch (empty unless enabled)
     size_t total;
 };
 
@@ -26,6 +27,7 @@ struct bp_handle {
     int P, S_max, J, Nz;
     int SCA;            // column stride of the per-(s,j) basis buffers
     int S;              // current number of PFs (host copy)
+    int S_legacy;       // PFs before the births of the current prediction
     int S_upd;          // S of the last bp_update
     int n;              // last completed step (state) or current step (predicted); the device holds it too
     int phase;          // 0: belief state, 1: predicted
@@ -58,7 +60,7 @@ struct bp_handle {
 // workspace, otherwise the caller binds one with ws_bind before the first update
 bp_status handle_create(const bp_geometry* geom, const bp_params* prm, int P, int S_max, int S0, uint64_t seed,
                         cudaStream_t st, bool own_ws, bp_handle** out, std::string* err);
-WsPlan ws_plan(const bp::DevGeom& G, int P, int S_max, int SCA, int nsplit_max);
+WsPlan ws_plan(const bp::DevGeom& G, const bp::DevParams& Pm, int SCA, int nsplit_max);
 void ws_bind(bp_handle* h, char* base);
 // launches of one prediction / one update on the handle's stream (no synchronisation);
 // update_enqueue also copies the control words to pinned memory when the PF count can

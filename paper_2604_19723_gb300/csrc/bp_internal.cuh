@@ -41,6 +41,7 @@ struct DevParams {
     double T_dec, T_pru, gamma_max, mu_max, eta_min, eta_max;
     double p_min[3], p_max[3], v_max[3];
     int zero_mean, mvec_scaling, regularize;
+    int birth_proposal, N_g;
     uint32_t key0, key1;
     int P, S_max;
 };
@@ -68,7 +69,7 @@ __host__ __device__ inline U4 philox(uint32_t c0, uint32_t c1, uint32_t c2, uint
 enum : uint32_t {
     RNG_MT_PREDICT = 1, RNG_ETA_PREDICT = 2, RNG_PF_GAUSS = 3, RNG_PF_GAMMA = 4, RNG_BIRTH = 5,
     RNG_RESAMPLE = 6, RNG_JITTER_MT = 7, RNG_JITTER_PF = 8, RNG_JITTER_ETA = 9, RNG_INIT_MT = 10,
-    RNG_INIT_ETA = 11, RNG_SYNTH_NOISE = 12
+    RNG_INIT_ETA = 11, RNG_SYNTH_NOISE = 12, RNG_BIRTH_CAND = 13, RNG_BIRTH_PROP = 14
 };
 constexpr int MAX_GAMMA_ATTEMPTS = 16;
 
@@ -351,6 +352,8 @@ struct DevState {
     int* idx;         // (1 + S_max + J) x P resampling indices
     int* ctrl;        // [0] S, [1] S_next, [2] births_skipped, [3] status, [4..] keep map
     int* step;        // [0] step index n of the Philox counters, advanced on the device (k_step_advance)
+    double* bprop;    // birth proposal scratch, real part (BpropLayout), or null
+    double2* bprop_c; // birth proposal scratch, complex part: steering matrices and residuals
     double* est;      // estimates buffer
 };
 

@@ -4,6 +4,31 @@
 
 namespace bp {
 
+// Scratch of the birth proposal (k_birth.cu).  Complex part (double2): the steering
+// matrices Psi_j [J][S_max][Nz] and the residuals z~_j [J][Nz].  Real part (double): the
+// estimates [1 + S_max][3] (MT first), per new PF q < Q the statistics [32] (valid, i*,
+// sum of costs, mu [3], C [3][3], L [3][3]), the costs [Q][N_g], the candidates
+// [Q][N_g][3], the proposal draws [Q][P][3] and per-block sums of their weights.
+struct BpropLayout {
+    int J, Nz, S_max, N_g, Q, P;
+    __host__ __device__ size_t psi(int j) const { return (size_t)j * S_max * Nz; }
+    __host__ __device__ size_t zres(int j) const { return (size_t)J * S_max * Nz + (size_t)j * Nz; }
+    __host__ __device__ size_t c_total() const { return (size_t)J * S_max * Nz + (size_t)J * Nz; }
+    __host__ __device__ size_t means() const { return 0; }
+    __host__ __device__ size_t stats(int q) const { return 3 * (size_t)(1 + S_max) + 32 * (size_t)q; }
+    __host__ __device__ size_t costs() const { return 3 * (size_t)(1 + S_max) + 32 * (size_t)Q; }
+    __host__ __device__ size_t cand() const { return costs() + (size_t)Q * N_g; }
+    __host__ __device__ size_t pos(int q) const { return cand() + (size_t)Q * N_g * 3 + (size_t)q * P * 3; }
+    __host__ __device__ size_t parts(int q) const { return pos(Q) + (size_t)q * ((P + 255) / 256); }
+    __host__ __device__ size_t r_total() const { return parts(Q); }
+};
+inline BpropLayout bprop_layout(const DevGeom& G, const DevParams& Pm) {
+    return BpropLayout{G.J, G.Nz, Pm.S_max, Pm.N_g, Pm.Q, Pm.P};
+}
+// the birth proposal of the new PFs S_L .. S_new - 1 (no-op unless enabled); returns launches
+int launch_birth_proposal(const DevGeom& G, const DevParams& Pm, const DevState& D, int S_L, int S_new,
+                          const float* z, cudaStream_t st);
+
 // Largest dynamic shared memory a block may opt in to on the current device.
 int smem_optin();
 // Raises a kernel's dynamic shared-memory limit to the opt-in maximum less its static

@@ -93,6 +93,8 @@ class Params:
     zero_mean: int = 0             # 1: ZM variant (mu == 0)
     mvec_scaling: int = 0          # 0: m-vectors as printed in S-V; 1: sqrt(pi) reading
     regularize: int = 1            # Gaussian-kernel jitter after resampling
+    birth_proposal: int = 0        # 1: new PFs drawn from the Bartlett proposal (Sec. IV-D)
+    N_g: int = 4096                # candidate positions per new PF of the proposal
 
     @property
     def birth_min(self):
@@ -260,6 +262,12 @@ def workload(name: str) -> Dict:
     if name == "paper_exp1":
         g = make_geometry(J=4, Nf=10, My=4, Mz=4, B=200e6)
         p = Params(T=0.1, sigma_v=0.5, sigma_mu=3e-3, sigma_sfv=1e-4)
+        return dict(geom=g, params=p, P=30000, S_max=16, N=200, K=4, visibility=1.0,
+                    clutter_mean=0.0, snr_db=20.0, seed=1, fixed_S=0)
+    if name == "paper_exp1_proposal":
+        # Experiment 1 with new PFs drawn from the Bartlett birth proposal (Sec. IV-D)
+        g = make_geometry(J=4, Nf=10, My=4, Mz=4, B=200e6)
+        p = Params(T=0.1, sigma_v=0.5, sigma_mu=3e-3, sigma_sfv=1e-4, birth_proposal=1, N_g=4096)
         return dict(geom=g, params=p, P=30000, S_max=16, N=200, K=4, visibility=1.0,
                     clutter_mean=0.0, snr_db=20.0, seed=1, fixed_S=0)
     if name == "paper_exp2":

@@ -513,3 +513,85 @@ def test_batched_scenario_shapes():
         else:
             assert g.My == g.Mz == 2 and 16 <= g.Nz <= 300 + 3 and g.Nf == -(-g.Nz // 4)
     assert len({d["seed"] for d in sc}) == len(sc)
+
+
+# ---------------------------------------------------------------- birth proposal (Sec. IV-D)
+def _proposal_case(seed=3, K=3, P=4000):
+    from oracle import birth_proposal as bpro
+    g = W.make_geometry(J=3, Nf=8, My=3, Mz=2)
+    prm = W.Params(Q=2, birth_proposal=1, N_g=512)
+    scn = W.make_scenario(g, prm, N=3, K=K, seed=seed, snr_db=30.0)
+    eta = synth.noise_variance(scn)
+    z = synth.observe(scn, 1, eta, seed + 9)
+    st = W.state_near_truth(scn, P=P, S=K + 1, n=0, seed=seed + 1, eta_true=eta, pos_std=0.005, sfv_std=0.005)
+    pred = model.predict(st, prm, g.J, seed=seed, S_max=K + 1 + prm.Q)
+    return bpro, g, prm, scn, z, st, pred
+
+
+def test_birth_proposal_residual_is_the_orthogonal_projection():
+    """z~ = (I - Psi Psi^+) z: orthogonal to every LoS / legacy steering column, and
+    projecting it again changes nothing."""
+    bpro, g, prm, scn, z, st, pred = _proposal_case()
+    x_hat = bpro.mt_mean(pred)
+    pos = bpro.legacy_means(pred, st.S)
+    zr = bpro.residual(g, z, x_hat, pos)
+    for j in range(g.J):
+        Psi = np.stack([geometry.steering(g, j, x_hat[None, :3], pos[s][None, :], los=(s == 0))[0]
+                        for s in range(st.S)], axis=1)
+        assert np.max(np.abs(Psi.conj().T @ zr[j])) < 1e-10 * np.linalg.norm(Psi) * np.linalg.norm(z[j])
+    zr2 = bpro.residual(g, zr, x_hat, pos)
+    assert np.allclose(zr2, zr, rtol=0, atol=1e-12 * np.max(np.abs(z)))
+    assert np.all(np.linalg.norm(zr, axis=1) < np.linalg.norm(z, axis=1))
+
+
+def test_bartlett_spectrum_peaks_at_the_unexplained_surface():
+    """One surface that no legacy PF explains: with the LoS projected out, the coherent
+    Bartlett spectrum over its partition peaks within a few cm of its SFV."""
+    from oracle import birth_proposal as bpro
+    g = W.make_geometry(J=4, Nf=10, My=4, Mz=4)
+    prm = W.Params(Q=1)
+    x = np.array([1.0, 2.0, 0.2])
+    sfv = np.array([[9.0, 3.0, 0.5]])
+    z = np.stack([geometry.steering(g, j, x[None], x[None], los=True)[0] * 1.0 +
+                  geometry.steering(g, j, x[None], sfv, los=False)[0] * 0.5 * np.exp(0.7j) for j in range(g.J)])
+    zr = bpro.residual(g, z, np.r_[x, 0, 0, 0], np.zeros((1, 3)))
+    r = np.random.default_rng(1)
+    lo, hi = np.asarray(prm.birth_min), np.asarray(prm.birth_max)
+    cand = np.concatenate([lo + (hi - lo) * r.random((20000, 3)), sfv + 0.02 * r.standard_normal((200, 3))])
+    c = bpro.bartlett(g, zr, np.r_[x, 0, 0, 0], cand)
+    i_star, mu, C = bpro.moments(cand, c)
+    assert np.linalg.norm(mu - sfv[0]) < 0.05
+    # the residual carries only the surface: its spectrum at the true SFV is |0.5 psi^H psi / Nz|^2 summed coherently
+    ref = abs(sum(0.5 * np.exp(0.7j) * np.vdot(geometry.steering(g, j, x[None], sfv, los=False)[0],
+                                                 geometry.steering(g, j, x[None], sfv, los=False)[0]) / g.Nz
+                  for j in range(g.J))) ** 2
+    c_true = bpro.bartlett(g, zr, np.r_[x, 0, 0, 0], sfv)[0]
+    assert c_true == pytest.approx(ref, rel=1e-3)   # the LoS projection removes ~nothing of the surface here
+
+
+def test_birth_proposal_weights_are_importance_weights():
+    """w_alpha sums to p_B, is zero outside the PF's partition, and reweights the
+    proposal draws to the uniform birth density: the weighted mean of any function of
+    the position matches its mean over the partition (checked on the position itself
+    and its square, within the Monte Carlo error of the weights)."""
+    bpro, g, prm, scn, z, st, pred = _proposal_case(P=20000)
+    pred2, props = bpro.apply(pred, prm, g, z, st.S, prm.N_g, seed=3)
+    pB = model.birth_probability(prm.mu_B, prm.Q)
+    for pr in props:
+        s = pr.slot
+        w = pred2.w_alpha[s]
+        assert w.sum() == pytest.approx(pB, rel=1e-12)
+        lo, hi = bpro.partition_bounds(prm, prm.Q, pr.q)
+        pos = pred2.phi[s, :3].astype(np.float64)
+        outside = np.any((pos < lo[:, None] - 1e-5) | (pos > hi[:, None] + 1e-5), axis=0)
+        assert np.all(w[outside] == 0)
+        # proposal draws: mean mu, covariance L L^T
+        assert np.allclose(pr.L @ pr.L.T, pr.C, atol=1e-12)
+        wn = w / w.sum()
+        ess = 1.0 / np.sum(wn ** 2)
+        for k in range(3):
+            if pr.L[k, k] == 0:
+                continue
+            se = (hi[k] - lo[k]) / math.sqrt(12 * max(ess, 1.0))
+            m = np.sum(wn * pos[k])
+            assert abs(m - 0.5 * (lo[k] + hi[k])) < 6 * se + 0.02 * (hi[k] - lo[k])
