@@ -50,6 +50,23 @@ def kappa_flops(P, S, J, Nz):
     return float(P) * S * J * per
 
 
+def kappa_tc_used(g, S):
+    """Whether the PF likelihood runs on the tensor cores (k_kappa_tc): 64 basis columns
+    (S > 32), 2 My Mz in {8, 16, 32} and its shared memory within 227 KB."""
+    Nm = g.My * g.Mz
+    if S <= 32 or 2 * Nm not in (8, 16, 32):
+        return False
+    rf = max(6 * 128 * 2 * Nm, 4 * 128 * 32 + 2 * 64 * 32)
+    smem = rf * 4 + 32 + g.Nz * 16 + 128 * 8 + (g.Nf + g.My + g.Mz) * 256 * 8
+    return smem <= 227 * 1024
+
+
+def kappa_contraction_flops(P, S, J, Nz):
+    """The two contractions of the PF likelihood (psi^H V over 64 columns incl. r0, then
+    V conj(h) over the S-1 basis columns), 8 flops per complex multiply-add."""
+    return float(P) * S * J * (8 * Nz * 64 + 8 * Nz * (S - 1))
+
+
 def iota_flops(P, S, J, Nf, My, Mz):
     """Algorithmic flops of one launch of the MT likelihood kernel, per (p, j): the
     Kronecker-factored Gram (S(S+1)/2 entries, Nf + My + Mz complex multiply-adds and
@@ -349,6 +366,22 @@ def run_gpu(args, rank, world):
             # the same algorithmic flops against the nominal FP64 rate, the precision class the
             # log determinant needs (the kernel emulates it with FP32 operations)
             r["vs_fp64_nominal"] = {"peak": FP64_NOMINAL_TFLOPS, "frac": a / FP64_NOMINAL_TFLOPS}
+        if name == "k_kappa" and kappa_tc_used(g, S):
+            # both contractions run on the tensor cores in 3xTF32: each algorithmic flop is
+            # three TF32 MMA flops, against the measured bf16 rate (sustained: the kernel runs
+            # inside a long step) times the nominal TF32/BF16 ratio (1.1 / 2.25 PFLOP/s)
+            tf32 = peaks.get("bf16_tflops_sustained", 1700.0) * (1.1 / 2.25)
+            eff = tf32 / 3.0
+            fc = kappa_contraction_flops(P, S, g.J, g.Nz)
+            ac = fc / (ms * 1e-3) / 1e12
+            r = {"bound": "tensor", "kernel": "k_kappa_tc (tcgen05 3xTF32, both contractions)", "achieved": ac,
+                 "peak": eff, "unit": "TFLOP/s", "frac": ac / eff, "traffic": traffic_for(name, args.workload, P),
+                 "ms_per_launch": ms,
+                 "peak_basis": f"3xTF32 effective: MEASURED_PEAKS bf16_tflops_sustained {peaks.get('bf16_tflops_sustained')} "
+                               f"x 1.1/2.25 (nominal TF32/BF16) / 3 products",
+                 "cuda_core_part": {"flops": fl - fc, "achieved": (fl - fc) / (ms * 1e-3) / 1e12, "peak": peak_alu,
+                                    "note": "element-wise float-float residual and amplitude sums on the FP32 lanes, "
+                                            "whole-kernel time"}}
         return r
     dominant = max(per_kernel, key=lambda n: per_kernel[n][0])
     other = "k_iota_blk" if dominant == "k_kappa" else "k_kappa"

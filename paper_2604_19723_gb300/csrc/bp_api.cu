@@ -562,7 +562,7 @@ void update_enqueue(bp_handle* h, const float* z_dev) {
     launch_table(h->G, h->Pm, D, S, nsplit, h->st);
     mark(h, 3);
     launch_stage(h->G, h->Pm, D, S, h->SCA, z_dev, h->gram, h->nu_b, h->V64, h->st);
-    if (S > 32) launch_kappa_btile(h->G, D, S, h->SCA, h->st);   // B tiles of the tensor-core variant (SC = 64)
+    if (S > 32) h->launches += launch_kappa_btile(h->G, D, S, h->SCA, h->st);   // B tiles of the tensor-core kernel
     mark(h, 4);
     launch_kappa(h->G, h->Pm, D, S, h->SCA, h->st);
     mark(h, 5);
@@ -578,7 +578,7 @@ void update_enqueue(bp_handle* h, const float* z_dev) {
         cudaEventRecord(h->ev[BP_PROF_STAGES], h->st);
         for (int i = 1; i < BP_PROF_STAGES; ++i) h->ev_valid[i] = true;
     }
-    h->launches += 1 + 3 + 3 + 1 + 2 + 1 + 5 + 3 + ((S > 32 && D.kB && kappa_tc_ok(h->G, h->SCA)) ? 1 : 0);
+    h->launches += 1 + 3 + 3 + 1 + 2 + 1 + 5 + 3;
     h->D.cur = 1 - h->D.cur;
     h->S_upd = S;
     h->phase = 0;

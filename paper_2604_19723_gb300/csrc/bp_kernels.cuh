@@ -130,7 +130,8 @@ void launch_stage(const DevGeom& G, const DevParams& Pm, const DevState& D, int 
 void launch_kappa(const DevGeom& G, const DevParams& Pm, const DevState& D, int S, int SCA, cudaStream_t st);
 bool kappa_tc_ok(const DevGeom& G, int SCA);
 size_t kappa_btile_floats(const DevGeom& G, int S_max);
-void launch_kappa_btile(const DevGeom& G, const DevState& D, int S, int SCA, cudaStream_t st);
+// operand tiles of both tensor-core passes of the PF likelihood; returns launches
+int launch_kappa_btile(const DevGeom& G, const DevState& D, int S, int SCA, cudaStream_t st);
 void launch_iota(const DevGeom& G, const DevParams& Pm, const DevState& D, int S, const float* z, cudaStream_t st);
 void launch_nu(const DevGeom& G, const DevParams& Pm, const DevState& D, int S, cudaStream_t st);
 int launch_normalize(const DevGeom& G, const DevParams& Pm, const DevState& D, int S, cudaStream_t st);

@@ -34,30 +34,15 @@ namespace bp {
 // 1/lambda_c and w_c = y~0_c/lambda_c beside it.  The basis columns are orthogonal,
 // so every amplitude term is a diagonal sum over the columns.
 
-// With TC (64 basis columns, 2*My*Mz in {8, 16, 32}) pass 1 runs on the tensor cores:
-// per frequency, the 256 particles' steering values (Re/Im interleaved, split into TF32
-// high and low parts) form two 128-row A tiles in shared memory, the matching rows of
-// [[Re V, Im V], [Im V, -Re V]] arrive as prebuilt TF32 hi/lo B tiles by a bulk copy,
-// and one thread issues hi.hi + hi.lo + lo.hi MMAs (3xTF32, FP32-level accuracy) into a
-// 256-column TMEM accumulator whose lane is the particle; h = psi^H V is read back from
-// TMEM.  Pass 2 and everything after are the same CUDA-core code for both variants.
-constexpr int KAPPA_TC_WAIT = 1 << 20;   // polls of an mbarrier before the kernel gives up
-
-template <int SC, bool TC>
-__global__ void __launch_bounds__(256, (SC <= 16 ? 2 : 1)) k_kappa(DevGeom G, DevParams Pm, DevState D, int S, int SCA, int fch,
-                                                                   const float* __restrict__ Bt) {
+template <int SC>
+__global__ void __launch_bounds__(256, (SC <= 16 ? 2 : 1)) k_kappa(DevGeom G, DevParams Pm, DevState D, int S, int SCA, int fch) {
     constexpr int KT = 256;
     constexpr int NC = SC - 1;           // basis columns (zero beyond S-2)
     constexpr int NP = SC / 2;           // column pairs per row
     extern __shared__ __align__(1024) float4 sm4[];
     const int s = blockIdx.y;
     const int P = Pm.P, J = G.J, Nz = G.Nz, Nm = G.My * G.Mz;
-    const int KC = 2 * Nm;                                             // real K per frequency (TC)
-    float* sA = reinterpret_cast<float*>(sm4);                         // TC: [2 tiles][hi, lo][128 x KC]
-    float* sB = sA + (TC ? 4 * 128 * KC : 0);                          // TC: [hi, lo][128 x KC]
-    uint64_t* mbar = reinterpret_cast<uint64_t*>(sB + (TC ? 2 * 128 * KC : 0));   // TC: [2]
-    uint32_t* tslot = reinterpret_cast<uint32_t*>(mbar + (TC ? 2 : 0));          // TC: TMEM base
-    float4* Vs = TC ? reinterpret_cast<float4*>(sA + 6 * 128 * KC + 8) : sm4;    // [fch * Nm][NP] rows staged
+    float4* Vs = sm4;                                                  // [fch * Nm][NP] rows staged
     float2* dls = reinterpret_cast<float2*>(Vs + (size_t)fch * Nm * NP); // [SC] 1/lambda_c (.x)
     float2* y0s = dls + SC;                                            // [SC] w_c
     float2* fac = y0s + SC;                                            // [nfac][KT]
@@ -66,17 +51,6 @@ __global__ void __launch_bounds__(256, (SC <= 16 ? 2 : 1)) k_kappa(DevGeom G, De
     const int p = blockIdx.x * KT + tid;
     const bool act = p < P;
     const int pp = act ? p : 0;
-    uint32_t tmem = 0, n_commit = 0, n_bulk = 0;
-    bool bad = false;
-    const uint32_t mbar_mma = TC ? tc::smem_u32(&mbar[0]) : 0u, mbar_b = TC ? tc::smem_u32(&mbar[1]) : 0u;
-    if constexpr (TC) {
-        if ((tid >> 5) == 0) tc::tmem_alloc(tslot, 256);
-        if (tid == 0) { tc::mbar_init(mbar_mma, 1); tc::mbar_init(mbar_b, 1); tc::mbar_init_fence(); }
-        tc::fence_before_sync();
-        __syncthreads();
-        tc::fence_after_sync();
-        tmem = *tslot;
-    }
     const float* ph = D.phi[D.cur] + (size_t)s * 6 * P;
     const float4* geo_s = D.geo + (size_t)s * J * P;
     const float2* geol_s = D.geo_lo + (size_t)s * J * P;
@@ -120,85 +94,6 @@ __global__ void __launch_bounds__(256, (SC <= 16 ? 2 : 1)) k_kappa(DevGeom G, De
         for (int c = 0; c < NC; ++c) h[c] = make_float2(0.f, 0.f);
         float2 pr = make_float2(0.f, 0.f);
         float nps = 0.f;
-        if constexpr (TC) {
-            const int tile = tid >> 7, row = tid & 127, warp = tid >> 5;
-            float* aHi = sA + (size_t)(tile * 2 + 0) * 128 * KC;
-            float* aLo = sA + (size_t)(tile * 2 + 1) * 128 * KC;
-            const size_t bchunk = (size_t)2 * 128 * KC;                // floats per frequency (hi + lo)
-            const float* gB = Bt + ((size_t)s * J + j) * G.Nf * bchunk;
-            const uint32_t idesc = tc::idesc_tf32_f32(128, 128);
-            const uint32_t sbo = (uint32_t)(KC / 4) * 128u;
-            for (int f = 0; f < G.Nf; ++f) {
-                // the A and B buffers are free once the previous frequency's MMAs completed
-                if (n_commit > 0 && !tc::mbar_wait(mbar_mma, (n_commit - 1) & 1u, KAPPA_TC_WAIT)) bad = true;
-                if (tid == 0 && !bad) {
-                    tc::mbar_expect_tx(mbar_b, (uint32_t)(bchunk * 4));
-                    tc::bulk_g2s(tc::smem_u32(sB), gB + (size_t)f * bchunk, (uint32_t)(bchunk * 4), mbar_b);
-                }
-                const float2 cb = cmul(Fc, fb[f * KT]);
-                for (int y = 0; y < G.My; ++y) {
-                    const float2 w = cmul(cb, fy[y * KT]);
-                    for (int m = 0; m < G.Mz; m += 2) {
-                        const float2 p0 = cmul(w, fz[m * KT]), p1 = cmul(w, fz[(m + 1) * KT]);
-                        nps += p0.x * p0.x + p0.y * p0.y + p1.x * p1.x + p1.y * p1.y;
-                        const float4 hi = make_float4(tc::tf32_rn(p0.x), tc::tf32_rn(p0.y), tc::tf32_rn(p1.x), tc::tf32_rn(p1.y));
-                        const float4 lo = make_float4(tc::tf32_rn(p0.x - hi.x), tc::tf32_rn(p0.y - hi.y),
-                                                      tc::tf32_rn(p1.x - hi.z), tc::tf32_rn(p1.y - hi.w));
-                        const int off = tc::core_off(row, 2 * (y * G.Mz + m), KC) >> 2;
-                        *reinterpret_cast<float4*>(aHi + off) = hi;
-                        *reinterpret_cast<float4*>(aLo + off) = lo;
-                    }
-                }
-                tc::fence_async_smem();
-                tc::fence_before_sync();
-                __syncthreads();
-                tc::fence_after_sync();
-                if (tid == 0 && !bad) {
-                    if (!tc::mbar_wait(mbar_b, n_bulk & 1u, KAPPA_TC_WAIT)) bad = true;
-                    if (!bad) {
-                        const uint32_t bH = tc::smem_u32(sB), bL = tc::smem_u32(sB + 128 * KC);
-                        for (int t = 0; t < 2; ++t) {
-                            const uint32_t aH = tc::smem_u32(sA + (size_t)(t * 2) * 128 * KC);
-                            const uint32_t aL = tc::smem_u32(sA + (size_t)(t * 2 + 1) * 128 * KC);
-                            for (int ks = 0; ks < KC / 8; ++ks) {
-                                const uint32_t o = (uint32_t)ks * 256u;
-                                const uint64_t dAH = tc::smem_desc(aH + o, 128, sbo), dAL = tc::smem_desc(aL + o, 128, sbo);
-                                const uint64_t dBH = tc::smem_desc(bH + o, 128, sbo), dBL = tc::smem_desc(bL + o, 128, sbo);
-                                const uint32_t d = tmem + (uint32_t)(t * 128);
-                                tc::mma_tf32(d, dAH, dBH, idesc, f > 0 || ks > 0);
-                                tc::mma_tf32(d, dAH, dBL, idesc, true);
-                                tc::mma_tf32(d, dAL, dBH, idesc, true);
-                            }
-                        }
-                        tc::mma_commit(mbar_mma);
-                    }
-                }
-                ++n_commit;
-                ++n_bulk;
-            }
-            if (!tc::mbar_wait(mbar_mma, (n_commit - 1) & 1u, KAPPA_TC_WAIT)) bad = true;
-            tc::fence_after_sync();
-            // h from TMEM: warp w reads lanes 32 (w mod 4) + lane of tile w / 4, i.e. particle tid;
-            // columns 0..63 hold Re h_c (c = 63: psi^H r0), 64..127 Im h_c
-            const uint32_t tb = tmem + ((uint32_t)((warp & 3) * 32) << 16) + (uint32_t)(tile * 128);
-            uint32_t v[32];
-            tc::tmem_ld32(tb + 0, v); tc::tmem_ld_wait();
-            #pragma unroll
-            for (int i = 0; i < 32; ++i) h[i].x = __uint_as_float(v[i]);
-            tc::tmem_ld32(tb + 32, v); tc::tmem_ld_wait();
-            #pragma unroll
-            for (int i = 0; i < 31; ++i) h[32 + i].x = __uint_as_float(v[i]);
-            pr.x = __uint_as_float(v[31]);
-            tc::tmem_ld32(tb + 64, v); tc::tmem_ld_wait();
-            #pragma unroll
-            for (int i = 0; i < 32; ++i) h[i].y = __uint_as_float(v[i]);
-            tc::tmem_ld32(tb + 96, v); tc::tmem_ld_wait();
-            #pragma unroll
-            for (int i = 0; i < 31; ++i) h[32 + i].y = __uint_as_float(v[i]);
-            pr.y = __uint_as_float(v[31]);
-            tc::fence_before_sync();
-            if (bad && (tid & 31) == 0) atomicOr(D.kerr, 1);
-        } else
         for (int f0 = 0; f0 < G.Nf; f0 += fch) {
           if (fch < G.Nf) { __syncthreads(); stage_rows(f0); __syncthreads(); }
           for (int f = f0; f < min(G.Nf, f0 + fch); ++f) {
@@ -343,12 +238,334 @@ __global__ void __launch_bounds__(256, (SC <= 16 ? 2 : 1)) k_kappa(DevGeom G, De
         delta_sum += dlt;
     }
     if (act) D.lw_y[(size_t)s * P + p] = delta_sum;
-    if constexpr (TC) {
+}
+
+// ---------------------------------------------------------------- kappa on the tensor cores
+// Both contractions of k_kappa run as tcgen05.mma kind::tf32 in 3xTF32 (hi.hi + hi.lo +
+// lo.hi: FP32-level products, FP32 accumulation) with the 256 particles of a block as two
+// 128-row M tiles and TMEM accumulators whose lane is the particle:
+//   pass 1, per frequency f: A = psi (Re/Im interleaved), B = rows of [[Re V, Im V],
+//     [Im V, -Re V]] -> h = psi^H V (63 columns) and psi^H r0 in TMEM columns 0..127 of
+//     each tile's 256-column region;
+//   pass 2, per group of frequencies (up to 64 real outputs) and K chunk of 32:
+//     A = [Re h, Im h] (from registers), B = rows [[Re V, Im V]; [Im V, -Re V]] over the
+//     basis columns (r0 excluded) -> the chunk's part of V conj(h) = V V^H psi for the
+//     group's elements, real parts in columns [0, nk), imaginary parts in [nk, 2 nk) of
+//     the chunk's own 64-column accumulator.
+// Pass 2 is the one contraction whose rounding enters the likelihood at first order, so
+// its four K chunks accumulate apart (12 MMA accumulations each) and are added pairwise
+// in FP32 when the element-wise float-float residual r = r0 - tau (psi - V V^H psi /
+// eta_bar) reads them back from TMEM, 8 elements at a time.  Operand tiles of B come
+// prebuilt (k_kappa_btile, k_kappa_btile2) by bulk copy; every mbarrier wait is bounded
+// (KAPPA_TC_WAIT polls), after which the kernel flags D.kerr, lets copies and MMAs in
+// flight land, frees TMEM and ends.
+constexpr int KAPPA_TC_WAIT = 1 << 20;
+constexpr int KAPPA_TC_KC2 = 32;   // real K per pass-2 chunk (16 basis columns)
+constexpr int KAPPA_TC_N2 = 64;    // pass-2 accumulator columns per chunk (4 chunks x 64 = 256 per tile)
+
+__host__ __device__ inline int kappa_tc_group_freqs(int Nm) { return KAPPA_TC_N2 / 2 / Nm; }
+__host__ __device__ inline int kappa_tc_groups(int Nf, int Nm) {
+    return (Nf + kappa_tc_group_freqs(Nm) - 1) / kappa_tc_group_freqs(Nm);
+}
+__host__ __device__ inline int round16(int x) { return (x + 15) & ~15; }
+
+__global__ void __launch_bounds__(256, 1) k_kappa_tc(DevGeom G, DevParams Pm, DevState D, int S, int SCA,
+                                                     const float* __restrict__ Bt1, const float* __restrict__ Bt2) {
+    constexpr int KT = 256, NC = 63, KC2 = KAPPA_TC_KC2;
+    extern __shared__ __align__(1024) float4 sm4[];
+    const int s = blockIdx.y;
+    const int P = Pm.P, J = G.J, Nz = G.Nz, Nm = G.My * G.Mz, Nf = G.Nf;
+    const int KC = 2 * Nm;                                     // pass-1 real K per frequency
+    const int GF = kappa_tc_group_freqs(Nm), NG = kappa_tc_groups(Nf, Nm);
+    const int RF = max(6 * 128 * KC, 4 * 128 * KC2 + 2 * KAPPA_TC_N2 * KC2);   // operand region (floats)
+    float* sR = reinterpret_cast<float*>(sm4);
+    uint64_t* mbar = reinterpret_cast<uint64_t*>(sR + RF);    // [2]: MMAs done, B arrived
+    uint32_t* tslot = reinterpret_cast<uint32_t*>(mbar + 2);
+    float4* r0s = reinterpret_cast<float4*>(sR + RF + 8);    // [Nz] r0 (hi.x, hi.y, lo.x, lo.y)
+    float2* dls = reinterpret_cast<float2*>(r0s + Nz);        // [64] 1/lambda_c (.x)
+    float2* y0s = dls + 64;                                   // [64] w_c
+    float2* fac = y0s + 64;                                   // [nfac][KT]
+    const int tid = threadIdx.x, warp = tid >> 5, tile = tid >> 7, row = tid & 127;
+    const int p = blockIdx.x * KT + tid;
+    const bool act = p < P;
+    const int pp = act ? p : 0;
+    const uint32_t mb_mma = tc::smem_u32(&mbar[0]), mb_b = tc::smem_u32(&mbar[1]);
+    uint32_t n_commit = 0, n_bulk = 0, n_waited_b = 0;
+    bool bad = false;
+    if (warp == 0) tc::tmem_alloc(tslot, 512);
+    if (tid == 0) { tc::mbar_init(mb_mma, 1); tc::mbar_init(mb_b, 1); tc::mbar_init_fence(); }
+    tc::fence_before_sync();
+    __syncthreads();
+    tc::fence_after_sync();
+    const uint32_t tmem = *tslot;
+    const uint32_t tlane = tmem + ((uint32_t)((warp & 3) * 32) << 16) + (uint32_t)(tile * 256);   // this thread's row
+    const float* ph = D.phi[D.cur] + (size_t)s * 6 * P;
+    const float4* geo_s = D.geo + (size_t)s * J * P;
+    const float2* geol_s = D.geo_lo + (size_t)s * J * P;
+    const float gmf = ph[3 * P + pp];
+    const float mrf = ph[4 * P + pp], mif = ph[5 * P + pp];
+    const double mr = mrf, mi = mif;
+    // one round: the B chunk by bulk copy (thread 0), A written by every thread (writeA),
+    // then thread 0 issues the 3xTF32 MMAs of both tiles (K in steps of 8)
+    auto round = [&](const float* gsrc, uint32_t bbytes, float* sA, float* sB, int Kt, uint32_t bLoOff,
+                     uint32_t idesc, uint32_t dcol, bool accum0, auto&& writeA) {
+        if (n_commit > 0 && !bad && !tc::mbar_wait(mb_mma, (n_commit - 1) & 1u, KAPPA_TC_WAIT)) bad = true;
+        if (tid == 0 && !bad) {
+            tc::mbar_expect_tx(mb_b, bbytes);
+            tc::bulk_g2s(tc::smem_u32(sB), gsrc, bbytes, mb_b);
+            ++n_bulk;
+        }
+        writeA();
+        tc::fence_async_smem();
         tc::fence_before_sync();
         __syncthreads();
         tc::fence_after_sync();
-        if ((tid >> 5) == 0) tc::tmem_dealloc(tmem, 256);
+        if (tid == 0 && !bad) {
+            if (!tc::mbar_wait(mb_b, n_waited_b & 1u, KAPPA_TC_WAIT)) bad = true;
+            else ++n_waited_b;
+            if (!bad) {
+                const uint32_t sbo = (uint32_t)(Kt / 4) * 128u;
+                const uint32_t bH = tc::smem_u32(sB), bL = bH + bLoOff;
+                for (int t = 0; t < 2; ++t) {
+                    const uint32_t aH = tc::smem_u32(sA + (size_t)(t * 2) * 128 * Kt);
+                    const uint32_t aL = tc::smem_u32(sA + (size_t)(t * 2 + 1) * 128 * Kt);
+                    for (int ks = 0; ks < Kt / 8; ++ks) {
+                        const uint32_t o = (uint32_t)ks * 256u;
+                        const uint64_t dAH = tc::smem_desc(aH + o, 128, sbo), dAL = tc::smem_desc(aL + o, 128, sbo);
+                        const uint64_t dBH = tc::smem_desc(bH + o, 128, sbo), dBL = tc::smem_desc(bL + o, 128, sbo);
+                        const uint32_t d = tmem + (uint32_t)(t * 256) + dcol;
+                        tc::mma_tf32(d, dAH, dBH, idesc, accum0 || ks > 0);
+                        tc::mma_tf32(d, dAH, dBL, idesc, true);
+                        tc::mma_tf32(d, dAL, dBH, idesc, true);
+                    }
+                }
+                tc::mma_commit(mb_mma);
+            }
+        }
+        ++n_commit;
+    };
+    auto wait_mma = [&]() {
+        if (!bad && !tc::mbar_wait(mb_mma, (n_commit - 1) & 1u, KAPPA_TC_WAIT)) bad = true;
+        tc::fence_after_sync();
+    };
+    double delta_sum = 0.0;
+    for (int j = 0; j < J; ++j) {
+        const float2* gV = D.kV + ((size_t)s * J + j) * Nz * SCA;
+        const float2* gr0l = D.kr0l + ((size_t)s * J + j) * Nz;
+        __syncthreads();
+        for (int k = tid; k < Nz; k += KT) {
+            const float2 hi = gV[(size_t)k * SCA + SCA - 1], lo = gr0l[k];
+            r0s[k] = make_float4(hi.x, hi.y, lo.x, lo.y);
+        }
+        {
+            const float2* gd = D.kdl + ((size_t)s * J + j) * SCA;
+            const float2* gy = D.ky0 + ((size_t)s * J + j) * SCA;
+            for (int t = tid; t < 64; t += KT) { dls[t] = gd[t]; y0s[t] = gy[t]; }
+        }
+        __syncthreads();
+        const double eb = D.eta_bar[j];
+        const float ebf = (float)eb;
+        const double ieb64 = 1.0 / eb;
+        const double zeta = D.zeta[s * J + j];
+        const double J0r = D.kJ0[s * J + j];
+        float2* fb = fac + tid;
+        float2* fy = fb + Nf * KT;
+        float2* fz = fy + G.My * KT;
+        const float2 Fc = factors_from_geo(G, geo_s[(size_t)j * P + pp], geol_s[(size_t)j * P + pp], fb, fy, fz, KT);
+        // ---- pass 1: h = psi^H V, pr = psi^H r0
+        float nps = 0.f;
+        {
+            float* sA = sR;
+            float* sB = sR + 4 * 128 * KC;
+            float* aHi = sA + (size_t)(tile * 2 + 0) * 128 * KC;
+            float* aLo = sA + (size_t)(tile * 2 + 1) * 128 * KC;
+            const size_t bchunk = (size_t)2 * 128 * KC;
+            const float* gB = Bt1 + ((size_t)s * J + j) * Nf * bchunk;
+            const uint32_t idesc = tc::idesc_tf32_f32(128, 128);
+            for (int f = 0; f < Nf; ++f) {
+                round(gB + (size_t)f * bchunk, (uint32_t)(bchunk * 4), sA, sB, KC, (uint32_t)(128 * KC * 4), idesc, 0u,
+                      f > 0, [&]() {
+                    const float2 cb = cmul(Fc, fb[f * KT]);
+                    for (int y = 0; y < G.My; ++y) {
+                        const float2 w = cmul(cb, fy[y * KT]);
+                        for (int m = 0; m < G.Mz; m += 2) {
+                            const float2 p0 = cmul(w, fz[m * KT]), p1 = cmul(w, fz[(m + 1) * KT]);
+                            nps += p0.x * p0.x + p0.y * p0.y + p1.x * p1.x + p1.y * p1.y;
+                            const float4 hi = make_float4(tc::tf32_rn(p0.x), tc::tf32_rn(p0.y), tc::tf32_rn(p1.x),
+                                                          tc::tf32_rn(p1.y));
+                            const float4 lo = make_float4(tc::tf32_rn(p0.x - hi.x), tc::tf32_rn(p0.y - hi.y),
+                                                          tc::tf32_rn(p1.x - hi.z), tc::tf32_rn(p1.y - hi.w));
+                            const int off = tc::core_off(row, 2 * (y * G.Mz + m), KC) >> 2;
+                            *reinterpret_cast<float4*>(aHi + off) = hi;
+                            *reinterpret_cast<float4*>(aLo + off) = lo;
+                        }
+                    }
+                });
+            }
+        }
+        wait_mma();
+        float2 h[NC];
+        float2 pr;
+        {
+            uint32_t v[32];
+            tc::tmem_ld32(tlane + 0, v); tc::tmem_ld_wait();
+            #pragma unroll
+            for (int i = 0; i < 32; ++i) h[i].x = __uint_as_float(v[i]);
+            tc::tmem_ld32(tlane + 32, v); tc::tmem_ld_wait();
+            #pragma unroll
+            for (int i = 0; i < 31; ++i) h[32 + i].x = __uint_as_float(v[i]);
+            pr.x = __uint_as_float(v[31]);
+            tc::tmem_ld32(tlane + 64, v); tc::tmem_ld_wait();
+            #pragma unroll
+            for (int i = 0; i < 32; ++i) h[i].y = __uint_as_float(v[i]);
+            tc::tmem_ld32(tlane + 96, v); tc::tmem_ld_wait();
+            #pragma unroll
+            for (int i = 0; i < 31; ++i) h[32 + i].y = __uint_as_float(v[i]);
+            pr.y = __uint_as_float(v[31]);
+        }
+        // tau (FP32; J is evaluated exactly at the tau used) and the O(S) amplitude sums
+        float hh = 0.f, tx0 = 0.f, ty0 = 0.f, tx1 = 0.f, ty1 = 0.f, gg0 = 0.f, gg1 = 0.f;
+        #pragma unroll
+        for (int c = 0; c < NC; ++c) {
+            hh = fmaf(h[c].x, h[c].x, fmaf(h[c].y, h[c].y, hh));
+            const float2 w = y0s[c];
+            const float dl = dls[c].x;
+            const float m2 = fmaf(h[c].x, h[c].x, h[c].y * h[c].y);
+            if (c & 1) {
+                tx1 = fmaf(w.x, h[c].x, fmaf(-w.y, h[c].y, tx1));
+                ty1 = fmaf(w.x, h[c].y, fmaf(w.y, h[c].x, ty1));
+                gg1 = fmaf(dl, m2, gg1);
+            } else {
+                tx0 = fmaf(w.x, h[c].x, fmaf(-w.y, h[c].y, tx0));
+                ty0 = fmaf(w.x, h[c].y, fmaf(w.y, h[c].x, ty0));
+                gg0 = fmaf(dl, m2, gg0);
+            }
+        }
+        const float ieb = 1.0f / ebf;
+        const float alpha = (nps - hh * ieb) * ieb;
+        const float zf = (float)zeta;
+        const float2 af = make_float2(zf * mrf, zf * mif);
+        const float q = (gmf + (mrf * mrf + mif * mif) * (1.0f - zf)) * zf;
+        const float iq = (q > 0.f) ? 1.0f / q : 0.f;
+        float2 tf = af;
+        if (q > 0.f) {
+            const float den = alpha + iq;
+            tf = make_float2((pr.x * ieb + af.x * iq) / den, (pr.y * ieb + af.y * iq) / den);
+        }
+        // ---- pass 2: V V^H psi per group of frequencies, then the element-wise residual
+        ff rr{0.f, 0.f};
+        float pn = 0.f;
+        tc::fence_before_sync();   // TMEM reads of h complete before pass 2 reuses the columns
+        for (int g = 0; g < NG; ++g) {
+            const int f0 = g * GF, nfg = min(GF, Nf - f0);
+            const int nk = nfg * Nm, nkp = round16(nk), N2 = 2 * nkp;
+            float* sA = sR;
+            float* sB = sR + 4 * 128 * KC2;
+            float* aHi = sA + (size_t)(tile * 2 + 0) * 128 * KC2;
+            float* aLo = sA + (size_t)(tile * 2 + 1) * 128 * KC2;
+            const uint32_t idesc = tc::idesc_tf32_f32(128, N2);
+            const float* gB = Bt2 + ((((size_t)s * J + j) * NG + g) * 4) * (size_t)(2 * KAPPA_TC_N2 * KC2);
+            #pragma unroll
+            for (int kc = 0; kc < 4; ++kc) {
+                round(gB + (size_t)kc * (2 * KAPPA_TC_N2 * KC2), (uint32_t)(2 * N2 * KC2 * 4), sA, sB, KC2,
+                      (uint32_t)(N2 * KC2 * 4), idesc, (uint32_t)(kc * KAPPA_TC_N2), false, [&]() {
+                    #pragma unroll
+                    for (int c2 = 0; c2 < KC2 / 4; ++c2) {       // basis columns c, c + 1
+                        const int c = kc * 16 + 2 * c2;
+                        const float2 u0 = h[c];
+                        const float2 u1 = (c + 1 < NC) ? h[c + 1] : make_float2(0.f, 0.f);
+                        const float4 hi = make_float4(tc::tf32_rn(u0.x), tc::tf32_rn(u0.y), tc::tf32_rn(u1.x), tc::tf32_rn(u1.y));
+                        const float4 lo = make_float4(tc::tf32_rn(u0.x - hi.x), tc::tf32_rn(u0.y - hi.y),
+                                                      tc::tf32_rn(u1.x - hi.z), tc::tf32_rn(u1.y - hi.w));
+                        const int off = tc::core_off(row, 4 * c2, KC2) >> 2;
+                        *reinterpret_cast<float4*>(aHi + off) = hi;
+                        *reinterpret_cast<float4*>(aLo + off) = lo;
+                    }
+                });
+            }
+            wait_mma();
+            for (int b = 0; b < nk; b += 8) {
+                // the four chunk accumulators, added pairwise: (a0 + a1) + (a2 + a3)
+                float vre[8], vim[8];
+                {
+                    uint32_t r0[8], r1[8], i0[8], i1[8];
+                    tc::tmem_ld8(tlane + (uint32_t)b, r0);
+                    tc::tmem_ld8(tlane + (uint32_t)(KAPPA_TC_N2 + b), r1);
+                    tc::tmem_ld8(tlane + (uint32_t)(nkp + b), i0);
+                    tc::tmem_ld8(tlane + (uint32_t)(KAPPA_TC_N2 + nkp + b), i1);
+                    tc::tmem_ld_wait();
+                    #pragma unroll
+                    for (int i = 0; i < 8; ++i) {
+                        vre[i] = __uint_as_float(r0[i]) + __uint_as_float(r1[i]);
+                        vim[i] = __uint_as_float(i0[i]) + __uint_as_float(i1[i]);
+                    }
+                    tc::tmem_ld8(tlane + (uint32_t)(2 * KAPPA_TC_N2 + b), r0);
+                    tc::tmem_ld8(tlane + (uint32_t)(3 * KAPPA_TC_N2 + b), r1);
+                    tc::tmem_ld8(tlane + (uint32_t)(2 * KAPPA_TC_N2 + nkp + b), i0);
+                    tc::tmem_ld8(tlane + (uint32_t)(3 * KAPPA_TC_N2 + nkp + b), i1);
+                    tc::tmem_ld_wait();
+                    #pragma unroll
+                    for (int i = 0; i < 8; ++i) {
+                        vre[i] += __uint_as_float(r0[i]) + __uint_as_float(r1[i]);
+                        vim[i] += __uint_as_float(i0[i]) + __uint_as_float(i1[i]);
+                    }
+                }
+                #pragma unroll
+                for (int i = 0; i < 8; ++i) {
+                    const int kl = b + i;
+                    if (kl >= nk) break;
+                    const int k = f0 * Nm + kl;
+                    const int f = k / Nm, ym = k - f * Nm, y = ym / G.Mz, m = ym - y * G.Mz;
+                    // psi_k exactly as pass 1 formed it
+                    const float2 cb = cmul(Fc, fb[f * KT]);
+                    const float2 w = cmul(cb, fy[y * KT]);
+                    const float2 ps = cmul(w, fz[m * KT]);
+                    const float vsx = vre[i], vsy = vim[i];
+                    const float2 pp2 = make_float2(ps.x - vsx * ieb, ps.y - vsy * ieb);
+                    pn += pp2.x * pp2.x + pp2.y * pp2.y;
+                    // t = tau pp2 exactly: re = p1 - p2, im = p3 + p4 (+ FMA errors)
+                    const float p1 = __fmul_rn(tf.x, pp2.x), e1 = fmaf(tf.x, pp2.x, -p1);
+                    const float p2 = __fmul_rn(tf.y, pp2.y), e2 = fmaf(tf.y, pp2.y, -p2);
+                    const float p3 = __fmul_rn(tf.x, pp2.y), e3 = fmaf(tf.x, pp2.y, -p3);
+                    const float p4 = __fmul_rn(tf.y, pp2.x), e4 = fmaf(tf.y, pp2.x, -p4);
+                    const float4 r0 = r0s[k];
+                    float sx, ex1, ex2, sy, ey1, ey2;
+                    ff rx, ry;
+                    two_sum(r0.x, -p1, sx, ex1);
+                    two_sum(sx, p2, rx.hi, ex2);
+                    rx.lo = __fadd_rn(__fadd_rn(r0.z, __fsub_rn(e2, e1)), __fadd_rn(ex1, ex2));
+                    two_sum(r0.y, -p3, sy, ey1);
+                    two_sum(sy, -p4, ry.hi, ey2);
+                    ry.lo = __fsub_rn(__fadd_rn(r0.w, __fadd_rn(ey1, ey2)), __fadd_rn(e3, e4));
+                    ff_acc_sq(rr, make_float2(rx.hi, ry.hi));
+                    rr.lo = fmaf(2.0f * rx.hi, rx.lo, fmaf(2.0f * ry.hi, ry.lo, rr.lo));
+                }
+            }
+            tc::fence_before_sync();   // TMEM reads complete before the next group's MMAs
+        }
+        const float Tx = tx0 + tx1, Ty = ty0 + ty1, gg = gg0 + gg1;
+        const double dyd = 2.0 * ((double)tf.x * Tx + (double)tf.y * Ty) * ieb64 -
+                           ((double)tf.x * tf.x + (double)tf.y * tf.y) * (double)gg * ieb64 * ieb64;
+        double dlt = J0r - ((double)rr.hi + (double)rr.lo) * ieb64 + dyd;
+        if (q > 0.f) {
+            const double dx = (double)tf.x - zeta * mr, dyt = (double)tf.y - zeta * mi;
+            dlt -= (dx * dx + dyt * dyt) * (double)iq;
+            const float alpha_acc = pn * ieb + gg * ieb * ieb;
+            dlt -= (double)log1pf(q * alpha_acc);
+        }
+        delta_sum += dlt;
     }
+    if (act) D.lw_y[(size_t)s * P + p] = delta_sum;
+    if (bad && (tid & 31) == 0) atomicOr(D.kerr, 1);
+    if (tid == 0) {
+        // after a timeout: let the copies and MMAs still in flight land (bounded)
+        for (uint32_t q = n_waited_b; q < n_bulk; ++q) tc::mbar_wait(mb_b, q & 1u, KAPPA_TC_WAIT);
+        if (n_commit > 0) tc::mbar_wait(mb_mma, (n_commit - 1) & 1u, KAPPA_TC_WAIT);
+    }
+    tc::fence_before_sync();
+    __syncthreads();
+    tc::fence_after_sync();
+    if (warp == 0) tc::tmem_dealloc(tmem, 512);
 }
 
 // ---------------------------------------------------------------- iota (warp per particle)
@@ -989,26 +1206,63 @@ __global__ void k_kappa_btile(DevGeom G, DevState D, int SCA, float* __restrict_
     }
 }
 
-// dynamic shared memory of the tensor-core variant: A/B operand tiles and barriers, the
-// factors of 256 particles, all Nz rows of V (64 columns) and the low part of r0
+// B tiles of the tensor-core pass 2, once per (s, j, group g of frequencies, K chunk kc):
+// rows n < nkp are the real parts, rows nkp <= n < 2 nkp the imaginary parts of the
+// group's elements e (rows past the group's nk elements are zero), against the real K
+// index 2 (c - 16 kc) + part of basis columns c (part 0 = Re h_c, 1 = Im h_c; the r0
+// column 63 excluded): Re row [Re V_ec, Im V_ec], Im row [Im V_ec, -Re V_ec]; TF32 hi/lo,
+// K-major core-matrix layout, [hi, lo] per slot of 2 x 64 x 32 floats.
+__global__ void k_kappa_btile2(DevGeom G, DevState D, int SCA, float* __restrict__ Bt2) {
+    constexpr int KC2 = KAPPA_TC_KC2;
+    const int s = blockIdx.x, j = blockIdx.y, g = blockIdx.z >> 2, kc = blockIdx.z & 3;
+    const int J = G.J, Nz = G.Nz, Nm = G.My * G.Mz, GF = kappa_tc_group_freqs(Nm), NG = kappa_tc_groups(G.Nf, Nm);
+    const int f0 = g * GF, nk = min(GF, G.Nf - f0) * Nm, nkp = round16(nk), N2 = 2 * nkp;
+    const float2* V = D.kV + ((size_t)s * J + j) * Nz * SCA;
+    float* out = Bt2 + ((((size_t)s * J + j) * NG + g) * 4 + kc) * (size_t)(2 * KAPPA_TC_N2 * KC2);
+    for (int t = threadIdx.x; t < N2 * KC2; t += blockDim.x) {
+        const int n = t / KC2, kk = t - n * KC2;
+        const bool im = n >= nkp;
+        const int e = im ? n - nkp : n;
+        const int c = kc * 16 + (kk >> 1), part = kk & 1;
+        float2 v = make_float2(0.f, 0.f);
+        if (e < nk && c < 63) v = V[(size_t)(f0 * Nm + e) * SCA + c];
+        const float b = im ? (part == 0 ? v.y : -v.x) : (part == 0 ? v.x : v.y);
+        const float hi = tc::tf32_rn(b);
+        const int off = tc::core_off(n, kk, KC2) >> 2;
+        out[off] = hi;
+        out[N2 * KC2 + off] = tc::tf32_rn(b - hi);
+    }
+}
+
+// dynamic shared memory of k_kappa_tc: the operand region (pass 1: A [2][hi, lo][128 x 2Nm],
+// B [hi, lo][128 x 2Nm]; pass 2: A [2][hi, lo][128 x 32], B [hi, lo][64 x 32]), barriers,
+// r0 (hi, lo) per element, 1/lambda_c and w_c, and the factors of 256 particles
 static size_t kappa_tc_smem(const DevGeom& G) {
     const size_t Nm = (size_t)G.My * G.Mz, nfac = (size_t)G.Nf + G.My + G.Mz;
-    const size_t tcb = 6 * 128 * (2 * Nm) * sizeof(float) + 32;
-    const size_t fixed = (2 * 64 + nfac * 256) * sizeof(float2);
-    return tcb + fixed + (size_t)G.Nf * Nm * 65 * sizeof(float2);
+    const size_t rf = std::max<size_t>(6 * 128 * 2 * Nm, 4 * 128 * KAPPA_TC_KC2 + 2 * KAPPA_TC_N2 * KAPPA_TC_KC2);
+    return rf * sizeof(float) + 32 + (size_t)G.Nz * sizeof(float4) + 128 * sizeof(float2) + nfac * 256 * sizeof(float2);
 }
 // the tensor-core variant applies with 64 basis columns (SCA = 64), 2 My Mz in {8, 16, 32}
-// and every row of V resident in shared memory
+// and its shared memory within the opt-in limit
 bool kappa_tc_ok(const DevGeom& G, int SCA) {
     const int KC = 2 * G.My * G.Mz;
     return SCA == 64 && (KC == 8 || KC == 16 || KC == 32) && kappa_tc_smem(G) <= 227 * 1024;
 }
-size_t kappa_btile_floats(const DevGeom& G, int S_max) {
+static size_t kappa_btile1_floats(const DevGeom& G, int S_max) {
     return (size_t)S_max * G.J * G.Nf * 2 * 128 * (2 * G.My * G.Mz);
 }
-void launch_kappa_btile(const DevGeom& G, const DevState& D, int S, int SCA, cudaStream_t st) {
-    if (!D.kB || !kappa_tc_ok(G, SCA)) return;
+size_t kappa_btile_floats(const DevGeom& G, int S_max) {
+    const int Nm = G.My * G.Mz;
+    return kappa_btile1_floats(G, S_max) +
+           (size_t)S_max * G.J * kappa_tc_groups(G.Nf, Nm) * 4 * (2 * KAPPA_TC_N2 * KAPPA_TC_KC2);
+}
+int launch_kappa_btile(const DevGeom& G, const DevState& D, int S, int SCA, cudaStream_t st) {
+    if (!D.kB || !kappa_tc_ok(G, SCA)) return 0;
+    const int Nm = G.My * G.Mz;
     k_kappa_btile<<<dim3(S, G.J, G.Nf), 256, 0, st>>>(G, D, SCA, D.kB);
+    k_kappa_btile2<<<dim3(S, G.J, kappa_tc_groups(G.Nf, Nm) * 4), 256, 0, st>>>(G, D, SCA,
+                                                                                D.kB + kappa_btile1_floats(G, S));
+    return 2;
 }
 
 template <int SC>
@@ -1020,8 +1274,8 @@ static void launch_kappa_sc(const DevGeom& G, const DevParams& Pm, const DevStat
     dim3 grid((Pm.P + 255) / 256, S);
     if constexpr (SC == 64) {
         if (D.kB && kappa_tc_ok(G, SCA)) {
-            smem_allow_max((const void*)k_kappa<SC, true>);
-            k_kappa<SC, true><<<grid, 256, kappa_tc_smem(G), st>>>(G, Pm, D, S, SCA, G.Nf, D.kB);
+            smem_allow_max((const void*)k_kappa_tc);
+            k_kappa_tc<<<grid, 256, kappa_tc_smem(G), st>>>(G, Pm, D, S, SCA, D.kB, D.kB + kappa_btile1_floats(G, S));
             return;
         }
     }
@@ -1029,8 +1283,8 @@ static void launch_kappa_sc(const DevGeom& G, const DevParams& Pm, const DevStat
     int fch = G.Nf;
     while (fch > 1 && fixed + fch * per_f > limit) fch = (fch + 1) / 2;
     const size_t smem = fixed + fch * per_f;
-    smem_allow_max((const void*)k_kappa<SC, false>);
-    k_kappa<SC, false><<<grid, 256, smem, st>>>(G, Pm, D, S, SCA, fch, nullptr);
+    smem_allow_max((const void*)k_kappa<SC>);
+    k_kappa<SC><<<grid, 256, smem, st>>>(G, Pm, D, S, SCA, fch);
 }
 
 void launch_kappa(const DevGeom& G, const DevParams& Pm, const DevState& D, int S, int SCA, cudaStream_t st) {
