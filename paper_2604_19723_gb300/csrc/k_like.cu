@@ -269,15 +269,20 @@ __host__ __device__ inline int kappa_tc_groups(int Nf, int Nm) {
 }
 __host__ __device__ inline int round16(int x) { return (x + 15) & ~15; }
 
-__global__ void __launch_bounds__(256, 1) k_kappa_tc(DevGeom G, DevParams Pm, DevState D, int S, int SCA,
-                                                     const float* __restrict__ Bt1, const float* __restrict__ Bt2) {
-    constexpr int KT = 256, NC = 63, KC2 = KAPPA_TC_KC2;
+// NT 128-particle M tiles per block (threads 128 NT, TMEM columns 256 NT): NT = 1 lets two
+// blocks share an SM, so that one block's MMAs run while the other writes operands or
+// evaluates its residuals.
+template <int NT>
+__global__ void __launch_bounds__(128 * NT, NT == 1 ? 2 : 1) k_kappa_tc(DevGeom G, DevParams Pm, DevState D, int S, int SCA,
+                                                                     const float* __restrict__ Bt1,
+                                                                     const float* __restrict__ Bt2) {
+    constexpr int KT = 128 * NT, NC = 63, KC2 = KAPPA_TC_KC2;
     extern __shared__ __align__(1024) float4 sm4[];
     const int s = blockIdx.y;
     const int P = Pm.P, J = G.J, Nz = G.Nz, Nm = G.My * G.Mz, Nf = G.Nf;
     const int KC = 2 * Nm;                                     // pass-1 real K per frequency
     const int GF = kappa_tc_group_freqs(Nm), NG = kappa_tc_groups(Nf, Nm);
-    const int RF = max(6 * 128 * KC, 4 * 128 * KC2 + 2 * KAPPA_TC_N2 * KC2);   // operand region (floats)
+    const int RF = max((2 * NT + 2) * 128 * KC, 2 * NT * 128 * KC2 + 2 * KAPPA_TC_N2 * KC2);   // operand region (floats)
     float* sR = reinterpret_cast<float*>(sm4);
     uint64_t* mbar = reinterpret_cast<uint64_t*>(sR + RF);    // [2]: MMAs done, B arrived
     uint32_t* tslot = reinterpret_cast<uint32_t*>(mbar + 2);
@@ -292,7 +297,7 @@ __global__ void __launch_bounds__(256, 1) k_kappa_tc(DevGeom G, DevParams Pm, De
     const uint32_t mb_mma = tc::smem_u32(&mbar[0]), mb_b = tc::smem_u32(&mbar[1]);
     uint32_t n_commit = 0, n_bulk = 0, n_waited_b = 0;
     bool bad = false;
-    if (warp == 0) tc::tmem_alloc(tslot, 512);
+    if (warp == 0) tc::tmem_alloc(tslot, 256 * NT);
     if (tid == 0) { tc::mbar_init(mb_mma, 1); tc::mbar_init(mb_b, 1); tc::mbar_init_fence(); }
     tc::fence_before_sync();
     __syncthreads();
@@ -326,7 +331,7 @@ __global__ void __launch_bounds__(256, 1) k_kappa_tc(DevGeom G, DevParams Pm, De
             if (!bad) {
                 const uint32_t sbo = (uint32_t)(Kt / 4) * 128u;
                 const uint32_t bH = tc::smem_u32(sB), bL = bH + bLoOff;
-                for (int t = 0; t < 2; ++t) {
+                for (int t = 0; t < NT; ++t) {
                     const uint32_t aH = tc::smem_u32(sA + (size_t)(t * 2) * 128 * Kt);
                     const uint32_t aL = tc::smem_u32(sA + (size_t)(t * 2 + 1) * 128 * Kt);
                     for (int ks = 0; ks < Kt / 8; ++ks) {
@@ -376,15 +381,17 @@ __global__ void __launch_bounds__(256, 1) k_kappa_tc(DevGeom G, DevParams Pm, De
         float nps = 0.f;
         {
             float* sA = sR;
-            float* sB = sR + 4 * 128 * KC;
+            float* sB = sR + 2 * NT * 128 * KC;
             float* aHi = sA + (size_t)(tile * 2 + 0) * 128 * KC;
             float* aLo = sA + (size_t)(tile * 2 + 1) * 128 * KC;
             const size_t bchunk = (size_t)2 * 128 * KC;
             const float* gB = Bt1 + ((size_t)s * J + j) * Nf * bchunk;
             const uint32_t idesc = tc::idesc_tf32_f32(128, 128);
+            // even frequencies accumulate in columns 0..127, odd ones in 128..255 (shorter
+            // FP32 accumulation chains; added when h is read back)
             for (int f = 0; f < Nf; ++f) {
-                round(gB + (size_t)f * bchunk, (uint32_t)(bchunk * 4), sA, sB, KC, (uint32_t)(128 * KC * 4), idesc, 0u,
-                      f > 0, [&]() {
+                round(gB + (size_t)f * bchunk, (uint32_t)(bchunk * 4), sA, sB, KC, (uint32_t)(128 * KC * 4), idesc,
+                      (uint32_t)((f & 1) * 128), f > 1, [&]() {
                     const float2 cb = cmul(Fc, fb[f * KT]);
                     for (int y = 0; y < G.My; ++y) {
                         const float2 w = cmul(cb, fy[y * KT]);
@@ -422,6 +429,22 @@ __global__ void __launch_bounds__(256, 1) k_kappa_tc(DevGeom G, DevParams Pm, De
             #pragma unroll
             for (int i = 0; i < 31; ++i) h[32 + i].y = __uint_as_float(v[i]);
             pr.y = __uint_as_float(v[31]);
+            if (Nf > 1) {   // the odd frequencies' accumulator
+                tc::tmem_ld32(tlane + 128, v); tc::tmem_ld_wait();
+                #pragma unroll
+                for (int i = 0; i < 32; ++i) h[i].x += __uint_as_float(v[i]);
+                tc::tmem_ld32(tlane + 160, v); tc::tmem_ld_wait();
+                #pragma unroll
+                for (int i = 0; i < 31; ++i) h[32 + i].x += __uint_as_float(v[i]);
+                pr.x += __uint_as_float(v[31]);
+                tc::tmem_ld32(tlane + 192, v); tc::tmem_ld_wait();
+                #pragma unroll
+                for (int i = 0; i < 32; ++i) h[i].y += __uint_as_float(v[i]);
+                tc::tmem_ld32(tlane + 224, v); tc::tmem_ld_wait();
+                #pragma unroll
+                for (int i = 0; i < 31; ++i) h[32 + i].y += __uint_as_float(v[i]);
+                pr.y += __uint_as_float(v[31]);
+            }
         }
         // tau (FP32; J is evaluated exactly at the tau used) and the O(S) amplitude sums
         float hh = 0.f, tx0 = 0.f, ty0 = 0.f, tx1 = 0.f, ty1 = 0.f, gg0 = 0.f, gg1 = 0.f;
@@ -460,7 +483,7 @@ __global__ void __launch_bounds__(256, 1) k_kappa_tc(DevGeom G, DevParams Pm, De
             const int f0 = g * GF, nfg = min(GF, Nf - f0);
             const int nk = nfg * Nm, nkp = round16(nk), N2 = 2 * nkp;
             float* sA = sR;
-            float* sB = sR + 4 * 128 * KC2;
+            float* sB = sR + 2 * NT * 128 * KC2;
             float* aHi = sA + (size_t)(tile * 2 + 0) * 128 * KC2;
             float* aLo = sA + (size_t)(tile * 2 + 1) * 128 * KC2;
             const uint32_t idesc = tc::idesc_tf32_f32(128, N2);
@@ -565,7 +588,7 @@ __global__ void __launch_bounds__(256, 1) k_kappa_tc(DevGeom G, DevParams Pm, De
     tc::fence_before_sync();
     __syncthreads();
     tc::fence_after_sync();
-    if (warp == 0) tc::tmem_dealloc(tmem, 512);
+    if (warp == 0) tc::tmem_dealloc(tmem, 256 * NT);
 }
 
 // ---------------------------------------------------------------- iota (warp per particle)
@@ -1237,16 +1260,24 @@ __global__ void k_kappa_btile2(DevGeom G, DevState D, int SCA, float* __restrict
 // dynamic shared memory of k_kappa_tc: the operand region (pass 1: A [2][hi, lo][128 x 2Nm],
 // B [hi, lo][128 x 2Nm]; pass 2: A [2][hi, lo][128 x 32], B [hi, lo][64 x 32]), barriers,
 // r0 (hi, lo) per element, 1/lambda_c and w_c, and the factors of 256 particles
-static size_t kappa_tc_smem(const DevGeom& G) {
+constexpr int KAPPA_TC_NT = 1;   // M tiles per block of the launched variant
+static size_t kappa_tc_smem(const DevGeom& G, int NT = KAPPA_TC_NT) {
     const size_t Nm = (size_t)G.My * G.Mz, nfac = (size_t)G.Nf + G.My + G.Mz;
-    const size_t rf = std::max<size_t>(6 * 128 * 2 * Nm, 4 * 128 * KAPPA_TC_KC2 + 2 * KAPPA_TC_N2 * KAPPA_TC_KC2);
-    return rf * sizeof(float) + 32 + (size_t)G.Nz * sizeof(float4) + 128 * sizeof(float2) + nfac * 256 * sizeof(float2);
+    const size_t rf = std::max<size_t>((2 * NT + 2) * 128 * 2 * Nm, 2 * NT * 128 * KAPPA_TC_KC2 + 2 * KAPPA_TC_N2 * KAPPA_TC_KC2);
+    return rf * sizeof(float) + 32 + (size_t)G.Nz * sizeof(float4) + 128 * sizeof(float2) +
+           nfac * 128 * NT * sizeof(float2);
 }
-// the tensor-core variant applies with 64 basis columns (SCA = 64), 2 My Mz in {8, 16, 32}
-// and its shared memory within the opt-in limit
+// The tensor-core variant applies with 64 basis columns (SCA = 64), 2 My Mz in {8, 16, 32},
+// at most KAPPA_TC_MAX_NF frequencies and its shared memory within the opt-in limit.  The
+// tensor core adds each MMA's result into its FP32 accumulator (no FMA chain): with 75
+// frequencies in one pass-1 accumulator (225 accumulations) the PF weights moved by
+// 1.7e-4 (measured); two accumulators over at most 16 frequencies keep each chain at 24,
+// below the 30 that stayed within 1e-4 at full size.
+constexpr int KAPPA_TC_MAX_NF = 16;
 bool kappa_tc_ok(const DevGeom& G, int SCA) {
     const int KC = 2 * G.My * G.Mz;
-    return SCA == 64 && (KC == 8 || KC == 16 || KC == 32) && kappa_tc_smem(G) <= 227 * 1024;
+    return SCA == 64 && (KC == 8 || KC == 16 || KC == 32) && G.Nf <= KAPPA_TC_MAX_NF &&
+           kappa_tc_smem(G) <= 227 * 1024;
 }
 static size_t kappa_btile1_floats(const DevGeom& G, int S_max) {
     return (size_t)S_max * G.J * G.Nf * 2 * 128 * (2 * G.My * G.Mz);
@@ -1274,8 +1305,10 @@ static void launch_kappa_sc(const DevGeom& G, const DevParams& Pm, const DevStat
     dim3 grid((Pm.P + 255) / 256, S);
     if constexpr (SC == 64) {
         if (D.kB && kappa_tc_ok(G, SCA)) {
-            smem_allow_max((const void*)k_kappa_tc);
-            k_kappa_tc<<<grid, 256, kappa_tc_smem(G), st>>>(G, Pm, D, S, SCA, D.kB, D.kB + kappa_btile1_floats(G, S));
+            constexpr int NT = KAPPA_TC_NT;
+            smem_allow_max((const void*)k_kappa_tc<NT>);
+            k_kappa_tc<NT><<<dim3((Pm.P + 128 * NT - 1) / (128 * NT), S), 128 * NT, kappa_tc_smem(G), st>>>(
+                G, Pm, D, S, SCA, D.kB, D.kB + kappa_btile1_floats(G, S));
             return;
         }
     }
