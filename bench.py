@@ -91,11 +91,11 @@ def a5_flops(P, S, J, Nz):
 # a single-pass metric set, at the full size of the workload), valid while the kernel
 # sources hash to the recorded value.
 TRAFFIC_RECORDS = {
-    "k_kappa": {"workload": "scale_64x100k", "P": 100000, "bytes": 858.85e6,
-                "sources_sha256": "2a16276e012f03d36121bddc626aca6805a32153822d36a6bb4b35a65ae8ff36",
+    "k_kappa": {"workload": "scale_64x100k", "P": 100000, "bytes": 925.64e6,
+                "sources_sha256": "1292387ebaba6953441ac9752ac6b80c47c954234dd29f38bca4fe8ead0e9524",
                 "profile": "profiles/dram_scale_64x100k.md"},
-    "k_iota_blk": {"workload": "scale_64x100k", "P": 100000, "bytes": 712.06e6,
-                   "sources_sha256": "2a16276e012f03d36121bddc626aca6805a32153822d36a6bb4b35a65ae8ff36",
+    "k_iota_blk": {"workload": "scale_64x100k", "P": 100000, "bytes": 708.67e6,
+                   "sources_sha256": "1292387ebaba6953441ac9752ac6b80c47c954234dd29f38bca4fe8ead0e9524",
                    "profile": "profiles/dram_scale_64x100k.md"},
 }
 KERNEL_SOURCES = ("paper_2604_19723_gb300/csrc/k_like.cu", "paper_2604_19723_gb300/csrc/bp_kernels.cuh",
