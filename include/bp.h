@@ -244,6 +244,32 @@ enum { BP_NOALLOC_MAX_P = 1 << 20 };
 bp_status bp_resample_noalloc(const double* w_dev, int P, uint64_t seed, int n, int kind, int index,
                               int* idx_dev, void* cuda_stream);
 
+/* ------------------------------------------------------------------ PCRLB
+ * Posterior Cramer-Rao lower bounds (Sec. VI, Supplementary Sec. S-VII) as accuracy
+ * references.  Global parameters: the MT state (6), the K SFV positions (3K), the
+ * nuisance phases (coherent = 1: one per component shared by all PAs, K+1; 0: one per
+ * component and PA, (K+1) J), the moduli ((K+1) J) and the common noise variance: dim =
+ * 6 + 3K + nph + (K+1) J + 1, components with the LoS first.  For the bound the complex
+ * amplitudes rho~ include path loss and carrier phase, and the array response is
+ * unit-modulus (Sec. S-VII).  Reading: the SFV rows of the Jacobian are the full
+ * derivative of the PA-to-virtual-MT vector (the printed mapping block holds the
+ * reflection fixed).  FP64, synchronous; 0 <= K <= 15. */
+
+/* Bayesian snapshot FIM: the mean over M realisations of sum_j G_j J_ch^(j) G_j^T
+ * (eq. FIMclassic; Table S-I for J_ch).  x: M x 6 MT states, sfv: M x K x 3, rho:
+ * M x J x (K+1) complex (interleaved) amplitudes rho~, eta: noise variance; fim: dim x
+ * dim, written.  Host pointers.  BP_ERR_CAPACITY if the shape exceeds shared memory. */
+bp_status bp_pcrlb_fim(const bp_geometry* geom, int K, int coherent, int M, const double* x, const double* sfv,
+                       const double* rho, double eta, double* fim, void* cuda_stream);
+
+/* The recursion J_{n|n} = J_B,n + (F J_{n-1|n-1}^-1 F^T + Q)^-1 (eq. posteriorCRLB,
+ * priorFIM) from J_{1|0} = J10 over N steps of snapshot FIMs Jsnap (N x dim x dim), with
+ * PEB_n = sqrt(tr P[0:3, 0:3]) and MEB_{k,n} = sqrt(tr P over SFV k), P = J_{n|n}^-1
+ * (peb: N, meb: N x K, written).  F, Q, J10: dim x dim.  Host pointers.  BP_ERR_NUMERIC
+ * if an inverted matrix is not positive definite. */
+bp_status bp_pcrlb_recursion(int dim, int N, int K, const double* F, const double* Q, const double* J10,
+                             const double* Jsnap, double* peb, double* meb, void* cuda_stream);
+
 /* ------------------------------------------------------------------ batches
  * Many independent filters ("scenarios": each its own geometry, parameters,
  * particle count and PF capacity) stepped together on one GPU.  The paper has

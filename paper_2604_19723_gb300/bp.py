@@ -27,7 +27,7 @@ ENTRY_POINTS = ("bp_init", "bp_predict", "bp_update", "bp_estimate", "bp_free", 
                 "bp_synthesize", "bp_launch_count", "bp_set_profiling", "bp_get_profile",
                 "bp_resample_noalloc", "bp_batch_init", "bp_batch_step", "bp_batch_z_offset", "bp_batch_z_floats",
                 "bp_batch_sync", "bp_batch_handle", "bp_batch_stream_of", "bp_batch_device_bytes", "bp_batch_free",
-                "bp_batch_last_error")
+                "bp_batch_last_error", "bp_pcrlb_fim", "bp_pcrlb_recursion")
 PROFILE_STAGES = ("predict", "row_sums", "table", "stage", "kappa", "iota", "nu", "normalize", "resample")
 
 
@@ -126,6 +126,9 @@ def load() -> C.CDLL:
     lib.bp_batch_free.argtypes = [vp]
     lib.bp_batch_last_error.argtypes = [vp]
     lib.bp_batch_last_error.restype = C.c_char_p
+    lib.bp_pcrlb_fim.argtypes = [C.POINTER(_Geometry), C.c_int, C.c_int, C.c_int, C.POINTER(C.c_double),
+                                 C.POINTER(C.c_double), C.POINTER(C.c_double), C.c_double, C.POINTER(C.c_double), vp]
+    lib.bp_pcrlb_recursion.argtypes = [C.c_int, C.c_int, C.c_int] + [C.POINTER(C.c_double)] * 6 + [vp]
     untyped = ("bp_last_error", "bp_launch_count", "bp_batch_z_offset", "bp_batch_z_floats",
                "bp_batch_device_bytes", "bp_batch_last_error")
     for f in ENTRY_POINTS:
@@ -433,6 +436,43 @@ class Batch:
         self._check(self.lib.bp_batch_handle(self.b, i, C.byref(h)), "bp_batch_handle")
         g, p, P, S_max, _, _ = self.scen[i]
         return _BatchMember(self, i, h, g, p, P, S_max)
+
+
+def pcrlb_dim(K: int, J: int, coherent: bool) -> int:
+    return 6 + 3 * K + ((K + 1) if coherent else (K + 1) * J) + (K + 1) * J + 1
+
+
+def pcrlb_fim(geom: Geometry, x, sfv, rho, eta: float, coherent: bool, stream=None) -> np.ndarray:
+    """Bayesian snapshot FIM (bp_pcrlb_fim): mean over the M realisations in x (M, 6),
+    sfv (M, K, 3), rho (M, J, K+1) complex."""
+    lib = load()
+    g = _GeomHolder(geom)
+    x = np.ascontiguousarray(np.atleast_2d(x), np.float64)
+    M = x.shape[0]
+    sfv = np.ascontiguousarray(np.asarray(sfv, np.float64).reshape(M, -1, 3), np.float64)
+    K = sfv.shape[1]
+    rho = np.asarray(rho).reshape(M, geom.J, K + 1)
+    rr = np.ascontiguousarray(np.stack([rho.real, rho.imag], -1), np.float64)
+    d = pcrlb_dim(K, geom.J, coherent)
+    out = np.zeros((d, d))
+    st = lib.bp_pcrlb_fim(C.byref(g.s), K, int(bool(coherent)), M, _dptr(x), _dptr(sfv) if K else None, _dptr(rr),
+                          float(eta), _dptr(out), C.c_void_p(_stream_handle(stream)))
+    _check(lib, None, st, "bp_pcrlb_fim")
+    return out
+
+
+def pcrlb_recursion(F, Q, J10, Jsnap, K: int, stream=None):
+    """PEB (N,) and MEB (N, K) of the recursion (bp_pcrlb_recursion)."""
+    lib = load()
+    F, Q, J10 = (np.ascontiguousarray(a, np.float64) for a in (F, Q, J10))
+    Js = np.ascontiguousarray(np.asarray(Jsnap, np.float64))
+    N, d = Js.shape[0], F.shape[0]
+    peb = np.zeros(N)
+    meb = np.zeros((N, max(K, 1)))
+    st = lib.bp_pcrlb_recursion(d, N, K, _dptr(F), _dptr(Q), _dptr(J10), _dptr(Js), _dptr(peb), _dptr(meb),
+                                C.c_void_p(_stream_handle(stream)))
+    _check(lib, None, st, "bp_pcrlb_recursion")
+    return peb, meb[:, :K]
 
 
 NOALLOC_MAX_P = 1 << 20

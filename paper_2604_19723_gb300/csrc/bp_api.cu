@@ -40,7 +40,7 @@ static void mark(bp_handle* h, int stage) {
 
 static int sc_bucket(int S) { return S <= 8 ? 8 : S <= 16 ? 16 : S <= 32 ? 32 : 64; }
 
-static bp_status validate_geom(const bp_geometry* g) {
+bp_status validate_geom(const bp_geometry* g) {
     if (!g || !g->p_pa || !g->R_pa || !g->p_y || !g->p_z) return BP_ERR_INVALID_ARG;
     if (g->J < 1 || g->J > J_MAX || g->Nf < 1 || g->Nf > NF_MAX || g->My < 1 || g->My > MY_MAX || g->Mz < 1 ||
         g->Mz > MZ_MAX || g->Nf * g->My * g->Mz > NZ_MAX)
@@ -49,7 +49,7 @@ static bp_status validate_geom(const bp_geometry* g) {
     return BP_OK;
 }
 
-static void fill_geom(DevGeom& G, const bp_geometry* g) {
+void fill_geom(DevGeom& G, const bp_geometry* g) {
     memset(&G, 0, sizeof(G));
     G.J = g->J; G.Nf = g->Nf; G.My = g->My; G.Mz = g->Mz; G.Nz = g->Nf * g->My * g->Mz;
     G.fc = g->fc; G.c = g->c; G.B = g->B; G.lam = g->c / g->fc;

@@ -69,3 +69,6 @@ void predict_enqueue(bp_handle* h);
 void update_enqueue(bp_handle* h, const float* z_dev);
 void update_finish(bp_handle* h);
 bool dynamic_pf_count(const bp_handle* h);
+// geometry checks and the device copy of its constants (shared with the PCRLB entry points)
+bp_status validate_geom(const bp_geometry* g);
+void fill_geom(bp::DevGeom& G, const bp_geometry* g);

@@ -595,3 +595,136 @@ def test_birth_proposal_weights_are_importance_weights():
             se = (hi[k] - lo[k]) / math.sqrt(12 * max(ess, 1.0))
             m = np.sum(wn * pos[k])
             assert abs(m - 0.5 * (lo[k] + hi[k])) < 6 * se + 0.02 * (hi[k] - lo[k])
+
+
+# ---------------------------------------------------------------- PCRLB (Sec. VI, S-VII)
+def _pcrlb_case(J=2):
+    g = W.make_geometry(J=J, Nf=4, My=2, Mz=2)
+    x = np.array([1.0, 2.0, 0.3, 0.1, 0.2, 0.0])
+    sfvs = np.array([[9.0, 3.0, 0.5], [-5.0, 6.0, 1.0]])
+    r = np.random.default_rng(4)
+    mod = 0.3 + r.random((J, 3))
+    ph = r.uniform(-np.pi, np.pi, 3)          # coherent: one nuisance phase per component
+    phj = r.uniform(-np.pi, np.pi, (J, 3))    # noncoherent: one per component and PA
+    return g, x, sfvs, mod, ph, phj
+
+
+def _mean_model(g, p, sfvs, mod, phases, coherent):
+    """Observation mean of every PA from global parameters: components k with modulus
+    mod[j, k], phase (nuisance + carrier -2 pi |r'| / lambda) and the unit-modulus response
+    at the local delay and angles (the PCRLB model of Sec. S-VII)."""
+    from oracle import pcrlb
+    lam = g.c / g.fc
+    out = []
+    for j in range(g.J):
+        mu = np.zeros(g.Nz, complex)
+        for k in range(len(sfvs) + 1):
+            rp, _ = pcrlb.local_vector(g, j, p, None if k == 0 else sfvs[k - 1], k == 0)
+            d, th, az = pcrlb.spherical(rp)
+            a = pcrlb.response(g, d / g.c, th, az)[0]
+            phi = (phases[k] if coherent else phases[j, k]) - 2 * np.pi * d / lam
+            mu += mod[j, k] * np.exp(1j * phi) * a
+        out.append(mu)
+    return out
+
+
+def _rho_t(g, p, sfvs, mod, phases, coherent):
+    from oracle import pcrlb
+    lam = g.c / g.fc
+    rho = np.zeros((g.J, len(sfvs) + 1), complex)
+    for j in range(g.J):
+        for k in range(len(sfvs) + 1):
+            rp, _ = pcrlb.local_vector(g, j, p, None if k == 0 else sfvs[k - 1], k == 0)
+            d = np.linalg.norm(rp)
+            rho[j, k] = mod[j, k] * np.exp(1j * ((phases[k] if coherent else phases[j, k]) - 2 * np.pi * d / lam))
+    return rho
+
+
+@pytest.mark.parametrize("coherent", [False, True])
+def test_pcrlb_snapshot_fim_equals_finite_difference_fisher(coherent):
+    """J_C assembled from Table S-I and the Jacobians of Sec. S-VII-B equals the Fisher
+    information of the complex Gaussian observation model computed from central finite
+    differences of its mean w.r.t. every global parameter: sum_j (2/eta) Re(G_j^H G_j)
+    plus J Nz / eta^2 for eta (Slepian-Bangs).  A wrong derivative, sign, index or
+    Jacobian block anywhere in the assembly fails it."""
+    from oracle import pcrlb
+    g, x, sfvs, mod, ph, phj = _pcrlb_case()
+    phases = ph if coherent else phj
+    eta = 2e-3
+    K = len(sfvs)
+    dd = pcrlb.dims(K, g.J, coherent)
+    Jfim = pcrlb.snapshot_fim(g, x, sfvs, _rho_t(g, x[:3], sfvs, mod, phases, coherent), eta, coherent)
+
+    def unpack(v):
+        p = v[0:3]
+        s = v[6:6 + 3 * K].reshape(K, 3)
+        phs = v[dd["o_ph"]:dd["o_a"]]
+        phs = phs if coherent else phs.reshape(g.J, K + 1)
+        m = v[dd["o_a"]:dd["o_eta"]].reshape(g.J, K + 1)
+        return p, s, m, phs
+
+    v0 = np.zeros(dd["dim"])
+    v0[0:6] = x
+    v0[6:6 + 3 * K] = sfvs.ravel()
+    v0[dd["o_ph"]:dd["o_a"]] = phases.ravel()
+    v0[dd["o_a"]:dd["o_eta"]] = mod.ravel()
+    v0[dd["o_eta"]] = eta
+    G = [np.zeros((g.Nz, dd["dim"]), complex) for _ in range(g.J)]
+    for i in range(dd["dim"] - 1):
+        h = 1e-6 * max(1.0, abs(v0[i]))
+        vp, vm = v0.copy(), v0.copy()
+        vp[i] += h
+        vm[i] -= h
+        mp = _mean_model(g, *unpack(vp), coherent)
+        mm = _mean_model(g, *unpack(vm), coherent)
+        for j in range(g.J):
+            G[j][:, i] = (mp[j] - mm[j]) / (2 * h)
+    Jnum = sum(2.0 / eta * np.real(Gj.conj().T @ Gj) for Gj in G)
+    Jnum[dd["o_eta"], dd["o_eta"]] = g.J * g.Nz / eta ** 2
+    scale = np.sqrt(np.outer(np.diag(Jnum), np.diag(Jnum))) + 1e-300
+    assert np.max(np.abs(Jfim - Jnum) / scale) < 1e-5
+
+
+def test_pcrlb_recursion_closed_forms():
+    """With no measurement information the posterior covariance follows the prediction
+    P_n = F P_{n-1} F^T + Q; with a static state (F = I, Q = 0) and a constant snapshot FIM
+    the information adds up: J_n = n J_B + J_{1|0}."""
+    from oracle import pcrlb
+    r = np.random.default_rng(2)
+    d = 5
+    A = r.standard_normal((d, d))
+    P0 = A @ A.T + d * np.eye(d)
+    F = np.eye(d) + 0.1 * r.standard_normal((d, d))
+    B = r.standard_normal((d, d))
+    Q = B @ B.T * 0.01 + 1e-3 * np.eye(d)
+    Js = pcrlb.recursion([np.zeros((d, d))] * 4, F, Q, np.linalg.inv(P0))
+    P = P0
+    for n in range(4):
+        assert np.allclose(np.linalg.inv(Js[n]), P, rtol=1e-9, atol=1e-12)
+        P = F @ P @ F.T + Q
+    JB = A @ A.T
+    Js = pcrlb.recursion([JB] * 5, np.eye(d), np.zeros((d, d)), np.linalg.inv(P0))
+    for n in range(5):
+        assert np.allclose(Js[n], (n + 1) * JB + np.linalg.inv(P0), rtol=1e-9)
+
+
+def test_pcrlb_coherent_bound_is_tighter():
+    """The coherent model has K~ nuisance phases instead of K~ J: its position bound is never
+    larger; with a single PA the two models are the same."""
+    from oracle import pcrlb
+    for J in (1, 3):
+        g, x, sfvs, mod, ph, phj = _pcrlb_case(J)
+        eta = 2e-3
+        prm = W.Params(motion_dims=3)
+        out = {}
+        for coherent in (False, True):
+            phases = ph if coherent else np.broadcast_to(ph, (J, 3)).copy()
+            Jc = pcrlb.snapshot_fim(g, x, sfvs, _rho_t(g, x[:3], sfvs, mod, phases, coherent), eta, coherent)
+            dd = pcrlb.dims(len(sfvs), J, coherent)
+            F, Q = pcrlb.transition(prm, len(sfvs), J, coherent, 10.0, 10.0, 10.0)
+            J10 = np.linalg.inv(Q + 1e-2 * np.eye(dd["dim"]))
+            post = pcrlb.recursion([Jc] * 3, F, Q, J10)
+            out[coherent] = pcrlb.bounds(post[-1], len(sfvs))
+        assert out[True][0] <= out[False][0] * (1 + 1e-9)
+        if J == 1:
+            assert out[True][0] == pytest.approx(out[False][0], rel=1e-9)
