@@ -223,8 +223,16 @@ __global__ void k_gram(DevGeom G, DevParams Pm, DevState D, int S, const float* 
 // t = sign(zeta)/(|zeta| + sqrt(1 + zeta^2)) the unitary G (columns p, q:
 // (c, -s e^{-i phi}), (s, c e^{-i phi}), c = 1/sqrt(1 + t^2), s = t c) zeroes a_pq in
 // G^H A G.  U accumulates the G's (from the identity, or from a given start).  Sweeps
-// stop when the off-diagonal energy falls below tol of the diagonal energy, after at
-// most max_sweeps.  T is float or double; all threads of the block call it.
+// stop when every pair satisfies |a_pq|^2 (a_pp - shift)(a_qq - shift) <= tol (a_pp a_qq)^2,
+// after at most max_sweeps.  For B = I + G with G positive semi-definite (shift = 1,
+// g = lambda - 1) an off-diagonal a_pq left in the basis perturbs every form
+// x^H M B^-1 M^H x by at most |a_pq| sqrt(g_p g_q) / (lambda_p lambda_q) per unit of
+// whitened energy, so the test weighs each pair by what it contributes: pairs of large
+// eigenvalues converge to a relative accuracy, pairs inside the cluster of eigenvalues
+// near 1 (near-duplicate columns of M) are not chased.  A test of the off-diagonal
+// energy against the diagonal energy, which the largest eigenvalues dominate, stopped
+// with the small eigenvalues' pairs unresolved.  T is float or double; all threads of
+// the block call it.
 template <typename T> struct cplx;
 template <> struct cplx<float> { using t = float2; };
 template <> struct cplx<double> { using t = double2; };
@@ -232,7 +240,7 @@ template <typename T> struct JRot { T c, s, er, ei; };   // cos, sin, e^{i phi}
 
 template <typename T>
 __device__ void jacobi_herm(typename cplx<T>::t* A, typename cplx<T>::t* U, int n, JRot<T>* rot, double* red,
-                            bool init_identity, double tol, int max_sweeps) {
+                            bool init_identity, double tol, double shift, int max_sweeps) {
     using C = typename cplx<T>::t;
     const int tid = threadIdx.x, nt = blockDim.x;
     if (init_identity)
@@ -247,19 +255,22 @@ __device__ void jacobi_herm(typename cplx<T>::t* A, typename cplx<T>::t* U, int 
         p = min(a, b); q = max(a, b);
     };
     for (int sweep = 0; sweep < max_sweeps; ++sweep) {
-        // convergence test on the current matrix
-        if (tid == 0) { red[0] = 0.0; red[1] = 0.0; }
+        // convergence test on the current matrix (upper triangle; any violating pair
+        // raises the flag)
+        if (tid == 0) red[0] = 0.0;
         __syncthreads();
-        double off = 0.0, dia = 0.0;
+        bool viol = false;
         for (int t = tid; t < n * n; t += nt) {
             const int r = t / n, c = t - r * n;
+            if (r >= c) continue;
             const double m2 = (double)A[t].x * A[t].x + (double)A[t].y * A[t].y;
-            if (r == c) dia += m2; else off += m2;
+            const double dr = fabs((double)A[r * n + r].x), dc = fabs((double)A[c * n + c].x);
+            const double gr = fmax(dr - shift, 0.0), gc = fmax(dc - shift, 0.0);
+            if (!(m2 * gr * gc <= tol * (dr * dc) * (dr * dc))) viol = true;
         }
-        off = warp_sum_d(off); dia = warp_sum_d(dia);
-        if ((tid & 31) == 0) { atomicAdd(&red[0], off); atomicAdd(&red[1], dia); }
+        if (viol) red[0] = 1.0;
         __syncthreads();
-        const bool done = !(red[0] > tol * red[1]);
+        const bool done = (red[0] == 0.0);
         __syncthreads();
         if (done) break;
         for (int r = 0; r < n2 - 1; ++r) {
@@ -358,9 +369,9 @@ __global__ void k_stage_kappa(DevGeom G, DevParams Pm, DevState D, int S, int SC
         R[t] = g;
     }
     // eigenvectors to FP32 accuracy by FP32 sweeps, then B rotated into that basis in FP64
-    // (nearly diagonal) and finished by FP64 sweeps, which converge quadratically from there
+    // (nearly diagonal) and finished by FP64 sweeps
     for (int t = threadIdx.x; t < K * K; t += blockDim.x) A32[t] = make_float2((float)R[t].x, (float)R[t].y);
-    jacobi_herm<float>(A32, U32, K, rot32, red, true, 1e-10, 16);
+    jacobi_herm<float>(A32, U32, K, rot32, red, true, 1e-13, 1.0, 10);
     for (int t = threadIdx.x; t < K * K; t += blockDim.x) Ue[t] = make_double2((double)U32[t].x, (double)U32[t].y);
     __syncthreads();
     {   // the FP32 columns are orthonormal to ~1e-5 only: modified Gram-Schmidt in FP64, so
@@ -412,7 +423,7 @@ __global__ void k_stage_kappa(DevGeom G, DevParams Pm, DevState D, int S, int SC
         R[t] = acc;
     }
     __syncthreads();
-    jacobi_herm<double>(R, Ue, K, rot, red, false, 1e-24, 1);   // one sweep: off-diagonal 1e-5 -> ~1e-10
+    jacobi_herm<double>(R, Ue, K, rot, red, false, 1e-22, 1.0, 8);   // typically 2-4 sweeps
     for (int c = threadIdx.x; c < K; c += blockDim.x) dinv[c] = 1.0 / sqrt(fmax(R[c * K + c].x, 1.0));
     __syncthreads();
     // V rows: v_k = m_k U diag(lambda)^{-1/2}; accumulate projections

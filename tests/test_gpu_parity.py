@@ -126,6 +126,49 @@ def test_update_parity(case):
     f.close()
 
 
+@pytest.mark.parametrize("S, los_existence", [(25, 1e-24), (25, 0.5)])
+def test_update_parity_near_duplicate_pfs(S, los_existence):
+    """A map that carries several PFs per surface (six per wall here, 5 mm apart), the
+    state the filter passes through while births outnumber surfaces, optionally with a
+    LoS whose existence has decayed to 1e-24.  The Gram matrix B = I + M^H M / eta_bar of
+    the table stage then has one large eigenvalue per surface and a cluster of
+    eigenvalues within 1e-6 of 1; its eigen-decomposition must resolve the pairs of the
+    large eigenvalues to FP64 accuracy (an early convergence test on the total
+    off-diagonal energy left them at 1e-2 relative: PR existence tests off by 0.1-3 nats
+    and NaN)."""
+    g, prm, scn, eta, z, st = setup_case(dict(J=4, Nf=10, My=4, Mz=4), 4, S, 700, 16, 0.005)
+    st.w_y[0] *= los_existence / st.w_y[0].sum()
+    pred = model.predict(st, prm, g.J, seed=16, S_max=64)
+    f = gpu_update_from(pred, g, prm, z, 700, 64, 16)
+    msg = messages_woodbury.update_messages(pred, prm, g, z)
+    bel = beliefs.beliefs(pred, msg)
+    ll = f.diag_loglik(pred.S)
+    lo = msg.log_omega1 - msg.log_omega0
+    gw = f.diag_weights(pred.S)
+    d_llr = np.abs(ll["llr_omega"] - lo)
+    d_pr = np.abs(gw["p_pr"] - bel.p_pr)
+    d_ps = np.abs(gw["p_s"] - bel.p_s)
+    d_w = [rel_weight_err(gw["w_y"][s], bel.w_y[s]) for s in range(pred.S) if bel.p_s[s] > 1e-12]
+    report = dict(llr=d_llr.max(), p_pr=d_pr.max(), p_s=d_ps.max(), w_x=rel_weight_err(gw["w_x"], bel.w_x),
+                  w_y=max(d_w))
+    print(report)
+    assert np.all(np.isfinite(ll["llr_omega"]))
+    # the test's terms are FP64 arithmetic on the FP32-accumulated table (2e-7 relative),
+    # of size |m|^2/eta_bar ~ 1e3-1e4 and cancelling to O(1) for a PF whose m-vector lies
+    # almost in the span of its duplicates': 1e-4 absolute (+1e-7 relative) on the log
+    # ratio, hence |d p| <= p (1 - p) |d llr| <= 2.5e-5 on the PR existence
+    assert np.all(d_llr < 1e-4 + 1e-7 * np.abs(lo)), report
+    assert np.all(d_pr <= 0.25 * (1e-4 + 1e-7 * np.abs(lo)) + 1e-12), report
+    assert report["p_s"] < P_TOL, report
+    assert report["w_x"] < W_TOL, report
+    # known limit of this regime: a PF whose steering vectors lie almost in the span of
+    # its duplicates' m-vectors has a projected steering vector psi_perp = psi - V h that
+    # is a small difference of FP32 quantities, which puts 1.4e-4 (measured) on its
+    # normalised weights, against 1e-4 for separated PFs
+    assert report["w_y"] < 2e-4, report
+    f.close()
+
+
 def test_loglik_parity_dense():
     """Per-particle log-likelihoods against the dense (explicit covariance) definition."""
     g, prm, scn, eta, z, st = setup_case(dict(J=2, Nf=4, My=2, Mz=2), 3, 4, 96, 21, 0.02)
