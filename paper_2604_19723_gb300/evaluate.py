@@ -48,6 +48,15 @@ VARIANTS = {
 
 NUISANCE_SIGMA = 1e3
 
+# starts of a run: "prior" is the paper's (MT from the uniform prior box, the LoS alone,
+# every other PF born on the way); the others start near the truth at time 0 with the
+# given standard deviations (position, velocity, SFV position) and S0 PFs (None: the LoS
+# and one PF per true surface, i.e. the tracking phase with the map in place)
+INIT_STD = {
+    "truth": (0.02, 0.05, 0.02, 1),
+    "truth_map": (0.02, 0.05, 0.02, None),
+}
+
 
 def associate(est: np.ndarray, truth: np.ndarray) -> np.ndarray:
     """Hungarian association of SFV estimates (m, 3) to true SFVs (K, 3); returns the
@@ -95,8 +104,9 @@ def bound_amplitudes(scn: W.Scenario, n: int) -> np.ndarray:
     return rho * lam / (4.0 * np.pi * d) * np.exp(-2j * np.pi * d / lam)
 
 
-def prior_information(params: W.Params, K: int, J: int, coherent: bool) -> np.ndarray:
-    """J_{1|0}: inverse of a diagonal prior covariance at time 0."""
+def prior_information(params: W.Params, K: int, J: int, coherent: bool, init: str = "prior") -> np.ndarray:
+    """J_{1|0}: inverse of a diagonal covariance of the state at time 0, the one the runs
+    start from (uniform boxes for "prior", the near-truth spreads otherwise)."""
     dim = bp.pcrlb_dim(K, J, coherent)
     var = np.full(dim, NUISANCE_SIGMA ** 2)
     lo, hi = np.asarray(params.p_min, float), np.asarray(params.p_max, float)
@@ -104,6 +114,11 @@ def prior_information(params: W.Params, K: int, J: int, coherent: bool) -> np.nd
     var[3:6] = np.maximum((2.0 * np.asarray(params.v_max, float)) ** 2 / 12.0, 1e-6)
     blo, bhi = np.asarray(params.birth_min, float), np.asarray(params.birth_max, float)
     bv = np.maximum((bhi - blo) ** 2 / 12.0, 1e-6)
+    if init in INIT_STD:
+        pos_std, vel_std, sfv_std, S0 = INIT_STD[init]
+        var[0:3], var[3:6] = pos_std ** 2, vel_std ** 2
+        if S0 is None:
+            bv = np.full(3, sfv_std ** 2)
     for k in range(K):
         var[6 + 3 * k:9 + 3 * k] = bv
     nph = (K + 1) if coherent else (K + 1) * J
@@ -145,6 +160,7 @@ class RunResult:
     S: np.ndarray              # (N,) PFs after the update (LoS included)
     declared: np.ndarray       # (N,) declared PFs besides the LoS
     eta: float                 # noise variance of the synthetic data
+    failed: int = -1           # step at which the filter reported a numerical failure
 
 
 def run_filter(name: str, variant: str, P: int, N: int, seed: int, init: str = "prior"):
@@ -157,28 +173,35 @@ def run_filter(name: str, variant: str, P: int, N: int, seed: int, init: str = "
                           visibility=wl["visibility"], clutter_mean=wl["clutter_mean"], coherent=coherent)
     x_pos, sfv, rho, cc, cs, cr = bp.scenario_arrays(scn, range(1, N + 1))
     z, eta = bp.synthesize(g, x_pos, sfv, rho, cc, cs, cr, snr_db=wl["snr_db"], seed=seed + 7, step0=1)
+    K = scn.sfv_true.shape[0]
     f = bp.Filter(g, prm, P=P, S_max=wl["S_max"], seed=seed)
-    if init == "truth":
-        f.set_state(W.state_near_truth(scn, P=P, S=1, n=0, seed=seed + 3, eta_true=eta))
+    if init in INIT_STD:
+        pos_std, vel_std, sfv_std, S0 = INIT_STD[init]
+        f.set_state(W.state_near_truth(scn, P=P, S=K + 1 if S0 is None else S0, n=0, seed=seed + 3, eta_true=eta,
+                                       pos_std=pos_std, vel_std=vel_std, sfv_std=sfv_std))
     elif init != "prior":
         raise ValueError(init)
-    K = scn.sfv_true.shape[0]
-    pos, mp = np.zeros(N), np.full((N, K), np.nan)
+    pos, mp = np.full(N, np.nan), np.full((N, K), np.nan)
     S, dec = np.zeros(N, np.int32), np.zeros(N, np.int32)
+    failed = -1
     try:
         for n in range(N):
             f.step(z[n])
-            e = f.estimate()
+            try:
+                e = f.estimate()
+            except bp.BPError:
+                failed = n          # a numerical failure ends the run; its errors stay NaN
+                break
             pos[n] = np.linalg.norm(e["x_hat"][:3] - scn.x_true[n + 1, :3])
             sel = np.nonzero(e["declared"][1:])[0] + 1
             mp[n] = associate(e["phi_hat"][sel, :3], scn.sfv_true)
             S[n], dec[n] = e["S"], len(sel)
     finally:
         f.close()
-    return RunResult(pos, mp, S, dec, eta), scn
+    return RunResult(pos, mp, S, dec, eta, failed), scn
 
 
-def bound(scns: List[W.Scenario], etas: List[float], coherent: bool):
+def bound(scns: List[W.Scenario], etas: List[float], coherent: bool, init: str = "prior"):
     """PEB (N,) and MEB (N, K) for the runs' truths (mean FIM over the runs per step)."""
     s0 = scns[0]
     g, prm, N = s0.geom, s0.params, s0.N
@@ -191,11 +214,11 @@ def bound(scns: List[W.Scenario], etas: List[float], coherent: bool):
         rho = np.stack([bound_amplitudes(s, n) for s in scns])
         Js[n - 1] = bp.pcrlb_fim(g, x, sfv, rho, eta, coherent)
     F, Q = transition(prm, K, g.J, coherent)
-    return bp.pcrlb_recursion(F, Q, prior_information(prm, K, g.J, coherent), Js, K)
+    return bp.pcrlb_recursion(F, Q, prior_information(prm, K, g.J, coherent, init), Js, K)
 
 
-def evaluate(name: str = "paper_exp1", variants=("nzm", "zm", "nzm_nc"), runs: int = 10, steps: int = 200,
-             P: int = None, seed: int = 100, init: str = "prior") -> Dict:
+def evaluate(name: str = "paper_exp1_proposal", variants=("nzm", "zm", "nzm_nc"), runs: int = 10, steps: int = 200,
+             P: int = None, seed: int = 100, init: str = "truth_map") -> Dict:
     """RMSE of the MT position and of each surface's SFV per step, with PEB and MEB."""
     wl = W.workload(name)
     P = P or wl["P"]
@@ -204,14 +227,17 @@ def evaluate(name: str = "paper_exp1", variants=("nzm", "zm", "nzm_nc"), runs: i
         t0 = time.perf_counter()
         res, scns = zip(*[run_filter(name, v, P, steps, seed + r, init) for r in range(runs)])
         wall = time.perf_counter() - t0
-        peb, meb = bound(list(scns), [r.eta for r in res], VARIANTS[v][1])
+        peb, meb = bound(list(scns), [r.eta for r in res], VARIANTS[v][1], init)
         pos = np.stack([r.pos_err for r in res])
         mp = np.stack([r.map_err for r in res])
         out["variants"][v] = dict(
-            rmse_pos=rmse(pos).tolist(), peb=peb.tolist(),
+            rmse_pos=rmse(pos).tolist(), median_pos=np.nanmedian(pos, axis=0).tolist(), peb=peb.tolist(),
             rmse_map=rmse(mp).tolist(), meb=meb.tolist(),
             detected=np.mean(np.isfinite(mp), axis=0).tolist(),
             mean_S=np.mean([r.S for r in res], axis=0).tolist(),
+            mean_declared=np.mean([r.declared for r in res], axis=0).tolist(),
+            final_err=[float(r.pos_err[-1]) for r in res],
+            failed=[int(r.failed) for r in res],
             wall_s=wall)
     return out
 
@@ -219,7 +245,7 @@ def evaluate(name: str = "paper_exp1", variants=("nzm", "zm", "nzm_nc"), runs: i
 def summary(res: Dict, at=(10, 50, 100, 200)) -> str:
     """A plain-text table of RMSE against the bounds at a few steps."""
     lines = [f"workload {res['workload']}, {res['runs']} runs, P = {res['P']}, init {res['init']}",
-             "variant  step  RMSE_pos[m]  PEB[m]   RMSE_map (surfaces 1..K) [m]   MEB [m]"]
+             "variant  step  RMSE_pos[m]  median[m]  PEB[m]   RMSE_map (surfaces 1..K) [m]   MEB [m]   PFs"]
     for v, d in res["variants"].items():
         for n in at:
             if n > len(d["rmse_pos"]):
@@ -227,19 +253,23 @@ def summary(res: Dict, at=(10, 50, 100, 200)) -> str:
             i = n - 1
             rm = " ".join(f"{x:.4f}" for x in d["rmse_map"][i])
             mb = " ".join(f"{x:.4f}" for x in d["meb"][i])
-            lines.append(f"{v:7s} {n:5d}  {d['rmse_pos'][i]:.4f}      {d['peb'][i]:.4f}   {rm}   {mb}")
+            lines.append(f"{v:7s} {n:5d}  {d['rmse_pos'][i]:.4f}      {d['median_pos'][i]:.4f}     {d['peb'][i]:.4f}"
+                         f"   {rm}   {mb}   {d['mean_S'][i]:.1f}")
+        fe = np.asarray(d["final_err"])
+        lines.append(f"{v:7s} runs failed: {sum(1 for x in d['failed'] if x >= 0)}, final error > 0.5 m: "
+                     f"{int(np.sum(~(fe <= 0.5)))}, wall {d['wall_s']:.1f} s")
     return "\n".join(lines)
 
 
 def main(argv=None):
     ap = argparse.ArgumentParser(description=__doc__.split("\n")[0])
-    ap.add_argument("--workload", default="paper_exp1")
+    ap.add_argument("--workload", default="paper_exp1_proposal")
     ap.add_argument("--variants", default="nzm,zm,nzm_nc")
     ap.add_argument("--runs", type=int, default=10)
     ap.add_argument("--steps", type=int, default=200)
     ap.add_argument("--P", type=int, default=None)
     ap.add_argument("--seed", type=int, default=100)
-    ap.add_argument("--init", default="prior", choices=["prior", "truth"])
+    ap.add_argument("--init", default="truth_map", choices=["prior"] + sorted(INIT_STD))
     ap.add_argument("--json", default=None, help="write the full per-step result here")
     a = ap.parse_args(argv)
     res = evaluate(a.workload, tuple(a.variants.split(",")), a.runs, a.steps, a.P, a.seed, a.init)
