@@ -352,6 +352,48 @@ bp_status bp_batch_free(bp_batch* b);
 /* Text of the last error on b (of the last bp_batch_init failure if b is NULL). */
 const char* bp_batch_last_error(const bp_batch* b);
 
+/* ------------------------------------------------------------------ proposal network
+ * The network of the learned MT proposal (no counterpart in the paper, whose
+ * proposal is the state-transition PDF): a perceptron 16 -> 64 -> 64 -> 16 with ReLU
+ * after both hidden layers, BF16 weights, inputs and activations, FP32 accumulation on
+ * the tensor cores.  Outputs y[0:3] = mean and y[3:6] = log standard deviation of a
+ * Gaussian over a 3-vector (the remaining 10 outputs are unused); training minimises
+ * the mean Gaussian negative log-likelihood of targets t (B x 3):
+ *   L = (1/B) sum_i sum_a [ (t_ia - y_ia)^2 exp(-2 y_i,3+a) / 2 + y_i,3+a ].
+ * Parameters (FP32 master copy, BP_MLP_NPARAM floats, in this order): W1 (64 x 16,
+ * row = output unit), b1 (64), W2 (64 x 64), b2 (64), W3 (16 x 64), b3 (16).
+ * The handle owns its parameters and Adam moments (beta1 0.9, beta2 0.999, eps 1e-8);
+ * X (B x 16), T (B x 3), Y (B x 16) are FP32 device arrays, row-major.  Calls run on
+ * the handle's stream.  Errors: BP_ERR_INVALID_ARG for NULL or out-of-range
+ * arguments, BP_ERR_CUDA for allocation or launch failures, BP_ERR_TIMEOUT when a
+ * bounded tensor-core wait gave up (results invalid). */
+enum { BP_MLP_IN = 16, BP_MLP_HIDDEN = 64, BP_MLP_OUT = 16, BP_MLP_NPARAM = 6288 };
+typedef struct bp_mlp bp_mlp;
+
+/* Copies the initial parameters (host, BP_MLP_NPARAM floats) to the device; Adam
+ * moments start at zero.  Synchronous. */
+bp_status bp_mlp_create(const float* params_host, void* cuda_stream, bp_mlp** out);
+
+/* The current parameters to host memory.  Synchronous. */
+bp_status bp_mlp_get_params(bp_mlp* h, float* params_host);
+
+/* Y = network(X) for B rows.  Synchronous (checks the tensor-core status). */
+bp_status bp_mlp_forward(bp_mlp* h, const float* X_dev, int B, float* Y_dev);
+
+/* Gradient of L with respect to every parameter (grad_dev: BP_MLP_NPARAM floats,
+ * device) and B L (loss_dev: one float, device, may be NULL), parameters unchanged.
+ * Synchronous. */
+bp_status bp_mlp_grads(bp_mlp* h, const float* X_dev, const float* T_dev, int B, float* grad_dev, float* loss_dev);
+
+/* One Adam step with learning rate lr on the gradient of L over this batch; loss_dev
+ * (device, may be NULL) receives B L before the step.  Asynchronous: bp_mlp_sync
+ * waits and reports a tensor-core timeout of any step since the last check. */
+bp_status bp_mlp_train_step(bp_mlp* h, const float* X_dev, const float* T_dev, int B, float lr, float* loss_dev);
+bp_status bp_mlp_sync(bp_mlp* h);
+
+bp_status bp_mlp_free(bp_mlp* h);
+const char* bp_mlp_last_error(const bp_mlp* h);
+
 #ifdef __cplusplus
 }
 #endif

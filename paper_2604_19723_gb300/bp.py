@@ -27,7 +27,9 @@ ENTRY_POINTS = ("bp_init", "bp_predict", "bp_update", "bp_estimate", "bp_free", 
                 "bp_synthesize", "bp_launch_count", "bp_set_profiling", "bp_get_profile",
                 "bp_resample_noalloc", "bp_batch_init", "bp_batch_step", "bp_batch_z_offset", "bp_batch_z_floats",
                 "bp_batch_sync", "bp_batch_handle", "bp_batch_stream_of", "bp_batch_device_bytes", "bp_batch_free",
-                "bp_batch_last_error", "bp_pcrlb_fim", "bp_pcrlb_recursion")
+                "bp_batch_last_error", "bp_pcrlb_fim", "bp_pcrlb_recursion",
+                "bp_mlp_create", "bp_mlp_get_params", "bp_mlp_forward", "bp_mlp_grads", "bp_mlp_train_step",
+                "bp_mlp_sync", "bp_mlp_free", "bp_mlp_last_error")
 PROFILE_STAGES = ("predict", "row_sums", "table", "stage", "kappa", "iota", "nu", "normalize", "resample")
 
 
@@ -129,8 +131,17 @@ def load() -> C.CDLL:
     lib.bp_pcrlb_fim.argtypes = [C.POINTER(_Geometry), C.c_int, C.c_int, C.c_int, C.POINTER(C.c_double),
                                  C.POINTER(C.c_double), C.POINTER(C.c_double), C.c_double, C.POINTER(C.c_double), vp]
     lib.bp_pcrlb_recursion.argtypes = [C.c_int, C.c_int, C.c_int] + [C.POINTER(C.c_double)] * 6 + [vp]
+    lib.bp_mlp_create.argtypes = [C.POINTER(C.c_float), vp, C.POINTER(vp)]
+    lib.bp_mlp_get_params.argtypes = [vp, C.POINTER(C.c_float)]
+    lib.bp_mlp_forward.argtypes = [vp, vp, C.c_int, vp]
+    lib.bp_mlp_grads.argtypes = [vp, vp, vp, C.c_int, vp, vp]
+    lib.bp_mlp_train_step.argtypes = [vp, vp, vp, C.c_int, C.c_float, vp]
+    lib.bp_mlp_sync.argtypes = [vp]
+    lib.bp_mlp_free.argtypes = [vp]
+    lib.bp_mlp_last_error.argtypes = [vp]
+    lib.bp_mlp_last_error.restype = C.c_char_p
     untyped = ("bp_last_error", "bp_launch_count", "bp_batch_z_offset", "bp_batch_z_floats",
-               "bp_batch_device_bytes", "bp_batch_last_error")
+               "bp_batch_device_bytes", "bp_batch_last_error", "bp_mlp_last_error")
     for f in ENTRY_POINTS:
         if f not in untyped:
             getattr(lib, f).restype = C.c_int
@@ -473,6 +484,72 @@ def pcrlb_recursion(F, Q, J10, Jsnap, K: int, stream=None):
                                 C.c_void_p(_stream_handle(stream)))
     _check(lib, None, st, "bp_pcrlb_recursion")
     return peb, meb[:, :K]
+
+
+MLP_IN, MLP_HIDDEN, MLP_OUT, MLP_NPARAM = 16, 64, 16, 6288
+
+
+class Mlp:
+    """The proposal network on the GPU (bp_mlp_*): BF16 tensor-core forward, backward
+    and Adam.  X (B x 16), T (B x 3) are torch CUDA float32 tensors."""
+
+    def __init__(self, params: np.ndarray, stream=None):
+        self.lib = load()
+        p = np.ascontiguousarray(params, np.float32)
+        assert p.size == MLP_NPARAM
+        h = C.c_void_p()
+        st = self.lib.bp_mlp_create(_fptr(p), C.c_void_p(_stream_handle(stream)), C.byref(h))
+        self._check(st, "bp_mlp_create", None)
+        self.h = h
+
+    def _check(self, st, what, h="self"):
+        if st != BP_OK:
+            hh = self.h if h == "self" else h
+            msg = self.lib.bp_mlp_last_error(hh) if hh else b""
+            raise BPError(st, f"{what}: {msg.decode() if msg else ''}")
+
+    def params(self) -> np.ndarray:
+        out = np.zeros(MLP_NPARAM, np.float32)
+        self._check(self.lib.bp_mlp_get_params(self.h, _fptr(out)), "bp_mlp_get_params")
+        return out
+
+    def forward(self, X):
+        import torch
+        X = X.contiguous()
+        Y = torch.empty((X.shape[0], MLP_OUT), dtype=torch.float32, device=X.device)
+        self._check(self.lib.bp_mlp_forward(self.h, C.c_void_p(X.data_ptr()), X.shape[0], C.c_void_p(Y.data_ptr())),
+                    "bp_mlp_forward")
+        return Y
+
+    def grads(self, X, T):
+        """(gradient of the mean loss, summed loss) without changing the parameters."""
+        import torch
+        X, T = X.contiguous(), T.contiguous()
+        g = torch.empty(MLP_NPARAM, dtype=torch.float32, device=X.device)
+        l = torch.empty(1, dtype=torch.float32, device=X.device)
+        self._check(self.lib.bp_mlp_grads(self.h, C.c_void_p(X.data_ptr()), C.c_void_p(T.data_ptr()), X.shape[0],
+                                          C.c_void_p(g.data_ptr()), C.c_void_p(l.data_ptr())), "bp_mlp_grads")
+        return g.cpu().numpy(), float(l.item())
+
+    def train_step(self, X, T, lr: float, loss_out=None):
+        self._check(self.lib.bp_mlp_train_step(self.h, C.c_void_p(X.data_ptr()), C.c_void_p(T.data_ptr()),
+                                               X.shape[0], C.c_float(lr),
+                                               C.c_void_p(loss_out.data_ptr() if loss_out is not None else None)),
+                    "bp_mlp_train_step")
+
+    def sync(self):
+        self._check(self.lib.bp_mlp_sync(self.h), "bp_mlp_sync")
+
+    def close(self):
+        if getattr(self, "h", None):
+            self.lib.bp_mlp_free(self.h)
+            self.h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
 
 
 NOALLOC_MAX_P = 1 << 20

@@ -1,6 +1,6 @@
 // Inline-PTX building blocks for the fifth-generation tensor cores (tcgen05) and
 // the bulk-copy engine of sm_100-class GPUs: shared-memory matrix descriptors,
-// the TF32 instruction descriptor, tensor-memory (TMEM) allocation, MMA issue and
+// the TF32 and BF16 instruction descriptors, tensor-memory (TMEM) allocation, MMA issue and
 // commit, bounded mbarrier waits, bulk global->shared copies and TMEM loads.
 //
 // Operand layout used throughout: K-major, no swizzle.  A tile of R rows x Kt
@@ -39,6 +39,19 @@ __host__ __device__ constexpr uint32_t idesc_tf32_f32(int m, int n) {
     return (1u << 4) | (2u << 7) | (2u << 10) | ((uint32_t)(n >> 3) << 17) | ((uint32_t)(m >> 4) << 24);
 }
 
+// instruction descriptor of kind::f16 with BF16 A and B (the same type for both) and
+// an F32 accumulator, both operands K-major, dense: A/B format code 1 = BF16
+__host__ __device__ constexpr uint32_t idesc_bf16_f32(int m, int n) {
+    return (1u << 4) | (1u << 7) | (1u << 10) | ((uint32_t)(n >> 3) << 17) | ((uint32_t)(m >> 4) << 24);
+}
+
+// byte offset of element (r, k) of a tile of R rows x Kt 2-byte elements, K-major, no
+// swizzle: core matrices of 8 rows x 16 bytes (8 x 8 elements), LBO = 128 B along K,
+// SBO = (Kt/8) * 128 B between groups of 8 rows
+__host__ __device__ inline int core_off16(int r, int k, int Kt) {
+    return (r >> 3) * (Kt >> 3) * 128 + (k >> 3) * 128 + (r & 7) * 16 + (k & 7) * 2;
+}
+
 // round to TF32 (10 explicit mantissa bits), nearest with ties away from zero
 __device__ __forceinline__ float tf32_rn(float x) {
     uint32_t r;
@@ -59,6 +72,12 @@ __device__ __forceinline__ void tmem_dealloc(uint32_t taddr, uint32_t ncols) {
 __device__ __forceinline__ void mma_tf32(uint32_t d_tmem, uint64_t a_desc, uint64_t b_desc, uint32_t idesc, bool acc) {
     asm volatile("{\n\t.reg .pred p;\n\tsetp.ne.b32 p, %4, 0;\n\t"
                  "tcgen05.mma.cta_group::1.kind::tf32 [%0], %1, %2, %3, p;\n\t}"
+                 :: "r"(d_tmem), "l"(a_desc), "l"(b_desc), "r"(idesc), "r"(acc ? 1u : 0u));
+}
+// D (+)= A B^T, BF16 operands (K = 16 per instruction), F32 accumulator
+__device__ __forceinline__ void mma_bf16(uint32_t d_tmem, uint64_t a_desc, uint64_t b_desc, uint32_t idesc, bool acc) {
+    asm volatile("{\n\t.reg .pred p;\n\tsetp.ne.b32 p, %4, 0;\n\t"
+                 "tcgen05.mma.cta_group::1.kind::f16 [%0], %1, %2, %3, p;\n\t}"
                  :: "r"(d_tmem), "l"(a_desc), "l"(b_desc), "r"(idesc), "r"(acc ? 1u : 0u));
 }
 // arrive on the mbarrier once every MMA issued so far by this thread has completed

@@ -409,3 +409,20 @@ def state_from_prior(params: Params, J: int, P: int, S: int, seed: int) -> State
                        eta=eta.astype(np.float32), w_x=np.full(P, 1.0 / P),
                        w_y=np.full((S, P), 0.5 / P), w_eta=np.full((J, P), 1.0 / P),
                        p_pr=np.full((S, J), params.pB_pr))
+
+
+# --------------------------------------------------------------------------
+# proposal network: initial parameters (random inputs of training)
+# --------------------------------------------------------------------------
+def mlp_init(seed: int, out_scale: float = 0.1) -> np.ndarray:
+    """Initial parameters of the 16-64-64-16 proposal network, packed W1, b1, W2, b2,
+    W3, b3: He-uniform weights for the ReLU layers, the output layer scaled down by
+    out_scale, zero biases.  FP32."""
+    rng = np.random.default_rng(seed)
+    parts = []
+    for fan_in, fan_out, scale in ((16, 64, 1.0), (64, 64, 1.0), (64, 16, out_scale)):
+        lim = scale * np.sqrt(6.0 / fan_in)
+        parts.append(rng.uniform(-lim, lim, size=(fan_out, fan_in)).reshape(-1))
+        parts.append(np.zeros(fan_out))
+    return np.concatenate(parts).astype(np.float32)
+
