@@ -186,8 +186,13 @@ bp_status bp_set_predicted(bp_handle* h, const bp_state_view* in);
  *        i*, sum of costs, mu [3], C [3x3], L [3x3], 0-padded), the Bartlett costs
  *        [Qe][Ng] and candidates [Qe][Ng][3] (double), the prediction weights
  *        w_alpha [Qe][P] (double), then the new PFs' particle positions [Qe][3][P]
- *        (float).  BP_ERR_STATE without a proposal in the last update. */
-enum { BP_DIAG_TABLE = 1, BP_DIAG_WEIGHTS = 2, BP_DIAG_LOGLIK = 3, BP_DIAG_INDICES = 4, BP_DIAG_PROPOSAL = 5 };
+ *        (float).  BP_ERR_STATE without a proposal in the last update.
+ * what = BP_DIAG_LPROP (a proposal network attached): the predicted mean xbar (6) and
+ *        the per-PA correlations (Re, Im of psi_j(xbar)^H z_j, |z_j|^2, |psi_j|^2) for
+ *        J PAs (double), the log importance ratios (P, double), the network inputs and
+ *        outputs (P x 16 each, float).  BP_ERR_STATE without a network. */
+enum { BP_DIAG_TABLE = 1, BP_DIAG_WEIGHTS = 2, BP_DIAG_LOGLIK = 3, BP_DIAG_INDICES = 4, BP_DIAG_PROPOSAL = 5,
+       BP_DIAG_LPROP = 6 };
 bp_status bp_get_diag(bp_handle* h, int what, void* host, size_t bytes);
 
 /* Synthetic observations from the generative model (eq. observation-generative),
@@ -393,6 +398,34 @@ bp_status bp_mlp_sync(bp_mlp* h);
 
 bp_status bp_mlp_free(bp_mlp* h);
 const char* bp_mlp_last_error(const bp_mlp* h);
+
+/* ------------------------------------------------------------------ learned MT proposal
+ * Attaches a proposal network to a filter (NULL detaches; the caller keeps the network
+ * alive while attached).  With a network attached, every bp_update first redraws the
+ * NCV process noise of each MT particle from N(mu, diag s^2) in units of sigma_v, with
+ * (mu, log s) = the network's outputs (log s clamped to [-4, 1]) for the input row
+ *   [(F x_{n-1} - xbar)_pos / 0.01 m, (F x_{n-1} - xbar)_vel / 0.1 m/s,
+ *    xbar_pos in ROI units (3), Re, Im of rho_j conj(rho_0) / |rho_0| for j = 1..3 (6), |rho_0|],
+ * xbar the weighted mean of the predicted particles and rho_j the normalised correlation
+ * psi_j(xbar)^H z_j / (|psi_j| |z_j|) of the LoS steering vector with z_j, and multiplies
+ * each prediction weight by N(u; 0, I) / N(u; mu, s^2) before normalising them (the
+ * importance ratio of the transition to the proposal, which keeps the posterior exact).
+ * Random draws: Philox purpose 15.  At most 4 PAs; not on handles of a batch
+ * (BP_ERR_STATE).  Diagnostics: BP_DIAG_LPROP. */
+bp_status bp_set_mt_proposal(bp_handle* h, bp_mlp* net);
+
+/* Training samples of the proposal network simulated from the model on the GPU (n rows
+ * of X (n x 16) and targets T (n x 3), device FP32): a previous true state uniform in
+ * the ROI of prm (velocity uniform within +-v_max), its NCV successor, a previous
+ * posterior mean with errors N(0, err_pos^2) / N(0, err_vel^2) and a particle around it
+ * with spreads spread_pos / spread_vel, the observation of the successor (LoS and the K
+ * surfaces sfv (K x 3, host) with moduli rho_abs (K + 1, host, LoS first), phases common
+ * to all PAs and uniform, complex Gaussian noise of variance eta), the input row at the
+ * predicted mean as above, and the target u that carries the particle's F x_{n-1} to the
+ * true successor (least squares through Gamma).  0 <= K <= 8, J <= 4.  Synchronous. */
+bp_status bp_lp_dataset(const bp_geometry* geom, const bp_params* prm, int K, const double* sfv, const double* rho_abs,
+                        double eta, double err_pos, double err_vel, double spread_pos, double spread_vel, int n,
+                        uint64_t seed, float* X_dev, float* T_dev, void* cuda_stream);
 
 #ifdef __cplusplus
 }

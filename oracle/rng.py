@@ -40,6 +40,8 @@ INIT_ETA = 11
 SYNTH_NOISE = 12
 BIRTH_CAND = 13      # candidate SFV positions of the birth proposal (item = candidate index, sub = partition)
 BIRTH_PROP = 14      # normals of particles drawn from the birth proposal (sub = PF slot)
+LEARNED_PROP = 15    # normals of the learned MT proposal (item = particle)
+LP_DATA = 16         # draws of the proposal network's training samples
 
 MAX_GAMMA_ATTEMPTS = 16
 

@@ -20,7 +20,7 @@ LIB_PATH = os.path.join(_HERE, "_lib", "libbp.so")
 BP_OK = 0
 STATUS = {0: "BP_OK", 1: "BP_ERR_INVALID_ARG", 2: "BP_ERR_CUDA", 3: "BP_ERR_CAPACITY",
           4: "BP_ERR_NUMERIC", 5: "BP_ERR_TIMEOUT", 6: "BP_ERR_STATE"}
-DIAG_TABLE, DIAG_WEIGHTS, DIAG_LOGLIK, DIAG_INDICES, DIAG_PROPOSAL = 1, 2, 3, 4, 5
+DIAG_TABLE, DIAG_WEIGHTS, DIAG_LOGLIK, DIAG_INDICES, DIAG_PROPOSAL, DIAG_LPROP = 1, 2, 3, 4, 5, 6
 
 ENTRY_POINTS = ("bp_init", "bp_predict", "bp_update", "bp_estimate", "bp_free", "bp_last_error",
                 "bp_get_state", "bp_set_state", "bp_get_predicted", "bp_set_predicted", "bp_get_diag",
@@ -29,7 +29,7 @@ ENTRY_POINTS = ("bp_init", "bp_predict", "bp_update", "bp_estimate", "bp_free", 
                 "bp_batch_sync", "bp_batch_handle", "bp_batch_stream_of", "bp_batch_device_bytes", "bp_batch_free",
                 "bp_batch_last_error", "bp_pcrlb_fim", "bp_pcrlb_recursion",
                 "bp_mlp_create", "bp_mlp_get_params", "bp_mlp_forward", "bp_mlp_grads", "bp_mlp_train_step",
-                "bp_mlp_sync", "bp_mlp_free", "bp_mlp_last_error")
+                "bp_mlp_sync", "bp_mlp_free", "bp_mlp_last_error", "bp_set_mt_proposal", "bp_lp_dataset")
 PROFILE_STAGES = ("predict", "row_sums", "table", "stage", "kappa", "iota", "nu", "normalize", "resample")
 
 
@@ -140,6 +140,9 @@ def load() -> C.CDLL:
     lib.bp_mlp_free.argtypes = [vp]
     lib.bp_mlp_last_error.argtypes = [vp]
     lib.bp_mlp_last_error.restype = C.c_char_p
+    lib.bp_set_mt_proposal.argtypes = [vp, vp]
+    lib.bp_lp_dataset.argtypes = [C.POINTER(_Geometry), C.POINTER(_Params), C.c_int, C.POINTER(C.c_double),
+                                  C.POINTER(C.c_double)] + [C.c_double] * 5 + [C.c_int, C.c_uint64, vp, vp, vp]
     untyped = ("bp_last_error", "bp_launch_count", "bp_batch_z_offset", "bp_batch_z_floats",
                "bp_batch_device_bytes", "bp_batch_last_error", "bp_mlp_last_error")
     for f in ENTRY_POINTS:
@@ -332,6 +335,26 @@ class Filter:
         ln = b[o:o + J * P].reshape(J, P); o += J * P
         lw = b[o:o + S * J].reshape(S, J)
         return dict(log_iota=li, delta_kappa=lk, log_nu=ln, llr_omega=lw)
+
+    def set_mt_proposal(self, net):
+        """Attach a proposal network (Mlp) to this filter, or detach it (None)."""
+        self._lp_net = net
+        _check(self.lib, self.h, self.lib.bp_set_mt_proposal(self.h, net.h if net is not None else None),
+               "bp_set_mt_proposal")
+
+    def diag_lproposal(self) -> Dict:
+        """The learned MT proposal of the last update: predicted mean, per-PA correlations,
+        log importance ratios, network inputs and outputs."""
+        J, P = self.geom.J, self.P
+        nd = 6 + 4 * J + P
+        nbytes = nd * 8 + 2 * P * 16 * 4
+        buf = np.zeros(nbytes, np.uint8)
+        _check(self.lib, self.h, self.lib.bp_get_diag(self.h, DIAG_LPROP, buf.ctypes.data_as(C.c_void_p), nbytes),
+               "bp_get_diag")
+        d = buf[:nd * 8].view(np.float64)
+        f = buf[nd * 8:].view(np.float32)
+        return dict(xbar=d[:6].copy(), cor=d[6:6 + 4 * J].reshape(J, 4).copy(), logr=d[6 + 4 * J:].copy(),
+                    X=f[:P * 16].reshape(P, 16).copy(), Y=f[P * 16:].reshape(P, 16).copy())
 
     def diag_proposal(self, Qe: int) -> Dict:
         """Birth proposal of the last update's Qe new PFs: statistics, Bartlett costs,
@@ -568,6 +591,26 @@ def resample_noalloc(w, seed: int, n: int, kind: int, index: int, out=None, stre
     if st != BP_OK:
         raise BPError(st, "bp_resample_noalloc" + (f": P = {P} exceeds {NOALLOC_MAX_P}" if st == 3 else ""))
     return out
+
+
+def lp_dataset(geom: Geometry, params: Params, sfv: np.ndarray, rho_abs: np.ndarray, eta: float, n: int, seed: int,
+               err_pos: float = 0.002, err_vel: float = 0.02, spread_pos: float = 0.003, spread_vel: float = 0.03,
+               stream=None):
+    """Training samples of the proposal network (bp_lp_dataset): torch CUDA tensors
+    X (n x 16) and T (n x 3)."""
+    import torch
+    lib = load()
+    g = _GeomHolder(geom)
+    pr = _params_struct(params)
+    sf = np.ascontiguousarray(np.asarray(sfv, np.float64).reshape(-1, 3))
+    ra = np.ascontiguousarray(np.asarray(rho_abs, np.float64))
+    X = torch.empty((n, MLP_IN), dtype=torch.float32, device="cuda")
+    T = torch.empty((n, 3), dtype=torch.float32, device="cuda")
+    st = lib.bp_lp_dataset(C.byref(g.s), C.byref(pr), sf.shape[0], _dptr(sf) if sf.size else None, _dptr(ra),
+                           float(eta), err_pos, err_vel, spread_pos, spread_vel, int(n), C.c_uint64(seed),
+                           C.c_void_p(X.data_ptr()), C.c_void_p(T.data_ptr()), C.c_void_p(_stream_handle(stream)))
+    _check(lib, None, st, "bp_lp_dataset")
+    return X, T
 
 
 def synthesize(geom: Geometry, x_pos: np.ndarray, sfv: np.ndarray, rho: np.ndarray,

@@ -249,6 +249,12 @@ bp_status bp_get_diag(bp_handle* h, int what, void* host, size_t bytes) {
         // the predicted particles stay in the buffer the update resampled from
         const float* pred_phi = D.phi[1 - D.cur];
         for (int s = h->S_legacy; s < S; ++s) parts.push_back({pred_phi + (size_t)s * 6 * P, (size_t)3 * P * sizeof(float)});
+    } else if (what == BP_DIAG_LPROP) {
+        if (!h->lp_net || !h->lp_buf) return fail(h, BP_ERR_STATE, "bp_get_diag: no proposal network attached");
+        parts.push_back({h->lp_buf, (size_t)(6 + 4 * J) * sizeof(double)});
+        parts.push_back({h->lp_logr, (size_t)P * sizeof(double)});
+        parts.push_back({h->lp_X, (size_t)P * 16 * sizeof(float)});
+        parts.push_back({h->lp_Y, (size_t)P * 16 * sizeof(float)});
     } else if (what == BP_DIAG_INDICES) {
         parts.push_back({D.idx, (size_t)P * sizeof(int)});
         parts.push_back({D.idx + P, (size_t)S * P * sizeof(int)});
@@ -551,7 +557,8 @@ void update_enqueue(bp_handle* h, const float* z_dev) {
     const int S = h->S, J = h->J, P = h->P;
     DevState& D = h->D;
     mark(h, 1);
-    // births drawn from the proposal need this step's observation
+    // the learned MT proposal and births drawn from the proposal need this step's observation
+    h->launches += launch_learned_proposal(h, z_dev);
     h->launches += launch_birth_proposal(h->G, h->Pm, D, h->S_legacy, S, z_dev, h->st);
     launch_row_sums(h->Pm, D, S, J, h->st);
     mark(h, 2);

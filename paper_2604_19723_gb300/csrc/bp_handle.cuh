@@ -48,6 +48,12 @@ struct bp_handle {
     char* ws_base;
     bool ws_owned;
     bool ws_shared;     // bound to a workspace that other filters overwrite: no diagnostics
+    // learned MT proposal (attached network, not owned; its buffers are)
+    bp_mlp* lp_net;
+    float* lp_X;        // P x 16 network inputs
+    float* lp_Y;        // P x 16 network outputs
+    double* lp_logr;    // P log importance ratios of the last update
+    double* lp_buf;     // predicted mean (6), per-PA correlations (4 J)
     int prof_on;
     cudaEvent_t ev[BP_PROF_STAGES + 1];
     bool ev_valid[BP_PROF_STAGES];
@@ -72,3 +78,9 @@ bool dynamic_pf_count(const bp_handle* h);
 // geometry checks and the device copy of its constants (shared with the PCRLB entry points)
 bp_status validate_geom(const bp_geometry* g);
 void fill_geom(bp::DevGeom& G, const bp_geometry* g);
+
+// proposal network forward pass on a stream (k_mlp.cu), and the learned MT proposal of
+// an update (k_lproposal.cu; returns its launch count, 0 without a network)
+void mlp_forward_async(const bp_mlp* net, const float* X, int B, float* Y, cudaStream_t st);
+int launch_learned_proposal(const bp_handle* h, const float* z_dev);
+

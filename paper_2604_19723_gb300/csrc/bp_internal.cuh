@@ -69,7 +69,8 @@ __host__ __device__ inline U4 philox(uint32_t c0, uint32_t c1, uint32_t c2, uint
 enum : uint32_t {
     RNG_MT_PREDICT = 1, RNG_ETA_PREDICT = 2, RNG_PF_GAUSS = 3, RNG_PF_GAMMA = 4, RNG_BIRTH = 5,
     RNG_RESAMPLE = 6, RNG_JITTER_MT = 7, RNG_JITTER_PF = 8, RNG_JITTER_ETA = 9, RNG_INIT_MT = 10,
-    RNG_INIT_ETA = 11, RNG_SYNTH_NOISE = 12, RNG_BIRTH_CAND = 13, RNG_BIRTH_PROP = 14
+    RNG_INIT_ETA = 11, RNG_SYNTH_NOISE = 12, RNG_BIRTH_CAND = 13, RNG_BIRTH_PROP = 14,
+    RNG_LEARNED_PROP = 15, RNG_LP_DATA = 16
 };
 constexpr int MAX_GAMMA_ATTEMPTS = 16;
 
@@ -150,6 +151,23 @@ __device__ inline PathGeo path_geo(const DevGeom& G, int j, double px, double py
     const double d = sqrt(lx * lx + ly * ly + lz * lz);
     const double inv = 1.0 / d;
     return PathGeo{d, lx * inv, ly * inv, lz * inv};
+}
+
+// cis(2 pi t) for a phase in cycles, reduced to its fractional part first
+__device__ inline double2 cis_cycles(double t) {
+    const double f = t - rint(t);
+    double s, c;
+    sincospi(2.0 * f, &s, &c);
+    return make_double2(c, s);
+}
+
+// element (f, y, m) of psi_j in FP64: lambda/(4 pi d) exp(j 2 pi (-(fc + f_f) d / c +
+// (p_y uy + p_z uz) / lambda))
+__device__ inline double2 steer_elem(const DevGeom& G, const PathGeo& g, int f, int y, int m) {
+    const double amp = G.lam / (4.0 * M_PI * g.d);
+    const double cyc = -(G.fc + G.f[f]) * g.d / G.c + (G.py[y] * g.uy + G.pz[m] * g.uz) / G.lam;
+    const double2 e = cis_cycles(cyc);
+    return make_double2(amp * e.x, amp * e.y);
 }
 
 // fractional part in [-1/2, 1/2]

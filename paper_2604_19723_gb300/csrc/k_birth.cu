@@ -11,22 +11,6 @@
 
 namespace bp {
 
-// cis(2 pi t) for a phase in cycles, reduced to its fractional part first
-__device__ inline double2 cis_cycles(double t) {
-    const double f = t - rint(t);
-    double s, c;
-    sincospi(2.0 * f, &s, &c);
-    return make_double2(c, s);
-}
-
-// element (f, y, m) of psi_j: lambda/(4 pi d) exp(j 2 pi (-(fc + f_f) d / c + (p_y uy + p_z uz) / lambda))
-__device__ inline double2 steer_elem(const DevGeom& G, const PathGeo& g, int f, int y, int m) {
-    const double amp = G.lam / (4.0 * M_PI * g.d);
-    const double cyc = -(G.fc + G.f[f]) * g.d / G.c + (G.py[y] * g.uy + G.pz[m] * g.uz) / G.lam;
-    const double2 e = cis_cycles(cyc);
-    return make_double2(amp * e.x, amp * e.y);
-}
-
 __device__ inline double block_sum_d(double v, double* red) {
     // fixed-order tree over the block (blockDim.x a power of two, <= 1024)
     const int t = threadIdx.x;

@@ -361,6 +361,13 @@ static bp_status mlp_launch(bp_mlp* h, bool train, const float* X, const float* 
     return BP_OK;
 }
 
+void mlp_forward_async(const bp_mlp* net, const float* X, int B, float* Y, cudaStream_t st) {
+    if (B < 1) return;
+    const MlpSmem L(false);
+    smem_allow_max((const void*)k_mlp<false>);
+    k_mlp<false><<<(B + 127) / 128, 128, L.total, st>>>(net->prm, X, nullptr, B, 0.f, Y, nullptr, nullptr, net->err);
+}
+
 extern "C" {
 
 bp_status bp_mlp_create(const float* params_host, void* cuda_stream, bp_mlp** out) {

@@ -1,0 +1,130 @@
+"""Learned MT proposal: training on the GPU and its gain over the transition proposal.
+
+The proposal network (bp_mlp_*, BF16 tensor-core kernels) is trained by its own Adam
+steps on samples that bp_lp_dataset simulates from the model of a workload (its
+geometry, surfaces, amplitudes and noise variance), then attached to filters with
+bp_set_mt_proposal.  The importance weights keep every filter's posterior exact, so
+the network can only change how well P particles cover it: `compare` runs the same
+observations with and without the network and reports the MT posterior's effective
+sample size and position error.
+
+Runs from the command line:  python -m paper_2604_19723_gb300.learned --runs 4 --steps 50 --P 2000
+"""
+from __future__ import annotations
+
+import argparse
+import dataclasses
+import json
+import time
+from typing import Dict
+
+import numpy as np
+
+from . import bp
+from . import workload as W
+
+
+def scenario_model(name: str, seed: int):
+    """Geometry, parameters, surfaces, moduli and noise variance of a workload's scene."""
+    wl = W.workload(name)
+    g, prm = wl["geom"], wl["params"]
+    scn = W.make_scenario(g, prm, N=2, K=wl["K"], seed=seed, snr_db=wl["snr_db"])
+    x_pos, sfv, rho, cc, cs, cr = bp.scenario_arrays(scn, [1])
+    _, eta = bp.synthesize(g, x_pos, sfv, rho, cc, cs, cr, snr_db=wl["snr_db"], seed=seed, step0=1)
+    return g, prm, scn.sfv_true, scn.rho_abs, eta
+
+
+def train_proposal(name: str = "paper_exp1_proposal", n_samples: int = 1 << 17, steps: int = 2000,
+                   batch: int = 4096, lr: float = 1e-3, seed: int = 7, data_seed: int = 1) -> Dict:
+    """Simulates n_samples training rows and runs `steps` Adam steps on random batches;
+    returns the network and the loss history (mean per row, every 100 steps)."""
+    import torch
+    g, prm, sfv, rho_abs, eta = scenario_model(name, data_seed)
+    t0 = time.perf_counter()
+    X, T = bp.lp_dataset(g, prm, sfv, rho_abs, eta, n_samples, seed=seed)
+    t_data = time.perf_counter() - t0
+    net = bp.Mlp(W.mlp_init(seed))
+    gen = torch.Generator(device="cuda")
+    gen.manual_seed(seed)
+    loss = torch.zeros(1, dtype=torch.float32, device="cuda")
+    hist = []
+    t0 = time.perf_counter()
+    for s in range(steps):
+        idx = torch.randint(0, n_samples, (batch,), device="cuda", generator=gen)
+        net.train_step(X[idx], T[idx], lr, loss)
+        if s % 100 == 0 or s == steps - 1:
+            hist.append((s, float(loss.item()) / batch))
+    net.sync()
+    return dict(net=net, loss=hist, data_s=t_data, train_s=time.perf_counter() - t0, eta=eta)
+
+
+def run(name: str, net, runs: int, steps: int, P: int, seed: int) -> Dict:
+    """The filter over `steps` steps of `runs` scenes (map in place at time 0), with the
+    network attached or (net None) with the transition proposal."""
+    wl = W.workload(name)
+    g, prm = wl["geom"], wl["params"]
+    err, ess = np.full((runs, steps), np.nan), np.full((runs, steps), np.nan)
+    wall = 0.0
+    for r in range(runs):
+        scn = W.make_scenario(g, prm, N=steps, K=wl["K"], seed=seed + r, snr_db=wl["snr_db"],
+                              visibility=wl["visibility"], clutter_mean=wl["clutter_mean"])
+        x_pos, sfv, rho, cc, cs, cr = bp.scenario_arrays(scn, range(1, steps + 1))
+        z, eta = bp.synthesize(g, x_pos, sfv, rho, cc, cs, cr, snr_db=wl["snr_db"], seed=seed + r + 7, step0=1)
+        f = bp.Filter(g, prm, P=P, S_max=wl["S_max"], seed=seed + r)
+        f.set_state(W.state_near_truth(scn, P=P, S=wl["K"] + 1, n=0, seed=seed + r + 3, eta_true=eta,
+                                       pos_std=0.02, vel_std=0.05, sfv_std=0.02))
+        if net is not None:
+            f.set_mt_proposal(net)
+        t0 = time.perf_counter()
+        try:
+            for n in range(steps):
+                f.step(z[n])
+                try:
+                    e = f.estimate()
+                except bp.BPError:
+                    break
+                err[r, n] = np.linalg.norm(e["x_hat"][:3] - scn.x_true[n + 1, :3])
+                ess[r, n] = e["ess_x"]
+        finally:
+            wall += time.perf_counter() - t0
+            f.close()
+    return dict(err=err, ess=ess, wall_s=wall)
+
+
+def compare(name: str = "paper_exp1_proposal", runs: int = 4, steps: int = 50, P: int = 2000, seed: int = 500,
+            train: Dict = None, P_transition: int = None) -> Dict:
+    """The same scenes with the learned proposal at P particles and with the transition
+    proposal at P_transition (default P)."""
+    train = train or train_proposal(name)
+    with_net = run(name, train["net"], runs, steps, P, seed)
+    plain = run(name, None, runs, steps, P_transition or P, seed)
+
+    def stats(d):
+        e = d["err"]
+        return dict(rmse=float(np.sqrt(np.nanmean(e ** 2))), median_err=float(np.nanmedian(e)),
+                    mean_ess=float(np.nanmean(d["ess"])), median_ess=float(np.nanmedian(d["ess"])),
+                    failed_steps=int(np.sum(np.isnan(e))), wall_s=d["wall_s"])
+
+    return dict(workload=name, runs=runs, steps=steps, P=P, P_transition=P_transition or P, loss=train["loss"],
+                train_s=train["train_s"],
+                data_s=train["data_s"], learned=stats(with_net), transition=stats(plain))
+
+
+def main(argv=None):
+    ap = argparse.ArgumentParser(description=__doc__.split("\n")[0])
+    ap.add_argument("--workload", default="paper_exp1_proposal")
+    ap.add_argument("--runs", type=int, default=4)
+    ap.add_argument("--steps", type=int, default=50)
+    ap.add_argument("--P", type=int, default=2000)
+    ap.add_argument("--samples", type=int, default=1 << 17)
+    ap.add_argument("--train-steps", type=int, default=2000)
+    ap.add_argument("--lr", type=float, default=1e-3)
+    ap.add_argument("--P-transition", type=int, default=None, help="particles of the transition-proposal runs")
+    a = ap.parse_args(argv)
+    tr = train_proposal(a.workload, a.samples, a.train_steps, lr=a.lr)
+    res = compare(a.workload, a.runs, a.steps, a.P, train=tr, P_transition=a.P_transition)
+    print(json.dumps(res))
+
+
+if __name__ == "__main__":
+    main()
