@@ -411,8 +411,29 @@ def run_gpu(args, rank, world):
     if rank == 0 and not args.no_cpu_baseline:
         out["cpu_baseline"] = cpu_baseline(wl, g, prm, scn, args.cpu_particles, z_all[:1].cpu().numpy())
     f.close()
+    if rank == 0 and world == 1 and not args.no_matched:
+        out["matched_accuracy"] = matched_accuracy()
     if rank == 0:
         print(json.dumps(out))
+
+
+def matched_accuracy(runs=2, steps=60, P_learned=2000, P_transition=30000):
+    """Steps/s at matched accuracy: the Experiment 1 shape (map in place at time 0, same
+    observations) with the learned MT proposal at P_learned particles against the plain
+    transition proposal at the paper's P_transition; network trained here on the GPU
+    (2^17 simulated samples, 2000 Adam steps).  Device time per step from CUDA events."""
+    try:
+        from paper_2604_19723_gb300 import learned
+        tr = learned.train_proposal("paper_exp1_proposal")
+        res = learned.compare("paper_exp1_proposal", runs=runs, steps=steps, P=P_learned, seed=900, train=tr,
+                              P_transition=P_transition)
+        keep = ("rmse", "median_err", "mean_ess", "ms_per_step", "steps_per_s", "failed_steps")
+        return {"workload": "paper_exp1_proposal, map in place at time 0", "runs": runs, "steps": steps,
+                "learned": dict(P=P_learned, **{k: res["learned"][k] for k in keep}),
+                "transition": dict(P=P_transition, **{k: res["transition"][k] for k in keep}),
+                "rmse_unit": "m", "train_s": res["train_s"], "final_loss": res["loss"][-1][1]}
+    except Exception as e:   # the headline line must not depend on this comparison
+        return {"error": f"{type(e).__name__}: {e}"}
 
 
 # ---------------------------------------------------------------- batched scenarios
@@ -592,6 +613,7 @@ def main():
     ap.add_argument("--cpu-particles", type=int, default=1024)
     ap.add_argument("--ref-particles", type=int, default=256)
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--no-matched", action="store_true", help="skip the learned-proposal matched-accuracy comparison")
     ap.add_argument("--scenarios", type=int, default=4096, help="batched workload: number of scenarios")
     ap.add_argument("--streams", type=int, default=32, help="batched workload: concurrent streams")
     ap.add_argument("--no-sequential", action="store_true", help="batched workload: skip the one-stream run")

@@ -60,17 +60,25 @@ def train_proposal(name: str = "paper_exp1_proposal", n_samples: int = 1 << 17, 
 
 def run(name: str, net, runs: int, steps: int, P: int, seed: int) -> Dict:
     """The filter over `steps` steps of `runs` scenes (map in place at time 0), with the
-    network attached or (net None) with the transition proposal."""
+    network attached or (net None) with the transition proposal.  Each step's device
+    time comes from CUDA events recorded on the filter's stream around bp_predict +
+    bp_update; the estimate is read outside them."""
+    import torch
     wl = W.workload(name)
     g, prm = wl["geom"], wl["params"]
     err, ess = np.full((runs, steps), np.nan), np.full((runs, steps), np.nan)
+    step_ms = []
     wall = 0.0
+    stream = torch.cuda.Stream()
     for r in range(runs):
         scn = W.make_scenario(g, prm, N=steps, K=wl["K"], seed=seed + r, snr_db=wl["snr_db"],
                               visibility=wl["visibility"], clutter_mean=wl["clutter_mean"])
         x_pos, sfv, rho, cc, cs, cr = bp.scenario_arrays(scn, range(1, steps + 1))
-        z, eta = bp.synthesize(g, x_pos, sfv, rho, cc, cs, cr, snr_db=wl["snr_db"], seed=seed + r + 7, step0=1)
-        f = bp.Filter(g, prm, P=P, S_max=wl["S_max"], seed=seed + r)
+        with torch.cuda.stream(stream):
+            z, eta = bp.synthesize(g, x_pos, sfv, rho, cc, cs, cr, snr_db=wl["snr_db"], seed=seed + r + 7, step0=1,
+                                   stream=stream)
+        stream.synchronize()
+        f = bp.Filter(g, prm, P=P, S_max=wl["S_max"], seed=seed + r, stream=stream)
         f.set_state(W.state_near_truth(scn, P=P, S=wl["K"] + 1, n=0, seed=seed + r + 3, eta_true=eta,
                                        pos_std=0.02, vel_std=0.05, sfv_std=0.02))
         if net is not None:
@@ -78,17 +86,21 @@ def run(name: str, net, runs: int, steps: int, P: int, seed: int) -> Dict:
         t0 = time.perf_counter()
         try:
             for n in range(steps):
+                e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+                e0.record(stream)
                 f.step(z[n])
+                e1.record(stream)
                 try:
                     e = f.estimate()
                 except bp.BPError:
                     break
+                step_ms.append(e0.elapsed_time(e1))
                 err[r, n] = np.linalg.norm(e["x_hat"][:3] - scn.x_true[n + 1, :3])
                 ess[r, n] = e["ess_x"]
         finally:
             wall += time.perf_counter() - t0
             f.close()
-    return dict(err=err, ess=ess, wall_s=wall)
+    return dict(err=err, ess=ess, wall_s=wall, step_ms=step_ms)
 
 
 def compare(name: str = "paper_exp1_proposal", runs: int = 4, steps: int = 50, P: int = 2000, seed: int = 500,
@@ -101,9 +113,11 @@ def compare(name: str = "paper_exp1_proposal", runs: int = 4, steps: int = 50, P
 
     def stats(d):
         e = d["err"]
+        ms = float(np.mean(d["step_ms"])) if d["step_ms"] else float("nan")
         return dict(rmse=float(np.sqrt(np.nanmean(e ** 2))), median_err=float(np.nanmedian(e)),
                     mean_ess=float(np.nanmean(d["ess"])), median_ess=float(np.nanmedian(d["ess"])),
-                    failed_steps=int(np.sum(np.isnan(e))), wall_s=d["wall_s"])
+                    failed_steps=int(np.sum(np.isnan(e))), ms_per_step=ms, steps_per_s=1e3 / ms,
+                    wall_s=d["wall_s"])
 
     return dict(workload=name, runs=runs, steps=steps, P=P, P_transition=P_transition or P, loss=train["loss"],
                 train_s=train["train_s"],
