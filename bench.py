@@ -91,11 +91,11 @@ def a5_flops(P, S, J, Nz):
 # a single-pass metric set, at the full size of the workload), valid while the kernel
 # sources hash to the recorded value.
 TRAFFIC_RECORDS = {
-    "k_kappa": {"workload": "scale_64x100k", "P": 100000, "bytes": 925.64e6,
-                "sources_sha256": "1292387ebaba6953441ac9752ac6b80c47c954234dd29f38bca4fe8ead0e9524",
+    "k_kappa": {"workload": "scale_64x100k", "P": 100000, "bytes": 923.65e6,
+                "sources_sha256": "7da57d7097ee9ab92cf8797afb827356965745f2175253c3589bc490e31d6e00",
                 "profile": "profiles/dram_scale_64x100k.md"},
-    "k_iota_blk": {"workload": "scale_64x100k", "P": 100000, "bytes": 708.67e6,
-                   "sources_sha256": "1292387ebaba6953441ac9752ac6b80c47c954234dd29f38bca4fe8ead0e9524",
+    "k_iota_blk": {"workload": "scale_64x100k", "P": 100000, "bytes": 706.63e6,
+                   "sources_sha256": "7da57d7097ee9ab92cf8797afb827356965745f2175253c3589bc490e31d6e00",
                    "profile": "profiles/dram_scale_64x100k.md"},
 }
 KERNEL_SOURCES = ("paper_2604_19723_gb300/csrc/k_like.cu", "paper_2604_19723_gb300/csrc/bp_kernels.cuh",
@@ -525,8 +525,18 @@ def run_batched(args, rank, world):
     t_init = time.perf_counter()
     b = bp.Batch(tup, n_streams=args.streams, shared_workspace=True, use_graph=True, stream=stream)
     t_init = time.perf_counter() - t_init
-    members = [b.member(i) for i in range(n)]
     z = make_z(b)
+    tuned = None
+    if not args.no_autotune:
+        # launch configuration picked by measurement on a sample of the scenarios
+        from paper_2604_19723_gb300 import autotune
+        b.close()
+        tuned = autotune.tune_batch(tup, z, sample=min(n, 64), steps=2, warmup=1, stream=stream)
+        args.streams, use_graph = tuned["best"]
+        t_init = time.perf_counter()
+        b = bp.Batch(tup, n_streams=args.streams, shared_workspace=True, use_graph=use_graph, stream=stream)
+        t_init = time.perf_counter() - t_init
+    members = [b.member(i) for i in range(n)]
     t_step, launches, clocks = timed(b, z, members)
     dev_bytes = b.device_bytes()
 
@@ -577,7 +587,8 @@ def run_batched(args, rank, world):
            "config": {"workload": "batched", "scenarios": n, "S": "U{1..64}", "P": "U{256..16384}",
                       "Nz": "U{5..300} (one antenna below 16, else 2x2 URA)", "J": 4,
                       "particle_PA_updates_per_step": updates, "streams": min(args.streams, n),
-                      "graph": True, "shared_workspace": True, "device_GB": dev_bytes / 1e9,
+                      "graph": bool(tuned["best"][1]) if tuned else True, "shared_workspace": True,
+                      "autotune": tuned, "device_GB": dev_bytes / 1e9,
                       "init_s": t_init, "l2": "flushed between timed steps (256 MB write)",
                       "parallelism": f"replicas x{world}"},
            "sequential": ({"ms_per_step": seq_ms, "value": world * updates / (seq_ms * 1e-3),
@@ -617,6 +628,8 @@ def main():
     ap.add_argument("--scenarios", type=int, default=4096, help="batched workload: number of scenarios")
     ap.add_argument("--streams", type=int, default=32, help="batched workload: concurrent streams")
     ap.add_argument("--no-sequential", action="store_true", help="batched workload: skip the one-stream run")
+    ap.add_argument("--no-autotune", action="store_true",
+                    help="batched workload: use --streams with graphs instead of the measured best configuration")
     args = ap.parse_args()
     world = int(os.environ.get("WORLD_SIZE", "1"))
     rank = int(os.environ.get("RANK", "0"))

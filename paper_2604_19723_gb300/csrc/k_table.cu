@@ -282,7 +282,12 @@ __device__ void jacobi_herm(typename cplx<T>::t* A, typename cplx<T>::t* U, int 
                 if (q < n) {
                     const C apq = A[p * n + q];
                     const T m = sqrt(apq.x * apq.x + apq.y * apq.y);
-                    if (m > T(1e-30)) {
+                    // a pair that already meets the convergence test is not rotated
+                    // (threshold Jacobi); its update below is skipped
+                    const double dp = fabs((double)A[p * n + p].x), dq = fabs((double)A[q * n + q].x);
+                    const double m2 = (double)m * (double)m;
+                    const bool small = m2 * fmax(dp - shift, 0.0) * fmax(dq - shift, 0.0) <= tol * (dp * dq) * (dp * dq);
+                    if (!small && m > T(1e-30)) {
                         const T zeta = (A[q * n + q].x - A[p * n + p].x) / (T(2) * m);
                         const T t = (zeta >= T(0) ? T(1) : T(-1)) / (fabs(zeta) + sqrt(T(1) + zeta * zeta));
                         const T c = T(1) / sqrt(T(1) + t * t);
@@ -299,6 +304,7 @@ __device__ void jacobi_herm(typename cplx<T>::t* A, typename cplx<T>::t* U, int 
                 pair_of(r, i, p, q);
                 if (q >= n) continue;
                 const JRot<T> g = rot[i];
+                if (g.s == T(0)) continue;
                 for (int w = 0; w < 2; ++w) {
                     C* X = w ? U : A;
                     const C xp = X[row * n + p], xq = X[row * n + q];
@@ -315,6 +321,7 @@ __device__ void jacobi_herm(typename cplx<T>::t* A, typename cplx<T>::t* U, int 
                 pair_of(r, i, p, q);
                 if (q >= n) continue;
                 const JRot<T> g = rot[i];
+                if (g.s == T(0)) continue;
                 const C ap = A[p * n + cc], aq = A[q * n + cc];
                 const T eqx = g.er * aq.x - g.ei * aq.y, eqy = g.er * aq.y + g.ei * aq.x;   // e^{i phi} a_q
                 A[p * n + cc].x = g.c * ap.x - g.s * eqx; A[p * n + cc].y = g.c * ap.y - g.s * eqy;
@@ -325,7 +332,7 @@ __device__ void jacobi_herm(typename cplx<T>::t* A, typename cplx<T>::t* U, int 
             for (int i = tid; i < half; i += nt) {
                 int p, q;
                 pair_of(r, i, p, q);
-                if (q >= n) continue;
+                if (q >= n || rot[i].s == T(0)) continue;
                 A[p * n + q].x = T(0); A[p * n + q].y = T(0);
                 A[q * n + p].x = T(0); A[q * n + p].y = T(0);
                 A[p * n + p].y = T(0);

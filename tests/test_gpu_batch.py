@@ -207,3 +207,30 @@ def test_batch_rejects_bad_arguments():
         bp.Batch([(g, prm, 256, 4, 5, 1)])          # S0 > S_max
     with pytest.raises(bp.BPError):
         bp.Batch([(g, prm, 256, 4, 2, 1)], n_streams=500)
+
+
+def test_autotuner_picks_the_fastest_measured_configuration():
+    """The tuner times every candidate on the batch and returns the fastest; a batch
+    built with its choice gives the same estimates as the default configuration."""
+    from paper_2604_19723_gb300 import autotune
+    inputs = make_inputs(CASES)
+    sc = [(d["g"], d["prm"], d["P"], d["S"], d["S"], d["seed"]) for d in inputs]
+    b0 = make_batch(inputs, n_streams=2)
+    z = torch.stack([concat_z(b0, inputs, 0), concat_z(b0, inputs, 1)])
+    b0.close()
+    cands = ((1, False), (2, True), (5, True))
+    res = autotune.tune_batch(sc, z, candidates=cands, steps=2, warmup=1)
+    assert len(res["ms"]) == 3 and all(v > 0 for v in res["ms"].values())
+    best_ms = res["ms"][f"{res['best'][0]} streams, graph {res['best'][1]}"]
+    assert best_ms == min(res["ms"].values())
+    outs = []
+    for n_streams, graph in (res["best"], (2, True)):
+        b = make_batch(inputs, n_streams=n_streams, use_graph=graph)
+        for i, d in enumerate(inputs):
+            b.member(i).set_state(d["st"])
+        b.step(z[0])
+        b.sync()
+        outs.append([b.member(i).estimate()["x_hat"] for i in range(len(inputs))])
+        b.close()
+    for a, c in zip(*outs):
+        assert np.max(np.abs(a - c)) < 1e-6
