@@ -343,7 +343,10 @@ __device__ void jacobi_herm(typename cplx<T>::t* A, typename cplx<T>::t* U, int 
     }
 }
 
-__global__ void k_stage_kappa(DevGeom G, DevParams Pm, DevState D, int S, int SC, const float* z,
+// 16 warps: the FP64 rotation and product loops are latency bound at one block per SM
+constexpr int STAGE_THREADS = 512;
+
+__global__ void __launch_bounds__(STAGE_THREADS) k_stage_kappa(DevGeom G, DevParams Pm, DevState D, int S, int SC, const float* z,
                               const double* gram, double* V64) {
     const int s = blockIdx.x, j = blockIdx.y;
     const int J = G.J, Nz = G.Nz, SM = Pm.S_max;
@@ -687,7 +690,7 @@ void launch_stage(const DevGeom& G, const DevParams& Pm, const DevState& D, int 
     const size_t sm1 = (3 * (size_t)K * K + 3 * (size_t)K) * sizeof(double2) + ((size_t)K + 8) * sizeof(double) +
                        32 * sizeof(JRot<double>);
     smem_allow_max((const void*)k_stage_kappa);
-    k_stage_kappa<<<dim3(S, G.J), 256, sm1, st>>>(G, Pm, D, S, SC, z, gram, V64);
+    k_stage_kappa<<<dim3(S, G.J), STAGE_THREADS, sm1, st>>>(G, Pm, D, S, SC, z, gram, V64);
     const size_t sm2 = ((size_t)S * S + 3 * (size_t)S) * sizeof(double2);
     smem_allow_max((const void*)k_nu_tridiag);
     k_nu_tridiag<<<G.J, 128, sm2, st>>>(Pm, D, S, gram, nu_b);
