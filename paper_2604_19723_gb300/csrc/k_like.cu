@@ -910,8 +910,13 @@ __host__ __device__ inline size_t iota_blk_smem(int S, int nfac, int Nf, int Nz)
            IB_SMAX * 8;
 }
 
+// blocks per SM: two 256-thread blocks at 128 registers (67 KB shared each).  Three
+// (capped at 80 registers, 112 B spilled) measured 127 ms against 120 ms at 64 x 100k:
+// the extra warps against the per-pivot barriers do not pay for the spills
+constexpr int IOTA_BLK_PER_SM = 2;
+
 template <int NCG>
-__global__ void __launch_bounds__(32 * NCG, (NCG == 4 ? 3 : 2)) k_iota_blk(DevGeom G, DevParams Pm, DevState D, int S, const float* z, int all) {
+__global__ void __launch_bounds__(32 * NCG, IOTA_BLK_PER_SM) k_iota_blk(DevGeom G, DevParams Pm, DevState D, int S, const float* z, int all) {
     constexpr int IB_T = 32 * NCG;
     constexpr int QA = 32 / NCG, QB = 64 / NCG;   // register slots of rows ra (< 32) and rb (>= 32)
     extern __shared__ float4 smb[];
@@ -1349,7 +1354,7 @@ void launch_iota_repair(const DevGeom& G, const DevParams& Pm, const DevState& D
     if (all) cudaMemsetAsync(D.flags, 0, sizeof(int), st);
     constexpr int NCG = IOTA_BLK_NCG;
     smem_allow_max((const void*)k_iota_blk<NCG>);
-    const int wave = (NCG == 4 ? 3 : 2) * 152;
+    const int wave = IOTA_BLK_PER_SM * 152;
     const int blocks = all ? std::min(Pm.P, 16 * wave) : wave;
     k_iota_blk<NCG><<<blocks, 32 * NCG, smem, st>>>(G, Pm, D, S, z, all);
 }
