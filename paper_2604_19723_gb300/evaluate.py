@@ -163,7 +163,7 @@ class RunResult:
     failed: int = -1           # step at which the filter reported a numerical failure
 
 
-def run_filter(name: str, variant: str, P: int, N: int, seed: int, init: str = "prior"):
+def run_filter(name: str, variant: str, P: int, N: int, seed: int, init: str = "prior", net=None):
     """One run of a variant on the named workload's shape (Philox key and truth from seed);
     returns (RunResult, Scenario)."""
     zm, coherent = VARIANTS[variant]
@@ -181,6 +181,8 @@ def run_filter(name: str, variant: str, P: int, N: int, seed: int, init: str = "
                                        pos_std=pos_std, vel_std=vel_std, sfv_std=sfv_std))
     elif init != "prior":
         raise ValueError(init)
+    if net is not None:
+        f.set_mt_proposal(net)
     pos, mp = np.full(N, np.nan), np.full((N, K), np.nan)
     S, dec = np.zeros(N, np.int32), np.zeros(N, np.int32)
     failed = -1
@@ -218,14 +220,16 @@ def bound(scns: List[W.Scenario], etas: List[float], coherent: bool, init: str =
 
 
 def evaluate(name: str = "paper_exp1_proposal", variants=("nzm", "zm", "nzm_nc"), runs: int = 10, steps: int = 200,
-             P: int = None, seed: int = 100, init: str = "truth_map") -> Dict:
-    """RMSE of the MT position and of each surface's SFV per step, with PEB and MEB."""
+             P: int = None, seed: int = 100, init: str = "truth_map", net=None) -> Dict:
+    """RMSE of the MT position and of each surface's SFV per step, with PEB and MEB; with
+    a proposal network (bp.Mlp) every run draws its MT particles from the learned
+    proposal."""
     wl = W.workload(name)
     P = P or wl["P"]
-    out = dict(workload=name, runs=runs, steps=steps, P=P, init=init, variants={})
+    out = dict(workload=name, runs=runs, steps=steps, P=P, init=init, learned=net is not None, variants={})
     for v in variants:
         t0 = time.perf_counter()
-        res, scns = zip(*[run_filter(name, v, P, steps, seed + r, init) for r in range(runs)])
+        res, scns = zip(*[run_filter(name, v, P, steps, seed + r, init, net) for r in range(runs)])
         wall = time.perf_counter() - t0
         peb, meb = bound(list(scns), [r.eta for r in res], VARIANTS[v][1], init)
         pos = np.stack([r.pos_err for r in res])
@@ -244,7 +248,8 @@ def evaluate(name: str = "paper_exp1_proposal", variants=("nzm", "zm", "nzm_nc")
 
 def summary(res: Dict, at=(10, 50, 100, 200)) -> str:
     """A plain-text table of RMSE against the bounds at a few steps."""
-    lines = [f"workload {res['workload']}, {res['runs']} runs, P = {res['P']}, init {res['init']}",
+    lines = [f"workload {res['workload']}, {res['runs']} runs, P = {res['P']}, init {res['init']}"
+             f"{', learned MT proposal' if res.get('learned') else ''}",
              "variant  step  RMSE_pos[m]  median[m]  PEB[m]   RMSE_map (surfaces 1..K) [m]   MEB [m]   PFs"]
     for v, d in res["variants"].items():
         for n in at:
@@ -271,8 +276,13 @@ def main(argv=None):
     ap.add_argument("--seed", type=int, default=100)
     ap.add_argument("--init", default="truth_map", choices=["prior"] + sorted(INIT_STD))
     ap.add_argument("--json", default=None, help="write the full per-step result here")
+    ap.add_argument("--learned", action="store_true", help="draw MT particles from a trained proposal network")
     a = ap.parse_args(argv)
-    res = evaluate(a.workload, tuple(a.variants.split(",")), a.runs, a.steps, a.P, a.seed, a.init)
+    net = None
+    if a.learned:
+        from . import learned
+        net = learned.train_proposal(a.workload)["net"]
+    res = evaluate(a.workload, tuple(a.variants.split(",")), a.runs, a.steps, a.P, a.seed, a.init, net)
     if a.json:
         with open(a.json, "w") as fh:
             json.dump(res, fh)
