@@ -7,7 +7,7 @@ key increments 0x9E3779B9 / 0xBB67AE85.  Pinned by the published known-answer
 vectors in tests/golden/philox4x32_10_kat.txt.
 
 Draw allocation (the same scheme is implemented independently in the CUDA
-library, from the description in the design doc):
+library, from this description):
   key     = (seed mod 2^32, seed div 2^32)
   counter = (c0 = item index, c1 = step n, c2 = purpose << 16 | sub, c3 = block)
 

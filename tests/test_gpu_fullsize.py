@@ -6,7 +6,7 @@ The message table is a sum over every particle, so the oracle computes it in ful
 checked on a sample of particles, which the oracle evaluates one by one with the
 dense (explicit covariance) definition.  The sample holds the particles nearest the
 true state (chosen from the seeded state, where the weight is), particles spread
-over the whole range, and the ragged last one.  The bound is the benchmark spec one on
+over the whole range, and the ragged last one.  The bound is the stated one on
 normalised weights, max_p |dw_p| / max_p w_p < 1e-4, with the weights normalised
 over the sample (a particle far from the truth has a log-likelihood 1e3-1e4 below
 the best one, FP32 rounding of 1e-7 relative on that scale, and a weight that is

@@ -2,7 +2,7 @@
 
 Stage-wise from identical inputs (the seeded generator of
 paper_2604_19723_gb300.workload), so that FP32 rounding of one stage does not
-feed the next.  Tolerances (the benchmark spec): 1e-5 absolute on existence
+feed the next.  Tolerances: 1e-5 absolute on existence
 probabilities, 1e-4 relative on normalised weights (max_p |dw_p| / max_p w_p),
 1e-4 on posterior means (m, m/s; relative for gamma, mu, eta).
 """
