@@ -501,7 +501,9 @@ __global__ void __launch_bounds__(STAGE_THREADS) k_stage_kappa(DevGeom G, DevPar
         const double e1e1 = red[0] - 2.0 * red[4] + red[6];
         const double pe1 = pe0 - 2.0 * pue_r + puu;
         const double Q11 = (e1e1 - pe1 / eb) / eb;
-        const double mAm = (red[3] - pmm / eb) / eb;
+        // m^H A^-1 m >= 0 (A positive definite); a negative value is cancellation
+        // rounding of a PF whose m-vector lies in the span of the others: clamp it
+        const double mAm = fmax((red[3] - pmm / eb) / eb, 0.0);
         // m^H A^-1 e1 = m^H A^-1 e0 - m^H A^-1 mu4
         const double2 mAe0 = make_double2((red[1] - pme_r / eb) / eb, (red[2] - pme_i / eb) / eb);
         const double2 mAu = make_double2((red[7] - pmu_r / eb) / eb, (mm4_im - pmu_i / eb) / eb);
