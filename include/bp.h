@@ -419,12 +419,13 @@ bp_status bp_set_mt_proposal(bp_handle* h, bp_mlp* net);
  * the ROI of prm (velocity uniform within +-v_max), its NCV successor, a previous
  * posterior mean with errors N(0, err_pos^2) / N(0, err_vel^2) and a particle around it
  * with spreads spread_pos / spread_vel, the observation of the successor (LoS and the K
- * surfaces sfv (K x 3, host) with moduli rho_abs (K + 1, host, LoS first), phases common
- * to all PAs and uniform, complex Gaussian noise of variance eta), the input row at the
+ * surfaces sfv (K x 3, host) with moduli rho_abs (K + 1, host, LoS first), uniform
+ * phases common to all PAs (coherent = 1) or drawn per PA (coherent = 0), complex
+ * Gaussian noise of variance eta), the input row at the
  * predicted mean as above, and the target u that carries the particle's F x_{n-1} to the
  * true successor (least squares through Gamma).  0 <= K <= 8, J <= 4.  Synchronous. */
 bp_status bp_lp_dataset(const bp_geometry* geom, const bp_params* prm, int K, const double* sfv, const double* rho_abs,
-                        double eta, double err_pos, double err_vel, double spread_pos, double spread_vel, int n,
+                        double eta, int coherent, double err_pos, double err_vel, double spread_pos, double spread_vel, int n,
                         uint64_t seed, float* X_dev, float* T_dev, void* cuda_stream);
 
 #ifdef __cplusplus

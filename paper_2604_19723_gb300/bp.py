@@ -142,7 +142,8 @@ def load() -> C.CDLL:
     lib.bp_mlp_last_error.restype = C.c_char_p
     lib.bp_set_mt_proposal.argtypes = [vp, vp]
     lib.bp_lp_dataset.argtypes = [C.POINTER(_Geometry), C.POINTER(_Params), C.c_int, C.POINTER(C.c_double),
-                                  C.POINTER(C.c_double)] + [C.c_double] * 5 + [C.c_int, C.c_uint64, vp, vp, vp]
+                                  C.POINTER(C.c_double), C.c_double, C.c_int] + [C.c_double] * 4 + \
+                                 [C.c_int, C.c_uint64, vp, vp, vp]
     untyped = ("bp_last_error", "bp_launch_count", "bp_batch_z_offset", "bp_batch_z_floats",
                "bp_batch_device_bytes", "bp_batch_last_error", "bp_mlp_last_error")
     for f in ENTRY_POINTS:
@@ -595,9 +596,9 @@ def resample_noalloc(w, seed: int, n: int, kind: int, index: int, out=None, stre
 
 def lp_dataset(geom: Geometry, params: Params, sfv: np.ndarray, rho_abs: np.ndarray, eta: float, n: int, seed: int,
                err_pos: float = 0.002, err_vel: float = 0.02, spread_pos: float = 0.003, spread_vel: float = 0.03,
-               stream=None):
+               coherent: bool = True, stream=None):
     """Training samples of the proposal network (bp_lp_dataset): torch CUDA tensors
-    X (n x 16) and T (n x 3)."""
+    X (n x 16) and T (n x 3); coherent: amplitude phases common to all PAs, else per PA."""
     import torch
     lib = load()
     g = _GeomHolder(geom)
@@ -607,7 +608,8 @@ def lp_dataset(geom: Geometry, params: Params, sfv: np.ndarray, rho_abs: np.ndar
     X = torch.empty((n, MLP_IN), dtype=torch.float32, device="cuda")
     T = torch.empty((n, 3), dtype=torch.float32, device="cuda")
     st = lib.bp_lp_dataset(C.byref(g.s), C.byref(pr), sf.shape[0], _dptr(sf) if sf.size else None, _dptr(ra),
-                           float(eta), err_pos, err_vel, spread_pos, spread_vel, int(n), C.c_uint64(seed),
+                           float(eta), int(bool(coherent)), err_pos, err_vel, spread_pos, spread_vel, int(n),
+                           C.c_uint64(seed),
                            C.c_void_p(X.data_ptr()), C.c_void_p(T.data_ptr()), C.c_void_p(_stream_handle(stream)))
     _check(lib, None, st, "bp_lp_dataset")
     return X, T

@@ -21,8 +21,9 @@
 //
 // k_lp_dataset simulates training samples from the model: previous true state uniform in
 // the ROI, its NCV successor, a previous posterior mean and a particle around it, the
-// observation of the successor (LoS + the given surfaces, common random phases, noise of
-// variance eta), the summary at the predicted mean, and the target u that carries the
+// observation of the successor (LoS + the given surfaces, random phases common to all PAs
+// or drawn per PA, noise of variance eta), the summary at the predicted mean, and the
+// target u that carries the
 // particle to the true successor (least squares through Gamma).
 #include <string>
 
@@ -180,7 +181,7 @@ __global__ void __launch_bounds__(1024) k_lp_norm(DevParams Pm, DevState D) {
 
 // ---------------------------------------------------------------- training data
 struct LpData {
-    int K;
+    int K, coherent;
     const double* sfv;      // K x 3
     const double* rho_abs;  // K + 1
     double eta, err_pos, err_vel, spr_pos, spr_vel;
@@ -234,18 +235,19 @@ __global__ void k_lp_dataset(DevGeom G, DevParams Pm, LpData L, int nsamp, float
         fq[k] = xq[k] + T * xq[3 + k];
         fq[3 + k] = xq[3 + k];
     }
-    // complex amplitudes of the components (common phases), applied to the factors b_f
-    double amp_r[LP_KMAX + 1], amp_i[LP_KMAX + 1];
-    for (int c = 0; c <= L.K; ++c) {
-        const U4 pr = draw(Pm, i, 0, RNG_LP_DATA, 4, c);
-        double sp, cp;
-        sincospi(2.0 * u24d(pr.x), &sp, &cp);
-        amp_r[c] = L.rho_abs[c] * cp;
-        amp_i[c] = L.rho_abs[c] * sp;
-    }
     // the observation of the successor (LoS + K surfaces + noise) and its summary at xb
     double cor[4][4] = {};
     for (int j = 0; j < J; ++j) {
+        // complex amplitudes of the components, applied to the factors b_f: phases common
+        // to all PAs (coherent data) or drawn per PA (noncoherent data)
+        double amp_r[LP_KMAX + 1], amp_i[LP_KMAX + 1];
+        for (int c = 0; c <= L.K; ++c) {
+            const U4 pr = draw(Pm, i, 0, RNG_LP_DATA, 4, L.coherent ? c : c + 32 * (j + 1));
+            double sp, cp;
+            sincospi(2.0 * u24d(pr.x), &sp, &cp);
+            amp_r[c] = L.rho_abs[c] * cp;
+            amp_i[c] = L.rho_abs[c] * sp;
+        }
         // factors of component c (c = K + 1: the LoS at xb): b_f carries the path loss
         // and (for true components) the complex amplitude
         for (int t = lane; t < NC * NFc; t += 32) {
@@ -362,7 +364,7 @@ bp_status bp_set_mt_proposal(bp_handle* h, bp_mlp* net) {
 }
 
 bp_status bp_lp_dataset(const bp_geometry* geom, const bp_params* prm, int K, const double* sfv, const double* rho_abs,
-                        double eta, double err_pos, double err_vel, double spread_pos, double spread_vel, int n,
+                        double eta, int coherent, double err_pos, double err_vel, double spread_pos, double spread_vel, int n,
                         uint64_t seed, float* X_dev, float* T_dev, void* cuda_stream) {
     if (validate_geom(geom) != BP_OK || !prm || K < 0 || K > LP_KMAX || (K > 0 && !sfv) || !rho_abs || !(eta > 0.0) || n < 1 ||
         !X_dev || !T_dev || !(err_pos >= 0) || !(err_vel >= 0) || !(spread_pos >= 0) || !(spread_vel >= 0) ||
@@ -383,7 +385,7 @@ bp_status bp_lp_dataset(const bp_geometry* geom, const bp_params* prm, int K, co
     bool ok = (K == 0 || cudaMemcpyAsync(buf, sfv, (size_t)K * 3 * sizeof(double), cudaMemcpyHostToDevice, st) == cudaSuccess) &&
               cudaMemcpyAsync(buf + 3 * K, rho_abs, (size_t)(K + 1) * sizeof(double), cudaMemcpyHostToDevice, st) == cudaSuccess;
     if (ok) {
-        LpData L{K, buf, buf + 3 * K, eta, err_pos, err_vel, spread_pos, spread_vel};
+        LpData L{K, coherent ? 1 : 0, buf, buf + 3 * K, eta, err_pos, err_vel, spread_pos, spread_vel};
         smem_allow_max((const void*)k_lp_dataset);
         k_lp_dataset<<<(n + 3) / 4, 128, smem, st>>>(G, Pm, L, n, X_dev, T_dev);
         ok = cudaGetLastError() == cudaSuccess && cudaStreamSynchronize(st) == cudaSuccess;

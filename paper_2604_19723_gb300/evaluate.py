@@ -222,14 +222,15 @@ def bound(scns: List[W.Scenario], etas: List[float], coherent: bool, init: str =
 def evaluate(name: str = "paper_exp1_proposal", variants=("nzm", "zm", "nzm_nc"), runs: int = 10, steps: int = 200,
              P: int = None, seed: int = 100, init: str = "truth_map", net=None) -> Dict:
     """RMSE of the MT position and of each surface's SFV per step, with PEB and MEB; with
-    a proposal network (bp.Mlp) every run draws its MT particles from the learned
-    proposal."""
+    a proposal network (bp.Mlp, or a dict coherent-data flag -> bp.Mlp) every run draws
+    its MT particles from the learned proposal."""
     wl = W.workload(name)
     P = P or wl["P"]
     out = dict(workload=name, runs=runs, steps=steps, P=P, init=init, learned=net is not None, variants={})
     for v in variants:
         t0 = time.perf_counter()
-        res, scns = zip(*[run_filter(name, v, P, steps, seed + r, init, net) for r in range(runs)])
+        vnet = net.get(VARIANTS[v][1]) if isinstance(net, dict) else net
+        res, scns = zip(*[run_filter(name, v, P, steps, seed + r, init, vnet) for r in range(runs)])
         wall = time.perf_counter() - t0
         peb, meb = bound(list(scns), [r.eta for r in res], VARIANTS[v][1], init)
         pos = np.stack([r.pos_err for r in res])
@@ -280,8 +281,10 @@ def main(argv=None):
     a = ap.parse_args(argv)
     net = None
     if a.learned:
+        # one network per kind of data: coherent for NZM and ZM, noncoherent for NZM-NC
         from . import learned
-        net = learned.train_proposal(a.workload)["net"]
+        kinds = {VARIANTS[v][1] for v in a.variants.split(",")}
+        net = {c: learned.train_proposal(a.workload, coherent=c)["net"] for c in kinds}
     res = evaluate(a.workload, tuple(a.variants.split(",")), a.runs, a.steps, a.P, a.seed, a.init, net)
     if a.json:
         with open(a.json, "w") as fh:

@@ -35,13 +35,15 @@ def scenario_model(name: str, seed: int):
 
 
 def train_proposal(name: str = "paper_exp1_proposal", n_samples: int = 1 << 17, steps: int = 2000,
-                   batch: int = 4096, lr: float = 1e-3, seed: int = 7, data_seed: int = 1) -> Dict:
-    """Simulates n_samples training rows and runs `steps` Adam steps on random batches;
-    returns the network and the loss history (mean per row, every 100 steps)."""
+                   batch: int = 4096, lr: float = 1e-3, seed: int = 7, data_seed: int = 1,
+                   coherent: bool = True) -> Dict:
+    """Simulates n_samples training rows (amplitude phases common to all PAs, or per PA
+    with coherent False) and runs `steps` Adam steps on random batches; returns the
+    network and the loss history (mean per row, every 100 steps)."""
     import torch
     g, prm, sfv, rho_abs, eta = scenario_model(name, data_seed)
     t0 = time.perf_counter()
-    X, T = bp.lp_dataset(g, prm, sfv, rho_abs, eta, n_samples, seed=seed)
+    X, T = bp.lp_dataset(g, prm, sfv, rho_abs, eta, n_samples, seed=seed, coherent=coherent)
     t_data = time.perf_counter() - t0
     net = bp.Mlp(W.mlp_init(seed))
     gen = torch.Generator(device="cuda")

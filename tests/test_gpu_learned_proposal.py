@@ -125,3 +125,19 @@ def test_trained_network_gains_over_the_transition():
     assert lr["failed_steps"] == 0
     assert lr["rmse"] < 0.5 * tr["rmse"], (lr, tr)
     assert lr["mean_ess"] > tr["mean_ess"], (lr, tr)
+
+
+def test_training_samples_coherent_and_noncoherent_phases():
+    """At the true state the LoS correlations of coherent data share the amplitude's
+    phase, so their ratios to PA 0 are near-real and positive; with phases drawn per PA
+    the ratios spread over the circle."""
+    g = W.make_geometry(J=4, Nf=10, My=4, Mz=4)
+    prm = W.Params()
+    sfv = W.room_sfvs(prm.p_min, prm.p_max)
+    kw = dict(err_pos=0.0, err_vel=0.0, spread_pos=0.0, spread_vel=0.0)
+    Xc, _ = bp.lp_dataset(g, prm, sfv, np.array([1.0, 0.5, 0.5, 0.5, 0.5]), 4e-8, 5000, seed=5, coherent=True, **kw)
+    Xn, _ = bp.lp_dataset(g, prm, sfv, np.array([1.0, 0.5, 0.5, 0.5, 0.5]), 4e-8, 5000, seed=5, coherent=False, **kw)
+    Xc, Xn = Xc.cpu().numpy(), Xn.cpu().numpy()
+    re_c, re_n = Xc[:, [9, 11, 13]], Xn[:, [9, 11, 13]]
+    assert np.median(re_c) > 0.3
+    assert abs(np.mean(re_n)) < 0.05 and abs(np.mean(Xn[:, [10, 12, 14]])) < 0.05
