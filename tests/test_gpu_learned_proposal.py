@@ -141,3 +141,28 @@ def test_training_samples_coherent_and_noncoherent_phases():
     re_c, re_n = Xc[:, [9, 11, 13]], Xn[:, [9, 11, 13]]
     assert np.median(re_c) > 0.3
     assert abs(np.mean(re_n)) < 0.05 and abs(np.mean(Xn[:, [10, 12, 14]])) < 0.05
+
+
+def test_attach_refused_on_batch_handles_and_detach_restores_the_transition():
+    """Handles of a batch share workspaces and take no network (BP_ERR_STATE); on a
+    single filter, detaching (None) brings back the transition proposal exactly."""
+    P, seed = 300, 64
+    g, prm, z, pred = setup(P, seed)
+    net = bp.Mlp(W.mlp_init(65, out_scale=0.3))
+    b = bp.Batch([(g, prm, P, 8, 5, seed)], n_streams=1)
+    with pytest.raises(bp.BPError):
+        b.member(0).set_mt_proposal(net)
+    b.close()
+    zt = torch.from_numpy(np.ascontiguousarray(z.astype(np.complex64))).cuda()
+    out = []
+    for attach in (False, True):
+        f = bp.Filter(g, prm, P=P, S_max=8, seed=seed)
+        if attach:
+            f.set_mt_proposal(net)
+            f.set_mt_proposal(None)
+        f.set_predicted(pred.n, pred.S, pred.x, pred.phi, pred.eta, pred.w_beta, pred.w_alpha, pred.w_xi, pred.zeta)
+        f.update(zt)
+        out.append(f.diag_weights(pred.S)["w_x"])
+        f.close()
+    assert np.allclose(out[0], out[1], rtol=1e-12, atol=0)
+    net.close()
