@@ -337,7 +337,9 @@ extern "C" {
 
 bp_status bp_set_mt_proposal(bp_handle* h, bp_mlp* net) {
     if (!h) return BP_ERR_INVALID_ARG;
-    if (h->ws_shared && net) {
+    // handles of a batch (their workspace is the batch's) replay captured graphs that a
+    // network attached later would not be part of
+    if (!h->ws_owned && net) {
         h->err = "bp_set_mt_proposal: not available on a handle of a batch";
         return BP_ERR_STATE;
     }
