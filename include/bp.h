@@ -213,6 +213,13 @@ bp_status bp_synthesize(const bp_geometry* geom, int n_steps, int step0, const d
 /* Number of kernels launched by this handle since bp_init (instrumentation). */
 long long bp_launch_count(const bp_handle* h);
 
+/* Self-test of the bounded device waits that the tensor-core kernels use: one thread
+ * waits, at most `limit` polls (1 .. 2^20), on an mbarrier phase that nothing completes.
+ * Returns BP_ERR_TIMEOUT (the expected outcome: the wait gave up and the kernel ended
+ * normally, the context stays usable), BP_OK if the phase completed, BP_ERR_CUDA on a
+ * launch failure.  Synchronous. */
+bp_status bp_selftest_wait(int limit, void* cuda_stream);
+
 /* Per-stage timing with CUDA events recorded on the handle's stream
  * (instrumentation, off by default).  bp_get_profile waits for the last
  * bp_predict / bp_update and writes the duration in milliseconds of each

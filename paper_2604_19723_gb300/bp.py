@@ -29,7 +29,8 @@ ENTRY_POINTS = ("bp_init", "bp_predict", "bp_update", "bp_estimate", "bp_free", 
                 "bp_batch_sync", "bp_batch_handle", "bp_batch_stream_of", "bp_batch_device_bytes", "bp_batch_free",
                 "bp_batch_last_error", "bp_pcrlb_fim", "bp_pcrlb_recursion",
                 "bp_mlp_create", "bp_mlp_get_params", "bp_mlp_forward", "bp_mlp_grads", "bp_mlp_train_step",
-                "bp_mlp_sync", "bp_mlp_free", "bp_mlp_last_error", "bp_set_mt_proposal", "bp_lp_dataset")
+                "bp_mlp_sync", "bp_mlp_free", "bp_mlp_last_error", "bp_set_mt_proposal", "bp_lp_dataset",
+                "bp_selftest_wait")
 PROFILE_STAGES = ("predict", "row_sums", "table", "stage", "kappa", "iota", "nu", "normalize", "resample")
 
 
@@ -141,6 +142,7 @@ def load() -> C.CDLL:
     lib.bp_mlp_last_error.argtypes = [vp]
     lib.bp_mlp_last_error.restype = C.c_char_p
     lib.bp_set_mt_proposal.argtypes = [vp, vp]
+    lib.bp_selftest_wait.argtypes = [C.c_int, vp]
     lib.bp_lp_dataset.argtypes = [C.POINTER(_Geometry), C.POINTER(_Params), C.c_int, C.POINTER(C.c_double),
                                   C.POINTER(C.c_double), C.c_double, C.c_int] + [C.c_double] * 4 + \
                                  [C.c_int, C.c_uint64, vp, vp, vp]
@@ -574,6 +576,13 @@ class Mlp:
             self.close()
         except Exception:
             pass
+
+
+def selftest_wait(limit: int = 4096, stream=None) -> int:
+    """bp_selftest_wait: the status of a bounded wait on a phase nothing completes
+    (BP_ERR_TIMEOUT expected)."""
+    lib = load()
+    return int(lib.bp_selftest_wait(int(limit), C.c_void_p(_stream_handle(stream))))
 
 
 NOALLOC_MAX_P = 1 << 20
