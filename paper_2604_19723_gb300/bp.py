@@ -197,7 +197,7 @@ class Filter:
 
     def __init__(self, geom: Geometry, params: Params, P: int, S_max: int, seed: int, stream=None):
         self.lib = load()
-        self.geom, self.params, self.P, self.S_max = geom, params, P, S_max
+        self.geom, self.params, self.P, self.S_max, self.seed = geom, params, P, S_max, seed
         self._g = _GeomHolder(geom)
         self._p = _params_struct(params)
         self.stream = _stream_handle(stream)
@@ -282,6 +282,25 @@ class Filter:
                  p_pr=np.ascontiguousarray(st.p_pr, np.float64))
         v = self._struct(st.n, st.S, a)
         _check(self.lib, self.h, self.lib.bp_set_state(self.h, C.byref(v)), "bp_set_state")
+
+    def save(self, path: str):
+        """Checkpoint: the belief state (particles, weights, existences, step index), P,
+        S_max and the seed to an .npz file.  A filter restored with `Filter.load` on the
+        same geometry and parameters continues with the same Philox streams (keyed by
+        seed and step)."""
+        st = self.get_state()
+        np.savez(path, n=st.n, S=st.S, x=st.x, phi=st.phi, eta=st.eta, w_x=st.w_x, w_y=st.w_y, w_eta=st.w_eta,
+                 p_pr=st.p_pr, P=self.P, S_max=self.S_max, seed=self.seed)
+
+    @classmethod
+    def load(cls, path: str, geom: Geometry, params: Params, stream=None) -> "Filter":
+        """Restores a checkpoint written by `save` into a new filter on the given geometry
+        and parameters (those the checkpoint was taken with)."""
+        d = np.load(path)
+        f = cls(geom, params, P=int(d["P"]), S_max=int(d["S_max"]), seed=int(d["seed"]), stream=stream)
+        f.set_state(StateArrays(n=int(d["n"]), S=int(d["S"]), x=d["x"], phi=d["phi"], eta=d["eta"], w_x=d["w_x"],
+                                w_y=d["w_y"], w_eta=d["w_eta"], p_pr=d["p_pr"]))
+        return f
 
     def get_predicted(self) -> Dict:
         a = self._view(self.S_max)

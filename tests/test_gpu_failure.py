@@ -45,3 +45,33 @@ def test_invalid_arguments_are_status_codes():
     with pytest.raises(bp.BPError) as e:
         bp.Filter(g, W.Params(motion_dims=5), P=16, S_max=8, seed=1)
     assert e.value.status == 1
+
+
+def test_checkpoint_and_resume_continue_the_same_run(tmp_path):
+    """A filter restored from a checkpoint after step 2 gives the estimates of the
+    uninterrupted run at steps 3 and 4 (same Philox streams, keyed by seed and step)."""
+    g = W.make_geometry(J=2, Nf=4, My=2, Mz=2)
+    prm = W.Params(Q=1)
+    scn = W.make_scenario(g, prm, N=5, K=3, seed=81)
+    eta = synth.noise_variance(scn)
+    zs = [torch.from_numpy(synth.observe(scn, n, eta, 82 + n).astype(np.complex64)).cuda() for n in range(1, 5)]
+    st = W.state_near_truth(scn, P=512, S=3, n=0, seed=83, eta_true=eta)
+    f = bp.Filter(g, prm, P=512, S_max=8, seed=84)
+    f.set_state(st)
+    for n in range(2):
+        f.step(zs[n])
+    path = str(tmp_path / "ckpt.npz")
+    f.save(path)
+    ref = []
+    for n in range(2, 4):
+        f.step(zs[n])
+        ref.append(f.estimate())
+    f.close()
+    r = bp.Filter.load(path, g, prm)
+    for n in range(2, 4):
+        r.step(zs[n])
+        e = r.estimate()
+        assert e["n"] == ref[n - 2]["n"] and e["S"] == ref[n - 2]["S"]
+        assert np.allclose(e["x_hat"], ref[n - 2]["x_hat"], rtol=0, atol=1e-9)
+        assert np.allclose(e["p_s"], ref[n - 2]["p_s"], rtol=0, atol=1e-9)
+    r.close()
