@@ -6,6 +6,8 @@
 #include <vector>
 #include <algorithm>
 
+#include <nvtx3/nvToolsExt.h>
+
 #include "bp_handle.cuh"
 
 using namespace bp;
@@ -34,8 +36,20 @@ static bool dalloc(bp_handle* h, T** p, size_t count) {
     return true;
 }
 
+// stage boundaries: CUDA events when profiling is on, and NVTX ranges (named like the
+// profile stages) around the launches of each stage for tools that attach
+static const char* const kStageNames[BP_PROF_STAGES] = {"bp.predict", "bp.row_sums", "bp.table", "bp.stage",
+                                                        "bp.kappa",   "bp.iota",     "bp.nu",    "bp.normalize",
+                                                        "bp.resample"};
 static void mark(bp_handle* h, int stage) {
     if (h->prof_on) cudaEventRecord(h->ev[stage], h->st);
+    if (h->nvtx_open) nvtxRangePop();
+    nvtxRangePushA(kStageNames[stage]);
+    h->nvtx_open = true;
+}
+static void mark_end(bp_handle* h) {
+    if (h->nvtx_open) nvtxRangePop();
+    h->nvtx_open = false;
 }
 
 static int sc_bucket(int S) { return S <= 8 ? 8 : S <= 16 ? 16 : S <= 32 ? 32 : 64; }
@@ -551,6 +565,7 @@ void predict_enqueue(bp_handle* h) {
     h->S = S_new;
     h->n += 1;
     h->phase = 1;
+    mark_end(h);
 }
 
 void update_enqueue(bp_handle* h, const float* z_dev) {
@@ -590,6 +605,7 @@ void update_enqueue(bp_handle* h, const float* z_dev) {
     h->S_upd = S;
     h->phase = 0;
     if (dynamic_pf_count(h)) cudaMemcpyAsync(h->h_ctrl, D.ctrl, 4 * sizeof(int), cudaMemcpyDeviceToHost, h->st);
+    mark_end(h);
 }
 
 void update_finish(bp_handle* h) {

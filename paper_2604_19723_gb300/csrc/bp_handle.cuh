@@ -55,6 +55,7 @@ struct bp_handle {
     double* lp_logr;    // P log importance ratios of the last update
     double* lp_buf;     // predicted mean (6), per-PA correlations (4 J)
     int prof_on;
+    bool nvtx_open;     // an NVTX stage range is open on this thread
     cudaEvent_t ev[BP_PROF_STAGES + 1];
     bool ev_valid[BP_PROF_STAGES];
     std::vector<void*> allocs;
