@@ -152,7 +152,11 @@ bp_status bp_predict(bp_handle* h);
  * duration on the handle's stream. */
 bp_status bp_update(bp_handle* h, const float* z_dev);
 
-/* Copies the estimates of the last bp_update to the host.  Synchronous. */
+/* Copies the estimates of the last bp_update to the host.  Synchronous.  Returns
+ * BP_ERR_NUMERIC when every MT weight underflowed, or when the observation of the last
+ * update held NaN or Inf (bp_last_error says which; the state is then invalid and a
+ * checkpoint should be restored), BP_ERR_TIMEOUT when a bounded tensor-core wait of the
+ * update gave up. */
 bp_status bp_estimate(bp_handle* h, bp_estimate_out* out);
 
 /* Releases every device buffer of the handle.  Synchronous. */

@@ -171,6 +171,8 @@ bp_status bp_estimate(bp_handle* h, bp_estimate_out* o) {
     if (o->phi_hat) for (int s = 0; s < 6 * S; ++s) o->phi_hat[s] = e[E.phi_hat() + s];
     if (o->p_pr) for (int s = 0; s < S * h->J; ++s) o->p_pr[s] = e[E.p_pr() + s];
     if (o->declared) for (int s = 0; s < S; ++s) o->declared[s] = e[E.declared() + s] != 0.0;
+    if ((int)e[E.status()] == EST_STATUS_BAD_Z)
+        return fail(h, BP_ERR_NUMERIC, "the observation of the last update holds NaN or Inf (the state is invalid)");
     if ((int)e[E.status()] == BP_ERR_NUMERIC) return fail(h, BP_ERR_NUMERIC, "all MT weights underflowed");
     return BP_OK;
 }

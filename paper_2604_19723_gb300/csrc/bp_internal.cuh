@@ -73,6 +73,9 @@ enum : uint32_t {
     RNG_LEARNED_PROP = 15, RNG_LP_DATA = 16
 };
 constexpr int MAX_GAMMA_ATTEMPTS = 16;
+// estimate status: the observation of the last update held NaN or Inf (reported as
+// BP_ERR_NUMERIC with its own message)
+constexpr int EST_STATUS_BAD_Z = 100;
 
 __device__ inline U4 draw(const DevParams& P, uint32_t item, uint32_t n, uint32_t purpose, uint32_t sub, uint32_t block) {
     return philox(item, n, (purpose << 16) | (sub & 0xFFFFu), block, P.key0, P.key1);

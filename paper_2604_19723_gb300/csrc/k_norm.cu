@@ -223,6 +223,9 @@ __global__ void k_estimate(DevGeom G, DevParams Pm, DevState D, int S) {
     est[E.skipped()] = D.ctrl[2];
     int status = 0;
     if (!(r0[2] > -INFINITY)) status = BP_ERR_NUMERIC;
+    // a NaN or Inf in z reaches |e|^2 of its PA first; report it as such
+    for (int j = 0; j < J; ++j)
+        if (!isfinite(D.nu_c[2 * j])) status = EST_STATUS_BAD_Z;
     est[E.status()] = status;
     D.ctrl[3] = status;
 }

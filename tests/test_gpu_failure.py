@@ -75,3 +75,20 @@ def test_checkpoint_and_resume_continue_the_same_run(tmp_path):
         assert np.allclose(e["x_hat"], ref[n - 2]["x_hat"], rtol=0, atol=1e-9)
         assert np.allclose(e["p_s"], ref[n - 2]["p_s"], rtol=0, atol=1e-9)
     r.close()
+
+
+def test_non_finite_observation_is_reported():
+    g = W.make_geometry(J=2, Nf=4, My=2, Mz=2)
+    prm = W.Params()
+    scn = W.make_scenario(g, prm, N=2, K=3, seed=91)
+    eta = synth.noise_variance(scn)
+    z = synth.observe(scn, 1, eta, 92).astype(np.complex64)
+    z[1, 3] = np.nan
+    st = W.state_near_truth(scn, P=256, S=3, n=0, seed=93, eta_true=eta)
+    f = bp.Filter(g, prm, P=256, S_max=8, seed=94)
+    f.set_state(st)
+    f.step(torch.from_numpy(z).cuda())
+    with pytest.raises(bp.BPError) as e:
+        f.estimate()
+    assert e.value.status == 4 and "NaN or Inf" in str(e.value)
+    f.close()
