@@ -411,7 +411,9 @@ def run_gpu(args, rank, world):
     if rank == 0 and not args.no_cpu_baseline:
         out["cpu_baseline"] = cpu_baseline(wl, g, prm, scn, args.cpu_particles, z_all[:1].cpu().numpy())
     f.close()
-    if rank == 0 and world == 1 and not args.no_matched:
+    # the matched-accuracy comparison rides on the headline line only (default workload
+    # at its full particle count)
+    if rank == 0 and world == 1 and not args.no_matched and args.workload == "scale_64x100k" and P == wl["P"]:
         out["matched_accuracy"] = matched_accuracy()
     if rank == 0:
         print(json.dumps(out))
