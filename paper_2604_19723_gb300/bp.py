@@ -15,7 +15,8 @@ import numpy as np
 from .workload import Geometry, Params, StateArrays
 
 _HERE = os.path.dirname(os.path.abspath(__file__))
-LIB_PATH = os.path.join(_HERE, "_lib", "libbp.so")
+# BP_CHECKED=1 selects the checked build (device-side index checks; `build --checked`)
+LIB_PATH = os.path.join(_HERE, "_lib", "libbp_checked.so" if os.environ.get("BP_CHECKED") == "1" else "libbp.so")
 
 BP_OK = 0
 STATUS = {0: "BP_OK", 1: "BP_ERR_INVALID_ARG", 2: "BP_ERR_CUDA", 3: "BP_ERR_CAPACITY",

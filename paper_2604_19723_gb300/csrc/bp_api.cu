@@ -154,7 +154,10 @@ bp_status bp_estimate(bp_handle* h, bp_estimate_out* o) {
         cudaStreamSynchronize(h->st) != cudaSuccess)
         return fail(h, BP_ERR_CUDA, std::string("bp_estimate: ") + cudaGetErrorString(cudaGetLastError()));
     if (*kerr_host != 0) {
+        const int k = *kerr_host;
         cudaMemsetAsync(h->D.kerr, 0, sizeof(int), h->st);
+        if (k & KERR_INDEX)
+            return fail(h, BP_ERR_STATE, "bp_estimate: a device index check failed in the last step (checked build)");
         return fail(h, BP_ERR_TIMEOUT, "bp_estimate: a tensor-core wait of the last update gave up (results invalid)");
     }
     const double* e = h->h_est;

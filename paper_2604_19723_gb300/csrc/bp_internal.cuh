@@ -73,6 +73,22 @@ enum : uint32_t {
     RNG_LEARNED_PROP = 15, RNG_LP_DATA = 16
 };
 constexpr int MAX_GAMMA_ATTEMPTS = 16;
+// Range check of a data-dependent index (checked builds, -DBP_CHECKED): a failed check
+// raises bit 2 of the kernel error word, which bp_estimate reports, and the caller skips
+// the access.  In normal builds the check compiles away.
+constexpr int KERR_TIMEOUT = 1, KERR_INDEX = 2;
+__device__ __forceinline__ bool bp_in_range(long long i, long long n, int* kerr) {
+#ifdef BP_CHECKED
+    if (i < 0 || i >= n) {
+        atomicOr(kerr, KERR_INDEX);
+        return false;
+    }
+#else
+    (void)i; (void)n; (void)kerr;
+#endif
+    return true;
+}
+
 // estimate status: the observation of the last update held NaN or Inf (reported as
 // BP_ERR_NUMERIC with its own message)
 constexpr int EST_STATUS_BAD_Z = 100;

@@ -785,7 +785,7 @@ __global__ void k_iota(DevGeom G, DevParams Pm, DevState D, int S, const float* 
         D.lw_x[p] = total;
         if (sqrtf(ratio2) > IOTA_RATIO_MAX) {
             const int slot = atomicAdd(&D.flags[0], 1);
-            D.flags[1 + slot] = p;
+            if (bp_in_range(slot, P, D.kerr)) D.flags[1 + slot] = p;
         }
     }
 }

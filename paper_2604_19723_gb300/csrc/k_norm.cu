@@ -267,7 +267,10 @@ __global__ void __launch_bounds__(1024) k_resample(DevGeom G, DevParams Pm, DevS
     const int a = blockIdx.x;   // 0: MT, 1..S_next: kept PF, then eta
     int b, kind, index;
     if (a == 0) { b = 0; kind = 0; index = 0; }
-    else if (a <= S_next) { index = D.ctrl[4 + a - 1]; b = 1 + index; kind = 1; }
+    else if (a <= S_next) {
+        index = D.ctrl[4 + a - 1]; b = 1 + index; kind = 1;
+        if (!bp_in_range(index, SM, D.kerr)) return;
+    }
     else if (a <= S_next + J) { index = a - S_next - 1; b = 1 + SM + index; kind = 2; }
     else return;
     const double* w = (kind == 0) ? D.wn_x : (kind == 1) ? D.wn_y + (size_t)index * P : D.wn_eta + (size_t)index * P;
@@ -319,7 +322,8 @@ __global__ void k_gather(DevGeom G, DevParams Pm, DevState D) {
     const int nxt = 1 - D.cur;
     if (i < P) {
         {   // MT
-            const int src = D.idx[i];
+            int src = D.idx[i];
+            if (!bp_in_range(src, P, D.kerr)) src = i;
             const float* L = D.Lchol;
             float e[6];
             normals8(Pm, i, n, RNG_JITTER_MT, 0, 6, e);
@@ -332,7 +336,9 @@ __global__ void k_gather(DevGeom G, DevParams Pm, DevState D) {
         }
         for (int t = 0; t < S_next; ++t) {
             const int s = D.ctrl[4 + t];
-            const int src = D.idx[(size_t)(1 + s) * P + i];
+            if (!bp_in_range(s, SM, D.kerr)) continue;
+            int src = D.idx[(size_t)(1 + s) * P + i];
+            if (!bp_in_range(src, P, D.kerr)) src = i;
             const float* L = D.Lchol + (size_t)(1 + s) * 36;
             float e[6];
             normals8(Pm, i, n, RNG_JITTER_PF, s, 6, e);
@@ -347,7 +353,8 @@ __global__ void k_gather(DevGeom G, DevParams Pm, DevState D) {
             }
         }
         for (int j = 0; j < J; ++j) {
-            const int src = D.idx[(size_t)(1 + SM + j) * P + i];
+            int src = D.idx[(size_t)(1 + SM + j) * P + i];
+            if (!bp_in_range(src, P, D.kerr)) src = i;
             const float L = D.Lchol[(size_t)(1 + SM + j) * 36];
             float e[1];
             normals8(Pm, i, n, RNG_JITTER_ETA, j, 1, e);
@@ -363,14 +370,15 @@ __global__ void k_compact(DevGeom G, DevParams Pm, DevState D) {
     const int S_next = D.ctrl[1];
     const int i = blockIdx.x * blockDim.x + threadIdx.x;
     __shared__ double ps_new[S_CAP_MAX];
-    if (threadIdx.x < S_next) ps_new[threadIdx.x] = D.p_s[D.ctrl[4 + threadIdx.x]];
+    if (threadIdx.x < S_next && bp_in_range(D.ctrl[4 + threadIdx.x], Pm.S_max, D.kerr))
+        ps_new[threadIdx.x] = D.p_s[D.ctrl[4 + threadIdx.x]];
     __syncthreads();
     if (i < P)
         for (int t = 0; t < S_next; ++t) D.w_y[(size_t)t * P + i] = ps_new[t] / P;
     if (blockIdx.x == 0)
         for (int u = threadIdx.x; u < S_next * J; u += blockDim.x) {
             const int t = u / J, j = u - t * J;
-            D.p_pr[t * J + j] = D.bel[BEL_PPR + D.ctrl[4 + t] * J + j];
+            if (bp_in_range(D.ctrl[4 + t], Pm.S_max, D.kerr)) D.p_pr[t * J + j] = D.bel[BEL_PPR + D.ctrl[4 + t] * J + j];
         }
 }
 
