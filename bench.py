@@ -91,11 +91,11 @@ def a5_flops(P, S, J, Nz):
 # a single-pass metric set, at the full size of the workload), valid while the kernel
 # sources hash to the recorded value.
 TRAFFIC_RECORDS = {
-    "k_kappa": {"workload": "scale_64x100k", "P": 100000, "bytes": 925.29e6,
-                "sources_sha256": "2fb49d414c53b1b368751a34d26b3f70920dd6298c5131b4d682ce6c1eed78b2",
+    "k_kappa": {"workload": "scale_64x100k", "P": 100000, "bytes": 923.59e6,
+                "sources_sha256": "a28bd4669d6f629dd45eb990cdfd9b5158b3111be47910162252d5d943efd458",
                 "profile": "profiles/dram_scale_64x100k.md"},
-    "k_iota_blk": {"workload": "scale_64x100k", "P": 100000, "bytes": 708.84e6,
-                   "sources_sha256": "2fb49d414c53b1b368751a34d26b3f70920dd6298c5131b4d682ce6c1eed78b2",
+    "k_iota_blk": {"workload": "scale_64x100k", "P": 100000, "bytes": 710.10e6,
+                   "sources_sha256": "a28bd4669d6f629dd45eb990cdfd9b5158b3111be47910162252d5d943efd458",
                    "profile": "profiles/dram_scale_64x100k.md"},
 }
 KERNEL_SOURCES = ("paper_2604_19723_gb300/csrc/k_like.cu", "paper_2604_19723_gb300/csrc/bp_kernels.cuh",
