@@ -397,6 +397,91 @@ def test_belief_normalisation_invariants():
         assert lhs == pytest.approx(1.0, abs=1e-12)
 
 
+def _real_cn_logpdf(z, m, C):
+    """log CN(z; m, C) as the real 2N-dim normal of [Re z, Im z] (scipy), independent of the oracle."""
+    Cr = 0.5 * np.block([[C.real, -C.imag], [C.imag, C.real]])
+    return st.multivariate_normal(mean=np.r_[m.real, m.imag], cov=Cr).logpdf(np.r_[z.real, z.imag])
+
+
+@pytest.mark.parametrize("W_s,J", [(0.5, 1), (0.2, 2), (0.85, 2)])
+def test_existence_posterior_is_the_bernoulli_posterior_for_a_point_mass(W_s, J):
+    """Sec. S-IV null term of C_y,s: one PF (the LoS), zeta = 1 on every PA, and every
+    belief a point mass (MT, PF and noise particles all equal).  Moment matching is then
+    exact, so p_s must be the posterior existence probability of a Bernoulli component
+    with prior W_s:  W prod_j CN(z_j; mu psi_j, eta I + gamma psi_j psi_j^H) /
+    (W prod_j CN(...) + (1 - W) prod_j CN(z_j; 0, eta I)).  Both densities come from the
+    enumeration in brute.mixture_moments with r_s fixed and from scipy's real normal."""
+    P = 5
+    g = W.make_geometry(J=J, Nf=3, My=2, Mz=1)
+    prm = W.Params(Q=0)
+    r = np.random.default_rng(17 + J)
+    x = np.zeros((6, P), np.float32)
+    x[:3] = np.array([0.7, 1.9, 0.1], np.float32)[:, None]
+    phi = np.zeros((1, 6, P), np.float32)
+    phi[0, 3] = 0.3
+    phi[0, 4] = 0.25
+    phi[0, 5] = -0.125
+    eta = np.full((J, P), 0.5, np.float32)
+    pred = model.Predicted(n=1, S=1, x=x, phi=phi, eta=eta, w_beta=np.full(P, 1.0 / P),
+                           w_alpha=np.full((1, P), W_s / P), w_xi=np.full((J, P), 1.0 / P),
+                           zeta=np.ones((1, J)), is_new=np.zeros(1, bool))
+    psi = messages_dense.all_steering(pred, g)          # (S, J, P, Nz)
+    Nz = psi.shape[-1]
+    z = (r.normal(size=(J, Nz)) + 1j * r.normal(size=(J, Nz))) * 0.6
+    msg = messages_dense.update_messages(pred, prm, g, z)
+    bel = beliefs.beliefs(pred, msg)
+    gam = np.array([0.3]); mu = np.array([0.25 - 0.125j])
+    l1 = l0 = 0.0
+    for j in range(J):
+        ps = psi[:, j, 0]
+        m1, C1 = brute.mixture_moments(ps, gam, mu, np.array([W_s]), np.ones(1), 0.5, fixed={("r", 0): 1})
+        m0, C0 = brute.mixture_moments(ps, gam, mu, np.array([W_s]), np.ones(1), 0.5, fixed={("r", 0): 0})
+        l1 += _real_cn_logpdf(z[j], m1, C1)
+        l0 += _real_cn_logpdf(z[j], m0, C0)
+    a = math.log(W_s) + l1
+    b = math.log1p(-W_s) + l0
+    p_exact = 1.0 / (1.0 + math.exp(b - a))
+    assert 1e-3 < p_exact < 1 - 1e-3                     # the case is not saturated
+    assert bel.p_s[0] == pytest.approx(p_exact, abs=1e-10)
+    assert np.allclose(bel.w_y[0], p_exact / P, rtol=1e-9)
+
+
+@pytest.mark.parametrize("dims", [3, 2])
+def test_legacy_pf_random_walk_moments(dims):
+    """Sec. V-A transitions of a legacy PF: p_sfv <- p_sfv + N(0, sigma_sfv^2 I) and
+    mu <- CN(mu, sigma_mu^2), circular with total variance sigma_mu^2 (reading R10).
+    The per-particle increments must have zero mean, covariance sigma_sfv^2 I (the z
+    component held in planar motion), E|d mu|^2 = sigma_mu^2, E[d mu^2] = 0; the LoS
+    slot keeps its (unused) SFV.  Tolerances are 6 Monte Carlo standard errors."""
+    P = 200000
+    prm = W.Params(Q=0, sigma_sfv=0.05, sigma_mu=0.2, motion_dims=dims)
+    r = np.random.default_rng(21)
+    phi = np.zeros((2, 6, P), np.float32)
+    phi[:, :3] = r.normal([[1.0], [2.0], [0.5]], 0.3, size=(2, 3, P)).astype(np.float32)
+    phi[:, 3] = r.uniform(0.5, 1.0, size=(2, P)).astype(np.float32)
+    phi[:, 4] = r.normal(0.3, 0.1, size=(2, P)).astype(np.float32)
+    phi[:, 5] = r.normal(-0.2, 0.1, size=(2, P)).astype(np.float32)
+    stt = W.StateArrays(n=3, S=2, x=np.zeros((6, P), np.float32), phi=phi,
+                        eta=np.full((1, P), 1e-6, np.float32), w_x=np.full(P, 1.0 / P),
+                        w_y=np.full((2, P), 0.5 / P), w_eta=np.full((1, P), 1.0 / P),
+                        p_pr=np.full((2, 1), 0.5))
+    pred = model.predict(stt, prm, 1, seed=6, S_max=2)
+    d = pred.phi[1].astype(float) - phi[1].astype(float)
+    sd = prm.sigma_sfv
+    k = 3 if dims == 3 else 2
+    assert np.all(np.abs(d[:k].mean(1)) < 6 * sd / math.sqrt(P))
+    C = np.cov(d[:k])
+    assert np.all(np.abs(C - sd * sd * np.eye(k)) < 6 * sd * sd * math.sqrt(2.0 / P))
+    if dims == 2:
+        assert np.all(d[2] == 0.0)
+    dmu = d[4] + 1j * d[5]
+    s2 = prm.sigma_mu ** 2
+    assert abs(dmu.mean()) < 6 * prm.sigma_mu / math.sqrt(P)
+    assert abs(np.mean(np.abs(dmu) ** 2) - s2) < 6 * s2 / math.sqrt(P)
+    assert abs(np.mean(dmu * dmu)) < 6 * s2 / math.sqrt(P)
+    assert np.all(pred.phi[0, :3] == phi[0, :3])        # LoS: no SFV random walk
+
+
 def test_pr_existence_logistic_equals_ratio():
     """Sec. S-VI: sigma(log-odds + log-LR) equals eq. (PR-normalization)."""
     r = np.random.default_rng(3)
