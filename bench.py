@@ -37,7 +37,6 @@ METRIC = "particle-measurement updates/sec and steps/sec at matched OSPA vs plai
 PAPER_UPDATES_PER_S = {"paper_exp1": 30000 * 4 / 0.420}
 UNIT = "(particle, PA) updates/s"
 FP32_LANES_PER_SM = 128
-SMS = 152
 FP64_NOMINAL_TFLOPS = 1.25   # GB300 dense FP64, nominal
 
 
@@ -79,12 +78,6 @@ def iota_flops(P, S, J, Nf, My, Mz):
     per = (S * (S + 1) / 2 * 8 * (Nf + My + Mz + 2) + 8 * S * Nf * (My * Mz + My + 1) + 8 * S * S
            + 8 * S ** 3 / 6 + 8 * S * S + 20 * Nz * S)
     return float(P) * J * per
-
-
-def a5_flops(P, S, J, Nz):
-    """The fused-likelihood step's algorithmic flops in the survey's count (per (j, p):
-    8 Nz S(2S+1) + 4 Nz S(S+1) + 9.3 S^3), for the three likelihood kernels together."""
-    return float(P) * J * (8 * Nz * S * (2 * S + 1) + 4 * Nz * S * (S + 1) + 9.3 * S ** 3)
 
 
 # DRAM bytes per launch from one ncu capture (dram__bytes_read.sum + dram__bytes_write.sum,
@@ -186,6 +179,37 @@ def make_inputs(name, steps, seed_offset=0):
     return wl, g, prm, scn
 
 
+def sm_count(dev=0):
+    """Streaming multiprocessors of the device (from its attributes)."""
+    import torch
+    return int(torch.cuda.get_device_properties(dev).multi_processor_count)
+
+
+def host_cpu():
+    """CPU model name and the number of online cores of this host."""
+    model = None
+    try:
+        with open("/proc/cpuinfo") as fh:
+            for line in fh:
+                k, _, v = line.partition(":")
+                if k.strip() in ("model name", "Model name", "CPU part") and v.strip():
+                    model = v.strip()
+                    if k.strip() != "CPU part":
+                        break
+    except OSError:
+        pass
+    if model is None or model.startswith("0x"):
+        try:
+            out = subprocess.run(["lscpu"], capture_output=True, text=True, timeout=10).stdout
+            for line in out.splitlines():
+                if line.strip().startswith("Model name:"):
+                    model = line.split(":", 1)[1].strip()
+                    break
+        except (OSError, subprocess.SubprocessError):
+            pass
+    return {"cpu_model": model or "unknown", "nproc": os.cpu_count() or 1}
+
+
 def measured_peaks():
     try:
         with open(os.path.join(ROOT, "MEASURED_PEAKS.json")) as f:
@@ -213,7 +237,7 @@ def cpu_baseline(wl, g, prm, scn, sample_P, z_host):
         cores = os.cpu_count() or 1
     return {"value": sample_P * g.J / dt, "unit": UNIT, "cores": cores, "kind": "oracle",
             "sample": f"one predict+update of {sample_P} particles x S={S} x J={g.J} x Nz={g.Nz} "
-                      f"(FP64 Woodbury-mode oracle, {dt:.2f} s)"}
+                      f"(FP64 Woodbury-mode oracle, {dt:.2f} s)", **host_cpu()}
 
 
 def run_reference(args, rank):
@@ -235,7 +259,8 @@ def run_reference(args, rank):
                           "dtype": "f64", "data": "synthetic", "impl": "reference",
                           "config": {"workload": "batched", "scenarios": len(sc),
                                      "parallelism": "oracle on the host cores", "sample": smp},
-                          "cpu_baseline": {"value": value, "unit": UNIT, "cores": cores, "kind": "oracle", "sample": smp},
+                          "cpu_baseline": {"value": value, "unit": UNIT, "cores": cores, "kind": "oracle", "sample": smp,
+                                           **host_cpu()},
                           "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}))
         return
     wl, g, prm, scn = make_inputs(args.workload, args.warmup + args.steps)
@@ -265,7 +290,7 @@ def run_reference(args, rank):
                       "parallelism": "oracle on the host cores",
                       "sample": f"{Ps} of the workload's {wl['P']} particles per step; value = sample updates / time"},
            "cpu_baseline": {"value": value, "unit": UNIT, "cores": cores, "kind": "oracle",
-                            "sample": f"{Ps} particles per step, FP64 Woodbury-mode oracle"},
+                            "sample": f"{Ps} particles per step, FP64 Woodbury-mode oracle", **host_cpu()},
            "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
     print(json.dumps(out))
 
@@ -348,6 +373,7 @@ def run_gpu(args, rank, world):
     clocks = clk.summary()
     peaks = measured_peaks()
     sm_mhz = clocks.get("sm_mhz") or peaks.get("sm_max_mhz", 2070.0)
+    SMS = sm_count(dev)
     peak_alu = SMS * FP32_LANES_PER_SM * 2 * sm_mhz * 1e6 / 1e12
     # roofline of the dominant kernel (by its measured time in this run)
     k_ms, i_ms = float(np.mean(kappa_ms)), float(np.mean(iota_ms))
@@ -362,7 +388,7 @@ def run_gpu(args, rank, world):
         r = {"bound": "alu", "kernel": label, "achieved": a, "peak": peak_alu, "unit": "TFLOP/s",
              "frac": a / peak_alu, "traffic": traffic_for(name, args.workload, P), "ms_per_launch": ms,
              "peak_basis": f"FP32 FMA lanes: {SMS} SMs x {FP32_LANES_PER_SM} x 2 flop x {sm_mhz:.0f} MHz "
-                           f"(median sampled); derived, not in MEASURED_PEAKS.json"}
+                           f"(median sampled; SM count from the device); derived, not in MEASURED_PEAKS.json"}
         if name == "k_iota_blk":
             # the same algorithmic flops against the nominal FP64 rate, the precision class the
             # log determinant needs (the kernel emulates it with FP32 operations)
@@ -386,8 +412,6 @@ def run_gpu(args, rank, world):
         return r
     dominant = max(per_kernel, key=lambda n: per_kernel[n][0])
     other = "k_iota_blk" if dominant == "k_kappa" else "k_kappa"
-    a5_ms = k_ms + i_ms + prof_tot.get("nu", 0.0) / args.steps
-    a5_ach = a5_flops(P, S, g.J, g.Nz) / (a5_ms * 1e-3) / 1e12
     out = {"metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
            "warmup": args.warmup, "ms_per_step": t_step, "steps_per_s": 1e3 / t_step,
            "higher_is_better": True, "scaling": "weak",
@@ -401,9 +425,6 @@ def run_gpu(args, rank, world):
            "stage_ms": {k: v / args.steps for k, v in prof_tot.items()},
            "roofline": roof(dominant),
            "roofline_next_kernel": roof(other),
-           "roofline_a5_fused": {"bound": "alu", "kernels": "k_kappa + k_iota_blk + k_nu",
-                                 "achieved": a5_ach, "peak": peak_alu, "unit": "TFLOP/s", "frac": a5_ach / peak_alu,
-                                 "flops_basis": "P J [8 Nz S(2S+1) + 4 Nz S(S+1) + 9.3 S^3]"},
            "e2e": {"value": world * P * g.J / (t_e2e * 1e-3), "unit": UNIT, "h2d_bytes_per_step": h2d,
                    "d2h_bytes_per_step": d2h, "ms_per_step": t_e2e},
            "gpu_launches": int(launches), "clocks": clocks,
@@ -576,6 +597,7 @@ def run_batched(args, rank, world):
 
     peaks = measured_peaks()
     sm_mhz = clocks.get("sm_mhz") or peaks.get("sm_max_mhz", 2070.0)
+    SMS = sm_count(dev)
     peak_alu = SMS * FP32_LANES_PER_SM * 2 * sm_mhz * 1e6 / 1e12
     fl = sum(kappa_flops(d["P"], d["S"], d["geom"].J, d["geom"].Nz) +
              iota_flops(d["P"], d["S"], d["geom"].J, d["geom"].Nf, d["geom"].My, d["geom"].Mz) for d in sc)
@@ -610,7 +632,7 @@ def run_batched(args, rank, world):
         cores = os.cpu_count() or 1
         out["cpu_baseline"] = {"value": v, "unit": UNIT, "cores": cores, "kind": "oracle",
                                "sample": f"one predict+update of {args.cpu_particles // 4} particles of each of the "
-                                         f"first 4 scenarios (FP64 Woodbury-mode oracle, {t:.2f} s)"}
+                                         f"first 4 scenarios (FP64 Woodbury-mode oracle, {t:.2f} s)", **host_cpu()}
     if rank == 0:
         print(json.dumps(out))
 

@@ -255,7 +255,9 @@ bp_status bp_get_profile(bp_handle* h, double* ms, int n);
  * contents (the first P entries are overwritten before use); calls whose
  * kernels may overlap on the GPU race and must be serialised by the caller.
  * Returns BP_ERR_INVALID_ARG for NULL pointers or out-of-range arguments,
- * BP_ERR_CUDA if the device address lookup or the launch fails. */
+ * BP_ERR_CUDA if the device address lookup or the launch fails, or if a CUDA
+ * error was already pending on entry (nothing is launched then, and the
+ * pending error is left in place for its owner). */
 enum { BP_NOALLOC_MAX_P = 1 << 20 };
 bp_status bp_resample_noalloc(const double* w_dev, int P, uint64_t seed, int n, int kind, int index,
                               int* idx_dev, void* cuda_stream);

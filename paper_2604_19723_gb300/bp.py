@@ -276,7 +276,18 @@ class Filter:
         return StateArrays(n=v.n, S=S, x=a["x"], phi=a["phi"][:S].copy(), eta=a["eta"], w_x=a["w_x"],
                            w_y=a["w_y"][:S].copy(), w_eta=a["w_eta"], p_pr=a["p_pr"][:S].copy())
 
+    def _check_shapes(self, S, shapes):
+        if not 1 <= S <= self.S_max:
+            raise ValueError(f"S = {S} outside 1 .. S_max = {self.S_max}")
+        for name, (arr, want) in shapes.items():
+            if tuple(np.shape(arr)) != want:
+                raise ValueError(f"{name} has shape {tuple(np.shape(arr))}, expected {want}")
+
     def set_state(self, st: StateArrays):
+        J, P, S = self.geom.J, self.P, int(st.S)
+        self._check_shapes(S, dict(x=(st.x, (6, P)), phi=(st.phi, (S, 6, P)), eta=(st.eta, (J, P)),
+                                   w_x=(st.w_x, (P,)), w_y=(st.w_y, (S, P)), w_eta=(st.w_eta, (J, P)),
+                                   p_pr=(st.p_pr, (S, J))))
         a = dict(x=np.ascontiguousarray(st.x, np.float32), phi=np.ascontiguousarray(st.phi, np.float32),
                  eta=np.ascontiguousarray(st.eta, np.float32), w_x=np.ascontiguousarray(st.w_x, np.float64),
                  w_y=np.ascontiguousarray(st.w_y, np.float64), w_eta=np.ascontiguousarray(st.w_eta, np.float64),
@@ -286,18 +297,25 @@ class Filter:
 
     def save(self, path: str):
         """Checkpoint: the belief state (particles, weights, existences, step index), P,
-        S_max and the seed to an .npz file.  A filter restored with `Filter.load` on the
-        same geometry and parameters continues with the same Philox streams (keyed by
-        seed and step)."""
+        S_max, the seed and the geometry's J and Nz to an .npz file.  A filter restored
+        with `Filter.load` on the same geometry and parameters continues with the same
+        Philox streams (keyed by seed and step).  A learned MT proposal is not part of
+        the checkpoint: save() refuses while one is attached (attach it again after
+        load, then save the network's parameters with the network)."""
+        if getattr(self, "_lp_net", None) is not None:
+            raise RuntimeError("save(): a learned MT proposal is attached; it is not part of the checkpoint")
         st = self.get_state()
         np.savez(path, n=st.n, S=st.S, x=st.x, phi=st.phi, eta=st.eta, w_x=st.w_x, w_y=st.w_y, w_eta=st.w_eta,
-                 p_pr=st.p_pr, P=self.P, S_max=self.S_max, seed=self.seed)
+                 p_pr=st.p_pr, P=self.P, S_max=self.S_max, seed=self.seed, J=self.geom.J, Nz=self.geom.Nz)
 
     @classmethod
     def load(cls, path: str, geom: Geometry, params: Params, stream=None) -> "Filter":
         """Restores a checkpoint written by `save` into a new filter on the given geometry
         and parameters (those the checkpoint was taken with)."""
         d = np.load(path)
+        if "J" not in d or int(d["J"]) != geom.J or int(d["Nz"]) != geom.Nz:
+            raise ValueError(f"checkpoint {path} was taken on another geometry "
+                             f"(J, Nz = {d.get('J')}, {d.get('Nz')}; here {geom.J}, {geom.Nz})")
         f = cls(geom, params, P=int(d["P"]), S_max=int(d["S_max"]), seed=int(d["seed"]), stream=stream)
         f.set_state(StateArrays(n=int(d["n"]), S=int(d["S"]), x=d["x"], phi=d["phi"], eta=d["eta"], w_x=d["w_x"],
                                 w_y=d["w_y"], w_eta=d["w_eta"], p_pr=d["p_pr"]))
@@ -612,12 +630,19 @@ def resample_noalloc(w, seed: int, n: int, kind: int, index: int, out=None, stre
     """Systematic resampling through bp_resample_noalloc (no device allocation inside
     the library).  w: torch CUDA float64 tensor of P weights; returns int32 indices."""
     import torch
+    if not (isinstance(w, torch.Tensor) and w.is_cuda and w.dtype == torch.float64 and w.dim() == 1
+            and w.is_contiguous()):
+        raise TypeError("resample_noalloc: w must be a 1-D contiguous CUDA float64 tensor")
     lib = load()
     P = int(w.numel())
     if out is None:
         out = torch.empty(P, dtype=torch.int32, device=w.device)
-    st = lib.bp_resample_noalloc(C.c_void_p(w.data_ptr()), P, C.c_uint64(seed), n, kind, index,
-                                 C.c_void_p(out.data_ptr()), C.c_void_p(_stream_handle(stream)))
+    elif not (isinstance(out, torch.Tensor) and out.device == w.device and out.dtype == torch.int32
+              and out.is_contiguous() and out.numel() >= P):
+        raise TypeError("resample_noalloc: out must be a contiguous int32 tensor of >= P elements on w's device")
+    with torch.cuda.device(w.device):
+        st = lib.bp_resample_noalloc(C.c_void_p(w.data_ptr()), P, C.c_uint64(seed), n, kind, index,
+                                     C.c_void_p(out.data_ptr()), C.c_void_p(_stream_handle(stream)))
     if st != BP_OK:
         raise BPError(st, "bp_resample_noalloc" + (f": P = {P} exceeds {NOALLOC_MAX_P}" if st == 3 else ""))
     return out

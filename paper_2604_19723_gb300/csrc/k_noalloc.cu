@@ -94,6 +94,9 @@ bp_status bp_resample_noalloc(const double* w_dev, int P, uint64_t seed, int n, 
         }
         cdf = g_noalloc_ptr[dev];
     }
+    // an error left pending by earlier work is not this call's: report it without
+    // launching, and leave it for its owner to read
+    if (cudaPeekAtLastError() != cudaSuccess) return BP_ERR_CUDA;
     const uint32_t item = ((uint32_t)kind << 16) | (uint32_t)index;
     k_resample_noalloc<<<1, 1024, 0, static_cast<cudaStream_t>(cuda_stream)>>>(
         w_dev, P, (uint32_t)(seed & 0xFFFFFFFFu), (uint32_t)(seed >> 32), (uint32_t)n, item, cdf, idx_dev);

@@ -40,3 +40,14 @@ def test_binding_lists_every_symbol():
 
 def test_last_error_without_handle(lib):
     assert lib.bp_last_error(None) is not None
+
+
+def test_noalloc_binding_rejects_bad_tensors_on_the_host():
+    """resample_noalloc checks its tensors before any library call: a float32, a
+    strided or a host tensor never reaches the kernel (which reads 8P bytes)."""
+    torch = pytest.importorskip("torch")
+    from paper_2604_19723_gb300 import bp
+    for w in (torch.ones(10, dtype=torch.float32), torch.ones(20, dtype=torch.float64)[::2],
+              torch.ones(10, dtype=torch.float64)):
+        with pytest.raises(TypeError):
+            bp.resample_noalloc(w, 1, 1, 0, 0)

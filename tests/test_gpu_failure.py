@@ -67,7 +67,14 @@ def test_checkpoint_and_resume_continue_the_same_run(tmp_path):
         f.step(zs[n])
         ref.append(f.estimate())
     f.close()
+    g2 = W.make_geometry(J=3, Nf=4, My=2, Mz=2)
+    with pytest.raises(ValueError, match="another geometry"):
+        bp.Filter.load(path, g2, prm)
     r = bp.Filter.load(path, g, prm)
+    bad = r.get_state()
+    bad.eta = bad.eta[:1]
+    with pytest.raises(ValueError, match="eta has shape"):
+        r.set_state(bad)
     for n in range(2, 4):
         r.step(zs[n])
         e = r.estimate()

@@ -58,6 +58,25 @@ def test_noalloc_resampler_matches_update_path():
     f.close()
 
 
+def test_noalloc_smaller_call_after_larger_on_a_side_stream():
+    """The static scratch keeps the previous call's contents: a P = 3000 call after a
+    P = 5000 call must not see the larger call's cumulative weights.  Both run on a
+    non-default stream; the indices equal the plain systematic rule on the host."""
+    r = np.random.default_rng(65)
+    s = torch.cuda.Stream()
+    for P in (5000, 3000):
+        w_host = r.gamma(0.4, size=P)
+        w = torch.from_numpy(w_host).cuda()
+        with torch.cuda.stream(s):
+            idx = bp.resample_noalloc(w, 66, 3, 1, 2, stream=s)
+        s.synchronize()
+        U = ((int(_philox_u0(66, (1 << 16) | 2, 3)) + 0.5) * 2.0 ** -32)
+        c = np.cumsum(w_host) / np.sum(w_host)
+        c[-1] = 1.0
+        ref = np.searchsorted(c, (U + np.arange(P)) / P, side="left")
+        _check(idx.cpu().numpy(), ref, w_host, U)
+
+
 def test_noalloc_rejects_capacity():
     w = torch.ones(bp.NOALLOC_MAX_P + 1, dtype=torch.float64, device="cuda")
     with pytest.raises(bp.BPError) as e:
