@@ -194,9 +194,13 @@ bp_status bp_set_predicted(bp_handle* h, const bp_state_view* in);
  * what = BP_DIAG_LPROP (a proposal network attached): the predicted mean xbar (6) and
  *        the per-PA correlations (Re, Im of psi_j(xbar)^H z_j, |z_j|^2, |psi_j|^2) for
  *        J PAs (double), the log importance ratios (P, double), the network inputs and
- *        outputs (P x 16 each, float).  BP_ERR_STATE without a network. */
+ *        outputs (P x 16 each, float).  BP_ERR_STATE without a network.
+ * what = BP_DIAG_IOTA (S >= 24 in the last update): the particles evaluated in
+ *        float-float, int32 [1 + P] (count, then their indices), and the error bound
+ *        (nats) of every particle's FP32 log iota sum, float [P].  The log iota of a
+ *        particle not in the list is its FP32 value (BP_DIAG_LOGLIK). */
 enum { BP_DIAG_TABLE = 1, BP_DIAG_WEIGHTS = 2, BP_DIAG_LOGLIK = 3, BP_DIAG_INDICES = 4, BP_DIAG_PROPOSAL = 5,
-       BP_DIAG_LPROP = 6 };
+       BP_DIAG_LPROP = 6, BP_DIAG_IOTA = 7 };
 bp_status bp_get_diag(bp_handle* h, int what, void* host, size_t bytes);
 
 /* Synthetic observations from the generative model (eq. observation-generative),

@@ -21,7 +21,7 @@ LIB_PATH = os.path.join(_HERE, "_lib", "libbp_checked.so" if os.environ.get("BP_
 BP_OK = 0
 STATUS = {0: "BP_OK", 1: "BP_ERR_INVALID_ARG", 2: "BP_ERR_CUDA", 3: "BP_ERR_CAPACITY",
           4: "BP_ERR_NUMERIC", 5: "BP_ERR_TIMEOUT", 6: "BP_ERR_STATE"}
-DIAG_TABLE, DIAG_WEIGHTS, DIAG_LOGLIK, DIAG_INDICES, DIAG_PROPOSAL, DIAG_LPROP = 1, 2, 3, 4, 5, 6
+DIAG_TABLE, DIAG_WEIGHTS, DIAG_LOGLIK, DIAG_INDICES, DIAG_PROPOSAL, DIAG_LPROP, DIAG_IOTA = 1, 2, 3, 4, 5, 6, 7
 
 ENTRY_POINTS = ("bp_init", "bp_predict", "bp_update", "bp_estimate", "bp_free", "bp_last_error",
                 "bp_get_state", "bp_set_state", "bp_get_predicted", "bp_set_predicted", "bp_get_diag",
@@ -376,6 +376,15 @@ class Filter:
         ln = b[o:o + J * P].reshape(J, P); o += J * P
         lw = b[o:o + S * J].reshape(S, J)
         return dict(log_iota=li, delta_kappa=lk, log_nu=ln, llr_omega=lw)
+
+    def diag_iota(self) -> Dict:
+        """The particles whose log iota was evaluated in float-float in the last update
+        (S >= 24) and the error bound of every particle's FP32 value (nats)."""
+        P = self.P
+        b = self._diag(DIAG_IOTA, (P + 1) * 4 + P * 4, np.uint8)
+        fl = np.frombuffer(b[:(P + 1) * 4].tobytes(), np.int32)
+        err = np.frombuffer(b[(P + 1) * 4:].tobytes(), np.float32)
+        return dict(selected=np.sort(fl[1:1 + fl[0]]), err=err.copy())
 
     def set_mt_proposal(self, net):
         """Attach a proposal network (Mlp) to this filter, or detach it (None)."""

@@ -274,6 +274,9 @@ bp_status bp_get_diag(bp_handle* h, int what, void* host, size_t bytes) {
         parts.push_back({h->lp_logr, (size_t)P * sizeof(double)});
         parts.push_back({h->lp_X, (size_t)P * 16 * sizeof(float)});
         parts.push_back({h->lp_Y, (size_t)P * 16 * sizeof(float)});
+    } else if (what == BP_DIAG_IOTA) {
+        parts.push_back({D.flags, (size_t)(P + 1) * sizeof(int)});
+        parts.push_back({D.iota_err, (size_t)P * sizeof(float)});
     } else if (what == BP_DIAG_INDICES) {
         parts.push_back({D.idx, (size_t)P * sizeof(int)});
         parts.push_back({D.idx + P, (size_t)S * P * sizeof(int)});
@@ -402,6 +405,7 @@ WsPlan ws_plan(const DevGeom& G, const DevParams& Pm, int SCA, int nsplit_max) {
     w.geo = take(SM * J * PP * sizeof(float4));
     w.geo_lo = take(SM * J * PP * sizeof(float2));
     w.flags = take((PP + 1) * sizeof(int));
+    w.isel = take(256 + PP * sizeof(float));
     w.tab = take(4 * SM * J * Nz * 2 * sizeof(double));
     w.tab_part = take((size_t)nsplit_max * 3 * SM * J * Nz * 2 * sizeof(double));
     w.kV = take(SM * J * Nz * (size_t)SCA * sizeof(float2));
@@ -430,6 +434,8 @@ void ws_bind(bp_handle* h, char* base) {
     D.geo = reinterpret_cast<float4*>(base + w.geo);
     D.geo_lo = reinterpret_cast<float2*>(base + w.geo_lo);
     D.flags = reinterpret_cast<int*>(base + w.flags);
+    D.iota_key = reinterpret_cast<unsigned long long*>(base + w.isel);
+    D.iota_err = reinterpret_cast<float*>(base + w.isel + 256);
     D.tab = reinterpret_cast<double*>(base + w.tab);
     D.tab_part = reinterpret_cast<double*>(base + w.tab_part);
     D.kV = reinterpret_cast<float2*>(base + w.kV);
@@ -468,6 +474,11 @@ bp_status handle_create(const bp_geometry* geom, const bp_params* prm, int P, in
     bp_handle* h = new bp_handle();
     h->st = st;
     fill_geom(h->G, geom);
+    if (iota_blk_smem_bytes(h->G, S_max) > 227 * 1024) {
+        delete h;
+        *err = "geometry and S_max need more shared memory than the MT likelihood kernel has (227 KB)";
+        return BP_ERR_CAPACITY;
+    }
     DevParams& Pm = h->Pm;
     memset(&Pm, 0, sizeof(Pm));
     Pm.T = prm->T; Pm.sigma_v = prm->sigma_v; Pm.motion_dims = prm->motion_dims;
@@ -593,7 +604,7 @@ void update_enqueue(bp_handle* h, const float* z_dev) {
     mark(h, 4);
     launch_kappa(h->G, h->Pm, D, S, h->SCA, h->st);
     mark(h, 5);
-    launch_iota(h->G, h->Pm, D, S, z_dev, h->st);
+    const int iota_launches = launch_iota(h->G, h->Pm, D, S, z_dev, h->st) + 1;
     launch_iota_repair(h->G, h->Pm, D, S, z_dev, h->st);
     mark(h, 6);
     launch_nu(h->G, h->Pm, D, S, h->st);
@@ -605,7 +616,7 @@ void update_enqueue(bp_handle* h, const float* z_dev) {
         cudaEventRecord(h->ev[BP_PROF_STAGES], h->st);
         for (int i = 1; i < BP_PROF_STAGES; ++i) h->ev_valid[i] = true;
     }
-    h->launches += 1 + 3 + 3 + 1 + 2 + 1 + 5 + 3;
+    h->launches += 1 + 3 + 3 + 1 + iota_launches + 1 + 5 + 3;
     h->D.cur = 1 - h->D.cur;
     h->S_upd = S;
     h->phase = 0;

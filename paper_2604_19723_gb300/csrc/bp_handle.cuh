@@ -14,7 +14,7 @@
 // filter on its own owns one; filters of a batch that run one after another on the
 // same stream share one, sized for the largest of them.
 struct WsPlan {
-    size_t lw_x, lw_y, lw_eta, geo, geo_lo, flags, tab, tab_part, kV, kr0l, kB, red_part, gram, V64, cdf, wn, idx;
+    size_t lw_x, lw_y, lw_eta, geo, geo_lo, flags, isel, tab, tab_part, kV, kr0l, kB, red_part, gram, V64, cdf, wn, idx;
     size_t bprop, bprop_c;   // birth proposal scratch (empty unless enabled)
     size_t total;
 };

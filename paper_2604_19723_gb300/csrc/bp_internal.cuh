@@ -367,6 +367,8 @@ struct DevState {
     float4* geo;      // [S_max][J][P] GeoRec of the current prediction: |r'| (hi, lo), u_y, u_z
     float2* geo_lo;   // [S_max][J][P] low parts of u_y, u_z
     int* flags;       // [0] count of flagged particles, then their indices (iota repair)
+    float* iota_err;  // P   error bound (nats) of the FP32 log iota~ sum (k_iota_bulk)
+    unsigned long long* iota_key;   // largest lower bound of the MT log-weights, as an ordered key
     double* tab;      // [4][S_max][J][Nz] double2 : m, mw, mu3, mu4
     double* tab_part; // table partial sums [nsplit][3][S_max][J][Nz] double2
     double* W;        // S_max    sum_p w_alpha

@@ -132,7 +132,14 @@ bool kappa_tc_ok(const DevGeom& G, int SCA);
 size_t kappa_btile_floats(const DevGeom& G, int S_max);
 // operand tiles of both tensor-core passes of the PF likelihood; returns launches
 int launch_kappa_btile(const DevGeom& G, const DevState& D, int S, int SCA, cudaStream_t st);
-void launch_iota(const DevGeom& G, const DevParams& Pm, const DevState& D, int S, const float* z, cudaStream_t st);
+// MT likelihood of every particle (returns its launches): the FP32 warp kernel with
+// ratio flags below IOTA_FF_ALL_S PFs, else k_iota_bulk and the selection of the particles
+// whose weights need the float-float evaluation; launch_iota_repair then evaluates the
+// flagged particles in float-float
+int launch_iota(const DevGeom& G, const DevParams& Pm, const DevState& D, int S, const float* z, cudaStream_t st);
+int launch_iota_bulk(const DevGeom& G, const DevParams& Pm, const DevState& D, int S, const float* z, cudaStream_t st);
+size_t iota_bulk_smem_bytes(const DevGeom& G, int S);
+size_t iota_blk_smem_bytes(const DevGeom& G, int S);
 void launch_nu(const DevGeom& G, const DevParams& Pm, const DevState& D, int S, cudaStream_t st);
 int launch_normalize(const DevGeom& G, const DevParams& Pm, const DevState& D, int S, cudaStream_t st);
 void launch_resample(const DevGeom& G, const DevParams& Pm, const DevState& D, int S, double* cdf, cudaStream_t st);

@@ -900,6 +900,72 @@ __device__ inline cff gent_value(const gent& g) {
 // double, A packed lower [S(S+1)/2] cff, then float2 z [Nz], factors [S][nfac | 1], cm [S], g [S], L packed [S(S+1)/2]
 // (also the partial sums g [S][Nf] before the Gram), then float amplitude [S],
 // A d [S], d [S], 1/L_kk [64], pivots [64] ff
+// e^{i 2 pi t} for a phase t = th + tl in cycles, as an unevaluated pair hi + lo good to
+// ~1e-9: the nearest 1/256 of a cycle from a table of FP64-rounded (hi, lo) values, turned
+// by the remainder angle phi (|phi| <= pi/256) through the angle-addition formulas with
+// cos phi - 1 and sin phi from their Taylor series (terms beyond phi^5 below 1e-14)
+__device__ inline void cis_pair(const float4* tab, float th, float tl, float2& hi, float2& lo) {
+    const float n = rintf(th * 256.0f);
+    const float rem = __fadd_rn(__fsub_rn(th, n * 0.00390625f), tl);   // th - n/256 is exact
+    const float4 T = tab[((int)n) & 255];                                // cos hi, cos lo, sin hi, sin lo
+    const float ph = 6.28318530717958648f * rem;
+    const float p2 = ph * ph;
+    const float cm1 = p2 * fmaf(p2, 1.0f / 24.0f, -0.5f);
+    const float sp = ph * fmaf(p2, fmaf(p2, 1.0f / 120.0f, -1.0f / 6.0f), 1.0f);
+    const float cr = fmaf(T.x, cm1, fmaf(-T.z, sp, T.y));
+    const float ci = fmaf(T.z, cm1, fmaf(T.x, sp, T.w));
+    fast_two_sum(T.x, cr, hi.x, lo.x);   // |cr| <= |T.x| unless T.x == 0
+    fast_two_sum(T.z, ci, hi.y, lo.y);
+}
+// the table: e^{i 2 pi n / 256}, n = 0..255, in FP64 and split into FP32 pairs
+__device__ inline void cis_table_fill(float4* tab, int tid, int nthreads) {
+    for (int n = tid; n < 256; n += nthreads) {
+        double sn, cs;
+        sincospi((double)n / 128.0, &sn, &cs);
+        const float ch = (float)cs, sh = (float)sn;
+        tab[n] = make_float4(ch, (float)(cs - (double)ch), sh, (float)(sn - (double)sh));
+    }
+}
+// steering factors of factors_from_geo_folded as (hi, lo) pairs (same phases, evaluated by
+// cis_pair); returns the amplitude A = lambda / (4 pi d)
+__device__ inline float factors_from_geo_pairs(const DevGeom& G, const float4* tab, float4 g, float2 gl, float2* fh,
+                                               float2* fl) {
+    const float d = g.x + g.y;
+    float h0, l0;
+    ff_frac_mul2(g.x, g.y, G.inv_lam_hi, G.inv_lam_lo, h0, l0);
+    for (int f = 0; f < G.Nf; ++f) {
+        float hf, lf, h, e;
+        ff_frac_mul2(g.x, g.y, G.fc_hi[f], G.fc_lo[f], hf, lf);
+        two_sum(h0, hf, h, e);
+        cis_pair(tab, -h, -(e + l0 + lf), fh[f], fl[f]);
+    }
+    for (int y = 0; y < G.My; ++y) {
+        const float p = __fmul_rn(G.py_l[y], g.z);
+        const float e = fmaf(G.py_l[y], gl.x, fmaf(G.py_lo[y], g.z, fmaf(G.py_l[y], g.z, -p)));
+        cis_pair(tab, p, e, fh[G.Nf + y], fl[G.Nf + y]);
+    }
+    for (int m = 0; m < G.Mz; ++m) {
+        const float p = __fmul_rn(G.pz_l[m], g.w);
+        const float e = fmaf(G.pz_l[m], gl.y, fmaf(G.pz_lo[m], g.w, fmaf(G.pz_l[m], g.w, -p)));
+        cis_pair(tab, p, e, fh[G.Nf + G.My + m], fl[G.Nf + G.My + m]);
+    }
+    return G.amp_c / d;
+}
+// (ah + al)(bh + bl) as hi + lo: exact products of the high parts, the rounding of their
+// sum, and the first-order cross terms
+__device__ inline float4 cpair_mul(float2 ah, float2 al, float2 bh, float2 bl) {
+    const float p1 = __fmul_rn(ah.x, bh.x), e1 = fmaf(ah.x, bh.x, -p1);
+    const float p2 = __fmul_rn(ah.y, bh.y), e2 = fmaf(ah.y, bh.y, -p2);
+    const float p3 = __fmul_rn(ah.x, bh.y), e3 = fmaf(ah.x, bh.y, -p3);
+    const float p4 = __fmul_rn(ah.y, bh.x), e4 = fmaf(ah.y, bh.x, -p4);
+    float rh, rl, ih, il;
+    two_sum(p1, -p2, rh, rl);
+    two_sum(p3, p4, ih, il);
+    rl += (e1 - e2) + fmaf(ah.x, bl.x, fmaf(al.x, bh.x, -fmaf(ah.y, bl.y, al.y * bh.y)));
+    il += (e3 + e4) + fmaf(ah.x, bl.y, fmaf(al.x, bh.y, fmaf(ah.y, bl.x, al.y * bh.x)));
+    return make_float4(rh, ih, rl, il);
+}
+
 __host__ __device__ inline size_t iota_blk_lsize(int S, int Nf) {
     const size_t a = (size_t)S * (S + 1) / 2, b = (size_t)S * Nf;
     return a > b ? a : b;
@@ -907,7 +973,9 @@ __host__ __device__ inline size_t iota_blk_lsize(int S, int Nf) {
 __host__ __device__ inline size_t iota_blk_smem(int S, int nfac, int Nf, int Nz) {
     return 2 * IB_SMAX * 16 + 2 * IB_SMAX * 8 + 4 * 8 + 16 * 8 + (size_t)S * (S + 1) / 2 * 16 +
            ((size_t)Nz + (size_t)S * (nfac | 1) + 2 * (size_t)S + iota_blk_lsize(S, Nf)) * 8 + 3 * (size_t)S * 4 + IB_SMAX * 4 +
-           IB_SMAX * 8;
+           IB_SMAX * 8 +
+           // residual: alignment slack, cis table [256] (float4), low parts of the factors [S][nfac | 1]
+           16 + 256 * 16 + (size_t)S * (nfac | 1) * 8;
 }
 
 // blocks per SM: two 256-thread blocks at 128 registers (67 KB shared each).  Three
@@ -938,6 +1006,9 @@ __global__ void __launch_bounds__(32 * NCG, IOTA_BLK_PER_SM) k_iota_blk(DevGeom 
     float* dS = adS + S;                                          // [S] d
     float* ild = dS + S;                                          // [IB_SMAX] 1 / L_kk
     ff* pivs = reinterpret_cast<ff*>(ild + IB_SMAX);              // [IB_SMAX] pivots
+    // [256] e^{i 2 pi n / 256} (hi, lo), on a 16-byte boundary (the float arrays above end on 4)
+    float4* ctab = reinterpret_cast<float4*>((reinterpret_cast<uintptr_t>(pivs + IB_SMAX) + 15) & ~(uintptr_t)15);
+    float2* flo = reinterpret_cast<float2*>(ctab + 256);          // [S][nfac] low parts of the factors
     const int tid = threadIdx.x, lane = tid & 31, wid = tid >> 5;
     const int cg = lane % NCG;
     const int rp = wid * (32 / NCG) + lane / NCG;
@@ -945,6 +1016,7 @@ __global__ void __launch_bounds__(32 * NCG, IOTA_BLK_PER_SM) k_iota_blk(DevGeom 
     const float* phi = D.phi[D.cur];
     __shared__ double lg_eb[J_MAX], inv_eb[J_MAX];
     if (tid < J) { lg_eb[tid] = log(D.eta_bar[tid]); inv_eb[tid] = 1.0 / D.eta_bar[tid]; }
+    cis_table_fill(ctab, tid, IB_T);
     const int count = all ? P : D.flags[0];
     for (int w = blockIdx.x; w < count; w += gridDim.x) {
         const int pp = all ? w : D.flags[1 + w];
@@ -959,7 +1031,7 @@ __global__ void __launch_bounds__(32 * NCG, IOTA_BLK_PER_SM) k_iota_blk(DevGeom 
                 const float* ph = phi + (size_t)s * 6 * P;
                 float2* fs = fac + (size_t)s * nfac;
                 const size_t gi = ((size_t)s * J + j) * P + pp;
-                const float A = factors_from_geo_folded(G, D.geo[gi], D.geo_lo[gi], fs, fs + Nf, fs + Nf + G.My, 1);
+                const float A = factors_from_geo_pairs(G, ctab, D.geo[gi], D.geo_lo[gi], fs, flo + (size_t)s * nfac);
                 const float pi = (float)(D.zeta[s * J + j] * D.W[s]);
                 const float gm = ph[3 * P + pp], mr = ph[4 * P + pp], mi = ph[5 * P + pp];
                 const float d = sqrtf(fmaxf(pi * (gm + (mr * mr + mi * mi) * (1.0f - pi)), 0.0f));
@@ -1156,17 +1228,53 @@ __global__ void __launch_bounds__(32 * NCG, IOTA_BLK_PER_SM) k_iota_blk(DevGeom 
                 if (lane == 0) red[0] = ff_to_d(yy);
             }
             __syncthreads();
-            // residual r = z - sum_s A_s (pi mu + d y)_s (b' kron a_y kron a_z)_s
+            // residual r = z - sum_s w_s (b' kron a_y kron a_z)_s, w_s = A_s (pi mu + d y)_s.  Its
+            // energy reaches ~1e4 noise units, so the steering values enter as (hi, lo) pairs
+            // (~1e-9), the products of the high parts are summed exactly on a grid fixed for
+            // this (p, j) (2^E > 4 (max_k |z_k| + sum_s |w_s|) bounds every partial sum), and
+            // the remainders and the low-part cross terms are summed in FP32
+            if (wid == 1) {
+                float b = 0.f, zm = 0.f;
+                for (int s = lane; s < S; s += 32) b += fabsf(cmS[s].x) + fabsf(cmS[s].y);
+                for (int k = lane; k < Nz; k += 32) zm = fmaxf(zm, fabsf(zs[k].x) + fabsf(zs[k].y));
+                b = warp_sum_f(b);
+                #pragma unroll
+                for (int o = 16; o > 0; o >>= 1) zm = fmaxf(zm, __shfl_xor_sync(0xffffffffu, zm, o));
+                if (lane == 0) red[2] = (double)(b + zm);
+            }
+            __syncthreads();
+            int gE;
+            frexpf(4.0f * (float)red[2] + 1e-30f, &gE);
+            const float GM = ldexpf(1.5f, gE);
             ff rr{0.f, 0.f};
             for (int k = tid; k < Nz; k += IB_T) {
                 const int f = k / Nm, ym = k - f * Nm, y = ym / G.Mz, m = ym - y * G.Mz;
-                float2 acc = zs[k];
+                const float2 zk = zs[k];
+                float2 gr, rm;
+                gr.x = __fsub_rn(__fadd_rn(zk.x, GM), GM);
+                gr.y = __fsub_rn(__fadd_rn(zk.y, GM), GM);
+                rm.x = __fsub_rn(zk.x, gr.x);
+                rm.y = __fsub_rn(zk.y, gr.y);
                 for (int s = 0; s < S; ++s) {
+                    // w_s (FP32, exact) times psi'_sk = b'_f a_y a_z as a (hi, lo) pair
                     const float2* fs = fac + (size_t)s * nfac;
-                    const float2 u = cmul(cmul(cmS[s], fs[f]), cmul(fs[Nf + y], fs[Nf + G.My + m]));
-                    acc.x -= u.x; acc.y -= u.y;
+                    const float2* fl = flo + (size_t)s * nfac;
+                    const float4 ay = cpair_mul(fs[Nf + y], fl[Nf + y], fs[Nf + G.My + m], fl[Nf + G.My + m]);
+                    const float4 c = cpair_mul(fs[f], fl[f], make_float2(ay.x, ay.y), make_float2(ay.z, ay.w));
+                    const float2 u = cmS[s];
+                    float t;
+                    t = __fsub_rn(fmaf(u.x, c.x, GM), GM); gr.x = __fsub_rn(gr.x, t); rm.x -= fmaf(u.x, c.x, -t);
+                    t = __fsub_rn(fmaf(-u.y, c.y, GM), GM); gr.x = __fsub_rn(gr.x, t); rm.x -= fmaf(-u.y, c.y, -t);
+                    t = __fsub_rn(fmaf(u.x, c.y, GM), GM); gr.y = __fsub_rn(gr.y, t); rm.y -= fmaf(u.x, c.y, -t);
+                    t = __fsub_rn(fmaf(u.y, c.x, GM), GM); gr.y = __fsub_rn(gr.y, t); rm.y -= fmaf(u.y, c.x, -t);
+                    rm.x -= fmaf(u.x, c.z, -u.y * c.w);
+                    rm.y -= fmaf(u.x, c.w, u.y * c.z);
                 }
-                ff_acc_sq(rr, acc);
+                float hx, lx, hy, ly;
+                two_sum(gr.x, rm.x, hx, lx);
+                two_sum(gr.y, rm.y, hy, ly);
+                ff_acc_sq(rr, make_float2(hx, hy));
+                rr.lo = fmaf(2.0f * hx, lx, fmaf(2.0f * hy, ly, rr.lo));
             }
             rr = warp_sum_ff(rr);
             if (lane == 0) red[8 + wid] = ff_to_d(rr);
@@ -1335,8 +1443,8 @@ void launch_kappa(const DevGeom& G, const DevParams& Pm, const DevState& D, int 
 // S below which the FP32 path runs first and only flagged particles are redone
 constexpr int IOTA_FF_ALL_S = 24;
 
-void launch_iota(const DevGeom& G, const DevParams& Pm, const DevState& D, int S, const float* z, cudaStream_t st) {
-    if (S >= IOTA_FF_ALL_S) return;   // k_iota_blk handles every particle (launch_iota_repair)
+int launch_iota(const DevGeom& G, const DevParams& Pm, const DevState& D, int S, const float* z, cudaStream_t st) {
+    if (S >= IOTA_FF_ALL_S) return launch_iota_bulk(G, Pm, D, S, z, st);
     const int nfac = G.Nf + G.My + G.Mz;
     const size_t per_warp = iota32_warp_f2(S, nfac, G.Nf) * sizeof(float2);
     int wpb = 8;
@@ -1345,18 +1453,19 @@ void launch_iota(const DevGeom& G, const DevParams& Pm, const DevState& D, int S
     cudaMemsetAsync(D.flags, 0, sizeof(int), st);
     smem_allow_max((const void*)k_iota);
     k_iota<<<(Pm.P + wpb - 1) / wpb, 32 * wpb, smem, st>>>(G, Pm, D, S, z);
+    return 1;
 }
 
 void launch_iota_repair(const DevGeom& G, const DevParams& Pm, const DevState& D, int S, const float* z, cudaStream_t st) {
     const int nfac = G.Nf + G.My + G.Mz;
     const size_t smem = iota_blk_smem(S, nfac, G.Nf, G.Nz);
-    const int all = S >= IOTA_FF_ALL_S ? 1 : 0;
-    if (all) cudaMemsetAsync(D.flags, 0, sizeof(int), st);
     constexpr int NCG = IOTA_BLK_NCG;
     smem_allow_max((const void*)k_iota_blk<NCG>);
-    const int wave = IOTA_BLK_PER_SM * 152;
-    const int blocks = all ? std::min(Pm.P, 16 * wave) : wave;
-    k_iota_blk<NCG><<<blocks, 32 * NCG, smem, st>>>(G, Pm, D, S, z, all);
+    int sms = 0, dev = 0;
+    cudaGetDevice(&dev);
+    cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+    const int wave = IOTA_BLK_PER_SM * std::max(sms, 1);
+    k_iota_blk<NCG><<<wave, 32 * NCG, smem, st>>>(G, Pm, D, S, z, 0);
 }
 
 void launch_nu(const DevGeom& G, const DevParams& Pm, const DevState& D, int S, cudaStream_t st) {
@@ -1364,4 +1473,10 @@ void launch_nu(const DevGeom& G, const DevParams& Pm, const DevState& D, int S, 
     k_nu<<<(n + 255) / 256, 256, 0, st>>>(G, Pm, D, S);
 }
 
+}  // namespace bp
+
+namespace bp {
+size_t iota_blk_smem_bytes(const DevGeom& G, int S) {
+    return iota_blk_smem(S, G.Nf + G.My + G.Mz, G.Nf, G.Nz);
+}
 }  // namespace bp

@@ -169,6 +169,48 @@ def test_update_parity_near_duplicate_pfs(S, los_existence):
     f.close()
 
 
+IOTA_BULK_CASES = [
+    # (geometry, K, S, P, seed, pos_std): S >= 24 takes the FP32 bulk kernel and the selection
+    (dict(J=4, Nf=10, My=4, Mz=4), 63, 64, 777, 17, 0.005),      # 64 PFs, ragged P over many blocks
+    (dict(J=2, Nf=6, My=3, Mz=2), 30, 33, 401, 18, 0.02),        # S = 33 (rows 33..63 padded), Nz = 36
+    (dict(J=3, Nf=10, My=4, Mz=4), 26, 27, 300, 19, 0.01),       # S in the 32-row variant
+]
+
+
+@pytest.mark.parametrize("case", IOTA_BULK_CASES)
+def test_iota_bulk_bounds_and_selection(case):
+    """Per-particle log iota sums against the FP64 oracle.  Particles evaluated in
+    float-float agree to 1e-4; every other particle's FP32 value lies within its
+    reported error bound (at most one nat); and every particle whose oracle log-weight
+    lies within Delta - 1 = 23 nats of the best one was evaluated in float-float."""
+    geom_kw, K, S, P, seed, pos = case
+    g, prm, scn, eta, z, st = setup_case(geom_kw, K, S, P, seed, pos)
+    pred = model.predict(st, prm, g.J, seed=seed, S_max=64)
+    f = gpu_update_from(pred, g, prm, z, P, 64, seed)
+    ll = f.diag_loglik(pred.S)["log_iota"]
+    di = f.diag_iota()
+    msg = messages_woodbury.update_messages(pred, prm, g, z)
+    ref = msg.log_iota.sum(0)
+    sel = np.zeros(P, bool)
+    sel[di["selected"]] = True
+    d = np.abs(ll - ref)
+    report = dict(selected=int(sel.sum()), sel_err=float(d[sel].max()) if sel.any() else 0.0,
+                  bulk_err=float(d[~sel].max()) if (~sel).any() else 0.0,
+                  bound_min_margin=float(np.min(di["err"][~sel] - d[~sel])) if (~sel).any() else 0.0,
+                  max_bound=float(np.max(di["err"][~sel])) if (~sel).any() else 0.0)
+    print(report)
+    assert sel.any()
+    assert np.all(d[sel] < 1e-4), report
+    assert np.all(d[~sel] <= di["err"][~sel]), report
+    assert np.all(di["err"][~sel] <= 1.0), report
+    lw = np.log(pred.w_beta) + ref
+    assert np.all(sel[lw >= lw.max() - 23.0]), report
+    gw = f.diag_weights(pred.S)
+    bel = beliefs.beliefs(pred, msg)
+    assert rel_weight_err(gw["w_x"], bel.w_x) < W_TOL, rel_weight_err(gw["w_x"], bel.w_x)
+    f.close()
+
+
 def test_loglik_parity_dense():
     """Per-particle log-likelihoods against the dense (explicit covariance) definition."""
     g, prm, scn, eta, z, st = setup_case(dict(J=2, Nf=4, My=2, Mz=2), 3, 4, 96, 21, 0.02)
