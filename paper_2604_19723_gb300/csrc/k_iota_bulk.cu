@@ -14,10 +14,13 @@
 // negligible: a particle more than Delta nats below the best carries at most e^-Delta
 // of the best weight, so an FP32 error of a nat there changes no weight by more than
 // e^-Delta relative to the largest.  Each particle's FP32 value therefore comes with
-// a bound on its error (pivot cancellation: ~8 eps A_kk / piv_k per pivot; the
-// difference |e|^2 - rhs^H A^-1 rhs: a few eps of its terms), and k_iota_select queues
-// every particle whose upper bound reaches within Delta of the largest lower bound, or
-// whose bound exceeds one nat, for k_iota_blk (the float-float evaluation).
+// a bound err_p on its error (pivot cancellation: ~8 eps A_kk / piv_k per pivot; the
+// difference |e|^2 - rhs^H A^-1 rhs: a few eps of its terms).  With u_p = log w_p + err_p
+// an upper bound of the true log-weight and L the largest lower bound over the particles,
+// the FP32 weight of p is off by at most e^(u_p - L) (e^err_p - 1) of the largest weight;
+// k_iota_select queues for k_iota_blk (the float-float evaluation) every particle for
+// which that bound reaches e^-Delta, so the P particles left in FP32 move the
+// normalisation by at most P e^-Delta.
 #include "bp_internal.cuh"
 #include "bp_kernels.cuh"
 
@@ -27,8 +30,7 @@ constexpr int IOTA_BULK_T = 64;              // 8 x 8 threads: row residue tr, c
 constexpr int IOTA_BULK_PER_SM = 6;
 constexpr float IOTA_ERR_PER_RATIO = 4.0e-6f;   // nats per unit of sum_k A_kk / piv_k (8 eps, x8 margin)
 constexpr float IOTA_ERR_PER_ENERGY = 1.0e-6f;  // nats per noise unit of |e|^2 + rhs^H A^-1 rhs (16 eps)
-constexpr double IOTA_SELECT_NATS = 24.0;       // Delta
-constexpr float IOTA_ERR_MAX = 1.0f;            // larger bounds always take the float-float path
+constexpr double IOTA_SELECT_NATS = 24.0;       // Delta: P e^-Delta = 4e-6 at P = 1e5, 1e-5 at 2.6e5
 
 // shared memory (bytes): e [Nz], factors [S][nst], published columns [3][SB], y [SB],
 // A pi mu [SB] (float2); d A [SB], diagonal [SB], reductions [8] (float)
@@ -337,17 +339,17 @@ __global__ void __launch_bounds__(256) k_iota_maxlow(DevParams Pm, DevState D) {
     }
 }
 
-// queue for the float-float path every particle of non-zero prior weight whose upper
-// bound reaches within Delta of the largest lower bound, whose bound exceeds
-// IOTA_ERR_MAX, or whose value is not finite
+// queue for the float-float path every particle of non-zero prior weight whose weight
+// error bound e^(u_p - L) (e^err_p - 1) reaches e^-Delta of the largest weight, or whose
+// value or bound is not finite
 __global__ void __launch_bounds__(256) k_iota_select(DevParams Pm, DevState D) {
     const double lo = dkey_value(*D.iota_key) - IOTA_SELECT_NATS;
     for (int p = blockIdx.x * blockDim.x + threadIdx.x; p < Pm.P; p += gridDim.x * blockDim.x) {
         const double w = D.w_x[p];
         if (!(w > 0.0)) continue;
         const double l = D.lw_x[p];
-        const float e = D.iota_err[p];
-        if (!(e <= IOTA_ERR_MAX) || !isfinite(l) || log(w) + l + (double)e >= lo) {
+        const double e = (double)D.iota_err[p];
+        if (!isfinite(l) || !(e < 30.0) || log(w) + l + e + log(expm1(e)) >= lo) {
             const int slot = atomicAdd(&D.flags[0], 1);
             if (bp_in_range(slot, Pm.P, D.kerr)) D.flags[1 + slot] = p;
         }

@@ -71,7 +71,9 @@ def test_full_size_64pf_sampled(pool):
     scn = W.make_scenario(g, prm, N=3, K=wl["K"], seed=wl["seed"], snr_db=wl["snr_db"],
                           visibility=wl["visibility"], clutter_mean=wl["clutter_mean"])
     eta = synth.noise_variance(scn)
-    z = synth.observe(scn, 1, eta, wl["seed"] + 100)
+    # the observation as the C ABI takes it (complex64), for both sides: its rounding alone
+    # moves |r|^2 / eta_bar by ~1e-2 at this residual energy
+    z = synth.observe(scn, 1, eta, wl["seed"] + 100).astype(np.complex64).astype(np.complex128)
     st = W.state_near_truth(scn, P=P, S=S, n=0, seed=wl["seed"] + 5, eta_true=eta, pos_std=0.01, sfv_std=0.01)
     pred = model.predict(st, prm, g.J, seed=wl["seed"], S_max=S_max)
     tab = messages_dense.message_table_streamed(pred, prm, g, chunk=4096, pool=pool)
@@ -84,6 +86,7 @@ def test_full_size_64pf_sampled(pool):
     gt = f.diag_table(pred.S)
     ll = f.diag_loglik(pred.S)
     gw = f.diag_weights(pred.S)
+    di = f.diag_iota()
     f.close()
 
     # message table over all 100000 particles (FP32 chunk sums, FP64 across chunks)
@@ -108,6 +111,22 @@ def test_full_size_64pf_sampled(pool):
     lwb = np.log(pred.w_beta[idx_i])
     e = rel_weight_err(lwb + ll["log_iota"][idx_i], lwb + li)
     assert e < W_TOL, e
+    # the log iota sums themselves, particle by particle (not only through the weights,
+    # which a sharply peaked posterior would forgive): the particles evaluated in
+    # float-float agree to 1e-4; every other one lies within its FP32 error bound and
+    # its weight error e^(lw - max lw) (e^|d| - 1) stays below e^-23 of the largest
+    sel = np.zeros(P, bool)
+    sel[di["selected"]] = True
+    d_i = np.abs(ll["log_iota"][idx_i] - li)
+    lw_all = np.log(pred.w_beta) + ll["log_iota"]
+    best = int(np.argmax(lw_all))                 # the largest weight (float-float, within 1e-4)
+    rel = lwb + li - lw_all[best]
+    s_i = sel[idx_i]
+    print(dict(selected=int(sel.sum()), sample_selected=int(s_i.sum()), sel_err=float(d_i[s_i].max())))
+    assert sel[best]
+    assert np.all(d_i[s_i] < 1e-4), d_i[s_i]
+    assert np.all(d_i[~s_i] <= di["err"][idx_i][~s_i])
+    assert np.all(np.exp(rel[~s_i]) * np.expm1(d_i[~s_i]) <= np.exp(-23.0))
 
     # PF and noise likelihoods: particles nearest the truth, a spread, the ragged last one
     idx = np.unique(np.r_[np.argsort(dist)[:24], np.linspace(0, P - 1, 16).astype(int), P - 1])
