@@ -78,7 +78,14 @@ def _lowrank_logcn(eta, Mcols, e):
 def update_messages(pred, params, geom, z, psi=None) -> Messages:
     if psi is None:
         psi = all_steering(pred, geom)
-    tab = message_table(pred, params, psi)
+    return messages_from_table(pred, message_table(pred, params, psi), geom, z, psi)
+
+
+def messages_from_table(pred, tab, geom, z, psi=None) -> Messages:
+    """Every update message of the particles in `pred` from a given message table (for
+    a subset of the particles the table was summed over)."""
+    if psi is None:
+        psi = all_steering(pred, geom)
     S, J, P = pred.S, geom.J, pred.x.shape[1]
     gam = pred.phi[:, 3].astype(np.float64)
     mu = pred.phi[:, 4].astype(np.float64) + 1j * pred.phi[:, 5].astype(np.float64)

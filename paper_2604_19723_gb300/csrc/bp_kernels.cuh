@@ -118,6 +118,82 @@ __device__ inline float factors_from_geo_folded(const DevGeom& G, float4 g, floa
     return G.amp_c / d;
 }
 
+// e^{i 2 pi t} for a phase t = th + tl in cycles, as an unevaluated pair hi + lo good to
+// ~1e-9: the nearest 1/256 of a cycle from a table of FP64-rounded (hi, lo) values, turned
+// by the remainder angle phi (|phi| <= pi/256) through the angle-addition formulas with
+// cos phi - 1 and sin phi from their Taylor series (terms beyond phi^5 below 1e-14)
+__device__ inline void cis_pair(const float4* tab, float th, float tl, float2& hi, float2& lo) {
+    const float n = rintf(th * 256.0f);
+    const float rem = __fadd_rn(__fsub_rn(th, n * 0.00390625f), tl);   // th - n/256 is exact
+    const float4 T = tab[((int)n) & 255];                                // cos hi, cos lo, sin hi, sin lo
+    const float ph = 6.28318530717958648f * rem;
+    const float p2 = ph * ph;
+    const float cm1 = p2 * fmaf(p2, 1.0f / 24.0f, -0.5f);
+    const float sp = ph * fmaf(p2, fmaf(p2, 1.0f / 120.0f, -1.0f / 6.0f), 1.0f);
+    const float cr = fmaf(T.x, cm1, fmaf(-T.z, sp, T.y));
+    const float ci = fmaf(T.z, cm1, fmaf(T.x, sp, T.w));
+    fast_two_sum(T.x, cr, hi.x, lo.x);   // |cr| <= |T.x| unless T.x == 0
+    fast_two_sum(T.z, ci, hi.y, lo.y);
+}
+// the table: e^{i 2 pi n / 256}, n = 0..255, in FP64 and split into FP32 pairs
+__device__ inline void cis_table_fill(float4* tab, int tid, int nthreads) {
+    for (int n = tid; n < 256; n += nthreads) {
+        double sn, cs;
+        sincospi((double)n / 128.0, &sn, &cs);
+        const float ch = (float)cs, sh = (float)sn;
+        tab[n] = make_float4(ch, (float)(cs - (double)ch), sh, (float)(sn - (double)sh));
+    }
+}
+// steering factors of factors_from_geo_folded as (hi, lo) pairs (same phases, evaluated by
+// cis_pair; element i at index i * stride); returns the amplitude A = lambda / (4 pi d)
+__device__ inline float factors_from_geo_pairs(const DevGeom& G, const float4* tab, float4 g, float2 gl, float2* fh,
+                                               float2* fl, int stride = 1) {
+    const float d = g.x + g.y;
+    float h0, l0;
+    ff_frac_mul2(g.x, g.y, G.inv_lam_hi, G.inv_lam_lo, h0, l0);
+    for (int f = 0; f < G.Nf; ++f) {
+        float hf, lf, h, e;
+        ff_frac_mul2(g.x, g.y, G.fc_hi[f], G.fc_lo[f], hf, lf);
+        two_sum(h0, hf, h, e);
+        cis_pair(tab, -h, -(e + l0 + lf), fh[f * stride], fl[f * stride]);
+    }
+    for (int y = 0; y < G.My; ++y) {
+        const float p = __fmul_rn(G.py_l[y], g.z);
+        const float e = fmaf(G.py_l[y], gl.x, fmaf(G.py_lo[y], g.z, fmaf(G.py_l[y], g.z, -p)));
+        cis_pair(tab, p, e, fh[(G.Nf + y) * stride], fl[(G.Nf + y) * stride]);
+    }
+    for (int m = 0; m < G.Mz; ++m) {
+        const float p = __fmul_rn(G.pz_l[m], g.w);
+        const float e = fmaf(G.pz_l[m], gl.y, fmaf(G.pz_lo[m], g.w, fmaf(G.pz_l[m], g.w, -p)));
+        cis_pair(tab, p, e, fh[(G.Nf + G.My + m) * stride], fl[(G.Nf + G.My + m) * stride]);
+    }
+    return G.amp_c / d;
+}
+// the frequency factor b'_f of factors_from_geo_pairs alone, from the record's distance
+// (dh + dl) and its carrier cycle count (h0 + l0, from ff_frac_mul2 with 1/lambda)
+__device__ inline void bprime_pair(const DevGeom& G, const float4* tab, float dh, float dl, float h0, float l0, int f,
+                                   float2& hi, float2& lo) {
+    float hf, lf, h, e;
+    ff_frac_mul2(dh, dl, G.fc_hi[f], G.fc_lo[f], hf, lf);
+    two_sum(h0, hf, h, e);
+    cis_pair(tab, -h, -(e + l0 + lf), hi, lo);
+}
+
+// (ah + al)(bh + bl) as hi + lo: exact products of the high parts, the rounding of their
+// sum, and the first-order cross terms
+__device__ inline float4 cpair_mul(float2 ah, float2 al, float2 bh, float2 bl) {
+    const float p1 = __fmul_rn(ah.x, bh.x), e1 = fmaf(ah.x, bh.x, -p1);
+    const float p2 = __fmul_rn(ah.y, bh.y), e2 = fmaf(ah.y, bh.y, -p2);
+    const float p3 = __fmul_rn(ah.x, bh.y), e3 = fmaf(ah.x, bh.y, -p3);
+    const float p4 = __fmul_rn(ah.y, bh.x), e4 = fmaf(ah.y, bh.x, -p4);
+    float rh, rl, ih, il;
+    two_sum(p1, -p2, rh, rl);
+    two_sum(p3, p4, ih, il);
+    rl += (e1 - e2) + fmaf(ah.x, bl.x, fmaf(al.x, bh.x, -fmaf(ah.y, bl.y, al.y * bh.y)));
+    il += (e3 + e4) + fmaf(ah.x, bl.y, fmaf(al.x, bh.y, fmaf(ah.y, bl.x, al.y * bh.x)));
+    return make_float4(rh, ih, rl, il);
+}
+
 void launch_geom(const DevGeom& G, const DevParams& Pm, const DevState& D, int S, cudaStream_t st);
 void launch_iota_repair(const DevGeom& G, const DevParams& Pm, const DevState& D, int S, const float* z, cudaStream_t st);
 

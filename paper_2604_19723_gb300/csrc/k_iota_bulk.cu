@@ -33,9 +33,11 @@ constexpr float IOTA_ERR_PER_ENERGY = 1.0e-6f;  // nats per noise unit of |e|^2 
 constexpr double IOTA_SELECT_NATS = 24.0;       // Delta: P e^-Delta = 4e-6 at P = 1e5, 1e-5 at 2.6e5
 
 // shared memory (bytes): e [Nz], factors [S][nst], published columns [3][SB], y [SB],
-// A pi mu [SB] (float2); d A [SB], diagonal [SB], reductions [8] (float)
-__host__ __device__ inline size_t iota_bulk_smem(int S, int nst, int Nz, int SB) {
-    return ((size_t)Nz + (size_t)S * nst + 5 * (size_t)SB) * sizeof(float2) + (2 * (size_t)SB + 8) * sizeof(float);
+// A pi mu [SB], A pi mu b' [S][Nf | 1], a_y a_z [S][Nm | 1] (float2); d A [SB], diagonal [SB],
+// reductions [8] (float)
+__host__ __device__ inline size_t iota_bulk_smem(int S, int nst, int Nz, int SB, int Nf, int Nm) {
+    return ((size_t)Nz + (size_t)S * nst + 5 * (size_t)SB + (size_t)S * ((Nf | 1) + (Nm | 1))) * sizeof(float2) +
+           (2 * (size_t)SB + 8) * sizeof(float);
 }
 
 __device__ __forceinline__ void cfma_c(float2& acc, float2 a, float2 b) {   // acc += conj(a) b
@@ -66,7 +68,10 @@ __global__ void __launch_bounds__(IOTA_BULK_T, IOTA_BULK_PER_SM) k_iota_bulk(Dev
     float2* pub = fac + (size_t)S * nst;                  // [3][SB] published columns
     float2* yb = pub + 3 * SB;                            // [SB]   y_k = rhs_k^(k) / piv_k
     float2* mt = yb + SB;                                 // [SB]   A_s pi_s mu_s
-    float* dA = reinterpret_cast<float*>(mt + SB);        // [SB]   d_s A_s
+    const int ust = Nf | 1, cst = Nm | 1;                 // odd row strides (bank spread)
+    float2* ub = mt + SB;                                 // [S][ust] A_s pi_s mu_s b'_sf
+    float2* cb2 = ub + (size_t)S * ust;                   // [S][cst] a_sy a_sm
+    float* dA = reinterpret_cast<float*>(cb2 + (size_t)S * cst);   // [SB]   d_s A_s
     float* dg0 = dA + SB;                                 // [SB]   A_kk before the elimination
     float* red = dg0 + SB;                                // [8]
     const float* phi = D.phi[D.cur];
@@ -100,16 +105,26 @@ __global__ void __launch_bounds__(IOTA_BULK_T, IOTA_BULK_PER_SM) k_iota_bulk(Dev
                 dA[t] = das;
             }
             __syncthreads();
-            // e = z - sum_s (A pi mu)_s psi'_s, element-wise; |e|^2
+            // Kronecker parts of the steering vectors: psi'_s[f, (y, m)] = b'_sf (a_sy a_sm)
+            for (int i = t; i < S * Nf; i += IOTA_BULK_T) {
+                const int s = i / Nf, f = i - s * Nf;
+                ub[(size_t)s * ust + f] = cmul(mt[s], fac[(size_t)s * nst + f]);
+            }
+            for (int i = t; i < S * Nm; i += IOTA_BULK_T) {
+                const int s = i / Nm, ym = i - s * Nm, y = ym / Mz, m = ym - y * Mz;
+                const float2* fs = fac + (size_t)s * nst;
+                cb2[(size_t)s * cst + ym] = cmul(fs[Nf + y], fs[Nf + My + m]);
+            }
+            __syncthreads();
+            // e = z - sum_s (A pi mu b')_sf (a_y a_z)_s,ym, element-wise; |e|^2
             float ee = 0.f;
             for (int k = t; k < Nz; k += IOTA_BULK_T) {
-                const int f = k / Nm, ym = k - f * Nm, y = ym / Mz, m = ym - y * Mz;
+                const int f = k / Nm, ym = k - f * Nm;
                 float2 acc = es[k];
                 for (int s = 0; s < S; ++s) {
-                    const float2* fs = fac + (size_t)s * nst;
-                    const float2 u = cmul(cmul(mt[s], fs[f]), cmul(fs[Nf + y], fs[Nf + My + m]));
-                    acc.x -= u.x;
-                    acc.y -= u.y;
+                    const float2 u = ub[(size_t)s * ust + f], c = cb2[(size_t)s * cst + ym];
+                    acc.x = fmaf(-u.x, c.x, fmaf(u.y, c.y, acc.x));
+                    acc.y = fmaf(-u.x, c.y, fmaf(-u.y, c.x, acc.y));
                 }
                 es[k] = acc;
                 ee = fmaf(acc.x, acc.x, fmaf(acc.y, acc.y, ee));
@@ -121,20 +136,13 @@ __global__ void __launch_bounds__(IOTA_BULK_T, IOTA_BULK_PER_SM) k_iota_bulk(Dev
             float2 rhs = make_float2(0.f, 0.f);
             if (t < S) {
                 const float2* fs = fac + (size_t)t * nst;
+                const float2* cs = cb2 + (size_t)t * cst;
                 float2 g = make_float2(0.f, 0.f);
                 for (int f = 0; f < Nf; ++f) {
-                    float2 accy = make_float2(0.f, 0.f);
-                    for (int y = 0; y < My; ++y) {
-                        float2 accm = make_float2(0.f, 0.f);
-                        const float2* ez = es + f * Nm + y * Mz;
-                        for (int m = 0; m < Mz; ++m) cfma_c(accm, fs[Nf + My + m], ez[m]);
-                        const float2 u = cmulc(fs[Nf + y], accm);
-                        accy.x += u.x;
-                        accy.y += u.y;
-                    }
-                    const float2 u = cmulc(fs[f], accy);
-                    g.x += u.x;
-                    g.y += u.y;
+                    float2 acc = make_float2(0.f, 0.f);
+                    const float2* ef = es + f * Nm;
+                    for (int ym = 0; ym < Nm; ++ym) cfma_c(acc, cs[ym], ef[ym]);
+                    cfma_c(g, fs[f], acc);
                 }
                 rhs = make_float2(dA[t] * g.x, dA[t] * g.y);
             }
@@ -341,7 +349,7 @@ __global__ void __launch_bounds__(256) k_iota_maxlow(DevParams Pm, DevState D) {
 
 // queue for the float-float path every particle of non-zero prior weight whose weight
 // error bound e^(u_p - L) (e^err_p - 1) reaches e^-Delta of the largest weight, or whose
-// value or bound is not finite
+// value or bound is not finite (a breakdown of the FP32 elimination)
 __global__ void __launch_bounds__(256) k_iota_select(DevParams Pm, DevState D) {
     const double lo = dkey_value(*D.iota_key) - IOTA_SELECT_NATS;
     for (int p = blockIdx.x * blockDim.x + threadIdx.x; p < Pm.P; p += gridDim.x * blockDim.x) {
@@ -349,7 +357,8 @@ __global__ void __launch_bounds__(256) k_iota_select(DevParams Pm, DevState D) {
         if (!(w > 0.0)) continue;
         const double l = D.lw_x[p];
         const double e = (double)D.iota_err[p];
-        if (!isfinite(l) || !(e < 30.0) || log(w) + l + e + log(expm1(e)) >= lo) {
+        const double lx = e > 30.0 ? e : log(expm1(e));   // log(e^err - 1)
+        if (!isfinite(l) || !isfinite(e) || log(w) + l + e + lx >= lo) {
             const int slot = atomicAdd(&D.flags[0], 1);
             if (bp_in_range(slot, Pm.P, D.kerr)) D.flags[1 + slot] = p;
         }
@@ -360,7 +369,7 @@ template <int NB>
 static void launch_bulk_nb(const DevGeom& G, const DevParams& Pm, const DevState& D, int S, const float* z,
                            cudaStream_t st) {
     const int nst = (G.Nf + G.My + G.Mz) | 1;
-    const size_t smem = iota_bulk_smem(S, nst, G.Nz, 8 * NB);
+    const size_t smem = iota_bulk_smem(S, nst, G.Nz, 8 * NB, G.Nf, G.My * G.Mz);
     smem_allow_max((const void*)k_iota_bulk<NB>);
     int sms = 0, dev = 0;
     cudaGetDevice(&dev);
@@ -382,7 +391,7 @@ int launch_iota_bulk(const DevGeom& G, const DevParams& Pm, const DevState& D, i
 }
 
 size_t iota_bulk_smem_bytes(const DevGeom& G, int S) {
-    return iota_bulk_smem(S, (G.Nf + G.My + G.Mz) | 1, G.Nz, S <= 32 ? 32 : 64);
+    return iota_bulk_smem(S, (G.Nf + G.My + G.Mz) | 1, G.Nz, S <= 32 ? 32 : 64, G.Nf, G.My * G.Mz);
 }
 
 }  // namespace bp

@@ -34,6 +34,44 @@ namespace bp {
 // 1/lambda_c and w_c = y~0_c/lambda_c beside it.  The basis columns are orthogonal,
 // so every amplitude term is a diagonal sum over the columns.
 
+// acc += a b: exact product, float-float sum (acc.lo left unnormalised)
+__device__ __forceinline__ void ff_acc_prod(ff& acc, float a, float b) {
+    const float p = __fmul_rn(a, b), e = fmaf(a, b, -p);
+    float s, t;
+    two_sum(acc.hi, p, s, t);
+    acc.hi = s;
+    acc.lo = __fadd_rn(acc.lo, __fadd_rn(t, e));
+}
+
+// The O(S) amplitude sums of the PF likelihood in the eigenbasis, T = sum_c w_c h_c and
+// gg = sum_c |h_c|^2 / lambda_c, in float-float from the FP32 factors: with PFs that nearly
+// duplicate one another both are large and almost cancel in 2 Re(tau conj T)/eta_bar -
+// |tau|^2 gg/eta_bar^2, and FP32 sums of them put ~1e-4 on normalised weights
+template <int NC>
+__device__ inline void kappa_amp_sums(const float2* w, const float2* dl, const float2 (&h)[NC], double& Tx, double& Ty,
+                                      double& gg) {
+    ff tx{0.f, 0.f}, ty{0.f, 0.f}, g{0.f, 0.f};
+    #pragma unroll
+    for (int c = 0; c < NC; ++c) {
+        const float2 wc = w[c];
+        const float lc = dl[c].x;
+        ff_acc_prod(tx, wc.x, h[c].x);
+        ff_acc_prod(tx, -wc.y, h[c].y);
+        ff_acc_prod(ty, wc.x, h[c].y);
+        ff_acc_prod(ty, wc.y, h[c].x);
+        // |h_c|^2 / lambda_c: exact squares, their sum in float-float, times 1/lambda_c
+        const float p1 = __fmul_rn(h[c].x, h[c].x), e1 = fmaf(h[c].x, h[c].x, -p1);
+        const float p2 = __fmul_rn(h[c].y, h[c].y), e2 = fmaf(h[c].y, h[c].y, -p2);
+        float m, me;
+        two_sum(p1, p2, m, me);
+        ff_acc_prod(g, lc, m);
+        g.lo = fmaf(lc, __fadd_rn(me, __fadd_rn(e1, e2)), g.lo);
+    }
+    Tx = (double)tx.hi + (double)tx.lo;
+    Ty = (double)ty.hi + (double)ty.lo;
+    gg = (double)g.hi + (double)g.lo;
+}
+
 template <int SC>
 __global__ void __launch_bounds__(256, (SC <= 16 ? 2 : 1)) k_kappa(DevGeom G, DevParams Pm, DevState D, int S, int SCA, int fch) {
     constexpr int KT = 256;
@@ -45,9 +83,15 @@ __global__ void __launch_bounds__(256, (SC <= 16 ? 2 : 1)) k_kappa(DevGeom G, De
     float4* Vs = sm4;                                                  // [fch * Nm][NP] rows staged
     float2* dls = reinterpret_cast<float2*>(Vs + (size_t)fch * Nm * NP); // [SC] 1/lambda_c (.x)
     float2* y0s = dls + SC;                                            // [SC] w_c
-    float2* fac = y0s + SC;                                            // [nfac][KT]
+    float2* fac = y0s + SC;                                            // [nfac][KT] factors (high parts)
     float2* r0ls = fac + (size_t)(G.Nf + G.My + G.Mz) * KT;           // [fch * Nm] low part of r0
+    float2* facl = r0ls + (size_t)fch * Nm;                            // [My + Mz][KT] low parts of a_y, a_z
+    // [256] e^{i 2 pi n / 256} as (hi, lo) pairs, on a 16-byte boundary
+    float4* ctab = reinterpret_cast<float4*>((reinterpret_cast<uintptr_t>(facl + (size_t)(G.My + G.Mz) * KT) + 15) &
+                                             ~(uintptr_t)15);
+    float* rn = reinterpret_cast<float*>(ctab + 256);                  // [fch * Nm] |V_k|^2 over the basis columns
     const int tid = threadIdx.x;
+    cis_table_fill(ctab, tid, KT);
     const int p = blockIdx.x * KT + tid;
     const bool act = p < P;
     const int pp = act ? p : 0;
@@ -69,7 +113,13 @@ __global__ void __launch_bounds__(256, (SC <= 16 ? 2 : 1)) k_kappa(DevGeom G, De
                 const int k = f0 * Nm + t / SC, c = t % SC;
                 Vs2[t] = (c < NC) ? gV[(size_t)k * SCA + c] : gV[(size_t)k * SCA + SCA - 1];
             }
-            for (int t = tid; t < nrow; t += KT) r0ls[t] = gr0l[f0 * Nm + t];
+            for (int t = tid; t < nrow; t += KT) {
+                r0ls[t] = gr0l[f0 * Nm + t];
+                const float2* vr = gV + (size_t)(f0 * Nm + t) * SCA;
+                float n2 = 0.f;
+                for (int c = 0; c < NC; ++c) n2 = fmaf(vr[c].x, vr[c].x, fmaf(vr[c].y, vr[c].y, n2));
+                rn[t] = n2;
+            }
         };
         __syncthreads();
         {
@@ -87,7 +137,30 @@ __global__ void __launch_bounds__(256, (SC <= 16 ? 2 : 1)) k_kappa(DevGeom G, De
         float2* fb = fac + tid;
         float2* fy = fb + G.Nf * KT;
         float2* fz = fy + G.My * KT;
-        const float2 Fc = factors_from_geo(G, geo_s[(size_t)j * P + pp], geol_s[(size_t)j * P + pp], fb, fy, fz, KT);
+        float2* fyl = facl + tid;
+        float2* fzl = fyl + G.My * KT;
+        // steering factors with the carrier folded into b', evaluated as (hi, lo) pairs; the high
+        // parts feed pass 1 (whose rounding only shifts the fitted amplitudes: second order),
+        // pass 2 takes the pairs (the low parts of b' are recomputed there per frequency)
+        const float4 grec = geo_s[(size_t)j * P + pp];
+        const float2 grl = geol_s[(size_t)j * P + pp];
+        const float Aamp = G.amp_c / (grec.x + grec.y);
+        float ch0, cl0;
+        ff_frac_mul2(grec.x, grec.y, G.inv_lam_hi, G.inv_lam_lo, ch0, cl0);
+        {
+            float2 lo_unused;
+            for (int f = 0; f < G.Nf; ++f) bprime_pair(G, ctab, grec.x, grec.y, ch0, cl0, f, fb[f * KT], lo_unused);
+            for (int y = 0; y < G.My; ++y) {
+                const float p = __fmul_rn(G.py_l[y], grec.z);
+                const float e = fmaf(G.py_l[y], grl.x, fmaf(G.py_lo[y], grec.z, fmaf(G.py_l[y], grec.z, -p)));
+                cis_pair(ctab, p, e, fy[y * KT], fyl[y * KT]);
+            }
+            for (int m = 0; m < G.Mz; ++m) {
+                const float p = __fmul_rn(G.pz_l[m], grec.w);
+                const float e = fmaf(G.pz_l[m], grl.y, fmaf(G.pz_lo[m], grec.w, fmaf(G.pz_l[m], grec.w, -p)));
+                cis_pair(ctab, p, e, fz[m * KT], fzl[m * KT]);
+            }
+        }
         // pass 1: h = psi^H V, pr = psi^H r0
         float2 h[NC];
         #pragma unroll
@@ -97,7 +170,7 @@ __global__ void __launch_bounds__(256, (SC <= 16 ? 2 : 1)) k_kappa(DevGeom G, De
         for (int f0 = 0; f0 < G.Nf; f0 += fch) {
           if (fch < G.Nf) { __syncthreads(); stage_rows(f0); __syncthreads(); }
           for (int f = f0; f < min(G.Nf, f0 + fch); ++f) {
-            const float2 cb = cmul(Fc, fb[f * KT]);
+            const float2 cb = make_float2(Aamp * fb[f * KT].x, Aamp * fb[f * KT].y);
             for (int y = 0; y < G.My; ++y) {
                 const float2 w = cmul(cb, fy[y * KT]);
                 for (int m = 0; m < G.Mz; ++m) {
@@ -129,6 +202,11 @@ __global__ void __launch_bounds__(256, (SC <= 16 ? 2 : 1)) k_kappa(DevGeom G, De
         // enters Delta at second order only
         const float ieb = 1.0f / ebf;
         const float alpha = (nps - hh * ieb) * ieb;
+        // a PF whose steering vector lies mostly in the span of the others' m-vectors (more
+        // than 3/4 of its energy) makes psi_perp a small difference: V conj(h) is then summed
+        // exactly (products on a grid fixed per element, 2^E > 8 |V_k| |h|), else in FP32 chains
+        const bool vh_exact = hh * ieb > 0.75f * nps;
+        const float hnorm = sqrtf(hh);
         const float zf = (float)zeta;
         const float2 af = make_float2(zf * mrf, zf * mif);
         const float q = (gmf + (mrf * mrf + mif * mif) * (1.0f - zf)) * zf;
@@ -148,39 +226,76 @@ __global__ void __launch_bounds__(256, (SC <= 16 ? 2 : 1)) k_kappa(DevGeom G, De
         for (int f0 = 0; f0 < G.Nf; f0 += fch) {
           if (fch < G.Nf) { __syncthreads(); stage_rows(f0); __syncthreads(); }
           for (int f = f0; f < min(G.Nf, f0 + fch); ++f) {
-            const float2 cb = cmul(Fc, fb[f * KT]);
+            // the steering element psi = A b' a_y a_z as a (hi, lo) pair (~1e-9): its error
+            // enters the residual at first order
+            float2 bh, bl;
+            bprime_pair(G, ctab, grec.x, grec.y, ch0, cl0, f, bh, bl);
+            const float2 cbh = make_float2(Aamp * bh.x, Aamp * bh.y);
+            const float2 cbl = make_float2(fmaf(Aamp, bh.x, -cbh.x) + Aamp * bl.x, fmaf(Aamp, bh.y, -cbh.y) + Aamp * bl.y);
             for (int y = 0; y < G.My; ++y) {
-                const float2 w = cmul(cb, fy[y * KT]);
+                const float4 wp = cpair_mul(cbh, cbl, fy[y * KT], fyl[y * KT]);
+                const float2 wh = make_float2(wp.x, wp.y), wl = make_float2(wp.z, wp.w);
                 for (int m = 0; m < G.Mz; ++m) {
-                    const float2 ps = cmul(w, fz[m * KT]);
+                    const float4 psp = cpair_mul(wh, wl, fz[m * KT], fzl[m * KT]);
                     const int kr = (f - f0) * Nm + y * G.Mz + m;
                     const float4* row = Vs + (size_t)kr * NP;
                     constexpr int NCH = NP >= 8 ? 8 : NP;
-                    float2 va[NCH];
-                    #pragma unroll
-                    for (int i = 0; i < NCH; ++i) va[i] = make_float2(0.f, 0.f);
-                    float2 r0 = make_float2(0.f, 0.f);
-                    #pragma unroll
-                    for (int c2 = 0; c2 < NP; ++c2) {
-                        const int ch = (NCH * c2) / NP;
-                        const float4 v = row[c2];
-                        va[ch].x = fmaf(v.x, h[2 * c2].x, fmaf(v.y, h[2 * c2].y, va[ch].x));
-                        va[ch].y = fmaf(v.y, h[2 * c2].x, fmaf(-v.x, h[2 * c2].y, va[ch].y));
-                        if (2 * c2 + 1 < NC) {
-                            va[ch].x = fmaf(v.z, h[2 * c2 + 1].x, fmaf(v.w, h[2 * c2 + 1].y, va[ch].x));
-                            va[ch].y = fmaf(v.w, h[2 * c2 + 1].x, fmaf(-v.z, h[2 * c2 + 1].y, va[ch].y));
-                        } else {
-                            r0 = make_float2(v.z, v.w);
-                        }
-                    }
-                    float vsx = 0.f, vsy = 0.f;   // pairwise sum of the chains
-                    #pragma unroll
-                    for (int w2 = NCH / 2; w2 >= 1; w2 /= 2) {
+                    float2 r0 = make_float2(row[NP - 1].z, row[NP - 1].w);
+                    float vsx = 0.f, vsy = 0.f, vlx = 0.f, vly = 0.f;   // V conj(h) = (vsx + vlx, vsy + vly)
+                    if (vh_exact) {
+                        int gE;
+                        frexpf(8.0f * sqrtf(rn[kr]) * hnorm + 1e-30f, &gE);
+                        const float GM = ldexpf(1.5f, gE);
+                        auto grid = [&](float a, float b, float& g, float& q) {
+                            const float t = __fsub_rn(fmaf(a, b, GM), GM);
+                            g = __fadd_rn(g, t);
+                            q += fmaf(a, b, -t);
+                        };
                         #pragma unroll
-                        for (int i = 0; i < w2; ++i) { va[i].x += va[i + w2].x; va[i].y += va[i + w2].y; }
+                        for (int c2 = 0; c2 < NP; ++c2) {
+                            const float4 v = row[c2];
+                            grid(v.x, h[2 * c2].x, vsx, vlx);
+                            grid(v.y, h[2 * c2].y, vsx, vlx);
+                            grid(v.y, h[2 * c2].x, vsy, vly);
+                            grid(-v.x, h[2 * c2].y, vsy, vly);
+                            if (2 * c2 + 1 < NC) {
+                                grid(v.z, h[2 * c2 + 1].x, vsx, vlx);
+                                grid(v.w, h[2 * c2 + 1].y, vsx, vlx);
+                                grid(v.w, h[2 * c2 + 1].x, vsy, vly);
+                                grid(-v.z, h[2 * c2 + 1].y, vsy, vly);
+                            }
+                        }
+                    } else {
+                        float2 va[NCH];
+                        #pragma unroll
+                        for (int i = 0; i < NCH; ++i) va[i] = make_float2(0.f, 0.f);
+                        #pragma unroll
+                        for (int c2 = 0; c2 < NP; ++c2) {
+                            const int ch = (NCH * c2) / NP;
+                            const float4 v = row[c2];
+                            va[ch].x = fmaf(v.x, h[2 * c2].x, fmaf(v.y, h[2 * c2].y, va[ch].x));
+                            va[ch].y = fmaf(v.y, h[2 * c2].x, fmaf(-v.x, h[2 * c2].y, va[ch].y));
+                            if (2 * c2 + 1 < NC) {
+                                va[ch].x = fmaf(v.z, h[2 * c2 + 1].x, fmaf(v.w, h[2 * c2 + 1].y, va[ch].x));
+                                va[ch].y = fmaf(v.w, h[2 * c2 + 1].x, fmaf(-v.z, h[2 * c2 + 1].y, va[ch].y));
+                            }
+                        }
+                        #pragma unroll
+                        for (int w2 = NCH / 2; w2 >= 1; w2 /= 2) {   // pairwise sum of the chains
+                            #pragma unroll
+                            for (int i = 0; i < w2; ++i) { va[i].x += va[i + w2].x; va[i].y += va[i + w2].y; }
+                        }
+                        vsx = va[0].x; vsy = va[0].y;
                     }
-                    vsx = va[0].x; vsy = va[0].y;
-                    const float2 pp2 = make_float2(ps.x - vsx * ieb, ps.y - vsy * ieb);
+                    // psi_perp = psi - V V^H psi / eta_bar with the product by 1/eta_bar and the
+                    // subtraction taken exactly
+                    const float dxh = vsx * ieb, dyh = vsy * ieb;
+                    const float dxl = fmaf(vsx, ieb, -dxh) + vlx * ieb, dyl = fmaf(vsy, ieb, -dyh) + vly * ieb;
+                    float2 pp2, ppl;
+                    two_sum(psp.x, -dxh, pp2.x, ppl.x);
+                    two_sum(psp.y, -dyh, pp2.y, ppl.y);
+                    ppl.x += psp.z - dxl;
+                    ppl.y += psp.w - dyl;
                     pn += pp2.x * pp2.x + pp2.y * pp2.y;
                     // t = tau pp2 exactly: re = p1 - p2, im = p3 + p4 (+ FMA errors)
                     const float p1 = __fmul_rn(tf.x, pp2.x), e1 = fmaf(tf.x, pp2.x, -p1);
@@ -193,9 +308,11 @@ __global__ void __launch_bounds__(256, (SC <= 16 ? 2 : 1)) k_kappa(DevGeom G, De
                     two_sum(r0.x, -p1, sx, ex1);
                     two_sum(sx, p2, rx.hi, ex2);
                     rx.lo = __fadd_rn(__fadd_rn(rl.x, __fsub_rn(e2, e1)), __fadd_rn(ex1, ex2));
+                    rx.lo = fmaf(-tf.x, ppl.x, fmaf(tf.y, ppl.y, rx.lo));   // - Re(tau psi_perp,lo)
                     two_sum(r0.y, -p3, sy, ey1);
                     two_sum(sy, -p4, ry.hi, ey2);
                     ry.lo = __fsub_rn(__fadd_rn(rl.y, __fadd_rn(ey1, ey2)), __fadd_rn(e3, e4));
+                    ry.lo = fmaf(-tf.x, ppl.y, fmaf(-tf.y, ppl.x, ry.lo));  // - Im(tau psi_perp,lo)
                     ff_acc_sq(rr, make_float2(rx.hi, ry.hi));
                     rr.lo = fmaf(2.0f * rx.hi, rx.lo, fmaf(2.0f * ry.hi, ry.lo, rr.lo));
                 }
@@ -205,26 +322,12 @@ __global__ void __launch_bounds__(256, (SC <= 16 ? 2 : 1)) k_kappa(DevGeom G, De
         // amplitude terms in the eigenbasis, x_c = conj(h_c) (= (V^H psi)_c):
         // |y0|^2 - |y|^2 = 2 Re(tau y0^H x_amp)/eta_bar - |tau|^2 |x_amp|^2/eta_bar^2 with
         // y0^H x_amp = sum_c conj(w_c) x_c = conj(sum_c w_c h_c), |x_amp|^2 = sum_c |h_c|^2/lambda_c
-        float tx0 = 0.f, ty0 = 0.f, tx1 = 0.f, ty1 = 0.f, gg0 = 0.f, gg1 = 0.f;
-        #pragma unroll
-        for (int c = 0; c < NC; ++c) {
-            const float2 w = y0s[c];
-            const float dl = dls[c].x;
-            const float m2 = fmaf(h[c].x, h[c].x, h[c].y * h[c].y);
-            if (c & 1) {
-                tx1 = fmaf(w.x, h[c].x, fmaf(-w.y, h[c].y, tx1));
-                ty1 = fmaf(w.x, h[c].y, fmaf(w.y, h[c].x, ty1));
-                gg1 = fmaf(dl, m2, gg1);
-            } else {
-                tx0 = fmaf(w.x, h[c].x, fmaf(-w.y, h[c].y, tx0));
-                ty0 = fmaf(w.x, h[c].y, fmaf(w.y, h[c].x, ty0));
-                gg0 = fmaf(dl, m2, gg0);
-            }
-        }
         // T = sum w h; Re(tau conj(T)) = tau.x T.x + tau.y T.y
-        const float Tx = tx0 + tx1, Ty = ty0 + ty1, gg = gg0 + gg1;
+        double Tx, Ty, ggd;
+        kappa_amp_sums<NC>(y0s, dls, h, Tx, Ty, ggd);
+        const float gg = (float)ggd;
         const double dyd = 2.0 * ((double)tf.x * Tx + (double)tf.y * Ty) * ieb64 -
-                           ((double)tf.x * tf.x + (double)tf.y * tf.y) * (double)gg * ieb64 * ieb64;
+                           ((double)tf.x * tf.x + (double)tf.y * tf.y) * ggd * ieb64 * ieb64;
         double dlt = J0r - ((double)rr.hi + (double)rr.lo) * ieb64 + dyd;
         if (q > 0.f) {
             // prior term |tau - a|^2 / q with the difference taken in FP64 (a may be
@@ -447,23 +550,12 @@ __global__ void __launch_bounds__(128 * NT, NT == 1 ? 2 : 1) k_kappa_tc(DevGeom 
             }
         }
         // tau (FP32; J is evaluated exactly at the tau used) and the O(S) amplitude sums
-        float hh = 0.f, tx0 = 0.f, ty0 = 0.f, tx1 = 0.f, ty1 = 0.f, gg0 = 0.f, gg1 = 0.f;
+        float hh = 0.f;
         #pragma unroll
-        for (int c = 0; c < NC; ++c) {
-            hh = fmaf(h[c].x, h[c].x, fmaf(h[c].y, h[c].y, hh));
-            const float2 w = y0s[c];
-            const float dl = dls[c].x;
-            const float m2 = fmaf(h[c].x, h[c].x, h[c].y * h[c].y);
-            if (c & 1) {
-                tx1 = fmaf(w.x, h[c].x, fmaf(-w.y, h[c].y, tx1));
-                ty1 = fmaf(w.x, h[c].y, fmaf(w.y, h[c].x, ty1));
-                gg1 = fmaf(dl, m2, gg1);
-            } else {
-                tx0 = fmaf(w.x, h[c].x, fmaf(-w.y, h[c].y, tx0));
-                ty0 = fmaf(w.x, h[c].y, fmaf(w.y, h[c].x, ty0));
-                gg0 = fmaf(dl, m2, gg0);
-            }
-        }
+        for (int c = 0; c < NC; ++c) hh = fmaf(h[c].x, h[c].x, fmaf(h[c].y, h[c].y, hh));
+        double Tx, Ty, ggd;
+        kappa_amp_sums<NC>(y0s, dls, h, Tx, Ty, ggd);
+        const float gg = (float)ggd;
         const float ieb = 1.0f / ebf;
         const float alpha = (nps - hh * ieb) * ieb;
         const float zf = (float)zeta;
@@ -566,9 +658,8 @@ __global__ void __launch_bounds__(128 * NT, NT == 1 ? 2 : 1) k_kappa_tc(DevGeom 
             }
             tc::fence_before_sync();   // TMEM reads complete before the next group's MMAs
         }
-        const float Tx = tx0 + tx1, Ty = ty0 + ty1, gg = gg0 + gg1;
         const double dyd = 2.0 * ((double)tf.x * Tx + (double)tf.y * Ty) * ieb64 -
-                           ((double)tf.x * tf.x + (double)tf.y * tf.y) * (double)gg * ieb64 * ieb64;
+                           ((double)tf.x * tf.x + (double)tf.y * tf.y) * ggd * ieb64 * ieb64;
         double dlt = J0r - ((double)rr.hi + (double)rr.lo) * ieb64 + dyd;
         if (q > 0.f) {
             const double dx = (double)tf.x - zeta * mr, dyt = (double)tf.y - zeta * mi;
@@ -900,72 +991,6 @@ __device__ inline cff gent_value(const gent& g) {
 // double, A packed lower [S(S+1)/2] cff, then float2 z [Nz], factors [S][nfac | 1], cm [S], g [S], L packed [S(S+1)/2]
 // (also the partial sums g [S][Nf] before the Gram), then float amplitude [S],
 // A d [S], d [S], 1/L_kk [64], pivots [64] ff
-// e^{i 2 pi t} for a phase t = th + tl in cycles, as an unevaluated pair hi + lo good to
-// ~1e-9: the nearest 1/256 of a cycle from a table of FP64-rounded (hi, lo) values, turned
-// by the remainder angle phi (|phi| <= pi/256) through the angle-addition formulas with
-// cos phi - 1 and sin phi from their Taylor series (terms beyond phi^5 below 1e-14)
-__device__ inline void cis_pair(const float4* tab, float th, float tl, float2& hi, float2& lo) {
-    const float n = rintf(th * 256.0f);
-    const float rem = __fadd_rn(__fsub_rn(th, n * 0.00390625f), tl);   // th - n/256 is exact
-    const float4 T = tab[((int)n) & 255];                                // cos hi, cos lo, sin hi, sin lo
-    const float ph = 6.28318530717958648f * rem;
-    const float p2 = ph * ph;
-    const float cm1 = p2 * fmaf(p2, 1.0f / 24.0f, -0.5f);
-    const float sp = ph * fmaf(p2, fmaf(p2, 1.0f / 120.0f, -1.0f / 6.0f), 1.0f);
-    const float cr = fmaf(T.x, cm1, fmaf(-T.z, sp, T.y));
-    const float ci = fmaf(T.z, cm1, fmaf(T.x, sp, T.w));
-    fast_two_sum(T.x, cr, hi.x, lo.x);   // |cr| <= |T.x| unless T.x == 0
-    fast_two_sum(T.z, ci, hi.y, lo.y);
-}
-// the table: e^{i 2 pi n / 256}, n = 0..255, in FP64 and split into FP32 pairs
-__device__ inline void cis_table_fill(float4* tab, int tid, int nthreads) {
-    for (int n = tid; n < 256; n += nthreads) {
-        double sn, cs;
-        sincospi((double)n / 128.0, &sn, &cs);
-        const float ch = (float)cs, sh = (float)sn;
-        tab[n] = make_float4(ch, (float)(cs - (double)ch), sh, (float)(sn - (double)sh));
-    }
-}
-// steering factors of factors_from_geo_folded as (hi, lo) pairs (same phases, evaluated by
-// cis_pair); returns the amplitude A = lambda / (4 pi d)
-__device__ inline float factors_from_geo_pairs(const DevGeom& G, const float4* tab, float4 g, float2 gl, float2* fh,
-                                               float2* fl) {
-    const float d = g.x + g.y;
-    float h0, l0;
-    ff_frac_mul2(g.x, g.y, G.inv_lam_hi, G.inv_lam_lo, h0, l0);
-    for (int f = 0; f < G.Nf; ++f) {
-        float hf, lf, h, e;
-        ff_frac_mul2(g.x, g.y, G.fc_hi[f], G.fc_lo[f], hf, lf);
-        two_sum(h0, hf, h, e);
-        cis_pair(tab, -h, -(e + l0 + lf), fh[f], fl[f]);
-    }
-    for (int y = 0; y < G.My; ++y) {
-        const float p = __fmul_rn(G.py_l[y], g.z);
-        const float e = fmaf(G.py_l[y], gl.x, fmaf(G.py_lo[y], g.z, fmaf(G.py_l[y], g.z, -p)));
-        cis_pair(tab, p, e, fh[G.Nf + y], fl[G.Nf + y]);
-    }
-    for (int m = 0; m < G.Mz; ++m) {
-        const float p = __fmul_rn(G.pz_l[m], g.w);
-        const float e = fmaf(G.pz_l[m], gl.y, fmaf(G.pz_lo[m], g.w, fmaf(G.pz_l[m], g.w, -p)));
-        cis_pair(tab, p, e, fh[G.Nf + G.My + m], fl[G.Nf + G.My + m]);
-    }
-    return G.amp_c / d;
-}
-// (ah + al)(bh + bl) as hi + lo: exact products of the high parts, the rounding of their
-// sum, and the first-order cross terms
-__device__ inline float4 cpair_mul(float2 ah, float2 al, float2 bh, float2 bl) {
-    const float p1 = __fmul_rn(ah.x, bh.x), e1 = fmaf(ah.x, bh.x, -p1);
-    const float p2 = __fmul_rn(ah.y, bh.y), e2 = fmaf(ah.y, bh.y, -p2);
-    const float p3 = __fmul_rn(ah.x, bh.y), e3 = fmaf(ah.x, bh.y, -p3);
-    const float p4 = __fmul_rn(ah.y, bh.x), e4 = fmaf(ah.y, bh.x, -p4);
-    float rh, rl, ih, il;
-    two_sum(p1, -p2, rh, rl);
-    two_sum(p3, p4, ih, il);
-    rl += (e1 - e2) + fmaf(ah.x, bl.x, fmaf(al.x, bh.x, -fmaf(ah.y, bl.y, al.y * bh.y)));
-    il += (e3 + e4) + fmaf(ah.x, bl.y, fmaf(al.x, bh.y, fmaf(ah.y, bl.x, al.y * bh.x)));
-    return make_float4(rh, ih, rl, il);
-}
-
 __host__ __device__ inline size_t iota_blk_lsize(int S, int Nf) {
     const size_t a = (size_t)S * (S + 1) / 2, b = (size_t)S * Nf;
     return a > b ? a : b;
@@ -1413,8 +1438,10 @@ template <int SC>
 static void launch_kappa_sc(const DevGeom& G, const DevParams& Pm, const DevState& D, int S, int SCA, cudaStream_t st) {
     const int nfac = G.Nf + G.My + G.Mz;
     const int Nm = G.My * G.Mz;
-    const size_t fixed = (2 * (size_t)SC + (size_t)nfac * 256) * sizeof(float2);
-    const size_t per_f = (size_t)Nm * (SC + 1) * sizeof(float2);   // V rows and the low part of r0
+    // 1/lambda, w [2 SC], factors [nfac][256], low parts of a_y, a_z [My + Mz][256] (float2),
+    // alignment slack and the (hi, lo) cis table [256] (float4)
+    const size_t fixed = (2 * (size_t)SC + ((size_t)nfac + G.My + G.Mz) * 256) * sizeof(float2) + 16 + 256 * sizeof(float4);
+    const size_t per_f = (size_t)Nm * (SC + 1) * sizeof(float2) + Nm * sizeof(float);   // V rows, low part of r0, |V_k|^2
     dim3 grid((Pm.P + 255) / 256, S);
     if constexpr (SC == 64) {
         if (D.kB && kappa_tc_ok(G, SCA)) {
