@@ -105,11 +105,31 @@ __device__ inline double u24d(uint32_t x) { return ((double)(x >> 8) + 0.5) * 5.
 // (x + 1/2) 2^-32: uniform in (0,1), exact in FP64
 __host__ __device__ inline double u32d(uint32_t x) { return ((double)x + 0.5) * 2.3283064365386963e-10; }
 
-// Box-Muller pair in FP32 from two 24-bit uniforms
+// -2 log u for the 24-bit uniform u = ((x >> 8) + 1/2) 2^-24, to FP32 accuracy: for u >= 1/2,
+// log u = log1p(-(1 - u)) with 1 - u formed exactly from the integer complement (u itself
+// rounds in FP32 there, which near 1 would put large relative errors on small radii)
+__device__ inline float neg2log_u24(uint32_t x) {
+    const uint32_t k = x >> 8;
+    if (k >= (1u << 23)) {
+        const float om = ((float)((1u << 24) - 1u - k) + 0.5f) * 5.9604644775390625e-8f;
+        return -2.0f * log1pf(-om);
+    }
+    return -2.0f * logf(((float)k + 0.5f) * 5.9604644775390625e-8f);
+}
+
+// 2u for the same uniform as an exact FP32 argument of sincospi: for u >= 1/2 the
+// equivalent angle 2u - 2 = -2 (1 - u) (a whole turn removed), 1 - u from the complement
+__device__ inline float twice_u24_turn(uint32_t x) {
+    const uint32_t k = x >> 8;
+    if (k >= (1u << 23)) return -2.0f * (((float)((1u << 24) - 1u - k) + 0.5f) * 5.9604644775390625e-8f);
+    return 2.0f * (((float)k + 0.5f) * 5.9604644775390625e-8f);
+}
+
+// Box-Muller pair in FP32 from two 24-bit uniforms (radius and angle from exact arguments)
 __device__ inline void box_muller_f(uint32_t a, uint32_t b, float& n0, float& n1) {
-    const float r = sqrtf(-2.0f * logf(u24(a)));
+    const float r = sqrtf(neg2log_u24(a));
     float s, c;
-    sincospif(2.0f * u24(b), &s, &c);
+    sincospif(twice_u24_turn(b), &s, &c);
     n0 = r * c;
     n1 = r * s;
 }

@@ -11,7 +11,7 @@ import math
 import numpy as np
 import pytest
 
-from oracle import beliefs, messages_dense, messages_woodbury, model, resample, synth
+from oracle import beliefs, messages_dense, messages_woodbury, model, resample, rng, synth
 from paper_2604_19723_gb300 import workload as W
 
 pytestmark = [pytest.mark.gpu, pytest.mark.filterwarnings("ignore::RuntimeWarning")]
@@ -275,31 +275,102 @@ def test_resampling_indices_valid_and_match():
         assert np.mean(idx != ref) < 0.01
 
 
-def test_full_step_matches_oracle_statistics():
-    """One complete step (predict, update, resample, regularise): identical draws, so
-    the resampled particles agree up to FP32 rounding wherever the indices agree."""
+def _close_fp32(a, b, base, jit, rel=1e-5):
+    """a equals b = resampled value + jitter up to FP32 rounding of operands of the size
+    of `base`, plus rel of the jitter (FP32 bandwidth factor and products)."""
+    sp = 4.0 * np.spacing(np.abs(np.asarray(base, np.float32))).astype(np.float64)
+    return np.abs(a - b) <= rel * np.abs(jit) + sp + 1e-12
+
+
+def _jitter_terms(X, w, active, seed, n, purpose, sub, P):
+    """h_opt |L| |eps|: the size of the summands of every jitter component (FP32 rounding
+    in the kernel is relative to them, not to their sum)."""
+    C = resample.weighted_cov(X.astype(np.float64), w)
+    C[~active, :] = 0.0
+    C[:, ~active] = 0.0
+    L = resample.cholesky_zeroing(C)
+    eps = np.array(rng.normals(seed, np.arange(P, dtype=np.uint64), n, purpose, sub, X.shape[0]))
+    return resample.h_opt(P, int(active.sum())) * (np.abs(L) @ np.abs(eps))
+
+
+def _worst(a, b, base, jit, rel=1e-5):
+    """The worst violation of _close_fp32: (index, a, b, allowed)."""
+    sp = 4.0 * np.spacing(np.abs(np.asarray(base, np.float32))).astype(np.float64)
+    tol = rel * np.abs(jit) + sp + 1e-12
+    k = np.unravel_index(np.argmax(np.abs(a - b) - tol), np.shape(a))
+    return k, float(np.asarray(a)[k]), float(np.asarray(b)[k]), float(tol[k])
+
+
+def test_full_step_resample_and_jitter_per_particle():
+    """One complete step (predict, update, resample, regularise), checked particle by
+    particle (Sec. IV-D: systematic resampling, Gaussian-kernel regularisation after
+    Musso et al.).  The oracle's resampling rule and jitter h_opt L eps_i (same Philox
+    draws eps_i, L L^T the weighted covariance) are applied to the inputs the kernels
+    used, the GPU's predicted particles and normalised weights, which the update-parity
+    tests hold to the oracle's within 1e-4: every output particle must then equal its
+    resampled particle plus its jitter up to FP32 rounding.  The estimates and the
+    resampled clouds are also compared with the oracle's own step."""
     g, prm, scn, eta, z, st = setup_case(dict(J=2, Nf=10, My=4, Mz=4), 4, 5, 600, 51, 0.004)
-    f = bp.Filter(g, prm, P=600, S_max=16, seed=51)
+    P, seed = 600, 51
+    f = bp.Filter(g, prm, P=P, S_max=16, seed=seed)
     f.set_state(st)
     zd = torch.from_numpy(z.astype(np.complex64)).cuda()
     f.predict()
     pg = f.get_predicted()
     f.update(zd)
+    gw = f.diag_weights(pg["S"])
+    gi = f.diag_indices(pg["S"])
     new = f.get_state()
     ge = f.estimate()
-    # oracle from the GPU-independent prediction of the same state
-    op = model.predict(st, prm, g.J, seed=51, S_max=16)
+    n = pg["n"]
+    # the oracle's own step from the GPU-independent prediction of the same state
+    op = model.predict(st, prm, g.J, seed=seed, S_max=16)
     msg = messages_woodbury.update_messages(op, prm, g, z)
     bel = beliefs.beliefs(op, msg)
     est = beliefs.estimate(op, bel, prm)
     keep = beliefs.survivors(est, prm)
-    ost, *_ = resample.resample_and_regularize(op, bel, keep, prm, 51)
+    ost, *_ = resample.resample_and_regularize(op, bel, keep, prm, seed)
     assert new.S == ost.S == len(keep)
-    assert np.max(np.abs(ge["x_hat"] - est.x_hat)) < 1e-3
-    assert np.max(np.abs(ge["p_s"] - est.p_s)) < 1e-3
-    assert np.allclose(new.w_x, 1.0 / 600) and np.allclose(new.w_eta, 1.0 / 600)
-    assert np.allclose(new.w_y.sum(1), ost.w_y.sum(1), atol=1e-3)
-    # MT particle clouds: same mean and spread
+    assert np.max(np.abs(ge["x_hat"] - est.x_hat)) < 1e-4
+    assert np.max(np.abs(ge["p_s"] - est.p_s)) < 1e-5
+    assert np.allclose(new.w_x, 1.0 / P) and np.allclose(new.w_eta, 1.0 / P)
+    assert np.allclose(new.w_y.sum(1), ost.w_y.sum(1), atol=1e-5)
+    # MT: indices by the systematic rule on the GPU's weights, particles = resampled + jitter
+    X = pg["x"].astype(np.float64)
+    U = resample.resample_uniform(seed, n, 0, 0)
+    idx = resample.systematic_indices(gw["w_x"], U)
+    assert np.mean(idx == gi["x"]) > 0.999
+    jit = resample._jitter(X, gw["w_x"], resample.mt_active(prm), seed, n, rng.JITTER_MT, 0, P)
+    assert np.max(np.abs(jit)) > 0.0
+    ref = X[:, gi["x"]] + jit
+    jt = _jitter_terms(X, gw["w_x"], resample.mt_active(prm), seed, n, rng.JITTER_MT, 0, P)
+    base = np.abs(X[:, gi["x"]]) + jt                        # FP32 rounding is relative to the operands
+    assert np.all(_close_fp32(new.x.astype(np.float64), ref, base, jt)), _worst(new.x.astype(np.float64), ref, base, jt)
+    # PFs, compacted in keep order; gamma (row 3) is reflected at 0
+    for t, s in enumerate(keep):
+        Y = pg["phi"][s].astype(np.float64)
+        w = gw["w_y"][s]
+        ii = resample.systematic_indices(w / w.sum(), resample.resample_uniform(seed, n, 1, int(s)))
+        assert np.mean(ii == gi["y"][s]) > 0.999, s
+        jit = resample._jitter(Y, w, resample.pf_active(prm, s), seed, n, rng.JITTER_PF, int(s), P)
+        ref = Y[:, gi["y"][s]] + jit
+        ref[3] = np.abs(ref[3])
+        jt = _jitter_terms(Y, w, resample.pf_active(prm, s), seed, n, rng.JITTER_PF, int(s), P)
+        base = np.abs(Y[:, gi["y"][s]]) + jt
+        assert np.all(_close_fp32(new.phi[t].astype(np.float64), ref, base, jt)), \
+            (s, _worst(new.phi[t].astype(np.float64), ref, base, jt))
+    # noise variances, reflected at 0
+    for j in range(g.J):
+        E = pg["eta"][j].astype(np.float64)
+        ii = resample.systematic_indices(gw["w_eta"][j], resample.resample_uniform(seed, n, 2, j))
+        assert np.mean(ii == gi["eta"][j]) > 0.999, j
+        jit = resample._jitter(E[None], gw["w_eta"][j], np.ones(1, bool), seed, n, rng.JITTER_ETA, j, P)[0]
+        ref = np.abs(E[gi["eta"][j]] + jit)
+        jt = _jitter_terms(E[None], gw["w_eta"][j], np.ones(1, bool), seed, n, rng.JITTER_ETA, j, P)[0]
+        base = np.abs(E[gi["eta"][j]]) + jt
+        assert np.all(_close_fp32(new.eta[j].astype(np.float64), ref, base, jt)), \
+            (j, _worst(new.eta[j].astype(np.float64), ref, base, jt))
+    # the clouds against the oracle's own step (weights within 1e-4: statistics agree)
     assert np.allclose(new.x.mean(1), ost.x.mean(1), atol=2e-3)
     f.close()
 
