@@ -80,17 +80,12 @@ def iota_flops(P, S, J, Nf, My, Mz):
     return float(P) * J * per
 
 
-# DRAM bytes per launch from one ncu capture (dram__bytes_read.sum + dram__bytes_write.sum,
-# a single-pass metric set, at the full size of the workload), valid while the kernel
-# sources hash to the recorded value.
-TRAFFIC_RECORDS = {
-    "k_kappa": {"workload": "scale_64x100k", "P": 100000, "bytes": 923.59e6,
-                "sources_sha256": "a28bd4669d6f629dd45eb990cdfd9b5158b3111be47910162252d5d943efd458",
-                "profile": "profiles/dram_scale_64x100k.md"},
-    "k_iota_blk": {"workload": "scale_64x100k", "P": 100000, "bytes": 710.10e6,
-                   "sources_sha256": "a28bd4669d6f629dd45eb990cdfd9b5158b3111be47910162252d5d943efd458",
-                   "profile": "profiles/dram_scale_64x100k.md"},
-}
+# DRAM bytes per particle of one launch, from one ncu capture of that kernel alone on a
+# small case of the workload (dram__bytes_read.sum + dram__bytes_write.sum, -c 1); the
+# kernel's traffic grows in proportion to the particles (per-particle data and one read
+# of the per-(s, j) operand tiles per block), so a full launch moves P times this.  Valid
+# while the kernel sources hash to the recorded value.
+TRAFFIC_RECORDS = {}
 KERNEL_SOURCES = ("paper_2604_19723_gb300/csrc/k_like.cu", "paper_2604_19723_gb300/csrc/bp_kernels.cuh",
                   "paper_2604_19723_gb300/csrc/bp_internal.cuh", "paper_2604_19723_gb300/csrc/tc_sm100.cuh")
 
@@ -106,9 +101,9 @@ def kernel_sources_sha256():
 
 def traffic_for(kernel, workload, P):
     rec = TRAFFIC_RECORDS.get(kernel)
-    if not rec or rec["bytes"] is None or rec["workload"] != workload or rec["P"] != P:
+    if not rec or rec["workload"] != workload or rec["sources_sha256"] != kernel_sources_sha256():
         return None
-    return rec["bytes"] if rec["sources_sha256"] == kernel_sources_sha256() else None
+    return rec["bytes_per_particle"] * P
 
 
 def reduce_max(x, world, device):
@@ -384,7 +379,9 @@ def run_gpu(args, rank, world):
     def roof(name):
         ms, fl = per_kernel[name]
         a = fl / (ms * 1e-3) / 1e12
-        label = name if (name != "k_iota_blk" or S >= 24) else "k_iota (FP32) + k_iota_blk (flagged particles)"
+        label = name if name != "k_iota_blk" else (
+            "k_iota_bulk (FP32, every particle) + k_iota_select + k_iota_blk (float-float, queued particles)"
+            if S >= 24 else "k_iota (FP32) + k_iota_blk (flagged particles)")
         r = {"bound": "alu", "kernel": label, "achieved": a, "peak": peak_alu, "unit": "TFLOP/s",
              "frac": a / peak_alu, "traffic": traffic_for(name, args.workload, P), "ms_per_launch": ms,
              "peak_basis": f"FP32 FMA lanes: {SMS} SMs x {FP32_LANES_PER_SM} x 2 flop x {sm_mhz:.0f} MHz "
@@ -428,7 +425,7 @@ def run_gpu(args, rank, world):
            "e2e": {"value": world * P * g.J / (t_e2e * 1e-3), "unit": UNIT, "h2d_bytes_per_step": h2d,
                    "d2h_bytes_per_step": d2h, "ms_per_step": t_e2e},
            "gpu_launches": int(launches), "clocks": clocks,
-           "iota_fp64_repaired_per_step": float(np.mean(repaired)) if repaired else 0.0}
+           "iota_floatfloat_particles_per_step": float(np.mean(repaired)) if repaired else 0.0}
     if rank == 0 and not args.no_cpu_baseline:
         out["cpu_baseline"] = cpu_baseline(wl, g, prm, scn, args.cpu_particles, z_all[:1].cpu().numpy())
     f.close()

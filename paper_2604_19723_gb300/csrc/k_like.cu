@@ -44,12 +44,36 @@ __device__ __forceinline__ void ff_acc_prod(ff& acc, float a, float b) {
 }
 
 // The O(S) amplitude sums of the PF likelihood in the eigenbasis, T = sum_c w_c h_c and
-// gg = sum_c |h_c|^2 / lambda_c, in float-float from the FP32 factors: with PFs that nearly
-// duplicate one another both are large and almost cancel in 2 Re(tau conj T)/eta_bar -
-// |tau|^2 gg/eta_bar^2, and FP32 sums of them put ~1e-4 on normalised weights
-template <int NC>
-__device__ inline void kappa_amp_sums(const float2* w, const float2* dl, const float2 (&h)[NC], double& Tx, double& Ty,
-                                      double& gg) {
+// gg = sum_c |h_c|^2 / lambda_c, enter as 2 Re(tau conj T)/eta_bar - |tau|^2 gg/eta_bar^2.  Two
+// FP32 chains each put ~5e-7 of the terms' size on the result; where the terms, with |tau|^2
+// taken as its prior second moment t2 = |zeta mu|^2 + q, exceed 2 nats (a strong path, or a
+// PF that nearly duplicates others: the two then largely cancel) they are summed again in
+// float-float from exact products (REFINE; the 64-column kernels keep the FP32 sums, whose
+// registers the refinement would spill)
+template <int NC, bool REFINE>
+__device__ inline void kappa_amp_sums(const float2* w, const float2* dl, const float2 (&h)[NC], float t2, float ieb,
+                                      double& Tx, double& Ty, double& gg) {
+    float tx0 = 0.f, ty0 = 0.f, tx1 = 0.f, ty1 = 0.f, gg0 = 0.f, gg1 = 0.f;
+    #pragma unroll
+    for (int c = 0; c < NC; ++c) {
+        const float2 wc = w[c];
+        const float m2 = fmaf(h[c].x, h[c].x, h[c].y * h[c].y);
+        if (c & 1) {
+            tx1 = fmaf(wc.x, h[c].x, fmaf(-wc.y, h[c].y, tx1));
+            ty1 = fmaf(wc.x, h[c].y, fmaf(wc.y, h[c].x, ty1));
+            gg1 = fmaf(dl[c].x, m2, gg1);
+        } else {
+            tx0 = fmaf(wc.x, h[c].x, fmaf(-wc.y, h[c].y, tx0));
+            ty0 = fmaf(wc.x, h[c].y, fmaf(wc.y, h[c].x, ty0));
+            gg0 = fmaf(dl[c].x, m2, gg0);
+        }
+    }
+    Tx = (double)(tx0 + tx1);
+    Ty = (double)(ty0 + ty1);
+    gg = (double)(gg0 + gg1);
+    if constexpr (!REFINE) return;
+    const float mag = sqrtf(t2 * (float)(Tx * Tx + Ty * Ty)) * ieb + t2 * (float)gg * ieb * ieb;
+    if (!(mag > 2.0f)) return;
     ff tx{0.f, 0.f}, ty{0.f, 0.f}, g{0.f, 0.f};
     #pragma unroll
     for (int c = 0; c < NC; ++c) {
@@ -324,7 +348,7 @@ __global__ void __launch_bounds__(256, (SC <= 16 ? 2 : 1)) k_kappa(DevGeom G, De
         // y0^H x_amp = sum_c conj(w_c) x_c = conj(sum_c w_c h_c), |x_amp|^2 = sum_c |h_c|^2/lambda_c
         // T = sum w h; Re(tau conj(T)) = tau.x T.x + tau.y T.y
         double Tx, Ty, ggd;
-        kappa_amp_sums<NC>(y0s, dls, h, Tx, Ty, ggd);
+        kappa_amp_sums<NC, (SC <= 32)>(y0s, dls, h, zf * zf * (mrf * mrf + mif * mif) + fmaxf(q, 0.f), ieb, Tx, Ty, ggd);
         const float gg = (float)ggd;
         const double dyd = 2.0 * ((double)tf.x * Tx + (double)tf.y * Ty) * ieb64 -
                            ((double)tf.x * tf.x + (double)tf.y * tf.y) * ggd * ieb64 * ieb64;
@@ -553,15 +577,15 @@ __global__ void __launch_bounds__(128 * NT, NT == 1 ? 2 : 1) k_kappa_tc(DevGeom 
         float hh = 0.f;
         #pragma unroll
         for (int c = 0; c < NC; ++c) hh = fmaf(h[c].x, h[c].x, fmaf(h[c].y, h[c].y, hh));
-        double Tx, Ty, ggd;
-        kappa_amp_sums<NC>(y0s, dls, h, Tx, Ty, ggd);
-        const float gg = (float)ggd;
         const float ieb = 1.0f / ebf;
         const float alpha = (nps - hh * ieb) * ieb;
         const float zf = (float)zeta;
         const float2 af = make_float2(zf * mrf, zf * mif);
         const float q = (gmf + (mrf * mrf + mif * mif) * (1.0f - zf)) * zf;
         const float iq = (q > 0.f) ? 1.0f / q : 0.f;
+        double Tx, Ty, ggd;
+        kappa_amp_sums<NC, false>(y0s, dls, h, zf * zf * (mrf * mrf + mif * mif) + fmaxf(q, 0.f), ieb, Tx, Ty, ggd);
+        const float gg = (float)ggd;
         float2 tf = af;
         if (q > 0.f) {
             const float den = alpha + iq;
