@@ -440,7 +440,7 @@ bp_status bp_set_mt_proposal(bp_handle* h, bp_mlp* net);
  * phases common to all PAs (coherent = 1) or drawn per PA (coherent = 0), complex
  * Gaussian noise of variance eta), the input row at the
  * predicted mean as above, and the target u that carries the particle's F x_{n-1} to the
- * true successor (least squares through Gamma).  0 <= K <= 8, J <= 4.  Synchronous. */
+ * true successor (least squares through Gamma).  0 <= K <= 64, J <= 4.  Synchronous. */
 bp_status bp_lp_dataset(const bp_geometry* geom, const bp_params* prm, int K, const double* sfv, const double* rho_abs,
                         double eta, int coherent, double err_pos, double err_vel, double spread_pos, double spread_vel, int n,
                         uint64_t seed, float* X_dev, float* T_dev, void* cuda_stream);

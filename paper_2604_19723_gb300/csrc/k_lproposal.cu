@@ -187,7 +187,7 @@ struct LpData {
     double eta, err_pos, err_vel, spr_pos, spr_vel;
 };
 
-constexpr int LP_KMAX = 8;
+constexpr int LP_KMAX = 64;
 
 // per-warp shared memory of the dataset kernel: Kronecker factors b_f, a_y, a_z of the
 // K + 1 true components and of the LoS at the predicted mean, for one PA
@@ -242,7 +242,7 @@ __global__ void k_lp_dataset(DevGeom G, DevParams Pm, LpData L, int nsamp, float
         // to all PAs (coherent data) or drawn per PA (noncoherent data)
         double amp_r[LP_KMAX + 1], amp_i[LP_KMAX + 1];
         for (int c = 0; c <= L.K; ++c) {
-            const U4 pr = draw(Pm, i, 0, RNG_LP_DATA, 4, L.coherent ? c : c + 32 * (j + 1));
+            const U4 pr = draw(Pm, i, 0, RNG_LP_DATA, 4, L.coherent ? c : c + 128 * (j + 1));
             double sp, cp;
             sincospi(2.0 * u24d(pr.x), &sp, &cp);
             amp_r[c] = L.rho_abs[c] * cp;

@@ -22,6 +22,9 @@ import numpy as np
 
 from . import bp
 from . import workload as W
+from .ospa import ospa
+
+OSPA_C = 1.0   # cut-off of the map's OSPA distance [m]; order p = 2
 
 
 def scenario_model(name: str, seed: int):
@@ -69,6 +72,7 @@ def run(name: str, net, runs: int, steps: int, P: int, seed: int) -> Dict:
     wl = W.workload(name)
     g, prm = wl["geom"], wl["params"]
     err, ess = np.full((runs, steps), np.nan), np.full((runs, steps), np.nan)
+    osp = np.full((runs, steps), np.nan)
     step_ms = []
     wall = 0.0
     stream = torch.cuda.Stream()
@@ -99,31 +103,53 @@ def run(name: str, net, runs: int, steps: int, P: int, seed: int) -> Dict:
                 step_ms.append(e0.elapsed_time(e1))
                 err[r, n] = np.linalg.norm(e["x_hat"][:3] - scn.x_true[n + 1, :3])
                 ess[r, n] = e["ess_x"]
+                decl = [s for s in range(1, e["S"]) if e["declared"][s]]
+                osp[r, n] = ospa(e["phi_hat"][decl, :3].reshape(-1, 3), scn.sfv_true, OSPA_C, 2.0)
         finally:
             wall += time.perf_counter() - t0
             f.close()
-    return dict(err=err, ess=ess, wall_s=wall, step_ms=step_ms)
+    return dict(err=err, ess=ess, ospa=osp, wall_s=wall, step_ms=step_ms)
 
 
 def compare(name: str = "paper_exp1_proposal", runs: int = 4, steps: int = 50, P: int = 2000, seed: int = 500,
-            train: Dict = None, P_transition: int = None) -> Dict:
-    """The same scenes with the learned proposal at P particles and with the transition
-    proposal at P_transition (default P)."""
+            train: Dict = None, P_transition: int = None, P_more=()) -> Dict:
+    """The same scenes with the learned proposal at P particles (and at every count in
+    P_more) and with the transition proposal at P_transition (default P)."""
     train = train or train_proposal(name)
     with_net = run(name, train["net"], runs, steps, P, seed)
+    more = {int(q): run(name, train["net"], runs, steps, int(q), seed) for q in P_more}
     plain = run(name, None, runs, steps, P_transition or P, seed)
 
     def stats(d):
         e = d["err"]
         ms = float(np.mean(d["step_ms"])) if d["step_ms"] else float("nan")
+        run_rmse = np.sqrt(np.nanmean(e ** 2, axis=1))
+        run_ospa = np.nanmean(d["ospa"], axis=1)
         return dict(rmse=float(np.sqrt(np.nanmean(e ** 2))), median_err=float(np.nanmedian(e)),
+                    rmse_runs_min_max=[float(np.nanmin(run_rmse)), float(np.nanmax(run_rmse))],
+                    ospa=float(np.nanmean(d["ospa"])), ospa_final=float(np.nanmean(d["ospa"][:, -1])),
+                    ospa_runs_min_max=[float(np.nanmin(run_ospa)), float(np.nanmax(run_ospa))],
                     mean_ess=float(np.nanmean(d["ess"])), median_ess=float(np.nanmedian(d["ess"])),
                     failed_steps=int(np.sum(np.isnan(e))), ms_per_step=ms, steps_per_s=1e3 / ms,
                     wall_s=d["wall_s"])
 
     return dict(workload=name, runs=runs, steps=steps, P=P, P_transition=P_transition or P, loss=train["loss"],
-                train_s=train["train_s"],
-                data_s=train["data_s"], learned=stats(with_net), transition=stats(plain))
+                train_s=train["train_s"], data_s=train["data_s"], ospa_c_m=OSPA_C, ospa_p=2,
+                learned=stats(with_net), learned_more={q: stats(d) for q, d in more.items()},
+                transition=stats(plain))
+
+
+def c5(runs: int = 10, steps: int = 200, P: int = 10000, P_transition: int = 100000, samples: int = 1 << 20,
+       train_steps: int = 2000, seed: int = 900, P_more=()) -> Dict:
+    """The learned-proposal comparison at the 64-PF scale (64 PFs held fixed, J = 4,
+    Nz = 160, 200 spurious paths per step): the network trained on `samples` rows simulated
+    from the scene's model, the learned proposal at P particles against the transition
+    proposal at P_transition, map scored by OSPA over the declared PFs and the MT by RMSE."""
+    tr = train_proposal("scale_64x100k", n_samples=samples, steps=train_steps)
+    res = compare("scale_64x100k", runs=runs, steps=steps, P=P, seed=seed, train=tr, P_transition=P_transition,
+                  P_more=P_more)
+    res["samples"] = samples
+    return res
 
 
 def main(argv=None):
@@ -132,12 +158,20 @@ def main(argv=None):
     ap.add_argument("--runs", type=int, default=4)
     ap.add_argument("--steps", type=int, default=50)
     ap.add_argument("--P", type=int, default=2000)
-    ap.add_argument("--samples", type=int, default=1 << 17)
+    ap.add_argument("--samples", type=int, default=None, help="training rows (2^17; 2^20 with --c5)")
+    ap.add_argument("--P-more", type=int, nargs="*", default=[], help="--c5: further particle counts of the learned arm")
     ap.add_argument("--train-steps", type=int, default=2000)
     ap.add_argument("--lr", type=float, default=1e-3)
     ap.add_argument("--P-transition", type=int, default=None, help="particles of the transition-proposal runs")
+    ap.add_argument("--c5", action="store_true", help="the 64-PF comparison (10000 vs 100000 particles by default)")
     a = ap.parse_args(argv)
-    tr = train_proposal(a.workload, a.samples, a.train_steps, lr=a.lr)
+    if a.c5:
+        res = c5(runs=a.runs, steps=a.steps, P=a.P if a.P != 2000 else 10000, samples=a.samples or (1 << 20),
+                 train_steps=a.train_steps, P_more=a.P_more)
+        res.pop("loss", None)
+        print(json.dumps(res))
+        return
+    tr = train_proposal(a.workload, a.samples or (1 << 17), a.train_steps, lr=a.lr)
     res = compare(a.workload, a.runs, a.steps, a.P, train=tr, P_transition=a.P_transition)
     print(json.dumps(res))
 
