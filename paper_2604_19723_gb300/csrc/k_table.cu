@@ -37,10 +37,13 @@ __global__ void k_table(DevGeom G, DevParams Pm, DevState D, int S, int nsplit, 
     const int P = Pm.P, J = G.J, Nf = G.Nf, Nm = G.My * G.Mz, Nz = G.Nz;
     const int per = (P + nsplit - 1) / nsplit;
     const int p0 = split * per, p1 = min(P, p0 + per);
-    float2* Bf = sm;                                          // [chunk][3][Nf]
-    float2* Ayz = sm + (size_t)chunk * 3 * Nf;                // [chunk][Nm]
-    float2* Fyz = Ayz + (size_t)chunk * Nm;                   // [chunk][My + Mz] scratch
+    // per-particle rows with odd strides: each thread writes its own particle's row, so an
+    // even stride would put a warp's stores into a few banks
     const int nyz = G.My + G.Mz;
+    const int bst = (3 * Nf) | 1, ast = Nm | 1, yst = nyz | 1;
+    float2* Bf = sm;                                          // [chunk][bst]: 3 rows of Nf
+    float2* Ayz = sm + (size_t)chunk * bst;                   // [chunk][ast]
+    float2* Fyz = Ayz + (size_t)chunk * ast;                  // [chunk][yst] scratch
     const double W = D.W[s];
     const double zeta = D.zeta[s * J + j];
     const float pi = (float)(zeta * W);
@@ -58,8 +61,8 @@ __global__ void k_table(DevGeom G, DevParams Pm, DevState D, int S, int nsplit, 
         __syncthreads();
         for (int t = threadIdx.x; t < cn; t += blockDim.x) {
             const int p = c0 + t;
-            float2* b0 = Bf + (size_t)t * 3 * Nf;
-            float2* fy = Fyz + (size_t)t * nyz;
+            float2* b0 = Bf + (size_t)t * bst;
+            float2* fy = Fyz + (size_t)t * yst;
             const float2 c = factors_from_geo(G, geo[p], geol[p], b0, fy, fy + G.My, 1);
             const float gm = ph[3 * P + p], mr = ph[4 * P + p], mi = ph[5 * P + p];
             const float m2 = mr * mr + mi * mi;
@@ -77,7 +80,7 @@ __global__ void k_table(DevGeom G, DevParams Pm, DevState D, int S, int nsplit, 
             }
             for (int y = 0; y < G.My; ++y)
                 for (int m = 0; m < G.Mz; ++m)
-                    Ayz[(size_t)t * Nm + y * G.Mz + m] = cmul(fy[y], fy[G.My + m]);
+                    Ayz[(size_t)t * ast + y * G.Mz + m] = cmul(fy[y], fy[G.My + m]);
         }
         __syncthreads();
         float acc[EPT][3][2];
@@ -91,10 +94,10 @@ __global__ void k_table(DevGeom G, DevParams Pm, DevState D, int S, int nsplit, 
                 const int k = threadIdx.x + e * blockDim.x;
                 if (k < Nz) {
                     const int f = k / Nm, ym = k - f * Nm;
-                    const float2 a = Ayz[(size_t)t * Nm + ym];
+                    const float2 a = Ayz[(size_t)t * ast + ym];
                     #pragma unroll
                     for (int i = 0; i < 3; ++i) {
-                        const float2 bv = Bf[((size_t)t * 3 + i) * Nf + f];
+                        const float2 bv = Bf[(size_t)t * bst + i * Nf + f];
                         const float2 v = cmul(bv, a);
                         acc[e][i][0] += v.x;
                         acc[e][i][1] += v.y;
@@ -343,50 +346,203 @@ __device__ void jacobi_herm(typename cplx<T>::t* A, typename cplx<T>::t* U, int 
     }
 }
 
-// 16 warps: the FP64 rotation and product loops are latency bound at one block per SM
-constexpr int STAGE_THREADS = 512;
+// The same cyclic Jacobi in FP64 on a Hermitian matrix held as its packed lower triangle
+// (element (r, c), r >= c, at r (r + 1)/2 + c): half the shared memory of the full matrix.
+// Each round takes two barriers: the rotations of its disjoint pairs, then one pass that
+// applies them, to U by columns and to A by 2 x 2 blocks between pairs (rows of pair i,
+// columns of pair i', i >= i': block <- G_i^H block G_i'), the diagonal blocks set to
+// their exact diagonal form.  Same rotation convention and convergence test as
+// jacobi_herm; U is updated from its given start.
+__device__ inline int pk_idx(int r, int c) { return r * (r + 1) / 2 + c; }
+__device__ inline double2 pk_get(const double2* A, int r, int c) {
+    if (r >= c) return A[pk_idx(r, c)];
+    const double2 v = A[pk_idx(c, r)];
+    return make_double2(v.x, -v.y);
+}
+__device__ inline void pk_set(double2* A, int r, int c, double2 v) {
+    if (r >= c) A[pk_idx(r, c)] = v;
+    else A[pk_idx(c, r)] = make_double2(v.x, -v.y);
+}
 
-__global__ void __launch_bounds__(STAGE_THREADS) k_stage_kappa(DevGeom G, DevParams Pm, DevState D, int S, int SC, const float* z,
-                              const double* gram, double* V64) {
+__device__ void jacobi_herm_packed(double2* A, double2* U, int n, JRot<double>* rot, double* red, double tol,
+                                   double shift, int max_sweeps) {
+    const int tid = threadIdx.x, nt = blockDim.x;
+    __syncthreads();
+    if (n < 2) return;
+    const int n2 = n + (n & 1), half = n2 / 2;
+    auto pair_of = [&](int r, int i, int& p, int& q) {
+        int a, b;
+        if (i == 0) { a = n2 - 1; b = r; }
+        else { a = (r + i) % (n2 - 1); b = (r - i + n2 - 1) % (n2 - 1); }
+        p = min(a, b); q = max(a, b);
+    };
+    const int nblk = half * (half + 1) / 2;
+    for (int sweep = 0; sweep < max_sweeps; ++sweep) {
+        if (tid == 0) red[0] = 0.0;
+        __syncthreads();
+        bool viol = false;
+        for (int t = tid; t < n * (n - 1) / 2; t += nt) {   // strictly lower elements (r, c)
+            int r = (int)((sqrt(8.0 * t + 1.0) + 1.0) * 0.5);
+            while (r * (r - 1) / 2 > t) --r;
+            while ((r + 1) * r / 2 <= t) ++r;
+            const int c = t - r * (r - 1) / 2;
+            const double2 v = A[pk_idx(r, c)];
+            const double m2 = v.x * v.x + v.y * v.y;
+            const double dr = fabs(A[pk_idx(r, r)].x), dc = fabs(A[pk_idx(c, c)].x);
+            const double gr = fmax(dr - shift, 0.0), gc = fmax(dc - shift, 0.0);
+            if (!(m2 * gr * gc <= tol * (dr * dc) * (dr * dc))) viol = true;
+        }
+        if (viol) red[0] = 1.0;
+        __syncthreads();
+        const bool done = (red[0] == 0.0);
+        __syncthreads();
+        if (done) break;
+        for (int r = 0; r < n2 - 1; ++r) {
+            for (int i = tid; i < half; i += nt) {
+                int p, q;
+                pair_of(r, i, p, q);
+                JRot<double> g{1.0, 0.0, 1.0, 0.0};
+                if (q < n) {
+                    const double2 apq = pk_get(A, p, q);
+                    const double m = sqrt(apq.x * apq.x + apq.y * apq.y);
+                    const double dp = fabs(A[pk_idx(p, p)].x), dq = fabs(A[pk_idx(q, q)].x);
+                    const bool small = m * m * fmax(dp - shift, 0.0) * fmax(dq - shift, 0.0) <= tol * (dp * dq) * (dp * dq);
+                    if (!small && m > 1e-30) {
+                        const double zeta = (A[pk_idx(q, q)].x - A[pk_idx(p, p)].x) / (2.0 * m);
+                        const double t = (zeta >= 0.0 ? 1.0 : -1.0) / (fabs(zeta) + sqrt(1.0 + zeta * zeta));
+                        const double c = 1.0 / sqrt(1.0 + t * t);
+                        g = JRot<double>{c, t * c, apq.x / m, apq.y / m};
+                    }
+                }
+                rot[i] = g;
+            }
+            __syncthreads();
+            // U by columns: (u_p, u_q) <- (c u_p - s e^{-i phi} u_q, s u_p + c e^{-i phi} u_q)
+            for (int t = tid; t < half * n; t += nt) {
+                const int i = t / n, row = t - i * n;
+                int p, q;
+                pair_of(r, i, p, q);
+                if (q >= n) continue;
+                const JRot<double> g = rot[i];
+                if (g.s == 0.0) continue;
+                const double2 xp = U[row * n + p], xq = U[row * n + q];
+                const double eqx = g.er * xq.x + g.ei * xq.y, eqy = g.er * xq.y - g.ei * xq.x;
+                U[row * n + p] = make_double2(g.c * xp.x - g.s * eqx, g.c * xp.y - g.s * eqy);
+                U[row * n + q] = make_double2(g.s * xp.x + g.c * eqx, g.s * xp.y + g.c * eqy);
+            }
+            // A by 2 x 2 blocks: rows of pair i, columns of pair i' <= i
+            for (int b = tid; b < nblk; b += nt) {
+                int i = (int)((sqrt(8.0 * b + 1.0) - 1.0) * 0.5);
+                while ((i + 1) * (i + 2) / 2 <= b) ++i;
+                while (i * (i + 1) / 2 > b) --i;
+                const int i2 = b - i * (i + 1) / 2;
+                const JRot<double> g1 = rot[i], g2 = rot[i2];
+                if (g1.s == 0.0 && g2.s == 0.0) continue;
+                int p1, q1, p2, q2;
+                pair_of(r, i, p1, q1);
+                pair_of(r, i2, p2, q2);
+                const bool v1 = q1 < n, v2 = q2 < n;   // the ghost index of odd n pairs with one real index
+                if (i == i2) {
+                    if (!v1) continue;
+                    // G^H [[a_pp, a_pq], [a_qp, a_qq]] G: diagonal by construction of the rotation
+                    const double2 apq = pk_get(A, p1, q1);
+                    const double app = A[pk_idx(p1, p1)].x, aqq = A[pk_idx(q1, q1)].x;
+                    const double re = g1.er * apq.x + g1.ei * apq.y;      // Re(e^{-i phi} a_pq) = |a_pq|
+                    const double c = g1.c, s = g1.s;
+                    const double npp = c * c * app - 2.0 * c * s * re + s * s * aqq;
+                    const double nqq = s * s * app + 2.0 * c * s * re + c * c * aqq;
+                    A[pk_idx(p1, p1)] = make_double2(npp, 0.0);
+                    A[pk_idx(q1, q1)] = make_double2(nqq, 0.0);
+                    A[pk_idx(q1, p1)] = make_double2(0.0, 0.0);
+                    continue;
+                }
+                // block X = [[x00, x01], [x10, x11]] at rows (p1, q1), columns (p2, q2)
+                double2 x00 = pk_get(A, p1, p2);
+                double2 x01 = v2 ? pk_get(A, p1, q2) : make_double2(0.0, 0.0);
+                double2 x10 = v1 ? pk_get(A, q1, p2) : make_double2(0.0, 0.0);
+                double2 x11 = (v1 && v2) ? pk_get(A, q1, q2) : make_double2(0.0, 0.0);
+                if (g2.s != 0.0) {   // X G2: columns (c x_p - s e^{-i phi} x_q, s x_p + c e^{-i phi} x_q)
+                    auto colrot = [&](double2& xp, double2& xq) {
+                        const double ex = g2.er * xq.x + g2.ei * xq.y, ey = g2.er * xq.y - g2.ei * xq.x;
+                        const double2 np = make_double2(g2.c * xp.x - g2.s * ex, g2.c * xp.y - g2.s * ey);
+                        const double2 nq = make_double2(g2.s * xp.x + g2.c * ex, g2.s * xp.y + g2.c * ey);
+                        xp = np; xq = nq;
+                    };
+                    colrot(x00, x01);
+                    colrot(x10, x11);
+                }
+                if (g1.s != 0.0) {   // G1^H X: rows (c a_p - s e^{i phi} a_q, s a_p + c e^{i phi} a_q)
+                    auto rowrot = [&](double2& ap, double2& aq) {
+                        const double ex = g1.er * aq.x - g1.ei * aq.y, ey = g1.er * aq.y + g1.ei * aq.x;
+                        const double2 np = make_double2(g1.c * ap.x - g1.s * ex, g1.c * ap.y - g1.s * ey);
+                        const double2 nq = make_double2(g1.s * ap.x + g1.c * ex, g1.s * ap.y + g1.c * ey);
+                        ap = np; aq = nq;
+                    };
+                    rowrot(x00, x10);
+                    rowrot(x01, x11);
+                }
+                pk_set(A, p1, p2, x00);
+                if (v2) pk_set(A, p1, q2, x01);
+                if (v1) pk_set(A, q1, p2, x10);
+                if (v1 && v2) pk_set(A, q1, q2, x11);
+            }
+            __syncthreads();
+        }
+    }
+}
+
+// 12 warps per block and two blocks per SM (106 KB of shared memory each): the FP64
+// rotation and product loops are latency bound
+constexpr int STAGE_THREADS = 384;
+
+__host__ __device__ inline size_t stage_kappa_smem(int K) {
+    return ((size_t)K * K + (size_t)K * (K + 1) / 2 + (size_t)(STAGE_THREADS / 32) * K) * sizeof(double2) +
+           8 * sizeof(double) + 32 * sizeof(JRot<double>);
+}
+
+__global__ void __launch_bounds__(STAGE_THREADS) k_stage_kappa(DevGeom G, DevParams Pm, DevState D, int S, int SC,
+                                                                  const float* z, const double* gram, double* V64) {
     const int s = blockIdx.x, j = blockIdx.y;
     const int J = G.J, Nz = G.Nz, SM = Pm.S_max;
     const int K = S - 1;                          // columns of M_{-s}
     const double eb = D.eta_bar[j];
     const size_t plane = (size_t)SM * J * Nz;
     const double2* tab = reinterpret_cast<const double2*>(D.tab);
+    const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5, nw = blockDim.x >> 5;
     extern __shared__ double2 sh[];
-    double2* R = sh;                             // K x K: B, then U^H B U, then its eigenvalues
-    double2* Ue = R + (size_t)K * K;             // K x K eigenvectors (columns)
-    double2* Wk = Ue + (size_t)K * K;            // K x K work: the FP32 solve (A32, U32), then B U
-    float2* A32 = reinterpret_cast<float2*>(Wk);
-    float2* U32 = A32 + (size_t)K * K;
-    double2* ye = Wk + (size_t)K * K;            // V^H e0 / eb      (K)
+    double2* Ue = sh;                            // K x K eigenvectors (columns), FP64
+    double2* Rp = Ue + (size_t)K * K;            // packed lower triangle of U^H B U, then the eigenvalues
+    float2* A32 = reinterpret_cast<float2*>(Ue); // the FP32 solve first: A32 in Ue's bytes, U32 in Rp's
+    float2* U32 = reinterpret_cast<float2*>(Rp); // (K^2 float2 <= K (K + 1)/2 double2)
+    double2* scr = Rp + (size_t)K * (K + 1) / 2; // [nw][K] columns of B U; then the projections below
+    double2* ye = scr;                           // V^H e0 / eb      (K)
     double2* vm = ye + K;                        // V^H m^w          (K)
     double2* v4 = vm + K;                        // V^H mu4          (K)
     double* dinv = reinterpret_cast<double*>(v4 + K);   // lambda^{-1/2}  (K)
-    double* red = dinv + K;                      // reduction scratch [8]
+    double* red = reinterpret_cast<double*>(scr + (size_t)nw * K);   // reduction scratch [8]
     JRot<double>* rot = reinterpret_cast<JRot<double>*>(red + 8);   // Jacobi pair rotations [32]
     JRot<float>* rot32 = reinterpret_cast<JRot<float>*>(rot);
     const double2* Gm = reinterpret_cast<const double2*>(gram) + (size_t)j * SM * SM;
     // column map c -> s'
     auto col = [&](int c) { return c < s ? c : c + 1; };
-    // B = I + G_{-s}/eb (Hermitian), then B = U diag(lambda) U^H
-    for (int t = threadIdx.x; t < K * K; t += blockDim.x) {
-        const int r = t / K, c = t - r * K;
+    // B = I + G_{-s}/eb (Hermitian), read from the Gram matrix in global memory (L2)
+    auto Bv = [&](int r, int c) {
         double2 g = Gm[col(r) * SM + col(c)];
         g.x /= eb; g.y /= eb;
         if (r == c) { g.x += 1.0; g.y = 0.0; }
-        R[t] = g;
-    }
+        return g;
+    };
     // eigenvectors to FP32 accuracy by FP32 sweeps, then B rotated into that basis in FP64
     // (nearly diagonal) and finished by FP64 sweeps
-    for (int t = threadIdx.x; t < K * K; t += blockDim.x) A32[t] = make_float2((float)R[t].x, (float)R[t].y);
+    for (int t = threadIdx.x; t < K * K; t += blockDim.x) {
+        const double2 g = Bv(t / K, t % K);
+        A32[t] = make_float2((float)g.x, (float)g.y);
+    }
     jacobi_herm<float>(A32, U32, K, rot32, red, true, 1e-13, 1.0, 10);
     for (int t = threadIdx.x; t < K * K; t += blockDim.x) Ue[t] = make_double2((double)U32[t].x, (double)U32[t].y);
     __syncthreads();
     {   // the FP32 columns are orthonormal to ~1e-5 only: modified Gram-Schmidt in FP64, so
         // that U^H B U below is a similarity transform of B
-        const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5, nw = blockDim.x >> 5;
         for (int c = 0; c < K; ++c) {
             if (wid == 0) {
                 double a = 0.0;
@@ -413,30 +569,34 @@ __global__ void __launch_bounds__(STAGE_THREADS) k_stage_kappa(DevGeom G, DevPar
             __syncthreads();
         }
     }
-    for (int t = threadIdx.x; t < K * K; t += blockDim.x) {          // Wk = B U
-        const int r = t / K, c = t - r * K;
-        double2 acc = make_double2(0.0, 0.0);
-        for (int m = 0; m < K; ++m) {
-            const double2 u = zmul(R[r * K + m], Ue[m * K + c]);
-            acc.x += u.x; acc.y += u.y;
+    // R = U^H B U (packed lower triangle), one column at a time per warp: v = B u_c, then
+    // R_rc = u_r^H v for r >= c
+    for (int c = wid; c < K; c += nw) {
+        double2* v = scr + (size_t)wid * K;
+        for (int m = lane; m < K; m += 32) {
+            double2 acc = make_double2(0.0, 0.0);
+            for (int n = 0; n < K; ++n) {
+                const double2 u = zmul(Bv(m, n), Ue[n * K + c]);
+                acc.x += u.x; acc.y += u.y;
+            }
+            v[m] = acc;
         }
-        Wk[t] = acc;
-    }
-    __syncthreads();
-    for (int t = threadIdx.x; t < K * K; t += blockDim.x) {          // R = U^H (B U)
-        const int r = t / K, c = t - r * K;
-        double2 acc = make_double2(0.0, 0.0);
-        for (int m = 0; m < K; ++m) {
-            const double2 u = zmulc(Ue[m * K + r], Wk[m * K + c]);
-            acc.x += u.x; acc.y += u.y;
+        __syncwarp();
+        for (int r = c + lane; r < K; r += 32) {
+            double2 acc = make_double2(0.0, 0.0);
+            for (int m = 0; m < K; ++m) {
+                const double2 u = zmulc(Ue[m * K + r], v[m]);
+                acc.x += u.x; acc.y += u.y;
+            }
+            Rp[pk_idx(r, c)] = (r == c) ? make_double2(acc.x, 0.0) : acc;
         }
-        R[t] = acc;
+        __syncwarp();
     }
     __syncthreads();
     // typically 2-3 sweeps; the weighted test at 1e-18 leaves ~1e-8 nats on the PR test
     // (emulated on 26- and 64-PF states)
-    jacobi_herm<double>(R, Ue, K, rot, red, false, 1e-18, 1.0, 8);
-    for (int c = threadIdx.x; c < K; c += blockDim.x) dinv[c] = 1.0 / sqrt(fmax(R[c * K + c].x, 1.0));
+    jacobi_herm_packed(Rp, Ue, K, rot, red, 1e-18, 1.0, 8);
+    for (int c = threadIdx.x; c < K; c += blockDim.x) dinv[c] = 1.0 / sqrt(fmax(Rp[pk_idx(c, c)].x, 1.0));
     __syncthreads();
     // V rows: v_k = m_k U diag(lambda)^{-1/2}; accumulate projections
     for (int t = threadIdx.x; t < 3 * K; t += blockDim.x) (t < K ? ye : (t < 2 * K ? vm : v4))[t % K] = make_double2(0, 0);
@@ -666,7 +826,7 @@ void launch_table(const DevGeom& G, const DevParams& Pm, const DevState& D, int 
     const int Nz = G.Nz;
     const int bs = Nz <= 256 ? ((Nz + 31) / 32) * 32 : 256;
     const int ept = (Nz + bs - 1) / bs;
-    const int per_particle = (3 * G.Nf + G.My * G.Mz + G.My + G.Mz) * (int)sizeof(float2);
+    const int per_particle = (((3 * G.Nf) | 1) + ((G.My * G.Mz) | 1) + ((G.My + G.Mz) | 1)) * (int)sizeof(float2);
     int chunk = 128;
     while (chunk > 16 && chunk * per_particle > 96 * 1024) chunk /= 2;
     const size_t smem = (size_t)chunk * per_particle;
@@ -691,8 +851,7 @@ void launch_stage(const DevGeom& G, const DevParams& Pm, const DevState& D, int 
     const int gx = min(64, (npair + 7) / 8);
     k_gram<<<dim3(gx, G.J), 256, 0, st>>>(G, Pm, D, S, z, gram, nu_b);
     const int K = S - 1;
-    const size_t sm1 = (3 * (size_t)K * K + 3 * (size_t)K) * sizeof(double2) + ((size_t)K + 8) * sizeof(double) +
-                       32 * sizeof(JRot<double>);
+    const size_t sm1 = stage_kappa_smem(K);
     smem_allow_max((const void*)k_stage_kappa);
     k_stage_kappa<<<dim3(S, G.J), STAGE_THREADS, sm1, st>>>(G, Pm, D, S, SC, z, gram, V64);
     const size_t sm2 = ((size_t)S * S + 3 * (size_t)S) * sizeof(double2);
