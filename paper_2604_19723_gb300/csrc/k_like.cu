@@ -395,6 +395,12 @@ __host__ __device__ inline int kappa_tc_groups(int Nf, int Nm) {
     return (Nf + kappa_tc_group_freqs(Nm) - 1) / kappa_tc_group_freqs(Nm);
 }
 __host__ __device__ inline int round16(int x) { return (x + 15) & ~15; }
+// operand region in floats: pass 1 A [NT][hi, lo][128 x KC] and one B slot [hi, lo][128 x KC];
+// pass 2 A [NT][hi, lo][128 x KC2] and two B slots [hi, lo][64 x KC2]
+__host__ __device__ inline int kappa_tc_region_floats(int KC, int NT) {
+    const int r1 = (2 * NT + 2) * 128 * KC, r2 = 2 * NT * 128 * KAPPA_TC_KC2 + 2 * 2 * KAPPA_TC_N2 * KAPPA_TC_KC2;
+    return r1 > r2 ? r1 : r2;
+}
 
 // NT 128-particle M tiles per block (threads 128 NT, TMEM columns 256 NT): NT = 1 lets two
 // blocks share an SM, so that one block's MMAs run while the other writes operands or
@@ -409,10 +415,10 @@ __global__ void __launch_bounds__(128 * NT, NT == 1 ? 2 : 1) k_kappa_tc(DevGeom 
     const int P = Pm.P, J = G.J, Nz = G.Nz, Nm = G.My * G.Mz, Nf = G.Nf;
     const int KC = 2 * Nm;                                     // pass-1 real K per frequency
     const int GF = kappa_tc_group_freqs(Nm), NG = kappa_tc_groups(Nf, Nm);
-    const int RF = max((2 * NT + 2) * 128 * KC, 2 * NT * 128 * KC2 + 2 * KAPPA_TC_N2 * KC2);   // operand region (floats)
+    const int RF = kappa_tc_region_floats(KC, NT);            // operand region (floats)
     float* sR = reinterpret_cast<float*>(sm4);
-    uint64_t* mbar = reinterpret_cast<uint64_t*>(sR + RF);    // [2]: MMAs done, B arrived
-    uint32_t* tslot = reinterpret_cast<uint32_t*>(mbar + 2);
+    uint64_t* mbar = reinterpret_cast<uint64_t*>(sR + RF);    // [3]: MMAs done, B slot 0, B slot 1 arrived
+    uint32_t* tslot = reinterpret_cast<uint32_t*>(mbar + 3);
     float4* r0s = reinterpret_cast<float4*>(sR + RF + 8);    // [Nz] r0 (hi.x, hi.y, lo.x, lo.y)
     float2* dls = reinterpret_cast<float2*>(r0s + Nz);        // [64] 1/lambda_c (.x)
     float2* y0s = dls + 64;                                   // [64] w_c
@@ -421,14 +427,45 @@ __global__ void __launch_bounds__(128 * NT, NT == 1 ? 2 : 1) k_kappa_tc(DevGeom 
     const int p = blockIdx.x * KT + tid;
     const bool act = p < P;
     const int pp = act ? p : 0;
-    const uint32_t mb_mma = tc::smem_u32(&mbar[0]), mb_b = tc::smem_u32(&mbar[1]);
-    uint32_t n_commit = 0, n_bulk = 0, n_waited_b = 0;
+    const uint32_t mb_mma = tc::smem_u32(&mbar[0]), mb_b0 = tc::smem_u32(&mbar[1]);   // slot sl: mb_b0 + 8 sl
+    uint32_t n_commit = 0;
+    uint32_t b_pend = 0, b_par = 0;   // thread 0: per B slot, a copy in flight / the parity of its next wait
     bool bad = false;
     if (warp == 0) tc::tmem_alloc(tslot, 256 * NT);
-    if (tid == 0) { tc::mbar_init(mb_mma, 1); tc::mbar_init(mb_b, 1); tc::mbar_init_fence(); }
+    if (tid == 0) { tc::mbar_init(mb_mma, 1); tc::mbar_init(mb_b0, 1); tc::mbar_init(mb_b0 + 8, 1); tc::mbar_init_fence(); }
     tc::fence_before_sync();
     __syncthreads();
     tc::fence_after_sync();
+    // B operand stream (thread 0): pass 1 takes one slot of 2 x 128 x KC floats at
+    // sR + 2 NT 128 KC; pass 2 two slots of 2 x 64 x KC2 floats after its A tiles, so that
+    // the copy of the next round's B runs under this round's MMAs.  A copy into a slot is
+    // issued only once the MMAs that read the slot's previous contents have completed.
+    const size_t bchunk1 = (size_t)2 * 128 * KC;
+    const size_t bslot2 = (size_t)2 * KAPPA_TC_N2 * KC2;
+    const int NQ = 4 * NG;   // pass-2 rounds per j
+    float* sB1 = sR + 2 * NT * 128 * KC;
+    float* sB2 = sR + 2 * NT * 128 * KC2;
+    auto issueB = [&](int sl, float* dst, const float* src, uint32_t bytes) {
+        if (tid != 0 || bad) return;
+        const uint32_t mb = mb_b0 + 8u * (uint32_t)sl;
+        tc::mbar_expect_tx(mb, bytes);
+        tc::bulk_g2s(tc::smem_u32(dst), src, bytes, mb);
+        b_pend |= 1u << sl;
+    };
+    auto waitB = [&](int sl) -> bool {   // thread 0
+        const uint32_t mb = mb_b0 + 8u * (uint32_t)sl;
+        if (!tc::mbar_wait(mb, (b_par >> sl) & 1u, KAPPA_TC_WAIT)) return false;
+        b_par ^= 1u << sl;
+        b_pend &= ~(1u << sl);
+        return true;
+    };
+    auto b1_src = [&](int j, int f) { return Bt1 + (((size_t)s * J + j) * Nf + f) * bchunk1; };
+    auto b2_src = [&](int j, int q) { return Bt2 + (((size_t)s * J + j) * NQ + q) * bslot2; };
+    auto b2_bytes = [&](int q) {
+        const int g = q >> 2, nk = min(GF, Nf - g * GF) * Nm;
+        return (uint32_t)(2 * (2 * round16(nk)) * KC2 * 4);
+    };
+    issueB(0, sB1, b1_src(0, 0), (uint32_t)(bchunk1 * 4));   // the first round's B, under the factor set-up
     const uint32_t tmem = *tslot;
     const uint32_t tlane = tmem + ((uint32_t)((warp & 3) * 32) << 16) + (uint32_t)(tile * 256);   // this thread's row
     const float* ph = D.phi[D.cur] + (size_t)s * 6 * P;
@@ -437,24 +474,20 @@ __global__ void __launch_bounds__(128 * NT, NT == 1 ? 2 : 1) k_kappa_tc(DevGeom 
     const float gmf = ph[3 * P + pp];
     const float mrf = ph[4 * P + pp], mif = ph[5 * P + pp];
     const double mr = mrf, mi = mif;
-    // one round: the B chunk by bulk copy (thread 0), A written by every thread (writeA),
-    // then thread 0 issues the 3xTF32 MMAs of both tiles (K in steps of 8)
-    auto round = [&](const float* gsrc, uint32_t bbytes, float* sA, float* sB, int Kt, uint32_t bLoOff,
-                     uint32_t idesc, uint32_t dcol, bool accum0, auto&& writeA) {
+    // one round: once the previous round's MMAs are done, issueNext() starts a B copy
+    // (thread 0) and every thread writes A (writeA); after the barrier thread 0 waits for
+    // this round's B (slot sl) and issues the 3xTF32 MMAs of both tiles (K in steps of 8)
+    auto round = [&](int sl, float* sA, float* sB, int Kt, uint32_t bLoOff, uint32_t idesc, uint32_t dcol,
+                     bool accum0, auto&& issueNext, auto&& writeA) {
         if (n_commit > 0 && !bad && !tc::mbar_wait(mb_mma, (n_commit - 1) & 1u, KAPPA_TC_WAIT)) bad = true;
-        if (tid == 0 && !bad) {
-            tc::mbar_expect_tx(mb_b, bbytes);
-            tc::bulk_g2s(tc::smem_u32(sB), gsrc, bbytes, mb_b);
-            ++n_bulk;
-        }
+        issueNext();
         writeA();
         tc::fence_async_smem();
         tc::fence_before_sync();
         __syncthreads();
         tc::fence_after_sync();
         if (tid == 0 && !bad) {
-            if (!tc::mbar_wait(mb_b, n_waited_b & 1u, KAPPA_TC_WAIT)) bad = true;
-            else ++n_waited_b;
+            if (!waitB(sl)) bad = true;
             if (!bad) {
                 const uint32_t sbo = (uint32_t)(Kt / 4) * 128u;
                 const uint32_t bH = tc::smem_u32(sB), bL = bH + bLoOff;
@@ -508,17 +541,15 @@ __global__ void __launch_bounds__(128 * NT, NT == 1 ? 2 : 1) k_kappa_tc(DevGeom 
         float nps = 0.f;
         {
             float* sA = sR;
-            float* sB = sR + 2 * NT * 128 * KC;
             float* aHi = sA + (size_t)(tile * 2 + 0) * 128 * KC;
             float* aLo = sA + (size_t)(tile * 2 + 1) * 128 * KC;
-            const size_t bchunk = (size_t)2 * 128 * KC;
-            const float* gB = Bt1 + ((size_t)s * J + j) * Nf * bchunk;
             const uint32_t idesc = tc::idesc_tf32_f32(128, 128);
             // even frequencies accumulate in columns 0..127, odd ones in 128..255 (shorter
-            // FP32 accumulation chains; added when h is read back)
+            // FP32 accumulation chains; added when h is read back); the first frequency's B
+            // was issued before this j began
             for (int f = 0; f < Nf; ++f) {
-                round(gB + (size_t)f * bchunk, (uint32_t)(bchunk * 4), sA, sB, KC, (uint32_t)(128 * KC * 4), idesc,
-                      (uint32_t)((f & 1) * 128), f > 1, [&]() {
+                round(0, sA, sB1, KC, (uint32_t)(128 * KC * 4), idesc, (uint32_t)((f & 1) * 128), f > 1,
+                      [&]() { if (f > 0) issueB(0, sB1, b1_src(j, f), (uint32_t)(bchunk1 * 4)); }, [&]() {
                     const float2 cb = cmul(Fc, fb[f * KT]);
                     for (int y = 0; y < G.My; ++y) {
                         const float2 w = cmul(cb, fy[y * KT]);
@@ -538,6 +569,9 @@ __global__ void __launch_bounds__(128 * NT, NT == 1 ? 2 : 1) k_kappa_tc(DevGeom 
             }
         }
         wait_mma();
+        // pass 2's first two B tiles, under the read-back of h and the amplitude sums
+        issueB(0, sB2, b2_src(j, 0), b2_bytes(0));
+        issueB(1, sB2 + bslot2, b2_src(j, 1), b2_bytes(1));
         float2 h[NC];
         float2 pr;
         {
@@ -599,15 +633,19 @@ __global__ void __launch_bounds__(128 * NT, NT == 1 ? 2 : 1) k_kappa_tc(DevGeom 
             const int f0 = g * GF, nfg = min(GF, Nf - f0);
             const int nk = nfg * Nm, nkp = round16(nk), N2 = 2 * nkp;
             float* sA = sR;
-            float* sB = sR + 2 * NT * 128 * KC2;
             float* aHi = sA + (size_t)(tile * 2 + 0) * 128 * KC2;
             float* aLo = sA + (size_t)(tile * 2 + 1) * 128 * KC2;
             const uint32_t idesc = tc::idesc_tf32_f32(128, N2);
-            const float* gB = Bt2 + ((((size_t)s * J + j) * NG + g) * 4) * (size_t)(2 * KAPPA_TC_N2 * KC2);
             #pragma unroll
             for (int kc = 0; kc < 4; ++kc) {
-                round(gB + (size_t)kc * (2 * KAPPA_TC_N2 * KC2), (uint32_t)(2 * N2 * KC2 * 4), sA, sB, KC2,
-                      (uint32_t)(N2 * KC2 * 4), idesc, (uint32_t)(kc * KAPPA_TC_N2), false, [&]() {
+                // round q = 4 g + kc reads slot q & 1 = kc & 1; the copy of round q + 1 goes to
+                // the slot that round q - 1 read
+                const int q = 4 * g + kc;
+                round(kc & 1, sA, sB2 + (size_t)(kc & 1) * bslot2, KC2, (uint32_t)(N2 * KC2 * 4), idesc,
+                      (uint32_t)(kc * KAPPA_TC_N2), false, [&]() {
+                    if (q >= 1 && q + 1 < NQ)
+                        issueB((q + 1) & 1, sB2 + (size_t)((q + 1) & 1) * bslot2, b2_src(j, q + 1), b2_bytes(q + 1));
+                }, [&]() {
                     #pragma unroll
                     for (int c2 = 0; c2 < KC2 / 4; ++c2) {       // basis columns c, c + 1
                         const int c = kc * 16 + 2 * c2;
@@ -623,6 +661,11 @@ __global__ void __launch_bounds__(128 * NT, NT == 1 ? 2 : 1) k_kappa_tc(DevGeom 
                 });
             }
             wait_mma();
+            // every MMA of this j is done: the next j's first B tile, under the residuals
+            if (g == NG - 1 && j + 1 < J) issueB(0, sB1, b1_src(j + 1, 0), (uint32_t)(bchunk1 * 4));
+            // element (f, y, m) of the group walked in order; w = Fc b_f a_y formed as pass 1 formed it
+            int cf = f0, cy = 0, cm = 0;
+            float2 w = cmul(cmul(Fc, fb[f0 * KT]), fy[0]);
             for (int b = 0; b < nk; b += 8) {
                 // the four chunk accumulators, added pairwise: (a0 + a1) + (a2 + a3)
                 float vre[8], vim[8];
@@ -654,11 +697,12 @@ __global__ void __launch_bounds__(128 * NT, NT == 1 ? 2 : 1) k_kappa_tc(DevGeom 
                     const int kl = b + i;
                     if (kl >= nk) break;
                     const int k = f0 * Nm + kl;
-                    const int f = k / Nm, ym = k - f * Nm, y = ym / G.Mz, m = ym - y * G.Mz;
-                    // psi_k exactly as pass 1 formed it
-                    const float2 cb = cmul(Fc, fb[f * KT]);
-                    const float2 w = cmul(cb, fy[y * KT]);
-                    const float2 ps = cmul(w, fz[m * KT]);
+                    const float2 ps = cmul(w, fz[cm * KT]);   // psi_k exactly as pass 1 formed it
+                    if (++cm == G.Mz) {
+                        cm = 0;
+                        if (++cy == G.My) { cy = 0; ++cf; }
+                        if (kl + 1 < nk) w = cmul(cmul(Fc, fb[cf * KT]), fy[cy * KT]);
+                    }
                     const float vsx = vre[i], vsy = vim[i];
                     const float2 pp2 = make_float2(ps.x - vsx * ieb, ps.y - vsy * ieb);
                     pn += pp2.x * pp2.x + pp2.y * pp2.y;
@@ -697,7 +741,8 @@ __global__ void __launch_bounds__(128 * NT, NT == 1 ? 2 : 1) k_kappa_tc(DevGeom 
     if (bad && (tid & 31) == 0) atomicOr(D.kerr, 1);
     if (tid == 0) {
         // after a timeout: let the copies and MMAs still in flight land (bounded)
-        for (uint32_t q = n_waited_b; q < n_bulk; ++q) tc::mbar_wait(mb_b, q & 1u, KAPPA_TC_WAIT);
+        for (int sl = 0; sl < 2; ++sl)
+            if ((b_pend >> sl) & 1u) waitB(sl);
         if (n_commit > 0) tc::mbar_wait(mb_mma, (n_commit - 1) & 1u, KAPPA_TC_WAIT);
     }
     tc::fence_before_sync();
@@ -1419,13 +1464,13 @@ __global__ void k_kappa_btile2(DevGeom G, DevState D, int SCA, float* __restrict
     }
 }
 
-// dynamic shared memory of k_kappa_tc: the operand region (pass 1: A [2][hi, lo][128 x 2Nm],
-// B [hi, lo][128 x 2Nm]; pass 2: A [2][hi, lo][128 x 32], B [hi, lo][64 x 32]), barriers,
+// dynamic shared memory of k_kappa_tc: the operand region (pass 1: A [NT][hi, lo][128 x 2Nm],
+// B [hi, lo][128 x 2Nm]; pass 2: A [NT][hi, lo][128 x 32], two B slots [hi, lo][64 x 32]), barriers,
 // r0 (hi, lo) per element, 1/lambda_c and w_c, and the factors of 256 particles
 constexpr int KAPPA_TC_NT = 1;   // M tiles per block of the launched variant
 static size_t kappa_tc_smem(const DevGeom& G, int NT = KAPPA_TC_NT) {
     const size_t Nm = (size_t)G.My * G.Mz, nfac = (size_t)G.Nf + G.My + G.Mz;
-    const size_t rf = std::max<size_t>((2 * NT + 2) * 128 * 2 * Nm, 2 * NT * 128 * KAPPA_TC_KC2 + 2 * KAPPA_TC_N2 * KAPPA_TC_KC2);
+    const size_t rf = (size_t)kappa_tc_region_floats(2 * (int)Nm, NT);
     return rf * sizeof(float) + 32 + (size_t)G.Nz * sizeof(float4) + 128 * sizeof(float2) +
            nfac * 128 * NT * sizeof(float2);
 }
