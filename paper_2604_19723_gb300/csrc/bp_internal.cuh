@@ -399,7 +399,7 @@ struct DevState {
     float2* kdl;      // [S_max][J][S_cap]       1/lambda_c of the eigen-whitened basis (.x; zero-padded)
     float* kB;        // [S_max][J][Nf][hi, lo][128 x 2 My Mz] TF32 B tiles of the tensor-core pass 1 (or null)
     int* kerr;        // nonzero after a bounded wait of a kernel gave up (reported by bp_estimate)
-    float2* ky0;      // [S_max][J][S_cap]       w_c = y~0_c / lambda_c, y~0 = V^H e0 / eta_bar
+    float2* ky0;      // [S_max][J][S_cap]       y~0 = V^H e0 / eta_bar (zero-padded)
     double* kJ0;      // [S_max][J]              |r0|^2/eta_bar
     // nu stage outputs (per j)
     double* nu_T;     // [J][S_max] diag a_k, [J][S_max] |offdiag|^2, [J][S_max] double2 b'

@@ -31,69 +31,63 @@ namespace bp {
 // block = (particle tile of KT threads, s); loop over j; V_{s,j} staged in shared
 // memory as rows of SC complex values (columns 0..SC-2 the eigen-whitened basis,
 // column SC-1 the null residual r0), read two columns per 128-bit broadcast load;
-// 1/lambda_c and w_c = y~0_c/lambda_c beside it.  The basis columns are orthogonal,
+// 1/lambda_c and y~0_c = (V^H e0)_c/eta_bar beside it.  The basis columns are orthogonal,
 // so every amplitude term is a diagonal sum over the columns.
 
-// acc += a b: exact product, float-float sum (acc.lo left unnormalised)
-__device__ __forceinline__ void ff_acc_prod(ff& acc, float a, float b) {
-    const float p = __fmul_rn(a, b), e = fmaf(a, b, -p);
-    float s, t;
-    two_sum(acc.hi, p, s, t);
-    acc.hi = s;
-    acc.lo = __fadd_rn(acc.lo, __fadd_rn(t, e));
+// The amplitude terms of the PF likelihood in the eigenbasis, with x_c = conj(h_c) =
+// (V^H psi)_c, y~0 = V^H e0/eta_bar and v_c = tau x_c/eta_bar:
+//     |y0|^2 - |y(tau)|^2 = sum_c (|y~0_c|^2 - |y~0_c - v_c|^2)/lambda_c
+//                        = sum_c Re(conj(v_c) (2 y~0_c - v_c))/lambda_c = sum_c g_c.
+// Each g_c is small where v_c is, and the sum has no constant of the size of |y~0|^2 to
+// cancel.  A column whose terms reach KAPPA_AMP_FF (l (|y~0_c| + |v_c|)^2, l = 1/lambda_c)
+// is summed in float-float from exact sums and products of its FP32 operands (a strong
+// path, or a PF whose steering vector lies largely in the others' span: FP32 would put
+// ~1e-7 of the term on the result, and the term varies from particle to particle); the
+// others in FP32, each within ~2e-7 nats.  v_c is rounded to FP32 first: the evaluation
+// point then moves by a rounding, which J, minimal there, feels only at second order.
+// Also gg = sum_c |h_c|^2/lambda_c, the eigenbasis part of alpha.
+// yt: y~0_c, il: 1/lambda_c (.x), u = tau/eta_bar; padded columns have yt = il = 0.
+constexpr float KAPPA_AMP_FF = 1.0f;
+
+__device__ __forceinline__ void kappa_amp_ff_term(ff& G, float l, float2 y, float vx, float vy) {
+    float ax, axl, ay, ayl;
+    two_sum(2.0f * y.x, -vx, ax, axl);   // 2 y~0 - v exactly (2 y~0 is exact)
+    two_sum(2.0f * y.y, -vy, ay, ayl);
+    const float p1 = __fmul_rn(vx, ax), e1 = fmaf(vx, ax, -p1);
+    const float p2 = __fmul_rn(vy, ay), e2 = fmaf(vy, ay, -p2);
+    float sh, sl;
+    two_sum(p1, p2, sh, sl);
+    const float lo = __fadd_rn(__fadd_rn(sl, __fadd_rn(e1, e2)), fmaf(vx, axl, __fmul_rn(vy, ayl)));
+    const float q = __fmul_rn(l, sh), eq = fmaf(l, sh, -q);
+    float t, et;
+    two_sum(G.hi, q, t, et);
+    G.hi = t;
+    G.lo = __fadd_rn(G.lo, __fadd_rn(et, fmaf(l, lo, eq)));
 }
 
-// The O(S) amplitude sums of the PF likelihood in the eigenbasis, T = sum_c w_c h_c and
-// gg = sum_c |h_c|^2 / lambda_c, enter as 2 Re(tau conj T)/eta_bar - |tau|^2 gg/eta_bar^2.  Two
-// FP32 chains each put ~5e-7 of the terms' size on the result; where the terms, with |tau|^2
-// taken as its prior second moment t2 = |zeta mu|^2 + q, exceed 2 nats (a strong path, or a
-// PF that nearly duplicates others: the two then largely cancel) they are summed again in
-// float-float from exact products (REFINE; the 64-column kernels keep the FP32 sums, whose
-// registers the refinement would spill)
-template <int NC, bool REFINE>
-__device__ inline void kappa_amp_sums(const float2* w, const float2* dl, const float2 (&h)[NC], float t2, float ieb,
-                                      double& Tx, double& Ty, double& gg) {
-    float tx0 = 0.f, ty0 = 0.f, tx1 = 0.f, ty1 = 0.f, gg0 = 0.f, gg1 = 0.f;
+template <int NC>
+__device__ inline void kappa_amp_terms(const float2* yt, const float2* il, const float2 (&h)[NC], float2 u,
+                                       double& dyd, float& gg) {
+    float g0 = 0.f, g1 = 0.f, q0 = 0.f, q1 = 0.f;
+    ff G{0.f, 0.f};
     #pragma unroll
     for (int c = 0; c < NC; ++c) {
-        const float2 wc = w[c];
-        const float m2 = fmaf(h[c].x, h[c].x, h[c].y * h[c].y);
-        if (c & 1) {
-            tx1 = fmaf(wc.x, h[c].x, fmaf(-wc.y, h[c].y, tx1));
-            ty1 = fmaf(wc.x, h[c].y, fmaf(wc.y, h[c].x, ty1));
-            gg1 = fmaf(dl[c].x, m2, gg1);
+        const float2 y = yt[c];
+        const float l = il[c].x;
+        const float vx = fmaf(u.x, h[c].x, u.y * h[c].y);     // v = u conj(h)
+        const float vy = fmaf(u.y, h[c].x, -(u.x * h[c].y));
+        const float m = fabsf(y.x) + fabsf(y.y) + fabsf(vx) + fabsf(vy);
+        if (l * m * m > KAPPA_AMP_FF) {
+            kappa_amp_ff_term(G, l, y, vx, vy);
         } else {
-            tx0 = fmaf(wc.x, h[c].x, fmaf(-wc.y, h[c].y, tx0));
-            ty0 = fmaf(wc.x, h[c].y, fmaf(wc.y, h[c].x, ty0));
-            gg0 = fmaf(dl[c].x, m2, gg0);
+            const float t = l * fmaf(vx, fmaf(2.0f, y.x, -vx), vy * fmaf(2.0f, y.y, -vy));
+            if (c & 1) g1 += t; else g0 += t;
         }
+        const float m2 = fmaf(h[c].x, h[c].x, h[c].y * h[c].y);
+        if (c & 1) q1 = fmaf(l, m2, q1); else q0 = fmaf(l, m2, q0);
     }
-    Tx = (double)(tx0 + tx1);
-    Ty = (double)(ty0 + ty1);
-    gg = (double)(gg0 + gg1);
-    if constexpr (!REFINE) return;
-    const float mag = sqrtf(t2 * (float)(Tx * Tx + Ty * Ty)) * ieb + t2 * (float)gg * ieb * ieb;
-    if (!(mag > 2.0f)) return;
-    ff tx{0.f, 0.f}, ty{0.f, 0.f}, g{0.f, 0.f};
-    #pragma unroll
-    for (int c = 0; c < NC; ++c) {
-        const float2 wc = w[c];
-        const float lc = dl[c].x;
-        ff_acc_prod(tx, wc.x, h[c].x);
-        ff_acc_prod(tx, -wc.y, h[c].y);
-        ff_acc_prod(ty, wc.x, h[c].y);
-        ff_acc_prod(ty, wc.y, h[c].x);
-        // |h_c|^2 / lambda_c: exact squares, their sum in float-float, times 1/lambda_c
-        const float p1 = __fmul_rn(h[c].x, h[c].x), e1 = fmaf(h[c].x, h[c].x, -p1);
-        const float p2 = __fmul_rn(h[c].y, h[c].y), e2 = fmaf(h[c].y, h[c].y, -p2);
-        float m, me;
-        two_sum(p1, p2, m, me);
-        ff_acc_prod(g, lc, m);
-        g.lo = fmaf(lc, __fadd_rn(me, __fadd_rn(e1, e2)), g.lo);
-    }
-    Tx = (double)tx.hi + (double)tx.lo;
-    Ty = (double)ty.hi + (double)ty.lo;
-    gg = (double)g.hi + (double)g.lo;
+    dyd = (double)G.hi + (double)G.lo + (double)(g0 + g1);
+    gg = q0 + q1;
 }
 
 template <int SC>
@@ -106,7 +100,7 @@ __global__ void __launch_bounds__(256, (SC <= 16 ? 2 : 1)) k_kappa(DevGeom G, De
     const int P = Pm.P, J = G.J, Nz = G.Nz, Nm = G.My * G.Mz;
     float4* Vs = sm4;                                                  // [fch * Nm][NP] rows staged
     float2* dls = reinterpret_cast<float2*>(Vs + (size_t)fch * Nm * NP); // [SC] 1/lambda_c (.x)
-    float2* y0s = dls + SC;                                            // [SC] w_c
+    float2* y0s = dls + SC;                                            // [SC] y~0_c
     float2* fac = y0s + SC;                                            // [nfac][KT] factors (high parts)
     float2* r0ls = fac + (size_t)(G.Nf + G.My + G.Mz) * KT;           // [fch * Nm] low part of r0
     float2* facl = r0ls + (size_t)fch * Nm;                            // [My + Mz][KT] low parts of a_y, a_z
@@ -343,15 +337,10 @@ __global__ void __launch_bounds__(256, (SC <= 16 ? 2 : 1)) k_kappa(DevGeom G, De
             }
           }
         }
-        // amplitude terms in the eigenbasis, x_c = conj(h_c) (= (V^H psi)_c):
-        // |y0|^2 - |y|^2 = 2 Re(tau y0^H x_amp)/eta_bar - |tau|^2 |x_amp|^2/eta_bar^2 with
-        // y0^H x_amp = sum_c conj(w_c) x_c = conj(sum_c w_c h_c), |x_amp|^2 = sum_c |h_c|^2/lambda_c
-        // T = sum w h; Re(tau conj(T)) = tau.x T.x + tau.y T.y
-        double Tx, Ty, ggd;
-        kappa_amp_sums<NC, (SC <= 32)>(y0s, dls, h, zf * zf * (mrf * mrf + mif * mif) + fmaxf(q, 0.f), ieb, Tx, Ty, ggd);
-        const float gg = (float)ggd;
-        const double dyd = 2.0 * ((double)tf.x * Tx + (double)tf.y * Ty) * ieb64 -
-                           ((double)tf.x * tf.x + (double)tf.y * tf.y) * ggd * ieb64 * ieb64;
+        // amplitude terms in the eigenbasis, column by column (kappa_amp_terms)
+        double dyd;
+        float gg;
+        kappa_amp_terms<NC>(y0s, dls, h, make_float2(tf.x * ieb, tf.y * ieb), dyd, gg);
         double dlt = J0r - ((double)rr.hi + (double)rr.lo) * ieb64 + dyd;
         if (q > 0.f) {
             // prior term |tau - a|^2 / q with the difference taken in FP64 (a may be
@@ -421,7 +410,7 @@ __global__ void __launch_bounds__(128 * NT, NT == 1 ? 2 : 1) k_kappa_tc(DevGeom 
     uint32_t* tslot = reinterpret_cast<uint32_t*>(mbar + 3);
     float4* r0s = reinterpret_cast<float4*>(sR + RF + 8);    // [Nz] r0 (hi.x, hi.y, lo.x, lo.y)
     float2* dls = reinterpret_cast<float2*>(r0s + Nz);        // [64] 1/lambda_c (.x)
-    float2* y0s = dls + 64;                                   // [64] w_c
+    float2* y0s = dls + 64;                                   // [64] y~0_c
     float2* fac = y0s + 64;                                   // [nfac][KT]
     const int tid = threadIdx.x, warp = tid >> 5, tile = tid >> 7, row = tid & 127;
     const int p = blockIdx.x * KT + tid;
@@ -617,14 +606,14 @@ __global__ void __launch_bounds__(128 * NT, NT == 1 ? 2 : 1) k_kappa_tc(DevGeom 
         const float2 af = make_float2(zf * mrf, zf * mif);
         const float q = (gmf + (mrf * mrf + mif * mif) * (1.0f - zf)) * zf;
         const float iq = (q > 0.f) ? 1.0f / q : 0.f;
-        double Tx, Ty, ggd;
-        kappa_amp_sums<NC, false>(y0s, dls, h, zf * zf * (mrf * mrf + mif * mif) + fmaxf(q, 0.f), ieb, Tx, Ty, ggd);
-        const float gg = (float)ggd;
         float2 tf = af;
         if (q > 0.f) {
             const float den = alpha + iq;
             tf = make_float2((pr.x * ieb + af.x * iq) / den, (pr.y * ieb + af.y * iq) / den);
         }
+        double dyd;   // amplitude terms in the eigenbasis (kappa_amp_terms)
+        float gg;
+        kappa_amp_terms<NC>(y0s, dls, h, make_float2(tf.x * ieb, tf.y * ieb), dyd, gg);
         // ---- pass 2: V V^H psi per group of frequencies, then the element-wise residual
         ff rr{0.f, 0.f};
         float pn = 0.f;
@@ -726,8 +715,6 @@ __global__ void __launch_bounds__(128 * NT, NT == 1 ? 2 : 1) k_kappa_tc(DevGeom 
             }
             tc::fence_before_sync();   // TMEM reads complete before the next group's MMAs
         }
-        const double dyd = 2.0 * ((double)tf.x * Tx + (double)tf.y * Ty) * ieb64 -
-                           ((double)tf.x * tf.x + (double)tf.y * tf.y) * ggd * ieb64 * ieb64;
         double dlt = J0r - ((double)rr.hi + (double)rr.lo) * ieb64 + dyd;
         if (q > 0.f) {
             const double dx = (double)tf.x - zeta * mr, dyt = (double)tf.y - zeta * mi;
@@ -1466,7 +1453,7 @@ __global__ void k_kappa_btile2(DevGeom G, DevState D, int SCA, float* __restrict
 
 // dynamic shared memory of k_kappa_tc: the operand region (pass 1: A [NT][hi, lo][128 x 2Nm],
 // B [hi, lo][128 x 2Nm]; pass 2: A [NT][hi, lo][128 x 32], two B slots [hi, lo][64 x 32]), barriers,
-// r0 (hi, lo) per element, 1/lambda_c and w_c, and the factors of 256 particles
+// r0 (hi, lo) per element, 1/lambda_c and y~0_c, and the factors of 256 particles
 constexpr int KAPPA_TC_NT = 1;   // M tiles per block of the launched variant
 static size_t kappa_tc_smem(const DevGeom& G, int NT = KAPPA_TC_NT) {
     const size_t Nm = (size_t)G.My * G.Mz, nfac = (size_t)G.Nf + G.My + G.Mz;

@@ -241,13 +241,34 @@ template <> struct cplx<float> { using t = float2; };
 template <> struct cplx<double> { using t = double2; };
 template <typename T> struct JRot { T c, s, er, ei; };   // cos, sin, e^{i phi}
 
+// Cyclic Jacobi on a Hermitian matrix held as its packed lower triangle (element (r, c),
+// r >= c, at r (r + 1)/2 + c), in T = float or double arithmetic (the convergence test in
+// FP64).  Each round of the round-robin ordering takes two barriers: the rotations of its
+// disjoint pairs, then one pass that applies them, to U by columns and to A by 2 x 2 blocks
+// between pairs (rows of pair i, columns of pair i', i >= i': block <- G_i^H block G_i'),
+// the diagonal blocks set to their exact diagonal form.  U is updated from its given
+// start.  A pair whose off-diagonal element already meets the convergence test is not
+// rotated (threshold Jacobi).
+__device__ inline int pk_idx(int r, int c) { return r * (r + 1) / 2 + c; }
+template <typename C>
+__device__ inline C pk_get(const C* A, int r, int c) {
+    if (r >= c) return A[pk_idx(r, c)];
+    C v = A[pk_idx(c, r)];
+    v.y = -v.y;
+    return v;
+}
+template <typename C>
+__device__ inline void pk_set(C* A, int r, int c, C v) {
+    if (r >= c) { A[pk_idx(r, c)] = v; return; }
+    v.y = -v.y;
+    A[pk_idx(c, r)] = v;
+}
+
 template <typename T>
-__device__ void jacobi_herm(typename cplx<T>::t* A, typename cplx<T>::t* U, int n, JRot<T>* rot, double* red,
-                            bool init_identity, double tol, double shift, int max_sweeps) {
+__device__ void jacobi_herm_packed(typename cplx<T>::t* A, typename cplx<T>::t* U, int n, JRot<T>* rot, double* red,
+                                   double tol, double shift, int max_sweeps) {
     using C = typename cplx<T>::t;
     const int tid = threadIdx.x, nt = blockDim.x;
-    if (init_identity)
-        for (int t = tid; t < n * n; t += nt) { U[t].x = (t / n == t % n) ? T(1) : T(0); U[t].y = T(0); }
     __syncthreads();
     if (n < 2) return;
     const int n2 = n + (n & 1), half = n2 / 2;
@@ -257,138 +278,20 @@ __device__ void jacobi_herm(typename cplx<T>::t* A, typename cplx<T>::t* U, int 
         else { a = (r + i) % (n2 - 1); b = (r - i + n2 - 1) % (n2 - 1); }
         p = min(a, b); q = max(a, b);
     };
-    for (int sweep = 0; sweep < max_sweeps; ++sweep) {
-        // convergence test on the current matrix (upper triangle; any violating pair
-        // raises the flag)
-        if (tid == 0) red[0] = 0.0;
-        __syncthreads();
-        bool viol = false;
-        for (int t = tid; t < n * n; t += nt) {
-            const int r = t / n, c = t - r * n;
-            if (r >= c) continue;
-            const double m2 = (double)A[t].x * A[t].x + (double)A[t].y * A[t].y;
-            const double dr = fabs((double)A[r * n + r].x), dc = fabs((double)A[c * n + c].x);
-            const double gr = fmax(dr - shift, 0.0), gc = fmax(dc - shift, 0.0);
-            if (!(m2 * gr * gc <= tol * (dr * dc) * (dr * dc))) viol = true;
-        }
-        if (viol) red[0] = 1.0;
-        __syncthreads();
-        const bool done = (red[0] == 0.0);
-        __syncthreads();
-        if (done) break;
-        for (int r = 0; r < n2 - 1; ++r) {
-            // rotation parameters of this round's pairs
-            for (int i = tid; i < half; i += nt) {
-                int p, q;
-                pair_of(r, i, p, q);
-                JRot<T> g{T(1), T(0), T(1), T(0)};
-                if (q < n) {
-                    const C apq = A[p * n + q];
-                    const T m = sqrt(apq.x * apq.x + apq.y * apq.y);
-                    // a pair that already meets the convergence test is not rotated
-                    // (threshold Jacobi); its update below is skipped
-                    const double dp = fabs((double)A[p * n + p].x), dq = fabs((double)A[q * n + q].x);
-                    const double m2 = (double)m * (double)m;
-                    const bool small = m2 * fmax(dp - shift, 0.0) * fmax(dq - shift, 0.0) <= tol * (dp * dq) * (dp * dq);
-                    if (!small && m > T(1e-30)) {
-                        const T zeta = (A[q * n + q].x - A[p * n + p].x) / (T(2) * m);
-                        const T t = (zeta >= T(0) ? T(1) : T(-1)) / (fabs(zeta) + sqrt(T(1) + zeta * zeta));
-                        const T c = T(1) / sqrt(T(1) + t * t);
-                        g = JRot<T>{c, t * c, apq.x / m, apq.y / m};
-                    }
-                }
-                rot[i] = g;
-            }
-            __syncthreads();
-            // columns p, q of A and U:  (x_p, x_q) <- (c x_p - s e^{-i phi} x_q, s x_p + c e^{-i phi} x_q)
-            for (int t = tid; t < half * n; t += nt) {
-                const int i = t / n, row = t - i * n;
-                int p, q;
-                pair_of(r, i, p, q);
-                if (q >= n) continue;
-                const JRot<T> g = rot[i];
-                if (g.s == T(0)) continue;
-                for (int w = 0; w < 2; ++w) {
-                    C* X = w ? U : A;
-                    const C xp = X[row * n + p], xq = X[row * n + q];
-                    const T eqx = g.er * xq.x + g.ei * xq.y, eqy = g.er * xq.y - g.ei * xq.x;   // e^{-i phi} x_q
-                    X[row * n + p].x = g.c * xp.x - g.s * eqx; X[row * n + p].y = g.c * xp.y - g.s * eqy;
-                    X[row * n + q].x = g.s * xp.x + g.c * eqx; X[row * n + q].y = g.s * xp.y + g.c * eqy;
-                }
-            }
-            __syncthreads();
-            // rows p, q of A:  (a_p, a_q) <- (c a_p - s e^{i phi} a_q, s a_p + c e^{i phi} a_q)
-            for (int t = tid; t < half * n; t += nt) {
-                const int i = t / n, cc = t - i * n;
-                int p, q;
-                pair_of(r, i, p, q);
-                if (q >= n) continue;
-                const JRot<T> g = rot[i];
-                if (g.s == T(0)) continue;
-                const C ap = A[p * n + cc], aq = A[q * n + cc];
-                const T eqx = g.er * aq.x - g.ei * aq.y, eqy = g.er * aq.y + g.ei * aq.x;   // e^{i phi} a_q
-                A[p * n + cc].x = g.c * ap.x - g.s * eqx; A[p * n + cc].y = g.c * ap.y - g.s * eqy;
-                A[q * n + cc].x = g.s * ap.x + g.c * eqx; A[q * n + cc].y = g.s * ap.y + g.c * eqy;
-            }
-            __syncthreads();
-            // the rotated pair: exact zeros off the diagonal, real diagonal
-            for (int i = tid; i < half; i += nt) {
-                int p, q;
-                pair_of(r, i, p, q);
-                if (q >= n || rot[i].s == T(0)) continue;
-                A[p * n + q].x = T(0); A[p * n + q].y = T(0);
-                A[q * n + p].x = T(0); A[q * n + p].y = T(0);
-                A[p * n + p].y = T(0);
-                A[q * n + q].y = T(0);
-            }
-            __syncthreads();
-        }
-    }
-}
-
-// The same cyclic Jacobi in FP64 on a Hermitian matrix held as its packed lower triangle
-// (element (r, c), r >= c, at r (r + 1)/2 + c): half the shared memory of the full matrix.
-// Each round takes two barriers: the rotations of its disjoint pairs, then one pass that
-// applies them, to U by columns and to A by 2 x 2 blocks between pairs (rows of pair i,
-// columns of pair i', i >= i': block <- G_i^H block G_i'), the diagonal blocks set to
-// their exact diagonal form.  Same rotation convention and convergence test as
-// jacobi_herm; U is updated from its given start.
-__device__ inline int pk_idx(int r, int c) { return r * (r + 1) / 2 + c; }
-__device__ inline double2 pk_get(const double2* A, int r, int c) {
-    if (r >= c) return A[pk_idx(r, c)];
-    const double2 v = A[pk_idx(c, r)];
-    return make_double2(v.x, -v.y);
-}
-__device__ inline void pk_set(double2* A, int r, int c, double2 v) {
-    if (r >= c) A[pk_idx(r, c)] = v;
-    else A[pk_idx(c, r)] = make_double2(v.x, -v.y);
-}
-
-__device__ void jacobi_herm_packed(double2* A, double2* U, int n, JRot<double>* rot, double* red, double tol,
-                                   double shift, int max_sweeps) {
-    const int tid = threadIdx.x, nt = blockDim.x;
-    __syncthreads();
-    if (n < 2) return;
-    const int n2 = n + (n & 1), half = n2 / 2;
-    auto pair_of = [&](int r, int i, int& p, int& q) {
-        int a, b;
-        if (i == 0) { a = n2 - 1; b = r; }
-        else { a = (r + i) % (n2 - 1); b = (r - i + n2 - 1) % (n2 - 1); }
-        p = min(a, b); q = max(a, b);
-    };
+    auto cz = []() { C z; z.x = T(0); z.y = T(0); return z; };
     const int nblk = half * (half + 1) / 2;
     for (int sweep = 0; sweep < max_sweeps; ++sweep) {
         if (tid == 0) red[0] = 0.0;
         __syncthreads();
         bool viol = false;
         for (int t = tid; t < n * (n - 1) / 2; t += nt) {   // strictly lower elements (r, c)
-            int r = (int)((sqrt(8.0 * t + 1.0) + 1.0) * 0.5);
+            int r = (int)((sqrtf((float)(8 * t + 1)) + 1.0f) * 0.5f);
             while (r * (r - 1) / 2 > t) --r;
             while ((r + 1) * r / 2 <= t) ++r;
             const int c = t - r * (r - 1) / 2;
-            const double2 v = A[pk_idx(r, c)];
-            const double m2 = v.x * v.x + v.y * v.y;
-            const double dr = fabs(A[pk_idx(r, r)].x), dc = fabs(A[pk_idx(c, c)].x);
+            const C v = A[pk_idx(r, c)];
+            const double m2 = (double)v.x * v.x + (double)v.y * v.y;
+            const double dr = fabs((double)A[pk_idx(r, r)].x), dc = fabs((double)A[pk_idx(c, c)].x);
             const double gr = fmax(dr - shift, 0.0), gc = fmax(dc - shift, 0.0);
             if (!(m2 * gr * gc <= tol * (dr * dc) * (dr * dc))) viol = true;
         }
@@ -401,17 +304,18 @@ __device__ void jacobi_herm_packed(double2* A, double2* U, int n, JRot<double>* 
             for (int i = tid; i < half; i += nt) {
                 int p, q;
                 pair_of(r, i, p, q);
-                JRot<double> g{1.0, 0.0, 1.0, 0.0};
+                JRot<T> g{T(1), T(0), T(1), T(0)};
                 if (q < n) {
-                    const double2 apq = pk_get(A, p, q);
-                    const double m = sqrt(apq.x * apq.x + apq.y * apq.y);
-                    const double dp = fabs(A[pk_idx(p, p)].x), dq = fabs(A[pk_idx(q, q)].x);
-                    const bool small = m * m * fmax(dp - shift, 0.0) * fmax(dq - shift, 0.0) <= tol * (dp * dq) * (dp * dq);
-                    if (!small && m > 1e-30) {
-                        const double zeta = (A[pk_idx(q, q)].x - A[pk_idx(p, p)].x) / (2.0 * m);
-                        const double t = (zeta >= 0.0 ? 1.0 : -1.0) / (fabs(zeta) + sqrt(1.0 + zeta * zeta));
-                        const double c = 1.0 / sqrt(1.0 + t * t);
-                        g = JRot<double>{c, t * c, apq.x / m, apq.y / m};
+                    const C apq = pk_get(A, p, q);
+                    const T m = sqrt(apq.x * apq.x + apq.y * apq.y);
+                    const double dp = fabs((double)A[pk_idx(p, p)].x), dq = fabs((double)A[pk_idx(q, q)].x);
+                    const double m2 = (double)m * (double)m;
+                    const bool small = m2 * fmax(dp - shift, 0.0) * fmax(dq - shift, 0.0) <= tol * (dp * dq) * (dp * dq);
+                    if (!small && m > T(1e-30)) {
+                        const T zeta = (A[pk_idx(q, q)].x - A[pk_idx(p, p)].x) / (T(2) * m);
+                        const T t = (zeta >= T(0) ? T(1) : T(-1)) / (fabs(zeta) + sqrt(T(1) + zeta * zeta));
+                        const T c = T(1) / sqrt(T(1) + t * t);
+                        g = JRot<T>{c, t * c, apq.x / m, apq.y / m};
                     }
                 }
                 rot[i] = g;
@@ -423,21 +327,24 @@ __device__ void jacobi_herm_packed(double2* A, double2* U, int n, JRot<double>* 
                 int p, q;
                 pair_of(r, i, p, q);
                 if (q >= n) continue;
-                const JRot<double> g = rot[i];
-                if (g.s == 0.0) continue;
-                const double2 xp = U[row * n + p], xq = U[row * n + q];
-                const double eqx = g.er * xq.x + g.ei * xq.y, eqy = g.er * xq.y - g.ei * xq.x;
-                U[row * n + p] = make_double2(g.c * xp.x - g.s * eqx, g.c * xp.y - g.s * eqy);
-                U[row * n + q] = make_double2(g.s * xp.x + g.c * eqx, g.s * xp.y + g.c * eqy);
+                const JRot<T> g = rot[i];
+                if (g.s == T(0)) continue;
+                const C xp = U[row * n + p], xq = U[row * n + q];
+                const T eqx = g.er * xq.x + g.ei * xq.y, eqy = g.er * xq.y - g.ei * xq.x;
+                C np, nq;
+                np.x = g.c * xp.x - g.s * eqx; np.y = g.c * xp.y - g.s * eqy;
+                nq.x = g.s * xp.x + g.c * eqx; nq.y = g.s * xp.y + g.c * eqy;
+                U[row * n + p] = np;
+                U[row * n + q] = nq;
             }
             // A by 2 x 2 blocks: rows of pair i, columns of pair i' <= i
             for (int b = tid; b < nblk; b += nt) {
-                int i = (int)((sqrt(8.0 * b + 1.0) - 1.0) * 0.5);
+                int i = (int)((sqrtf((float)(8 * b + 1)) - 1.0f) * 0.5f);
                 while ((i + 1) * (i + 2) / 2 <= b) ++i;
                 while (i * (i + 1) / 2 > b) --i;
                 const int i2 = b - i * (i + 1) / 2;
-                const JRot<double> g1 = rot[i], g2 = rot[i2];
-                if (g1.s == 0.0 && g2.s == 0.0) continue;
+                const JRot<T> g1 = rot[i], g2 = rot[i2];
+                if (g1.s == T(0) && g2.s == T(0)) continue;
                 int p1, q1, p2, q2;
                 pair_of(r, i, p1, q1);
                 pair_of(r, i2, p2, q2);
@@ -445,37 +352,40 @@ __device__ void jacobi_herm_packed(double2* A, double2* U, int n, JRot<double>* 
                 if (i == i2) {
                     if (!v1) continue;
                     // G^H [[a_pp, a_pq], [a_qp, a_qq]] G: diagonal by construction of the rotation
-                    const double2 apq = pk_get(A, p1, q1);
-                    const double app = A[pk_idx(p1, p1)].x, aqq = A[pk_idx(q1, q1)].x;
-                    const double re = g1.er * apq.x + g1.ei * apq.y;      // Re(e^{-i phi} a_pq) = |a_pq|
-                    const double c = g1.c, s = g1.s;
-                    const double npp = c * c * app - 2.0 * c * s * re + s * s * aqq;
-                    const double nqq = s * s * app + 2.0 * c * s * re + c * c * aqq;
-                    A[pk_idx(p1, p1)] = make_double2(npp, 0.0);
-                    A[pk_idx(q1, q1)] = make_double2(nqq, 0.0);
-                    A[pk_idx(q1, p1)] = make_double2(0.0, 0.0);
+                    const C apq = pk_get(A, p1, q1);
+                    const T app = A[pk_idx(p1, p1)].x, aqq = A[pk_idx(q1, q1)].x;
+                    const T re = g1.er * apq.x + g1.ei * apq.y;      // Re(e^{-i phi} a_pq) = |a_pq|
+                    const T c = g1.c, s = g1.s;
+                    C dpp = cz(), dqq = cz();
+                    dpp.x = c * c * app - T(2) * c * s * re + s * s * aqq;
+                    dqq.x = s * s * app + T(2) * c * s * re + c * c * aqq;
+                    A[pk_idx(p1, p1)] = dpp;
+                    A[pk_idx(q1, q1)] = dqq;
+                    A[pk_idx(q1, p1)] = cz();
                     continue;
                 }
                 // block X = [[x00, x01], [x10, x11]] at rows (p1, q1), columns (p2, q2)
-                double2 x00 = pk_get(A, p1, p2);
-                double2 x01 = v2 ? pk_get(A, p1, q2) : make_double2(0.0, 0.0);
-                double2 x10 = v1 ? pk_get(A, q1, p2) : make_double2(0.0, 0.0);
-                double2 x11 = (v1 && v2) ? pk_get(A, q1, q2) : make_double2(0.0, 0.0);
-                if (g2.s != 0.0) {   // X G2: columns (c x_p - s e^{-i phi} x_q, s x_p + c e^{-i phi} x_q)
-                    auto colrot = [&](double2& xp, double2& xq) {
-                        const double ex = g2.er * xq.x + g2.ei * xq.y, ey = g2.er * xq.y - g2.ei * xq.x;
-                        const double2 np = make_double2(g2.c * xp.x - g2.s * ex, g2.c * xp.y - g2.s * ey);
-                        const double2 nq = make_double2(g2.s * xp.x + g2.c * ex, g2.s * xp.y + g2.c * ey);
+                C x00 = pk_get(A, p1, p2);
+                C x01 = v2 ? pk_get(A, p1, q2) : cz();
+                C x10 = v1 ? pk_get(A, q1, p2) : cz();
+                C x11 = (v1 && v2) ? pk_get(A, q1, q2) : cz();
+                if (g2.s != T(0)) {   // X G2: columns (c x_p - s e^{-i phi} x_q, s x_p + c e^{-i phi} x_q)
+                    auto colrot = [&](C& xp, C& xq) {
+                        const T ex = g2.er * xq.x + g2.ei * xq.y, ey = g2.er * xq.y - g2.ei * xq.x;
+                        C np, nq;
+                        np.x = g2.c * xp.x - g2.s * ex; np.y = g2.c * xp.y - g2.s * ey;
+                        nq.x = g2.s * xp.x + g2.c * ex; nq.y = g2.s * xp.y + g2.c * ey;
                         xp = np; xq = nq;
                     };
                     colrot(x00, x01);
                     colrot(x10, x11);
                 }
-                if (g1.s != 0.0) {   // G1^H X: rows (c a_p - s e^{i phi} a_q, s a_p + c e^{i phi} a_q)
-                    auto rowrot = [&](double2& ap, double2& aq) {
-                        const double ex = g1.er * aq.x - g1.ei * aq.y, ey = g1.er * aq.y + g1.ei * aq.x;
-                        const double2 np = make_double2(g1.c * ap.x - g1.s * ex, g1.c * ap.y - g1.s * ey);
-                        const double2 nq = make_double2(g1.s * ap.x + g1.c * ex, g1.s * ap.y + g1.c * ey);
+                if (g1.s != T(0)) {   // G1^H X: rows (c a_p - s e^{i phi} a_q, s a_p + c e^{i phi} a_q)
+                    auto rowrot = [&](C& ap, C& aq) {
+                        const T ex = g1.er * aq.x - g1.ei * aq.y, ey = g1.er * aq.y + g1.ei * aq.x;
+                        C np, nq;
+                        np.x = g1.c * ap.x - g1.s * ex; np.y = g1.c * ap.y - g1.s * ey;
+                        nq.x = g1.s * ap.x + g1.c * ex; nq.y = g1.s * ap.y + g1.c * ey;
                         ap = np; aq = nq;
                     };
                     rowrot(x00, x10);
@@ -495,9 +405,14 @@ __device__ void jacobi_herm_packed(double2* A, double2* U, int n, JRot<double>* 
 // rotation and product loops are latency bound
 constexpr int STAGE_THREADS = 384;
 
-__host__ __device__ inline size_t stage_kappa_smem(int K) {
-    return ((size_t)K * K + (size_t)K * (K + 1) / 2 + (size_t)(STAGE_THREADS / 32) * K) * sizeof(double2) +
-           8 * sizeof(double) + 32 * sizeof(JRot<double>);
+constexpr int STAGE_WRED = 9;   // per-warp partial sums of the omega test's scalars
+__host__ __device__ inline size_t stage_kappa_rp(int K, int Nz) {   // the packed region, then e0 (Nz)
+    const size_t t = (size_t)K * (K + 1) / 2;
+    return t > (size_t)Nz ? t : (size_t)Nz;
+}
+__host__ __device__ inline size_t stage_kappa_smem(int K, int Nz) {
+    return ((size_t)K * K + stage_kappa_rp(K, Nz) + (size_t)(STAGE_THREADS / 32) * K) * sizeof(double2) +
+           8 * sizeof(double) + 32 * sizeof(JRot<double>) + (size_t)STAGE_WRED * (STAGE_THREADS / 32) * sizeof(double);
 }
 
 __global__ void __launch_bounds__(STAGE_THREADS) k_stage_kappa(DevGeom G, DevParams Pm, DevState D, int S, int SC,
@@ -514,13 +429,16 @@ __global__ void __launch_bounds__(STAGE_THREADS) k_stage_kappa(DevGeom G, DevPar
     double2* Rp = Ue + (size_t)K * K;            // packed lower triangle of U^H B U, then the eigenvalues
     float2* A32 = reinterpret_cast<float2*>(Ue); // the FP32 solve first: A32 in Ue's bytes, U32 in Rp's
     float2* U32 = reinterpret_cast<float2*>(Rp); // (K^2 float2 <= K (K + 1)/2 double2)
-    double2* scr = Rp + (size_t)K * (K + 1) / 2; // [nw][K] columns of B U; then the projections below
+    double2* scr = Rp + stage_kappa_rp(K, Nz);  // [nw][K] columns of B U; then the projections below
     double2* ye = scr;                           // V^H e0 / eb      (K)
     double2* vm = ye + K;                        // V^H m^w          (K)
     double2* v4 = vm + K;                        // V^H mu4          (K)
     double* dinv = reinterpret_cast<double*>(v4 + K);   // lambda^{-1/2}  (K)
+    double2* pa = scr + 4 * (size_t)K;           // M^H e0, M^H m^w, M^H mu4 (3 K; nw >= 7)
+    double2* E0 = Rp;                            // e0 = z - sum_{t != s} mu3_t once Rp is free (Nz)
     double* red = reinterpret_cast<double*>(scr + (size_t)nw * K);   // reduction scratch [8]
     JRot<double>* rot = reinterpret_cast<JRot<double>*>(red + 8);   // Jacobi pair rotations [32]
+    double* wred = reinterpret_cast<double*>(rot + 32);              // [STAGE_WRED][nw]
     JRot<float>* rot32 = reinterpret_cast<JRot<float>*>(rot);
     const double2* Gm = reinterpret_cast<const double2*>(gram) + (size_t)j * SM * SM;
     // column map c -> s'
@@ -534,11 +452,15 @@ __global__ void __launch_bounds__(STAGE_THREADS) k_stage_kappa(DevGeom G, DevPar
     };
     // eigenvectors to FP32 accuracy by FP32 sweeps, then B rotated into that basis in FP64
     // (nearly diagonal) and finished by FP64 sweeps
-    for (int t = threadIdx.x; t < K * K; t += blockDim.x) {
-        const double2 g = Bv(t / K, t % K);
+    for (int t = threadIdx.x; t < K * (K + 1) / 2; t += blockDim.x) {   // packed lower triangle
+        int r = (int)((sqrtf((float)(8 * t + 1)) - 1.0f) * 0.5f);
+        while ((r + 1) * (r + 2) / 2 <= t) ++r;
+        while (r * (r + 1) / 2 > t) --r;
+        const double2 g = Bv(r, t - r * (r + 1) / 2);
         A32[t] = make_float2((float)g.x, (float)g.y);
     }
-    jacobi_herm<float>(A32, U32, K, rot32, red, true, 1e-13, 1.0, 10);
+    for (int t = threadIdx.x; t < K * K; t += blockDim.x) U32[t] = make_float2(t / K == t % K ? 1.f : 0.f, 0.f);
+    jacobi_herm_packed<float>(A32, U32, K, rot32, red, 1e-13, 1.0, 10);
     for (int t = threadIdx.x; t < K * K; t += blockDim.x) Ue[t] = make_double2((double)U32[t].x, (double)U32[t].y);
     __syncthreads();
     {   // the FP32 columns are orthonormal to ~1e-5 only: modified Gram-Schmidt in FP64, so
@@ -574,12 +496,16 @@ __global__ void __launch_bounds__(STAGE_THREADS) k_stage_kappa(DevGeom G, DevPar
     for (int c = wid; c < K; c += nw) {
         double2* v = scr + (size_t)wid * K;
         for (int m = lane; m < K; m += 32) {
+            // (B u_c)_m = u_mc + (G_{-s} u_c)_m / eb, with G_mn = conj(G_nm): the Gram is stored
+            // with both triangles, bitwise Hermitian, so lanes m read consecutive addresses
             double2 acc = make_double2(0.0, 0.0);
             for (int n = 0; n < K; ++n) {
-                const double2 u = zmul(Bv(m, n), Ue[n * K + c]);
+                const double2 g = Gm[col(n) * SM + col(m)];
+                const double2 u = zmulc(g, Ue[n * K + c]);
                 acc.x += u.x; acc.y += u.y;
             }
-            v[m] = acc;
+            const double2 um = Ue[m * K + c];
+            v[m] = make_double2(um.x + acc.x / eb, um.y + acc.y / eb);
         }
         __syncwarp();
         for (int r = c + lane; r < K; r += 32) {
@@ -595,56 +521,108 @@ __global__ void __launch_bounds__(STAGE_THREADS) k_stage_kappa(DevGeom G, DevPar
     __syncthreads();
     // typically 2-3 sweeps; the weighted test at 1e-18 leaves ~1e-8 nats on the PR test
     // (emulated on 26- and 64-PF states)
-    jacobi_herm_packed(Rp, Ue, K, rot, red, 1e-18, 1.0, 8);
+    jacobi_herm_packed<double>(Rp, Ue, K, rot, red, 1e-18, 1.0, 8);
     for (int c = threadIdx.x; c < K; c += blockDim.x) dinv[c] = 1.0 / sqrt(fmax(Rp[pk_idx(c, c)].x, 1.0));
     __syncthreads();
-    // V rows: v_k = m_k U diag(lambda)^{-1/2}; accumulate projections
-    for (int t = threadIdx.x; t < 3 * K; t += blockDim.x) (t < K ? ye : (t < 2 * K ? vm : v4))[t % K] = make_double2(0, 0);
-    if (threadIdx.x < 8) red[threadIdx.x] = 0.0;
-    __syncthreads();
-    double2* Vs = reinterpret_cast<double2*>(V64) + ((size_t)s * J + j) * Nz * SC;
-    for (int k = threadIdx.x; k < Nz; k += blockDim.x) {
-        double2 e0 = make_double2((double)z[2 * (j * Nz + k)], (double)z[2 * (j * Nz + k) + 1]);
-        for (int t = 0; t < S; ++t) {
-            if (t == s) continue;
-            const double2 m3 = tab[2 * plane + ((size_t)t * J + j) * Nz + k];
-            e0.x -= m3.x; e0.y -= m3.y;
-        }
-        const double2 mw = tab[1 * plane + ((size_t)s * J + j) * Nz + k];
-        const double2 m4 = tab[3 * plane + ((size_t)s * J + j) * Nz + k];
-        for (int c = 0; c < K; ++c) {
-            double2 acc = make_double2(0.0, 0.0);
-            for (int t = 0; t < K; ++t) {
-                const double2 u = zmul(tab[0 * plane + ((size_t)col(t) * J + j) * Nz + k], Ue[t * K + c]);
-                acc.x += u.x; acc.y += u.y;
+    // e0 = z - sum_{t != s} mu3_t per element (into the freed packed region) and the
+    // block sums of |e0|^2, m^H e0, |m|^2, mu4^H e0, |mu4|^2, m^H mu4 (m = m^w_s)
+    {
+        double acc[STAGE_WRED] = {0, 0, 0, 0, 0, 0, 0, 0, 0};
+        for (int k = threadIdx.x; k < Nz; k += blockDim.x) {
+            double2 e0 = make_double2((double)z[2 * (j * Nz + k)], (double)z[2 * (j * Nz + k) + 1]);
+            for (int t = 0; t < S; ++t) {
+                if (t == s) continue;
+                const double2 m3 = tab[2 * plane + ((size_t)t * J + j) * Nz + k];
+                e0.x -= m3.x; e0.y -= m3.y;
             }
-            const double2 v = make_double2(acc.x * dinv[c], acc.y * dinv[c]);
-            Vs[(size_t)k * SC + c] = v;
-            const double2 a1 = zmulc(v, e0), a2 = zmulc(v, mw), a3 = zmulc(v, m4);
-            atomicAdd(&ye[c].x, a1.x); atomicAdd(&ye[c].y, a1.y);
-            atomicAdd(&vm[c].x, a2.x); atomicAdd(&vm[c].y, a2.y);
-            atomicAdd(&v4[c].x, a3.x); atomicAdd(&v4[c].y, a3.y);
+            E0[k] = e0;
+            const double2 mw = tab[1 * plane + ((size_t)s * J + j) * Nz + k];
+            const double2 m4 = tab[3 * plane + ((size_t)s * J + j) * Nz + k];
+            const double2 me = zmulc(mw, e0), ue = zmulc(m4, e0), mu = zmulc(mw, m4);
+            acc[0] += e0.x * e0.x + e0.y * e0.y;
+            acc[1] += me.x; acc[2] += me.y;
+            acc[3] += mw.x * mw.x + mw.y * mw.y;
+            acc[4] += ue.x; acc[5] += ue.y;
+            acc[6] += m4.x * m4.x + m4.y * m4.y;
+            acc[7] += mu.x; acc[8] += mu.y;
         }
-        // scalar products for omega: |e0|^2, m^H e0, m^H m, mu4^H e0, mu4^H mu4, m^H mu4
-        atomicAdd(&red[0], e0.x * e0.x + e0.y * e0.y);
-        const double2 me = zmulc(mw, e0), mm4 = zmulc(mw, m4), ue = zmulc(m4, e0);
-        atomicAdd(&red[1], me.x); atomicAdd(&red[2], me.y);
-        atomicAdd(&red[3], mw.x * mw.x + mw.y * mw.y);
-        atomicAdd(&red[4], ue.x); atomicAdd(&red[5], ue.y);
-        atomicAdd(&red[6], m4.x * m4.x + m4.y * m4.y);
-        atomicAdd(&red[7], mm4.x);
+        #pragma unroll
+        for (int q = 0; q < STAGE_WRED; ++q) {
+            const double v = warp_sum_d(acc[q]);
+            if (lane == 0) wred[q * nw + wid] = v;
+        }
     }
     __syncthreads();
-    // second scalar m^H mu4 imaginary part needed too: recompute cheaply below via projections
-    // ---- omega test (FP64), a^H A^-1 b = (a^H b - (V^H a)^H (V^H b)/eb)/eb
+    if (threadIdx.x < STAGE_WRED) {
+        double v = 0.0;
+        for (int w = 0; w < nw; ++w) v += wred[threadIdx.x * nw + w];
+        wred[threadIdx.x * nw] = v;   // the block sum in slot 0
+    }
+    // M^H e0, M^H m^w, M^H mu4 over the columns t of M_{-s}: one warp per column
+    for (int t = wid; t < K; t += nw) {
+        const double2* mt = tab + ((size_t)col(t) * J + j) * Nz;
+        const double2* mwp = tab + 1 * plane + ((size_t)s * J + j) * Nz;
+        const double2* m4p = tab + 3 * plane + ((size_t)s * J + j) * Nz;
+        double ax = 0, ay = 0, bx = 0, by = 0, cx = 0, cy = 0;
+        for (int k = lane; k < Nz; k += 32) {
+            const double2 m = mt[k];
+            const double2 u1 = zmulc(m, E0[k]), u2 = zmulc(m, mwp[k]), u3 = zmulc(m, m4p[k]);
+            ax += u1.x; ay += u1.y; bx += u2.x; by += u2.y; cx += u3.x; cy += u3.y;
+        }
+        ax = warp_sum_d(ax); ay = warp_sum_d(ay);
+        bx = warp_sum_d(bx); by = warp_sum_d(by);
+        cx = warp_sum_d(cx); cy = warp_sum_d(cy);
+        if (lane == 0) {
+            pa[t] = make_double2(ax, ay);
+            pa[K + t] = make_double2(bx, by);
+            pa[2 * K + t] = make_double2(cx, cy);
+        }
+    }
+    __syncthreads();
+    // V^H x = diag(lambda)^{-1/2} U^H (M^H x): V = M U diag(lambda)^{-1/2}
+    for (int c = threadIdx.x; c < K; c += blockDim.x) {
+        double2 a1 = make_double2(0, 0), a2 = make_double2(0, 0), a3 = make_double2(0, 0);
+        for (int t = 0; t < K; ++t) {
+            const double2 u = Ue[t * K + c];
+            const double2 q1 = zmulc(u, pa[t]), q2 = zmulc(u, pa[K + t]), q3 = zmulc(u, pa[2 * K + t]);
+            a1.x += q1.x; a1.y += q1.y; a2.x += q2.x; a2.y += q2.y; a3.x += q3.x; a3.y += q3.y;
+        }
+        const double d = dinv[c];
+        ye[c] = make_double2(d * a1.x, d * a1.y);
+        vm[c] = make_double2(d * a2.x, d * a2.y);
+        v4[c] = make_double2(d * a3.x, d * a3.y);
+    }
+    // V rows v_k = m_k U diag(lambda)^{-1/2} (FP64), eight columns per work item so that
+    // each m_t(k) is read once per item; consecutive threads take consecutive elements
+    double2* Vs = reinterpret_cast<double2*>(V64) + ((size_t)s * J + j) * Nz * SC;
+    {
+        constexpr int CB = 8;
+        const int nch = (K + CB - 1) / CB;
+        for (int it = threadIdx.x; it < Nz * nch; it += blockDim.x) {
+            const int k = it % Nz, c0 = (it / Nz) * CB;
+            double2 acc[CB];
+            #pragma unroll
+            for (int q = 0; q < CB; ++q) acc[q] = make_double2(0.0, 0.0);
+            for (int t = 0; t < K; ++t) {
+                const double2 m = tab[((size_t)col(t) * J + j) * Nz + k];
+                const double2* ut = Ue + (size_t)t * K + c0;
+                #pragma unroll
+                for (int q = 0; q < CB; ++q) {
+                    if (c0 + q < K) {
+                        const double2 u = zmul(m, ut[q]);
+                        acc[q].x += u.x; acc[q].y += u.y;
+                    }
+                }
+            }
+            #pragma unroll
+            for (int q = 0; q < CB; ++q)
+                if (c0 + q < K) Vs[(size_t)k * SC + c0 + q] = make_double2(acc[q].x * dinv[c0 + q], acc[q].y * dinv[c0 + q]);
+        }
+    }
+    __syncthreads();
+    if (threadIdx.x < 8) red[threadIdx.x] = wred[threadIdx.x * nw];
     __shared__ double mm4_im;
-    if (threadIdx.x == 0) mm4_im = 0.0;
-    __syncthreads();
-    for (int k = threadIdx.x; k < Nz; k += blockDim.x) {
-        const double2 mw = tab[1 * plane + ((size_t)s * J + j) * Nz + k];
-        const double2 m4 = tab[3 * plane + ((size_t)s * J + j) * Nz + k];
-        atomicAdd(&mm4_im, zmulc(mw, m4).y);
-    }
+    if (threadIdx.x == 0) mm4_im = wred[8 * nw];
     __syncthreads();
     if (threadIdx.x == 0) {
         double pe0 = 0, pme_r = 0, pme_i = 0, pmm = 0, pue_r = 0, pue_i = 0, puu = 0, pmu_r = 0, pmu_i = 0;
@@ -691,12 +669,7 @@ __global__ void __launch_bounds__(STAGE_THREADS) k_stage_kappa(DevGeom G, DevPar
     if (threadIdx.x == 0) rr[0] = 0.0;
     __syncthreads();
     for (int k = threadIdx.x; k < Nz; k += blockDim.x) {
-        double2 e0 = make_double2((double)z[2 * (j * Nz + k)], (double)z[2 * (j * Nz + k) + 1]);
-        for (int t = 0; t < S; ++t) {
-            if (t == s) continue;
-            const double2 m3 = tab[2 * plane + ((size_t)t * J + j) * Nz + k];
-            e0.x -= m3.x; e0.y -= m3.y;
-        }
+        double2 e0 = E0[k];
         for (int c = 0; c < K; ++c) {
             const double2 v = Vs[(size_t)k * SC + c];
             const double2 u = zmul(v, ye[c]);
@@ -711,14 +684,13 @@ __global__ void __launch_bounds__(STAGE_THREADS) k_stage_kappa(DevGeom G, DevPar
     }
     __syncthreads();
     if (threadIdx.x == 0) D.kJ0[s * J + j] = rr[0] / eb;   // the |y|^2 part enters the particle kernel as a difference
-    // per-particle amplitude terms in the eigenbasis: with y~0 = V^H e0/eb and x = V^H psi,
-    // y0^H x_amp = sum_c lambda_c^{-1} conj(y~0_c) x_c and |x_amp|^2 = sum_c lambda_c^{-1} |x_c|^2:
-    // w_c = lambda_c^{-1} y~0_c and lambda_c^{-1} (padded with zeros)
+    // the particle kernels take y~0 = V^H e0/eb and 1/lambda_c (padded with zeros) and form
+    // the amplitude terms sum_c (|y~0_c|^2 - |y~0_c - tau x_c/eb|^2)/lambda_c column by column
     float2* ky = D.ky0 + ((size_t)s * J + j) * SC;
     float2* kd = D.kdl + ((size_t)s * J + j) * SC;
     for (int c = threadIdx.x; c < SC; c += blockDim.x) {
         const double il = (c < K) ? dinv[c] * dinv[c] : 0.0;
-        ky[c] = (c < K) ? make_float2((float)(il * ye[c].x), (float)(il * ye[c].y)) : make_float2(0.f, 0.f);
+        ky[c] = (c < K) ? make_float2((float)ye[c].x, (float)ye[c].y) : make_float2(0.f, 0.f);
         kd[c] = make_float2((float)il, 0.f);
     }
 }
@@ -851,7 +823,7 @@ void launch_stage(const DevGeom& G, const DevParams& Pm, const DevState& D, int 
     const int gx = min(64, (npair + 7) / 8);
     k_gram<<<dim3(gx, G.J), 256, 0, st>>>(G, Pm, D, S, z, gram, nu_b);
     const int K = S - 1;
-    const size_t sm1 = stage_kappa_smem(K);
+    const size_t sm1 = stage_kappa_smem(K, G.Nz);
     smem_allow_max((const void*)k_stage_kappa);
     k_stage_kappa<<<dim3(S, G.J), STAGE_THREADS, sm1, st>>>(G, Pm, D, S, SC, z, gram, V64);
     const size_t sm2 = ((size_t)S * S + 3 * (size_t)S) * sizeof(double2);

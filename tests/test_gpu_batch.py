@@ -55,7 +55,8 @@ def make_inputs(cases, dynamic=False):
         prm = params_for(seed, dynamic)
         scn = W.make_scenario(g, prm, N=3, K=S - 1, seed=seed, snr_db=20.0)
         eta = synth.noise_variance(scn)
-        zs = [synth.observe(scn, n, eta, seed + 100 + n) for n in (1, 2)]
+        # the observations as the C ABI takes them (complex64), for both sides
+        zs = [synth.observe(scn, n, eta, seed + 100 + n).astype(np.complex64).astype(np.complex128) for n in (1, 2)]
         st = W.state_near_truth(scn, P=P, S=S, n=0, seed=seed + 1, eta_true=eta, pos_std=0.005, sfv_std=0.005)
         out.append(dict(g=g, prm=prm, S=S, P=P, seed=seed, st=st, zs=zs))
     return out
@@ -68,6 +69,29 @@ def concat_z(batch, inputs, step):
         zi = np.ascontiguousarray(d["zs"][step].astype(np.complex64)).view(np.float32).reshape(-1)
         z[o:o + zi.size] = torch.from_numpy(zi).cuda()
     return z
+
+
+def gpu_prediction(d, pred_o):
+    """The particles a single filter with the scenario's key predicts from d["st"], as an
+    oracle Predicted; checked against the oracle's own prediction pred_o."""
+    g = d["g"]
+    f = bp.Filter(g, d["prm"], P=d["P"], S_max=d["S"], seed=d["seed"])
+    f.set_state(d["st"])
+    f.predict()
+    gp = f.get_predicted()
+    f.close()
+    assert gp["S"] == pred_o.S and gp["n"] == pred_o.n
+    scale = np.maximum(np.abs(pred_o.x.astype(float)), 1.0)
+    assert np.max(np.abs(gp["x"] - pred_o.x) / scale) < 1e-6
+    assert np.max(np.abs(gp["eta"] - pred_o.eta) / pred_o.eta) < 1e-6
+    for k in range(6):
+        sc = np.maximum(np.abs(pred_o.phi[:, k].astype(float)), 1e-3 if k >= 3 else 1.0)
+        assert np.max(np.abs(gp["phi"][:, k] - pred_o.phi[:, k]) / sc) < 2e-6, k
+    assert np.allclose(gp["w_alpha"], pred_o.w_alpha, rtol=1e-14, atol=0)
+    assert np.allclose(gp["zeta"], pred_o.zeta, rtol=1e-14, atol=0)
+    return model.Predicted(n=pred_o.n, S=pred_o.S, x=gp["x"].copy(), phi=gp["phi"].copy(), eta=gp["eta"].copy(),
+                           w_beta=gp["w_beta"].copy(), w_alpha=gp["w_alpha"].copy(), w_xi=gp["w_xi"].copy(),
+                           zeta=gp["zeta"].copy(), is_new=pred_o.is_new)
 
 
 def make_batch(inputs, S_max=None, **kw):
@@ -101,7 +125,12 @@ def test_batch_step_matches_oracle(use_graph):
     b.sync()
     for i, d in enumerate(inputs):
         g, prm, st = d["g"], d["prm"], d["st"]
-        pred = model.predict(st, prm, g.J, seed=d["seed"], S_max=d["S"])
+        # the update is compared on the particles the GPU predicted (a single filter with
+        # the same key predicts the same particles as the batch); those are checked against
+        # the oracle's FP64 prediction at the predict-parity tolerances, as in the
+        # single-filter tests, which compare the two stages apart
+        pred_o = model.predict(st, prm, g.J, seed=d["seed"], S_max=d["S"])
+        pred = gpu_prediction(d, pred_o)
         msg = messages_woodbury.update_messages(pred, prm, g, d["zs"][0])
         bel = beliefs.beliefs(pred, msg)
         est = beliefs.estimate(pred, bel, prm)

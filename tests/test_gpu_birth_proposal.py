@@ -39,7 +39,8 @@ def setup(geom_kw, K, P, seed, N_g):
     prm = W.Params(Q=2, birth_proposal=1, N_g=N_g, T_pru=0.0)
     scn = W.make_scenario(g, prm, N=3, K=K, seed=seed, snr_db=25.0)
     eta = synth.noise_variance(scn)
-    z = synth.observe(scn, 1, eta, seed + 100)
+    # the observation as the C ABI takes it (complex64), for both sides
+    z = synth.observe(scn, 1, eta, seed + 100).astype(np.complex64).astype(np.complex128)
     # legacy PFs: the LoS and the first K - 1 surfaces; the last surface is unexplained
     st = W.state_near_truth(scn, P=P, S=K, n=0, seed=seed + 1, eta_true=eta, pos_std=0.005, sfv_std=0.005)
     return g, prm, scn, z, st

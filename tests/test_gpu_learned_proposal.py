@@ -22,7 +22,8 @@ def setup(P, seed, motion_dims=3, K=4):
     prm = W.Params(motion_dims=motion_dims, Q=0)
     scn = W.make_scenario(g, prm, N=3, K=K, seed=seed, snr_db=20.0)
     eta = synth.noise_variance(scn)
-    z = synth.observe(scn, 1, eta, seed + 100)
+    # the observation as the C ABI takes it (complex64), for both sides
+    z = synth.observe(scn, 1, eta, seed + 100).astype(np.complex64).astype(np.complex128)
     st = W.state_near_truth(scn, P=P, S=K + 1, n=0, seed=seed + 1, eta_true=eta, pos_std=0.005, sfv_std=0.005)
     pred = model.predict(st, prm, g.J, seed=seed, S_max=8)
     return g, prm, z, pred

@@ -36,7 +36,8 @@ def setup_case(geom_kw, K, S, P, seed, pos_std=0.005, snr_db=20.0, params=None, 
     prm = params or W.Params()
     scn = W.make_scenario(g, prm, N=3, K=K, seed=seed, snr_db=snr_db)
     eta = synth.noise_variance(scn)
-    z = synth.observe(scn, 1, eta, seed + 100)
+    # the observation as the C ABI takes it (complex64), for both sides
+    z = synth.observe(scn, 1, eta, seed + 100).astype(np.complex64).astype(np.complex128)
     st = W.state_near_truth(scn, P=P, S=S, n=0, seed=seed + 1, eta_true=eta, pos_std=pos_std,
                             sfv_std=pos_std, uniform_weights=uniform)
     return g, prm, scn, eta, z, st
