@@ -113,6 +113,12 @@ bp_status bp_init(const bp_geometry* geom, const bp_params* prm, int P, int S_ma
 bp_status bp_free(bp_handle* h) {
     if (!h) return BP_ERR_INVALID_ARG;
     if (h->st) cudaStreamSynchronize(h->st); else cudaDeviceSynchronize();
+    if (h->st_side) {
+        cudaStreamSynchronize(h->st_side);
+        cudaStreamDestroy(h->st_side);
+    }
+    if (h->ev_fork) cudaEventDestroy(h->ev_fork);
+    if (h->ev_join) cudaEventDestroy(h->ev_join);
     if (h->prof_on) for (int i = 0; i <= BP_PROF_STAGES; ++i) cudaEventDestroy(h->ev[i]);
     for (void* p : h->allocs) cudaFree(p);
     if (h->ws_owned && h->ws_base) cudaFree(h->ws_base);
@@ -542,6 +548,19 @@ bp_status handle_create(const bp_geometry* geom, const bp_params* prm, int P, in
             h->ws_owned = true;
             ws_bind(h, static_cast<char*>(q));
         }
+        // the side stream of the tridiagonalisation; without it everything runs on st
+        if (ok) {
+            bool side = cudaStreamCreateWithFlags(&h->st_side, cudaStreamNonBlocking) == cudaSuccess;
+            side = side && cudaEventCreateWithFlags(&h->ev_fork, cudaEventDisableTiming) == cudaSuccess;
+            side = side && cudaEventCreateWithFlags(&h->ev_join, cudaEventDisableTiming) == cudaSuccess;
+            if (!side) {
+                if (h->st_side) cudaStreamDestroy(h->st_side);
+                if (h->ev_fork) cudaEventDestroy(h->ev_fork);
+                if (h->ev_join) cudaEventDestroy(h->ev_join);
+                h->st_side = nullptr; h->ev_fork = nullptr; h->ev_join = nullptr;
+                cudaGetLastError();
+            }
+        }
     }
     if (ok) {
         ok &= cudaMallocHost(&h->h_ctrl, (4 + S_max) * sizeof(int)) == cudaSuccess;
@@ -599,7 +618,7 @@ void update_enqueue(bp_handle* h, const float* z_dev) {
     launch_geom(h->G, h->Pm, D, S, h->st);
     launch_table(h->G, h->Pm, D, S, nsplit, h->st);
     mark(h, 3);
-    launch_stage(h->G, h->Pm, D, S, h->SCA, z_dev, h->gram, h->nu_b, h->V64, h->st);
+    launch_stage(h->G, h->Pm, D, S, h->SCA, z_dev, h->gram, h->nu_b, h->V64, h->st, h->st_side, h->ev_fork, h->ev_join);
     if (S > 32) h->launches += launch_kappa_btile(h->G, D, S, h->SCA, h->st);   // B tiles of the tensor-core kernel
     mark(h, 4);
     launch_kappa(h->G, h->Pm, D, S, h->SCA, h->st);
@@ -607,6 +626,7 @@ void update_enqueue(bp_handle* h, const float* z_dev) {
     const int iota_launches = launch_iota(h->G, h->Pm, D, S, z_dev, h->st) + 1;
     launch_iota_repair(h->G, h->Pm, D, S, z_dev, h->st);
     mark(h, 6);
+    if (h->st_side) cudaStreamWaitEvent(h->st, h->ev_join, 0);   // the tridiagonal forms
     launch_nu(h->G, h->Pm, D, S, h->st);
     mark(h, 7);
     launch_normalize(h->G, h->Pm, D, S, h->st);

@@ -24,6 +24,10 @@ struct bp_handle {
     bp::DevParams Pm;
     bp::DevState D;
     cudaStream_t st;
+    // single filters: a side stream for the noise-likelihood tridiagonalisation, which
+    // runs beside the PF basis stage (fork after the Gram, join before its consumer)
+    cudaStream_t st_side;
+    cudaEvent_t ev_fork, ev_join;
     int P, S_max, J, Nz;
     int SCA;            // column stride of the per-(s,j) basis buffers
     int S;              // current number of PFs (host copy)

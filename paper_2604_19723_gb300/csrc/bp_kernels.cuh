@@ -201,8 +201,11 @@ void launch_init(const DevGeom& G, const DevParams& Pm, const DevState& D, int S
 int launch_predict(const DevGeom& G, const DevParams& Pm, const DevState& D, int S_old, int S_new, cudaStream_t st);
 void launch_row_sums(const DevParams& Pm, const DevState& D, int S, int J, cudaStream_t st);
 void launch_table(const DevGeom& G, const DevParams& Pm, const DevState& D, int S, int nsplit, cudaStream_t st);
+// the PF basis stage; with a side stream the noise-likelihood tridiagonalisation runs there
+// (forked after the Gram through ev_fork, ev_join recorded after it)
 void launch_stage(const DevGeom& G, const DevParams& Pm, const DevState& D, int S, int SC, const float* z,
-                  double* gram, double* nu_b, double* V64, cudaStream_t st);
+                  double* gram, double* nu_b, double* V64, cudaStream_t st, cudaStream_t side = nullptr,
+                  cudaEvent_t ev_fork = nullptr, cudaEvent_t ev_join = nullptr);
 void launch_kappa(const DevGeom& G, const DevParams& Pm, const DevState& D, int S, int SCA, cudaStream_t st);
 bool kappa_tc_ok(const DevGeom& G, int SCA);
 size_t kappa_btile_floats(const DevGeom& G, int S_max);

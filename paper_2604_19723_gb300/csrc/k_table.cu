@@ -818,17 +818,26 @@ void launch_table(const DevGeom& G, const DevParams& Pm, const DevState& D, int 
 }
 
 void launch_stage(const DevGeom& G, const DevParams& Pm, const DevState& D, int S, int SC, const float* z,
-                  double* gram, double* nu_b, double* V64, cudaStream_t st) {
+                  double* gram, double* nu_b, double* V64, cudaStream_t st, cudaStream_t side, cudaEvent_t ev_fork,
+                  cudaEvent_t ev_join) {
     const int npair = S * (S + 1) / 2 + S + 1;
     const int gx = min(64, (npair + 7) / 8);
     k_gram<<<dim3(gx, G.J), 256, 0, st>>>(G, Pm, D, S, z, gram, nu_b);
+    // J blocks of tridiagonalisation: on the side stream they fill the SMs the S x J basis
+    // blocks leave free
+    const bool fork = side && ev_fork && ev_join;
+    if (fork) {
+        cudaEventRecord(ev_fork, st);
+        cudaStreamWaitEvent(side, ev_fork, 0);
+    }
+    const size_t sm2 = ((size_t)S * S + 3 * (size_t)S) * sizeof(double2);
+    smem_allow_max((const void*)k_nu_tridiag);
+    k_nu_tridiag<<<G.J, 128, sm2, fork ? side : st>>>(Pm, D, S, gram, nu_b);
+    if (fork) cudaEventRecord(ev_join, side);
     const int K = S - 1;
     const size_t sm1 = stage_kappa_smem(K, G.Nz);
     smem_allow_max((const void*)k_stage_kappa);
     k_stage_kappa<<<dim3(S, G.J), STAGE_THREADS, sm1, st>>>(G, Pm, D, S, SC, z, gram, V64);
-    const size_t sm2 = ((size_t)S * S + 3 * (size_t)S) * sizeof(double2);
-    smem_allow_max((const void*)k_nu_tridiag);
-    k_nu_tridiag<<<G.J, 128, sm2, st>>>(Pm, D, S, gram, nu_b);
 }
 
 void smem_allow_max(const void* kernel) {
