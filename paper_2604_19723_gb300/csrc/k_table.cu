@@ -706,38 +706,46 @@ __global__ void k_nu_tridiag(DevParams Pm, DevState D, int S, const double* gram
     double2* v = A + (size_t)S * S;  // S
     double2* pv = v + S;             // S
     double2* b = pv + S;             // S
-    __shared__ double scal[4];
+    __shared__ double red[32][3];
+    const int tid = threadIdx.x, nt = blockDim.x, lane = tid & 31, wid = tid >> 5, nw = nt >> 5;
+    // block sums of three values, returned to every thread
+    auto bsum3 = [&](double& x0, double& x1, double& x2) {
+        x0 = warp_sum_d(x0); x1 = warp_sum_d(x1); x2 = warp_sum_d(x2);
+        __syncthreads();
+        if (lane == 0) { red[wid][0] = x0; red[wid][1] = x1; red[wid][2] = x2; }
+        __syncthreads();
+        x0 = x1 = x2 = 0.0;
+        for (int w = 0; w < nw; ++w) { x0 += red[w][0]; x1 += red[w][1]; x2 += red[w][2]; }
+    };
     const double2* Gm = reinterpret_cast<const double2*>(gram) + (size_t)j * SM * SM;
     const double2* bv = reinterpret_cast<const double2*>(nu_b) + (size_t)j * (SM + 1);
-    for (int t = threadIdx.x; t < S * S; t += blockDim.x) A[t] = Gm[(t / S) * SM + (t % S)];
-    for (int t = threadIdx.x; t < S; t += blockDim.x) b[t] = bv[t];
+    for (int t = tid; t < S * S; t += nt) A[t] = Gm[(t / S) * SM + (t % S)];
+    for (int t = tid; t < S; t += nt) b[t] = bv[t];
     __syncthreads();
     for (int k = 0; k + 2 < S; ++k) {
-        // x = A[k+1:, k]
-        if (threadIdx.x == 0) {
-            double nx = 0.0;
-            for (int i = k + 1; i < S; ++i) nx += A[i * S + k].x * A[i * S + k].x + A[i * S + k].y * A[i * S + k].y;
-            nx = sqrt(nx);
-            const double2 x0 = A[(k + 1) * S + k];
-            const double ax0 = sqrt(x0.x * x0.x + x0.y * x0.y);
-            const double2 ph = ax0 > 0 ? make_double2(x0.x / ax0, x0.y / ax0) : make_double2(1.0, 0.0);
-            // alpha = -ph * |x|; v = x - alpha e1
-            scal[0] = nx; scal[1] = ph.x; scal[2] = ph.y;
-            double vn = 0.0;
-            for (int i = k + 1; i < S; ++i) {
-                double2 vi = A[i * S + k];
-                if (i == k + 1) { vi.x += ph.x * nx; vi.y += ph.y * nx; }
-                v[i] = vi;
-                vn += vi.x * vi.x + vi.y * vi.y;
-            }
-            vn = sqrt(vn);
-            scal[3] = vn;
-            for (int i = k + 1; i < S; ++i) { if (vn > 0) { v[i].x /= vn; v[i].y /= vn; } else v[i] = make_double2(0, 0); }
+        // x = A[k+1:, k]; alpha = -ph |x| with ph the phase of x_0; v = (x - alpha e1)/|x - alpha e1|
+        double nx = 0.0, u1 = 0.0, u2 = 0.0;
+        for (int i = k + 1 + tid; i < S; i += nt) nx += A[i * S + k].x * A[i * S + k].x + A[i * S + k].y * A[i * S + k].y;
+        bsum3(nx, u1, u2);
+        nx = sqrt(nx);
+        const double2 x0 = A[(k + 1) * S + k];
+        const double ax0 = sqrt(x0.x * x0.x + x0.y * x0.y);
+        const double2 ph = ax0 > 0 ? make_double2(x0.x / ax0, x0.y / ax0) : make_double2(1.0, 0.0);
+        double vn = 0.0;
+        u1 = u2 = 0.0;
+        for (int i = k + 1 + tid; i < S; i += nt) {
+            double2 vi = A[i * S + k];
+            if (i == k + 1) { vi.x += ph.x * nx; vi.y += ph.y * nx; }
+            v[i] = vi;
+            vn += vi.x * vi.x + vi.y * vi.y;
         }
+        bsum3(vn, u1, u2);
+        vn = sqrt(vn);
+        if (vn == 0.0) continue;   // the column is zero already (uniform across the block)
+        for (int i = k + 1 + tid; i < S; i += nt) { v[i].x /= vn; v[i].y /= vn; }
         __syncthreads();
-        if (scal[3] == 0.0) { __syncthreads(); continue; }
-        // p = A v (rows k+1..), restricted to the trailing block
-        for (int i = k + 1 + threadIdx.x; i < S; i += blockDim.x) {
+        // p = A v on the trailing block
+        for (int i = k + 1 + tid; i < S; i += nt) {
             double2 acc = make_double2(0, 0);
             for (int c = k + 1; c < S; ++c) {
                 const double2 u = zmul(A[i * S + c], v[c]);
@@ -746,30 +754,34 @@ __global__ void k_nu_tridiag(DevParams Pm, DevState D, int S, const double* gram
             pv[i] = acc;
         }
         __syncthreads();
-        if (threadIdx.x == 0) {
-            double Kr = 0.0;
-            for (int i = k + 1; i < S; ++i) Kr += zmulc(v[i], pv[i]).x;   // v^H A v (real)
-            for (int i = k + 1; i < S; ++i) { pv[i].x -= Kr * v[i].x; pv[i].y -= Kr * v[i].y; }   // w = p - K v
-            // b <- H b = b - 2 v (v^H b)
-            double2 vb = make_double2(0, 0);
-            for (int i = k + 1; i < S; ++i) { const double2 u = zmulc(v[i], b[i]); vb.x += u.x; vb.y += u.y; }
-            for (int i = k + 1; i < S; ++i) { const double2 u = zmul(v[i], vb); b[i].x -= 2.0 * u.x; b[i].y -= 2.0 * u.y; }
+        // K = v^H A v (real), v^H b
+        double kr = 0.0, vbx = 0.0, vby = 0.0;
+        for (int i = k + 1 + tid; i < S; i += nt) {
+            kr += zmulc(v[i], pv[i]).x;
+            const double2 u = zmulc(v[i], b[i]);
+            vbx += u.x; vby += u.y;
+        }
+        bsum3(kr, vbx, vby);
+        // w = p - K v; b <- H b = b - 2 v (v^H b)
+        for (int i = k + 1 + tid; i < S; i += nt) {
+            pv[i].x -= kr * v[i].x; pv[i].y -= kr * v[i].y;
+            const double2 u = zmul(v[i], make_double2(vbx, vby));
+            b[i].x -= 2.0 * u.x; b[i].y -= 2.0 * u.y;
         }
         __syncthreads();
         // A <- A - 2 v w^H - 2 w v^H on the trailing block; column k: below-diagonal -> alpha e1
-        for (int t = threadIdx.x; t < (S - k - 1) * (S - k - 1); t += blockDim.x) {
+        for (int t = tid; t < (S - k - 1) * (S - k - 1); t += nt) {
             const int r = k + 1 + t / (S - k - 1), c = k + 1 + t % (S - k - 1);
             const double2 a1 = zmul(v[r], make_double2(pv[c].x, -pv[c].y));
             const double2 a2 = zmul(pv[r], make_double2(v[c].x, -v[c].y));
             A[r * S + c].x -= 2.0 * (a1.x + a2.x);
             A[r * S + c].y -= 2.0 * (a1.y + a2.y);
         }
-        __syncthreads();
-        if (threadIdx.x == 0) {
-            const double2 al = make_double2(-scal[1] * scal[0], -scal[2] * scal[0]);
-            A[(k + 1) * S + k] = al;
-            A[k * S + k + 1] = make_double2(al.x, -al.y);
-            for (int i = k + 2; i < S; ++i) { A[i * S + k] = make_double2(0, 0); A[k * S + i] = make_double2(0, 0); }
+        const double2 al = make_double2(-ph.x * nx, -ph.y * nx);
+        for (int i = k + 1 + tid; i < S; i += nt) {
+            const double2 e = (i == k + 1) ? al : make_double2(0, 0);
+            A[i * S + k] = e;
+            A[k * S + i] = make_double2(e.x, -e.y);
         }
         __syncthreads();
     }
