@@ -559,6 +559,16 @@ def run_batched(args, rank, world):
         t_init = time.perf_counter()
         b = bp.Batch(tup, n_streams=args.streams, shared_workspace=True, use_graph=use_graph, stream=stream)
         t_init = time.perf_counter() - t_init
+    tiles, tile_res = None, {}
+    if not args.no_tile_tune:
+        # kernel tile shapes per shape class, measured on single filters rebuilt from the
+        # members' states (the batch's graphs are captured again with them)
+        from paper_2604_19723_gb300 import autotune
+        t0 = time.perf_counter()
+        tile_res = autotune.tune_batch_tiles(b, tup, z[0], reps=1)
+        tiles = {"classes": len(tile_res), "seconds": time.perf_counter() - t0,
+                 "choices": {k: {"scenarios": v["scenarios"], "best": {f: x for f, x in v["best"].items() if x}}
+                             for k, v in tile_res.items()}}
     members = [b.member(i) for i in range(n)]
     t_step, launches, clocks = timed(b, z, members)
     dev_bytes = b.device_bytes()
@@ -590,6 +600,10 @@ def run_batched(args, rank, world):
     seq_ms = None
     if not args.no_sequential:
         b1 = bp.Batch(tup, n_streams=1, shared_workspace=True, use_graph=False, stream=stream)
+        if args.sequential_tiles:
+            for v in tile_res.values():
+                for i in v["members"]:
+                    b1.set_tiles(i, **v["best"])
         m1 = [b1.member(i) for i in range(n)]
         seq_ms, _, _ = timed(b1, z, m1)
         del m1
@@ -612,11 +626,13 @@ def run_batched(args, rank, world):
                       "Nz": "U{5..300} (one antenna below 16, else 2x2 URA)", "J": 4,
                       "particle_PA_updates_per_step": updates, "streams": min(args.streams, n),
                       "graph": bool(tuned["best"][1]) if tuned else True, "shared_workspace": True,
-                      "autotune": tuned, "device_GB": dev_bytes / 1e9,
+                      "autotune": tuned, "tiles": tiles, "device_GB": dev_bytes / 1e9,
                       "init_s": t_init, "l2": "flushed between timed steps (256 MB write)",
                       "parallelism": f"replicas x{world}"},
            "sequential": ({"ms_per_step": seq_ms, "value": world * updates / (seq_ms * 1e-3),
-                           "speedup": seq_ms / t_step, "how": "same scenarios, one stream, direct launches"}
+                           "speedup": seq_ms / t_step,
+                           "how": "same scenarios, one stream, direct launches, " +
+                                  ("the tuned tiles" if args.sequential_tiles and tile_res else "built-in tiles")}
                           if seq_ms else None),
            "roofline": {"bound": "alu", "kernel": "k_kappa + k_iota/k_iota_blk of every scenario (whole step time)",
                         "achieved": ach, "peak": peak_alu, "unit": "TFLOP/s", "frac": ach / peak_alu,
@@ -652,6 +668,9 @@ def main():
     ap.add_argument("--scenarios", type=int, default=4096, help="batched workload: number of scenarios")
     ap.add_argument("--streams", type=int, default=32, help="batched workload: concurrent streams")
     ap.add_argument("--no-sequential", action="store_true", help="batched workload: skip the one-stream run")
+    ap.add_argument("--no-tile-tune", action="store_true", help="batched workload: built-in kernel tile shapes")
+    ap.add_argument("--sequential-tiles", action="store_true",
+                    help="batched workload: the one-stream run uses the tuned tiles too")
     ap.add_argument("--no-autotune", action="store_true",
                     help="batched workload: use --streams with graphs instead of the measured best configuration")
     args = ap.parse_args()

@@ -238,6 +238,35 @@ enum { BP_PROF_STAGES = 9 };
 bp_status bp_set_profiling(bp_handle* h, int on);
 bp_status bp_get_profile(bp_handle* h, double* ms, int n);
 
+/* Kernel tile configuration of a filter: the knobs of the measured autotuner
+ * (paper_2604_19723_gb300/autotune.py).  The paper has no counterpart; results
+ * depend on them only through FP32 rounding.  0 in a field = the built-in
+ * choice.
+ *   kappa_sc      column bucket S~ of the CUDA-core PF likelihood (S~ - 1 basis
+ *                 columns held per particle): 8, 16, 24, 32, 48 or 64.  Used
+ *                 when S <= kappa_sc <= the filter's basis stride (32 for
+ *                 S_max <= 32, else 64), otherwise the smallest bucket >= S.
+ *   kappa_blocks  CUDA-core PF-likelihood blocks of 256 particles per SM: 1 or 2
+ *                 (2 caps registers at 128 per thread and shrinks the staged
+ *                 frequency chunk; buckets <= 32 only, else 1 is used).
+ *   kappa_fch     frequencies of V staged in shared memory per chunk (the Nz
+ *                 tile), clamped to what fits.
+ *   kappa_tc      1: the tensor-core PF likelihood wherever the shape allows it
+ *                 (64 basis columns, 2 My Mz in {8, 16, 32}, Nf <= 16);
+ *                 -1: never.
+ *   table_chunk   particles per shared-memory chunk of the message table: 16,
+ *                 32, 64 or 128 (clamped to what fits).
+ *   table_split   particle splits of the message-table grid (>= 1; clamped to
+ *                 P / 256 and the workspace's partial-sum capacity).
+ * bp_set_tiles validates and stores the fields (BP_ERR_INVALID_ARG for a value
+ * outside the lists above; nothing is changed then); they apply from the next
+ * bp_update.  bp_get_tiles returns the stored fields.  Host-only calls. */
+typedef struct {
+    int kappa_sc, kappa_blocks, kappa_fch, kappa_tc, table_chunk, table_split;
+} bp_tiles;
+bp_status bp_set_tiles(bp_handle* h, const bp_tiles* t);
+bp_status bp_get_tiles(const bp_handle* h, bp_tiles* t);
+
 /* Systematic resampling of one belief that allocates no device memory.
  * The paper has no counterpart: this entry point exists for callers that
  * cannot call cudaMalloc (code under CUDA graph capture, real-time loops that
@@ -362,6 +391,10 @@ bp_status bp_batch_sync(bp_batch* b);
 
 /* Handle of scenario i (owned by the batch). */
 bp_status bp_batch_handle(bp_batch* b, int i, bp_handle** h);
+
+/* bp_set_tiles on scenario i; the captured step graphs are dropped and
+ * captured again at the next bp_batch_step. */
+bp_status bp_batch_set_tiles(bp_batch* b, int i, const bp_tiles* t);
 
 /* Stream index a scenario was dealt to, and the bytes of device memory the
  * batch holds (state + workspaces), for inspection. */

@@ -31,8 +31,13 @@ ENTRY_POINTS = ("bp_init", "bp_predict", "bp_update", "bp_estimate", "bp_free", 
                 "bp_batch_last_error", "bp_pcrlb_fim", "bp_pcrlb_recursion",
                 "bp_mlp_create", "bp_mlp_get_params", "bp_mlp_forward", "bp_mlp_grads", "bp_mlp_train_step",
                 "bp_mlp_sync", "bp_mlp_free", "bp_mlp_last_error", "bp_set_mt_proposal", "bp_lp_dataset",
-                "bp_selftest_wait")
+                "bp_selftest_wait", "bp_set_tiles", "bp_get_tiles", "bp_batch_set_tiles")
+TILE_FIELDS = ("kappa_sc", "kappa_blocks", "kappa_fch", "kappa_tc", "table_chunk", "table_split")
 PROFILE_STAGES = ("predict", "row_sums", "table", "stage", "kappa", "iota", "nu", "normalize", "resample")
+
+
+class _Tiles(C.Structure):
+    _fields_ = [(f, C.c_int) for f in TILE_FIELDS]
 
 
 class BPError(RuntimeError):
@@ -144,6 +149,9 @@ def load() -> C.CDLL:
     lib.bp_mlp_last_error.restype = C.c_char_p
     lib.bp_set_mt_proposal.argtypes = [vp, vp]
     lib.bp_selftest_wait.argtypes = [C.c_int, vp]
+    lib.bp_set_tiles.argtypes = [vp, C.POINTER(_Tiles)]
+    lib.bp_get_tiles.argtypes = [vp, C.POINTER(_Tiles)]
+    lib.bp_batch_set_tiles.argtypes = [vp, C.c_int, C.POINTER(_Tiles)]
     lib.bp_lp_dataset.argtypes = [C.POINTER(_Geometry), C.POINTER(_Params), C.c_int, C.POINTER(C.c_double),
                                   C.POINTER(C.c_double), C.c_double, C.c_int] + [C.c_double] * 4 + \
                                  [C.c_int, C.c_uint64, vp, vp, vp]
@@ -237,6 +245,21 @@ class Filter:
 
     def set_profiling(self, on: bool):
         _check(self.lib, self.h, self.lib.bp_set_profiling(self.h, int(bool(on))), "bp_set_profiling")
+
+    def set_tiles(self, **tiles):
+        """Kernel tile requests (bp_set_tiles): any of TILE_FIELDS; fields not given keep
+        their value, 0 = built-in."""
+        t = self.get_tiles()
+        for k, v in tiles.items():
+            if k not in TILE_FIELDS:
+                raise ValueError(f"unknown tile field {k}")
+            t[k] = int(v)
+        _check(self.lib, self.h, self.lib.bp_set_tiles(self.h, C.byref(_Tiles(**t))), "bp_set_tiles")
+
+    def get_tiles(self) -> Dict[str, int]:
+        t = _Tiles()
+        _check(self.lib, self.h, self.lib.bp_get_tiles(self.h, C.byref(t)), "bp_get_tiles")
+        return {f: int(getattr(t, f)) for f in TILE_FIELDS}
 
     def profile(self) -> Dict[str, float]:
         """Durations (ms) of each stage of the last predict and update."""
@@ -440,9 +463,14 @@ class _BatchMember(Filter):
     def __init__(self, batch, i, h, geom, params, P, S_max):
         self.lib, self.h, self.geom, self.params, self.P, self.S_max = batch.lib, h, geom, params, P, S_max
         self._batch = batch   # keeps the batch (and the handle) alive
+        self._i = i
 
     def close(self):
         self.h = None
+
+    def set_tiles(self, **tiles):
+        """Through the batch, which drops its captured graphs."""
+        self._batch.set_tiles(self._i, **tiles)
 
     def predict(self):
         raise BPError(6, "a batch scenario steps through Batch.step")
@@ -514,6 +542,15 @@ class Batch:
 
     def device_bytes(self) -> int:
         return int(self.lib.bp_batch_device_bytes(self.b))
+
+    def set_tiles(self, i: int, **tiles):
+        """bp_batch_set_tiles on scenario i (fields not given keep their value)."""
+        t = self.member(i).get_tiles()
+        for k, v in tiles.items():
+            if k not in TILE_FIELDS:
+                raise ValueError(f"unknown tile field {k}")
+            t[k] = int(v)
+        self._check(self.lib.bp_batch_set_tiles(self.b, i, C.byref(_Tiles(**t))), "bp_batch_set_tiles")
 
     def member(self, i: int) -> Filter:
         h = C.c_void_p()

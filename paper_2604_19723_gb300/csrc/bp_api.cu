@@ -303,6 +303,26 @@ bp_status bp_get_diag(bp_handle* h, int what, void* host, size_t bytes) {
     return BP_OK;
 }
 
+bp_status bp_set_tiles(bp_handle* h, const bp_tiles* t) {
+    if (!h || !t) return BP_ERR_INVALID_ARG;
+    const int sc = t->kappa_sc;
+    const bool ok = (sc == 0 || sc == 8 || sc == 16 || sc == 24 || sc == 32 || sc == 48 || sc == 64) &&
+                    (t->kappa_blocks == 0 || t->kappa_blocks == 1 || t->kappa_blocks == 2) && t->kappa_fch >= 0 &&
+                    (t->kappa_tc == 0 || t->kappa_tc == 1 || t->kappa_tc == -1) &&
+                    (t->table_chunk == 0 || t->table_chunk == 16 || t->table_chunk == 32 || t->table_chunk == 64 ||
+                     t->table_chunk == 128) &&
+                    t->table_split >= 0;
+    if (!ok) return fail(h, BP_ERR_INVALID_ARG, "bp_set_tiles: a field is outside its list of values");
+    h->tiles = *t;
+    return BP_OK;
+}
+
+bp_status bp_get_tiles(const bp_handle* h, bp_tiles* t) {
+    if (!h || !t) return BP_ERR_INVALID_ARG;
+    *t = h->tiles;
+    return BP_OK;
+}
+
 bp_status bp_set_profiling(bp_handle* h, int on) {
     if (!h) return BP_ERR_INVALID_ARG;
     if (on && !h->prof_on) {
@@ -612,16 +632,18 @@ void update_enqueue(bp_handle* h, const float* z_dev) {
     h->launches += launch_birth_proposal(h->G, h->Pm, D, h->S_legacy, S, z_dev, h->st);
     launch_row_sums(h->Pm, D, S, J, h->st);
     mark(h, 2);
-    int nsplit = std::max(1, (4 * 152 + S * J - 1) / (S * J));
+    int nsplit = h->tiles.table_split > 0 ? h->tiles.table_split : std::max(1, (4 * 152 + S * J - 1) / (S * J));
     nsplit = std::min(nsplit, std::max(1, P / 256));
     nsplit = std::min(nsplit, h->nsplit_max);
     launch_geom(h->G, h->Pm, D, S, h->st);
-    launch_table(h->G, h->Pm, D, S, nsplit, h->st);
+    launch_table(h->G, h->Pm, D, S, nsplit, h->tiles.table_chunk, h->st);
     mark(h, 3);
     launch_stage(h->G, h->Pm, D, S, h->SCA, z_dev, h->gram, h->nu_b, h->V64, h->st, h->st_side, h->ev_fork, h->ev_join);
-    if (S > 32) h->launches += launch_kappa_btile(h->G, D, S, h->SCA, h->st);   // B tiles of the tensor-core kernel
+    const KappaPlan kp = plan_kappa(h->G, D, S, h->SCA, h->tiles.kappa_sc, h->tiles.kappa_blocks, h->tiles.kappa_fch,
+                                    h->tiles.kappa_tc);
+    if (kp.tc) h->launches += launch_kappa_btile(h->G, D, S, h->SCA, h->st);   // B tiles of the tensor-core kernel
     mark(h, 4);
-    launch_kappa(h->G, h->Pm, D, S, h->SCA, h->st);
+    launch_kappa(h->G, h->Pm, D, S, h->SCA, kp, h->st);
     mark(h, 5);
     const int iota_launches = launch_iota(h->G, h->Pm, D, S, z_dev, h->st) + 1;
     launch_iota_repair(h->G, h->Pm, D, S, z_dev, h->st);

@@ -306,6 +306,18 @@ bp_status bp_batch_handle(bp_batch* b, int i, bp_handle** h) {
     return BP_OK;
 }
 
+bp_status bp_batch_set_tiles(bp_batch* b, int i, const bp_tiles* t) {
+    if (!b || !t || i < 0 || i >= (int)b->h.size()) return BP_ERR_INVALID_ARG;
+    const bp_status s = bp_set_tiles(b->h[i], t);
+    if (s != BP_OK) return bfail(b, s, "bp_batch_set_tiles: a field is outside its list of values");
+    // the captured graphs hold the old launch configurations
+    for (int k = 0; k < 2; ++k) {
+        if (b->exec[k]) cudaGraphExecDestroy(b->exec[k]);
+        b->exec[k] = nullptr;
+    }
+    return BP_OK;
+}
+
 int bp_batch_stream_of(const bp_batch* b, int i) {
     return (b && i >= 0 && i < (int)b->stream_of.size()) ? b->stream_of[i] : -1;
 }

@@ -37,6 +37,7 @@ struct bp_handle {
     int phase;          // 0: belief state, 1: predicted
     int births_skipped;
     int nsplit_max;
+    bp_tiles tiles;     // kernel tile requests (bp_set_tiles; zero = built-in)
     long long launches;
     size_t dev_bytes;   // device memory of the handle's own allocations (workspace excluded)
     // per-handle scratch

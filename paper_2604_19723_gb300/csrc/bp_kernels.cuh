@@ -200,13 +200,21 @@ void launch_iota_repair(const DevGeom& G, const DevParams& Pm, const DevState& D
 void launch_init(const DevGeom& G, const DevParams& Pm, const DevState& D, int S0, cudaStream_t st);
 int launch_predict(const DevGeom& G, const DevParams& Pm, const DevState& D, int S_old, int S_new, cudaStream_t st);
 void launch_row_sums(const DevParams& Pm, const DevState& D, int S, int J, cudaStream_t st);
-void launch_table(const DevGeom& G, const DevParams& Pm, const DevState& D, int S, int nsplit, cudaStream_t st);
+// chunk_req: particles per shared-memory chunk (16, 32, 64, 128; 0 = 128), halved to fit
+void launch_table(const DevGeom& G, const DevParams& Pm, const DevState& D, int S, int nsplit, int chunk_req,
+                  cudaStream_t st);
 // the PF basis stage; with a side stream the noise-likelihood tridiagonalisation runs there
 // (forked after the Gram through ev_fork, ev_join recorded after it)
 void launch_stage(const DevGeom& G, const DevParams& Pm, const DevState& D, int S, int SC, const float* z,
                   double* gram, double* nu_b, double* V64, cudaStream_t st, cudaStream_t side = nullptr,
                   cudaEvent_t ev_fork = nullptr, cudaEvent_t ev_join = nullptr);
-void launch_kappa(const DevGeom& G, const DevParams& Pm, const DevState& D, int S, int SCA, cudaStream_t st);
+// the PF-likelihood launch chosen from S, the shape and the tile requests (0 = built-in):
+// column bucket sc, tensor-core kernel or CUDA-core one with mb blocks per SM and fch
+// frequencies staged per chunk (smem bytes)
+struct KappaPlan { int sc, mb, fch; bool tc; size_t smem; };
+KappaPlan plan_kappa(const DevGeom& G, const DevState& D, int S, int SCA, int t_sc, int t_mb, int t_fch, int t_tc);
+void launch_kappa(const DevGeom& G, const DevParams& Pm, const DevState& D, int S, int SCA, const KappaPlan& k,
+                  cudaStream_t st);
 bool kappa_tc_ok(const DevGeom& G, int SCA);
 size_t kappa_btile_floats(const DevGeom& G, int S_max);
 // operand tiles of both tensor-core passes of the PF likelihood; returns launches

@@ -90,8 +90,9 @@ __device__ inline void kappa_amp_terms(const float2* yt, const float2* il, const
     gg = q0 + q1;
 }
 
-template <int SC>
-__global__ void __launch_bounds__(256, (SC <= 16 ? 2 : 1)) k_kappa(DevGeom G, DevParams Pm, DevState D, int S, int SCA, int fch) {
+// MB blocks per SM (register cap 65536 / (256 MB) per thread)
+template <int SC, int MB>
+__global__ void __launch_bounds__(256, MB) k_kappa(DevGeom G, DevParams Pm, DevState D, int S, int SCA, int fch) {
     constexpr int KT = 256;
     constexpr int NC = SC - 1;           // basis columns (zero beyond S-2)
     constexpr int NP = SC / 2;           // column pairs per row
@@ -1490,37 +1491,70 @@ int launch_kappa_btile(const DevGeom& G, const DevState& D, int S, int SCA, cuda
     return 2;
 }
 
-template <int SC>
-static void launch_kappa_sc(const DevGeom& G, const DevParams& Pm, const DevState& D, int S, int SCA, cudaStream_t st) {
-    const int nfac = G.Nf + G.My + G.Mz;
-    const int Nm = G.My * G.Mz;
-    // 1/lambda, w [2 SC], factors [nfac][256], low parts of a_y, a_z [My + Mz][256] (float2),
-    // alignment slack and the (hi, lo) cis table [256] (float4)
-    const size_t fixed = (2 * (size_t)SC + ((size_t)nfac + G.My + G.Mz) * 256) * sizeof(float2) + 16 + 256 * sizeof(float4);
-    const size_t per_f = (size_t)Nm * (SC + 1) * sizeof(float2) + Nm * sizeof(float);   // V rows, low part of r0, |V_k|^2
-    dim3 grid((Pm.P + 255) / 256, S);
-    if constexpr (SC == 64) {
-        if (D.kB && kappa_tc_ok(G, SCA)) {
-            constexpr int NT = KAPPA_TC_NT;
-            smem_allow_max((const void*)k_kappa_tc<NT>);
-            k_kappa_tc<NT><<<dim3((Pm.P + 128 * NT - 1) / (128 * NT), S), 128 * NT, kappa_tc_smem(G), st>>>(
-                G, Pm, D, S, SCA, D.kB, D.kB + kappa_btile1_floats(G, S));
-            return;
-        }
-    }
-    const size_t limit = 200 * 1024;
+// shared memory of the CUDA-core PF likelihood: 1/lambda, y~0 [2 SC], factors [nfac][256],
+// low parts of a_y, a_z [My + Mz][256] (float2), alignment slack and the (hi, lo) cis table
+// [256] (float4), then per staged frequency the V rows, the low part of r0 and |V_k|^2
+static size_t kappa_smem_fixed(const DevGeom& G, int SC) {
+    const size_t nfac = (size_t)G.Nf + G.My + G.Mz;
+    return (2 * (size_t)SC + (nfac + G.My + G.Mz) * 256) * sizeof(float2) + 16 + 256 * sizeof(float4);
+}
+static size_t kappa_smem_per_f(const DevGeom& G, int SC) {
+    const size_t Nm = (size_t)G.My * G.Mz;
+    return Nm * (SC + 1) * sizeof(float2) + Nm * sizeof(float);
+}
+// shared-memory budget per block: one block per SM, or two (228 KB per SM, 1 KB reserved each)
+static size_t kappa_smem_budget(int mb) { return mb == 2 ? 112 * 1024 : 200 * 1024; }
+
+static bool kappa_sc_valid(int sc) { return sc == 8 || sc == 16 || sc == 24 || sc == 32 || sc == 48 || sc == 64; }
+
+KappaPlan plan_kappa(const DevGeom& G, const DevState& D, int S, int SCA, int t_sc, int t_mb, int t_fch, int t_tc) {
+    KappaPlan k{};
+    // the bucket: the requested one where it holds S and fits the basis stride, else the
+    // smallest that holds S; the tensor-core kernel where allowed and not declined
+    const bool tc_shape = D.kB && kappa_tc_ok(G, SCA);
+    if (kappa_sc_valid(t_sc) && t_sc >= S && t_sc <= SCA) k.sc = t_sc;
+    else if (S > 32 && tc_shape && t_tc >= 0) k.sc = 64;
+    else k.sc = S <= 8 ? 8 : S <= 16 ? 16 : S <= 24 ? 24 : S <= 32 ? 32 : S <= 48 ? 48 : 64;
+    k.tc = k.sc == 64 && tc_shape && t_tc >= 0;
+    if (k.tc) return k;
+    k.mb = (k.sc <= 16) ? 2 : (t_mb == 2 && k.sc <= 32 ? 2 : 1);
+    const size_t fixed = kappa_smem_fixed(G, k.sc), per_f = kappa_smem_per_f(G, k.sc);
+    if (k.mb == 2 && k.sc > 16 && fixed + per_f > kappa_smem_budget(2)) k.mb = 1;
+    const size_t limit = kappa_smem_budget(k.mb);
     int fch = G.Nf;
     while (fch > 1 && fixed + fch * per_f > limit) fch = (fch + 1) / 2;
-    const size_t smem = fixed + fch * per_f;
-    smem_allow_max((const void*)k_kappa<SC>);
-    k_kappa<SC><<<grid, 256, smem, st>>>(G, Pm, D, S, SCA, fch);
+    if (t_fch > 0 && t_fch < fch) fch = t_fch;
+    k.fch = fch;
+    k.smem = fixed + (size_t)fch * per_f;
+    return k;
 }
 
-void launch_kappa(const DevGeom& G, const DevParams& Pm, const DevState& D, int S, int SCA, cudaStream_t st) {
-    if (S <= 8) launch_kappa_sc<8>(G, Pm, D, S, SCA, st);
-    else if (S <= 16) launch_kappa_sc<16>(G, Pm, D, S, SCA, st);
-    else if (S <= 32) launch_kappa_sc<32>(G, Pm, D, S, SCA, st);
-    else launch_kappa_sc<64>(G, Pm, D, S, SCA, st);
+template <int SC, int MB>
+static void launch_kappa_cc(const DevGeom& G, const DevParams& Pm, const DevState& D, int S, int SCA, int fch,
+                            size_t smem, cudaStream_t st) {
+    smem_allow_max((const void*)k_kappa<SC, MB>);
+    k_kappa<SC, MB><<<dim3((Pm.P + 255) / 256, S), 256, smem, st>>>(G, Pm, D, S, SCA, fch);
+}
+
+void launch_kappa(const DevGeom& G, const DevParams& Pm, const DevState& D, int S, int SCA, const KappaPlan& k,
+                  cudaStream_t st) {
+    if (k.tc) {
+        constexpr int NT = KAPPA_TC_NT;
+        smem_allow_max((const void*)k_kappa_tc<NT>);
+        k_kappa_tc<NT><<<dim3((Pm.P + 128 * NT - 1) / (128 * NT), S), 128 * NT, kappa_tc_smem(G), st>>>(
+            G, Pm, D, S, SCA, D.kB, D.kB + kappa_btile1_floats(G, S));
+        return;
+    }
+    switch (k.sc * 4 + k.mb) {
+        case 8 * 4 + 2:  launch_kappa_cc<8, 2>(G, Pm, D, S, SCA, k.fch, k.smem, st); break;
+        case 16 * 4 + 2: launch_kappa_cc<16, 2>(G, Pm, D, S, SCA, k.fch, k.smem, st); break;
+        case 24 * 4 + 1: launch_kappa_cc<24, 1>(G, Pm, D, S, SCA, k.fch, k.smem, st); break;
+        case 24 * 4 + 2: launch_kappa_cc<24, 2>(G, Pm, D, S, SCA, k.fch, k.smem, st); break;
+        case 32 * 4 + 1: launch_kappa_cc<32, 1>(G, Pm, D, S, SCA, k.fch, k.smem, st); break;
+        case 32 * 4 + 2: launch_kappa_cc<32, 2>(G, Pm, D, S, SCA, k.fch, k.smem, st); break;
+        case 48 * 4 + 1: launch_kappa_cc<48, 1>(G, Pm, D, S, SCA, k.fch, k.smem, st); break;
+        default:         launch_kappa_cc<64, 1>(G, Pm, D, S, SCA, k.fch, k.smem, st); break;
+    }
 }
 
 // S below which the FP32 path runs first and only flagged particles are redone

@@ -806,12 +806,13 @@ __global__ void k_nu_tridiag(DevParams Pm, DevState D, int S, const double* gram
     }
 }
 
-void launch_table(const DevGeom& G, const DevParams& Pm, const DevState& D, int S, int nsplit, cudaStream_t st) {
+void launch_table(const DevGeom& G, const DevParams& Pm, const DevState& D, int S, int nsplit, int chunk_req,
+                  cudaStream_t st) {
     const int Nz = G.Nz;
     const int bs = Nz <= 256 ? ((Nz + 31) / 32) * 32 : 256;
     const int ept = (Nz + bs - 1) / bs;
     const int per_particle = (((3 * G.Nf) | 1) + ((G.My * G.Mz) | 1) + ((G.My + G.Mz) | 1)) * (int)sizeof(float2);
-    int chunk = 128;
+    int chunk = (chunk_req == 16 || chunk_req == 32 || chunk_req == 64) ? chunk_req : 128;
     while (chunk > 16 && chunk * per_particle > 96 * 1024) chunk /= 2;
     const size_t smem = (size_t)chunk * per_particle;
     dim3 grid(nsplit, S, G.J);
