@@ -80,12 +80,19 @@ def iota_flops(P, S, J, Nf, My, Mz):
     return float(P) * J * per
 
 
-# DRAM bytes per particle of one launch, from one ncu capture of that kernel alone on a
-# small case of the workload (dram__bytes_read.sum + dram__bytes_write.sum, -c 1); the
-# kernel's traffic grows in proportion to the particles (per-particle data and one read
-# of the per-(s, j) operand tiles per block), so a full launch moves P times this.  Valid
-# while the kernel sources hash to the recorded value.
-TRAFFIC_RECORDS = {}
+# DRAM bytes of one launch of a kernel (dram__bytes_read.sum + dram__bytes_write.sum), from
+# a one-pass ncu capture of that kernel alone (-c 1) running the bench command itself at
+# full size.  The kernels' traffic does not scale with the particles (operand tiles read
+# once per PF and then served from L2), so a record applies only to the workload and
+# particle count it was taken at, and only while the kernel sources hash to the recorded
+# value.
+TRAFFIC_RECORDS = {
+    "k_kappa_tc": {"workload": "scale_64x100k", "P": 100000, "bytes": 871952384 + 50390016,
+                   "sources_sha256": "9015fc95616b0dff1dab2d0de8feac7a2ff9b16dc100b40806a6b91ec165ef0a",
+                   "how": "ncu --metrics dram__bytes_read.sum,dram__bytes_write.sum,gpu__time_duration.sum "
+                          "--clock-control none -k regex:^k_kappa_tc$ -c 1 python bench.py --steps 2 "
+                          "--warmup 1 --no-matched --no-cpu-baseline"},
+}
 KERNEL_SOURCES = ("paper_2604_19723_gb300/csrc/k_like.cu", "paper_2604_19723_gb300/csrc/bp_kernels.cuh",
                   "paper_2604_19723_gb300/csrc/bp_internal.cuh", "paper_2604_19723_gb300/csrc/tc_sm100.cuh")
 
@@ -101,9 +108,9 @@ def kernel_sources_sha256():
 
 def traffic_for(kernel, workload, P):
     rec = TRAFFIC_RECORDS.get(kernel)
-    if not rec or rec["workload"] != workload or rec["sources_sha256"] != kernel_sources_sha256():
+    if not rec or rec["workload"] != workload or rec["P"] != P or rec["sources_sha256"] != kernel_sources_sha256():
         return None
-    return rec["bytes_per_particle"] * P
+    return rec["bytes"]
 
 
 def reduce_max(x, world, device):
