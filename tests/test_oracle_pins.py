@@ -530,6 +530,52 @@ def test_regularisation_jitter_covariance():
     assert np.allclose(np.cov(jit), h * h * resample.weighted_cov(X, w), rtol=0.03, atol=1e-5)
 
 
+def test_h_opt_minimises_the_gaussian_kernel_amise():
+    """h_opt (Musso et al., as cited in Sec. IV-D, the regularisation paragraph) is the
+    bandwidth that minimises the asymptotic mean integrated squared error of a Gaussian
+    kernel estimate of a Gaussian density in whitened coordinates:
+    AMISE(h) = R(K)/(P h^d) + h^4/4 int (Laplacian f)^2.  Both integrals are taken here by
+    quadrature on a grid and AMISE is minimised numerically, independent of the formula."""
+    from scipy import optimize
+    for d in (1, 2, 3):
+        g = np.linspace(-7.0, 7.0, 121)
+        dx = g[1] - g[0]
+        r2 = sum(x * x for x in np.meshgrid(*([g] * d), indexing="ij"))
+        f = np.exp(-r2 / 2) / (2 * np.pi) ** (d / 2)
+        lap2 = np.sum(((r2 - d) * f) ** 2) * dx ** d      # int (Laplacian f)^2
+        RK = np.sum(f ** 2) * dx ** d                       # int K^2, K the standard normal
+        for P in (100, 3000, 100000):
+            h = optimize.minimize_scalar(lambda t: RK / (P * t ** d) + t ** 4 / 4 * lap2, bounds=(1e-4, 5.0),
+                                         method="bounded", options={"xatol": 1e-12}).x
+            assert resample.h_opt(P, d) == pytest.approx(h, rel=1e-6), (d, P)
+
+
+def test_regularisation_covariance_is_the_weighted_moment():
+    """The kernel's covariance is the second central moment of the belief, i.e. of the
+    weighted particle set (reading R8): two clouds of coincident particles at a and b with
+    total weights w and 1 - w have covariance w (1 - w) (a - b)(a - b)^T whatever the
+    particle counts, a rank-one matrix, so the zeroing Cholesky leaves one column and the
+    jitter moves particles along a - b only, with variance h_opt^2 w (1 - w) |a - b|^2."""
+    P, w = 200000, 0.3
+    a, b = np.array([1.0, -2.0, 0.5]), np.array([1.4, -1.0, 0.5])
+    n_a = P // 4                                   # 1/4 of the particles carry weight w
+    X = np.concatenate([np.repeat(a[:, None], n_a, 1), np.repeat(b[:, None], P - n_a, 1)], axis=1)
+    wt = np.concatenate([np.full(n_a, w / n_a), np.full(P - n_a, (1 - w) / (P - n_a))])
+    D = a - b
+    C = resample.weighted_cov(X, wt)
+    assert np.allclose(C, w * (1 - w) * np.outer(D, D), rtol=1e-9, atol=1e-14)
+    # the unweighted moment of the same set differs: (1/4)(3/4) instead of w (1 - w)
+    assert not np.allclose(np.cov(X, bias=True), C, rtol=1e-3)
+    jit = resample._jitter(X, wt, np.ones(3, bool), 5, 1, rng.JITTER_PF, 2, P)
+    h = resample.h_opt(P, 3)
+    along = D / np.linalg.norm(D)
+    proj = along @ jit
+    assert np.var(proj) == pytest.approx(h * h * w * (1 - w) * (D @ D), rel=0.02)
+    # off a - b only what FP64 rounding leaves in the rank-one factor (a second pivot of
+    # ~1e-17 keeps a column of ~sqrt(1e-17))
+    assert np.max(np.abs(jit - np.outer(along, proj))) < 1e-6 * np.max(np.abs(jit))
+
+
 def test_zeroing_cholesky():
     C = np.diag([4.0, 0.0, 9.0])
     C[0, 2] = C[2, 0] = 1.0
