@@ -255,9 +255,10 @@ bp_status bp_get_profile(bp_handle* h, double* ms, int n);
  *                 (64 basis columns, 2 My Mz in {8, 16, 32}, Nf <= 16);
  *                 -1: never.
  *   table_chunk   particles per shared-memory chunk of the message table: 16,
- *                 32, 64 or 128 (clamped to what fits).
+ *                 32, 64 or 128 (clamped to what fits; built-in 64).
  *   table_split   particle splits of the message-table grid (>= 1; clamped to
- *                 P / 256 and the workspace's partial-sum capacity).
+ *                 P / 256 and the workspace's partial-sum capacity; built-in
+ *                 about 4096 blocks over the S x J problems).
  * bp_set_tiles validates and stores the fields (BP_ERR_INVALID_ARG for a value
  * outside the lists above; nothing is changed then); they apply from the next
  * bp_update.  bp_get_tiles returns the stored fields.  Host-only calls. */

@@ -632,7 +632,8 @@ void update_enqueue(bp_handle* h, const float* z_dev) {
     h->launches += launch_birth_proposal(h->G, h->Pm, D, h->S_legacy, S, z_dev, h->st);
     launch_row_sums(h->Pm, D, S, J, h->st);
     mark(h, 2);
-    int nsplit = h->tiles.table_split > 0 ? h->tiles.table_split : std::max(1, (4 * 152 + S * J - 1) / (S * J));
+    // the built-in split aims at ~4096 table blocks (several waves of short blocks)
+    int nsplit = h->tiles.table_split > 0 ? h->tiles.table_split : std::max(1, (4096 + S * J - 1) / (S * J));
     nsplit = std::min(nsplit, std::max(1, P / 256));
     nsplit = std::min(nsplit, h->nsplit_max);
     launch_geom(h->G, h->Pm, D, S, h->st);

@@ -200,7 +200,7 @@ void launch_iota_repair(const DevGeom& G, const DevParams& Pm, const DevState& D
 void launch_init(const DevGeom& G, const DevParams& Pm, const DevState& D, int S0, cudaStream_t st);
 int launch_predict(const DevGeom& G, const DevParams& Pm, const DevState& D, int S_old, int S_new, cudaStream_t st);
 void launch_row_sums(const DevParams& Pm, const DevState& D, int S, int J, cudaStream_t st);
-// chunk_req: particles per shared-memory chunk (16, 32, 64, 128; 0 = 128), halved to fit
+// chunk_req: particles per shared-memory chunk (16, 32, 64, 128; 0 = 64), halved to fit
 void launch_table(const DevGeom& G, const DevParams& Pm, const DevState& D, int S, int nsplit, int chunk_req,
                   cudaStream_t st);
 // the PF basis stage; with a side stream the noise-likelihood tridiagonalisation runs there
