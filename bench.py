@@ -87,8 +87,8 @@ def iota_flops(P, S, J, Nf, My, Mz):
 # particle count it was taken at, and only while the kernel sources hash to the recorded
 # value.
 TRAFFIC_RECORDS = {
-    "k_kappa_tc": {"workload": "scale_64x100k", "P": 100000, "bytes": 871952384 + 50390016,
-                   "sources_sha256": "9015fc95616b0dff1dab2d0de8feac7a2ff9b16dc100b40806a6b91ec165ef0a",
+    "k_kappa_tc": {"workload": "scale_64x100k", "P": 100000, "bytes": 873929216 + 50618368,
+                   "sources_sha256": "22c89609d08009e26757bdf82add7c304b0be579e5787e6a4c38b6d392418d43",
                    "how": "ncu --metrics dram__bytes_read.sum,dram__bytes_write.sum,gpu__time_duration.sum "
                           "--clock-control none -k regex:^k_kappa_tc$ -c 1 python bench.py --steps 2 "
                           "--warmup 1 --no-matched --no-cpu-baseline"},
