@@ -65,6 +65,16 @@ __device__ __forceinline__ void kappa_amp_ff_term(ff& G, float l, float2 y, floa
     G.lo = __fadd_rn(G.lo, __fadd_rn(et, fmaf(l, lo, eq)));
 }
 
+// column c's g_c into G (float-float) or g (FP32), and |h_c|^2/lambda_c into q
+__device__ __forceinline__ void kappa_amp_col(ff& G, float& g, float& q, float2 y, float l, float2 hc, float2 u) {
+    const float vx = fmaf(u.x, hc.x, u.y * hc.y);     // v = u conj(h)
+    const float vy = fmaf(u.y, hc.x, -(u.x * hc.y));
+    const float m = fabsf(y.x) + fabsf(y.y) + fabsf(vx) + fabsf(vy);
+    if (l * m * m > KAPPA_AMP_FF) kappa_amp_ff_term(G, l, y, vx, vy);
+    else g += l * fmaf(vx, fmaf(2.0f, y.x, -vx), vy * fmaf(2.0f, y.y, -vy));
+    q = fmaf(l, fmaf(hc.x, hc.x, hc.y * hc.y), q);
+}
+
 template <int NC>
 __device__ inline void kappa_amp_terms(const float2* yt, const float2* il, const float2 (&h)[NC], float2 u,
                                        double& dyd, float& gg) {
@@ -72,19 +82,8 @@ __device__ inline void kappa_amp_terms(const float2* yt, const float2* il, const
     ff G{0.f, 0.f};
     #pragma unroll
     for (int c = 0; c < NC; ++c) {
-        const float2 y = yt[c];
-        const float l = il[c].x;
-        const float vx = fmaf(u.x, h[c].x, u.y * h[c].y);     // v = u conj(h)
-        const float vy = fmaf(u.y, h[c].x, -(u.x * h[c].y));
-        const float m = fabsf(y.x) + fabsf(y.y) + fabsf(vx) + fabsf(vy);
-        if (l * m * m > KAPPA_AMP_FF) {
-            kappa_amp_ff_term(G, l, y, vx, vy);
-        } else {
-            const float t = l * fmaf(vx, fmaf(2.0f, y.x, -vx), vy * fmaf(2.0f, y.y, -vy));
-            if (c & 1) g1 += t; else g0 += t;
-        }
-        const float m2 = fmaf(h[c].x, h[c].x, h[c].y * h[c].y);
-        if (c & 1) q1 = fmaf(l, m2, q1); else q0 = fmaf(l, m2, q0);
+        if (c & 1) kappa_amp_col(G, g1, q1, yt[c], il[c].x, h[c], u);
+        else       kappa_amp_col(G, g0, q0, yt[c], il[c].x, h[c], u);
     }
     dyd = (double)G.hi + (double)G.lo + (double)(g0 + g1);
     gg = q0 + q1;
@@ -612,9 +611,41 @@ __global__ void __launch_bounds__(128 * NT, NT == 1 ? 2 : 1) k_kappa_tc(DevGeom 
             const float den = alpha + iq;
             tf = make_float2((pr.x * ieb + af.x * iq) / den, (pr.y * ieb + af.y * iq) / den);
         }
-        double dyd;   // amplitude terms in the eigenbasis (kappa_amp_terms)
+        // amplitude terms in the eigenbasis (kappa_amp_terms), h read again from the pass-1
+        // accumulators in TMEM eight columns at a time (summed as the read-back above summed
+        // them): a rolled loop keeps the per-column code out of the instruction cache's way
+        double dyd;
         float gg;
-        kappa_amp_terms<NC>(y0s, dls, h, make_float2(tf.x * ieb, tf.y * ieb), dyd, gg);
+        {
+            const float2 u = make_float2(tf.x * ieb, tf.y * ieb);
+            float g0 = 0.f, g1 = 0.f, q0 = 0.f, q1 = 0.f;
+            ff G{0.f, 0.f};
+            #pragma unroll 1
+            for (int c0 = 0; c0 < 64; c0 += 8) {
+                uint32_t a[8], b[8];
+                float hx[8], hy[8];
+                tc::tmem_ld8(tlane + (uint32_t)c0, a);
+                if (Nf > 1) tc::tmem_ld8(tlane + (uint32_t)(128 + c0), b);
+                tc::tmem_ld_wait();
+                #pragma unroll
+                for (int i = 0; i < 8; ++i) hx[i] = Nf > 1 ? __uint_as_float(a[i]) + __uint_as_float(b[i]) : __uint_as_float(a[i]);
+                tc::tmem_ld8(tlane + (uint32_t)(64 + c0), a);
+                if (Nf > 1) tc::tmem_ld8(tlane + (uint32_t)(192 + c0), b);
+                tc::tmem_ld_wait();
+                #pragma unroll
+                for (int i = 0; i < 8; ++i) hy[i] = Nf > 1 ? __uint_as_float(a[i]) + __uint_as_float(b[i]) : __uint_as_float(a[i]);
+                #pragma unroll
+                for (int i = 0; i < 8; ++i) {
+                    const int c = c0 + i;
+                    if (c < NC) {   // column 63 holds psi^H r0
+                        if (i & 1) kappa_amp_col(G, g1, q1, y0s[c], dls[c].x, make_float2(hx[i], hy[i]), u);
+                        else       kappa_amp_col(G, g0, q0, y0s[c], dls[c].x, make_float2(hx[i], hy[i]), u);
+                    }
+                }
+            }
+            dyd = (double)G.hi + (double)G.lo + (double)(g0 + g1);
+            gg = q0 + q1;
+        }
         // ---- pass 2: V V^H psi per group of frequencies, then the element-wise residual
         ff rr{0.f, 0.f};
         float pn = 0.f;
