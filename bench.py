@@ -51,13 +51,14 @@ def kappa_flops(P, S, J, Nz):
 
 def kappa_tc_used(g, S):
     """Whether the PF likelihood runs on the tensor cores (k_kappa_tc): 64 basis columns
-    (S > 32), 2 My Mz in {8, 16, 32}, at most 16 frequencies and its shared memory within
-    227 KB."""
+    (S > 32), 2 My Mz in {8, 16, 32} and its shared memory within 227 KB (the frequency
+    factors are kept in shared memory up to 16 frequencies, formed when used above)."""
     Nm = g.My * g.Mz
-    if S <= 32 or 2 * Nm not in (8, 16, 32) or g.Nf > 16:
+    if S <= 32 or 2 * Nm not in (8, 16, 32):
         return False
-    rf = max(4 * 128 * 2 * Nm, 2 * 128 * 32 + 2 * 64 * 32)   # one 128-particle tile per block
-    smem = rf * 4 + 32 + g.Nz * 16 + 128 * 8 + (g.Nf + g.My + g.Mz) * 128 * 8
+    rf = max(4 * 128 * 32, 2 * 128 * 32 + 2 * 2 * 64 * 32)   # one 128-particle tile per block
+    nf = g.Nf if g.Nf <= 16 else 0
+    smem = rf * 4 + 32 + g.Nz * 16 + 128 * 8 + (nf + g.My + g.Mz) * 128 * 8
     return smem <= 227 * 1024
 
 

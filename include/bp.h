@@ -252,7 +252,7 @@ bp_status bp_get_profile(bp_handle* h, double* ms, int n);
  *   kappa_fch     frequencies of V staged in shared memory per chunk (the Nz
  *                 tile), clamped to what fits.
  *   kappa_tc      1: the tensor-core PF likelihood wherever the shape allows it
- *                 (64 basis columns, 2 My Mz in {8, 16, 32}, Nf <= 16);
+ *                 (64 basis columns, 2 My Mz in {8, 16, 32});
  *                 -1: never.
  *   table_chunk   particles per shared-memory chunk of the message table: 16,
  *                 32, 64 or 128 (clamped to what fits; built-in 64).

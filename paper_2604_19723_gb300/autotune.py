@@ -72,8 +72,8 @@ def basis_stride(S_max: int) -> int:
 
 def tensor_core_shape(geom, S_max: int) -> bool:
     """Whether the tensor-core PF likelihood applies to this shape (64 basis columns,
-    2 My Mz in {8, 16, 32}, at most 16 frequencies)."""
-    return basis_stride(S_max) == 64 and 2 * geom.My * geom.Mz in (8, 16, 32) and geom.Nf <= 16
+    2 My Mz in {8, 16, 32})."""
+    return basis_stride(S_max) == 64 and 2 * geom.My * geom.Mz in (8, 16, 32)
 
 
 def kappa_candidates(S: int, S_max: int, geom) -> List[Dict[str, int]]:

@@ -87,18 +87,26 @@ __device__ inline void array_factors(const DevGeom& G, float4 g, float2 gl, floa
         az[m * stride] = cispi_ff(2.0f * p, 2.0f * e);
     }
 }
-__device__ inline float2 factors_from_geo(const DevGeom& G, float4 g, float2 gl, float2* b, float2* ay, float2* az, int stride) {
+// the amplitude and carrier factor A e^{-i 2 pi d / lambda} of the steering vector
+__device__ inline float2 carrier_factor(const DevGeom& G, float4 g) {
     const float d = g.x + g.y;
     const float A = G.amp_c / d;
     float h, l;
     ff_frac_mul2(g.x, g.y, G.inv_lam_hi, G.inv_lam_lo, h, l);
     const float2 c = cispi_ff(-2.0f * h, -2.0f * l);
-    for (int f = 0; f < G.Nf; ++f) {
-        ff_frac_mul2(g.x, g.y, G.fc_hi[f], G.fc_lo[f], h, l);
-        b[f * stride] = cispi_ff(-2.0f * h, -2.0f * l);
-    }
-    array_factors(G, g, gl, ay, az, stride);
     return make_float2(A * c.x, A * c.y);
+}
+// frequency factor b_f = e^{-i 2 pi d f_f / c}
+__device__ inline float2 freq_factor(const DevGeom& G, float4 g, int f) {
+    float h, l;
+    ff_frac_mul2(g.x, g.y, G.fc_hi[f], G.fc_lo[f], h, l);
+    return cispi_ff(-2.0f * h, -2.0f * l);
+}
+__device__ inline float2 factors_from_geo(const DevGeom& G, float4 g, float2 gl, float2* b, float2* ay, float2* az, int stride) {
+    const float2 Fc = carrier_factor(G, g);
+    for (int f = 0; f < G.Nf; ++f) b[f * stride] = freq_factor(G, g, f);
+    array_factors(G, g, gl, ay, az, stride);
+    return Fc;
 }
 
 // As factors_from_geo, with the carrier phase folded into the frequency factor:

@@ -384,10 +384,22 @@ __host__ __device__ inline int kappa_tc_groups(int Nf, int Nm) {
     return (Nf + kappa_tc_group_freqs(Nm) - 1) / kappa_tc_group_freqs(Nm);
 }
 __host__ __device__ inline int round16(int x) { return (x + 15) & ~15; }
-// operand region in floats: pass 1 A [NT][hi, lo][128 x KC] and one B slot [hi, lo][128 x KC];
+// Pass 1 takes KAPPA_TC_KR real K per round: KR / (2 My Mz) frequencies.  Its two
+// accumulators alternate by round; every KAPPA_TC_SEG rounds of one (five when a round is
+// one frequency of the 4 x 4 URA, as validated at full size; else two, i.e. 24 MMA
+// accumulations, the chain that stayed within 1e-4) it is added into registers and
+// restarted.  Above KAPPA_TC_FLY_NF frequencies the frequency factors are formed when
+// used instead of being kept in shared memory.
+constexpr int KAPPA_TC_KR = 32;
+constexpr int KAPPA_TC_FLY_NF = 16;
+__host__ __device__ inline int kappa_tc_f1(int Nm) { return KAPPA_TC_KR / (2 * Nm); }
+__host__ __device__ inline int kappa_tc_r1(int Nf, int Nm) { return (Nf + kappa_tc_f1(Nm) - 1) / kappa_tc_f1(Nm); }
+__host__ __device__ inline int kappa_tc_seg(int Nm) { return 2 * Nm == KAPPA_TC_KR ? 5 : 2; }
+// operand region in floats: pass 1 A [NT][hi, lo][128 x KR] and one B slot [hi, lo][128 x KR];
 // pass 2 A [NT][hi, lo][128 x KC2] and two B slots [hi, lo][64 x KC2]
 __host__ __device__ inline int kappa_tc_region_floats(int KC, int NT) {
-    const int r1 = (2 * NT + 2) * 128 * KC, r2 = 2 * NT * 128 * KAPPA_TC_KC2 + 2 * 2 * KAPPA_TC_N2 * KAPPA_TC_KC2;
+    (void)KC;
+    const int r1 = (2 * NT + 2) * 128 * KAPPA_TC_KR, r2 = 2 * NT * 128 * KAPPA_TC_KC2 + 2 * 2 * KAPPA_TC_N2 * KAPPA_TC_KC2;
     return r1 > r2 ? r1 : r2;
 }
 
@@ -403,6 +415,9 @@ __global__ void __launch_bounds__(128 * NT, NT == 1 ? 2 : 1) k_kappa_tc(DevGeom 
     const int s = blockIdx.y;
     const int P = Pm.P, J = G.J, Nz = G.Nz, Nm = G.My * G.Mz, Nf = G.Nf;
     const int KC = 2 * Nm;                                     // pass-1 real K per frequency
+    constexpr int KR = KAPPA_TC_KR;                            // pass-1 real K per round
+    const int F1 = kappa_tc_f1(Nm), R1 = kappa_tc_r1(Nf, Nm), SEG = kappa_tc_seg(Nm);
+    const bool fly = Nf > KAPPA_TC_FLY_NF;                     // frequency factors formed when used
     const int GF = kappa_tc_group_freqs(Nm), NG = kappa_tc_groups(Nf, Nm);
     const int RF = kappa_tc_region_floats(KC, NT);            // operand region (floats)
     float* sR = reinterpret_cast<float*>(sm4);
@@ -425,14 +440,14 @@ __global__ void __launch_bounds__(128 * NT, NT == 1 ? 2 : 1) k_kappa_tc(DevGeom 
     tc::fence_before_sync();
     __syncthreads();
     tc::fence_after_sync();
-    // B operand stream (thread 0): pass 1 takes one slot of 2 x 128 x KC floats at
-    // sR + 2 NT 128 KC; pass 2 two slots of 2 x 64 x KC2 floats after its A tiles, so that
+    // B operand stream (thread 0): pass 1 takes one slot of 2 x 128 x KR floats at
+    // sR + 2 NT 128 KR; pass 2 two slots of 2 x 64 x KC2 floats after its A tiles, so that
     // the copy of the next round's B runs under this round's MMAs.  A copy into a slot is
     // issued only once the MMAs that read the slot's previous contents have completed.
-    const size_t bchunk1 = (size_t)2 * 128 * KC;
+    const size_t bchunk1 = (size_t)2 * 128 * KR;
     const size_t bslot2 = (size_t)2 * KAPPA_TC_N2 * KC2;
     const int NQ = 4 * NG;   // pass-2 rounds per j
-    float* sB1 = sR + 2 * NT * 128 * KC;
+    float* sB1 = sR + 2 * NT * 128 * KR;
     float* sB2 = sR + 2 * NT * 128 * KC2;
     auto issueB = [&](int sl, float* dst, const float* src, uint32_t bytes) {
         if (tid != 0 || bad) return;
@@ -448,7 +463,7 @@ __global__ void __launch_bounds__(128 * NT, NT == 1 ? 2 : 1) k_kappa_tc(DevGeom 
         b_pend &= ~(1u << sl);
         return true;
     };
-    auto b1_src = [&](int j, int f) { return Bt1 + (((size_t)s * J + j) * Nf + f) * bchunk1; };
+    auto b1_src = [&](int j, int r) { return Bt1 + (((size_t)s * J + j) * R1 + r) * bchunk1; };
     auto b2_src = [&](int j, int q) { return Bt2 + (((size_t)s * J + j) * NQ + q) * bslot2; };
     auto b2_bytes = [&](int q) {
         const int g = q >> 2, nk = min(GF, Nf - g * GF) * Nm;
@@ -522,36 +537,86 @@ __global__ void __launch_bounds__(128 * NT, NT == 1 ? 2 : 1) k_kappa_tc(DevGeom 
         const double ieb64 = 1.0 / eb;
         const double zeta = D.zeta[s * J + j];
         const double J0r = D.kJ0[s * J + j];
-        float2* fb = fac + tid;
-        float2* fy = fb + Nf * KT;
+        float2* fb = fac + tid;                                // [Nf][KT] unless fly
+        float2* fy = fb + (fly ? 0 : Nf) * KT;
         float2* fz = fy + G.My * KT;
-        const float2 Fc = factors_from_geo(G, geo_s[(size_t)j * P + pp], geol_s[(size_t)j * P + pp], fb, fy, fz, KT);
-        // ---- pass 1: h = psi^H V, pr = psi^H r0
+        const float4 grec = geo_s[(size_t)j * P + pp];
+        float2 Fc;
+        if (fly) {
+            Fc = carrier_factor(G, grec);
+            array_factors(G, grec, geol_s[(size_t)j * P + pp], fy, fz, KT);
+        } else {
+            Fc = factors_from_geo(G, grec, geol_s[(size_t)j * P + pp], fb, fy, fz, KT);
+        }
+        // b_f as pass 1 and pass 2 both take it (the shared copy holds the same values)
+        auto bfac = [&](int f) { return fly ? freq_factor(G, grec, f) : fb[f * KT]; };
+        // h = psi^H V and pr = psi^H r0, summed over the pass-1 accumulator segments
+        float2 h[NC];
+        float2 pr = make_float2(0.f, 0.f);
+        #pragma unroll
+        for (int c = 0; c < NC; ++c) h[c] = make_float2(0.f, 0.f);
+        // adds the pass-1 accumulator at TMEM column base (128 columns: Re h 0..62, Re pr,
+        // Im h 0..62, Im pr) into h and pr
+        auto absorb = [&](uint32_t base) {
+            uint32_t v[32];
+            tc::tmem_ld32(tlane + base + 0, v); tc::tmem_ld_wait();
+            #pragma unroll
+            for (int i = 0; i < 32; ++i) h[i].x += __uint_as_float(v[i]);
+            tc::tmem_ld32(tlane + base + 32, v); tc::tmem_ld_wait();
+            #pragma unroll
+            for (int i = 0; i < 31; ++i) h[32 + i].x += __uint_as_float(v[i]);
+            pr.x += __uint_as_float(v[31]);
+            tc::tmem_ld32(tlane + base + 64, v); tc::tmem_ld_wait();
+            #pragma unroll
+            for (int i = 0; i < 32; ++i) h[i].y += __uint_as_float(v[i]);
+            tc::tmem_ld32(tlane + base + 96, v); tc::tmem_ld_wait();
+            #pragma unroll
+            for (int i = 0; i < 31; ++i) h[32 + i].y += __uint_as_float(v[i]);
+            pr.y += __uint_as_float(v[31]);
+        };
+        // ---- pass 1: h = psi^H V, pr = psi^H r0, F1 frequencies per round
         float nps = 0.f;
         {
             float* sA = sR;
-            float* aHi = sA + (size_t)(tile * 2 + 0) * 128 * KC;
-            float* aLo = sA + (size_t)(tile * 2 + 1) * 128 * KC;
+            float* aHi = sA + (size_t)(tile * 2 + 0) * 128 * KR;
+            float* aLo = sA + (size_t)(tile * 2 + 1) * 128 * KR;
             const uint32_t idesc = tc::idesc_tf32_f32(128, 128);
-            // even frequencies accumulate in columns 0..127, odd ones in 128..255 (shorter
-            // FP32 accumulation chains; added when h is read back); the first frequency's B
-            // was issued before this j began
-            for (int f = 0; f < Nf; ++f) {
-                round(0, sA, sB1, KC, (uint32_t)(128 * KC * 4), idesc, (uint32_t)((f & 1) * 128), f > 1,
-                      [&]() { if (f > 0) issueB(0, sB1, b1_src(j, f), (uint32_t)(bchunk1 * 4)); }, [&]() {
-                    const float2 cb = cmul(Fc, fb[f * KT]);
-                    for (int y = 0; y < G.My; ++y) {
-                        const float2 w = cmul(cb, fy[y * KT]);
-                        for (int m = 0; m < G.Mz; m += 2) {
-                            const float2 p0 = cmul(w, fz[m * KT]), p1 = cmul(w, fz[(m + 1) * KT]);
-                            nps += p0.x * p0.x + p0.y * p0.y + p1.x * p1.x + p1.y * p1.y;
-                            const float4 hi = make_float4(tc::tf32_rn(p0.x), tc::tf32_rn(p0.y), tc::tf32_rn(p1.x),
-                                                          tc::tf32_rn(p1.y));
-                            const float4 lo = make_float4(tc::tf32_rn(p0.x - hi.x), tc::tf32_rn(p0.y - hi.y),
-                                                          tc::tf32_rn(p1.x - hi.z), tc::tf32_rn(p1.y - hi.w));
-                            const int off = tc::core_off(row, 2 * (y * G.Mz + m), KC) >> 2;
-                            *reinterpret_cast<float4*>(aHi + off) = hi;
-                            *reinterpret_cast<float4*>(aLo + off) = lo;
+            // even rounds accumulate in columns 0..127, odd ones in 128..255; a segment of SEG
+            // rounds of one accumulator is added into h (after the MMAs of the previous round
+            // are done, before this round overwrites it); the first round's B was issued
+            // before this j began
+            for (int r = 0; r < R1; ++r) {
+                const int q = r & 1;
+                const bool seg_start = ((r >> 1) % SEG) == 0;
+                round(0, sA, sB1, KR, (uint32_t)(128 * KR * 4), idesc, (uint32_t)(q * 128), !seg_start,
+                      [&]() {
+                    if (seg_start && r >= 2) absorb((uint32_t)(q * 128));
+                    if (r > 0) issueB(0, sB1, b1_src(j, r), (uint32_t)(bchunk1 * 4));
+                }, [&]() {
+                    for (int i = 0; i < F1; ++i) {
+                        const int f = r * F1 + i;
+                        if (f >= Nf) {   // past the last frequency: zero operands
+                            for (int kk = i * KC; kk < (i + 1) * KC; kk += 4) {
+                                const int off = tc::core_off(row, kk, KR) >> 2;
+                                *reinterpret_cast<float4*>(aHi + off) = make_float4(0.f, 0.f, 0.f, 0.f);
+                                *reinterpret_cast<float4*>(aLo + off) = make_float4(0.f, 0.f, 0.f, 0.f);
+                            }
+                            continue;
+                        }
+                        const float2 cb = cmul(Fc, bfac(f));
+                        for (int y = 0; y < G.My; ++y) {
+                            const float2 w = cmul(cb, fy[y * KT]);
+                            for (int m = 0; m < G.Mz; m += 2) {
+                                const float2 p0 = cmul(w, fz[m * KT]), p1 = cmul(w, fz[(m + 1) * KT]);
+                                nps += p0.x * p0.x + p0.y * p0.y + p1.x * p1.x + p1.y * p1.y;
+                                const float4 hi = make_float4(tc::tf32_rn(p0.x), tc::tf32_rn(p0.y), tc::tf32_rn(p1.x),
+                                                              tc::tf32_rn(p1.y));
+                                const float4 lo = make_float4(tc::tf32_rn(p0.x - hi.x), tc::tf32_rn(p0.y - hi.y),
+                                                              tc::tf32_rn(p1.x - hi.z), tc::tf32_rn(p1.y - hi.w));
+                                const int off = tc::core_off(row, i * KC + 2 * (y * G.Mz + m), KR) >> 2;
+                                *reinterpret_cast<float4*>(aHi + off) = hi;
+                                *reinterpret_cast<float4*>(aLo + off) = lo;
+                            }
                         }
                     }
                 });
@@ -561,40 +626,25 @@ __global__ void __launch_bounds__(128 * NT, NT == 1 ? 2 : 1) k_kappa_tc(DevGeom 
         // pass 2's first two B tiles, under the read-back of h and the amplitude sums
         issueB(0, sB2, b2_src(j, 0), b2_bytes(0));
         issueB(1, sB2 + bslot2, b2_src(j, 1), b2_bytes(1));
-        float2 h[NC];
-        float2 pr;
-        {
+        absorb(0);                       // the segments still in TMEM
+        if (R1 > 1) absorb(128);
+        {   // h and pr back into columns 0..127, where the amplitude loop reads them
             uint32_t v[32];
-            tc::tmem_ld32(tlane + 0, v); tc::tmem_ld_wait();
             #pragma unroll
-            for (int i = 0; i < 32; ++i) h[i].x = __uint_as_float(v[i]);
-            tc::tmem_ld32(tlane + 32, v); tc::tmem_ld_wait();
+            for (int i = 0; i < 32; ++i) v[i] = __float_as_uint(h[i].x);
+            tc::tmem_st32(tlane + 0, v);
             #pragma unroll
-            for (int i = 0; i < 31; ++i) h[32 + i].x = __uint_as_float(v[i]);
-            pr.x = __uint_as_float(v[31]);
-            tc::tmem_ld32(tlane + 64, v); tc::tmem_ld_wait();
+            for (int i = 0; i < 31; ++i) v[i] = __float_as_uint(h[32 + i].x);
+            v[31] = __float_as_uint(pr.x);
+            tc::tmem_st32(tlane + 32, v);
             #pragma unroll
-            for (int i = 0; i < 32; ++i) h[i].y = __uint_as_float(v[i]);
-            tc::tmem_ld32(tlane + 96, v); tc::tmem_ld_wait();
+            for (int i = 0; i < 32; ++i) v[i] = __float_as_uint(h[i].y);
+            tc::tmem_st32(tlane + 64, v);
             #pragma unroll
-            for (int i = 0; i < 31; ++i) h[32 + i].y = __uint_as_float(v[i]);
-            pr.y = __uint_as_float(v[31]);
-            if (Nf > 1) {   // the odd frequencies' accumulator
-                tc::tmem_ld32(tlane + 128, v); tc::tmem_ld_wait();
-                #pragma unroll
-                for (int i = 0; i < 32; ++i) h[i].x += __uint_as_float(v[i]);
-                tc::tmem_ld32(tlane + 160, v); tc::tmem_ld_wait();
-                #pragma unroll
-                for (int i = 0; i < 31; ++i) h[32 + i].x += __uint_as_float(v[i]);
-                pr.x += __uint_as_float(v[31]);
-                tc::tmem_ld32(tlane + 192, v); tc::tmem_ld_wait();
-                #pragma unroll
-                for (int i = 0; i < 32; ++i) h[i].y += __uint_as_float(v[i]);
-                tc::tmem_ld32(tlane + 224, v); tc::tmem_ld_wait();
-                #pragma unroll
-                for (int i = 0; i < 31; ++i) h[32 + i].y += __uint_as_float(v[i]);
-                pr.y += __uint_as_float(v[31]);
-            }
+            for (int i = 0; i < 31; ++i) v[i] = __float_as_uint(h[32 + i].y);
+            v[31] = __float_as_uint(pr.y);
+            tc::tmem_st32(tlane + 96, v);
+            tc::tmem_st_wait();
         }
         // tau (FP32; J is evaluated exactly at the tau used) and the O(S) amplitude sums
         float hh = 0.f;
@@ -611,9 +661,9 @@ __global__ void __launch_bounds__(128 * NT, NT == 1 ? 2 : 1) k_kappa_tc(DevGeom 
             const float den = alpha + iq;
             tf = make_float2((pr.x * ieb + af.x * iq) / den, (pr.y * ieb + af.y * iq) / den);
         }
-        // amplitude terms in the eigenbasis (kappa_amp_terms), h read again from the pass-1
-        // accumulators in TMEM eight columns at a time (summed as the read-back above summed
-        // them): a rolled loop keeps the per-column code out of the instruction cache's way
+        // amplitude terms in the eigenbasis (kappa_amp_terms), h read again from TMEM columns
+        // 0..127 (written back above) eight columns at a time: a rolled loop keeps the
+        // per-column code out of the instruction cache's way
         double dyd;
         float gg;
         {
@@ -625,15 +675,10 @@ __global__ void __launch_bounds__(128 * NT, NT == 1 ? 2 : 1) k_kappa_tc(DevGeom 
                 uint32_t a[8], b[8];
                 float hx[8], hy[8];
                 tc::tmem_ld8(tlane + (uint32_t)c0, a);
-                if (Nf > 1) tc::tmem_ld8(tlane + (uint32_t)(128 + c0), b);
+                tc::tmem_ld8(tlane + (uint32_t)(64 + c0), b);
                 tc::tmem_ld_wait();
                 #pragma unroll
-                for (int i = 0; i < 8; ++i) hx[i] = Nf > 1 ? __uint_as_float(a[i]) + __uint_as_float(b[i]) : __uint_as_float(a[i]);
-                tc::tmem_ld8(tlane + (uint32_t)(64 + c0), a);
-                if (Nf > 1) tc::tmem_ld8(tlane + (uint32_t)(192 + c0), b);
-                tc::tmem_ld_wait();
-                #pragma unroll
-                for (int i = 0; i < 8; ++i) hy[i] = Nf > 1 ? __uint_as_float(a[i]) + __uint_as_float(b[i]) : __uint_as_float(a[i]);
+                for (int i = 0; i < 8; ++i) { hx[i] = __uint_as_float(a[i]); hy[i] = __uint_as_float(b[i]); }
                 #pragma unroll
                 for (int i = 0; i < 8; ++i) {
                     const int c = c0 + i;
@@ -686,7 +731,7 @@ __global__ void __launch_bounds__(128 * NT, NT == 1 ? 2 : 1) k_kappa_tc(DevGeom 
             if (g == NG - 1 && j + 1 < J) issueB(0, sB1, b1_src(j + 1, 0), (uint32_t)(bchunk1 * 4));
             // element (f, y, m) of the group walked in order; w = Fc b_f a_y formed as pass 1 formed it
             int cf = f0, cy = 0, cm = 0;
-            float2 w = cmul(cmul(Fc, fb[f0 * KT]), fy[0]);
+            float2 w = cmul(cmul(Fc, bfac(f0)), fy[0]);
             for (int b = 0; b < nk; b += 8) {
                 // the four chunk accumulators, added pairwise: (a0 + a1) + (a2 + a3)
                 float vre[8], vim[8];
@@ -722,7 +767,7 @@ __global__ void __launch_bounds__(128 * NT, NT == 1 ? 2 : 1) k_kappa_tc(DevGeom 
                     if (++cm == G.Mz) {
                         cm = 0;
                         if (++cy == G.My) { cy = 0; ++cf; }
-                        if (kl + 1 < nk) w = cmul(cmul(Fc, fb[cf * KT]), fy[cy * KT]);
+                        if (kl + 1 < nk) w = cmul(cmul(Fc, bfac(cf)), fy[cy * KT]);
                     }
                     const float vsx = vre[i], vsy = vim[i];
                     const float2 pp2 = make_float2(ps.x - vsx * ieb, ps.y - vsy * ieb);
@@ -1434,24 +1479,28 @@ __global__ void k_nu(DevGeom G, DevParams Pm, DevState D, int S) {
     D.lw_eta[(size_t)j * P + p] = lnu;
 }
 
-// B tiles of the tensor-core pass 1, once per (s, j, frequency): rows n of
+// B tiles of the tensor-core pass 1, once per (s, j, round r of F1 frequencies): rows n of
 // [[Re V, Im V], [Im V, -Re V]]^T (n < 64: Re h_n, n >= 64: Im h_{n-64}) against the real
-// K index 2e + part of the frequency's elements e (part 0 = Re psi, 1 = Im psi), split into
-// TF32 high and low parts, in the K-major core-matrix layout; [hi, lo] per chunk.
+// K index KC i + 2e + part of the round's frequency i and its elements e (part 0 = Re psi,
+// 1 = Im psi; zero past the last frequency), split into TF32 high and low parts, in the
+// K-major core-matrix layout; [hi, lo] per round.
 __global__ void k_kappa_btile(DevGeom G, DevState D, int SCA, float* __restrict__ Bt) {
-    const int s = blockIdx.x, j = blockIdx.y, f = blockIdx.z;
+    constexpr int KR = KAPPA_TC_KR;
+    const int s = blockIdx.x, j = blockIdx.y, r = blockIdx.z;
     const int J = G.J, Nz = G.Nz, Nm = G.My * G.Mz, KC = 2 * Nm;
+    const int F1 = kappa_tc_f1(Nm), R1 = kappa_tc_r1(G.Nf, Nm);
     const float2* V = D.kV + ((size_t)s * J + j) * Nz * SCA;
-    float* out = Bt + (((size_t)s * J + j) * G.Nf + f) * 2 * 128 * KC;
-    for (int t = threadIdx.x; t < 128 * KC; t += blockDim.x) {
-        const int n = t / KC, kk = t - n * KC;
-        const int e = kk >> 1, part = kk & 1;
-        const float2 v = V[(size_t)(f * Nm + e) * SCA + (n & 63)];
+    float* out = Bt + (((size_t)s * J + j) * R1 + r) * 2 * 128 * KR;
+    for (int t = threadIdx.x; t < 128 * KR; t += blockDim.x) {
+        const int n = t / KR, kk = t - n * KR;
+        const int i = kk / KC, kk2 = kk - i * KC, f = r * F1 + i;
+        const int e = kk2 >> 1, part = kk2 & 1;
+        const float2 v = (f < G.Nf) ? V[(size_t)(f * Nm + e) * SCA + (n & 63)] : make_float2(0.f, 0.f);
         const float b = (n < 64) ? (part == 0 ? v.x : v.y) : (part == 0 ? v.y : -v.x);
         const float hi = tc::tf32_rn(b);
-        const int off = tc::core_off(n, kk, KC) >> 2;
+        const int off = tc::core_off(n, kk, KR) >> 2;
         out[off] = hi;
-        out[128 * KC + off] = tc::tf32_rn(b - hi);
+        out[128 * KR + off] = tc::tf32_rn(b - hi);
     }
 }
 
@@ -1488,25 +1537,23 @@ __global__ void k_kappa_btile2(DevGeom G, DevState D, int SCA, float* __restrict
 // r0 (hi, lo) per element, 1/lambda_c and y~0_c, and the factors of 256 particles
 constexpr int KAPPA_TC_NT = 1;   // M tiles per block of the launched variant
 static size_t kappa_tc_smem(const DevGeom& G, int NT = KAPPA_TC_NT) {
-    const size_t Nm = (size_t)G.My * G.Mz, nfac = (size_t)G.Nf + G.My + G.Mz;
+    const size_t Nm = (size_t)G.My * G.Mz;
+    const size_t nfac = (size_t)(G.Nf > KAPPA_TC_FLY_NF ? 0 : G.Nf) + G.My + G.Mz;
     const size_t rf = (size_t)kappa_tc_region_floats(2 * (int)Nm, NT);
     return rf * sizeof(float) + 32 + (size_t)G.Nz * sizeof(float4) + 128 * sizeof(float2) +
            nfac * 128 * NT * sizeof(float2);
 }
-// The tensor-core variant applies with 64 basis columns (SCA = 64), 2 My Mz in {8, 16, 32},
-// at most KAPPA_TC_MAX_NF frequencies and its shared memory within the opt-in limit.  The
-// tensor core adds each MMA's result into its FP32 accumulator (no FMA chain): with 75
-// frequencies in one pass-1 accumulator (225 accumulations) the PF weights moved by
-// 1.7e-4 (measured); two accumulators over at most 16 frequencies keep each chain at 24,
-// below the 30 that stayed within 1e-4 at full size.
-constexpr int KAPPA_TC_MAX_NF = 16;
+// The tensor-core variant applies with 64 basis columns (SCA = 64), 2 My Mz in {8, 16, 32}
+// and its shared memory within the opt-in limit.  The tensor core adds each MMA's result
+// into its FP32 accumulator (no FMA chain): with 75 frequencies of the 2 x 2 URA in one
+// pass-1 accumulator (225 accumulations) the PF weights moved by 1.7e-4 (measured), with 24
+// they stayed within 1e-4; hence the segments of KAPPA_TC_SEG rounds.
 bool kappa_tc_ok(const DevGeom& G, int SCA) {
     const int KC = 2 * G.My * G.Mz;
-    return SCA == 64 && (KC == 8 || KC == 16 || KC == 32) && G.Nf <= KAPPA_TC_MAX_NF &&
-           kappa_tc_smem(G) <= 227 * 1024;
+    return SCA == 64 && (KC == 8 || KC == 16 || KC == 32) && kappa_tc_smem(G) <= 227 * 1024;
 }
 static size_t kappa_btile1_floats(const DevGeom& G, int S_max) {
-    return (size_t)S_max * G.J * G.Nf * 2 * 128 * (2 * G.My * G.Mz);
+    return (size_t)S_max * G.J * kappa_tc_r1(G.Nf, G.My * G.Mz) * 2 * 128 * KAPPA_TC_KR;
 }
 size_t kappa_btile_floats(const DevGeom& G, int S_max) {
     const int Nm = G.My * G.Mz;
@@ -1516,7 +1563,7 @@ size_t kappa_btile_floats(const DevGeom& G, int S_max) {
 int launch_kappa_btile(const DevGeom& G, const DevState& D, int S, int SCA, cudaStream_t st) {
     if (!D.kB || !kappa_tc_ok(G, SCA)) return 0;
     const int Nm = G.My * G.Mz;
-    k_kappa_btile<<<dim3(S, G.J, G.Nf), 256, 0, st>>>(G, D, SCA, D.kB);
+    k_kappa_btile<<<dim3(S, G.J, kappa_tc_r1(G.Nf, Nm)), 256, 0, st>>>(G, D, SCA, D.kB);
     k_kappa_btile2<<<dim3(S, G.J, kappa_tc_groups(G.Nf, Nm) * 4), 256, 0, st>>>(G, D, SCA,
                                                                                 D.kB + kappa_btile1_floats(G, S));
     return 2;

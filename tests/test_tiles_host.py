@@ -28,7 +28,7 @@ def test_kappa_candidates_hold_S_within_the_basis_stride():
 def test_tensor_core_shape_matches_the_kernel_rules():
     assert A.tensor_core_shape(W.make_geometry(J=4, Nf=10, My=4, Mz=4), 64)
     assert not A.tensor_core_shape(W.make_geometry(J=4, Nf=10, My=4, Mz=4), 32)     # stride 32
-    assert not A.tensor_core_shape(W.make_geometry(J=4, Nf=17, My=2, Mz=2), 64)     # Nf > 16
+    assert A.tensor_core_shape(W.make_geometry(J=4, Nf=75, My=2, Mz=2), 64)         # frequencies grouped
     assert not A.tensor_core_shape(W.make_geometry(J=4, Nf=10, My=8, Mz=8), 64)     # 2 My Mz = 128
     assert A.tensor_core_shape(W.make_geometry(J=4, Nf=16, My=2, Mz=2), 64)
 
