@@ -88,8 +88,8 @@ def iota_flops(P, S, J, Nf, My, Mz):
 # particle count it was taken at, and only while the kernel sources hash to the recorded
 # value.
 TRAFFIC_RECORDS = {
-    "k_kappa_tc": {"workload": "scale_64x100k", "P": 100000, "bytes": 873929216 + 50618368,
-                   "sources_sha256": "22c89609d08009e26757bdf82add7c304b0be579e5787e6a4c38b6d392418d43",
+    "k_kappa_tc": {"workload": "scale_64x100k", "P": 100000, "bytes": 873119232 + 50664448,
+                   "sources_sha256": "1110bf0b1cfc98075cd47b06617919570f7d65d3df893ff6bb438e748e463a97",
                    "how": "ncu --metrics dram__bytes_read.sum,dram__bytes_write.sum,gpu__time_duration.sum "
                           "--clock-control none -k regex:^k_kappa_tc$ -c 1 python bench.py --steps 2 "
                           "--warmup 1 --no-matched --no-cpu-baseline"},
