@@ -407,7 +407,8 @@ def run_gpu(args, rank, world):
             fc = kappa_contraction_flops(P, S, g.J, g.Nz)
             ac = fc / (ms * 1e-3) / 1e12
             r = {"bound": "tensor", "kernel": "k_kappa_tc (tcgen05 3xTF32, both contractions)", "achieved": ac,
-                 "peak": eff, "unit": "TFLOP/s", "frac": ac / eff, "traffic": traffic_for(name, args.workload, P),
+                 "peak": eff, "unit": "TFLOP/s", "frac": ac / eff,
+                 "traffic": traffic_for("k_kappa_tc", args.workload, P),
                  "ms_per_launch": ms,
                  "peak_basis": f"3xTF32 effective: MEASURED_PEAKS bf16_tflops_sustained {peaks.get('bf16_tflops_sustained')} "
                                f"x 1.1/2.25 (nominal TF32/BF16) / 3 products",

@@ -665,9 +665,7 @@ __global__ void __launch_bounds__(STAGE_THREADS) k_stage_kappa(DevGeom G, DevPar
     __syncthreads();
     // r0 = e0 - V y~0 (rows), |r0|^2; store V, r0 as FP32
     float2* kV = D.kV + ((size_t)s * J + j) * Nz * SC;
-    double* rr = red;   // reuse
-    if (threadIdx.x == 0) rr[0] = 0.0;
-    __syncthreads();
+    double r2 = 0.0;   // |r0|^2, summed in a fixed order (warps, then warp slots)
     for (int k = threadIdx.x; k < Nz; k += blockDim.x) {
         double2 e0 = E0[k];
         for (int c = 0; c < K; ++c) {
@@ -680,10 +678,16 @@ __global__ void __launch_bounds__(STAGE_THREADS) k_stage_kappa(DevGeom G, DevPar
         const float2 r0h = make_float2((float)e0.x, (float)e0.y);
         kV[(size_t)k * SC + SC - 1] = r0h;   // r0 in the last column, its low part apart
         D.kr0l[((size_t)s * J + j) * Nz + k] = make_float2((float)(e0.x - (double)r0h.x), (float)(e0.y - (double)r0h.y));
-        atomicAdd(&rr[0], e0.x * e0.x + e0.y * e0.y);
+        r2 += e0.x * e0.x + e0.y * e0.y;
     }
+    r2 = warp_sum_d(r2);
+    if (lane == 0) wred[wid] = r2;
     __syncthreads();
-    if (threadIdx.x == 0) D.kJ0[s * J + j] = rr[0] / eb;   // the |y|^2 part enters the particle kernel as a difference
+    if (threadIdx.x == 0) {   // the |y|^2 part enters the particle kernel as a difference
+        double v = 0.0;
+        for (int w = 0; w < nw; ++w) v += wred[w];
+        D.kJ0[s * J + j] = v / eb;
+    }
     // the particle kernels take y~0 = V^H e0/eb and 1/lambda_c (padded with zeros) and form
     // the amplitude terms sum_c (|y~0_c|^2 - |y~0_c - tau x_c/eb|^2)/lambda_c column by column
     float2* ky = D.ky0 + ((size_t)s * J + j) * SC;
