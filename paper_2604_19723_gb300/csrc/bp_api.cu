@@ -68,8 +68,16 @@ void fill_geom(DevGeom& G, const bp_geometry* g) {
     G.J = g->J; G.Nf = g->Nf; G.My = g->My; G.Mz = g->Mz; G.Nz = g->Nf * g->My * g->Mz;
     G.fc = g->fc; G.c = g->c; G.B = g->B; G.lam = g->c / g->fc;
     for (int j = 0; j < g->J; ++j) {
-        for (int k = 0; k < 3; ++k) G.p_pa[j][k] = g->p_pa[3 * j + k];
-        for (int k = 0; k < 9; ++k) G.R[j][k] = g->R_pa[9 * j + k];
+        for (int k = 0; k < 3; ++k) {
+            G.p_pa[j][k] = g->p_pa[3 * j + k];
+            G.pa_h[j][k] = (float)G.p_pa[j][k];
+            G.pa_l[j][k] = (float)(G.p_pa[j][k] - (double)G.pa_h[j][k]);
+        }
+        for (int k = 0; k < 9; ++k) {
+            G.R[j][k] = g->R_pa[9 * j + k];
+            G.R_h[j][k] = (float)G.R[j][k];
+            G.R_l[j][k] = (float)(G.R[j][k] - (double)G.R_h[j][k]);
+        }
     }
     for (int f = 0; f < g->Nf; ++f) G.f[f] = (g->Nf == 1) ? 0.0 : -0.5 * g->B + f * (g->B / (g->Nf - 1));
     for (int y = 0; y < g->My; ++y) G.py[y] = g->p_y[y];

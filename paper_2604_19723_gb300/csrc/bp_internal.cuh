@@ -30,6 +30,9 @@ struct DevGeom {
     float py_l[MY_MAX], pz_l[MZ_MAX];     // p_y / lambda, p_z / lambda (float-float with *_lo)
     float py_lo[MY_MAX], pz_lo[MZ_MAX];
     float amp_c;             // lambda / (4 pi)
+    // the PA positions and rotations as FP32 pairs (hi + lo), for the float-float geometry
+    float pa_h[J_MAX][3], pa_l[J_MAX][3];
+    float R_h[J_MAX][9], R_l[J_MAX][9];
 };
 
 struct DevParams {
