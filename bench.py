@@ -49,23 +49,21 @@ def kappa_flops(P, S, J, Nz):
     return float(P) * S * J * per
 
 
-def kappa_tc_used(g, S):
-    """Whether the PF likelihood runs on the tensor cores (k_kappa_tc): 64 basis columns
-    (S > 32), 2 My Mz in {8, 16, 32} and its shared memory within 227 KB (the frequency
-    factors are kept in shared memory up to 16 frequencies, formed when used above)."""
-    Nm = g.My * g.Mz
-    if S <= 32 or 2 * Nm not in (8, 16, 32):
+def kappa_tc_used(g, S, S_max):
+    """Whether the PF likelihood runs on the tensor cores (k_kappa_tc) with its built-in
+    tiles: a shape the kernel takes (autotune.tensor_core_shape) and a column bucket equal
+    to the basis stride (S > 32 at stride 64, S > 24 at stride 32)."""
+    from paper_2604_19723_gb300 import autotune
+    if not autotune.tensor_core_shape(g, S_max):
         return False
-    rf = max(4 * 128 * 32, 2 * 128 * 32 + 2 * 2 * 64 * 32)   # one 128-particle tile per block
-    nf = g.Nf if g.Nf <= 16 else 0
-    smem = rf * 4 + 32 + g.Nz * 16 + 128 * 8 + (nf + g.My + g.Mz) * 128 * 8
-    return smem <= 227 * 1024
+    width = autotune.basis_stride(S_max)
+    return S > (32 if width == 64 else 24)
 
 
 def kappa_contraction_flops(P, S, J, Nz):
-    """The two contractions of the PF likelihood (psi^H V over 64 columns incl. r0, then
-    V conj(h) over the S-1 basis columns), 8 flops per complex multiply-add."""
-    return float(P) * S * J * (8 * Nz * 64 + 8 * Nz * (S - 1))
+    """The two contractions of the PF likelihood (psi^H V over the S-1 basis columns and
+    r0, then V conj(h) over the S-1 basis columns), 8 flops per complex multiply-add."""
+    return float(P) * S * J * (8 * Nz * S + 8 * Nz * (S - 1))
 
 
 def iota_flops(P, S, J, Nf, My, Mz):
@@ -398,7 +396,7 @@ def run_gpu(args, rank, world):
             # the same algorithmic flops against the nominal FP64 rate, the precision class the
             # log determinant needs (the kernel emulates it with FP32 operations)
             r["vs_fp64_nominal"] = {"peak": FP64_NOMINAL_TFLOPS, "frac": a / FP64_NOMINAL_TFLOPS}
-        if name == "k_kappa" and kappa_tc_used(g, S):
+        if name == "k_kappa" and kappa_tc_used(g, S, S_max):
             # both contractions run on the tensor cores in 3xTF32: each algorithmic flop is
             # three TF32 MMA flops, against the measured bf16 rate (sustained: the kernel runs
             # inside a long step) times the nominal TF32/BF16 ratio (1.1 / 2.25 PFLOP/s)

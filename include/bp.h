@@ -251,9 +251,12 @@ bp_status bp_get_profile(bp_handle* h, double* ms, int n);
  *                 frequency chunk; buckets <= 32 only, else 1 is used).
  *   kappa_fch     frequencies of V staged in shared memory per chunk (the Nz
  *                 tile), clamped to what fits.
- *   kappa_tc      1: the tensor-core PF likelihood wherever the shape allows it
- *                 (64 basis columns, 2 My Mz in {8, 16, 32});
- *                 -1: never.
+ *   kappa_tc      1: the tensor-core PF likelihood wherever the shape allows it,
+ *                 at the bucket equal to the basis stride (Mz even, and either
+ *                 64 basis columns with 2 My Mz in {8, 16, 32}, or 32 or 64
+ *                 columns with My Mz a multiple of 16, at least 32; shared
+ *                 memory within 227 KB); built-in (0): the same where the
+ *                 bucket is the stride; -1: never.
  *   table_chunk   particles per shared-memory chunk of the message table: 16,
  *                 32, 64 or 128 (clamped to what fits; built-in 64).
  *   table_split   particle splits of the message-table grid (>= 1; clamped to

@@ -70,10 +70,38 @@ def basis_stride(S_max: int) -> int:
     return 8 if S_max <= 8 else 16 if S_max <= 16 else 32 if S_max <= 32 else 64
 
 
+def tensor_core_large(geom) -> bool:
+    """The arrays whose tensor-core pass-1 rounds lie within one frequency (My Mz a
+    multiple of 16, at least 32); their kernel forms the steering elements as (hi, lo)
+    pairs in pass 2."""
+    nm = geom.My * geom.Mz
+    return nm >= 32 and nm % 16 == 0
+
+
+def tensor_core_smem(geom, width: int) -> int:
+    """Dynamic shared memory of the tensor-core PF likelihood (one 128-particle tile per
+    block; width = basis columns incl. r0): the operand region of either pass, barriers,
+    r0 per element, 1/lambda and y~0, the factors (frequency factors kept up to 16, and
+    never for the large arrays), and for the large arrays the low parts of a_z and the
+    (hi, lo) cis table."""
+    large = tensor_core_large(geom)
+    region = max(2 * 128 * 32 + 2 * (2 * width) * 32, 2 * 128 * 32 + 2 * 2 * 64 * 32)
+    nfac = (geom.Nf if geom.Nf <= 16 and not large else 0) + geom.My + geom.Mz
+    pairs = geom.Mz * 128 * 8 + 16 + 256 * 16 if large else 0
+    return region * 4 + 32 + geom.Nf * geom.My * geom.Mz * 16 + 2 * width * 8 + nfac * 128 * 8 + pairs
+
+
 def tensor_core_shape(geom, S_max: int) -> bool:
-    """Whether the tensor-core PF likelihood applies to this shape (64 basis columns,
-    2 My Mz in {8, 16, 32})."""
-    return basis_stride(S_max) == 64 and 2 * geom.My * geom.Mz in (8, 16, 32)
+    """Whether the tensor-core PF likelihood applies to this shape: Mz even and either
+    64 basis columns with 2 My Mz in {8, 16, 32} (a pass-1 round is whole frequencies) or
+    64 or 32 columns with My Mz a multiple of 16, at least 32 (a round is part of one
+    frequency); its shared memory within 227 KB.  It runs at the basis stride's width."""
+    width, nm = basis_stride(S_max), geom.My * geom.Mz
+    if geom.Mz % 2:
+        return False
+    whole = width == 64 and 2 * nm in (8, 16, 32)
+    part = width in (32, 64) and tensor_core_large(geom)
+    return (whole or part) and tensor_core_smem(geom, width) <= 227 * 1024
 
 
 def kappa_candidates(S: int, S_max: int, geom) -> List[Dict[str, int]]:
@@ -84,8 +112,9 @@ def kappa_candidates(S: int, S_max: int, geom) -> List[Dict[str, int]]:
     bks = [b for b in BUCKETS if S <= b <= top][:2]
     out = []
     for b in bks:
+        if b == top and tensor_core_shape(geom, S_max):
+            out.append(dict(kappa_sc=b, kappa_tc=1, kappa_blocks=0, kappa_fch=0))
         if b == 64 and tensor_core_shape(geom, S_max):
-            out.append(dict(kappa_sc=64, kappa_tc=1, kappa_blocks=0, kappa_fch=0))
             out.append(dict(kappa_sc=64, kappa_tc=-1, kappa_blocks=0, kappa_fch=0))
             continue
         for mb in ((1, 2) if b in (24, 32) else (0,)):

@@ -444,7 +444,7 @@ WsPlan ws_plan(const DevGeom& G, const DevParams& Pm, int SCA, int nsplit_max) {
     w.tab_part = take((size_t)nsplit_max * 3 * SM * J * Nz * 2 * sizeof(double));
     w.kV = take(SM * J * Nz * (size_t)SCA * sizeof(float2));
     w.kr0l = take(SM * J * Nz * sizeof(float2));
-    w.kB = kappa_tc_ok(G, SCA) ? take(kappa_btile_floats(G, S_max) * sizeof(float)) : take(0);
+    w.kB = kappa_tc_ok(G, SCA) ? take(kappa_btile_floats(G, S_max, SCA) * sizeof(float)) : take(0);
     w.red_part = take(nbel * 64 * RED_W * 2 * sizeof(double));
     w.gram = take(J * SM * SM * 2 * sizeof(double));
     w.V64 = take(SM * J * Nz * (size_t)SCA * 2 * sizeof(double));

@@ -400,7 +400,8 @@ struct DevState {
     float2* kV;       // [S_max][J][Nz][S_cap]   whitened basis, column S_cap-1 = r0 (FP32 part)
     float2* kr0l;     // [S_max][J][Nz]          low part of r0 (r0 = FP32 part + low part)
     float2* kdl;      // [S_max][J][S_cap]       1/lambda_c of the eigen-whitened basis (.x; zero-padded)
-    float* kB;        // [S_max][J][Nf][hi, lo][128 x 2 My Mz] TF32 B tiles of the tensor-core pass 1 (or null)
+    float* kB;        // TF32 B tiles of the tensor-core PF likelihood (or null): pass 1
+                      // [S][J][rounds][hi, lo][2 S_cap x 32], then pass 2 [S][J][groups][S_cap/16][hi, lo][64 x 32]
     int* kerr;        // nonzero after a bounded wait of a kernel gave up (reported by bp_estimate)
     float2* ky0;      // [S_max][J][S_cap]       y~0 = V^H e0 / eta_bar (zero-padded)
     double* kJ0;      // [S_max][J]              |r0|^2/eta_bar

@@ -224,7 +224,7 @@ KappaPlan plan_kappa(const DevGeom& G, const DevState& D, int S, int SCA, int t_
 void launch_kappa(const DevGeom& G, const DevParams& Pm, const DevState& D, int S, int SCA, const KappaPlan& k,
                   cudaStream_t st);
 bool kappa_tc_ok(const DevGeom& G, int SCA);
-size_t kappa_btile_floats(const DevGeom& G, int S_max);
+size_t kappa_btile_floats(const DevGeom& G, int S_max, int SCA);
 // operand tiles of both tensor-core passes of the PF likelihood; returns launches
 int launch_kappa_btile(const DevGeom& G, const DevState& D, int S, int SCA, cudaStream_t st);
 // MT likelihood of every particle (returns its launches): the FP32 warp kernel with

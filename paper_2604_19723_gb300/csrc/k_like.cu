@@ -358,18 +358,19 @@ __global__ void __launch_bounds__(256, MB) k_kappa(DevGeom G, DevParams Pm, DevS
 
 // ---------------------------------------------------------------- kappa on the tensor cores
 // Both contractions of k_kappa run as tcgen05.mma kind::tf32 in 3xTF32 (hi.hi + hi.lo +
-// lo.hi: FP32-level products, FP32 accumulation) with the 256 particles of a block as two
-// 128-row M tiles and TMEM accumulators whose lane is the particle:
-//   pass 1, per frequency f: A = psi (Re/Im interleaved), B = rows of [[Re V, Im V],
-//     [Im V, -Re V]] -> h = psi^H V (63 columns) and psi^H r0 in TMEM columns 0..127 of
-//     each tile's 256-column region;
-//   pass 2, per group of frequencies (up to 64 real outputs) and K chunk of 32:
+// lo.hi: FP32-level products, FP32 accumulation) with the 128 NT particles of a block as NT
+// 128-row M tiles and TMEM accumulators whose lane is the particle.  SW = 64 or 32 basis
+// columns (SW - 1 eigen-whitened columns and r0):
+//   pass 1, per round of 16 elements: A = psi (Re/Im interleaved), B = rows of
+//     [[Re V, Im V], [Im V, -Re V]] -> h = psi^H V (SW - 1 columns) and psi^H r0 in
+//     2 SW TMEM columns;
+//   pass 2, per group of 32 elements (up to 64 real outputs) and K chunk of 32:
 //     A = [Re h, Im h] (from registers), B = rows [[Re V, Im V]; [Im V, -Re V]] over the
 //     basis columns (r0 excluded) -> the chunk's part of V conj(h) = V V^H psi for the
 //     group's elements, real parts in columns [0, nk), imaginary parts in [nk, 2 nk) of
 //     the chunk's own 64-column accumulator.
 // Pass 2 is the one contraction whose rounding enters the likelihood at first order, so
-// its four K chunks accumulate apart (12 MMA accumulations each) and are added pairwise
+// its SW / 16 K chunks accumulate apart (12 MMA accumulations each) and are added pairwise
 // in FP32 when the element-wise float-float residual r = r0 - tau (psi - V V^H psi /
 // eta_bar) reads them back from TMEM, 8 elements at a time.  Operand tiles of B come
 // prebuilt (k_kappa_btile, k_kappa_btile2) by bulk copy; every mbarrier wait is bounded
@@ -377,57 +378,72 @@ __global__ void __launch_bounds__(256, MB) k_kappa(DevGeom G, DevParams Pm, DevS
 // flight land, frees TMEM and ends.
 constexpr int KAPPA_TC_WAIT = 1 << 20;
 constexpr int KAPPA_TC_KC2 = 32;   // real K per pass-2 chunk (16 basis columns)
-constexpr int KAPPA_TC_N2 = 64;    // pass-2 accumulator columns per chunk (4 chunks x 64 = 256 per tile)
+constexpr int KAPPA_TC_N2 = 64;    // pass-2 accumulator columns per chunk (SW / 16 chunks x 64 per tile)
 
-__host__ __device__ inline int kappa_tc_group_freqs(int Nm) { return KAPPA_TC_N2 / 2 / Nm; }
-__host__ __device__ inline int kappa_tc_groups(int Nf, int Nm) {
-    return (Nf + kappa_tc_group_freqs(Nm) - 1) / kappa_tc_group_freqs(Nm);
-}
+// The elements k = f Nm + y Mz + m (Nm = My Mz) are taken in ranges: pass 1 in rounds of
+// 16 (KAPPA_TC_KR real K), pass 2 in groups of 32 (up to 64 real outputs).  With
+// 2 My Mz in {8, 16, 32} a round is KR / (2 Nm) whole frequencies and a group 32 / Nm;
+// with Nm a multiple of 16 a round is part of one frequency.
+__host__ __device__ inline int kappa_tc_groups(int Nf, int Nm) { return (Nf * Nm + 31) / 32; }
 __host__ __device__ inline int round16(int x) { return (x + 15) & ~15; }
-// Pass 1 takes KAPPA_TC_KR real K per round: KR / (2 My Mz) frequencies.  Its two
-// accumulators alternate by round; every KAPPA_TC_SEG rounds of one (five when a round is
-// one frequency of the 4 x 4 URA, as validated at full size; else two, i.e. 24 MMA
-// accumulations, the chain that stayed within 1e-4) it is added into registers and
-// restarted.  Above KAPPA_TC_FLY_NF frequencies the frequency factors are formed when
-// used instead of being kept in shared memory.
+// Pass 1's two accumulators alternate by round; every KAPPA_TC_SEG rounds of one (five
+// when a round is one frequency of the 4 x 4 URA, as validated at full size; else two,
+// i.e. 24 MMA accumulations, the chain that stayed within 1e-4) it is added into
+// registers and restarted.  Above KAPPA_TC_FLY_NF frequencies the frequency factors are
+// formed when used instead of being kept in shared memory.
 constexpr int KAPPA_TC_KR = 32;
 constexpr int KAPPA_TC_FLY_NF = 16;
-__host__ __device__ inline int kappa_tc_f1(int Nm) { return KAPPA_TC_KR / (2 * Nm); }
-__host__ __device__ inline int kappa_tc_r1(int Nf, int Nm) { return (Nf + kappa_tc_f1(Nm) - 1) / kappa_tc_f1(Nm); }
+__host__ __device__ inline int kappa_tc_f1(int Nm) { return KAPPA_TC_KR / (2 * Nm); }   // 0 when Nm > 16
+__host__ __device__ inline int kappa_tc_r1(int Nf, int Nm) { return (Nf * Nm + 15) / 16; }
 __host__ __device__ inline int kappa_tc_seg(int Nm) { return 2 * Nm == KAPPA_TC_KR ? 5 : 2; }
-// operand region in floats: pass 1 A [NT][hi, lo][128 x KR] and one B slot [hi, lo][128 x KR];
-// pass 2 A [NT][hi, lo][128 x KC2] and two B slots [hi, lo][64 x KC2]
-__host__ __device__ inline int kappa_tc_region_floats(int KC, int NT) {
-    (void)KC;
-    const int r1 = (2 * NT + 2) * 128 * KAPPA_TC_KR, r2 = 2 * NT * 128 * KAPPA_TC_KC2 + 2 * 2 * KAPPA_TC_N2 * KAPPA_TC_KC2;
+// operand region in floats for SW basis columns (incl. r0): pass 1 A [NT][hi, lo][128 x KR]
+// and one B slot [hi, lo][2 SW x KR]; pass 2 A [NT][hi, lo][128 x KC2] and two B slots
+// [hi, lo][64 x KC2]
+__host__ __device__ inline int kappa_tc_region_floats(int SW, int NT) {
+    const int r1 = 2 * NT * 128 * KAPPA_TC_KR + 2 * (2 * SW) * KAPPA_TC_KR;
+    const int r2 = 2 * NT * 128 * KAPPA_TC_KC2 + 2 * 2 * KAPPA_TC_N2 * KAPPA_TC_KC2;
     return r1 > r2 ? r1 : r2;
 }
 
 // NT 128-particle M tiles per block (threads 128 NT, TMEM columns 256 NT): NT = 1 lets two
 // blocks share an SM, so that one block's MMAs run while the other writes operands or
 // evaluates its residuals.
-template <int NT>
+// LARGE: the arrays of My Mz >= 32 elements (a multiple of 16): pass-1 rounds within one
+// frequency, and pass 2 forms psi as a (hi, lo) pair (~1e-9) from factors evaluated by
+// cis_pair, with psi - V conj(h) / eta_bar taken exactly; at Nz = 1024 and 30 dB the FP32
+// steering values' few ulps, which enter the residual at first order, put 1.2e-4 on the PF
+// weights.  Its frequency factors are formed when used.
+template <int NT, int SW, bool LARGE>
 __global__ void __launch_bounds__(128 * NT, NT == 1 ? 2 : 1) k_kappa_tc(DevGeom G, DevParams Pm, DevState D, int S, int SCA,
                                                                      const float* __restrict__ Bt1,
                                                                      const float* __restrict__ Bt2) {
-    constexpr int KT = 128 * NT, NC = 63, KC2 = KAPPA_TC_KC2;
+    static_assert(SW == 64 || SW == 32, "basis width");
+    static_assert(SW == 64 || LARGE, "32 columns only for the large arrays");
+    constexpr int KT = 128 * NT, NC = SW - 1, KC2 = KAPPA_TC_KC2;
+    constexpr int N1 = 2 * SW;                                 // pass-1 accumulator columns
+    constexpr int NCH = SW / 16;                               // pass-2 K chunks
     extern __shared__ __align__(1024) float4 sm4[];
     const int s = blockIdx.y;
     const int P = Pm.P, J = G.J, Nz = G.Nz, Nm = G.My * G.Mz, Nf = G.Nf;
     const int KC = 2 * Nm;                                     // pass-1 real K per frequency
     constexpr int KR = KAPPA_TC_KR;                            // pass-1 real K per round
     const int F1 = kappa_tc_f1(Nm), R1 = kappa_tc_r1(Nf, Nm), SEG = kappa_tc_seg(Nm);
-    const bool fly = Nf > KAPPA_TC_FLY_NF;                     // frequency factors formed when used
-    const int GF = kappa_tc_group_freqs(Nm), NG = kappa_tc_groups(Nf, Nm);
-    const int RF = kappa_tc_region_floats(KC, NT);            // operand region (floats)
+    const bool fly = LARGE || Nf > KAPPA_TC_FLY_NF;            // frequency factors formed when used
+    const int NG = kappa_tc_groups(Nf, Nm);
+    const int RF = kappa_tc_region_floats(SW, NT);            // operand region (floats)
     float* sR = reinterpret_cast<float*>(sm4);
     uint64_t* mbar = reinterpret_cast<uint64_t*>(sR + RF);    // [3]: MMAs done, B slot 0, B slot 1 arrived
     uint32_t* tslot = reinterpret_cast<uint32_t*>(mbar + 3);
     float4* r0s = reinterpret_cast<float4*>(sR + RF + 8);    // [Nz] r0 (hi.x, hi.y, lo.x, lo.y)
-    float2* dls = reinterpret_cast<float2*>(r0s + Nz);        // [64] 1/lambda_c (.x)
-    float2* y0s = dls + 64;                                   // [64] y~0_c
-    float2* fac = y0s + 64;                                   // [nfac][KT]
+    float2* dls = reinterpret_cast<float2*>(r0s + Nz);        // [SW] 1/lambda_c (.x)
+    float2* y0s = dls + SW;                                   // [SW] y~0_c
+    float2* fac = y0s + SW;                                   // [nfac][KT]
+    // LARGE: [Mz][KT] low parts of a_z, then the (hi, lo) cis table [256] on a 16-byte boundary
+    float2* facl = fac + (size_t)((fly ? 0 : Nf) + G.My + G.Mz) * KT;
+    float4* ctab = reinterpret_cast<float4*>((reinterpret_cast<uintptr_t>(facl + (size_t)G.Mz * KT) + 15) &
+                                             ~(uintptr_t)15);
     const int tid = threadIdx.x, warp = tid >> 5, tile = tid >> 7, row = tid & 127;
+    if (LARGE) cis_table_fill(ctab, tid, KT);   // read after the first barrier of the j loop
     const int p = blockIdx.x * KT + tid;
     const bool act = p < P;
     const int pp = act ? p : 0;
@@ -440,13 +456,13 @@ __global__ void __launch_bounds__(128 * NT, NT == 1 ? 2 : 1) k_kappa_tc(DevGeom 
     tc::fence_before_sync();
     __syncthreads();
     tc::fence_after_sync();
-    // B operand stream (thread 0): pass 1 takes one slot of 2 x 128 x KR floats at
+    // B operand stream (thread 0): pass 1 takes one slot of 2 x N1 x KR floats at
     // sR + 2 NT 128 KR; pass 2 two slots of 2 x 64 x KC2 floats after its A tiles, so that
     // the copy of the next round's B runs under this round's MMAs.  A copy into a slot is
     // issued only once the MMAs that read the slot's previous contents have completed.
-    const size_t bchunk1 = (size_t)2 * 128 * KR;
+    const size_t bchunk1 = (size_t)2 * N1 * KR;
     const size_t bslot2 = (size_t)2 * KAPPA_TC_N2 * KC2;
-    const int NQ = 4 * NG;   // pass-2 rounds per j
+    const int NQ = NCH * NG;   // pass-2 rounds per j
     float* sB1 = sR + 2 * NT * 128 * KR;
     float* sB2 = sR + 2 * NT * 128 * KC2;
     auto issueB = [&](int sl, float* dst, const float* src, uint32_t bytes) {
@@ -466,7 +482,7 @@ __global__ void __launch_bounds__(128 * NT, NT == 1 ? 2 : 1) k_kappa_tc(DevGeom 
     auto b1_src = [&](int j, int r) { return Bt1 + (((size_t)s * J + j) * R1 + r) * bchunk1; };
     auto b2_src = [&](int j, int q) { return Bt2 + (((size_t)s * J + j) * NQ + q) * bslot2; };
     auto b2_bytes = [&](int q) {
-        const int g = q >> 2, nk = min(GF, Nf - g * GF) * Nm;
+        const int g = q / NCH, nk = min(32, Nz - 32 * g);
         return (uint32_t)(2 * (2 * round16(nk)) * KC2 * 4);
     };
     issueB(0, sB1, b1_src(0, 0), (uint32_t)(bchunk1 * 4));   // the first round's B, under the factor set-up
@@ -529,7 +545,7 @@ __global__ void __launch_bounds__(128 * NT, NT == 1 ? 2 : 1) k_kappa_tc(DevGeom 
         {
             const float2* gd = D.kdl + ((size_t)s * J + j) * SCA;
             const float2* gy = D.ky0 + ((size_t)s * J + j) * SCA;
-            for (int t = tid; t < 64; t += KT) { dls[t] = gd[t]; y0s[t] = gy[t]; }
+            for (int t = tid; t < SW; t += KT) { dls[t] = gd[t]; y0s[t] = gy[t]; }
         }
         __syncthreads();
         const double eb = D.eta_bar[j];
@@ -541,58 +557,111 @@ __global__ void __launch_bounds__(128 * NT, NT == 1 ? 2 : 1) k_kappa_tc(DevGeom 
         float2* fy = fb + (fly ? 0 : Nf) * KT;
         float2* fz = fy + G.My * KT;
         const float4 grec = geo_s[(size_t)j * P + pp];
+        const float2 grl = geol_s[(size_t)j * P + pp];
         float2 Fc;
-        if (fly) {
+        float Aamp = 0.f, ch0 = 0.f, cl0 = 0.f;   // LARGE: psi = A (b' kron a_y kron a_z), carrier in b'
+        float2* fzl = facl + tid;
+        // the phase of a_y (cycles, float-float) and its (hi, lo) pair
+        auto ay_phase = [&](int y, float& p, float& e) {
+            p = __fmul_rn(G.py_l[y], grec.z);
+            e = fmaf(G.py_l[y], grl.x, fmaf(G.py_lo[y], grec.z, fmaf(G.py_l[y], grec.z, -p)));
+        };
+        if (LARGE) {
+            Aamp = G.amp_c / (grec.x + grec.y);
+            ff_frac_mul2(grec.x, grec.y, G.inv_lam_hi, G.inv_lam_lo, ch0, cl0);
+            Fc = make_float2(Aamp, 0.f);   // cmul(Fc, b') = A b' exactly
+            float2 lo_unused;
+            for (int y = 0; y < G.My; ++y) {
+                float p, e;
+                ay_phase(y, p, e);
+                cis_pair(ctab, p, e, fy[y * KT], lo_unused);
+            }
+            for (int m = 0; m < G.Mz; ++m) {
+                const float p = __fmul_rn(G.pz_l[m], grec.w);
+                const float e = fmaf(G.pz_l[m], grl.y, fmaf(G.pz_lo[m], grec.w, fmaf(G.pz_l[m], grec.w, -p)));
+                cis_pair(ctab, p, e, fz[m * KT], fzl[m * KT]);
+            }
+        } else if (fly) {
             Fc = carrier_factor(G, grec);
-            array_factors(G, grec, geol_s[(size_t)j * P + pp], fy, fz, KT);
+            array_factors(G, grec, grl, fy, fz, KT);
         } else {
-            Fc = factors_from_geo(G, grec, geol_s[(size_t)j * P + pp], fb, fy, fz, KT);
+            Fc = factors_from_geo(G, grec, grl, fb, fy, fz, KT);
         }
-        // b_f as pass 1 and pass 2 both take it (the shared copy holds the same values)
-        auto bfac = [&](int f) { return fly ? freq_factor(G, grec, f) : fb[f * KT]; };
+        // b_f as pass 1 and pass 2 both take it (the shared copy holds the same values);
+        // LARGE: the high part of b'_f
+        auto bfac = [&](int f) {
+            if (LARGE) {
+                float2 bh, bl;
+                bprime_pair(G, ctab, grec.x, grec.y, ch0, cl0, f, bh, bl);
+                return bh;
+            }
+            return fly ? freq_factor(G, grec, f) : fb[f * KT];
+        };
         // h = psi^H V and pr = psi^H r0, summed over the pass-1 accumulator segments
         float2 h[NC];
         float2 pr = make_float2(0.f, 0.f);
         #pragma unroll
         for (int c = 0; c < NC; ++c) h[c] = make_float2(0.f, 0.f);
-        // adds the pass-1 accumulator at TMEM column base (128 columns: Re h 0..62, Re pr,
-        // Im h 0..62, Im pr) into h and pr
+        // adds the pass-1 accumulator at TMEM column base (N1 columns: Re h 0..NC-1, Re pr,
+        // Im h 0..NC-1, Im pr) into h and pr, 32 columns at a time
         auto absorb = [&](uint32_t base) {
-            uint32_t v[32];
-            tc::tmem_ld32(tlane + base + 0, v); tc::tmem_ld_wait();
             #pragma unroll
-            for (int i = 0; i < 32; ++i) h[i].x += __uint_as_float(v[i]);
-            tc::tmem_ld32(tlane + base + 32, v); tc::tmem_ld_wait();
-            #pragma unroll
-            for (int i = 0; i < 31; ++i) h[32 + i].x += __uint_as_float(v[i]);
-            pr.x += __uint_as_float(v[31]);
-            tc::tmem_ld32(tlane + base + 64, v); tc::tmem_ld_wait();
-            #pragma unroll
-            for (int i = 0; i < 32; ++i) h[i].y += __uint_as_float(v[i]);
-            tc::tmem_ld32(tlane + base + 96, v); tc::tmem_ld_wait();
-            #pragma unroll
-            for (int i = 0; i < 31; ++i) h[32 + i].y += __uint_as_float(v[i]);
-            pr.y += __uint_as_float(v[31]);
+            for (int part = 0; part < 2; ++part) {
+                #pragma unroll
+                for (int c0 = 0; c0 < SW; c0 += 32) {
+                    uint32_t v[32];
+                    tc::tmem_ld32(tlane + base + (uint32_t)(part * SW + c0), v);
+                    tc::tmem_ld_wait();
+                    #pragma unroll
+                    for (int i = 0; i < 32; ++i) {
+                        const float a = __uint_as_float(v[i]);
+                        if (c0 + i < NC) { if (part == 0) h[c0 + i].x += a; else h[c0 + i].y += a; }
+                        else             { if (part == 0) pr.x += a; else pr.y += a; }
+                    }
+                }
+            }
         };
-        // ---- pass 1: h = psi^H V, pr = psi^H r0, F1 frequencies per round
+        // ---- pass 1: h = psi^H V, pr = psi^H r0, 16 elements per round
         float nps = 0.f;
         {
             float* sA = sR;
             float* aHi = sA + (size_t)(tile * 2 + 0) * 128 * KR;
             float* aLo = sA + (size_t)(tile * 2 + 1) * 128 * KR;
-            const uint32_t idesc = tc::idesc_tf32_f32(128, 128);
-            // even rounds accumulate in columns 0..127, odd ones in 128..255; a segment of SEG
-            // rounds of one accumulator is added into h (after the MMAs of the previous round
-            // are done, before this round overwrites it); the first round's B was issued
-            // before this j began
+            const uint32_t idesc = tc::idesc_tf32_f32(128, N1);
+            // even rounds accumulate in columns 0..N1-1, odd ones in N1..2 N1-1; a segment of
+            // SEG rounds of one accumulator is added into h (after the MMAs of the previous
+            // round are done, before this round overwrites it); the first round's B was
+            // issued before this j began
             for (int r = 0; r < R1; ++r) {
                 const int q = r & 1;
                 const bool seg_start = ((r >> 1) % SEG) == 0;
-                round(0, sA, sB1, KR, (uint32_t)(128 * KR * 4), idesc, (uint32_t)(q * 128), !seg_start,
+                round(0, sA, sB1, KR, (uint32_t)(N1 * KR * 4), idesc, (uint32_t)(q * N1), !seg_start,
                       [&]() {
-                    if (seg_start && r >= 2) absorb((uint32_t)(q * 128));
+                    if (seg_start && r >= 2) absorb((uint32_t)(q * N1));
                     if (r > 0) issueB(0, sB1, b1_src(j, r), (uint32_t)(bchunk1 * 4));
                 }, [&]() {
+                    if constexpr (LARGE) {
+                        // Nm a multiple of 16: the round is elements 16 r .. 16 r + 15 of one
+                        // frequency, walked in pairs (m, m + 1) of a row (Mz even)
+                        const int k0 = r * 16, f = k0 / Nm, e0 = k0 - f * Nm;
+                        const float2 cb = cmul(Fc, bfac(f));
+                        int y = e0 / G.Mz, m = e0 - y * G.Mz;
+                        float2 w = cmul(cb, fy[y * KT]);
+                        #pragma unroll 1
+                        for (int l = 0; l < 16; l += 2) {
+                            const float2 p0 = cmul(w, fz[m * KT]), p1 = cmul(w, fz[(m + 1) * KT]);
+                            nps += p0.x * p0.x + p0.y * p0.y + p1.x * p1.x + p1.y * p1.y;
+                            const float4 hi = make_float4(tc::tf32_rn(p0.x), tc::tf32_rn(p0.y), tc::tf32_rn(p1.x),
+                                                          tc::tf32_rn(p1.y));
+                            const float4 lo = make_float4(tc::tf32_rn(p0.x - hi.x), tc::tf32_rn(p0.y - hi.y),
+                                                          tc::tf32_rn(p1.x - hi.z), tc::tf32_rn(p1.y - hi.w));
+                            const int off = tc::core_off(row, 2 * l, KR) >> 2;
+                            *reinterpret_cast<float4*>(aHi + off) = hi;
+                            *reinterpret_cast<float4*>(aLo + off) = lo;
+                            m += 2;
+                            if (m == G.Mz && l + 2 < 16) { m = 0; ++y; w = cmul(cb, fy[y * KT]); }
+                        }
+                    } else {
                     for (int i = 0; i < F1; ++i) {
                         const int f = r * F1 + i;
                         if (f >= Nf) {   // past the last frequency: zero operands
@@ -619,6 +688,7 @@ __global__ void __launch_bounds__(128 * NT, NT == 1 ? 2 : 1) k_kappa_tc(DevGeom 
                             }
                         }
                     }
+                    }
                 });
             }
         }
@@ -627,25 +697,23 @@ __global__ void __launch_bounds__(128 * NT, NT == 1 ? 2 : 1) k_kappa_tc(DevGeom 
         issueB(0, sB2, b2_src(j, 0), b2_bytes(0));
         issueB(1, sB2 + bslot2, b2_src(j, 1), b2_bytes(1));
         absorb(0);                       // the segments still in TMEM
-        if (R1 > 1) absorb(128);
-        {   // h and pr back into columns 0..127, where the amplitude loop reads them
-            uint32_t v[32];
+        if (R1 > 1) absorb((uint32_t)N1);
+        // h and pr back into columns 0..N1-1 (the accumulator layout), where the amplitude
+        // loop reads them
+        #pragma unroll
+        for (int part = 0; part < 2; ++part) {
             #pragma unroll
-            for (int i = 0; i < 32; ++i) v[i] = __float_as_uint(h[i].x);
-            tc::tmem_st32(tlane + 0, v);
-            #pragma unroll
-            for (int i = 0; i < 31; ++i) v[i] = __float_as_uint(h[32 + i].x);
-            v[31] = __float_as_uint(pr.x);
-            tc::tmem_st32(tlane + 32, v);
-            #pragma unroll
-            for (int i = 0; i < 32; ++i) v[i] = __float_as_uint(h[i].y);
-            tc::tmem_st32(tlane + 64, v);
-            #pragma unroll
-            for (int i = 0; i < 31; ++i) v[i] = __float_as_uint(h[32 + i].y);
-            v[31] = __float_as_uint(pr.y);
-            tc::tmem_st32(tlane + 96, v);
-            tc::tmem_st_wait();
+            for (int c0 = 0; c0 < SW; c0 += 32) {
+                uint32_t v[32];
+                #pragma unroll
+                for (int i = 0; i < 32; ++i) {
+                    const float2 a = (c0 + i < NC) ? h[c0 + i] : pr;
+                    v[i] = __float_as_uint(part == 0 ? a.x : a.y);
+                }
+                tc::tmem_st32(tlane + (uint32_t)(part * SW + c0), v);
+            }
         }
+        tc::tmem_st_wait();
         // tau (FP32; J is evaluated exactly at the tau used) and the O(S) amplitude sums
         float hh = 0.f;
         #pragma unroll
@@ -662,7 +730,7 @@ __global__ void __launch_bounds__(128 * NT, NT == 1 ? 2 : 1) k_kappa_tc(DevGeom 
             tf = make_float2((pr.x * ieb + af.x * iq) / den, (pr.y * ieb + af.y * iq) / den);
         }
         // amplitude terms in the eigenbasis (kappa_amp_terms), h read again from TMEM columns
-        // 0..127 (written back above) eight columns at a time: a rolled loop keeps the
+        // 0..N1-1 (written back above) eight columns at a time: a rolled loop keeps the
         // per-column code out of the instruction cache's way
         double dyd;
         float gg;
@@ -671,18 +739,18 @@ __global__ void __launch_bounds__(128 * NT, NT == 1 ? 2 : 1) k_kappa_tc(DevGeom 
             float g0 = 0.f, g1 = 0.f, q0 = 0.f, q1 = 0.f;
             ff G{0.f, 0.f};
             #pragma unroll 1
-            for (int c0 = 0; c0 < 64; c0 += 8) {
+            for (int c0 = 0; c0 < SW; c0 += 8) {
                 uint32_t a[8], b[8];
                 float hx[8], hy[8];
                 tc::tmem_ld8(tlane + (uint32_t)c0, a);
-                tc::tmem_ld8(tlane + (uint32_t)(64 + c0), b);
+                tc::tmem_ld8(tlane + (uint32_t)(SW + c0), b);
                 tc::tmem_ld_wait();
                 #pragma unroll
                 for (int i = 0; i < 8; ++i) { hx[i] = __uint_as_float(a[i]); hy[i] = __uint_as_float(b[i]); }
                 #pragma unroll
                 for (int i = 0; i < 8; ++i) {
                     const int c = c0 + i;
-                    if (c < NC) {   // column 63 holds psi^H r0
+                    if (c < NC) {   // column NC holds psi^H r0
                         if (i & 1) kappa_amp_col(G, g1, q1, y0s[c], dls[c].x, make_float2(hx[i], hy[i]), u);
                         else       kappa_amp_col(G, g0, q0, y0s[c], dls[c].x, make_float2(hx[i], hy[i]), u);
                     }
@@ -696,17 +764,16 @@ __global__ void __launch_bounds__(128 * NT, NT == 1 ? 2 : 1) k_kappa_tc(DevGeom 
         float pn = 0.f;
         tc::fence_before_sync();   // TMEM reads of h complete before pass 2 reuses the columns
         for (int g = 0; g < NG; ++g) {
-            const int f0 = g * GF, nfg = min(GF, Nf - f0);
-            const int nk = nfg * Nm, nkp = round16(nk), N2 = 2 * nkp;
+            const int k0 = 32 * g, nk = min(32, Nz - k0), nkp = round16(nk), N2 = 2 * nkp;
             float* sA = sR;
             float* aHi = sA + (size_t)(tile * 2 + 0) * 128 * KC2;
             float* aLo = sA + (size_t)(tile * 2 + 1) * 128 * KC2;
             const uint32_t idesc = tc::idesc_tf32_f32(128, N2);
             #pragma unroll
-            for (int kc = 0; kc < 4; ++kc) {
-                // round q = 4 g + kc reads slot q & 1 = kc & 1; the copy of round q + 1 goes to
-                // the slot that round q - 1 read
-                const int q = 4 * g + kc;
+            for (int kc = 0; kc < NCH; ++kc) {
+                // round q = NCH g + kc reads slot q & 1 = kc & 1 (NCH is even); the copy of
+                // round q + 1 goes to the slot that round q - 1 read
+                const int q = NCH * g + kc;
                 round(kc & 1, sA, sB2 + (size_t)(kc & 1) * bslot2, KC2, (uint32_t)(N2 * KC2 * 4), idesc,
                       (uint32_t)(kc * KAPPA_TC_N2), false, [&]() {
                     if (q >= 1 && q + 1 < NQ)
@@ -729,48 +796,75 @@ __global__ void __launch_bounds__(128 * NT, NT == 1 ? 2 : 1) k_kappa_tc(DevGeom 
             wait_mma();
             // every MMA of this j is done: the next j's first B tile, under the residuals
             if (g == NG - 1 && j + 1 < J) issueB(0, sB1, b1_src(j + 1, 0), (uint32_t)(bchunk1 * 4));
-            // element (f, y, m) of the group walked in order; w = Fc b_f a_y formed as pass 1 formed it
-            int cf = f0, cy = 0, cm = 0;
-            float2 w = cmul(cmul(Fc, bfac(f0)), fy[0]);
+            // element (f, y, m) of the group walked in order from k0; w = Fc b_f a_y formed as
+            // pass 1 formed it (LARGE: the pair (wh, wl) = A b'_f a_y from cis_pair factors)
+            int cf = k0 / Nm, cy = (k0 - cf * Nm) / G.Mz, cm = k0 - cf * Nm - cy * G.Mz;
+            float2 w = make_float2(0.f, 0.f), wh = w, wl = w;
+            auto set_w = [&]() {
+                if (LARGE) {
+                    float2 bh, bl, ayh, ayl;
+                    bprime_pair(G, ctab, grec.x, grec.y, ch0, cl0, cf, bh, bl);
+                    const float2 cbh = make_float2(Aamp * bh.x, Aamp * bh.y);
+                    const float2 cbl = make_float2(fmaf(Aamp, bh.x, -cbh.x) + Aamp * bl.x,
+                                                   fmaf(Aamp, bh.y, -cbh.y) + Aamp * bl.y);
+                    float p, e;
+                    ay_phase(cy, p, e);
+                    cis_pair(ctab, p, e, ayh, ayl);
+                    const float4 wp = cpair_mul(cbh, cbl, ayh, ayl);
+                    wh = make_float2(wp.x, wp.y);
+                    wl = make_float2(wp.z, wp.w);
+                } else {
+                    w = cmul(cmul(Fc, bfac(cf)), fy[cy * KT]);
+                }
+            };
+            set_w();
             for (int b = 0; b < nk; b += 8) {
-                // the four chunk accumulators, added pairwise: (a0 + a1) + (a2 + a3)
+                // the chunk accumulators, added pairwise: (a0 + a1) [+ (a2 + a3)]
                 float vre[8], vim[8];
-                {
+                #pragma unroll
+                for (int c2 = 0; c2 < NCH; c2 += 2) {
                     uint32_t r0[8], r1[8], i0[8], i1[8];
-                    tc::tmem_ld8(tlane + (uint32_t)b, r0);
-                    tc::tmem_ld8(tlane + (uint32_t)(KAPPA_TC_N2 + b), r1);
-                    tc::tmem_ld8(tlane + (uint32_t)(nkp + b), i0);
-                    tc::tmem_ld8(tlane + (uint32_t)(KAPPA_TC_N2 + nkp + b), i1);
+                    tc::tmem_ld8(tlane + (uint32_t)(c2 * KAPPA_TC_N2 + b), r0);
+                    tc::tmem_ld8(tlane + (uint32_t)((c2 + 1) * KAPPA_TC_N2 + b), r1);
+                    tc::tmem_ld8(tlane + (uint32_t)(c2 * KAPPA_TC_N2 + nkp + b), i0);
+                    tc::tmem_ld8(tlane + (uint32_t)((c2 + 1) * KAPPA_TC_N2 + nkp + b), i1);
                     tc::tmem_ld_wait();
                     #pragma unroll
                     for (int i = 0; i < 8; ++i) {
-                        vre[i] = __uint_as_float(r0[i]) + __uint_as_float(r1[i]);
-                        vim[i] = __uint_as_float(i0[i]) + __uint_as_float(i1[i]);
-                    }
-                    tc::tmem_ld8(tlane + (uint32_t)(2 * KAPPA_TC_N2 + b), r0);
-                    tc::tmem_ld8(tlane + (uint32_t)(3 * KAPPA_TC_N2 + b), r1);
-                    tc::tmem_ld8(tlane + (uint32_t)(2 * KAPPA_TC_N2 + nkp + b), i0);
-                    tc::tmem_ld8(tlane + (uint32_t)(3 * KAPPA_TC_N2 + nkp + b), i1);
-                    tc::tmem_ld_wait();
-                    #pragma unroll
-                    for (int i = 0; i < 8; ++i) {
-                        vre[i] += __uint_as_float(r0[i]) + __uint_as_float(r1[i]);
-                        vim[i] += __uint_as_float(i0[i]) + __uint_as_float(i1[i]);
+                        const float ar = __uint_as_float(r0[i]) + __uint_as_float(r1[i]);
+                        const float ai = __uint_as_float(i0[i]) + __uint_as_float(i1[i]);
+                        if (c2 == 0) { vre[i] = ar; vim[i] = ai; }
+                        else         { vre[i] += ar; vim[i] += ai; }
                     }
                 }
                 #pragma unroll
                 for (int i = 0; i < 8; ++i) {
                     const int kl = b + i;
                     if (kl >= nk) break;
-                    const int k = f0 * Nm + kl;
-                    const float2 ps = cmul(w, fz[cm * KT]);   // psi_k exactly as pass 1 formed it
+                    const int k = k0 + kl;
+                    float2 ps;         // psi_k exactly as pass 1 formed it
+                    float4 psp;        // LARGE: psi_k as a (hi, lo) pair
+                    if (LARGE) psp = cpair_mul(wh, wl, fz[cm * KT], fzl[cm * KT]);
+                    else       ps = cmul(w, fz[cm * KT]);
                     if (++cm == G.Mz) {
                         cm = 0;
                         if (++cy == G.My) { cy = 0; ++cf; }
-                        if (kl + 1 < nk) w = cmul(cmul(Fc, bfac(cf)), fy[cy * KT]);
+                        if (kl + 1 < nk) set_w();
                     }
                     const float vsx = vre[i], vsy = vim[i];
-                    const float2 pp2 = make_float2(ps.x - vsx * ieb, ps.y - vsy * ieb);
+                    float2 pp2, ppl = make_float2(0.f, 0.f);
+                    if (LARGE) {
+                        // psi_perp = psi - V V^H psi / eta_bar with the product by 1/eta_bar and
+                        // the subtraction taken exactly; its low part ppl
+                        const float dxh = vsx * ieb, dyh = vsy * ieb;
+                        const float dxl = fmaf(vsx, ieb, -dxh), dyl = fmaf(vsy, ieb, -dyh);
+                        two_sum(psp.x, -dxh, pp2.x, ppl.x);
+                        two_sum(psp.y, -dyh, pp2.y, ppl.y);
+                        ppl.x += psp.z - dxl;
+                        ppl.y += psp.w - dyl;
+                    } else {
+                        pp2 = make_float2(ps.x - vsx * ieb, ps.y - vsy * ieb);
+                    }
                     pn += pp2.x * pp2.x + pp2.y * pp2.y;
                     // t = tau pp2 exactly: re = p1 - p2, im = p3 + p4 (+ FMA errors)
                     const float p1 = __fmul_rn(tf.x, pp2.x), e1 = fmaf(tf.x, pp2.x, -p1);
@@ -786,6 +880,10 @@ __global__ void __launch_bounds__(128 * NT, NT == 1 ? 2 : 1) k_kappa_tc(DevGeom 
                     two_sum(r0.y, -p3, sy, ey1);
                     two_sum(sy, -p4, ry.hi, ey2);
                     ry.lo = __fsub_rn(__fadd_rn(r0.w, __fadd_rn(ey1, ey2)), __fadd_rn(e3, e4));
+                    if (LARGE) {
+                        rx.lo = fmaf(-tf.x, ppl.x, fmaf(tf.y, ppl.y, rx.lo));    // - Re(tau psi_perp,lo)
+                        ry.lo = fmaf(-tf.x, ppl.y, fmaf(-tf.y, ppl.x, ry.lo));   // - Im(tau psi_perp,lo)
+                    }
                     ff_acc_sq(rr, make_float2(rx.hi, ry.hi));
                     rr.lo = fmaf(2.0f * rx.hi, rx.lo, fmaf(2.0f * ry.hi, ry.lo, rr.lo));
                 }
@@ -1479,51 +1577,53 @@ __global__ void k_nu(DevGeom G, DevParams Pm, DevState D, int S) {
     D.lw_eta[(size_t)j * P + p] = lnu;
 }
 
-// B tiles of the tensor-core pass 1, once per (s, j, round r of F1 frequencies): rows n of
-// [[Re V, Im V], [Im V, -Re V]]^T (n < 64: Re h_n, n >= 64: Im h_{n-64}) against the real
-// K index KC i + 2e + part of the round's frequency i and its elements e (part 0 = Re psi,
-// 1 = Im psi; zero past the last frequency), split into TF32 high and low parts, in the
-// K-major core-matrix layout; [hi, lo] per round.
+// B tiles of the tensor-core pass 1, once per (s, j, round r of elements 16 r .. 16 r + 15):
+// rows n of [[Re V, Im V], [Im V, -Re V]]^T (n < SW: Re h_n, n >= SW: Im h_{n-SW}, SW = SCA
+// basis columns incl. r0) against the real K index 2 e + part of the round's element e
+// (part 0 = Re psi, 1 = Im psi; zero past the last element), split into TF32 high and low
+// parts, in the K-major core-matrix layout; [hi, lo] per round.
 __global__ void k_kappa_btile(DevGeom G, DevState D, int SCA, float* __restrict__ Bt) {
     constexpr int KR = KAPPA_TC_KR;
     const int s = blockIdx.x, j = blockIdx.y, r = blockIdx.z;
-    const int J = G.J, Nz = G.Nz, Nm = G.My * G.Mz, KC = 2 * Nm;
-    const int F1 = kappa_tc_f1(Nm), R1 = kappa_tc_r1(G.Nf, Nm);
+    const int J = G.J, Nz = G.Nz, Nm = G.My * G.Mz, N1 = 2 * SCA;
+    const int R1 = kappa_tc_r1(G.Nf, Nm);
     const float2* V = D.kV + ((size_t)s * J + j) * Nz * SCA;
-    float* out = Bt + (((size_t)s * J + j) * R1 + r) * 2 * 128 * KR;
-    for (int t = threadIdx.x; t < 128 * KR; t += blockDim.x) {
+    float* out = Bt + (((size_t)s * J + j) * R1 + r) * 2 * N1 * KR;
+    for (int t = threadIdx.x; t < N1 * KR; t += blockDim.x) {
         const int n = t / KR, kk = t - n * KR;
-        const int i = kk / KC, kk2 = kk - i * KC, f = r * F1 + i;
-        const int e = kk2 >> 1, part = kk2 & 1;
-        const float2 v = (f < G.Nf) ? V[(size_t)(f * Nm + e) * SCA + (n & 63)] : make_float2(0.f, 0.f);
-        const float b = (n < 64) ? (part == 0 ? v.x : v.y) : (part == 0 ? v.y : -v.x);
+        const int k = r * 16 + (kk >> 1), part = kk & 1;
+        const int c = n < SCA ? n : n - SCA;
+        const float2 v = (k < Nz) ? V[(size_t)k * SCA + c] : make_float2(0.f, 0.f);
+        const float b = (n < SCA) ? (part == 0 ? v.x : v.y) : (part == 0 ? v.y : -v.x);
         const float hi = tc::tf32_rn(b);
         const int off = tc::core_off(n, kk, KR) >> 2;
         out[off] = hi;
-        out[128 * KR + off] = tc::tf32_rn(b - hi);
+        out[N1 * KR + off] = tc::tf32_rn(b - hi);
     }
 }
 
-// B tiles of the tensor-core pass 2, once per (s, j, group g of frequencies, K chunk kc):
-// rows n < nkp are the real parts, rows nkp <= n < 2 nkp the imaginary parts of the
-// group's elements e (rows past the group's nk elements are zero), against the real K
-// index 2 (c - 16 kc) + part of basis columns c (part 0 = Re h_c, 1 = Im h_c; the r0
-// column 63 excluded): Re row [Re V_ec, Im V_ec], Im row [Im V_ec, -Re V_ec]; TF32 hi/lo,
-// K-major core-matrix layout, [hi, lo] per slot of 2 x 64 x 32 floats.
+// B tiles of the tensor-core pass 2, once per (s, j, group g of elements 32 g .. 32 g + 31,
+// K chunk kc of SCA / 16): rows n < nkp are the real parts, rows nkp <= n < 2 nkp the
+// imaginary parts of the group's elements e (rows past the group's nk elements are zero),
+// against the real K index 2 (c - 16 kc) + part of basis columns c (part 0 = Re h_c,
+// 1 = Im h_c; the r0 column SCA - 1 excluded): Re row [Re V_ec, Im V_ec], Im row
+// [Im V_ec, -Re V_ec]; TF32 hi/lo, K-major core-matrix layout, [hi, lo] per slot of
+// 2 x 64 x 32 floats.
 __global__ void k_kappa_btile2(DevGeom G, DevState D, int SCA, float* __restrict__ Bt2) {
     constexpr int KC2 = KAPPA_TC_KC2;
-    const int s = blockIdx.x, j = blockIdx.y, g = blockIdx.z >> 2, kc = blockIdx.z & 3;
-    const int J = G.J, Nz = G.Nz, Nm = G.My * G.Mz, GF = kappa_tc_group_freqs(Nm), NG = kappa_tc_groups(G.Nf, Nm);
-    const int f0 = g * GF, nk = min(GF, G.Nf - f0) * Nm, nkp = round16(nk), N2 = 2 * nkp;
+    const int NCH = SCA / 16;
+    const int s = blockIdx.x, j = blockIdx.y, g = blockIdx.z / NCH, kc = blockIdx.z - g * NCH;
+    const int J = G.J, Nz = G.Nz, Nm = G.My * G.Mz, NG = kappa_tc_groups(G.Nf, Nm);
+    const int k0 = 32 * g, nk = min(32, Nz - k0), nkp = round16(nk), N2 = 2 * nkp;
     const float2* V = D.kV + ((size_t)s * J + j) * Nz * SCA;
-    float* out = Bt2 + ((((size_t)s * J + j) * NG + g) * 4 + kc) * (size_t)(2 * KAPPA_TC_N2 * KC2);
+    float* out = Bt2 + ((((size_t)s * J + j) * NG + g) * NCH + kc) * (size_t)(2 * KAPPA_TC_N2 * KC2);
     for (int t = threadIdx.x; t < N2 * KC2; t += blockDim.x) {
         const int n = t / KC2, kk = t - n * KC2;
         const bool im = n >= nkp;
         const int e = im ? n - nkp : n;
         const int c = kc * 16 + (kk >> 1), part = kk & 1;
         float2 v = make_float2(0.f, 0.f);
-        if (e < nk && c < 63) v = V[(size_t)(f0 * Nm + e) * SCA + c];
+        if (e < nk && c < SCA - 1) v = V[(size_t)(k0 + e) * SCA + c];
         const float b = im ? (part == 0 ? v.y : -v.x) : (part == 0 ? v.x : v.y);
         const float hi = tc::tf32_rn(b);
         const int off = tc::core_off(n, kk, KC2) >> 2;
@@ -1532,40 +1632,53 @@ __global__ void k_kappa_btile2(DevGeom G, DevState D, int SCA, float* __restrict
     }
 }
 
-// dynamic shared memory of k_kappa_tc: the operand region (pass 1: A [NT][hi, lo][128 x 2Nm],
-// B [hi, lo][128 x 2Nm]; pass 2: A [NT][hi, lo][128 x 32], two B slots [hi, lo][64 x 32]), barriers,
-// r0 (hi, lo) per element, 1/lambda_c and y~0_c, and the factors of 256 particles
+// dynamic shared memory of k_kappa_tc: the operand region (pass 1: A [NT][hi, lo][128 x 32],
+// B [hi, lo][2 SW x 32]; pass 2: A [NT][hi, lo][128 x 32], two B slots [hi, lo][64 x 32]),
+// barriers, r0 (hi, lo) per element, 1/lambda_c and y~0_c, and the factors of 128 NT particles
 constexpr int KAPPA_TC_NT = 1;   // M tiles per block of the launched variant
-static size_t kappa_tc_smem(const DevGeom& G, int NT = KAPPA_TC_NT) {
-    const size_t Nm = (size_t)G.My * G.Mz;
-    const size_t nfac = (size_t)(G.Nf > KAPPA_TC_FLY_NF ? 0 : G.Nf) + G.My + G.Mz;
-    const size_t rf = (size_t)kappa_tc_region_floats(2 * (int)Nm, NT);
-    return rf * sizeof(float) + 32 + (size_t)G.Nz * sizeof(float4) + 128 * sizeof(float2) +
-           nfac * 128 * NT * sizeof(float2);
-}
-// The tensor-core variant applies with 64 basis columns (SCA = 64), 2 My Mz in {8, 16, 32}
-// and its shared memory within the opt-in limit.  The tensor core adds each MMA's result
-// into its FP32 accumulator (no FMA chain): with 75 frequencies of the 2 x 2 URA in one
-// pass-1 accumulator (225 accumulations) the PF weights moved by 1.7e-4 (measured), with 24
-// they stayed within 1e-4; hence the segments of KAPPA_TC_SEG rounds.
-bool kappa_tc_ok(const DevGeom& G, int SCA) {
-    const int KC = 2 * G.My * G.Mz;
-    return SCA == 64 && (KC == 8 || KC == 16 || KC == 32) && kappa_tc_smem(G) <= 227 * 1024;
-}
-static size_t kappa_btile1_floats(const DevGeom& G, int S_max) {
-    return (size_t)S_max * G.J * kappa_tc_r1(G.Nf, G.My * G.Mz) * 2 * 128 * KAPPA_TC_KR;
-}
-size_t kappa_btile_floats(const DevGeom& G, int S_max) {
+static bool kappa_tc_large(const DevGeom& G) {
     const int Nm = G.My * G.Mz;
-    return kappa_btile1_floats(G, S_max) +
-           (size_t)S_max * G.J * kappa_tc_groups(G.Nf, Nm) * 4 * (2 * KAPPA_TC_N2 * KAPPA_TC_KC2);
+    return Nm >= 32 && Nm % 16 == 0;
+}
+static size_t kappa_tc_smem(const DevGeom& G, int SW, int NT = KAPPA_TC_NT) {
+    const bool large = kappa_tc_large(G);
+    const size_t nfac = (size_t)(large || G.Nf > KAPPA_TC_FLY_NF ? 0 : G.Nf) + G.My + G.Mz;
+    const size_t rf = (size_t)kappa_tc_region_floats(SW, NT);
+    const size_t pairs = large ? (size_t)G.Mz * 128 * NT * sizeof(float2) + 16 + 256 * sizeof(float4) : 0;
+    return rf * sizeof(float) + 32 + (size_t)G.Nz * sizeof(float4) + 2 * (size_t)SW * sizeof(float2) +
+           nfac * 128 * NT * sizeof(float2) + pairs;
+}
+// The tensor-core variant applies to
+//   * 64 basis columns (SCA = 64) with 2 My Mz in {8, 16, 32} (a pass-1 round is whole
+//     frequencies), and
+//   * 64 or 32 basis columns with My Mz a multiple of 16, at least 32 (a round is part of
+//     one frequency; the large arrays, whose CUDA-core kernel stages few frequencies),
+// both with Mz even (a pass-1 round writes the pairs (m, m + 1) of a row) and the shared
+// memory within the opt-in limit.  The tensor core adds each MMA's result into its FP32
+// accumulator (no FMA chain): with 75 frequencies of the 2 x 2 URA in one pass-1
+// accumulator (225 accumulations) the PF weights moved by 1.7e-4 (measured), with 24 they
+// stayed within 1e-4; hence the segments of KAPPA_TC_SEG rounds.
+bool kappa_tc_ok(const DevGeom& G, int SCA) {
+    const int Nm = G.My * G.Mz, KC = 2 * Nm;
+    if (G.Mz % 2 != 0) return false;
+    const bool whole = SCA == 64 && (KC == 8 || KC == 16 || KC == 32);
+    const bool part = (SCA == 64 || SCA == 32) && kappa_tc_large(G);
+    return (whole || part) && kappa_tc_smem(G, SCA) <= 227 * 1024;
+}
+static size_t kappa_btile1_floats(const DevGeom& G, int S_max, int SCA) {
+    return (size_t)S_max * G.J * kappa_tc_r1(G.Nf, G.My * G.Mz) * 2 * (2 * SCA) * KAPPA_TC_KR;
+}
+size_t kappa_btile_floats(const DevGeom& G, int S_max, int SCA) {
+    const int Nm = G.My * G.Mz;
+    return kappa_btile1_floats(G, S_max, SCA) +
+           (size_t)S_max * G.J * kappa_tc_groups(G.Nf, Nm) * (SCA / 16) * (2 * KAPPA_TC_N2 * KAPPA_TC_KC2);
 }
 int launch_kappa_btile(const DevGeom& G, const DevState& D, int S, int SCA, cudaStream_t st) {
     if (!D.kB || !kappa_tc_ok(G, SCA)) return 0;
     const int Nm = G.My * G.Mz;
     k_kappa_btile<<<dim3(S, G.J, kappa_tc_r1(G.Nf, Nm)), 256, 0, st>>>(G, D, SCA, D.kB);
-    k_kappa_btile2<<<dim3(S, G.J, kappa_tc_groups(G.Nf, Nm) * 4), 256, 0, st>>>(G, D, SCA,
-                                                                                D.kB + kappa_btile1_floats(G, S));
+    k_kappa_btile2<<<dim3(S, G.J, kappa_tc_groups(G.Nf, Nm) * (SCA / 16)), 256, 0, st>>>(
+        G, D, SCA, D.kB + kappa_btile1_floats(G, S, SCA));
     return 2;
 }
 
@@ -1589,11 +1702,12 @@ KappaPlan plan_kappa(const DevGeom& G, const DevState& D, int S, int SCA, int t_
     KappaPlan k{};
     // the bucket: the requested one where it holds S and fits the basis stride, else the
     // smallest that holds S; the tensor-core kernel where allowed and not declined
+    // (the kernel's width is the basis stride: 64, or 32 for the large arrays)
     const bool tc_shape = D.kB && kappa_tc_ok(G, SCA);
     if (kappa_sc_valid(t_sc) && t_sc >= S && t_sc <= SCA) k.sc = t_sc;
     else if (S > 32 && tc_shape && t_tc >= 0) k.sc = 64;
     else k.sc = S <= 8 ? 8 : S <= 16 ? 16 : S <= 24 ? 24 : S <= 32 ? 32 : S <= 48 ? 48 : 64;
-    k.tc = k.sc == 64 && tc_shape && t_tc >= 0;
+    k.tc = k.sc == SCA && tc_shape && t_tc >= 0;
     if (k.tc) return k;
     k.mb = (k.sc <= 16) ? 2 : (t_mb == 2 && k.sc <= 32 ? 2 : 1);
     const size_t fixed = kappa_smem_fixed(G, k.sc), per_f = kappa_smem_per_f(G, k.sc);
@@ -1618,9 +1732,18 @@ void launch_kappa(const DevGeom& G, const DevParams& Pm, const DevState& D, int 
                   cudaStream_t st) {
     if (k.tc) {
         constexpr int NT = KAPPA_TC_NT;
-        smem_allow_max((const void*)k_kappa_tc<NT>);
-        k_kappa_tc<NT><<<dim3((Pm.P + 128 * NT - 1) / (128 * NT), S), 128 * NT, kappa_tc_smem(G), st>>>(
-            G, Pm, D, S, SCA, D.kB, D.kB + kappa_btile1_floats(G, S));
+        const dim3 grid((Pm.P + 128 * NT - 1) / (128 * NT), S);
+        const float* bt2 = D.kB + kappa_btile1_floats(G, S, SCA);
+        if (!kappa_tc_large(G)) {
+            smem_allow_max((const void*)k_kappa_tc<NT, 64, false>);
+            k_kappa_tc<NT, 64, false><<<grid, 128 * NT, kappa_tc_smem(G, 64), st>>>(G, Pm, D, S, SCA, D.kB, bt2);
+        } else if (SCA == 64) {
+            smem_allow_max((const void*)k_kappa_tc<NT, 64, true>);
+            k_kappa_tc<NT, 64, true><<<grid, 128 * NT, kappa_tc_smem(G, 64), st>>>(G, Pm, D, S, SCA, D.kB, bt2);
+        } else {
+            smem_allow_max((const void*)k_kappa_tc<NT, 32, true>);
+            k_kappa_tc<NT, 32, true><<<grid, 128 * NT, kappa_tc_smem(G, 32), st>>>(G, Pm, D, S, SCA, D.kB, bt2);
+        }
         return;
     }
     switch (k.sc * 4 + k.mb) {

@@ -3,9 +3,9 @@ SNR 30 dB, 500 unmodelled spurious paths per step, against the FP64 oracle throu
 C ABI, with every output's error printed (and recorded in the design notes).
 
 At 30 dB and Nz = 1024 the quadratic forms reach ~Nz (1 + SNR) ~ 1e6 noise units, the
-regime where FP32 log-likelihoods lose their digits; this shape also takes the CUDA-core
-PF likelihood (2 My Mz = 128 is outside the tensor-core kernel's operand shapes) with
-frequency-chunked staging, and the 32-row variant of the FP32 MT kernel.
+regime where FP32 log-likelihoods lose their digits; this shape also takes the 32-column
+tensor-core PF likelihood with pass-1 rounds of a quarter frequency (the 8 x 8 URA's 64
+elements per frequency), and the 32-row variant of the FP32 MT kernel.
 
   * test_stress_shape_stagewise: the full stage-wise parity at P = 1000 (ragged over the
     256-particle tiles), the oracle evaluating every particle (Woodbury form).

@@ -3,7 +3,8 @@
   * the tile fields are validated on the host;
   * every candidate the tuner measures (PF-likelihood column buckets S~ = 16, 24, 32, 48,
     64, one or two blocks per SM, a quarter frequency chunk, tensor-core kernel on or
-    off; message-table particle chunks) gives the FP64 oracle's update within the
+    off, at 64 columns and, for arrays of 32 or more elements, at 32; message-table
+    particle chunks) gives the FP64 oracle's update within the
     parity tolerances (Supplementary Sec. S-V: the PF message kappa~ in the
     eigen-whitened basis does not depend on how its columns are tiled);
   * the tuner keeps the measured minimum and leaves it on the filter;
@@ -33,6 +34,8 @@ CASES = [
     (dict(J=4, Nf=20, My=2, Mz=2), 20, 20, 333, 62),     # buckets 24, 32; two blocks per SM
     (dict(J=4, Nf=10, My=4, Mz=4), 40, 64, 257, 63),     # bucket 48, 64 on the tensor cores or not
     (dict(J=4, Nf=75, My=2, Mz=2), 40, 40, 256, 64),     # buckets 48, 64 (CUDA-core), frequency chunks
+    (dict(J=4, Nf=6, My=4, Mz=8), 40, 64, 300, 65),      # 4 x 8 array: tensor-core rounds of half a frequency
+    (dict(J=4, Nf=3, My=8, Mz=8), 28, 32, 300, 66),      # 8 x 8 array: the 32-column tensor-core kernel or not
 ]
 
 
