@@ -194,6 +194,48 @@ def _check(lib, h, status, what):
         raise BPError(status, f"{what}: {msg.decode() if msg else ''}")
 
 
+def device_array_problem(is_tensor: bool, is_cuda: bool, on_current_device: bool, contiguous: bool, dtype: str,
+                         shape: tuple, want_dtypes: tuple, want_floats: int, want_cols: Optional[int] = None
+                         ) -> Optional[str]:
+    """Why an array cannot be handed to the library as a raw device pointer, or None.
+    The library reads exactly want_floats FP32 values from it (a complex64 element is
+    two) and cannot check the buffer itself: it must be a contiguous CUDA tensor on the
+    current device, of one of want_dtypes, with want_floats values (and want_cols
+    columns, for a row-major matrix)."""
+    if not is_tensor:
+        return "expected a torch tensor"
+    if not is_cuda:
+        return "expected a CUDA tensor (the library reads device memory)"
+    if not on_current_device:
+        return "the tensor is on another device than the current one"
+    if dtype not in want_dtypes:
+        return f"dtype {dtype}, expected one of {', '.join(want_dtypes)}"
+    if not contiguous:
+        return "expected a contiguous tensor"
+    n = 1
+    for d in shape:
+        n *= int(d)
+    floats = 2 * n if dtype == "complex64" else n
+    if floats != want_floats:
+        return f"{floats} FP32 values, expected {want_floats}"
+    if want_cols is not None and (len(shape) != 2 or int(shape[1]) != want_cols):
+        return f"shape {tuple(shape)}, expected (rows, {want_cols})"
+    return None
+
+
+def _device_array(t, what: str, want_dtypes: tuple, want_floats: int, want_cols: Optional[int] = None) -> None:
+    """Raises BPError(BP_ERR_INVALID_ARG) when device_array_problem finds t unfit."""
+    import torch
+    is_tensor = isinstance(t, torch.Tensor)
+    problem = device_array_problem(
+        is_tensor, is_tensor and t.is_cuda,
+        is_tensor and t.is_cuda and t.get_device() == torch.cuda.current_device(),
+        is_tensor and t.is_contiguous(), str(t.dtype).replace("torch.", "") if is_tensor else "",
+        tuple(t.shape) if is_tensor else (), want_dtypes, want_floats, want_cols)
+    if problem:
+        raise BPError(1, f"{what}: {problem}")
+
+
 def _stream_handle(stream) -> Optional[int]:
     if stream is None:
         import torch
@@ -234,6 +276,7 @@ class Filter:
 
     def update(self, z):
         """z: torch CUDA tensor of J x Nz complex64 (or J x Nz x 2 float32), contiguous."""
+        _device_array(z, "bp_update: z", ("complex64", "float32"), 2 * self.geom.J * self.geom.Nz)
         _check(self.lib, self.h, self.lib.bp_update(self.h, C.c_void_p(z.data_ptr())), "bp_update")
 
     def step(self, z):
@@ -532,6 +575,7 @@ class Batch:
     def step(self, z):
         """z: torch CUDA float32 tensor of z_floats() values (the scenarios' J x Nz complex
         observations concatenated in scenario order)."""
+        _device_array(z, "bp_batch_step: z", ("float32", "complex64"), self.z_floats())
         self._check(self.lib.bp_batch_step(self.b, C.c_void_p(z.data_ptr())), "bp_batch_step")
 
     def sync(self):
@@ -626,6 +670,7 @@ class Mlp:
     def forward(self, X):
         import torch
         X = X.contiguous()
+        _device_array(X, "bp_mlp_forward: X", ("float32",), X.numel(), MLP_IN)
         Y = torch.empty((X.shape[0], MLP_OUT), dtype=torch.float32, device=X.device)
         self._check(self.lib.bp_mlp_forward(self.h, C.c_void_p(X.data_ptr()), X.shape[0], C.c_void_p(Y.data_ptr())),
                     "bp_mlp_forward")
@@ -635,6 +680,8 @@ class Mlp:
         """(gradient of the mean loss, summed loss) without changing the parameters."""
         import torch
         X, T = X.contiguous(), T.contiguous()
+        _device_array(X, "bp_mlp_grads: X", ("float32",), X.numel(), MLP_IN)
+        _device_array(T, "bp_mlp_grads: T", ("float32",), 3 * X.shape[0], 3)
         g = torch.empty(MLP_NPARAM, dtype=torch.float32, device=X.device)
         l = torch.empty(1, dtype=torch.float32, device=X.device)
         self._check(self.lib.bp_mlp_grads(self.h, C.c_void_p(X.data_ptr()), C.c_void_p(T.data_ptr()), X.shape[0],
@@ -642,6 +689,10 @@ class Mlp:
         return g.cpu().numpy(), float(l.item())
 
     def train_step(self, X, T, lr: float, loss_out=None):
+        _device_array(X, "bp_mlp_train_step: X", ("float32",), X.numel() if hasattr(X, "numel") else -1, MLP_IN)
+        _device_array(T, "bp_mlp_train_step: T", ("float32",), 3 * X.shape[0], 3)
+        if loss_out is not None:
+            _device_array(loss_out, "bp_mlp_train_step: loss_out", ("float32",), 1)
         self._check(self.lib.bp_mlp_train_step(self.h, C.c_void_p(X.data_ptr()), C.c_void_p(T.data_ptr()),
                                                X.shape[0], C.c_float(lr),
                                                C.c_void_p(loss_out.data_ptr() if loss_out is not None else None)),
